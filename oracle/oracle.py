@@ -1,0 +1,228 @@
+"""ctypes front end of the FP64 C oracle (``gs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  Arrays are
+numpy float64; parameters use the [D][n] structure-of-arrays layout of
+``synth.scenes``.  Functions follow GS-Scale §2.4 (render steps 1-5), Eq. 1
+(eager Adam) and Eqs. 2-3 with the pseudocode of Fig. 10 (deferred Adam).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+c_i64, c_i32, c_dbl = C.c_int64, C.c_int32, C.c_double
+P_DBL = C.POINTER(C.c_double)
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("R", c_dbl * 9), ("t", c_dbl * 3), ("fx", c_dbl), ("fy", c_dbl), ("cx", c_dbl),
+                ("cy", c_dbl), ("near_z", c_dbl), ("far_z", c_dbl), ("width", c_i32),
+                ("height", c_i32), ("tile_w", c_i32), ("tile_h", c_i32)]
+
+
+SPLAT = np.dtype([("keep", "<i4"), ("rect", "<i4", 4), ("clampx", "<i4"), ("clampy", "<i4"),
+                  ("rgb_clamped", "<i4", 3), ("pad", "<i4"), ("depth", "<f8"), ("mean2d", "<f8", 2),
+                  ("cov2d", "<f8", 3), ("conic", "<f8", 3), ("radius", "<f8"), ("opacity", "<f8"),
+                  ("rgb", "<f8", 3), ("margin", "<f8"), ("depth_f32", "<f8")], align=True)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        _lib.orc_count_keys.restype = c_i64
+        _lib.orc_loss_l1.restype = c_dbl
+        _lib.orc_splat_size.restype = C.c_int
+        _lib.orc_num_threads.restype = C.c_int
+        assert _lib.orc_splat_size() == SPLAT.itemsize, "splat layout mismatch"
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def n_params(deg: int) -> int:
+    return 11 + 3 * (deg + 1) ** 2
+
+
+def camera(cam, tile=(16, 16)) -> OrcCamera:
+    """Convert a ``synth.scenes.Camera`` (float64 fields) to the oracle's struct."""
+    c = OrcCamera()
+    R = np.asarray(cam.R, np.float64).reshape(9)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(cam.t[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_z, c.far_z = float(cam.near), float(cam.far)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
+    return c
+
+
+def tiles_of(oc: OrcCamera):
+    return (oc.width + oc.tile_w - 1) // oc.tile_w, (oc.height + oc.tile_h - 1) // oc.tile_h
+
+
+def _f64(params) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+
+
+def project(params, deg: int, oc: OrcCamera) -> np.ndarray:
+    """Step 1 of §2.4 for every Gaussian: returns the SPLAT record array."""
+    P = _f64(params)
+    n = P.shape[1]
+    out = np.zeros(n, SPLAT)
+    lib().orc_project(c_i64(n), C.c_int(deg), _p(P), c_i64(n), C.byref(oc), _p(out))
+    return out
+
+
+def build_lists(splats: np.ndarray, oc: OrcCamera):
+    """Step 2 of §2.4: sorted (tile, Gaussian id) keys and per-tile ranges."""
+    n = splats.shape[0]
+    K = lib().orc_count_keys(c_i64(n), _p(splats))
+    tx, ty = tiles_of(oc)
+    key_tile = np.zeros(max(K, 1), np.int32)
+    key_gid = np.zeros(max(K, 1), np.int64)
+    ranges = np.zeros(2 * tx * ty, np.int64)
+    lib().orc_build_lists(c_i64(n), _p(splats), C.byref(oc), _p(key_tile), _p(key_gid), _p(ranges))
+    return key_tile[:K], key_gid[:K], ranges.reshape(-1, 2)
+
+
+def composite(splats, oc: OrcCamera, key_gid, ranges, bg=(0.0, 0.0, 0.0)):
+    """Step 3 of §2.4.  Returns image [3][H][W], contributor counts, final T,
+    the per-pixel decision margin and a hash of each pixel's contributor
+    sequence (ids and alpha-clamp states)."""
+    H, W = oc.height, oc.width
+    img = np.zeros((3, H, W))
+    ncon = np.zeros((H, W), np.int32)
+    Tf = np.zeros((H, W))
+    mg = np.zeros((H, W))
+    hs = np.zeros((H, W), np.uint64)
+    bgv = np.asarray(bg, np.float64)
+    kg = np.ascontiguousarray(key_gid, np.int64)
+    rg = np.ascontiguousarray(ranges, np.int64)
+    lib().orc_composite(c_i64(splats.shape[0]), _p(splats), C.byref(oc), _p(kg), _p(rg), _p(bgv),
+                        _p(img), _p(ncon), _p(Tf), _p(mg), _p(hs))
+    return img, ncon, Tf, mg, hs
+
+
+def composite_brute(splats, oc: OrcCamera, bg=(0.0, 0.0, 0.0)):
+    img = np.zeros((3, oc.height, oc.width))
+    bgv = np.asarray(bg, np.float64)
+    lib().orc_composite_brute(c_i64(splats.shape[0]), _p(splats), C.byref(oc), _p(bgv), _p(img))
+    return img
+
+
+def loss_l1(image, target):
+    """Step 4 of §2.4 with L1: (loss, dL/dimage)."""
+    img = np.ascontiguousarray(image, np.float64)
+    tgt = np.ascontiguousarray(target, np.float64)
+    d = np.zeros_like(img)
+    loss = lib().orc_loss_l1(c_i64(img.size), _p(img), _p(tgt), _p(d))
+    return loss, d
+
+
+def backward(params, deg, oc, splats, key_gid, ranges, dimage, bg=(0.0, 0.0, 0.0)):
+    """Step 5 of §2.4: dL/dparams [D][n] and the per-Gaussian screen-space
+    sums [n][9] = (mean2d x, y, conic A, B, C, opacity, r, g, b)."""
+    P = _f64(params)
+    D, n = P.shape
+    grad = np.zeros((D, n))
+    sg = np.zeros((n, 9))
+    bgv = np.asarray(bg, np.float64)
+    di = np.ascontiguousarray(dimage, np.float64)
+    lib().orc_backward(c_i64(n), C.c_int(deg), _p(P), c_i64(n), C.byref(oc), _p(splats),
+                       _p(np.ascontiguousarray(key_gid, np.int64)),
+                       _p(np.ascontiguousarray(ranges, np.int64)), _p(bgv), _p(di), _p(grad), _p(sg))
+    return grad, sg
+
+
+def render(params, deg, cam, tile=(16, 16), bg=(0.0, 0.0, 0.0)):
+    """Project, build lists and composite one view."""
+    oc = camera(cam, tile)
+    sp = project(params, deg, oc)
+    kt, kg, rg = build_lists(sp, oc)
+    img, ncon, Tf, mg, hs = composite(sp, oc, kg, rg, bg)
+    return dict(cam=oc, splats=sp, key_tile=kt, key_gid=kg, ranges=rg, image=img, n_contrib=ncon,
+                T_final=Tf, margin=mg, decision_hash=hs)
+
+
+def render_loss_backward(params, deg, cam, target, tile=(16, 16)):
+    """One forward + L1 loss + backward; returns the render dict plus loss and grads."""
+    r = render(params, deg, cam, tile)
+    loss, dimg = loss_l1(r["image"], target)
+    grad, sg = backward(params, deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], dimg)
+    r.update(loss=loss, dimage=dimg, grad=grad, splat_grad=sg)
+    return r
+
+
+def sh_basis(deg, direction):
+    Y = np.zeros(16)
+    dY = np.zeros(48)
+    d = np.ascontiguousarray(direction, np.float64)
+    lib().orc_sh_basis(C.c_int(deg), _p(d), _p(Y), _p(dY))
+    return Y, dY.reshape(16, 3)
+
+
+# ---------------------------------------------------------------- Adam
+
+class AdamHyper:
+    def __init__(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15):
+        self.lr = np.full(6, lr, np.float64) if np.isscalar(lr) else np.asarray(lr, np.float64)
+        self.beta1, self.beta2, self.eps, self.max_defer = beta1, beta2, eps, max_defer
+
+
+def adam_eager(w, m, v, g, t, hp: AdamHyper):
+    """Eq. 1 at step t on every value (in place)."""
+    D, n = w.shape
+    lib().orc_adam_eager(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v),
+                         _p(np.ascontiguousarray(g, np.float64)), C.c_int(t), _p(hp.lr),
+                         c_dbl(hp.beta1), c_dbl(hp.beta2), c_dbl(hp.eps))
+
+
+def adam_lut(t, lr, hp: AdamHyper):
+    K = hp.max_defer + 1
+    pl, ml, vl = np.zeros(K), np.zeros(K), np.zeros(K)
+    lib().orc_adam_lut(C.c_int(t), c_dbl(lr), c_dbl(hp.beta1), c_dbl(hp.beta2), C.c_int(hp.max_defer),
+                       _p(pl), _p(ml), _p(vl))
+    return pl, ml, vl
+
+
+def adam_deferred(w, m, v, counter, ids, g_compact, t, hp: AdamHyper, mode=0, geo_eager=False):
+    """Deferred update at step t (in place).  mode 0: lookup tables (Eq. 3),
+    mode 1: exact replay of the zero-gradient steps."""
+    D, n = w.shape
+    ids = np.ascontiguousarray(ids, np.int32)
+    gc = np.ascontiguousarray(g_compact, np.float64).reshape(D, ids.shape[0])
+    assert counter.dtype == np.uint8
+    lib().orc_adam_deferred(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v), _p(counter), _p(ids),
+                            c_i64(ids.shape[0]), _p(gc), C.c_int(t), _p(hp.lr), c_dbl(hp.beta1),
+                            c_dbl(hp.beta2), c_dbl(hp.eps), C.c_int(hp.max_defer), C.c_int(mode),
+                            C.c_int(int(geo_eager)))
+
+
+def adam_materialize(w, m, v, counter, t_done, hp: AdamHyper, mode=0, geo_eager=False):
+    D, n = w.shape
+    wo, mo, vo = np.zeros_like(w), np.zeros_like(m), np.zeros_like(v)
+    lib().orc_adam_materialize(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v), _p(counter),
+                               C.c_int(t_done), _p(hp.lr), c_dbl(hp.beta1), c_dbl(hp.beta2),
+                               c_dbl(hp.eps), C.c_int(hp.max_defer), C.c_int(mode),
+                               C.c_int(int(geo_eager)), _p(wo), _p(mo), _p(vo))
+    return wo, mo, vo
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def depth_bits(depth_f64) -> np.ndarray:
+    return np.asarray(depth_f64, np.float64).astype(np.float32).view(np.uint32)
+
+
