@@ -1,0 +1,368 @@
+"""Benchmark of the 3DGS training hot path (GS-Scale, arXiv 2509.15645) on B300.
+
+One step = one training iteration on one view: frustum cull of all Gaussians,
+gather with deferred restore, tile rasterizer forward + L1 loss + backward,
+deferred Adam (gs_step, replayed as a CUDA graph).  Workload: 10M Gaussians
+on a 1x1 km aerial heightfield, SH degree 3, 1920x1080 nadir-to-oblique
+views, FP32 (synthetic, seeded; see synth/scenes.py).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3DGS train steps/s at 10M Gaussians 1080p; cull+Adam HBM GB/s vs peak"
+UNIT = "steps/s"
+WORKLOAD = "aerial10m_1080p_sh3"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- workload
+
+def build_workload(n, n_views, seed_views=2):
+    from synth import scenes
+    cfg = scenes.cfg_aerial(n=n, n_views=n_views, seed_views=seed_views)
+    tgt_scene = scenes.heightfield_scene(n, seed=1, half_extent=cfg["half_extent"], amplitude=20.0,
+                                         wavelength=(100.0, 125.0), n_clusters=200)
+    return cfg, tgt_scene
+
+
+def algorithmic_bytes(N, D, n_vis, n_upd, n_restore):
+    """Bytes the method must move per launch (roofline section)."""
+    cull = 40.0 * N + 1.0 * N + 80.0 * n_restore + N / 8.0 + 4.0 * N / 2048.0
+    apply = 24.0 * D * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 2.0 * n_upd
+    select = 2.0 * N + N / 4.0
+    return cull, apply, select
+
+
+def run_ours(args):
+    import torch
+    import paper_2509_15645_b300 as gs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    N = args.gaussians
+    cfg, tgt_params = build_workload(N, args.views, seed_views=2 + rank)
+    cams = cfg["cams"]
+    deg = cfg["sh_degree"]
+    D = 11 + 3 * (deg + 1) ** 2
+    H, W = cams[0].height, cams[0].width
+
+    ctx = gs.Context(max_gaussians=N, max_visible=int(N * 0.6), max_keys=80_000_000, max_width=W, max_height=H,
+                     tile=(16, 16), max_views=1, max_sh_degree=deg, device=local)
+    # targets: the seed-1 scene rendered by the same library (setup, untimed)
+    tscene = gs.GaussianScene(tgt_params, deg, device=dev, with_optimizer=False)
+    del tgt_params
+    targets = []
+    for cam in cams:
+        ids, nv = ctx.cull(tscene, cam)
+        targets.append(ctx.render_fwd(tscene, cam, ids, nv).clone())
+    ctx.sync_status()
+    del tscene
+    scene = gs.GaussianScene(cfg["scene"], deg, device=dev)
+    del cfg["scene"]
+    torch.cuda.empty_cache()
+    adam = gs.adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15)
+    loss = torch.zeros(1, device=dev)
+    stream = torch.cuda.current_stream()
+
+    K, Wm = args.steps, args.warmup
+    tcap = max(Wm + K, 16) + 8
+    ctx.timing_enable(tcap)
+    for s in range(Wm):
+        v = s % len(cams)
+        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
+    ctx.sync_status()
+    ctx.timing_read(tcap)            # discard warm-up timings
+
+    # ---- timed region: inputs resident in HBM (params 2.4 GB > L2: no flush needed)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(K):
+        v = (Wm + s) % len(cams)
+        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    spans = ctx.timing_read(tcap)
+    ctx.sync_status()
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * K / (ms_total / 1e3)
+    kernels = ctx.step_kernel_count()
+
+    # ---- counts per view (untimed pass over the same views) for the algorithmic bytes
+    stats = []
+    for s in range(len(cams)):
+        v = (Wm + K + s) % len(cams)
+        n_restore_geo = int((scene.counter[:N] > 0).sum().item())
+        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
+        c = ctx.counters().cpu().tolist()
+        stats.append((c[0], c[1], c[2], n_restore_geo))
+    ctx.timing_read(tcap)
+    n_vis = float(np.mean([x[0] for x in stats]))
+    n_keys = float(np.mean([x[1] for x in stats]))
+    n_upd = float(np.mean([x[2] for x in stats]))
+    n_rest = float(np.mean([x[3] for x in stats]))
+    b_cull, b_apply, b_select = algorithmic_bytes(N, D, n_vis, n_upd, n_rest)
+
+    def avg(k):
+        vals = [sp[k] for sp in spans if sp[k] >= 0]
+        return float(np.mean(vals)) if vals else None
+
+    st = {k: avg(k) for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply")}
+    peak, peak_src = _peaks()
+    gbs = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms else None
+    cull_gbs, apply_gbs = gbs(b_cull, st["cull"]), gbs(b_apply, st["adam_apply"])
+    adam_stage_gbs = gbs(b_apply + b_select, st["adam"])
+    ca_gbs = gbs(b_cull + b_apply + b_select, (st["cull"] or 0) + (st["adam"] or 0))
+    # dominant kernel of the memory-bound pair for the roofline line
+    dom = ("adam_apply", b_apply, st["adam_apply"]) if (st["adam_apply"] or 0) >= (st["cull"] or 0) else \
+        ("cull", b_cull, st["cull"])
+    roof = {"kernel": {"adam_apply": "k_adam_apply", "cull": "k_cull"}[dom[0]], "bound": "hbm",
+            "achieved": round(gbs(dom[1], dom[2]), 1), "peak": peak, "unit": "GB/s",
+            "frac": round(gbs(dom[1], dom[2]) / peak, 4), "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": round(dom[1]), "traffic": None}
+
+    # ---- end to end through the public API: target H2D from pinned host memory,
+    # gs_step, loss D2H, every step
+    host_t = [t.cpu().pin_memory() for t in targets]
+    dev_t = torch.empty_like(targets[0])
+    host_loss = torch.zeros(1).pin_memory()
+    for s in range(2):
+        dev_t.copy_(host_t[s % len(cams)], non_blocking=True)
+        ctx.step(scene, [cams[s % len(cams)]], [dev_t], adam, loss=loss)
+        host_loss.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    ctx.timing_read(tcap)
+    ctx.timing_enable(0)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.step(scene, [cams[0]], [dev_t], adam, loss=loss)        # re-capture without timing nodes
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for s in range(K):
+        v = s % len(cams)
+        dev_t.copy_(host_t[v], non_blocking=True)
+        ctx.step(scene, [cams[v]], [dev_t], adam, loss=loss)
+        host_loss.copy_(loss, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    ctx.sync_status()
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": round(ms_total / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
+        "config": {"workload": WORKLOAD, "gaussians": N, "image": f"{W}x{H}", "sh_degree": deg,
+                   "views_per_step": 1, "form": "plain_fp32", "adam": "deferred", "tile": "16x16",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (parameters+moments 7.1 GB), no flush",
+                   "visible_per_view": round(n_vis), "keys_per_view": round(n_keys), "update_set": round(n_upd)},
+        "roofline": roof,
+        "cull_adam": {"cull_gbs": cull_gbs and round(cull_gbs, 1), "adam_apply_gbs": apply_gbs and round(apply_gbs, 1),
+                      "adam_stage_gbs": adam_stage_gbs and round(adam_stage_gbs, 1),
+                      "cull_plus_adam_gbs": ca_gbs and round(ca_gbs, 1), "peak_gbs": peak,
+                      "cull_plus_adam_frac": ca_gbs and round(ca_gbs / peak, 4)},
+        "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in st.items()},
+        "e2e": {"value": round(world * K / (e2e_ms / 1e3), 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
+        "clocks": clk,
+        "gpu_launches": int(kernels * K),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, sample_frac=0.1)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- oracle (CPU)
+
+def _oracle_step(orc, P, deg, cam, target, W_, M_, V_, C_, t, hp):
+    r = orc.render_loss_backward(P if W_ is None else W_, deg, cam, target)
+    kept = np.nonzero(r["splats"]["keep"])[0].astype(np.int32)
+    orc.adam_deferred(W_, M_, V_, C_, kept, r["grad"][:, kept], t, hp)
+    return r["loss"], kept.size
+
+
+def oracle_sample(frac, seed=0):
+    """A random `frac` of the workload's Gaussians (oracle baseline sample)."""
+    from synth import scenes
+    cfg = scenes.cfg_aerial(n=10_000_000, n_views=16, seed_views=2)
+    P = cfg["scene"]
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(P.shape[1], int(P.shape[1] * frac), replace=False))
+    Ps = np.ascontiguousarray(P[:, sel]).astype(np.float64)
+    del P, cfg["scene"]
+    return Ps, cfg
+
+
+def cpu_baseline(args, sample_frac=0.1, steps=1):
+    from oracle import oracle as orc
+    Ps, cfg = oracle_sample(sample_frac)
+    deg = cfg["sh_degree"]
+    cam = cfg["cams"][0]
+    target = np.zeros((3, cam.height, cam.width))
+    W_, M_, V_ = Ps.copy(), np.zeros_like(Ps), np.zeros_like(Ps)
+    C_ = np.zeros(Ps.shape[1], np.uint8)
+    hp = orc.AdamHyper(lr=1e-3, eps=1e-15)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        _oracle_step(orc, Ps, deg, cam, target, W_, M_, V_, C_, s + 1, hp)
+    dt = (time.perf_counter() - t0) / steps
+    scale = 1.0 / sample_frac
+    return {"value": round(1.0 / (dt * scale), 6), "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle step (cull+render+L1+backward+deferred Adam) on a random {sample_frac:.0%} of the "
+                      f"10M Gaussians, one 1920x1080 view, {steps} step(s); time scaled linearly by "
+                      f"{scale:.0f}x to the full Gaussian count",
+            "seconds_per_sample_step": round(dt, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    frac = 0.02
+    Ps, cfg = oracle_sample(frac)
+    deg = cfg["sh_degree"]
+    cams = cfg["cams"]
+    W_, M_, V_ = Ps.copy(), np.zeros_like(Ps), np.zeros_like(Ps)
+    C_ = np.zeros(Ps.shape[1], np.uint8)
+    hp = orc.AdamHyper(lr=1e-3, eps=1e-15)
+    target = np.zeros((3, cams[0].height, cams[0].width))
+    for s in range(args.warmup):
+        _oracle_step(orc, Ps, deg, cams[s % len(cams)], target, W_, M_, V_, C_, s + 1, hp)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        _oracle_step(orc, Ps, deg, cams[(args.warmup + s) % len(cams)], target, W_, M_, V_, C_,
+                     args.warmup + s + 1, hp)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / (dt / frac)
+    sample = (f"FP64 oracle step on a random {frac:.0%} of the 10M Gaussians, one 1920x1080 view per step; "
+              f"time scaled linearly by {1 / frac:.0f}x")
+    out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / value, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded aerial heightfield)", "impl": "reference",
+           "config": {"workload": WORKLOAD, "gaussians": 10_000_000, "image": "1920x1080", "sh_degree": 3,
+                      "views_per_step": 1, "form": "fp64 oracle"},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--gaussians", type=int, default=10_000_000)
+    ap.add_argument("--views", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * gs_b300.h -- C ABI of the B300 (sm_103a) 3D Gaussian Splatting training hot path.
+ *
+ * Method: GS-Scale (arXiv 2509.15645).  One training iteration (§2.4, steps 1-6)
+ * is: frustum cull of every Gaussian -> gather of the visible subset (with the
+ * deferred-update restore of §4.3.3 applied on the fly) -> differentiable tile
+ * rasterizer (EWA projection, tile keys, key sort, front-to-back alpha
+ * compositing, and its adjoint) -> deferred Adam (Eqs. 2-3, Fig. 10, §4.3.2).
+ *
+ * Conventions for every call
+ *  - Pointers marked "device" point to CUDA device memory on the context's
+ *    device; "host" pointers to ordinary host memory.  The caller owns every
+ *    buffer it passes; the context owns only its scratch workspace.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and never synchronises, except
+ *    gs_sync_status and gs_create/gs_destroy.  A context must be driven from
+ *    one stream at a time.
+ *  - Invalid arguments return GS_ERR_INVALID_ARG before anything is launched;
+ *    a failed launch returns GS_ERR_CUDA.  Errors found on the device (a
+ *    capacity overflow, a non-finite loss) are latched in a device status word
+ *    and returned by the next gs_sync_status.  Nothing traps or asserts.
+ *  - Counts that depend on the data (the number of visible Gaussians, the
+ *    number of tile keys) stay on the device; kernels read them there, so a
+ *    whole step can be captured in a CUDA graph.
+ *
+ * Parameter layout (§2.3: 59 parameters per Gaussian at SH degree 3):
+ * structure of arrays, plane r of Gaussian i at [r * pitch + i]:
+ *   geo  rows 0..2 mean, 3..5 log-scale, 6..9 quaternion (w,x,y,z),
+ *        10 opacity logit                                  (11 planes, fp32)
+ *   sh   row 3k + c = SH coefficient k of colour c,  k < (L+1)^2
+ *                                                    (3 (L+1)^2 planes)
+ * D = 11 + 3 (L+1)^2 (14 at degree 0, 59 at degree 3).  Optimizer moments
+ * m, v use the same D planes in the same order (geo planes first, then sh).
+ * Compact per-visible-Gaussian arrays use planes of pitch `cap` (a capacity):
+ * [r * cap + k] for the k-th visible Gaussian.
+ */
+#ifndef GS_B300_H
+#define GS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,
+    GS_ERR_OOM = 2,
+    GS_ERR_CUDA = 3,
+    GS_ERR_BUDGET = 4,
+    GS_ERR_CAPACITY = 5,   /* more visible Gaussians or tile keys than the context holds */
+    GS_ERR_TIMEOUT = 6,
+    GS_ERR_NUMERIC = 7     /* non-finite loss */
+} gs_status;
+
+/* Storage precision of SH planes and of the moments m, v. */
+enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1 };
+
+/* Adam variants: deferred with the restore tables of Fig. 10 (the method) or
+ * eager (Eq. 1 on every Gaussian each step: the baseline the paper improves). */
+enum { GS_ADAM_DEFERRED = 0, GS_ADAM_EAGER = 2 };
+
+typedef struct gs_ctx gs_ctx;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  R is the
+ * world->camera rotation (row-major), t the translation: p_cam = R mu + t.
+ * Pixel (i, j) has its centre at (i + 0.5, j + 0.5). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_z, far_z;
+    int32_t width, height;
+} gs_camera;
+
+/* A Gaussian set with its optimizer state (all device pointers). */
+typedef struct {
+    int64_t n;             /* number of Gaussians (< 2^31) */
+    int64_t pitch;         /* elements between planes, >= n, multiple of 4 */
+    int32_t sh_degree;     /* 0..3 */
+    int32_t precision;     /* GS_FP32 or GS_BF16_SH_MOM (sh, m, v stored as bf16) */
+    float *geo;            /* [11][pitch] fp32 */
+    void *sh;              /* [3 (L+1)^2][pitch] fp32 or bf16 */
+    void *m;               /* [D][pitch] fp32 or bf16, NULL = no optimizer state (render only) */
+    void *v;               /* [D][pitch] */
+    uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
+    int32_t step;          /* optimizer steps completed; the next step is step + 1 */
+    int32_t reserved;
+} gs_scene;
+
+/* Adam hyper-parameters (§4.3.2).  lr per parameter group:
+ * 0 mean, 1 log-scale, 2 quaternion, 3 opacity, 4 SH DC, 5 SH rest. */
+typedef struct {
+    float lr[6];
+    float beta1, beta2, eps;
+    int32_t max_defer;     /* MAX of the counter, at most 15 (4-bit counter) */
+    int32_t mode;          /* GS_ADAM_DEFERRED or GS_ADAM_EAGER */
+    int32_t reserved;
+} gs_adam_cfg;
+
+/* Context capacities, fixed at creation. */
+typedef struct {
+    int64_t max_gaussians;   /* largest scene n */
+    int64_t max_visible;     /* capacity of the compact visible set per view */
+    int64_t max_keys;        /* capacity of (tile, Gaussian) keys per view */
+    int32_t max_width, max_height;
+    int32_t tile_w, tile_h;  /* raster tile; tile_w * tile_h in {64, 128, 256} */
+    int32_t max_views;       /* views per gs_step, 1..8 */
+    int32_t max_sh_degree;   /* 0..3 */
+} gs_config;
+
+/* ------------------------------------------------------------------ context */
+
+/* Bytes of device workspace a context with this configuration needs. */
+GS_API gs_status gs_workspace_size(const gs_config *cfg, size_t *bytes);
+
+/* Create a context on `device`.  `workspace` (device, >= gs_workspace_size
+ * bytes, 256-byte aligned) is borrowed for the context's lifetime; pass NULL
+ * to let the context allocate it itself.  *out receives the handle. */
+GS_API gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *workspace, size_t workspace_bytes);
+
+/* Release the context (and the workspace it allocated, if any). */
+GS_API gs_status gs_destroy(gs_ctx *ctx);
+
+/* Text of the last error recorded on this context (never NULL). */
+GS_API const char *gs_last_error(const gs_ctx *ctx);
+
+/* Synchronise `stream`, then return and clear the first error latched on the
+ * device since the last call (GS_OK if none). */
+GS_API gs_status gs_sync_status(gs_ctx *ctx, void *stream);
+
+/* Device pointer to the context's int32 counters: [0] visible count of the
+ * last gs_cull, [1] key count of the last render, [2] update-set size of the
+ * last deferred Adam step. */
+GS_API const int32_t *gs_device_counters(const gs_ctx *ctx);
+
+/* ------------------------------------------------------------------ hot path */
+
+/* Frustum cull (§2.4 step 1; done on the GPU as in §4.2.1).  For every
+ * Gaussian: 3D near/far test, EWA projection of its covariance, 3-sigma radius
+ * and tile rectangle, and the 2D image-bounds test.  If `adam` is non-NULL and
+ * the scene has optimizer state, the geometry is first restored with the
+ * deferred-update tables of the coming step (§4.3.3), without modifying it.
+ * Outputs (device): ids_out[max_visible] = visible Gaussian indices in
+ * ascending order, *n_vis_out = their count (clamped to max_visible; overflow
+ * latches GS_ERR_CAPACITY).  The visibility bitmask stays in the context for
+ * the next gs_adam_deferred. */
+GS_API gs_status gs_cull(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                  int32_t *ids_out, int32_t *n_vis_out, void *stream);
+
+/* Render one view (§2.4 steps 1-3) of the Gaussians ids[0..*n_vis) (device,
+ * ascending, from gs_cull): gather with restore (as gs_cull), projection and
+ * SH colour, tile keys, depth/tile sort, front-to-back compositing on a black
+ * background.  image_out (device fp32 [3][H][W]).  The context keeps what the
+ * backward needs (compact parameters, splats, sorted keys, tile ranges) until
+ * the next gs_render_fwd. */
+GS_API gs_status gs_render_fwd(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                        const int32_t *ids, const int32_t *n_vis, float *image_out, void *stream);
+
+/* Adjoint of the last gs_render_fwd (§2.4 step 5): dL_dimage (device fp32
+ * [3][H][W]) -> grad_compact (device fp32 [D][cap], row r of the k-th visible
+ * Gaussian at [r * cap + k]; cap >= that render's visible count), overwritten.
+ * Transmittance is recomputed per tile, not stored per pixel. */
+GS_API gs_status gs_render_bwd(gs_ctx *ctx, const float *dL_dimage, float *grad_compact, int64_t cap, void *stream);
+
+/* L1 loss of §2.4 step 4: *loss_out = mean |image - target| over `count`
+ * values; dL_dimage = sign(image - target) / count.  All device fp32. */
+GS_API gs_status gs_loss_l1(gs_ctx *ctx, const float *image, const float *target, int64_t count, float *loss_out,
+                     float *dL_dimage, void *stream);
+
+/* One optimizer step (§4.3, Eqs. 1-3).  ids/n_vis (device) are the Gaussians
+ * with a gradient this step (ascending; the last gs_cull's visibility mask in
+ * the context must describe the same set), grad_compact (device fp32 [D][cap])
+ * their gradients.  Deferred mode: update set = ids U {counter == max_defer};
+ * each member is restored through the tables, stepped with Eq. 1 and its
+ * counter cleared; every other counter is incremented.  Eager mode: every
+ * Gaussian is stepped.  Increments scene->step. */
+GS_API gs_status gs_adam_deferred(gs_ctx *ctx, gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
+                           const float *grad_compact, int64_t cap, const gs_adam_cfg *adam, void *stream);
+
+/* The current (eager-equivalent) parameters and moments without modifying the
+ * scene: catch-up of each Gaussian's deferred steps (tests, checkpoints).
+ * Outputs (device fp32 [D][pitch], may be NULL). */
+GS_API gs_status gs_adam_materialize(gs_ctx *ctx, const gs_scene *scene, const gs_adam_cfg *adam, float *w_out,
+                              float *m_out, float *v_out, void *stream);
+
+/* Scatter compact gradients to a full [D][pitch] array (zero elsewhere). */
+GS_API gs_status gs_grad_scatter(gs_ctx *ctx, const gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
+                          const float *grad_compact, int64_t cap, float *grad_full, void *stream);
+
+/* One whole training iteration on n_views views (§2.4 steps 1-6): cull every
+ * view, render, L1 loss against targets[v] (device fp32 [3][H][W] each),
+ * backward, gradients summed over the views, one optimizer step over the union
+ * of the visible sets.  *loss_out (device) = sum over views of the L1 losses.
+ * Replays a CUDA graph captured on the first call with the same scene
+ * pointers, view count and image sizes.  Increments scene->step. */
+GS_API gs_status gs_step(gs_ctx *ctx, gs_scene *scene, const gs_camera *views, const float *const *targets,
+                  int32_t n_views, const gs_adam_cfg *adam, float *loss_out, void *stream);
+
+/* Stage timing of gs_step with CUDA events (benchmarks).  After
+ * gs_timing_enable(ctx, max_steps), each gs_step records events on its stream
+ * around: the whole step, the first view's cull kernel, its render forward and
+ * backward, the optimizer stage, and the optimizer's apply kernel (the
+ * D-plane sweep).  gs_timing_read synchronises the device, writes elapsed
+ * milliseconds ms_out[step * GS_TIMING_SPANS + span] for up to max_steps
+ * recorded steps, stores their number in *steps_out and restarts recording.
+ * Enabling or disabling timing re-captures the step graph. */
+enum { GS_SPAN_STEP = 0, GS_SPAN_CULL = 1, GS_SPAN_FWD = 2, GS_SPAN_BWD = 3, GS_SPAN_ADAM = 4,
+       GS_SPAN_ADAM_APPLY = 5, GS_TIMING_SPANS = 6 };
+GS_API gs_status gs_timing_enable(gs_ctx *ctx, int32_t max_steps);
+GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, int32_t *steps_out);
+
+/* Number of kernel launches in the captured gs_step graph (0 before the first
+ * gs_step). */
+GS_API gs_status gs_step_kernel_count(const gs_ctx *ctx, int32_t *kernels);
+
+/* Inspection of the last gs_render_fwd (tests, debugging).  Device pointers,
+ * owned by the context, valid until the next render: *tile_of_key[K] and
+ * *splat_of_key[K] the (tile id, compact visible index) pairs in sorted order,
+ * *n_keys the count K, *ranges[2 * tiles] the [begin, end) of each tile. */
+GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key, const uint32_t **splat_of_key,
+                                 const int32_t **n_keys, const uint32_t **ranges);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_B300_H */

@@ -67,6 +67,7 @@ typedef struct {
     double rgb[3];
     double margin;       /* smallest relative distance of a cull decision to its threshold */
     double depth_f32;    /* depth rounded to float32 (used only for the key) */
+    double radius_margin;/* relative distance of 3 sqrt(lambda_max) to the integer ceil() rounds across */
 } orc_splat;
 
 static const double ALPHA_MAX = 0.999, ALPHA_MIN = 1.0 / 255.0, T_STOP = 1e-4;
@@ -242,6 +243,7 @@ static void project_one(int deg, const double *P, int64_t pitch, int64_t i, cons
     double r3 = 3.0 * sqrt(lam);
     double r = ceil(r3);
     margin = dmin(margin, fabs(r3 - nearbyint(r3)) / r3);
+    out->radius_margin = fabs(r3 - nearbyint(r3)) / r3;
     out->radius = r;
     out->mean2d[0] = fx * S.u + cam->cx;
     out->mean2d[1] = fy * S.w + cam->cy;
@@ -364,16 +366,20 @@ static int pixel_walk(const orc_splat *sp, const int64_t *list, int64_t len, dou
     for (int64_t e = 0; e < len; e++) {
         const orc_splat *g = &sp[list[e]];
         double dx = g->mean2d[0] - px, dy = g->mean2d[1] - py;
-        double scale = dmax(dmax(fabs(g->mean2d[0]), fabs(g->mean2d[1])), g->radius);
-        margin = dmin(margin, fabs(g->radius - fabs(dx)) / scale);
-        margin = dmin(margin, fabs(g->radius - fabs(dy)) / scale);
-        if (fabs(dx) > g->radius || fabs(dy) > g->radius) continue;
         double sigma = 0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) + g->conic[1] * dx * dy;
-        if (sigma < 0) continue;
         double G = exp(-sigma);
         double raw = g->opacity * G;
         double alpha = dmin(ALPHA_MAX, raw);
-        margin = dmin(margin, rel(raw, ALPHA_MAX));
+        /* margins only of decisions that can change this pixel's value: the
+         * square test where the Gaussian would contribute, the 1/255 floor and
+         * the transmittance stop (the 0.999 clamp is continuous in value) */
+        if (alpha >= ALPHA_MIN && sigma >= 0) {
+            double scale = dmax(dmax(fabs(g->mean2d[0]), fabs(g->mean2d[1])), g->radius);
+            margin = dmin(margin, fabs(g->radius - fabs(dx)) / scale);
+            margin = dmin(margin, fabs(g->radius - fabs(dy)) / scale);
+        }
+        if (fabs(dx) > g->radius || fabs(dy) > g->radius) continue;
+        if (sigma < 0) continue;
         margin = dmin(margin, rel(alpha, ALPHA_MIN));
         if (alpha < ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);

@@ -28,7 +28,8 @@ class OrcCamera(C.Structure):
 SPLAT = np.dtype([("keep", "<i4"), ("rect", "<i4", 4), ("clampx", "<i4"), ("clampy", "<i4"),
                   ("rgb_clamped", "<i4", 3), ("pad", "<i4"), ("depth", "<f8"), ("mean2d", "<f8", 2),
                   ("cov2d", "<f8", 3), ("conic", "<f8", 3), ("radius", "<f8"), ("opacity", "<f8"),
-                  ("rgb", "<f8", 3), ("margin", "<f8"), ("depth_f32", "<f8")], align=True)
+                  ("rgb", "<f8", 3), ("margin", "<f8"), ("depth_f32", "<f8"),
+                  ("radius_margin", "<f8")], align=True)
 
 
 def lib():

@@ -1,0 +1,11 @@
+"""B300 (sm_103a) hot path of GS-Scale 3DGS training: frustum cull, gather with
+deferred restore, differentiable tile rasterizer, deferred Adam.
+
+The compute lives in ``libgs_b300.so`` (hand-written CUDA behind the C ABI of
+include/gs_b300.h); this package only marshals arguments.  Importing it loads
+the library and fails if it has not been built.
+"""
+from . import _lib
+from .api import Context, GaussianScene, adam_struct, camera_struct, n_params, render  # noqa: F401
+
+_lib.load()

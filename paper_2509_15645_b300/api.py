@@ -1,0 +1,268 @@
+"""Torch-facing wrappers of the C ABI.
+
+PyTorch supplies device memory and streams only; every step of the hot path
+runs in the CUDA library.  Layouts follow include/gs_b300.h: parameters are
+[D][pitch] float32 planes (geometry rows 0..10, SH rows 11..), compact
+per-visible arrays are [D][cap].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+def n_params(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class _DeviceArray:
+    """Exposes a raw device int32 array to torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (int(ptr), False), "version": 3}
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> L.Camera:
+    """From any object with R (3x3), t (3), fx, fy, cx, cy, width, height,
+    near, far (e.g. ``synth.scenes.Camera``)."""
+    c = L.Camera()
+    R = [float(x) for row in cam.R for x in row]
+    for k in range(9):
+        c.R[k] = R[k]
+    for k in range(3):
+        c.t[k] = float(cam.t[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_z, c.far_z = float(getattr(cam, "near", 0.01)), float(getattr(cam, "far", 1e10))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L.GS_ADAM_DEFERRED) -> L.AdamCfg:
+    a = L.AdamCfg()
+    lrs = [lr] * 6 if isinstance(lr, (int, float)) else list(lr)
+    for k in range(6):
+        a.lr[k] = float(lrs[k])
+    a.beta1, a.beta2, a.eps, a.max_defer, a.mode = beta1, beta2, eps, max_defer, mode
+    return a
+
+
+class GaussianScene:
+    """A Gaussian set on the device with its optimizer state.
+
+    ``w`` is one [D][pitch] float32 tensor (geometry planes then SH planes),
+    ``m``/``v`` the Adam moments, ``counter`` the defer counters."""
+
+    def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True):
+        D, n = params.shape
+        assert D == n_params(sh_degree)
+        self.n, self.sh_degree, self.D = n, sh_degree, D
+        self.pitch = (n + 3) // 4 * 4
+        self.w = torch.zeros(D, self.pitch, dtype=torch.float32, device=device)
+        self.w[:, :n] = torch.as_tensor(params, dtype=torch.float32).to(device)
+        if with_optimizer:
+            self.m = torch.zeros_like(self.w)
+            self.v = torch.zeros_like(self.w)
+            self.counter = torch.zeros(self.pitch, dtype=torch.uint8, device=device)
+        else:
+            self.m = self.v = self.counter = None
+        self.step = 0
+
+    def struct(self) -> L.Scene:
+        s = L.Scene()
+        s.n, s.pitch, s.sh_degree, s.precision = self.n, self.pitch, self.sh_degree, L.GS_FP32
+        s.geo = self.w.data_ptr()
+        s.sh = self.w.data_ptr() + 11 * self.pitch * 4
+        s.m = self.m.data_ptr() if self.m is not None else None
+        s.v = self.v.data_ptr() if self.v is not None else None
+        s.counter = self.counter.data_ptr() if self.counter is not None else None
+        s.step = self.step
+        return s
+
+    def params(self):
+        return self.w[:, :self.n]
+
+
+class Context:
+    """One gs_ctx: scratch workspace (a torch allocation) and the hot-path calls."""
+
+    def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(16, 16), max_views=1,
+                 max_sh_degree=3, device=0):
+        self.lib = L.load()
+        cfg = L.Config()
+        cfg.max_gaussians, cfg.max_visible, cfg.max_keys = int(max_gaussians), int(max_visible), int(max_keys)
+        cfg.max_width, cfg.max_height = int(max_width), int(max_height)
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+        cfg.max_views, cfg.max_sh_degree = int(max_views), int(max_sh_degree)
+        self.cfg = cfg
+        nb = C.c_size_t(0)
+        self._check(self.lib.gs_workspace_size(C.byref(cfg), C.byref(nb)), "workspace size")
+        self.device = torch.device("cuda", device)
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        self._check(self.lib.gs_create(C.byref(h), C.byref(cfg), device, _ptr(self.workspace), nb.value), "create")
+        self.h = h
+        self.max_visible = int(max_visible)
+
+    def _check(self, st, what=""):
+        if st != L.GS_OK:
+            msg = self.lib.gs_last_error(self.h).decode() if getattr(self, "h", None) else what
+            raise L.GsError(st, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def sync_status(self, stream=None):
+        st = self.lib.gs_sync_status(self.h, _stream(stream))
+        self._check(st, "device status")
+
+    def counters(self):
+        """The context's device counters (a torch view, no copy): [0] visible
+        count of the last cull, [1] keys of the last render, [2] update-set size
+        of the last deferred Adam step, [3] latched status."""
+        p = self.lib.gs_device_counters(self.h)
+        return torch.as_tensor(_DeviceArray(p, 8), device=self.device)
+
+    def render_lists(self, tiles):
+        """Sorted (tile, compact index) keys and tile ranges of the last render
+        (torch views of context memory)."""
+        kt, kv, nk, rg = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self._check(self.lib.gs_render_lists(self.h, C.byref(kt), C.byref(kv), C.byref(nk), C.byref(rg)), "lists")
+        n = int(torch.as_tensor(_DeviceArray(nk.value, 1), device=self.device).item())
+        keys = torch.as_tensor(_DeviceArray(kt.value, max(n, 1)), device=self.device)[:n]
+        vals = torch.as_tensor(_DeviceArray(kv.value, max(n, 1)), device=self.device)[:n]
+        ranges = torch.as_tensor(_DeviceArray(rg.value, 2 * tiles), device=self.device).view(tiles, 2)
+        return keys, vals, ranges
+
+    def cull(self, scene: GaussianScene, cam, adam=None, stream=None):
+        ids = torch.empty(self.max_visible, dtype=torch.int32, device=self.device)
+        n_vis = torch.zeros(1, dtype=torch.int32, device=self.device)
+        sc = scene.struct()
+        cs = camera_struct(cam)
+        st = self.lib.gs_cull(self.h, C.byref(sc), C.byref(cs), C.byref(adam) if adam is not None else None,
+                              _ptr(ids), _ptr(n_vis), _stream(stream))
+        self._check(st, "gs_cull")
+        return ids, n_vis
+
+    def render_fwd(self, scene: GaussianScene, cam, ids, n_vis, adam=None, stream=None):
+        img = torch.empty(3, int(cam.height), int(cam.width), dtype=torch.float32, device=self.device)
+        sc = scene.struct()
+        cs = camera_struct(cam)
+        st = self.lib.gs_render_fwd(self.h, C.byref(sc), C.byref(cs), C.byref(adam) if adam is not None else None,
+                                    _ptr(ids), _ptr(n_vis), _ptr(img), _stream(stream))
+        self._check(st, "gs_render_fwd")
+        return img
+
+    def render_bwd(self, dimage, D, cap=None, stream=None):
+        cap = cap or self.max_visible
+        g = torch.empty(D, cap, dtype=torch.float32, device=self.device)
+        st = self.lib.gs_render_bwd(self.h, _ptr(dimage.contiguous()), _ptr(g), cap, _stream(stream))
+        self._check(st, "gs_render_bwd")
+        return g
+
+    def loss_l1(self, image, target, stream=None):
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        dimg = torch.empty_like(image)
+        st = self.lib.gs_loss_l1(self.h, _ptr(image), _ptr(target), image.numel(), _ptr(loss), _ptr(dimg),
+                                 _stream(stream))
+        self._check(st, "gs_loss_l1")
+        return loss, dimg
+
+    def adam_deferred(self, scene: GaussianScene, ids, n_vis, grad_compact, adam, stream=None):
+        sc = scene.struct()
+        st = self.lib.gs_adam_deferred(self.h, C.byref(sc), _ptr(ids), _ptr(n_vis), _ptr(grad_compact),
+                                       grad_compact.shape[1], C.byref(adam), _stream(stream))
+        self._check(st, "gs_adam_deferred")
+        scene.step = sc.step
+
+    def materialize(self, scene: GaussianScene, adam, stream=None):
+        w = torch.empty_like(scene.w)
+        m = torch.empty_like(scene.w)
+        v = torch.empty_like(scene.w)
+        sc = scene.struct()
+        st = self.lib.gs_adam_materialize(self.h, C.byref(sc), C.byref(adam), _ptr(w), _ptr(m), _ptr(v),
+                                          _stream(stream))
+        self._check(st, "gs_adam_materialize")
+        return w, m, v
+
+    def grad_scatter(self, scene: GaussianScene, ids, n_vis, grad_compact, stream=None):
+        full = torch.empty_like(scene.w)
+        sc = scene.struct()
+        st = self.lib.gs_grad_scatter(self.h, C.byref(sc), _ptr(ids), _ptr(n_vis), _ptr(grad_compact),
+                                      grad_compact.shape[1], _ptr(full), _stream(stream))
+        self._check(st, "gs_grad_scatter")
+        return full
+
+    def timing_enable(self, max_steps):
+        self._check(self.lib.gs_timing_enable(self.h, int(max_steps)), "gs_timing_enable")
+
+    def timing_read(self, max_steps):
+        """Per-step stage durations (ms) recorded with CUDA events inside gs_step:
+        a list of dicts keyed by step, cull, fwd, bwd, adam, adam_apply."""
+        buf = (C.c_float * (max_steps * len(L.SPANS)))()
+        n = C.c_int32(0)
+        self._check(self.lib.gs_timing_read(self.h, buf, int(max_steps), C.byref(n)), "gs_timing_read")
+        k = len(L.SPANS)
+        return [dict(zip(L.SPANS, buf[s * k:(s + 1) * k])) for s in range(n.value)]
+
+    def step_kernel_count(self):
+        n = C.c_int32(0)
+        self._check(self.lib.gs_step_kernel_count(self.h, C.byref(n)), "gs_step_kernel_count")
+        return n.value
+
+    def step(self, scene: GaussianScene, cams, targets, adam, loss=None, stream=None):
+        nv = len(cams)
+        cs = (L.Camera * nv)(*[camera_struct(c) for c in cams])
+        tp = (C.c_void_p * nv)(*[t.data_ptr() for t in targets])
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        sc = scene.struct()
+        st = self.lib.gs_step(self.h, C.byref(sc), cs, tp, nv, C.byref(adam), _ptr(loss), _stream(stream))
+        self._check(st, "gs_step")
+        scene.step = sc.step
+        return loss
+
+
+class _Render(torch.autograd.Function):
+    """image = render(w) for a fixed visible set; the backward is gs_render_bwd
+    followed by a scatter of the compact gradients to w's [D][pitch] layout."""
+
+    @staticmethod
+    def forward(fctx, w, gctx, scene, cam, ids, n_vis):
+        img = gctx.render_fwd(scene, cam, ids, n_vis)
+        fctx.gctx, fctx.scene, fctx.ids, fctx.n_vis = gctx, scene, ids, n_vis
+        return img
+
+    @staticmethod
+    def backward(fctx, dimg):
+        gc = fctx.gctx.render_bwd(dimg.contiguous(), fctx.scene.D)
+        gfull = fctx.gctx.grad_scatter(fctx.scene, fctx.ids, fctx.n_vis, gc)
+        return gfull, None, None, None, None, None
+
+
+def render(gctx: Context, scene: GaussianScene, cam, ids, n_vis):
+    """Differentiable render of one view with respect to ``scene.w``."""
+    return _Render.apply(scene.w, gctx, scene, cam, ids, n_vis)
+
+
+__all__ = ["Context", "GaussianScene", "render", "camera_struct", "adam_struct", "n_params"]

@@ -1,0 +1,266 @@
+// gs_internal.cuh -- device-side data structures and the per-Gaussian / per-pixel
+// arithmetic shared by the kernels of the 3DGS training hot path (GS-Scale,
+// arXiv 2509.15645, §2.4 steps 1-6 and §4.3).  Everything here is FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs_b300.h"
+
+namespace gs {
+
+constexpr int ROW_MEAN = 0, ROW_LS = 3, ROW_QUAT = 6, ROW_OPAC = 10, N_GEO = 11;
+constexpr int MAX_VIEWS = 8;
+constexpr int LUT_N = 16;       // counter values 0..15 (4-bit counter of §4.3.2)
+constexpr int N_GROUPS = 6;     // lr groups: mean, log-scale, quat, opacity, SH DC, SH rest
+constexpr int CHUNK = 2048;     // Gaussians per compaction chunk (64 mask words)
+constexpr int CHUNK_WORDS = CHUNK / 32;
+
+// Camera as the kernels read it: the API camera plus derived constants.
+struct DevCam {
+    float R[9], t[3];
+    float fx, fy, cx, cy, near_z, far_z;
+    float limx, limy;            // guard band: 1.3 * tan(half fov)
+    float campos[3];             // camera centre in world space
+    int width, height, tile_w, tile_h, tiles_x, tiles_y;
+};
+
+// Restore tables of the deferred update (Fig. 10, §4.3.2) for one step t.
+struct DevLut {
+    float param[N_GROUPS][LUT_N];   // param_lut[d] (contains lr)
+    float mom[LUT_N], var[LUT_N];   // b1^(d+1), b2^(d+1)
+    float step_size[N_GROUPS];      // lr / (1 - b1^t)
+    float bias_corr;                // sqrt(1 - b2^t)
+    float omb1, omb2, eps;          // 1 - b1, 1 - b2, eps
+    float b1, b2;
+    int max_defer;
+    int step;                       // t
+    int restore;                    // 0: render/cull without restore
+};
+
+struct DevArgs {
+    DevCam cam[MAX_VIEWS];
+    const float *target[MAX_VIEWS];
+    DevLut lut;
+    int n_views;
+};
+
+// Device-resident counters and status (one per context).
+struct Counters {
+    int n_vis;        // last cull
+    int n_keys;       // last render
+    int n_upd;        // last deferred Adam update set
+    int status;       // first latched gs_status
+    float loss;       // last loss
+    int n_union;      // gs_step: union of the views' visible sets
+    int pad[2];
+};
+
+__device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status, 0, code); }
+
+__host__ __device__ __forceinline__ int lr_group(int row)
+{
+    return row < 3 ? 0 : row < 6 ? 1 : row < 10 ? 2 : row == 10 ? 3 : row < 14 ? 4 : 5;
+}
+
+// ---------------------------------------------------------------------------
+// Deferred restore (Eq. 3 with eps factored out): the current value of a
+// parameter whose last d updates were deferred.  d = 0 leaves it untouched.
+__device__ __forceinline__ float restore_param(float w, float m, float v, float plut, int d, float eps)
+{
+    return d ? w - plut * m / (sqrtf(v) + eps) : w;
+}
+
+// ---------------------------------------------------------------------------
+// Projection of one Gaussian (§2.4 step 1), FP32.  The cull and the render
+// call the same function so that their visibility decisions coincide.
+struct Proj {
+    float p[3];            // camera-space mean
+    float s[3];            // scales
+    float qh[4], qn;       // normalised quaternion and the norm
+    float Rq[9];           // rotation of the Gaussian
+    float T[6];            // J W (2 x 3)
+    float S3[6];           // Sigma3: xx, xy, xz, yy, yz, zz
+    float a, b, c, det;    // Sigma2 (with low-pass) and its determinant
+    float conA, conB, conC;
+    float mx, my, radius;
+    int cu, cw;            // guard-band clamps
+    int rect[4];
+    int keep;
+};
+
+__device__ __forceinline__ void quat_rot(const float q[4], float R[9])
+{
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// g[0..9] = mean(3), log-scale(3), quaternion(4).
+__device__ __forceinline__ void project_gaussian(const float g[10], const DevCam &cam, Proj &P)
+{
+    P.keep = 0;
+    P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
+    const float *R = cam.R;
+    P.p[0] = R[0] * g[0] + R[1] * g[1] + R[2] * g[2] + cam.t[0];
+    P.p[1] = R[3] * g[0] + R[4] * g[1] + R[5] * g[2] + cam.t[1];
+    P.p[2] = R[6] * g[0] + R[7] * g[1] + R[8] * g[2] + cam.t[2];
+    float pz = P.p[2];
+    if (!(pz > cam.near_z && pz < cam.far_z)) return;
+    P.s[0] = expf(g[3]); P.s[1] = expf(g[4]); P.s[2] = expf(g[5]);
+    float qn2 = g[6] * g[6] + g[7] * g[7] + g[8] * g[8] + g[9] * g[9];
+    if (qn2 > 0.f) {
+        P.qn = sqrtf(qn2);
+        float inv = 1.f / P.qn;
+        P.qh[0] = g[6] * inv; P.qh[1] = g[7] * inv; P.qh[2] = g[8] * inv; P.qh[3] = g[9] * inv;
+    } else {
+        P.qn = 1.f; P.qh[0] = 1.f; P.qh[1] = P.qh[2] = P.qh[3] = 0.f;
+    }
+    quat_rot(P.qh, P.Rq);
+    // Sigma3 = M M^T, M = Rq diag(s)
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) M[r * 3 + c] = P.Rq[r * 3 + c] * P.s[c];
+    P.S3[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    P.S3[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    P.S3[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    P.S3[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    P.S3[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    P.S3[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    float iz = 1.f / pz;
+    float u = P.p[0] * iz, w = P.p[1] * iz;
+    float tu = fminf(cam.limx, fmaxf(-cam.limx, u));
+    float tw = fminf(cam.limy, fmaxf(-cam.limy, w));
+    P.cu = (u < -cam.limx) || (u > cam.limx);
+    P.cw = (w < -cam.limy) || (w > cam.limy);
+    float J00 = cam.fx * iz, J02 = -cam.fx * tu * iz;
+    float J11 = cam.fy * iz, J12 = -cam.fy * tw * iz;
+    // T = J W (W = camera rotation R)
+    P.T[0] = J00 * R[0] + J02 * R[6];
+    P.T[1] = J00 * R[1] + J02 * R[7];
+    P.T[2] = J00 * R[2] + J02 * R[8];
+    P.T[3] = J11 * R[3] + J12 * R[6];
+    P.T[4] = J11 * R[4] + J12 * R[7];
+    P.T[5] = J11 * R[5] + J12 * R[8];
+    // Sigma2 = T Sigma3 T^T + 0.3 I
+    const float *S = P.S3;
+    float u0 = S[0] * P.T[0] + S[1] * P.T[1] + S[2] * P.T[2];
+    float u1 = S[1] * P.T[0] + S[3] * P.T[1] + S[4] * P.T[2];
+    float u2 = S[2] * P.T[0] + S[4] * P.T[1] + S[5] * P.T[2];
+    float v0 = S[0] * P.T[3] + S[1] * P.T[4] + S[2] * P.T[5];
+    float v1 = S[1] * P.T[3] + S[3] * P.T[4] + S[4] * P.T[5];
+    float v2 = S[2] * P.T[3] + S[4] * P.T[4] + S[5] * P.T[5];
+    P.a = P.T[0] * u0 + P.T[1] * u1 + P.T[2] * u2 + 0.3f;
+    P.b = P.T[0] * v0 + P.T[1] * v1 + P.T[2] * v2;
+    P.c = P.T[3] * v0 + P.T[4] * v1 + P.T[5] * v2 + 0.3f;
+    P.det = P.a * P.c - P.b * P.b;
+    if (!(P.det > 0.f)) return;
+    float idet = 1.f / P.det;
+    P.conA = P.c * idet; P.conB = -P.b * idet; P.conC = P.a * idet;
+    float mid = 0.5f * (P.a + P.c);
+    float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - P.det));
+    P.radius = ceilf(3.f * sqrtf(lam));
+    P.mx = cam.fx * u + cam.cx;
+    P.my = cam.fy * w + cam.cy;
+    float itw = 1.f / (float)cam.tile_w, ith = 1.f / (float)cam.tile_h;
+    int x0 = (int)floorf((P.mx - P.radius) * itw), x1 = (int)ceilf((P.mx + P.radius) * itw);
+    int y0 = (int)floorf((P.my - P.radius) * ith), y1 = (int)ceilf((P.my + P.radius) * ith);
+    x0 = min(max(x0, 0), cam.tiles_x); x1 = min(max(x1, 0), cam.tiles_x);
+    y0 = min(max(y0, 0), cam.tiles_y); y1 = min(max(y1, 0), cam.tiles_y);
+    P.rect[0] = x0; P.rect[1] = x1; P.rect[2] = y0; P.rect[3] = y1;
+    P.keep = (P.radius > 0.f) && (x1 > x0) && (y1 > y0);
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics to degree 3 (3DGS ordering and signs) of a unit
+// direction; nk = (deg+1)^2 values.
+struct SHC {
+    static constexpr float c0 = 0.28209479177387814f;
+    static constexpr float c1 = 0.4886025119029199f;
+    static constexpr float c2a = 1.0925484305920792f, c2b = 0.31539156525252005f, c2c = 0.5462742152960396f;
+    static constexpr float c3a = 0.5900435899266435f, c3b = 2.890611442640554f, c3c = 0.4570457994644658f;
+    static constexpr float c3d = 0.3731763325901154f, c3e = 1.445305721320277f;
+};
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16])
+{
+    Y[0] = SHC::c0;
+    if (deg < 1) return;
+    Y[1] = -SHC::c1 * y; Y[2] = SHC::c1 * z; Y[3] = -SHC::c1 * x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = SHC::c2a * x * y;
+    Y[5] = -SHC::c2a * y * z;
+    Y[6] = SHC::c2b * (2.f * zz - xx - yy);
+    Y[7] = -SHC::c2a * x * z;
+    Y[8] = SHC::c2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -SHC::c3a * y * (3.f * xx - yy);
+    Y[10] = SHC::c3b * x * y * z;
+    Y[11] = -SHC::c3c * y * (4.f * zz - xx - yy);
+    Y[12] = SHC::c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -SHC::c3c * x * (4.f * zz - xx - yy);
+    Y[14] = SHC::c3e * z * (xx - yy);
+    Y[15] = -SHC::c3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of sum_k Y_k(x,y,z) h_k with respect to (x, y, z) (independent variables).
+__device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z, const float h[16], float g[3])
+{
+    g[0] = g[1] = g[2] = 0.f;
+    if (deg < 1) return;
+    g[0] += -SHC::c1 * h[3];
+    g[1] += -SHC::c1 * h[1];
+    g[2] += SHC::c1 * h[2];
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += SHC::c2a * y * h[4] - SHC::c2a * z * h[7] - 2.f * SHC::c2b * x * h[6] + 2.f * SHC::c2c * x * h[8];
+    g[1] += SHC::c2a * x * h[4] - SHC::c2a * z * h[5] - 2.f * SHC::c2b * y * h[6] - 2.f * SHC::c2c * y * h[8];
+    g[2] += -SHC::c2a * y * h[5] - SHC::c2a * x * h[7] + 4.f * SHC::c2b * z * h[6];
+    if (deg < 3) return;
+    g[0] += -SHC::c3a * 6.f * x * y * h[9] + SHC::c3b * y * z * h[10] + SHC::c3c * 2.f * x * y * h[11]
+            - 6.f * SHC::c3d * x * z * h[12] - SHC::c3c * (4.f * zz - 3.f * xx - yy) * h[13]
+            + 2.f * SHC::c3e * x * z * h[14] - SHC::c3a * (3.f * xx - 3.f * yy) * h[15];
+    g[1] += -SHC::c3a * (3.f * xx - 3.f * yy) * h[9] + SHC::c3b * x * z * h[10]
+            - SHC::c3c * (4.f * zz - xx - 3.f * yy) * h[11] - 6.f * SHC::c3d * y * z * h[12]
+            + SHC::c3c * 2.f * x * y * h[13] - 2.f * SHC::c3e * y * z * h[14] + SHC::c3a * 6.f * x * y * h[15];
+    g[2] += SHC::c3b * x * y * h[10] - SHC::c3c * 8.f * y * z * h[11]
+            + SHC::c3d * (6.f * zz - 3.f * xx - 3.f * yy) * h[12] - SHC::c3c * 8.f * x * z * h[13]
+            + SHC::c3e * (xx - yy) * h[14];
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel contribution test and alpha (§2.4 step 3).  The forward and both
+// passes of the backward call this one function with the same operands, so
+// their discrete decisions agree bit for bit.  Returns alpha, or 0 when the
+// Gaussian does not contribute; *G = exp(-sigma), *clamped = 0.999 clamp hit.
+constexpr float ALPHA_MAX = 0.999f, ALPHA_MIN = 1.f / 255.f, T_STOP = 1e-4f;
+
+__device__ __forceinline__ float splat_alpha(float4 r0, float4 r1, float px, float py, float &dx, float &dy,
+                                             float &G, bool &clamped)
+{
+    // r0 = (mean x, mean y, radius, opacity), r1 = (A, B, C, depth)
+    dx = __fsub_rn(r0.x, px);
+    dy = __fsub_rn(r0.y, py);
+    if (fabsf(dx) > r0.z || fabsf(dy) > r0.z) return 0.f;
+    float sig = __fmaf_rn(r1.y, __fmul_rn(dx, dy),
+                          __fmul_rn(0.5f, __fmaf_rn(r1.x, __fmul_rn(dx, dx), __fmul_rn(r1.z, __fmul_rn(dy, dy)))));
+    if (sig < 0.f) return 0.f;
+    G = __expf(-sig);
+    float raw = __fmul_rn(r0.w, G);
+    clamped = raw > ALPHA_MAX;
+    float alpha = fminf(ALPHA_MAX, raw);
+    return alpha < ALPHA_MIN ? 0.f : alpha;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers implemented in the .cu files.
+struct Scan;   // fwd
+
+void launch_set_args(const DevArgs &a, DevArgs *dst, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,108 @@
+// gs_kernels.cuh -- host-side launchers of the hot-path kernels and the
+// scratch-workspace view they share.
+#pragma once
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Length of a scan: fixed, or mul * ceil(min(*n_dev, cap) / div) + add.
+struct ScanLen {
+    const int *n_dev;
+    int mul, div, add, fixed, cap;
+};
+
+struct Work {
+    uint32_t *partials;   // >= 1024 scan partials
+    uint32_t *hist;       // radix histograms
+    int *status;          // device status word
+    int scan_grid;        // blocks of the scan kernels (<= 1024)
+    int num_sms;
+    cudaEvent_t *tev;     // timing points of the current step, or nullptr
+    void mark(int p, cudaStream_t s) const
+    {
+        // External: recorded as an event node when the stream is being captured
+        if (tev) cudaEventRecordWithFlags(tev[p], s, cudaEventRecordExternal);
+    }
+    int grid(int64_t threads, int block, int per_sm = 8) const
+    {
+        int64_t b = (threads + block - 1) / block;
+        int64_t mx = (int64_t)num_sms * per_sm;
+        if (b > mx) b = mx;
+        return (int)(b < 1 ? 1 : b);
+    }
+};
+
+// k_scan.cu
+void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *total_out, int total_cap,
+                    cudaStream_t s);
+void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
+                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s);
+int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
+               Work &w, cudaStream_t s);
+
+// Scene pointers as the kernels take them.
+struct SceneView {
+    float *geo;
+    float *sh;
+    float *m;
+    float *v;
+    uint8_t *counter;
+    int64_t n, pitch;
+    int deg, D;
+};
+
+// Timing points recorded inside a step (see gs_timing_enable).
+enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_ADAM0, TP_APPLY0, TP_APPLY1,
+       TP_ADAM1, TP_STEP1, TP_COUNT };
+
+// k_cull.cu: visibility bitmask + per-chunk counts (restore if lut.restore).
+void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
+                 cudaStream_t s);
+void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t *mask, int64_t n, Work &w,
+                        cudaStream_t s);
+void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s);
+
+// k_adam.cu
+void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                          const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
+                          int *n_upd, Work &w, cudaStream_t s);
+void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, Work &w, cudaStream_t s);
+void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
+                        Work &w, cudaStream_t s);
+void launch_grad_scatter(const int32_t *ids, const int *n_dev, int cap, const float *gc, int64_t gcap, int D,
+                         float *gfull, int64_t pitch, Work &w, cudaStream_t s);
+
+// k_render.cu
+struct RenderBufs {
+    float *compact;          // [D][cap] restored parameters of the visible set
+    int64_t cap;             // visible capacity
+    float4 *rec0, *rec1, *rec2;
+    uint32_t *dkey, *tcnt;
+    uint2 *rect;
+    uint32_t *dk[2], *dv[2]; // depth sort buffers
+    uint32_t *rank_cnt;      // [cap + 1]
+    uint32_t *tk[2], *tv[2]; // tile sort buffers
+    int64_t kcap;            // key capacity
+    uint2 *ranges;           // [tiles]
+    float *g9;               // [9][cap] screen-space gradient sums
+    int *n_keys;             // device
+    // filled by render_fwd
+    const uint32_t *sorted_keys;
+    const uint32_t *sorted_vals;
+    int tiles;
+};
+
+void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
+                    RenderBufs &rb, const DevCam &cam_host, float *image, bool use_target, float *dimage,
+                    float *loss, Work &w, cudaStream_t s);
+void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
+                     const DevCam &cam_host, const float *dimage, float *grad, int64_t gcap,
+                     const uint32_t *remap_mask, const uint32_t *remap_prefix, const int32_t *ids, bool accumulate,
+                     Work &w, cudaStream_t s);
+void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
+                    cudaStream_t s);
+void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s);
+
+}  // namespace gs

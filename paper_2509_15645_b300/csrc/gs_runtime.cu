@@ -1,0 +1,741 @@
+// gs_runtime.cu -- context, workspace, argument blocks and the C ABI of
+// include/gs_b300.h.  No kernel arithmetic lives here: every step of the hot
+// path is a kernel in k_cull.cu, k_scan.cu, k_render.cu or k_adam.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gs_kernels.cuh"
+
+using namespace gs;
+
+namespace {
+
+enum { SLOT_CULL = 0, SLOT_RENDER = 1, SLOT_ADAM = 2, SLOT_STEP = 3, N_SLOTS = 4 };
+
+struct GraphCache {
+    cudaGraph_t graph = nullptr;   // kept alive: its node handles address the exec's nodes
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t args_node = nullptr;
+    cudaKernelNodeParams args_params{};
+    // what the captured graph baked in
+    float *geo = nullptr;
+    void *sh = nullptr, *m = nullptr, *v = nullptr;
+    uint8_t *counter = nullptr;
+    int64_t n = 0, pitch = 0;
+    int deg = -1, n_views = 0, mode = -1;
+    int W[MAX_VIEWS] = {0}, H[MAX_VIEWS] = {0};
+    float *loss = nullptr;
+    bool timed = false;
+    cudaGraphNode_t ev_node[TP_COUNT] = {nullptr};
+    int kernels = 0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+    int device = 0;
+    int num_sms = 148;
+    gs_config cfg{};
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    DevArgs *args = nullptr;     // [N_SLOTS]
+    Counters *cnt = nullptr;
+    int *nvis_view = nullptr;    // [MAX_VIEWS] visible counts of gs_step's views
+    int *n_render = nullptr;     // visible count of the last gs_render_fwd
+    int *n_tmp = nullptr;
+    int64_t nwords = 0, nchunks = 0;
+    uint32_t *mask = nullptr, *wprefix = nullptr, *chunk = nullptr;
+    uint32_t *umask = nullptr, *uchunk = nullptr;
+    int32_t *uids = nullptr;
+    uint32_t *amask = nullptr, *aprefix = nullptr, *achunk = nullptr;
+    uint32_t *vmask[MAX_VIEWS] = {nullptr};
+    uint32_t *vprefix[MAX_VIEWS] = {nullptr};
+    int32_t *vids[MAX_VIEWS] = {nullptr};
+    uint32_t *union_mask = nullptr, *union_prefix = nullptr, *union_chunk = nullptr;
+    float *img = nullptr, *dimg = nullptr, *grad_u = nullptr;
+    int64_t gcap_u = 0;
+    RenderBufs rb{};
+    Work w{};
+    // state kept from the last gs_render_fwd for gs_render_bwd
+    bool have_fwd = false;
+    SceneView fwd_sc{};
+    DevCam fwd_cam{};
+    GraphCache graph;
+    // stage timing
+    int t_max = 0, t_used = 0;
+    cudaEvent_t *t_events = nullptr;   // [t_max][TP_COUNT]
+    char err[512] = {0};
+};
+
+static void timing_free(gs_ctx *c)
+{
+    if (c->t_events) {
+        for (int k = 0; k < c->t_max * TP_COUNT; k++) cudaEventDestroy(c->t_events[k]);
+        free(c->t_events);
+    }
+    c->t_events = nullptr;
+    c->t_max = c->t_used = 0;
+}
+
+static gs_status fail(gs_ctx *c, gs_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+static gs_status cuda_check(gs_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    return GS_OK;
+}
+
+static int n_params(int deg) { return N_GEO + 3 * (deg + 1) * (deg + 1); }
+
+// ---------------------------------------------------------------------------
+// Workspace layout.  The same walk sizes the workspace (base == nullptr) and
+// hands out the pointers.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T> T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static bool valid_cfg(const gs_config *c)
+{
+    if (!c) return false;
+    int tp = c->tile_w * c->tile_h;
+    return c->max_gaussians > 0 && c->max_gaussians < (1ll << 31) - CHUNK && c->max_visible > 0 &&
+           c->max_visible < (1ll << 31) && c->max_keys > 0 && c->max_keys < (1ll << 32) - 1 && c->max_width > 0 &&
+           c->max_height > 0 && c->tile_w > 0 && c->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256) &&
+           c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
+           c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h;
+}
+
+static void carve(gs_ctx *c, char *base)
+{
+    const gs_config &g = c->cfg;
+    Carver k{base};
+    const int64_t N = g.max_gaussians, V = g.max_visible, K = g.max_keys;
+    const int D = n_params(g.max_sh_degree);
+    const int64_t NW = (N + 31) / 32 + CHUNK_WORDS, NC = (N + CHUNK - 1) / CHUNK + 1;
+    const int64_t tiles = (int64_t)((g.max_width + g.tile_w - 1) / g.tile_w) * ((g.max_height + g.tile_h - 1) / g.tile_h);
+    const int64_t P = 3ll * g.max_width * g.max_height;
+    c->nwords = NW;
+    c->nchunks = NC;
+    c->args = k.take<DevArgs>(N_SLOTS);
+    c->cnt = k.take<Counters>(1);
+    c->nvis_view = k.take<int>(MAX_VIEWS);
+    c->n_render = k.take<int>(1);
+    c->n_tmp = k.take<int>(4);
+    c->mask = k.take<uint32_t>(NW);
+    c->wprefix = k.take<uint32_t>(NW);
+    c->chunk = k.take<uint32_t>(NC);
+    c->umask = k.take<uint32_t>(NW);
+    c->uchunk = k.take<uint32_t>(NC);
+    c->uids = k.take<int32_t>(N);
+    c->amask = k.take<uint32_t>(NW);
+    c->aprefix = k.take<uint32_t>(NW);
+    c->achunk = k.take<uint32_t>(NC);
+    for (int v = 0; v < g.max_views; v++) {
+        c->vmask[v] = k.take<uint32_t>(NW);
+        c->vprefix[v] = k.take<uint32_t>(NW);
+        c->vids[v] = k.take<int32_t>(V);
+    }
+    if (g.max_views > 1) {
+        c->union_mask = k.take<uint32_t>(NW);
+        c->union_prefix = k.take<uint32_t>(NW);
+        c->union_chunk = k.take<uint32_t>(NC);
+    }
+    RenderBufs &rb = c->rb;
+    rb.cap = V;
+    rb.kcap = K;
+    rb.compact = k.take<float>((size_t)D * V);
+    rb.rec0 = k.take<float4>(V);
+    rb.rec1 = k.take<float4>(V);
+    rb.rec2 = k.take<float4>(V);
+    rb.tcnt = k.take<uint32_t>(V);
+    rb.rect = k.take<uint2>(V);
+    for (int j = 0; j < 2; j++) {
+        rb.dk[j] = k.take<uint32_t>(V);
+        rb.dv[j] = k.take<uint32_t>(V);
+    }
+    rb.rank_cnt = k.take<uint32_t>(V + 1);
+    for (int j = 0; j < 2; j++) {
+        rb.tk[j] = k.take<uint32_t>(K);
+        rb.tv[j] = k.take<uint32_t>(K);
+    }
+    rb.ranges = k.take<uint2>(tiles);
+    rb.g9 = k.take<float>(9 * V);
+    rb.n_keys = base ? &c->cnt->n_keys : nullptr;
+    int64_t big = K > V ? K : V;
+    c->w.hist = k.take<uint32_t>(256 * ((big + 4095) / 4096) + 256);
+    c->w.partials = k.take<uint32_t>(1024);
+    c->img = k.take<float>(P);
+    c->dimg = k.take<float>(P);
+    c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
+    c->grad_u = k.take<float>((size_t)D * c->gcap_u);
+    c->ws_bytes = k.off + 256;
+}
+
+// ---------------------------------------------------------------------------
+static DevCam make_cam(const gs_camera &a, const gs_config &g)
+{
+    DevCam c{};
+    memcpy(c.R, a.R, sizeof(c.R));
+    memcpy(c.t, a.t, sizeof(c.t));
+    c.fx = a.fx; c.fy = a.fy; c.cx = a.cx; c.cy = a.cy;
+    c.near_z = a.near_z; c.far_z = a.far_z;
+    c.limx = (float)(1.3 * (0.5 * a.width / (double)a.fx));
+    c.limy = (float)(1.3 * (0.5 * a.height / (double)a.fy));
+    for (int i = 0; i < 3; i++)
+        c.campos[i] = (float)(-((double)a.R[0 * 3 + i] * a.t[0] + (double)a.R[1 * 3 + i] * a.t[1] + (double)a.R[2 * 3 + i] * a.t[2]));
+    c.width = a.width;
+    c.height = a.height;
+    c.tile_w = g.tile_w;
+    c.tile_h = g.tile_h;
+    c.tiles_x = (a.width + g.tile_w - 1) / g.tile_w;
+    c.tiles_y = (a.height + g.tile_h - 1) / g.tile_h;
+    return c;
+}
+
+// Tables of the deferred update (Fig. 10, §4.3.2) for step t, computed in
+// double and rounded to float.  Entries with delay >= t are never used.
+static DevLut make_lut(const gs_adam_cfg *a, int t, bool restore)
+{
+    DevLut L{};
+    L.restore = 0;
+    if (!a) return L;
+    const double b1 = a->beta1, b2 = a->beta2;
+    const double scale = b1 / std::sqrt(b2);
+    for (int g = 0; g < N_GROUPS; g++) {
+        double prev = 0.0;
+        L.param[g][0] = 0.f;
+        for (int i = 1; i < LUT_N; i++) {
+            if (i <= a->max_defer && i <= t - 1) {
+                prev = scale * prev + (a->lr[g] * b1) / (std::sqrt(b2 / (1.0 - std::pow(b2, t - i))) * (1.0 - std::pow(b1, t - i)));
+                L.param[g][i] = (float)prev;
+            } else {
+                L.param[g][i] = 0.f;
+            }
+        }
+        L.step_size[g] = (float)(a->lr[g] / (1.0 - std::pow(b1, t)));
+    }
+    for (int i = 0; i < LUT_N; i++) {
+        L.mom[i] = (float)std::pow(b1, i + 1);
+        L.var[i] = (float)std::pow(b2, i + 1);
+    }
+    L.bias_corr = (float)std::sqrt(1.0 - std::pow(b2, t));
+    L.omb1 = (float)(1.0 - b1);
+    L.omb2 = (float)(1.0 - b2);
+    L.eps = a->eps;
+    L.b1 = a->beta1;
+    L.b2 = a->beta2;
+    L.max_defer = a->max_defer;
+    L.step = t;
+    L.restore = restore ? 1 : 0;
+    return L;
+}
+
+__global__ void k_set_args(DevArgs a, DevArgs *dst)
+{
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&a);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevArgs) / 4); k += blockDim.x) d[k] = src[k];
+}
+
+static void set_args(gs_ctx *c, int slot, const DevArgs &a, cudaStream_t s)
+{
+    k_set_args<<<1, 128, 0, s>>>(a, c->args + slot);
+}
+
+static bool valid_cam(const gs_ctx *c, const gs_camera *cam)
+{
+    return cam && cam->width > 0 && cam->height > 0 && cam->width <= c->cfg.max_width &&
+           cam->height <= c->cfg.max_height && cam->fx > 0.f && cam->fy > 0.f && cam->far_z > cam->near_z &&
+           std::isfinite(cam->fx) && std::isfinite(cam->fy);
+}
+
+static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneView &sv)
+{
+    if (!s) return fail(c, GS_ERR_INVALID_ARG, "scene is NULL");
+    if (s->n <= 0 || s->n > c->cfg.max_gaussians) return fail(c, GS_ERR_INVALID_ARG, "scene n=%lld out of range", (long long)s->n);
+    if (s->pitch < s->n || (s->pitch & 3)) return fail(c, GS_ERR_INVALID_ARG, "pitch must be >= n and a multiple of 4");
+    if (s->sh_degree < 0 || s->sh_degree > c->cfg.max_sh_degree) return fail(c, GS_ERR_INVALID_ARG, "sh_degree out of range");
+    if (s->precision != GS_FP32) return fail(c, GS_ERR_INVALID_ARG, "precision form not supported by this build");
+    if (!s->geo || !s->sh) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
+    if (need_opt && (!s->m || !s->v || !s->counter)) return fail(c, GS_ERR_INVALID_ARG, "optimizer state is NULL");
+    sv.geo = s->geo;
+    sv.sh = (float *)s->sh;
+    sv.m = (float *)s->m;
+    sv.v = (float *)s->v;
+    sv.counter = s->counter;
+    sv.n = s->n;
+    sv.pitch = s->pitch;
+    sv.deg = s->sh_degree;
+    sv.D = n_params(s->sh_degree);
+    return GS_OK;
+}
+
+static bool valid_adam(const gs_adam_cfg *a)
+{
+    if (!a) return false;
+    if (!(a->beta1 >= 0.f && a->beta1 < 1.f && a->beta2 >= 0.f && a->beta2 < 1.f && a->eps >= 0.f)) return false;
+    if (a->max_defer < 1 || a->max_defer > LUT_N - 1) return false;
+    return a->mode == GS_ADAM_DEFERRED || a->mode == GS_ADAM_EAGER;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+gs_status gs_workspace_size(const gs_config *cfg, size_t *bytes)
+{
+    if (!valid_cfg(cfg) || !bytes) return GS_ERR_INVALID_ARG;
+    gs_ctx tmp;
+    tmp.cfg = *cfg;
+    carve(&tmp, nullptr);
+    *bytes = tmp.ws_bytes;
+    return GS_OK;
+}
+
+gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *workspace, size_t workspace_bytes)
+{
+    if (!out || !valid_cfg(cfg)) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    gs_ctx *c = new (std::nothrow) gs_ctx();
+    if (!c) return GS_ERR_OOM;
+    c->cfg = *cfg;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    carve(c, nullptr);
+    if (workspace) {
+        if (workspace_bytes < c->ws_bytes || ((uintptr_t)workspace & 255)) {
+            delete c;
+            return GS_ERR_INVALID_ARG;
+        }
+        c->ws = workspace;
+    } else {
+        if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return GS_ERR_OOM;
+        }
+        c->own_ws = true;
+    }
+    carve(c, (char *)c->ws);
+    c->w.status = &c->cnt->status;
+    c->w.num_sms = c->num_sms;
+    c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
+    if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        gs_destroy(c);
+        return GS_ERR_CUDA;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx *c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    if (c->graph.graph) cudaGraphDestroy(c->graph.graph);
+    timing_free(c);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+    return GS_OK;
+}
+
+const char *gs_last_error(const gs_ctx *c) { return c ? c->err : "null context"; }
+
+const int32_t *gs_device_counters(const gs_ctx *c) { return c ? reinterpret_cast<const int32_t *>(c->cnt) : nullptr; }
+
+gs_status gs_sync_status(gs_ctx *c, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "gs_sync_status");
+    int st = 0;
+    if (cudaMemcpy(&st, &c->cnt->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_check(c, "gs_sync_status read");
+    int zero = 0;
+    cudaMemcpy(&c->cnt->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (st) fail(c, (gs_status)st, "device latched status %d", st);
+    return (gs_status)st;
+}
+
+gs_status gs_cull(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam, int32_t *ids_out,
+                  int32_t *n_vis_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv);
+    if (st) return st;
+    if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
+    if (!ids_out || !n_vis_out) return fail(c, GS_ERR_INVALID_ARG, "NULL output");
+    if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.cam[0] = make_cam(*cam, c->cfg);
+    a.lut = make_lut(adam, scene->step + 1, adam && adam->mode == GS_ADAM_DEFERRED && sv.m && sv.v && sv.counter);
+    a.n_views = 1;
+    set_args(c, SLOT_CULL, a, s);
+    launch_cull(sv, c->args + SLOT_CULL, 0, c->mask, c->chunk, c->w, s);
+    compact_mask(c->mask, sv.n, c->chunk, true, ids_out, c->wprefix, (int)c->cfg.max_visible, &c->cnt->n_vis, c->w, s);
+    cudaMemcpyAsync(n_vis_out, &c->cnt->n_vis, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    return cuda_check(c, "gs_cull");
+}
+
+gs_status gs_render_fwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                        const int32_t *ids, const int32_t *n_vis, float *image_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv);
+    if (st) return st;
+    if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
+    if (!ids || !n_vis || !image_out) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.cam[0] = make_cam(*cam, c->cfg);
+    a.lut = make_lut(adam, scene->step + 1, adam && adam->mode == GS_ADAM_DEFERRED && sv.m && sv.v && sv.counter);
+    a.n_views = 1;
+    set_args(c, SLOT_RENDER, a, s);
+    cudaMemcpyAsync(c->n_render, n_vis, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], image_out, false, nullptr,
+                   nullptr, c->w, s);
+    c->have_fwd = true;
+    c->fwd_sc = sv;
+    c->fwd_cam = a.cam[0];
+    return cuda_check(c, "gs_render_fwd");
+}
+
+gs_status gs_render_bwd(gs_ctx *c, const float *dL_dimage, float *grad_compact, int64_t cap, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->have_fwd) return fail(c, GS_ERR_INVALID_ARG, "gs_render_bwd without a gs_render_fwd");
+    if (!dL_dimage || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    render_backward(c->fwd_sc, c->args + SLOT_RENDER, 0, c->n_render, c->rb, c->fwd_cam, dL_dimage, grad_compact, cap,
+                    nullptr, nullptr, nullptr, false, c->w, s);
+    return cuda_check(c, "gs_render_bwd");
+}
+
+gs_status gs_loss_l1(gs_ctx *c, const float *image, const float *target, int64_t count, float *loss_out,
+                     float *dL_dimage, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!image || !target || !loss_out || count <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
+    launch_loss_l1(image, target, count, loss_out, dL_dimage, c->w, (cudaStream_t)stream);
+    return cuda_check(c, "gs_loss_l1");
+}
+
+gs_status gs_adam_deferred(gs_ctx *c, gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
+                           const float *grad_compact, int64_t cap, const gs_adam_cfg *adam, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, true, sv);
+    if (st) return st;
+    if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (!ids || !n_vis || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED);
+    a.n_views = 0;
+    set_args(c, SLOT_ADAM, a, s);
+    int icap = (int)(cap < c->cfg.max_visible ? cap : c->cfg.max_visible);
+    launch_ids_to_mask(ids, n_vis, icap, c->amask, sv.n, c->w, s);
+    compact_mask(c->amask, sv.n, c->achunk, false, nullptr, c->aprefix, (int)sv.n, c->n_tmp, c->w, s);
+    if (adam->mode == GS_ADAM_DEFERRED)
+        launch_adam_deferred(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->umask, c->uchunk,
+                             c->uids, &c->cnt->n_upd, c->w, s);
+    else
+        launch_adam_eager(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->w, s);
+    st = cuda_check(c, "gs_adam_deferred");
+    if (!st) scene->step += 1;
+    return st;
+}
+
+gs_status gs_adam_materialize(gs_ctx *c, const gs_scene *scene, const gs_adam_cfg *adam, float *w_out, float *m_out,
+                              float *v_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, true, sv);
+    if (st) return st;
+    if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.lut = make_lut(adam, scene->step + 1, true);
+    set_args(c, SLOT_ADAM, a, s);
+    launch_materialize(sv, c->args + SLOT_ADAM, w_out, m_out, v_out, c->w, s);
+    return cuda_check(c, "gs_adam_materialize");
+}
+
+gs_status gs_grad_scatter(gs_ctx *c, const gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
+                          const float *grad_compact, int64_t cap, float *grad_full, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv);
+    if (st) return st;
+    if (!ids || !n_vis || !grad_compact || !grad_full || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
+    int icap = (int)(cap < c->cfg.max_visible ? cap : c->cfg.max_visible);
+    launch_grad_scatter(ids, n_vis, icap, grad_compact, cap, sv.D, grad_full, sv.pitch, c->w, (cudaStream_t)stream);
+    return cuda_check(c, "gs_grad_scatter");
+}
+
+gs_status gs_timing_enable(gs_ctx *c, int32_t max_steps)
+{
+    if (!c || max_steps < 0 || max_steps > 1000000) return GS_ERR_INVALID_ARG;
+    timing_free(c);
+    if (max_steps == 0) return GS_OK;
+    c->t_events = (cudaEvent_t *)calloc((size_t)max_steps * TP_COUNT, sizeof(cudaEvent_t));
+    if (!c->t_events) return GS_ERR_OOM;
+    c->t_max = max_steps;
+    for (int k = 0; k < max_steps * TP_COUNT; k++)
+        if (cudaEventCreate(&c->t_events[k]) != cudaSuccess) {
+            c->t_max = k / TP_COUNT;
+            timing_free(c);
+            return cuda_check(c, "gs_timing_enable");
+        }
+    return GS_OK;
+}
+
+gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *steps_out)
+{
+    if (!c || !ms_out || !steps_out) return GS_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_check(c, "gs_timing_read");
+    static const int span[GS_TIMING_SPANS][2] = {{TP_STEP0, TP_STEP1}, {TP_CULL0, TP_CULL1}, {TP_FWD0, TP_FWD1},
+                                                 {TP_BWD0, TP_BWD1}, {TP_ADAM0, TP_ADAM1}, {TP_APPLY0, TP_APPLY1}};
+    int n = c->t_used < max_steps ? c->t_used : max_steps;
+    for (int st = 0; st < n; st++) {
+        cudaEvent_t *ev = c->t_events + (size_t)st * TP_COUNT;
+        for (int k = 0; k < GS_TIMING_SPANS; k++) {
+            float ms = -1.f;
+            if (cudaEventElapsedTime(&ms, ev[span[k][0]], ev[span[k][1]]) != cudaSuccess) {
+                cudaGetLastError();
+                ms = -1.f;
+            }
+            ms_out[st * GS_TIMING_SPANS + k] = ms;
+        }
+    }
+    *steps_out = n;
+    c->t_used = 0;
+    return GS_OK;
+}
+
+gs_status gs_step_kernel_count(const gs_ctx *c, int32_t *kernels)
+{
+    if (!c || !kernels) return GS_ERR_INVALID_ARG;
+    *kernels = c->graph.exec ? c->graph.kernels : 0;
+    return GS_OK;
+}
+
+gs_status gs_render_lists(const gs_ctx *c, const uint32_t **tile_of_key, const uint32_t **splat_of_key,
+                          const int32_t **n_keys, const uint32_t **ranges)
+{
+    if (!c || !c->have_fwd || !tile_of_key || !splat_of_key || !n_keys || !ranges) return GS_ERR_INVALID_ARG;
+    *tile_of_key = c->rb.sorted_keys;
+    *splat_of_key = c->rb.sorted_vals;
+    *n_keys = c->rb.n_keys;
+    *ranges = reinterpret_cast<const uint32_t *>(c->rb.ranges);
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gs_step: the whole iteration enqueued on one stream; captured once into a
+// CUDA graph and replayed, with only the argument block (cameras, targets,
+// restore tables of the new step) updated between replays.
+static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, int mode, float *loss,
+                         cudaStream_t s)
+{
+    const int V = (int)c->cfg.max_visible;
+    DevArgs *args = c->args + SLOT_STEP;
+    c->w.mark(TP_STEP0, s);
+    set_args(c, SLOT_STEP, a, s);
+    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    for (int v = 0; v < n_views; v++) {
+        launch_cull(sv, args, v, c->vmask[v], c->chunk, c->w, s);
+        compact_mask(c->vmask[v], sv.n, c->chunk, true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
+    }
+    cudaMemcpyAsync(&c->cnt->n_vis, c->nvis_view, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    const uint32_t *gmask = c->vmask[0], *gprefix = c->vprefix[0];
+    int64_t gcap = V;
+    if (n_views > 1) {
+        const int64_t nw = (sv.n + 31) / 32;
+        cudaMemsetAsync(c->union_mask, 0, nw * sizeof(uint32_t), s);
+        for (int v = 0; v < n_views; v++) launch_mask_or(c->union_mask, c->vmask[v], nw, c->w, s);
+        compact_mask(c->union_mask, sv.n, c->union_chunk, false, nullptr, c->union_prefix, (int)c->gcap_u,
+                     &c->cnt->n_union, c->w, s);
+        launch_zero_rows(c->grad_u, sv.D, c->gcap_u, &c->cnt->n_union, (int)c->gcap_u, c->w, s);
+        gmask = c->union_mask;
+        gprefix = c->union_prefix;
+        gcap = c->gcap_u;
+    }
+    for (int v = 0; v < n_views; v++) {
+        if (v == 0) c->w.mark(TP_FWD0, s);
+        render_forward(sv, args, v, c->vids[v], c->nvis_view + v, c->rb, a.cam[v], c->img, true, c->dimg, loss, c->w, s);
+        if (v == 0) c->w.mark(TP_FWD1, s);
+        if (v == 0) c->w.mark(TP_BWD0, s);
+        render_backward(sv, args, v, c->nvis_view + v, c->rb, a.cam[v], c->dimg, c->grad_u, gcap,
+                        n_views > 1 ? gmask : nullptr, n_views > 1 ? gprefix : nullptr, c->vids[v], n_views > 1, c->w, s);
+        if (v == 0) c->w.mark(TP_BWD1, s);
+    }
+    c->w.mark(TP_ADAM0, s);
+    if (mode == GS_ADAM_DEFERRED)
+        launch_adam_deferred(sv, args, gmask, gprefix, c->grad_u, gcap, c->umask, c->uchunk, c->uids, &c->cnt->n_upd,
+                             c->w, s);
+    else
+        launch_adam_eager(sv, args, gmask, gprefix, c->grad_u, gcap, c->w, s);
+    c->w.mark(TP_ADAM1, s);
+    c->w.mark(TP_STEP1, s);
+}
+
+static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
+                          float *loss, bool timed)
+{
+    if (!g.exec || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
+        g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree || g.n_views != n_views || g.mode != mode ||
+        g.loss != loss || g.timed != timed)
+        return false;
+    for (int v = 0; v < n_views; v++)
+        if (g.W[v] != views[v].width || g.H[v] != views[v].height) return false;
+    return true;
+}
+
+gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const float *const *targets, int32_t n_views,
+                  const gs_adam_cfg *adam, float *loss_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, true, sv);
+    if (st) return st;
+    if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (n_views < 1 || n_views > c->cfg.max_views || !views || !targets || !loss_out)
+        return fail(c, GS_ERR_INVALID_ARG, "invalid views/targets/loss");
+    DevArgs a{};
+    for (int v = 0; v < n_views; v++) {
+        if (!valid_cam(c, &views[v]) || !targets[v]) return fail(c, GS_ERR_INVALID_ARG, "invalid view %d", v);
+        a.cam[v] = make_cam(views[v], c->cfg);
+        a.target[v] = targets[v];
+    }
+    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED);
+    a.n_views = n_views;
+    cudaStream_t s = (cudaStream_t)stream;
+    GraphCache &g = c->graph;
+    const bool timed = c->t_events != nullptr;
+    if (timed && c->t_used >= c->t_max) return fail(c, GS_ERR_CAPACITY, "timing buffer full: call gs_timing_read");
+    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed)) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        if (g.graph) {
+            cudaGraphDestroy(g.graph);
+            g.graph = nullptr;
+        }
+        cudaStream_t cs = s;
+        bool own = false;
+        if (s == nullptr || s == cudaStreamLegacy) {   // the legacy stream cannot be captured
+            cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            own = true;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            if (own) cudaStreamDestroy(cs);
+            return cuda_check(c, "gs_step begin capture");
+        }
+        c->w.tev = timed ? c->t_events : nullptr;        // slot 0 events identify the nodes
+        enqueue_step(c, sv, a, n_views, adam->mode, loss_out, cs);
+        c->w.tev = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (own) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "gs_step capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return fail(c, GS_ERR_CUDA, "gs_step instantiate: %s", cudaGetErrorString(e));
+        }
+        // locate the argument-block node
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        cudaGraphNode_t *nodes = (cudaGraphNode_t *)malloc(nn * sizeof(cudaGraphNode_t));
+        cudaGraphGetNodes(graph, nodes, &nn);
+        g.args_node = nullptr;
+        g.kernels = 0;
+        for (int p = 0; p < TP_COUNT; p++) g.ev_node[p] = nullptr;
+        for (size_t k = 0; k < nn; k++) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nodes[k], &ty);
+            if (ty == cudaGraphNodeTypeEventRecord && timed) {
+                cudaEvent_t ev;
+                cudaGraphEventRecordNodeGetEvent(nodes[k], &ev);
+                for (int p = 0; p < TP_COUNT; p++)
+                    if (ev == c->t_events[p]) g.ev_node[p] = nodes[k];
+                continue;
+            }
+            if (ty != cudaGraphNodeTypeKernel) continue;
+            g.kernels++;
+            cudaKernelNodeParams p;
+            if (cudaGraphKernelNodeGetParams(nodes[k], &p) == cudaSuccess && p.func == (void *)k_set_args) {
+                g.args_node = nodes[k];
+                g.args_params = p;
+            }
+        }
+        free(nodes);
+        g.graph = graph;
+        if (!g.args_node) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            return fail(c, GS_ERR_CUDA, "gs_step: argument node not found");
+        }
+        g.geo = scene->geo; g.sh = scene->sh; g.m = scene->m; g.v = scene->v; g.counter = scene->counter;
+        g.n = scene->n; g.pitch = scene->pitch; g.deg = scene->sh_degree; g.n_views = n_views; g.mode = adam->mode;
+        g.loss = loss_out;
+        g.timed = timed;
+        for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
+    }
+    if (timed) {
+        cudaEvent_t *ev = c->t_events + (size_t)c->t_used * TP_COUNT;
+        for (int p = 0; p < TP_COUNT; p++)
+            if (g.ev_node[p] && cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev_node[p], ev[p]) != cudaSuccess)
+                return cuda_check(c, "gs_step timing event");
+        c->t_used++;
+    }
+    DevArgs *dst = c->args + SLOT_STEP;
+    void *kargs[2] = {&a, &dst};
+    cudaKernelNodeParams p = g.args_params;
+    p.kernelParams = kargs;
+    p.extra = nullptr;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(g.exec, g.args_node, &p);
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "gs_step set args: %s", cudaGetErrorString(e));
+    e = cudaGraphLaunch(g.exec, s);
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "gs_step launch: %s", cudaGetErrorString(e));
+    scene->step += 1;
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// k_adam.cu -- the optimizer step of GS-Scale §4.3 on the GPU.
+//
+// Deferred Adam (Eqs. 2-3, pseudocode of Fig. 10): the update set is the
+// Gaussians with a gradient this step plus those whose 4-bit counter reached
+// MAX.  Members are restored through the tables (param_lut, mom_lut, var_lut)
+// and stepped with Eq. 1; every other counter is incremented.  The paper runs
+// this loop on the CPU with OpenMP over update_ids; here it is two HBM sweeps:
+//   k_adam_select  -- counters (1 B) + visibility mask: update-set bitmask,
+//                     counters of non-members incremented in place;
+//   k_compact      -- ordered id list of the update set (k_scan.cu);
+//   k_adam_apply   -- one thread per member, all D planes of w, m, v (+ g):
+//                     28 B read/written per parameter, coalesced because the
+//                     Gaussians are stored in Morton order and views see runs.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr int ADAM_BLOCK = 256;
+
+__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_select(uint8_t *__restrict__ counter,
+                                                            const uint32_t *__restrict__ vmask, int64_t n,
+                                                            const DevArgs *__restrict__ args,
+                                                            uint32_t *__restrict__ umask,
+                                                            uint32_t *__restrict__ uchunk)
+{
+    __shared__ uint32_t s_cnt[ADAM_BLOCK / 32];
+    const int max_defer = args->lut.max_defer;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        uint32_t cnt = 0;
+#pragma unroll 2
+        for (int j = 0; j < CHUNK / ADAM_BLOCK; j++) {
+            int64_t wbase = c * CHUNK + j * ADAM_BLOCK + wid * 32;
+            int64_t i = wbase + lane;
+            bool in_u = false;
+            uint32_t vw = 0;
+            if (wbase < n) vw = vmask[wbase >> 5];
+            if (i < n) {
+                int cv = counter[i];
+                bool vis = (vw >> lane) & 1u;
+                in_u = vis || cv >= max_defer;
+                if (!in_u) counter[i] = (uint8_t)(cv + 1);
+            }
+            uint32_t word = __ballot_sync(0xffffffffu, in_u);
+            if (lane == 0 && wbase < n) {
+                umask[wbase >> 5] = word;
+                cnt += __popc(word);
+            }
+        }
+        if (lane == 0) s_cnt[wid] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < ADAM_BLOCK / 32; k++) t += s_cnt[k];
+            uchunk[c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Shared copy of the step's tables.
+struct SLut {
+    float param[N_GROUPS][LUT_N];
+    float mom[LUT_N], var[LUT_N];
+    float step_size[N_GROUPS];
+    float bias_corr, omb1, omb2, eps;
+};
+
+__device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
+{
+    int t = threadIdx.x;
+    if (t < N_GROUPS * LUT_N) s.param[t / LUT_N][t % LUT_N] = L.param[t / LUT_N][t % LUT_N];
+    if (t < LUT_N) { s.mom[t] = L.mom[t]; s.var[t] = L.var[t]; }
+    if (t < N_GROUPS) s.step_size[t] = L.step_size[t];
+    if (t == 0) { s.bias_corr = L.bias_corr; s.omb1 = L.omb1; s.omb2 = L.omb2; s.eps = L.eps; }
+    __syncthreads();
+}
+
+// Restore (delay d) + Eq. 1 for one value.  d = 0 is the plain Adam step.
+__device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
+{
+    float m_new = L.mom[d] * m + L.omb1 * g;
+    float v_new = L.var[d] * v + L.omb2 * g * g;
+    float wr = restore_param(w, m, v, L.param[grp][d], d, L.eps);
+    float denom = sqrtf(v_new) / L.bias_corr + L.eps;
+    w = wr - L.step_size[grp] * m_new / denom;
+    m = m_new;
+    v = v_new;
+}
+
+__device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask, const uint32_t *__restrict__ vprefix,
+                                             int64_t i)
+{
+    uint32_t word = vmask[i >> 5];
+    uint32_t bit = (uint32_t)(i & 31);
+    if (!((word >> bit) & 1u)) return -1;
+    return (int)(vprefix[i >> 5] + __popc(word & ((1u << bit) - 1u)));
+}
+
+template <int UNROLL>
+__device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__restrict__ sh, float *__restrict__ m,
+                                          float *__restrict__ v, int64_t pitch, int D, int64_t i, int k,
+                                          const float *__restrict__ grad, int64_t gcap, int d, const SLut &L)
+{
+    for (int r0 = 0; r0 < D; r0 += UNROLL) {
+        float w_[UNROLL], m_[UNROLL], v_[UNROLL], g_[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            int r = r0 + u;
+            if (r < D) {
+                const float *wp = r < N_GEO ? geo + r * pitch + i : sh + (r - N_GEO) * pitch + i;
+                w_[u] = *wp;
+                m_[u] = m[r * pitch + i];
+                v_[u] = v[r * pitch + i];
+                g_[u] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            int r = r0 + u;
+            if (r < D) {
+                adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
+                float *wp = r < N_GEO ? geo + r * pitch + i : sh + (r - N_GEO) * pitch + i;
+                *wp = w_[u];
+                m[r * pitch + i] = m_[u];
+                v[r * pitch + i] = v_[u];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ geo, float *__restrict__ sh,
+                                                           float *__restrict__ m, float *__restrict__ v,
+                                                           uint8_t *__restrict__ counter, int64_t pitch, int D,
+                                                           const int32_t *__restrict__ uids, const int *n_upd_p,
+                                                           const uint32_t *__restrict__ vmask,
+                                                           const uint32_t *__restrict__ vprefix,
+                                                           const float *__restrict__ grad, int64_t gcap,
+                                                           const DevArgs *__restrict__ args)
+{
+    __shared__ SLut L;
+    load_slut(L, args->lut);
+    const int n_upd = *n_upd_p;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_upd; u += gridDim.x * blockDim.x) {
+        int64_t i = uids[u];
+        int d = counter[i];
+        int k = compact_index(vmask, vprefix, i);
+        if (k >= gcap) k = -1;     // outside the caller's gradient buffer: treated as zero gradient
+        adam_rows<4>(geo, sh, m, v, pitch, D, i, k, grad, gcap, d, L);
+        counter[i] = 0;
+    }
+}
+
+void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                          const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
+                          int *n_upd, Work &w, cudaStream_t s)
+{
+    int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
+    k_adam_select<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.counter, vmask, sc.n, args, umask,
+                                                                                uchunk);
+    compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s);
+    w.mark(TP_APPLY0, s);
+    k_adam_apply<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.counter, sc.pitch, sc.D,
+                                                               uids, n_upd, vmask, vprefix, grad, gcap, args);
+    w.mark(TP_APPLY1, s);
+}
+
+// Eager Adam (Eq. 1 for every Gaussian, every step): the baseline the
+// deferred update removes; counters are left alone.
+__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(float *__restrict__ geo, float *__restrict__ sh,
+                                                           float *__restrict__ m, float *__restrict__ v, int64_t pitch,
+                                                           int64_t n, int D, const uint32_t *__restrict__ vmask,
+                                                           const uint32_t *__restrict__ vprefix,
+                                                           const float *__restrict__ grad, int64_t gcap,
+                                                           const DevArgs *__restrict__ args)
+{
+    __shared__ SLut L;
+    load_slut(L, args->lut);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int k = compact_index(vmask, vprefix, i);
+        if (k >= gcap) k = -1;
+        adam_rows<4>(geo, sh, m, v, pitch, D, i, k, grad, gcap, 0, L);
+    }
+}
+
+void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, Work &w, cudaStream_t s)
+{
+    w.mark(TP_APPLY0, s);
+    k_adam_eager<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.pitch, sc.n, sc.D, vmask,
+                                                               vprefix, grad, gcap, args);
+    w.mark(TP_APPLY1, s);
+}
+
+// Catch-up without a step: m b1^c, v b2^c, w - param_lut[c] m / (sqrt(v) + eps).
+__global__ void k_materialize(const float *__restrict__ geo, const float *__restrict__ sh, const float *__restrict__ m,
+                              const float *__restrict__ v, const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
+                              int D, const DevArgs *__restrict__ args, float *w_out, float *m_out, float *v_out)
+{
+    __shared__ SLut L;
+    load_slut(L, args->lut);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int d = counter ? counter[i] : 0;
+        for (int r = 0; r < D; r++) {
+            float w = r < N_GEO ? geo[r * pitch + i] : sh[(r - N_GEO) * pitch + i];
+            float mm = m[r * pitch + i], vv = v[r * pitch + i];
+            if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[lr_group(r)][d], d, L.eps);
+            if (m_out) m_out[r * pitch + i] = d ? L.mom[d - 1] * mm : mm;
+            if (v_out) v_out[r * pitch + i] = d ? L.var[d - 1] * vv : vv;
+        }
+    }
+}
+
+void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
+                        Work &w, cudaStream_t s)
+{
+    k_materialize<<<w.grid(sc.n, 256), 256, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.counter, sc.pitch, sc.n, sc.D, args,
+                                                   w_out, m_out, v_out);
+}
+
+__global__ void k_grad_scatter(const int32_t *__restrict__ ids, const int *n_dev, int cap,
+                               const float *__restrict__ gc, int64_t gcap, int D, float *gfull, int64_t pitch)
+{
+    int cnt = min(*n_dev, cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        int64_t i = ids[k];
+        if (i < 0 || i >= pitch) continue;
+        for (int r = 0; r < D; r++) gfull[r * pitch + i] = gc[r * gcap + k];
+    }
+}
+
+void launch_grad_scatter(const int32_t *ids, const int *n_dev, int cap, const float *gc, int64_t gcap, int D,
+                         float *gfull, int64_t pitch, Work &w, cudaStream_t s)
+{
+    cudaMemsetAsync(gfull, 0, (size_t)D * pitch * sizeof(float), s);
+    k_grad_scatter<<<w.grid(cap, 256), 256, 0, s>>>(ids, n_dev, cap, gc, gcap, D, gfull, pitch);
+}
+
+}  // namespace gs

@@ -1,0 +1,114 @@
+// k_cull.cu -- frustum cull of every Gaussian (§2.4 step 1, run on the GPU as
+// in §4.2.1), plus small bitmask helpers.
+//
+// One sweep over the geometry planes (mean, log-scale, quaternion: 40 B per
+// Gaussian, plus m, v and the counter when the deferred restore of §4.3.3 is
+// applied to Gaussians whose counter is non-zero).  Output: one visibility bit
+// per Gaussian (warp ballot) and the number of visible Gaussians per
+// 2048-Gaussian chunk, from which k_scan.cu builds the ordered id list.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr int CULL_BLOCK = 256;
+
+__global__ void __launch_bounds__(CULL_BLOCK) k_cull(const float *__restrict__ geo, const float *__restrict__ m,
+                                                     const float *__restrict__ v, const uint8_t *__restrict__ counter,
+                                                     int64_t pitch, int64_t n, const DevArgs *__restrict__ args,
+                                                     int view, uint32_t *__restrict__ mask,
+                                                     uint32_t *__restrict__ chunk_cnt)
+{
+    __shared__ DevCam s_cam;
+    __shared__ float s_plut[3][LUT_N];
+    __shared__ float s_eps;
+    __shared__ int s_restore;
+    __shared__ uint32_t s_cnt[CULL_BLOCK / 32];
+    if (threadIdx.x < sizeof(DevCam) / 4)
+        ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
+    if (threadIdx.x < 3 * LUT_N) s_plut[threadIdx.x / LUT_N][threadIdx.x % LUT_N] = args->lut.param[threadIdx.x / LUT_N][threadIdx.x % LUT_N];
+    if (threadIdx.x == 0) {
+        s_eps = args->lut.eps;
+        s_restore = args->lut.restore && m != nullptr && v != nullptr && counter != nullptr;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nchunks = (n + CHUNK - 1) / CHUNK;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        uint32_t cnt = 0;
+#pragma unroll 1
+        for (int j = 0; j < CHUNK / CULL_BLOCK; j++) {
+            int64_t wbase = c * CHUNK + j * CULL_BLOCK + wid * 32;
+            int64_t i = wbase + lane;
+            int keep = 0;
+            if (i < n) {
+                float g[10];
+#pragma unroll
+                for (int r = 0; r < 10; r++) g[r] = __ldg(geo + r * pitch + i);
+                int d = s_restore ? counter[i] : 0;
+                if (d) {
+#pragma unroll
+                    for (int r = 0; r < 10; r++)
+                        g[r] = restore_param(g[r], __ldg(m + r * pitch + i), __ldg(v + r * pitch + i),
+                                             s_plut[lr_group(r)][d], d, s_eps);
+                }
+                Proj P;
+                project_gaussian(g, s_cam, P);
+                keep = P.keep;
+            }
+            uint32_t word = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0 && wbase < n) {
+                mask[wbase >> 5] = word;
+                cnt += __popc(word);
+            }
+        }
+        if (lane == 0) s_cnt[wid] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < CULL_BLOCK / 32; k++) t += s_cnt[k];
+            chunk_cnt[c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
+                 cudaStream_t s)
+{
+    int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
+    if (view == 0) w.mark(TP_CULL0, s);
+    k_cull<<<w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8), CULL_BLOCK, 0, s>>>(sc.geo, sc.m, sc.v, sc.counter, sc.pitch,
+                                                                           sc.n, args, view, mask, chunk_cnt);
+    if (view == 0) w.mark(TP_CULL1, s);
+}
+
+// Build a bitmask from an id list (ids < n).
+__global__ void k_ids_to_mask(const int32_t *__restrict__ ids, const int *n_dev, int cap, uint32_t *mask, int64_t n)
+{
+    int cnt = *n_dev;
+    if (cnt > cap) cnt = cap;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        int i = ids[k];
+        if (i >= 0 && i < n) atomicOr(mask + (i >> 5), 1u << (i & 31));
+    }
+}
+
+void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t *mask, int64_t n, Work &w,
+                        cudaStream_t s)
+{
+    cudaMemsetAsync(mask, 0, ((n + 31) / 32) * sizeof(uint32_t), s);
+    k_ids_to_mask<<<w.grid(cap, 256), 256, 0, s>>>(ids, n_dev, cap, mask, n);
+}
+
+__global__ void k_mask_or(uint32_t *dst, const uint32_t *__restrict__ src, int64_t nwords)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nwords; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] |= src[k];
+}
+
+void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s)
+{
+    k_mask_or<<<w.grid(nwords, 256), 256, 0, s>>>(dst, src, nwords);
+}
+
+}  // namespace gs

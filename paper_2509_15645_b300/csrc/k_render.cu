@@ -1,0 +1,635 @@
+// k_render.cu -- the differentiable tile rasterizer of §2.4 (steps 1-5) on the
+// visible subset chosen by the cull.
+//
+//   k_gather_project  gather of the visible Gaussians' D planes with the
+//                     deferred restore (parameter forwarding of §4.2.2 done in
+//                     place), EWA projection, SH colour, opacity -> 48 B splat
+//                     record, depth key and tile count per Gaussian
+//   depth sort        stable radix sort of the visible set by float depth bits
+//   k_emit            (tile id, Gaussian) keys in depth order
+//   tile sort         stable radix sort by tile id: per-tile depth order with
+//                     ties in ascending Gaussian id
+//   k_raster_fwd      one block per tile, one thread per pixel; the tile's
+//                     splats are staged through shared memory in batches and
+//                     composited front to back
+//   k_raster_bwd      recomputes each pixel's transmittance by a forward replay
+//                     over the tile (nothing stored per pixel), then walks the
+//                     list back to front; warp-shuffle reduction before the
+//                     atomics into the per-splat screen-space gradients
+//   k_project_bwd     chain rule to mean, log-scale, quaternion, opacity logit
+//                     and SH coefficients
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr int PROJ_BLOCK = 128;
+
+struct SLutR {
+    float param[N_GROUPS][LUT_N];
+    float eps;
+    int restore;
+};
+
+__global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
+                                                               const int *n_vis_p, int cap,
+                                                               const DevArgs *__restrict__ args, int view,
+                                                               float *__restrict__ compact, float4 *__restrict__ rec0,
+                                                               float4 *__restrict__ rec1, float4 *__restrict__ rec2,
+                                                               uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
+                                                               uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect)
+{
+    __shared__ DevCam s_cam;
+    __shared__ SLutR L;
+    if (threadIdx.x < sizeof(DevCam) / 4)
+        ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
+    for (int t = threadIdx.x; t < N_GROUPS * LUT_N; t += blockDim.x) L.param[t / LUT_N][t % LUT_N] = args->lut.param[t / LUT_N][t % LUT_N];
+    if (threadIdx.x == 0) {
+        L.eps = args->lut.eps;
+        L.restore = args->lut.restore && sc.m && sc.v && sc.counter;
+    }
+    __syncthreads();
+    const int n_vis = min(*n_vis_p, cap);
+    const int nk = (sc.deg + 1) * (sc.deg + 1);
+    const int64_t pitch = sc.pitch;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_vis; k += gridDim.x * blockDim.x) {
+        const int64_t i = ids[k];
+        if (i < 0 || i >= sc.n) {           // caller-supplied id out of range: an empty splat
+            rec0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rec1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rec2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            dkey[k] = 0u;
+            dval[k] = (uint32_t)k;
+            tcnt[k] = 0u;
+            rect[k] = make_uint2(0u, 0u);
+            for (int r = 0; r < sc.D; r++) compact[r * (int64_t)cap + k] = 0.f;
+            continue;
+        }
+        const int d = L.restore ? sc.counter[i] : 0;
+        float g[N_GEO];
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) {
+            float w = __ldg(sc.geo + r * pitch + i);
+            if (d) w = restore_param(w, __ldg(sc.m + r * pitch + i), __ldg(sc.v + r * pitch + i), L.param[lr_group(r)][d], d, L.eps);
+            g[r] = w;
+            compact[r * (int64_t)cap + k] = w;
+        }
+        Proj P;
+        project_gaussian(g, s_cam, P);
+        float vx = g[0] - s_cam.campos[0], vy = g[1] - s_cam.campos[1], vz = g[2] - s_cam.campos[2];
+        float ivn = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
+        float Y[16];
+        sh_basis(sc.deg, vx * ivn, vy * ivn, vz * ivn, Y);
+        float rgb[3] = {0.f, 0.f, 0.f};
+        for (int kk = 0; kk < nk; kk++) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                int r = 3 * kk + c;
+                float w = __ldg(sc.sh + r * pitch + i);
+                if (d) w = restore_param(w, __ldg(sc.m + (N_GEO + r) * pitch + i), __ldg(sc.v + (N_GEO + r) * pitch + i),
+                                         L.param[kk == 0 ? 4 : 5][d], d, L.eps);
+                compact[(N_GEO + r) * (int64_t)cap + k] = w;
+                rgb[c] += Y[kk] * w;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) rgb[c] = fmaxf(rgb[c] + 0.5f, 0.f);
+        float o = 1.f / (1.f + expf(-g[ROW_OPAC]));
+        rec0[k] = make_float4(P.mx, P.my, P.radius, o);
+        rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
+        rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+        dkey[k] = __float_as_uint(P.p[2]);
+        dval[k] = (uint32_t)k;
+        uint32_t cnt = P.keep ? (uint32_t)((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2])) : 0u;
+        tcnt[k] = cnt;
+        rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
+    }
+}
+
+__global__ void k_rank_counts(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ tcnt,
+                              const int *n_vis_p, int cap, uint32_t *rank_cnt)
+{
+    int n = min(*n_vis_p, cap);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        rank_cnt[r] = tcnt[sorted_vals[r]];
+}
+
+__global__ void k_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
+                       const uint2 *__restrict__ rect, const int *n_vis_p, int cap, int64_t kcap,
+                       const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval)
+{
+    int n = min(*n_vis_p, cap);
+    int tiles_x = args->cam[view].tiles_x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        uint32_t k = sorted_vals[r];
+        int64_t o = ofs[r];
+        uint2 rc = rect[k];
+        int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        for (int ty = y0; ty < y1; ty++)
+            for (int tx = x0; tx < x1; tx++) {
+                if (o < kcap) {
+                    tkey[o] = (uint32_t)(ty * tiles_x + tx);
+                    tval[o] = k;
+                }
+                o++;
+            }
+    }
+}
+
+__global__ void k_tile_ranges(const uint32_t *__restrict__ tkey, const int *n_keys_p, int64_t kcap, uint2 *ranges)
+{
+    int n = (int)min((int64_t)*n_keys_p, kcap);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        uint32_t t = tkey[p];
+        if (p == 0 || tkey[p - 1] != t) ranges[t].x = (uint32_t)p;
+        if (p == n - 1 || tkey[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+constexpr int RB = 256;   // max threads per raster block (tile_w * tile_h)
+
+__device__ __forceinline__ float block_sum(float x, float *s_red)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_red[wid] = x;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_red[k];
+    return t;
+}
+
+__global__ void __launch_bounds__(RB) k_raster_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
+                                                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                   const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
+                                                   int view, float *__restrict__ image, int use_target,
+                                                   float *__restrict__ dimage, float *__restrict__ loss)
+{
+    const float *target = use_target ? args->target[view] : nullptr;
+    __shared__ float4 s0[RB], s1[RB], s2[RB];
+    __shared__ float s_red[RB / 32];
+    const DevCam &cam = args->cam[view];
+    const int W = cam.width, H = cam.height, tw = cam.tile_w, tiles_x = cam.tiles_x;
+    const int tile = blockIdx.x;
+    const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
+    const int y = (tile / tiles_x) * cam.tile_h + (int)threadIdx.x / tw;
+    const bool inside = x < W && y < H;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = ranges[tile];
+    const int nt = blockDim.x;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    bool done = !inside;
+    for (uint32_t b = rg.x; b < rg.y; b += nt) {
+        if (__syncthreads_count(!done) == 0) break;
+        uint32_t idx = b + threadIdx.x;
+        if (idx < rg.y) {
+            uint32_t k = svals[idx];
+            s0[threadIdx.x] = rec0[k];
+            s1[threadIdx.x] = rec1[k];
+            s2[threadIdx.x] = rec2[k];
+        }
+        __syncthreads();
+        int nb = min(nt, (int)(rg.y - b));
+        if (!done) {
+            for (int j = 0; j < nb; j++) {
+                float dx, dy, G;
+                bool cl;
+                float a = splat_alpha(s0[j], s1[j], px, py, dx, dy, G, cl);
+                if (a == 0.f) continue;
+                float Tn = T * (1.f - a);
+                if (Tn < T_STOP) {
+                    done = true;
+                    break;
+                }
+                float4 c = s2[j];
+                float aT = a * T;
+                C0 += c.x * aT;
+                C1 += c.y * aT;
+                C2 += c.z * aT;
+                T = Tn;
+            }
+        }
+    }
+    const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+    float part = 0.f;
+    if (inside) {
+        image[pix] = C0;
+        image[HW + pix] = C1;
+        image[2 * HW + pix] = C2;
+        if (target) {
+            float inv = 1.f / (float)(3 * HW);
+            float d0 = C0 - target[pix], d1 = C1 - target[HW + pix], d2 = C2 - target[2 * HW + pix];
+            dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
+            dimage[HW + pix] = (d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f));
+            dimage[2 * HW + pix] = (d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f));
+            part = (fabsf(d0) + fabsf(d1) + fabsf(d2)) * inv;
+        }
+    }
+    if (target) {
+        __syncthreads();
+        float t = block_sum(part, s_red);
+        if (threadIdx.x == 0) atomicAdd(loss, t);
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(RB) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
+                                                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                   const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
+                                                   int view, const float *__restrict__ dimage, float *__restrict__ g9,
+                                                   int64_t gcap)
+{
+    __shared__ float4 s0[RB], s1[RB], s2[RB];
+    __shared__ uint32_t s_k[RB];
+    __shared__ int s_end;
+    const DevCam &cam = args->cam[view];
+    const int W = cam.width, H = cam.height, tw = cam.tile_w, tiles_x = cam.tiles_x;
+    const int tile = blockIdx.x;
+    const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
+    const int y = (tile / tiles_x) * cam.tile_h + (int)threadIdx.x / tw;
+    const bool inside = x < W && y < H;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = ranges[tile];
+    const int nt = blockDim.x;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_end = (int)rg.x;
+    // phase 1: forward replay -> final transmittance and last contributor
+    float T = 1.f;
+    int last = -1;
+    bool done = !inside;
+    for (uint32_t b = rg.x; b < rg.y; b += nt) {
+        if (__syncthreads_count(!done) == 0) break;
+        uint32_t idx = b + threadIdx.x;
+        if (idx < rg.y) {
+            uint32_t k = svals[idx];
+            s0[threadIdx.x] = rec0[k];
+            s1[threadIdx.x] = rec1[k];
+        }
+        __syncthreads();
+        int nb = min(nt, (int)(rg.y - b));
+        if (!done) {
+            for (int j = 0; j < nb; j++) {
+                float dx, dy, G;
+                bool cl;
+                float a = splat_alpha(s0[j], s1[j], px, py, dx, dy, G, cl);
+                if (a == 0.f) continue;
+                float Tn = T * (1.f - a);
+                if (Tn < T_STOP) {
+                    done = true;
+                    break;
+                }
+                T = Tn;
+                last = (int)(b + j);
+            }
+        }
+    }
+    __syncthreads();
+    if (last >= 0) atomicMax(&s_end, last + 1);
+    __syncthreads();
+    const int end = s_end;
+    // phase 2: back to front
+    const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) {
+        g0 = dimage[pix];
+        g1 = dimage[HW + pix];
+        g2 = dimage[2 * HW + pix];
+    }
+    float R0 = 0.f, R1 = 0.f, R2 = 0.f;          // colour behind the current splat (background 0)
+    float la = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
+    float Tc = T;
+    for (int bend = end; bend > (int)rg.x; bend -= nt) {
+        int bstart = max((int)rg.x, bend - nt);
+        __syncthreads();
+        int idx = bstart + (int)threadIdx.x;
+        if (idx < bend) {
+            uint32_t k = svals[idx];
+            s_k[threadIdx.x] = k;
+            s0[threadIdx.x] = rec0[k];
+            s1[threadIdx.x] = rec1[k];
+            s2[threadIdx.x] = rec2[k];
+        }
+        __syncthreads();
+        for (int j = bend - bstart - 1; j >= 0; j--) {
+            const int gi = bstart + j;
+            float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contrib = false;
+            if (gi <= last) {
+                float dx, dy, G;
+                bool cl;
+                float4 r0 = s0[j], r1 = s1[j];
+                float a = splat_alpha(r0, r1, px, py, dx, dy, G, cl);
+                if (a != 0.f) {
+                    contrib = true;
+                    Tc = Tc / (1.f - a);
+                    float4 c = s2[j];
+                    R0 = la * lc0 + (1.f - la) * R0;
+                    R1 = la * lc1 + (1.f - la) * R1;
+                    R2 = la * lc2 + (1.f - la) * R2;
+                    float dLda = Tc * (g0 * (c.x - R0) + g1 * (c.y - R1) + g2 * (c.z - R2));
+                    float aT = a * Tc;
+                    v[6] = g0 * aT;
+                    v[7] = g1 * aT;
+                    v[8] = g2 * aT;
+                    if (!cl) {
+                        v[5] = G * dLda;
+                        float ds = -a * dLda;
+                        v[0] = ds * (r1.x * dx + r1.y * dy);
+                        v[1] = ds * (r1.y * dx + r1.z * dy);
+                        v[2] = 0.5f * ds * dx * dx;
+                        v[3] = ds * dx * dy;
+                        v[4] = 0.5f * ds * dy * dy;
+                    }
+                    la = a;
+                    lc0 = c.x;
+                    lc1 = c.y;
+                    lc2 = c.z;
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const uint32_t k = s_k[j];
+#pragma unroll
+                for (int f = 0; f < 9; f++) {
+                    float s = warp_sum(v[f]);
+                    if (lane == 0 && s != 0.f) atomicAdd(g9 + f * gcap + k, s);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chain rule of the projection (FP32 counterpart of the adjoint in §2.4 step 5).
+__global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restrict__ compact, int cap, int deg,
+                                                            const int *n_vis_p, const DevArgs *__restrict__ args, int view,
+                                                            const float *__restrict__ g9, float *__restrict__ grad,
+                                                            int64_t gcap, const int32_t *__restrict__ ids,
+                                                            const uint32_t *__restrict__ rmask,
+                                                            const uint32_t *__restrict__ rprefix, int accumulate,
+                                                            int *status)
+{
+    __shared__ DevCam s_cam;
+    if (threadIdx.x < sizeof(DevCam) / 4)
+        ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
+    __syncthreads();
+    const int n_vis = min(*n_vis_p, cap);
+    const int nk = (deg + 1) * (deg + 1);
+    const int D = N_GEO + 3 * nk;
+    const DevCam &cam = s_cam;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_vis; k += gridDim.x * blockDim.x) {
+        int64_t kk = k;
+        if (rmask) {
+            int64_t i = ids[k];
+            if (i < 0) continue;
+            uint32_t word = rmask[i >> 5];
+            kk = rprefix[i >> 5] + __popc(word & ((1u << (i & 31)) - 1u));
+        }
+        if (kk >= gcap) {          // the caller's gradient buffer is smaller than the visible set
+            latch(status, GS_ERR_CAPACITY);
+            continue;
+        }
+        float g[N_GEO];
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) g[r] = compact[r * (int64_t)cap + k];
+        float gs[9];
+#pragma unroll
+        for (int f = 0; f < 9; f++) gs[f] = g9[f * (int64_t)cap + k];
+        Proj P;
+        project_gaussian(g, cam, P);
+        float out[N_GEO];
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) out[r] = 0.f;
+        bool ok = P.keep != 0;
+        // ---- colour: SH coefficients and the viewing direction
+        float vx = g[0] - cam.campos[0], vy = g[1] - cam.campos[1], vz = g[2] - cam.campos[2];
+        float vn = sqrtf(vx * vx + vy * vy + vz * vz), ivn = 1.f / vn;
+        float dir[3] = {vx * ivn, vy * ivn, vz * ivn};
+        float Y[16];
+        sh_basis(deg, dir[0], dir[1], dir[2], Y);
+        float raw[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q < nk; q++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) raw[c] += Y[q] * compact[(N_GEO + 3 * q + c) * (int64_t)cap + k];
+        float grgb[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) grgb[c] = (ok && raw[c] + 0.5f >= 0.f) ? gs[6 + c] : 0.f;
+        float h[16];
+        for (int q = 0; q < nk; q++) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float coef = compact[(N_GEO + 3 * q + c) * (int64_t)cap + k];
+                acc += grgb[c] * coef;
+                float gv = Y[q] * grgb[c];
+                float *dst = grad + (N_GEO + 3 * q + c) * gcap + kk;
+                if (accumulate) *dst += gv; else *dst = gv;
+            }
+            h[q] = acc;
+        }
+        float gdir[3];
+        sh_basis_vjp(deg, dir[0], dir[1], dir[2], h, gdir);
+        float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+        float gmu[3] = {(gdir[0] - dir[0] * dd) * ivn, (gdir[1] - dir[1] * dd) * ivn, (gdir[2] - dir[2] * dd) * ivn};
+        if (ok) {
+            // ---- opacity logit
+            float o = 1.f / (1.f + expf(-g[ROW_OPAC]));
+            out[ROW_OPAC] = gs[5] * o * (1.f - o);
+            // ---- conic -> covariance (a, b, c)
+            float a = P.a, b = P.b, c = P.c;
+            float id2 = 1.f / (P.det * P.det);
+            float gA = gs[2], gB = gs[3], gC = gs[4];
+            float ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
+            float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * id2;
+            float gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+            float hb = 0.5f * gb;
+            // ---- Sigma2 = T Sigma3 T^T + 0.3 I
+            const float *T = P.T;
+            // gS3 = ga t0 t0^T + hb (t0 t1^T + t1 t0^T) + gc t1 t1^T (symmetric)
+            float gS[9];
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int q = 0; q < 3; q++)
+                    gS[r * 3 + q] = ga * T[r] * T[q] + hb * (T[r] * T[3 + q] + T[3 + r] * T[q]) + gc * T[3 + r] * T[3 + q];
+            // gT = 2 G2 T Sigma3
+            float S3f[9] = {P.S3[0], P.S3[1], P.S3[2], P.S3[1], P.S3[3], P.S3[4], P.S3[2], P.S3[4], P.S3[5]};
+            float e0[3], e1[3];
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                e0[q] = 2.f * (ga * T[q] + hb * T[3 + q]);
+                e1[q] = 2.f * (hb * T[q] + gc * T[3 + q]);
+            }
+            float gT[6];
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                gT[q] = e0[0] * S3f[0 * 3 + q] + e0[1] * S3f[1 * 3 + q] + e0[2] * S3f[2 * 3 + q];
+                gT[3 + q] = e1[0] * S3f[0 * 3 + q] + e1[1] * S3f[1 * 3 + q] + e1[2] * S3f[2 * 3 + q];
+            }
+            // gJ = gT W^T (entries 00, 02, 11, 12)
+            const float *R = cam.R;
+            float gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
+            float gJ02 = gT[0] * R[6] + gT[1] * R[7] + gT[2] * R[8];
+            float gJ11 = gT[3] * R[3] + gT[4] * R[4] + gT[5] * R[5];
+            float gJ12 = gT[3] * R[6] + gT[4] * R[7] + gT[5] * R[8];
+            float pxc = P.p[0], pyc = P.p[1], pz = P.p[2];
+            float iz = 1.f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
+            float fx = cam.fx, fy = cam.fy;
+            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+            gp2 += -(gJ00 * fx + gJ11 * fy) * iz2;
+            if (!P.cu) {
+                gp0 += -gJ02 * fx * iz2;
+                gp2 += 2.f * gJ02 * fx * pxc * iz3;
+            } else {
+                float lim = pxc > 0.f ? cam.limx : -cam.limx;
+                gp2 += gJ02 * fx * lim * iz2;
+            }
+            if (!P.cw) {
+                gp1 += -gJ12 * fy * iz2;
+                gp2 += 2.f * gJ12 * fy * pyc * iz3;
+            } else {
+                float lim = pyc > 0.f ? cam.limy : -cam.limy;
+                gp2 += gJ12 * fy * lim * iz2;
+            }
+            // mean2d
+            gp0 += gs[0] * fx * iz;
+            gp1 += gs[1] * fy * iz;
+            gp2 += -(gs[0] * fx * pxc + gs[1] * fy * pyc) * iz2;
+            // p = W mu + t
+            gmu[0] += R[0] * gp0 + R[3] * gp1 + R[6] * gp2;
+            gmu[1] += R[1] * gp0 + R[4] * gp1 + R[7] * gp2;
+            gmu[2] += R[2] * gp0 + R[5] * gp1 + R[8] * gp2;
+            // Sigma3 = M M^T, M = Rq diag(s): gM = 2 gS M
+            float M[9];
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int q = 0; q < 3; q++) M[r * 3 + q] = P.Rq[r * 3 + q] * P.s[q];
+            float gR[9];
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                float gsc = 0.f;
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    float gm = 2.f * (gS[r * 3 + 0] * M[0 * 3 + q] + gS[r * 3 + 1] * M[1 * 3 + q] + gS[r * 3 + 2] * M[2 * 3 + q]);
+                    gsc += gm * P.Rq[r * 3 + q];
+                    gR[r * 3 + q] = gm * P.s[q];
+                }
+                out[ROW_LS + q] = gsc * P.s[q];
+            }
+            // rotation -> normalised quaternion -> quaternion
+            float qw = P.qh[0], qx = P.qh[1], qy = P.qh[2], qz = P.qh[3];
+            float gw = -2.f * qz * gR[1] + 2.f * qy * gR[2] + 2.f * qz * gR[3] - 2.f * qx * gR[5] - 2.f * qy * gR[6] + 2.f * qx * gR[7];
+            float gx = 2.f * qy * gR[1] + 2.f * qz * gR[2] + 2.f * qy * gR[3] - 4.f * qx * gR[4] - 2.f * qw * gR[5] + 2.f * qz * gR[6] + 2.f * qw * gR[7] - 4.f * qx * gR[8];
+            float gy = -4.f * qy * gR[0] + 2.f * qx * gR[1] + 2.f * qw * gR[2] + 2.f * qx * gR[3] + 2.f * qz * gR[5] - 2.f * qw * gR[6] + 2.f * qz * gR[7] - 4.f * qy * gR[8];
+            float gz = -4.f * qz * gR[0] - 2.f * qw * gR[1] + 2.f * qx * gR[2] + 2.f * qw * gR[3] - 4.f * qz * gR[4] + 2.f * qy * gR[5] + 2.f * qx * gR[6] + 2.f * qy * gR[7];
+            float dq = gw * qw + gx * qx + gy * qy + gz * qz;
+            float iqn = 1.f / P.qn;
+            out[ROW_QUAT + 0] = (gw - qw * dq) * iqn;
+            out[ROW_QUAT + 1] = (gx - qx * dq) * iqn;
+            out[ROW_QUAT + 2] = (gy - qy * dq) * iqn;
+            out[ROW_QUAT + 3] = (gz - qz * dq) * iqn;
+        }
+        out[0] = ok ? gmu[0] : 0.f;
+        out[1] = ok ? gmu[1] : 0.f;
+        out[2] = ok ? gmu[2] : 0.f;
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) {
+            float *dst = grad + r * gcap + kk;
+            if (accumulate) *dst += out[r]; else *dst = out[r];
+        }
+        (void)D;
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap)
+{
+    int n = n_dev ? min(*n_dev, cap) : cap;
+    int64_t total = (int64_t)rows * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / n, k = e - r * n;
+        buf[r * pitch + k] = 0.f;
+    }
+}
+
+void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s)
+{
+    k_zero_rows<<<w.grid((int64_t)rows * cap, 256), 256, 0, s>>>(buf, rows, pitch, n_dev, cap);
+}
+
+__global__ void k_loss_l1(const float *__restrict__ image, const float *__restrict__ target, int64_t count,
+                          float *loss, float *dimage)
+{
+    __shared__ float s_red[32];
+    float inv = 1.f / (float)count, part = 0.f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        float d = image[e] - target[e];
+        part += fabsf(d);
+        if (dimage) dimage[e] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    }
+    float t = block_sum(part * inv, s_red);
+    if (threadIdx.x == 0) atomicAdd(loss, t);
+}
+
+void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
+                    cudaStream_t s)
+{
+    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    k_loss_l1<<<w.grid(count, 256, 4), 256, 0, s>>>(image, target, count, loss, dimage);
+}
+
+static int bits_for(int n)
+{
+    int b = 1;
+    while ((1 << b) < n) b++;
+    return b;
+}
+
+void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
+                    RenderBufs &rb, const DevCam &cam, float *image, bool use_target, float *dimage, float *loss,
+                    Work &w, cudaStream_t s)
+{
+    const int cap = (int)rb.cap;
+    k_gather_project<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
+        sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1, rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect);
+    // depth order of the visible set (stable: ties keep ascending index)
+    int dcur = radix_sort(rb.dk[0], rb.dv[0], rb.dk[1], rb.dv[1], n_vis, cap, 32, w, s);
+    const uint32_t *dsorted = rb.dv[dcur];
+    k_rank_counts<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.tcnt, n_vis, cap, rb.rank_cnt);
+    ScanLen L{n_vis, 1, 1, 0, 0, cap};
+    scan_exclusive(rb.rank_cnt, rb.rank_cnt, L, w, rb.n_keys, (int)rb.kcap, s);
+    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, n_vis, cap, rb.kcap, args, view, rb.tk[0],
+                                            rb.tv[0]);
+    const int tiles = cam.tiles_x * cam.tiles_y;
+    int tcur = radix_sort(rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_keys, (int)rb.kcap, bits_for(tiles), w, s);
+    cudaMemsetAsync(rb.ranges, 0, (size_t)tiles * sizeof(uint2), s);
+    k_tile_ranges<<<w.grid(rb.kcap, 256), 256, 0, s>>>(rb.tk[tcur], rb.n_keys, rb.kcap, rb.ranges);
+    rb.sorted_keys = rb.tk[tcur];
+    rb.sorted_vals = rb.tv[tcur];
+    rb.tiles = tiles;
+    k_raster_fwd<<<tiles, cam.tile_w * cam.tile_h, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args,
+                                                           view, image, use_target ? 1 : 0, dimage, loss);
+}
+
+void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
+                     const DevCam &cam, const float *dimage, float *grad, int64_t gcap, const uint32_t *remap_mask,
+                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s)
+{
+    const int cap = (int)rb.cap;
+    launch_zero_rows(rb.g9, 9, cap, n_vis, cap, w, s);
+    k_raster_bwd<<<rb.tiles, cam.tile_w * cam.tile_h, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2,
+                                                              args, view, dimage, rb.g9, cap);
+    k_project_bwd<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9,
+                                                                     grad, gcap, ids, remap_mask, remap_prefix,
+                                                                     accumulate ? 1 : 0, w.status);
+}
+
+}  // namespace gs

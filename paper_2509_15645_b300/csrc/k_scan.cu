@@ -1,0 +1,290 @@
+// k_scan.cu -- device-wide exclusive scan, ordered compaction of a bitmask,
+// and a stable LSD radix sort, all with data-dependent lengths read from
+// device memory so that callers never synchronise (graph capture).
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr int SCAN_BLOCK = 256;
+constexpr int SCAN_ITEMS = 8;
+
+__device__ __forceinline__ int scan_length(ScanLen L)
+{
+    if (!L.n_dev) return L.fixed;
+    int n = *L.n_dev;
+    if (L.cap > 0 && n > L.cap) n = L.cap;
+    return L.mul * ((n + L.div - 1) / L.div) + L.add;
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *total, uint32_t *s_warp)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = s_warp[wid] + incl - x;
+    if (total) *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, ScanLen L, uint32_t *partials)
+{
+    __shared__ uint32_t s_warp[33];
+    int len = scan_length(L);
+    int seg = (len + gridDim.x - 1) / gridDim.x;
+    int lo = blockIdx.x * seg, hi = min(len, lo + seg);
+    uint32_t acc = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += in[i];
+    uint32_t tot;
+    block_excl_scan(acc, &tot, s_warp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_partials(uint32_t *partials, int g, int *total_out, int total_cap, int *status)
+{
+    __shared__ uint32_t s_warp[33];
+    // g <= 1024: each of 256 threads holds up to 4 partials
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        int idx = threadIdx.x * 4 + j;
+        v[j] = idx < g ? partials[idx] : 0u;
+        s += v[j];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, &tot, s_warp);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        int idx = threadIdx.x * 4 + j;
+        if (idx < g) partials[idx] = ex;
+        ex += v[j];
+    }
+    if (threadIdx.x == 0 && total_out) {
+        int t = (int)tot;
+        if (total_cap > 0 && t > total_cap) {
+            if (status) latch(status, GS_ERR_CAPACITY);
+            t = total_cap;
+        }
+        *total_out = t;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t *in, uint32_t *out, ScanLen L, const uint32_t *__restrict__ partials)
+{
+    __shared__ uint32_t s_warp[33];
+    int len = scan_length(L);
+    int seg = (len + gridDim.x - 1) / gridDim.x;
+    int lo = blockIdx.x * seg, hi = min(len, lo + seg);
+    uint32_t carry = partials[blockIdx.x];
+    for (int base = lo; base < hi; base += SCAN_BLOCK * SCAN_ITEMS) {
+        uint32_t v[SCAN_ITEMS], s = 0;
+        int i0 = base + threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            v[j] = (i0 + j < hi) ? in[i0 + j] : 0u;
+            s += v[j];
+        }
+        uint32_t tot;
+        uint32_t ex = block_excl_scan(s, &tot, s_warp) + carry;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            if (i0 + j < hi) out[i0 + j] = ex;
+            ex += v[j];
+        }
+        carry += tot;
+    }
+}
+
+void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *total_out, int total_cap,
+                    cudaStream_t s)
+{
+    int g = w.scan_grid;
+    k_scan_reduce<<<g, SCAN_BLOCK, 0, s>>>(in, L, w.partials);
+    k_scan_partials<<<1, 256, 0, s>>>(w.partials, g, total_out, total_cap, w.status);
+    k_scan_down<<<g, SCAN_BLOCK, 0, s>>>(in, out, L, w.partials);
+}
+
+// ---------------------------------------------------------------------------
+// Ordered compaction of a bitmask (bit i of word i/32).  chunk_ofs holds the
+// exclusive scan of per-chunk popcounts.  Writes ids (ascending, only those
+// below cap) and word_prefix[w] = number of set bits before word w.
+__global__ void k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords, const uint32_t *__restrict__ chunk_ofs,
+                               int32_t *ids, uint32_t *word_prefix, int cap)
+{
+    __shared__ uint32_t s_pref[CHUNK_WORDS];
+    __shared__ uint32_t s_warp[33];
+    int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        int64_t w0 = c * CHUNK_WORDS;
+        uint32_t word = 0;
+        if (threadIdx.x < CHUNK_WORDS && w0 + threadIdx.x < nwords) word = mask[w0 + threadIdx.x];
+        uint32_t cnt = threadIdx.x < CHUNK_WORDS ? __popc(word) : 0u;
+        uint32_t ex = block_excl_scan(cnt, nullptr, s_warp);
+        uint32_t base = chunk_ofs[c];
+        if (threadIdx.x < CHUNK_WORDS) {
+            s_pref[threadIdx.x] = base + ex;
+            if (w0 + threadIdx.x < nwords && word_prefix) word_prefix[w0 + threadIdx.x] = base + ex;
+        }
+        __syncthreads();
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int j = wid; j < CHUNK_WORDS; j += nw) {
+            if (w0 + j >= nwords) break;
+            uint32_t m = mask[w0 + j];
+            if ((m >> lane) & 1u) {
+                uint32_t pos = s_pref[j] + __popc(m & ((1u << lane) - 1u));
+                if (ids && (int)pos < cap) ids[pos] = (int32_t)((w0 + j) * 32 + lane);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_chunk_counts(const uint32_t *__restrict__ mask, int64_t nwords, uint32_t *chunk_cnt)
+{
+    int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = warp; c < nchunks; c += nwarps) {
+        int64_t w0 = c * CHUNK_WORDS;
+        uint32_t s = 0;
+        for (int j = lane; j < CHUNK_WORDS; j += 32)
+            if (w0 + j < nwords) s += __popc(mask[w0 + j]);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) chunk_cnt[c] = s;
+    }
+}
+
+void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
+                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s)
+{
+    int64_t nwords = (n + 31) / 32;
+    int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
+    if (!have_counts)
+        k_chunk_counts<<<w.grid(nchunks * 32, 256), 256, 0, s>>>(mask, nwords, chunk_cnt);
+    ScanLen L{nullptr, 1, 1, 0, (int)nchunks, 0};
+    scan_exclusive(chunk_cnt, chunk_cnt, L, w, count_out, cap, s);
+    k_compact_mask<<<w.grid(nchunks * 256, 256), 256, 0, s>>>(mask, nwords, chunk_cnt, ids, word_prefix, cap);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value) pairs on bits [0, nbits) of the key,
+// 8-bit digits.  Each pass: per-tile digit histograms -> exclusive scan over
+// (digit, tile) -> stable scatter with per-tile ranks.
+constexpr int RS_BLOCK = 256, RS_ITEMS = 16, RS_TILE = RS_BLOCK * RS_ITEMS, RS_WARPS = RS_BLOCK / 32;
+
+__device__ __forceinline__ int rs_count(const int *n_dev, int cap)
+{
+    int n = *n_dev;
+    return n > cap ? cap : n;
+}
+
+__global__ void __launch_bounds__(RS_BLOCK) k_radix_hist(const uint32_t *__restrict__ keys, const int *n_dev, int cap,
+                                                         int shift, uint32_t dmask, uint32_t *hist)
+{
+    __shared__ uint32_t s_h[256];
+    int n = rs_count(n_dev, cap);
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        s_h[threadIdx.x] = 0;
+        __syncthreads();
+        int base = t * RS_TILE;
+#pragma unroll 4
+        for (int j = 0; j < RS_ITEMS; j++) {
+            int idx = base + j * RS_BLOCK + threadIdx.x;
+            if (idx < n) atomicAdd(&s_h[(keys[idx] >> shift) & dmask], 1u);
+        }
+        __syncthreads();
+        hist[threadIdx.x * ntiles + t] = s_h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RS_BLOCK) k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                            uint32_t *kout, uint32_t *vout, const int *n_dev, int cap,
+                                                            int shift, uint32_t dmask, const uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s_ofs[256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_wc[RS_WARPS][256];
+    int n = rs_count(n_dev, cap);
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t lt = (1u << lane) - 1u;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        s_ofs[threadIdx.x] = hist[threadIdx.x * ntiles + t];
+        s_run[threadIdx.x] = 0;
+        int base = t * RS_TILE;
+        for (int j = 0; j < RS_ITEMS; j++) {
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; w++) s_wc[w][threadIdx.x] = 0;
+            __syncthreads();
+            int idx = base + j * RS_BLOCK + threadIdx.x;
+            bool valid = idx < n;
+            uint32_t key = valid ? kin[idx] : 0u, val = valid ? vin[idx] : 0u;
+            uint32_t d = (key >> shift) & dmask;
+            uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+            uint32_t wrank = __popc(peers & lt);
+            if (valid && wrank == 0) s_wc[wid][d] = __popc(peers);
+            __syncthreads();
+            {
+                uint32_t run = s_run[threadIdx.x];
+#pragma unroll
+                for (int w = 0; w < RS_WARPS; w++) {
+                    uint32_t c = s_wc[w][threadIdx.x];
+                    s_wc[w][threadIdx.x] = run;
+                    run += c;
+                }
+                s_run[threadIdx.x] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = s_ofs[d] + s_wc[wid][d] + wrank;
+                kout[pos] = key;
+                vout[pos] = val;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
+               Work &w, cudaStream_t s)
+{
+    int cur = 0;
+    uint32_t *K[2] = {k0, k1}, *V[2] = {v0, v1};
+    int ntiles_cap = (cap + RS_TILE - 1) / RS_TILE;
+    int g = w.grid((int64_t)ntiles_cap * RS_BLOCK, RS_BLOCK);
+    for (int shift = 0; shift < nbits; shift += 8) {
+        int bits = nbits - shift < 8 ? nbits - shift : 8;
+        uint32_t dmask = (1u << bits) - 1u;
+        k_radix_hist<<<g, RS_BLOCK, 0, s>>>(K[cur], n_dev, cap, shift, dmask, w.hist);
+        ScanLen L{n_dev, 256, RS_TILE, 0, 0, cap};
+        scan_exclusive(w.hist, w.hist, L, w, nullptr, 0, s);
+        k_radix_scatter<<<g, RS_BLOCK, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1], n_dev, cap, shift, dmask, w.hist);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+}  // namespace gs

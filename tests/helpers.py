@@ -1,0 +1,74 @@
+"""Shared helpers of the GPU parity tests: inputs rounded to what the GPU sees,
+oracle runs on those inputs, and comparison rules for discrete decisions."""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+# A discrete decision (cull, rect edge, alpha threshold, square test, T stop)
+# whose FP64 margin is below this relative distance may legitimately go the
+# other way in FP32; such Gaussians / pixels are excluded and counted.
+TIE_TOL = 1e-5
+
+
+def cam_f32(cam):
+    """The camera with every field rounded to float32, as the GPU receives it."""
+    c = copy.copy(cam)
+    c.R = np.asarray(cam.R, np.float32).astype(np.float64)
+    c.t = np.asarray(cam.t, np.float32).astype(np.float64)
+    for k in ("fx", "fy", "cx", "cy", "near", "far"):
+        setattr(c, k, float(np.float32(getattr(cam, k))))
+    return c
+
+
+def hp32(orc, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15):
+    """Oracle Adam hyper-parameters rounded to float32, as the C ABI carries them."""
+    lr32 = np.asarray(np.broadcast_to(lr, (6,)), np.float32).astype(np.float64)
+    r = lambda x: float(np.float32(x))
+    return orc.AdamHyper(lr=lr32, beta1=r(beta1), beta2=r(beta2), eps=r(eps), max_defer=max_defer)
+
+
+def f32(params):
+    return np.asarray(params, np.float32).astype(np.float64)
+
+
+def rel_group_error(g_gpu, g_ref, rows):
+    """||gpu - ref|| / ||ref|| over a group of parameter rows."""
+    a = g_gpu[rows].ravel()
+    b = g_ref[rows].ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
+          "sh_dc": slice(11, 14), "sh_rest": slice(14, None)}
+
+
+def check_lists(gpu_tiles, gpu_gids, oracle_tiles, oracle_gids, depth_bits, exclude):
+    """GPU (tile, Gaussian id) sequence against the oracle's.  Keys of excluded
+    Gaussians are dropped from both; within a tile, neighbours may differ in
+    order only when their float32 depths are within 2 ulp."""
+    keep_g = ~np.isin(gpu_gids, exclude)
+    keep_o = ~np.isin(oracle_gids, exclude)
+    gt, gg = gpu_tiles[keep_g], gpu_gids[keep_g]
+    ot, og = oracle_tiles[keep_o], oracle_gids[keep_o]
+    assert gt.shape == ot.shape, (gt.shape, ot.shape)
+    np.testing.assert_array_equal(gt, ot)
+    if np.array_equal(gg, og):
+        return 0
+    bad = np.nonzero(gg != og)[0]
+    # allowed only as swaps of near-equal depths inside one tile
+    for p in bad:
+        t = gt[p]
+        lo = p
+        while lo > 0 and gt[lo - 1] == t:
+            lo -= 1
+        hi = p
+        while hi + 1 < len(gt) and gt[hi + 1] == t:
+            hi += 1
+        assert sorted(gg[lo:hi + 1]) == sorted(og[lo:hi + 1])
+        d = depth_bits[gg[p]].astype(np.int64)
+        e = depth_bits[og[p]].astype(np.int64)
+        assert abs(d - e) <= 2, (p, gg[p], og[p], d, e)
+    return len(bad)

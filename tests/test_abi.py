@@ -1,0 +1,99 @@
+"""The C-ABI library loads and exports every entry point the header declares;
+host-side argument checks work without a GPU (no compute calls here)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names += re.findall(r"GS_API\s+[\w\s\*]+?\b(gs_\w+)\s*\(", open(h).read())
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_15645_b300 import _lib
+    from paper_2509_15645_b300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2509_15645_b300 import _lib
+    assert set(names) == set(_lib.EXPORTS), set(names) ^ set(_lib.EXPORTS)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the ABI structs have the C compiler's sizes and offsets."""
+    import subprocess
+    from paper_2509_15645_b300 import _lib
+    structs = {"gs_camera": _lib.Camera, "gs_scene": _lib.Scene, "gs_adam_cfg": _lib.AdamCfg, "gs_config": _lib.Config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs_b300.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def _cfg(**kw):
+    from paper_2509_15645_b300 import _lib
+    c = _lib.Config()
+    d = dict(max_gaussians=10_000_000, max_visible=4_000_000, max_keys=40_000_000, max_width=1920,
+             max_height=1080, tile_w=16, tile_h=16, max_views=4, max_sh_degree=3)
+    d.update(kw)
+    for k, v in d.items():
+        setattr(c, k, v)
+    return c
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_2509_15645_b300 import _lib
+    nb = C.c_size_t(0)
+    assert lib.gs_workspace_size(C.byref(_cfg()), C.byref(nb)) == _lib.GS_OK
+    assert nb.value > 59 * 4_000_000 * 4          # at least the compact parameter planes
+    small = C.c_size_t(0)
+    lib.gs_workspace_size(C.byref(_cfg(max_gaussians=1000, max_visible=1000, max_keys=10000, max_views=1)),
+                          C.byref(small))
+    assert 0 < small.value < nb.value
+    for bad in (dict(tile_w=10), dict(max_views=0), dict(max_views=9), dict(max_sh_degree=4),
+                dict(max_gaussians=0), dict(max_width=0), dict(max_keys=0)):
+        assert lib.gs_workspace_size(C.byref(_cfg(**bad)), C.byref(nb)) == _lib.GS_ERR_INVALID_ARG, bad
+
+
+def test_null_context_is_rejected(lib):
+    from paper_2509_15645_b300 import _lib
+    sc, cam, ad = _lib.Scene(), _lib.Camera(), _lib.AdamCfg()
+    z = C.c_void_p(0)
+    assert lib.gs_cull(None, C.byref(sc), C.byref(cam), None, z, z, z) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_render_fwd(None, C.byref(sc), C.byref(cam), None, z, z, z, z) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_render_bwd(None, z, z, 1, z) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_adam_deferred(None, C.byref(sc), z, z, z, 1, C.byref(ad), z) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_step(None, C.byref(sc), C.byref(cam), None, 1, C.byref(ad), z, z) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_destroy(None) == _lib.GS_ERR_INVALID_ARG
+    assert lib.gs_last_error(None) == b"null context"
+    c = _cfg()
+    h = C.c_void_p()
+    c.tile_w = 7
+    assert lib.gs_create(C.byref(h), C.byref(c), 0, None, 0) == _lib.GS_ERR_INVALID_ARG

@@ -1,0 +1,418 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Discrete results (cull sets, key lists, counters) are
+bit-exact except decisions whose FP64 margin is a tie at FP32 resolution;
+images within 1e-5 absolute, gradients within 1e-4 relative (per parameter
+group), optimizer state within FP32 rounding of the FP64 values."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2509_15645_b300 as gs
+    return gs
+
+
+def make_ctx(gs, n, W, H, deg=3, tile=(16, 16), max_vis=None, max_keys=None, views=1):
+    return gs.Context(max_gaussians=n, max_visible=max_vis or n, max_keys=max_keys or (64 * n + 4096),
+                      max_width=W, max_height=H, tile=tile, max_views=views, max_sh_degree=deg)
+
+
+def _case(name):
+    """(params float32 [D][n], camera, sh degree, tile)."""
+    if name == "cube10k":
+        c = scenes.cfg_small_step()
+        return c["scene"], c["cams"][0], 0, (16, 16)
+    if name == "cube_offaxis_sh3":
+        P = scenes.uniform_cube_scene(6000, seed=3, sh_degree=3, log_scale_mean=-3.2)
+        P[14:] *= 10.0
+        cam = scenes.camera_lookat((0.9, -0.6, -2.4), (0.4, 0.3, 0.2), 96, 72, 70.0, up=(0, -1, 0))
+        return P, cam, 3, (16, 16)
+    if name == "ragged_tiles":
+        P = scenes.uniform_cube_scene(1037, seed=4, sh_degree=1, log_scale_mean=-2.5)
+        cam = scenes.camera_lookat((0.1, 0.2, -3.0), (0.0, 0.0, 0.0), 77, 45, 60.0, up=(0, -1, 0))
+        return P, cam, 1, (16, 16)
+    if name == "tile32x8":
+        P = scenes.uniform_cube_scene(3000, seed=5, sh_degree=2, log_scale_mean=-3.0)
+        cam = scenes.camera_lookat((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 80, 64, 60.0, up=(0, -1, 0))
+        return P, cam, 2, (32, 8)
+    if name == "degenerate":
+        c = scenes.cfg_diff_check(n=8000, width=96)
+        return c["scene"], c["cams"][0], 3, (16, 16)
+    raise KeyError(name)
+
+
+CASES = ["cube10k", "cube_offaxis_sh3", "ragged_tiles", "tile32x8", "degenerate"]
+
+
+def _run_fwd(gs, orc, name):
+    P, cam, deg, tile = _case(name)
+    camf = cam_f32(cam)
+    n = P.shape[1]
+    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=tile)
+    scene = gs.GaussianScene(P, deg)
+    ids, nv = ctx.cull(scene, camf)
+    img = ctx.render_fwd(scene, camf, ids, nv)
+    ctx.sync_status()
+    nvis = int(nv.item())
+    gids = ids[:nvis].cpu().numpy()
+    r = orc.render(f32(P), deg, camf, tile)
+    return dict(P=P, cam=camf, deg=deg, tile=tile, ctx=ctx, scene=scene, ids=ids, nv=nv, gids=gids,
+                img=img.cpu().numpy().astype(np.float64), r=r)
+
+
+def _pixel_exclusions(r, gpu_ids=None):
+    """Pixels whose value may legitimately differ between FP32 and FP64: a
+    near-tie among the decisions that can change the pixel (square test of a
+    contributing Gaussian, the 1/255 floor, the transmittance stop), or inside
+    the 3-sigma square of a Gaussian whose integer radius or keep decision is a
+    near-tie."""
+    ex = r["margin"] < TIE_TOL
+    sp = r["splats"]
+    H, W = ex.shape
+    flagged = (sp["radius_margin"] < TIE_TOL) & (sp["keep"] == 1)
+    if gpu_ids is not None:
+        diff = np.setxor1d(gpu_ids, np.nonzero(sp["keep"])[0])
+        flagged[diff] = True
+    for i in np.nonzero(flagged)[0]:
+        mx, my = sp["mean2d"][i]
+        rr = sp["radius"][i] + 1
+        if not (np.isfinite(mx) and np.isfinite(my) and rr > 1):
+            continue
+        x0, x1 = int(max(0, np.floor(mx - rr))), int(min(W, np.ceil(mx + rr)))
+        y0, y1 = int(max(0, np.floor(my - rr))), int(min(H, np.ceil(my + rr)))
+        ex[y0:y1, x0:x1] = True
+    return ex
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_cull_parity(gs, orc, name):
+    d = _run_fwd(gs, orc, name)
+    sp = d["r"]["splats"]
+    kept = np.nonzero(sp["keep"])[0]
+    tie = sp["margin"] < TIE_TOL
+    assert np.all(np.diff(d["gids"]) > 0), "ids must be ascending"
+    diff = np.setxor1d(d["gids"], kept)
+    assert np.all(tie[diff]), f"non-tie cull mismatches: {diff[~tie[diff]][:10]}"
+    assert tie.sum() <= max(3, 0.01 * sp.shape[0])
+    assert len(kept) > 0
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_key_lists_parity(gs, orc, name):
+    d = _run_fwd(gs, orc, name)
+    r = d["r"]
+    tx, ty = (d["cam"].width + d["tile"][0] - 1) // d["tile"][0], (d["cam"].height + d["tile"][1] - 1) // d["tile"][1]
+    keys, vals, ranges = d["ctx"].render_lists(tx * ty)
+    keys = keys.cpu().numpy().astype(np.int64)
+    vals = vals.cpu().numpy().astype(np.int64)
+    gpu_gid = d["gids"][vals]
+    sp = r["splats"]
+    exclude = np.nonzero(sp["margin"] < TIE_TOL)[0]
+    dbits = sp["depth"].astype(np.float32).view(np.uint32)
+    swaps = check_lists(keys, gpu_gid, r["key_tile"].astype(np.int64), r["key_gid"], dbits, exclude)
+    assert swaps <= 4
+    # ranges delimit each tile's run
+    rg = ranges.cpu().numpy().astype(np.int64)
+    for t in range(tx * ty):
+        b, e = rg[t]
+        assert np.all(keys[b:e] == t)
+        assert e - b == np.count_nonzero(keys == t)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_render_forward_parity(gs, orc, name):
+    d = _run_fwd(gs, orc, name)
+    ref = d["r"]["image"]
+    ex = _pixel_exclusions(d["r"], d["gids"])
+    err = np.abs(d["img"] - ref)
+    ok = ~ex[None, :, :].repeat(3, 0)
+    assert ex.mean() < 0.03, f"too many tie pixels: {ex.mean()}"
+    assert err[ok].max() <= 1e-5, (err[ok].max(), np.unravel_index(np.argmax(np.where(ok, err, 0)), err.shape))
+    assert ref.max() > 0.05
+
+
+def _target(orc, P_like, cam, deg, tile, seed):
+    T = scenes.uniform_cube_scene(P_like.shape[1], seed=seed, sh_degree=deg)
+    return orc.render(f32(T), deg, cam, tile)["image"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_render_backward_parity(gs, orc, name):
+    d = _run_fwd(gs, orc, name)
+    P, cam, deg, tile = d["P"], d["cam"], d["deg"], d["tile"]
+    target = _target(orc, P, cam, deg, tile, seed=11)
+    r = d["r"]
+    loss, dimg = orc.loss_l1(r["image"], target)
+    g_ref, _ = orc.backward(f32(P), deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], dimg)
+    D = P.shape[0]
+    dimg_t = torch.as_tensor(dimg, dtype=torch.float32, device="cuda")
+    gc = d["ctx"].render_bwd(dimg_t, D)
+    full = d["ctx"].grad_scatter(d["scene"], d["ids"], d["nv"], gc)
+    d["ctx"].sync_status()
+    g_gpu = full[:, :P.shape[1]].cpu().numpy().astype(np.float64)
+    errs = {k: rel_group_error(g_gpu, g_ref, s) for k, s in GROUPS.items() if g_ref[s].size}
+    assert max(errs.values()) <= 1e-4, errs
+
+
+def test_loss_l1_kernel(gs):
+    ctx = make_ctx(gs, 64, 40, 30)
+    rng = np.random.default_rng(0)
+    a = rng.random((3, 30, 40)).astype(np.float32)
+    b = rng.random((3, 30, 40)).astype(np.float32)
+    b[1, 2, 3] = a[1, 2, 3]
+    ta, tb = torch.as_tensor(a, device="cuda"), torch.as_tensor(b, device="cuda")
+    loss, dimg = ctx.loss_l1(ta, tb)
+    ctx.sync_status()
+    ref = np.mean(np.abs(a.astype(np.float64) - b))
+    assert abs(loss.item() - ref) <= 1e-6 * ref
+    np.testing.assert_array_equal(dimg.cpu().numpy(), (np.sign(a - b) / a.size).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------- Adam
+
+def _adam_state(rng, D, n, t):
+    w = rng.normal(size=(D, n)).astype(np.float32)
+    m = (rng.normal(size=(D, n)) * 1e-3).astype(np.float32)
+    v = rng.uniform(1e-8, 1e-6, size=(D, n)).astype(np.float32)
+    cnt = rng.integers(0, min(16, t), n).astype(np.uint8)
+    return w, m, v, cnt
+
+
+@pytest.mark.parametrize("mode", ["deferred", "eager"])
+@pytest.mark.parametrize("n,t", [(1000, 40), (4099, 3), (70001, 500)])
+def test_adam_step_parity(gs, orc, mode, n, t):
+    rng = np.random.default_rng(n + t)
+    deg, D = 3, 59
+    w, m, v, cnt = _adam_state(rng, D, n, t)
+    lr = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4]
+    ids = np.sort(rng.choice(n, n // 5, replace=False)).astype(np.int32)
+    gc = (rng.normal(size=(D, ids.size)) * 1e-3).astype(np.float32)
+    scene = gs.GaussianScene(w, deg)
+    scene.m[:, :n] = torch.as_tensor(m, device="cuda")
+    scene.v[:, :n] = torch.as_tensor(v, device="cuda")
+    scene.counter[:n] = torch.as_tensor(cnt, device="cuda")
+    scene.step = t - 1
+    ctx = make_ctx(gs, n, 64, 64)
+    adam = gs.adam_struct(lr=lr, eps=1e-15, mode=0 if mode == "deferred" else 2)
+    ids_t = torch.as_tensor(ids, device="cuda")
+    nv = torch.tensor([ids.size], dtype=torch.int32, device="cuda")
+    gct = torch.zeros(D, ctx.max_visible, dtype=torch.float32, device="cuda")
+    gct[:, :ids.size] = torch.as_tensor(gc, device="cuda")
+    ctx.adam_deferred(scene, ids_t, nv, gct, adam)
+    ctx.sync_status()
+    hp = hp32(orc, lr=lr, eps=1e-15)
+    W, M, V, Cn = f32(w), f32(m), f32(v), cnt.copy()
+    if mode == "deferred":
+        orc.adam_deferred(W, M, V, Cn, ids, f32(gc), t, hp, mode=0)
+    else:
+        g = np.zeros((D, n))
+        g[:, ids] = f32(gc)
+        orc.adam_eager(W, M, V, g, t, hp)
+    gw = scene.w[:, :n].cpu().numpy().astype(np.float64)
+    gm = scene.m[:, :n].cpu().numpy().astype(np.float64)
+    gv = scene.v[:, :n].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(scene.counter[:n].cpu().numpy(), Cn)
+    assert scene.step == t
+    # FP32 error bounds: every term of each update rounds with relative error u
+    u = 2.0 ** -24
+    g = np.zeros((D, n))
+    g[:, ids] = f32(gc)
+    upd = np.zeros(n, bool)
+    upd[ids] = True
+    if mode == "deferred":
+        upd |= cnt >= 15
+        dly = np.where(upd, cnt, 0).astype(int)
+    else:
+        upd[:] = True
+        dly = np.zeros(n, int)
+    m0, v0, w0 = f32(m), f32(v), f32(w)
+    b1p, b2p = hp.beta1 ** (dly + 1), hp.beta2 ** (dly + 1)
+    bm = 8 * u * (b1p * np.abs(m0) + (1 - hp.beta1) * np.abs(g)) + 1e-30
+    bv = 8 * u * (b2p * v0 + (1 - hp.beta2) * g * g) + 1e-38
+    restore = np.zeros((D, n))
+    for grp, rows in enumerate([slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, D)]):
+        pl, _, _ = orc.adam_lut(t, hp.lr[grp], hp)
+        pl = np.nan_to_num(pl)
+        restore[rows] = pl[dly] * np.abs(m0[rows]) / np.sqrt(v0[rows])
+    bw = 16 * u * (np.abs(w0) + restore + np.abs(W - w0)) + 1e-30
+    for name, a, b, bound in (("m", gm, M, bm), ("v", gv, V, bv), ("w", gw, W, bw)):
+        err = np.abs(a - b)
+        assert np.all(err[:, upd] <= bound[:, upd]), (name, np.max(err / bound))
+        np.testing.assert_array_equal(a[:, ~upd], b[:, ~upd])   # untouched
+
+
+def test_materialize_parity(gs, orc):
+    rng = np.random.default_rng(5)
+    n, D, t_done = 5000, 14, 30
+    w, m, v, cnt = _adam_state(rng, D, n, t_done + 1)
+    scene = gs.GaussianScene(w, 0)
+    scene.m[:, :n] = torch.as_tensor(m, device="cuda")
+    scene.v[:, :n] = torch.as_tensor(v, device="cuda")
+    scene.counter[:n] = torch.as_tensor(cnt, device="cuda")
+    scene.step = t_done
+    ctx = make_ctx(gs, n, 64, 64, deg=0)
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    wo, mo, vo = ctx.materialize(scene, adam)
+    ctx.sync_status()
+    hp = hp32(orc, lr=1e-3, eps=1e-15)
+    W, M, V = orc.adam_materialize(f32(w), f32(m), f32(v), cnt, t_done, hp, mode=0)
+    u = 2.0 ** -24
+    np.testing.assert_allclose(mo[:, :n].cpu().numpy(), M, rtol=8 * u, atol=0)
+    np.testing.assert_allclose(vo[:, :n].cpu().numpy(), V, rtol=8 * u, atol=0)
+    gw = wo[:, :n].cpu().numpy().astype(np.float64)
+    bound = 16 * u * (np.abs(f32(w)) + np.abs(W - f32(w)))
+    assert np.all(np.abs(gw - W) <= bound + 1e-30), np.max(np.abs(gw - W) / (bound + 1e-30))
+
+
+def test_deferred_trajectory_tracks_eager(gs, orc):
+    """Many GPU steps of deferred Adam, materialised, against the FP64 eager
+    trajectory on the same gradients (the paper's claim of identical training
+    up to the eps approximation, here at FP32)."""
+    rng = np.random.default_rng(9)
+    n, D, steps = 3000, 14, 60
+    w0 = rng.normal(size=(D, n)).astype(np.float32)
+    scene = gs.GaussianScene(w0, 0)
+    ctx = make_ctx(gs, n, 64, 64, deg=0)
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    hp = hp32(orc, lr=1e-3, eps=1e-15)
+    We, Me, Ve = f32(w0), np.zeros((D, n)), np.zeros((D, n))
+    for t in range(1, steps + 1):
+        c = rng.integers(0, n)
+        ids = np.arange(max(0, c - 300), min(n, c + 300), dtype=np.int32)
+        gc = (rng.normal(size=(D, ids.size)) * 1e-2).astype(np.float32)
+        gct = torch.zeros(D, ctx.max_visible, device="cuda")
+        gct[:, :ids.size] = torch.as_tensor(gc, device="cuda")
+        ctx.adam_deferred(scene, torch.as_tensor(ids, device="cuda"),
+                          torch.tensor([ids.size], dtype=torch.int32, device="cuda"), gct, adam)
+        g = np.zeros((D, n))
+        g[:, ids] = f32(gc)
+        orc.adam_eager(We, Me, Ve, g, t, hp)
+    ctx.sync_status()
+    wo, mo, vo = ctx.materialize(scene, adam)
+    np.testing.assert_allclose(wo[:, :n].cpu().numpy(), We, rtol=0, atol=2e-5)
+    np.testing.assert_allclose(mo[:, :n].cpu().numpy(), Me, rtol=1e-4, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------- whole step
+
+def test_step_parity(gs, orc):
+    """gs_step (CUDA graph: cull -> render -> L1 -> backward -> deferred Adam)
+    against the oracle pipeline from the same state, twice in a row."""
+    c = scenes.cfg_small_step()
+    P, cam, deg, tile = c["scene"], cam_f32(c["cams"][0]), 0, (16, 16)
+    n, D = P.shape[1], P.shape[0]
+    target = orc.render(f32(c["target_scene"]), 0, cam, tile)["image"]
+    scene = gs.GaussianScene(P, deg)
+    ctx = make_ctx(gs, n, cam.width, cam.height, deg=0)
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    hp = hp32(orc, lr=1e-3, eps=1e-15)
+    tgt = torch.as_tensor(target, dtype=torch.float32, device="cuda")
+    W, M, V, Cn = f32(P), np.zeros((D, n)), np.zeros((D, n)), np.zeros(n, np.uint8)
+    for t in (1, 2):
+        # oracle from the GPU's current state (one-step parity)
+        W = scene.w[:, :n].cpu().numpy().astype(np.float64)
+        M = scene.m[:, :n].cpu().numpy().astype(np.float64)
+        V = scene.v[:, :n].cpu().numpy().astype(np.float64)
+        Cn = scene.counter[:n].cpu().numpy().copy()
+        Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)   # current params for the render
+        rr = orc.render_loss_backward(Wcur, deg, cam, target, tile)
+        loss = ctx.step(scene, [cam], [tgt], adam)
+        ctx.sync_status()
+        assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7
+        kept = np.nonzero(rr["splats"]["keep"])[0].astype(np.int32)
+        orc.adam_deferred(W, M, V, Cn, kept, rr["grad"][:, kept], t, hp)
+        np.testing.assert_array_equal(scene.counter[:n].cpu().numpy(), Cn)
+        gw = scene.w[:, :n].cpu().numpy()
+        gm = scene.m[:, :n].cpu().numpy()
+        # moments carry the gradient: compare per group, relative to the group's scale
+        for k, s in GROUPS.items():
+            if M[s].size:
+                assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
+        assert np.max(np.abs(gw - W)) <= 2e-3 * 1e-3 + 1e-6
+
+
+# ---------------------------------------------------------------------------- autograd
+
+def test_autograd_function(gs, orc):
+    P, cam, deg, tile = _case("cube_offaxis_sh3")
+    camf = cam_f32(cam)
+    ctx = make_ctx(gs, P.shape[1], camf.width, camf.height, deg=3)
+    scene = gs.GaussianScene(P, deg, with_optimizer=False)
+    ids, nv = ctx.cull(scene, camf)
+    w = scene.w.detach().requires_grad_(True)
+    scene.w = w
+    img = gs.render(ctx, scene, camf, ids, nv)
+    rng = np.random.default_rng(1)
+    wimg = torch.as_tensor(rng.normal(size=img.shape), dtype=torch.float32, device="cuda")
+    (g,) = torch.autograd.grad((img * wimg).sum(), w)
+    r = orc.render(f32(P), deg, camf, tile)
+    g_ref, _ = orc.backward(f32(P), deg, r["cam"], r["splats"], r["key_gid"], r["ranges"],
+                            wimg.cpu().numpy().astype(np.float64))
+    g_gpu = g[:, :P.shape[1]].cpu().numpy().astype(np.float64)
+    errs = {k: rel_group_error(g_gpu, g_ref, s) for k, s in GROUPS.items()}
+    assert max(errs.values()) <= 1e-4, errs
+
+
+# ---------------------------------------------------------------------------- edge cases
+
+def test_empty_view(gs):
+    P = scenes.uniform_cube_scene(500, seed=0, sh_degree=0)
+    cam = scenes.camera_from_pose(np.eye(3), (0.0, 0.0, -5.0), 32, 32, 60.0)   # cube behind the camera
+    ctx = make_ctx(gs, 500, 32, 32, deg=0)
+    scene = gs.GaussianScene(P, 0)
+    ids, nv = ctx.cull(scene, cam)
+    img = ctx.render_fwd(scene, cam, ids, nv)
+    gc = ctx.render_bwd(torch.ones_like(img), 14)
+    ctx.adam_deferred(scene, ids, nv, gc, gs.adam_struct())
+    ctx.sync_status()
+    assert nv.item() == 0
+    assert img.abs().max().item() == 0.0
+    assert int(scene.counter[:500].max().item()) == 1
+
+
+def test_single_gaussian_and_ragged_n(gs, orc):
+    for n in (1, 31, 33, 2049):
+        P = scenes.uniform_cube_scene(n, seed=n, sh_degree=0, log_scale_mean=-2.0)
+        cam = scenes.camera_from_pose(np.eye(3), (0.0, 0.0, 3.0), 40, 24, 60.0)
+        camf = cam_f32(cam)
+        ctx = make_ctx(gs, n, 40, 24, deg=0)
+        scene = gs.GaussianScene(P, 0)
+        ids, nv = ctx.cull(scene, camf)
+        img = ctx.render_fwd(scene, camf, ids, nv)
+        ctx.sync_status()
+        r = orc.render(f32(P), 0, camf)
+        kept = np.nonzero(r["splats"]["keep"])[0]
+        np.testing.assert_array_equal(ids[:nv.item()].cpu().numpy(), kept)
+        ex = _pixel_exclusions(r, ids[:nv.item()].cpu().numpy())
+        err = np.abs(img.cpu().numpy() - r["image"])[:, ~ex]
+        assert err.max() <= 1e-5
+
+
+def test_capacity_overflow_is_reported(gs):
+    from paper_2509_15645_b300 import _lib
+    c = scenes.cfg_small_step()
+    P, cam = c["scene"], c["cams"][0]
+    ctx = make_ctx(gs, P.shape[1], 64, 64, deg=0, max_vis=100)
+    scene = gs.GaussianScene(P, 0)
+    ids, nv = ctx.cull(scene, cam)
+    with pytest.raises(_lib.GsError) as e:
+        ctx.sync_status()
+    assert e.value.status == _lib.GS_ERR_CAPACITY
+    assert nv.item() == 100
+    ctx2 = make_ctx(gs, P.shape[1], 64, 64, deg=0, max_keys=1000)
+    ids, nv = ctx2.cull(scene, cam)
+    ctx2.render_fwd(scene, cam, ids, nv)
+    with pytest.raises(_lib.GsError) as e:
+        ctx2.sync_status()
+    assert e.value.status == _lib.GS_ERR_CAPACITY
+    ctx2.sync_status()   # cleared
