@@ -160,11 +160,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for s in range(K):
         v = (Wm + s) % len(cams)
         ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist:
