@@ -222,6 +222,27 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
  * gs_step). */
 GS_API gs_status gs_step_kernel_count(const gs_ctx *ctx, int32_t *kernels);
 
+/* Largest scene gs_cull_noalloc accepts. */
+#define GS_CULL_NOALLOC_MAX_GAUSSIANS (1 << 24)
+
+/* gs_cull without a context and without any device allocation.  The paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc (and so
+ * cannot create a gs_ctx with its own workspace), e.g. code inside a framework
+ * whose memory pool owns all device memory, loops that forbid allocation after
+ * start-up, or callers that must keep a fixed device footprint.  Same
+ * arguments and results as gs_cull on a context with tile size tile_w x
+ * tile_h: ids_out (device, room for scene->n ids) receives the visible
+ * Gaussians in ascending order and *n_vis_out (device) their count.
+ * Its scratch is a fixed ~2.1 MB array of device memory inside the library,
+ * held on every GPU that loads the library until the process exits.
+ * Returns GS_ERR_CAPACITY, launching nothing, if scene->n exceeds
+ * GS_CULL_NOALLOC_MAX_GAUSSIANS.  The first call on each device looks up that
+ * array's address (with the device current) and should come before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race;
+ * serialise them (one stream, or events). */
+GS_API gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam, int32_t tile_w,
+                                 int32_t tile_h, int32_t *ids_out, int32_t *n_vis_out, void *stream);
+
 /* Inspection of the last gs_render_fwd (tests, debugging).  Device pointers,
  * owned by the context, valid until the next render: *tile_of_key[K] and
  * *splat_of_key[K] the (tile id, compact visible index) pairs in sorted order,

@@ -55,6 +55,8 @@ EXPORTS = {
     "gs_timing_enable": (c_i32, [c_vp, c_i32]),
     "gs_timing_read": (c_i32, [c_vp, C.POINTER(c_f32), c_i32, C.POINTER(c_i32)]),
     "gs_step_kernel_count": (c_i32, [c_vp, C.POINTER(c_i32)]),
+    "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
+                                c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),

@@ -1,0 +1,163 @@
+// gs_noalloc.cu -- gs_cull_noalloc: the frustum cull without any device
+// allocation, for callers that cannot call cudaMalloc (and so cannot create a
+// gs_ctx with its own workspace): code running inside a framework whose
+// memory pool owns every device byte, loops that forbid allocation after
+// start-up, or callers that must keep a fixed, known device footprint.
+//
+// Its scratch (argument block, visibility bitmask, per-chunk counts, scan
+// partials) is one file-scope __device__ array of fixed size, resident on
+// every GPU that loads the library until the process exits.  Host code never
+// names that array directly: on the first call on each device (with that
+// device current) its address is fetched once with cudaGetSymbolAddress and
+// cached.  Because of that set-up, the first call on a device should come
+// before any stream capture.  All calls share the one array and it keeps the
+// last call's contents, so calls that overlap on the GPU (other streams,
+// other threads) race; every byte a call reads is written or cleared by that
+// same call first.
+#include <cmath>
+#include <mutex>
+
+#include "gs_kernels.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int64_t NA_MAX = GS_CULL_NOALLOC_MAX_GAUSSIANS;
+constexpr int64_t NA_WORDS = NA_MAX / 32 + CHUNK_WORDS;
+constexpr int64_t NA_CHUNKS = NA_MAX / CHUNK + 1;
+
+// Byte layout of the scratch array (each part 256-byte aligned).
+constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t OFF_ARGS = 0;
+constexpr size_t OFF_STATUS = round256(OFF_ARGS + sizeof(DevArgs));           // int status, int count
+constexpr size_t OFF_PARTIALS = round256(OFF_STATUS + 2 * sizeof(int));
+constexpr size_t OFF_CHUNKS = round256(OFF_PARTIALS + 1024 * sizeof(uint32_t));
+constexpr size_t OFF_MASK = round256(OFF_CHUNKS + NA_CHUNKS * sizeof(uint32_t));
+constexpr size_t SCRATCH_BYTES = round256(OFF_MASK + NA_WORDS * sizeof(uint32_t));
+
+static __device__ __align__(256) unsigned char g_cull_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mutex;
+unsigned char *g_scratch[MAX_DEVICES] = {nullptr};
+int g_sms[MAX_DEVICES] = {0};
+
+__global__ void k_noalloc_args(DevArgs a, DevArgs *dst)
+{
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&a);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevArgs) / 4); k += blockDim.x) d[k] = src[k];
+}
+
+// Once per device, with that device current: the scratch array's device address.
+gs_status scratch_for_current_device(unsigned char **base, int *sms)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_cull_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GS_ERR_CUDA;
+        }
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return GS_ERR_CUDA;
+        g_scratch[dev] = static_cast<unsigned char *>(p);
+        g_sms[dev] = n;
+    }
+    *base = g_scratch[dev];
+    *sms = g_sms[dev];
+    return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                                     int32_t tile_w, int32_t tile_h, int32_t *ids_out, int32_t *n_vis_out,
+                                     void *stream)
+{
+    if (!scene || !cam || !ids_out || !n_vis_out || !scene->geo) return GS_ERR_INVALID_ARG;
+    if (scene->n <= 0 || scene->pitch < scene->n || (scene->pitch & 3)) return GS_ERR_INVALID_ARG;
+    if (scene->n > NA_MAX) return GS_ERR_CAPACITY;     // beyond the fixed scratch: refused, nothing launched
+    if (tile_w <= 0 || tile_h <= 0 || cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f) ||
+        !(cam->far_z > cam->near_z) || cam->width >= 65536 * tile_w || cam->height >= 65536 * tile_h)
+        return GS_ERR_INVALID_ARG;
+    if (scene->precision != GS_FP32) return GS_ERR_INVALID_ARG;
+    const bool restore = adam && adam->mode == GS_ADAM_DEFERRED && scene->m && scene->v && scene->counter;
+    if (adam && (adam->max_defer < 1 || adam->max_defer > LUT_N - 1)) return GS_ERR_INVALID_ARG;
+
+    unsigned char *base = nullptr;
+    int sms = 0;
+    gs_status st = scratch_for_current_device(&base, &sms);
+    if (st != GS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // argument block: the camera, and the restore tables of the coming step
+    DevArgs a{};
+    DevCam &c = a.cam[0];
+    for (int k = 0; k < 9; k++) c.R[k] = cam->R[k];
+    for (int k = 0; k < 3; k++) c.t[k] = cam->t[k];
+    c.fx = cam->fx; c.fy = cam->fy; c.cx = cam->cx; c.cy = cam->cy;
+    c.near_z = cam->near_z; c.far_z = cam->far_z;
+    c.limx = (float)(1.3 * (0.5 * cam->width / (double)cam->fx));
+    c.limy = (float)(1.3 * (0.5 * cam->height / (double)cam->fy));
+    for (int i = 0; i < 3; i++)
+        c.campos[i] = (float)(-((double)cam->R[0 * 3 + i] * cam->t[0] + (double)cam->R[1 * 3 + i] * cam->t[1] +
+                                (double)cam->R[2 * 3 + i] * cam->t[2]));
+    c.width = cam->width; c.height = cam->height;
+    c.tile_w = tile_w; c.tile_h = tile_h;
+    c.tiles_x = (cam->width + tile_w - 1) / tile_w;
+    c.tiles_y = (cam->height + tile_h - 1) / tile_h;
+    a.n_views = 1;
+    if (restore) {
+        const int t = scene->step + 1;
+        const double b1 = adam->beta1, b2 = adam->beta2, scale = b1 / std::sqrt(b2);
+        for (int g = 0; g < N_GROUPS; g++) {
+            double prev = 0.0;
+            for (int i = 1; i < LUT_N; i++) {
+                if (i <= adam->max_defer && i <= t - 1) {
+                    prev = scale * prev + (adam->lr[g] * b1) /
+                                              (std::sqrt(b2 / (1.0 - std::pow(b2, t - i))) * (1.0 - std::pow(b1, t - i)));
+                    a.lut.param[g][i] = (float)prev;
+                }
+            }
+        }
+        a.lut.eps = adam->eps;
+        a.lut.max_defer = adam->max_defer;
+        a.lut.step = t;
+        a.lut.restore = 1;
+    }
+
+    DevArgs *args = reinterpret_cast<DevArgs *>(base + OFF_ARGS);
+    int *status = reinterpret_cast<int *>(base + OFF_STATUS);
+    Work w{};
+    w.partials = reinterpret_cast<uint32_t *>(base + OFF_PARTIALS);
+    w.hist = nullptr;
+    w.status = status;
+    w.num_sms = sms;
+    w.scan_grid = sms * 2 > 1024 ? 1024 : sms * 2;
+    w.tev = nullptr;
+    uint32_t *chunks = reinterpret_cast<uint32_t *>(base + OFF_CHUNKS);
+    uint32_t *mask = reinterpret_cast<uint32_t *>(base + OFF_MASK);
+
+    SceneView sv{};
+    sv.geo = scene->geo;
+    sv.sh = (float *)scene->sh;
+    sv.m = (float *)scene->m;
+    sv.v = (float *)scene->v;
+    sv.counter = scene->counter;
+    sv.n = scene->n;
+    sv.pitch = scene->pitch;
+    sv.deg = scene->sh_degree;
+    sv.D = N_GEO + 3 * (scene->sh_degree + 1) * (scene->sh_degree + 1);
+
+    k_noalloc_args<<<1, 128, 0, s>>>(a, args);
+    cudaMemsetAsync(status, 0, 2 * sizeof(int), s);                 // status and count start at zero
+    launch_cull(sv, args, 0, mask, chunks, w, s);                    // writes every mask word and chunk count used
+    compact_mask(mask, sv.n, chunks, true, ids_out, nullptr, (int)sv.n, n_vis_out, w, s);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
