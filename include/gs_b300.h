@@ -91,6 +91,10 @@ typedef struct {
     void *sh;              /* [3 (L+1)^2][pitch] fp32 or bf16 */
     void *m;               /* [D][pitch] fp32 or bf16, NULL = no optimizer state (render only) */
     void *v;               /* [D][pitch] */
+    float *rdir;           /* [D][pitch] fp32 restore direction m / (sqrt(v) + eps) of each parameter, kept
+                              by the optimizer so a deferred restore is one multiply-add; must equal that
+                              expression (all zero when m = v = 0; see gs_refresh_rdir).  NULL: the
+                              kernels recompute it from m and v */
     uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
     int32_t step;          /* optimizer steps completed; the next step is step + 1 */
     int32_t reserved;
@@ -112,7 +116,7 @@ typedef struct {
     int64_t max_visible;     /* capacity of the compact visible set per view */
     int64_t max_keys;        /* capacity of (tile, Gaussian) keys per view */
     int32_t max_width, max_height;
-    int32_t tile_w, tile_h;  /* raster tile; tile_w * tile_h in {64, 128, 256} */
+    int32_t tile_w, tile_h;  /* raster tile: tile_w in {4, 8, 16, 32, 64}, tile_w * tile_h in {64, 128, 256} */
     int32_t max_views;       /* views per gs_step, 1..8 */
     int32_t max_sh_degree;   /* 0..3 */
 } gs_config;
@@ -186,6 +190,10 @@ GS_API gs_status gs_loss_l1(gs_ctx *ctx, const float *image, const float *target
 GS_API gs_status gs_adam_deferred(gs_ctx *ctx, gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
                            const float *grad_compact, int64_t cap, const gs_adam_cfg *adam, void *stream);
 
+/* Recompute scene->rdir = m / (sqrt(v) + eps) for every parameter (after m or
+ * v were set by other means, or eps changed). */
+GS_API gs_status gs_refresh_rdir(gs_ctx *ctx, const gs_scene *scene, const gs_adam_cfg *adam, void *stream);
+
 /* The current (eager-equivalent) parameters and moments without modifying the
  * scene: catch-up of each Gaussian's deferred steps (tests, checkpoints).
  * Outputs (device fp32 [D][pitch], may be NULL). */
@@ -217,6 +225,26 @@ enum { GS_SPAN_STEP = 0, GS_SPAN_CULL = 1, GS_SPAN_FWD = 2, GS_SPAN_BWD = 3, GS_
        GS_SPAN_ADAM_APPLY = 5, GS_TIMING_SPANS = 6 };
 GS_API gs_status gs_timing_enable(gs_ctx *ctx, int32_t max_steps);
 GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, int32_t *steps_out);
+
+/* Rasterizer variants: pixels per thread 1 << (v >> 1) and a shared-memory
+ * splat batch of (v & 1 ? 256 : 128) records.  Every variant computes the same
+ * image bit for bit; they differ only in speed.  A tile shape allows a variant
+ * when tile_h is a multiple of its pixels per thread and the block has 32 to
+ * 256 threads. */
+#define GS_RASTER_VARIANTS 6
+
+/* Autotuner: time every variant the context's tile shape allows on this scene
+ * and view (cull, render forward, backward; CUDA events, best of three) and
+ * keep the fastest for this context.  Synchronises the stream; call it outside
+ * stream capture.  *chosen_out (host, may be NULL) receives the variant,
+ * ms_out (host, GS_RASTER_VARIANTS floats, may be NULL) the forward+backward
+ * milliseconds of each (-1 where not allowed). */
+GS_API gs_status gs_autotune(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, int32_t *chosen_out,
+                             float *ms_out, void *stream);
+
+/* Select a rasterizer variant explicitly (tests); GS_ERR_INVALID_ARG if the
+ * tile shape does not allow it. */
+GS_API gs_status gs_set_raster_variant(gs_ctx *ctx, int32_t variant);
 
 /* Number of kernel launches in the captured gs_step graph (0 before the first
  * gs_step). */

@@ -13,6 +13,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_BUDGET, GS_ERR_CAPACI
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR_CUDA", 4: "GS_ERR_BUDGET",
                 5: "GS_ERR_CAPACITY", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_NUMERIC"}
 GS_FP32, GS_BF16_SH_MOM = 0, 1
+RASTER_VARIANTS = 6
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
 
@@ -24,7 +25,8 @@ class Camera(C.Structure):
 
 class Scene(C.Structure):
     _fields_ = [("n", c_i64), ("pitch", c_i64), ("sh_degree", c_i32), ("precision", c_i32), ("geo", c_vp),
-                ("sh", c_vp), ("m", c_vp), ("v", c_vp), ("counter", c_vp), ("step", c_i32), ("reserved", c_i32)]
+                ("sh", c_vp), ("m", c_vp), ("v", c_vp), ("rdir", c_vp), ("counter", c_vp), ("step", c_i32),
+                ("reserved", c_i32)]
 
 
 class AdamCfg(C.Structure):
@@ -50,11 +52,14 @@ EXPORTS = {
     "gs_render_bwd": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp]),
     "gs_loss_l1": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "gs_adam_deferred": (c_i32, [c_vp, C.POINTER(Scene), c_vp, c_vp, c_vp, c_i64, C.POINTER(AdamCfg), c_vp]),
+    "gs_refresh_rdir": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(AdamCfg), c_vp]),
     "gs_adam_materialize": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(AdamCfg), c_vp, c_vp, c_vp, c_vp]),
     "gs_grad_scatter": (c_i32, [c_vp, C.POINTER(Scene), c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "gs_timing_enable": (c_i32, [c_vp, c_i32]),
     "gs_timing_read": (c_i32, [c_vp, C.POINTER(c_f32), c_i32, C.POINTER(c_i32)]),
     "gs_step_kernel_count": (c_i32, [c_vp, C.POINTER(c_i32)]),
+    "gs_autotune": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_i32), C.POINTER(c_f32), c_vp]),
+    "gs_set_raster_variant": (c_i32, [c_vp, c_i32]),
     "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
                                 c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),

@@ -64,7 +64,7 @@ class GaussianScene:
     ``w`` is one [D][pitch] float32 tensor (geometry planes then SH planes),
     ``m``/``v`` the Adam moments, ``counter`` the defer counters."""
 
-    def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True):
+    def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True):
         D, n = params.shape
         assert D == n_params(sh_degree)
         self.n, self.sh_degree, self.D = n, sh_degree, D
@@ -75,8 +75,10 @@ class GaussianScene:
             self.m = torch.zeros_like(self.w)
             self.v = torch.zeros_like(self.w)
             self.counter = torch.zeros(self.pitch, dtype=torch.uint8, device=device)
+            # restore directions m / (sqrt(v) + eps): zero while m = v = 0
+            self.rdir = torch.zeros_like(self.w) if with_rdir else None
         else:
-            self.m = self.v = self.counter = None
+            self.m = self.v = self.counter = self.rdir = None
         self.step = 0
 
     def struct(self) -> L.Scene:
@@ -86,6 +88,7 @@ class GaussianScene:
         s.sh = self.w.data_ptr() + 11 * self.pitch * 4
         s.m = self.m.data_ptr() if self.m is not None else None
         s.v = self.v.data_ptr() if self.v is not None else None
+        s.rdir = self.rdir.data_ptr() if getattr(self, "rdir", None) is not None else None
         s.counter = self.counter.data_ptr() if self.counter is not None else None
         s.step = self.step
         return s
@@ -195,6 +198,11 @@ class Context:
         self._check(st, "gs_adam_deferred")
         scene.step = sc.step
 
+    def refresh_rdir(self, scene: GaussianScene, adam, stream=None):
+        """Recompute the restore directions after m or v were set directly."""
+        sc = scene.struct()
+        self._check(self.lib.gs_refresh_rdir(self.h, C.byref(sc), C.byref(adam), _stream(stream)), "gs_refresh_rdir")
+
     def materialize(self, scene: GaussianScene, adam, stream=None):
         w = torch.empty_like(scene.w)
         m = torch.empty_like(scene.w)
@@ -212,6 +220,20 @@ class Context:
                                       grad_compact.shape[1], _ptr(full), _stream(stream))
         self._check(st, "gs_grad_scatter")
         return full
+
+    def autotune(self, scene: GaussianScene, cam, stream=None):
+        """Time the rasterizer variants on this scene and view; keep the fastest.
+        Returns (chosen variant, per-variant ms or None where not allowed)."""
+        chosen = C.c_int32(-1)
+        ms = (C.c_float * L.RASTER_VARIANTS)()
+        sc = scene.struct()
+        cs = camera_struct(cam)
+        self._check(self.lib.gs_autotune(self.h, C.byref(sc), C.byref(cs), C.byref(chosen), ms, _stream(stream)),
+                    "gs_autotune")
+        return chosen.value, [None if t < 0 else t for t in ms]
+
+    def set_raster_variant(self, v):
+        self._check(self.lib.gs_set_raster_variant(self.h, int(v)), "gs_set_raster_variant")
 
     def timing_enable(self, max_steps):
         self._check(self.lib.gs_timing_enable(self.h, int(max_steps)), "gs_timing_enable")

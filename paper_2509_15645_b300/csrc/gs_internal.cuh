@@ -67,9 +67,20 @@ __host__ __device__ __forceinline__ int lr_group(int row)
 // ---------------------------------------------------------------------------
 // Deferred restore (Eq. 3 with eps factored out): the current value of a
 // parameter whose last d updates were deferred.  d = 0 leaves it untouched.
+// The restore direction m / (sqrt(v) + eps) is kept per parameter by the
+// optimizer (the scene's rdir planes) so that the restore is one FMA; the two
+// helpers below are the only places either quantity is formed, so a stored
+// direction and a recomputed one give the same restored value bit for bit.
+__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return m / (sqrtf(v) + eps); }
+
+__device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, int d)
+{
+    return d ? __fmaf_rn(-plut, dir, w) : w;
+}
+
 __device__ __forceinline__ float restore_param(float w, float m, float v, float plut, int d, float eps)
 {
-    return d ? w - plut * m / (sqrtf(v) + eps) : w;
+    return d ? restore_with_dir(w, restore_dir(m, v, eps), plut, d) : w;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +266,23 @@ __device__ __forceinline__ float splat_alpha(float4 r0, float4 r1, float px, flo
     clamped = raw > ALPHA_MAX;
     float alpha = fminf(ALPHA_MAX, raw);
     return alpha < ALPHA_MIN ? 0.f : alpha;
+}
+
+// The same test and alpha without branches: identical operations, so identical
+// results and decisions; the caller masks with the returned value (0 = no
+// contribution).  Used where several pixels per thread are evaluated together.
+__device__ __forceinline__ float splat_alpha_nb(float4 r0, float4 r1, float dx, float py, float &dy, float &G,
+                                               bool &clamped)
+{
+    dy = __fsub_rn(r0.y, py);
+    float sig = __fmaf_rn(r1.y, __fmul_rn(dx, dy),
+                          __fmul_rn(0.5f, __fmaf_rn(r1.x, __fmul_rn(dx, dx), __fmul_rn(r1.z, __fmul_rn(dy, dy)))));
+    G = __expf(-sig);
+    float raw = __fmul_rn(r0.w, G);
+    clamped = raw > ALPHA_MAX;
+    float alpha = fminf(ALPHA_MAX, raw);
+    bool ok = (fabsf(dx) <= r0.z) && (fabsf(dy) <= r0.z) && (sig >= 0.f) && (alpha >= ALPHA_MIN);
+    return ok ? alpha : 0.f;
 }
 
 // ---------------------------------------------------------------------------

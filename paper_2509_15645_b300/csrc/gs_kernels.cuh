@@ -47,6 +47,7 @@ struct SceneView {
     float *sh;
     float *m;
     float *v;
+    float *rdir;          // restore directions, or nullptr
     uint8_t *counter;
     int64_t n, pitch;
     int deg, D;
@@ -69,6 +70,7 @@ void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32
                           int *n_upd, Work &w, cudaStream_t s);
 void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s);
+void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s);
 void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
                         Work &w, cudaStream_t s);
 void launch_grad_scatter(const int32_t *ids, const int *n_dev, int cap, const float *gc, int64_t gcap, int D,
@@ -88,11 +90,15 @@ struct RenderBufs {
     uint2 *ranges;           // [tiles]
     float *g9;               // [9][cap] screen-space gradient sums
     int *n_keys;             // device
+    int variant;             // rasterizer variant (pixels per thread, batch), see raster_variant_ok
     // filled by render_fwd
     const uint32_t *sorted_keys;
     const uint32_t *sorted_vals;
     int tiles;
 };
+
+constexpr int N_RASTER_VARIANTS = 6;
+bool raster_variant_ok(int v, int tile_w, int tile_h);
 
 void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
                     RenderBufs &rb, const DevCam &cam_host, float *image, bool use_target, float *dimage,

@@ -149,6 +149,7 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     sv.sh = (float *)scene->sh;
     sv.m = (float *)scene->m;
     sv.v = (float *)scene->v;
+    sv.rdir = (scene->m && scene->v) ? scene->rdir : nullptr;
     sv.counter = scene->counter;
     sv.n = scene->n;
     sv.pitch = scene->pitch;

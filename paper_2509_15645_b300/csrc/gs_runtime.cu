@@ -24,12 +24,14 @@ struct GraphCache {
     // what the captured graph baked in
     float *geo = nullptr;
     void *sh = nullptr, *m = nullptr, *v = nullptr;
+    float *rdir = nullptr;
     uint8_t *counter = nullptr;
     int64_t n = 0, pitch = 0;
     int deg = -1, n_views = 0, mode = -1;
     int W[MAX_VIEWS] = {0}, H[MAX_VIEWS] = {0};
     float *loss = nullptr;
     bool timed = false;
+    int variant = -1;
     cudaGraphNode_t ev_node[TP_COUNT] = {nullptr};
     int kernels = 0;
 };
@@ -123,7 +125,7 @@ static bool valid_cfg(const gs_config *c)
     int tp = c->tile_w * c->tile_h;
     return c->max_gaussians > 0 && c->max_gaussians < (1ll << 31) - CHUNK && c->max_visible > 0 &&
            c->max_visible < (1ll << 31) && c->max_keys > 0 && c->max_keys < (1ll << 32) - 1 && c->max_width > 0 &&
-           c->max_height > 0 && c->tile_w > 0 && c->tile_h > 0 && (tp == 64 || tp == 128 || tp == 256) &&
+           c->max_height > 0 && c->tile_w >= 4 && c->tile_h > 0 && 64 % c->tile_w == 0 && (tp == 64 || tp == 128 || tp == 256) &&
            c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h;
 }
@@ -285,6 +287,7 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     sv.sh = (float *)s->sh;
     sv.m = (float *)s->m;
     sv.v = (float *)s->v;
+    sv.rdir = (s->m && s->v) ? s->rdir : nullptr;
     sv.counter = s->counter;
     sv.n = s->n;
     sv.pitch = s->pitch;
@@ -345,6 +348,8 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
     carve(c, (char *)c->ws);
     c->w.status = &c->cnt->status;
     c->w.num_sms = c->num_sms;
+    c->rb.variant = 1;
+    if (!raster_variant_ok(c->rb.variant, cfg->tile_w, cfg->tile_h)) c->rb.variant = 0;
     c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
     if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         gs_destroy(c);
@@ -494,6 +499,22 @@ gs_status gs_adam_materialize(gs_ctx *c, const gs_scene *scene, const gs_adam_cf
     return cuda_check(c, "gs_adam_materialize");
 }
 
+gs_status gs_refresh_rdir(gs_ctx *c, const gs_scene *scene, const gs_adam_cfg *adam, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, true, sv);
+    if (st) return st;
+    if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (!sv.rdir) return fail(c, GS_ERR_INVALID_ARG, "scene has no rdir planes");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.lut = make_lut(adam, scene->step + 1, true);
+    set_args(c, SLOT_ADAM, a, s);
+    launch_refresh_rdir(sv, c->args + SLOT_ADAM, c->w, s);
+    return cuda_check(c, "gs_refresh_rdir");
+}
+
 gs_status gs_grad_scatter(gs_ctx *c, const gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
                           const float *grad_compact, int64_t cap, float *grad_full, void *stream)
 {
@@ -545,6 +566,72 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
     *steps_out = n;
     c->t_used = 0;
     return GS_OK;
+}
+
+gs_status gs_set_raster_variant(gs_ctx *c, int32_t variant)
+{
+    if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h)) return GS_ERR_INVALID_ARG;
+    c->rb.variant = variant;
+    return GS_OK;
+}
+
+gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, int32_t *chosen_out, float *ms_out,
+                      void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv);
+    if (st) return st;
+    if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.cam[0] = make_cam(*cam, c->cfg);
+    a.n_views = 1;
+    set_args(c, SLOT_RENDER, a, s);
+    int32_t *ids = c->vids[0];
+    launch_cull(sv, c->args + SLOT_RENDER, 0, c->mask, c->chunk, c->w, s);
+    compact_mask(c->mask, sv.n, c->chunk, true, ids, c->wprefix, (int)c->cfg.max_visible, c->n_render, c->w, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int keep = c->rb.variant;
+    float best = 1e30f;
+    int best_v = keep;
+    for (int v = 0; v < N_RASTER_VARIANTS; v++) {
+        if (ms_out) ms_out[v] = -1.f;
+        if (!raster_variant_ok(v, c->cfg.tile_w, c->cfg.tile_h)) continue;
+        c->rb.variant = v;
+        float vbest = 1e30f;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaEventRecord(e0, s);
+            render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], c->img, false, nullptr,
+                           nullptr, c->w, s);
+            // the rendered image itself serves as a dense dL/dimage
+            render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rb, a.cam[0], c->img, c->grad_u,
+                            c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                c->rb.variant = keep;
+                return cuda_check(c, "gs_autotune");
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < vbest) vbest = ms;      // the first run warms caches and clocks
+        }
+        if (ms_out) ms_out[v] = vbest;
+        if (vbest < best) {
+            best = vbest;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->rb.variant = best_v;
+    c->have_fwd = false;
+    if (chosen_out) *chosen_out = best_v;
+    return cuda_check(c, "gs_autotune");
 }
 
 gs_status gs_step_kernel_count(const gs_ctx *c, int32_t *kernels)
@@ -615,11 +702,11 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
 }
 
 static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
-                          float *loss, bool timed)
+                          float *loss, bool timed, int variant)
 {
     if (!g.exec || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
-        g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree || g.n_views != n_views || g.mode != mode ||
-        g.loss != loss || g.timed != timed)
+        g.rdir != sc->rdir || g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree || g.n_views != n_views || g.mode != mode ||
+        g.loss != loss || g.timed != timed || g.variant != variant)
         return false;
     for (int v = 0; v < n_views; v++)
         if (g.W[v] != views[v].width || g.H[v] != views[v].height) return false;
@@ -648,7 +735,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
     GraphCache &g = c->graph;
     const bool timed = c->t_events != nullptr;
     if (timed && c->t_used >= c->t_max) return fail(c, GS_ERR_CAPACITY, "timing buffer full: call gs_timing_read");
-    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed)) {
+    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rb.variant)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -713,9 +800,11 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
             return fail(c, GS_ERR_CUDA, "gs_step: argument node not found");
         }
         g.geo = scene->geo; g.sh = scene->sh; g.m = scene->m; g.v = scene->v; g.counter = scene->counter;
+        g.rdir = scene->rdir;
         g.n = scene->n; g.pitch = scene->pitch; g.deg = scene->sh_degree; g.n_views = n_views; g.mode = adam->mode;
         g.loss = loss_out;
         g.timed = timed;
+        g.variant = c->rb.variant;
         for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
     }
     if (timed) {

@@ -100,8 +100,9 @@ __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask,
 
 template <int UNROLL>
 __device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__restrict__ sh, float *__restrict__ m,
-                                          float *__restrict__ v, int64_t pitch, int D, int64_t i, int k,
-                                          const float *__restrict__ grad, int64_t gcap, int d, const SLut &L)
+                                          float *__restrict__ v, float *__restrict__ rdir, int64_t pitch, int D,
+                                          int64_t i, int k, const float *__restrict__ grad, int64_t gcap, int d,
+                                          const SLut &L)
 {
     for (int r0 = 0; r0 < D; r0 += UNROLL) {
         float w_[UNROLL], m_[UNROLL], v_[UNROLL], g_[UNROLL];
@@ -125,6 +126,7 @@ __device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__rest
                 *wp = w_[u];
                 m[r * pitch + i] = m_[u];
                 v[r * pitch + i] = v_[u];
+                if (rdir) rdir[r * pitch + i] = restore_dir(m_[u], v_[u], L.eps);
             }
         }
     }
@@ -132,6 +134,7 @@ __device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__rest
 
 __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ geo, float *__restrict__ sh,
                                                            float *__restrict__ m, float *__restrict__ v,
+                                                           float *__restrict__ rdir,
                                                            uint8_t *__restrict__ counter, int64_t pitch, int D,
                                                            const int32_t *__restrict__ uids, const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ g
         int d = counter[i];
         int k = compact_index(vmask, vprefix, i);
         if (k >= gcap) k = -1;     // outside the caller's gradient buffer: treated as zero gradient
-        adam_rows<4>(geo, sh, m, v, pitch, D, i, k, grad, gcap, d, L);
+        adam_rows<4>(geo, sh, m, v, rdir, pitch, D, i, k, grad, gcap, d, L);
         counter[i] = 0;
     }
 }
@@ -161,15 +164,17 @@ void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32
                                                                                 uchunk);
     compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s);
     w.mark(TP_APPLY0, s);
-    k_adam_apply<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.counter, sc.pitch, sc.D,
-                                                               uids, n_upd, vmask, vprefix, grad, gcap, args);
+    k_adam_apply<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.counter,
+                                                               sc.pitch, sc.D, uids, n_upd, vmask, vprefix, grad,
+                                                               gcap, args);
     w.mark(TP_APPLY1, s);
 }
 
 // Eager Adam (Eq. 1 for every Gaussian, every step): the baseline the
 // deferred update removes; counters are left alone.
 __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(float *__restrict__ geo, float *__restrict__ sh,
-                                                           float *__restrict__ m, float *__restrict__ v, int64_t pitch,
+                                                           float *__restrict__ m, float *__restrict__ v,
+                                                           float *__restrict__ rdir, int64_t pitch,
                                                            int64_t n, int D, const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
                                                            const float *__restrict__ grad, int64_t gcap,
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(float *__restrict__ g
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int k = compact_index(vmask, vprefix, i);
         if (k >= gcap) k = -1;
-        adam_rows<4>(geo, sh, m, v, pitch, D, i, k, grad, gcap, 0, L);
+        adam_rows<4>(geo, sh, m, v, rdir, pitch, D, i, k, grad, gcap, 0, L);
     }
 }
 
@@ -188,9 +193,26 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s)
 {
     w.mark(TP_APPLY0, s);
-    k_adam_eager<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.pitch, sc.n, sc.D, vmask,
-                                                               vprefix, grad, gcap, args);
+    k_adam_eager<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.pitch, sc.n,
+                                                               sc.D, vmask, vprefix, grad, gcap, args);
     w.mark(TP_APPLY1, s);
+}
+
+// rdir = m / (sqrt(v) + eps) for every parameter.
+__global__ void k_refresh_rdir(const float *__restrict__ m, const float *__restrict__ v, float *__restrict__ rdir,
+                               int64_t pitch, int64_t n, int D, const DevArgs *__restrict__ args)
+{
+    const float eps = args->lut.eps;
+    const int64_t total = (int64_t)D * pitch;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        if (e % pitch < n) rdir[e] = restore_dir(m[e], v[e], eps);
+}
+
+void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s)
+{
+    if (!sc.rdir) return;
+    k_refresh_rdir<<<w.grid((int64_t)sc.D * sc.pitch, 256, 4), 256, 0, s>>>(sc.m, sc.v, sc.rdir, sc.pitch, sc.n, sc.D,
+                                                                          args);
 }
 
 // Catch-up without a step: m b1^c, v b2^c, w - param_lut[c] m / (sqrt(v) + eps).

@@ -13,7 +13,8 @@ namespace gs {
 constexpr int CULL_BLOCK = 256;
 
 __global__ void __launch_bounds__(CULL_BLOCK) k_cull(const float *__restrict__ geo, const float *__restrict__ m,
-                                                     const float *__restrict__ v, const uint8_t *__restrict__ counter,
+                                                     const float *__restrict__ v, const float *__restrict__ rdir,
+                                                     const uint8_t *__restrict__ counter,
                                                      int64_t pitch, int64_t n, const DevArgs *__restrict__ args,
                                                      int view, uint32_t *__restrict__ mask,
                                                      uint32_t *__restrict__ chunk_cnt)
@@ -44,12 +45,25 @@ __global__ void __launch_bounds__(CULL_BLOCK) k_cull(const float *__restrict__ g
                 float g[10];
 #pragma unroll
                 for (int r = 0; r < 10; r++) g[r] = __ldg(geo + r * pitch + i);
-                int d = s_restore ? counter[i] : 0;
-                if (d) {
+                if (s_restore && rdir) {
+                    // restore through the stored directions: w and dir loads issued together
+                    float dd[10];
 #pragma unroll
-                    for (int r = 0; r < 10; r++)
-                        g[r] = restore_param(g[r], __ldg(m + r * pitch + i), __ldg(v + r * pitch + i),
-                                             s_plut[lr_group(r)][d], d, s_eps);
+                    for (int r = 0; r < 10; r++) dd[r] = __ldg(rdir + r * pitch + i);
+                    const int d = counter[i];
+#pragma unroll
+                    for (int r = 0; r < 10; r++) g[r] = restore_with_dir(g[r], dd[r], s_plut[lr_group(r)][d], d);
+                } else if (s_restore) {
+                    // m, v loads are issued together with w, not after the counter arrives
+                    float mm[10], vv[10];
+#pragma unroll
+                    for (int r = 0; r < 10; r++) {
+                        mm[r] = __ldg(m + r * pitch + i);
+                        vv[r] = __ldg(v + r * pitch + i);
+                    }
+                    const int d = counter[i];
+#pragma unroll
+                    for (int r = 0; r < 10; r++) g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], d, s_eps);
                 }
                 Proj P;
                 project_gaussian(g, s_cam, P);
@@ -77,8 +91,8 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (view == 0) w.mark(TP_CULL0, s);
-    k_cull<<<w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8), CULL_BLOCK, 0, s>>>(sc.geo, sc.m, sc.v, sc.counter, sc.pitch,
-                                                                           sc.n, args, view, mask, chunk_cnt);
+    k_cull<<<w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8), CULL_BLOCK, 0, s>>>(sc.geo, sc.m, sc.v, sc.rdir, sc.counter,
+                                                                           sc.pitch, sc.n, args, view, mask, chunk_cnt);
     if (view == 0) w.mark(TP_CULL1, s);
 }
 

@@ -30,6 +30,7 @@ struct SLutR {
     int restore;
 };
 
+template <int DEG>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
                                                                const int *n_vis_p, int cap,
                                                                const DevArgs *__restrict__ args, int view,
@@ -38,6 +39,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                                                                uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                                uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect)
 {
+    constexpr int NK = (DEG + 1) * (DEG + 1);
+    constexpr int D = N_GEO + 3 * NK;
     __shared__ DevCam s_cam;
     __shared__ SLutR L;
     if (threadIdx.x < sizeof(DevCam) / 4)
@@ -49,7 +52,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
     }
     __syncthreads();
     const int n_vis = min(*n_vis_p, cap);
-    const int nk = (sc.deg + 1) * (sc.deg + 1);
     const int64_t pitch = sc.pitch;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_vis; k += gridDim.x * blockDim.x) {
         const int64_t i = ids[k];
@@ -61,39 +63,42 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
             dval[k] = (uint32_t)k;
             tcnt[k] = 0u;
             rect[k] = make_uint2(0u, 0u);
-            for (int r = 0; r < sc.D; r++) compact[r * (int64_t)cap + k] = 0.f;
+            for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = 0.f;
             continue;
         }
-        const int d = L.restore ? sc.counter[i] : 0;
-        float g[N_GEO];
+        // gather all D planes (with m, v when restoring) before any arithmetic
+        float w[D];
 #pragma unroll
-        for (int r = 0; r < N_GEO; r++) {
-            float w = __ldg(sc.geo + r * pitch + i);
-            if (d) w = restore_param(w, __ldg(sc.m + r * pitch + i), __ldg(sc.v + r * pitch + i), L.param[lr_group(r)][d], d, L.eps);
-            g[r] = w;
-            compact[r * (int64_t)cap + k] = w;
-        }
-        Proj P;
-        project_gaussian(g, s_cam, P);
-        float vx = g[0] - s_cam.campos[0], vy = g[1] - s_cam.campos[1], vz = g[2] - s_cam.campos[2];
-        float ivn = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
-        float Y[16];
-        sh_basis(sc.deg, vx * ivn, vy * ivn, vz * ivn, Y);
-        float rgb[3] = {0.f, 0.f, 0.f};
-        for (int kk = 0; kk < nk; kk++) {
+        for (int r = 0; r < D; r++) w[r] = __ldg((r < N_GEO ? sc.geo + r * pitch : sc.sh + (r - N_GEO) * pitch) + i);
+        if (L.restore) {
+            const int d = sc.counter[i];
+            if (d && sc.rdir) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int r = 3 * kk + c;
-                float w = __ldg(sc.sh + r * pitch + i);
-                if (d) w = restore_param(w, __ldg(sc.m + (N_GEO + r) * pitch + i), __ldg(sc.v + (N_GEO + r) * pitch + i),
-                                         L.param[kk == 0 ? 4 : 5][d], d, L.eps);
-                compact[(N_GEO + r) * (int64_t)cap + k] = w;
-                rgb[c] += Y[kk] * w;
+                for (int r = 0; r < D; r++)
+                    w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d], d);
+            } else if (d) {
+#pragma unroll
+                for (int r = 0; r < D; r++)
+                    w[r] = restore_param(w[r], __ldg(sc.m + r * pitch + i), __ldg(sc.v + r * pitch + i),
+                                         L.param[lr_group(r)][d], d, L.eps);
             }
         }
 #pragma unroll
+        for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = w[r];
+        Proj P;
+        project_gaussian(w, s_cam, P);
+        float vx = w[0] - s_cam.campos[0], vy = w[1] - s_cam.campos[1], vz = w[2] - s_cam.campos[2];
+        float ivn = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
+        float Y[16];
+        sh_basis(DEG, vx * ivn, vy * ivn, vz * ivn, Y);
+        float rgb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < NK; kk++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) rgb[c] += Y[kk] * w[N_GEO + 3 * kk + c];
+#pragma unroll
         for (int c = 0; c < 3; c++) rgb[c] = fmaxf(rgb[c] + 0.5f, 0.f);
-        float o = 1.f / (1.f + expf(-g[ROW_OPAC]));
+        float o = 1.f / (1.f + expf(-w[ROW_OPAC]));
         rec0[k] = make_float4(P.mx, P.my, P.radius, o);
         rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
         rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
@@ -146,8 +151,12 @@ __global__ void k_tile_ranges(const uint32_t *__restrict__ tkey, const int *n_ke
 }
 
 // ---------------------------------------------------------------------------
-constexpr int RB = 256;   // max threads per raster block (tile_w * tile_h)
-
+// Rasterizer blocks: one tile per block.  Each thread owns PPT vertically
+// adjacent pixels of one column (block = tile pixels / PPT threads), so the
+// per-splat warp reductions of the backward are shared by PPT pixels; the
+// per-pixel work is branch-free so the PPT dependency chains interleave.  The
+// tile's sorted splats stream through shared memory in batches of BATCH
+// records.  (PPT, BATCH) is chosen per context by gs_autotune.
 __device__ __forceinline__ float block_sum(float x, float *s_red)
 {
 #pragma unroll
@@ -161,70 +170,171 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
     return t;
 }
 
-__global__ void __launch_bounds__(RB) k_raster_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
-                                                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                   const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                   int view, float *__restrict__ image, int use_target,
-                                                   float *__restrict__ dimage, float *__restrict__ loss)
+// Can splat (r0, r1) reach alpha >= 1/255 at any pixel centre of the box
+// [X0, X1] x [Y0, Y1]?  Intersects the box with the splat's square (widened
+// by a small margin), takes the minimum of sigma over the remaining rectangle
+// (zero if the mean is inside, otherwise on an edge, where sigma is a 1-D
+// quadratic) and compares o exp(-sigma_min) with the floor, with 0.1% slack.
+// It only ever says "no" when no pixel can pass the per-pixel tests, so
+// dropping such splats leaves every pixel's result unchanged.
+__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
 {
-    const float *target = use_target ? args->target[view] : nullptr;
-    __shared__ float4 s0[RB], s1[RB], s2[RB];
-    __shared__ float s_red[RB / 32];
-    const DevCam &cam = args->cam[view];
-    const int W = cam.width, H = cam.height, tw = cam.tile_w, tiles_x = cam.tiles_x;
-    const int tile = blockIdx.x;
-    const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
-    const int y = (tile / tiles_x) * cam.tile_h + (int)threadIdx.x / tw;
-    const bool inside = x < W && y < H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    const uint2 rg = ranges[tile];
-    const int nt = blockDim.x;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    bool done = !inside;
-    for (uint32_t b = rg.x; b < rg.y; b += nt) {
-        if (__syncthreads_count(!done) == 0) break;
-        uint32_t idx = b + threadIdx.x;
-        if (idx < rg.y) {
-            uint32_t k = svals[idx];
-            s0[threadIdx.x] = rec0[k];
-            s1[threadIdx.x] = rec1[k];
-            s2[threadIdx.x] = rec2[k];
+    const float margin = 1e-3f;
+    const float x0 = fmaxf(X0, r0.x - r0.z - margin), x1 = fminf(X1, r0.x + r0.z + margin);
+    const float y0 = fmaxf(Y0, r0.y - r0.z - margin), y1 = fminf(Y1, r0.y + r0.z + margin);
+    if (x0 > x1 || y0 > y1) return false;
+    // d = mean - p over the rectangle
+    const float dxl = r0.x - x1, dxh = r0.x - x0, dyl = r0.y - y1, dyh = r0.y - y0;
+    const float A = r1.x, B = r1.y, C = r1.z;
+    float smin = 0.f;
+    if (!(dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f)) {
+        smin = 3.4e38f;
+        // edges dx = const: minimiser dy = -B dx / C
+        const float dxs[2] = {dxl, dxh};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float dx = dxs[k];
+            const float dy = fminf(fmaxf(-B * dx / C, dyl), dyh);
+            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
         }
+        const float dys[2] = {dyl, dyh};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float dy = dys[k];
+            const float dx = fminf(fmaxf(-B * dy / A, dxl), dxh);
+            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+        }
+        smin = fmaxf(smin, 0.f);
+    }
+    return r0.w * __expf(-smin) >= ALPHA_MIN * 0.999f;
+}
+
+// Stage the tile's list entries [b, b + cnt) into shared memory, keeping, in
+// list order, only the splats that can reach some pixel of the tile.  Returns
+// the number kept.  s_gi receives each kept entry's position in the list.
+template <bool COLOR, bool INDEX>
+__device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
+                                           const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
+                                           uint32_t b, int cnt, float X0, float X1, float Y0, float Y1, float4 *s0,
+                                           float4 *s1, float4 *s2, uint32_t *s_k, int *s_gi, int *s_wcnt)
+{
+    const int nt = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = nt >> 5;
+    int base = 0;
+    for (int r0 = 0; r0 < cnt; r0 += nt) {
+        const int e = r0 + (int)threadIdx.x;
+        bool keep = false;
+        float4 a0, a1, a2;
+        uint32_t k = 0;
+        if (e < cnt) {
+            k = svals[b + e];
+            a0 = rec0[k];
+            a1 = rec1[k];
+            keep = splat_reaches_box(a0, a1, X0, X1, Y0, Y1);
+            if (COLOR && keep) a2 = rec2[k];
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
         __syncthreads();
-        int nb = min(nt, (int)(rg.y - b));
-        if (!done) {
-            for (int j = 0; j < nb; j++) {
-                float dx, dy, G;
+        int off = base, tot = 0;
+        for (int w = 0; w < nw; w++) {
+            const int c = s_wcnt[w];
+            off += w < wid ? c : 0;
+            tot += c;
+        }
+        if (keep) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            s0[pos] = a0;
+            s1[pos] = a1;
+            if (COLOR) s2[pos] = a2;
+            if (INDEX) {
+                s_k[pos] = k;
+                s_gi[pos] = (int)b + e;
+            }
+        }
+        base += tot;
+        __syncthreads();
+    }
+    return base;
+}
+
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
+                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                    const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
+                                                    int view, float *__restrict__ image, int use_target,
+                                                    float *__restrict__ dimage, float *__restrict__ loss)
+{
+    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
+    __shared__ int s_wcnt[8];
+    __shared__ float s_red[8];
+    const DevCam &cam = args->cam[view];
+    const float *target = use_target ? args->target[view] : nullptr;
+    const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
+    const int tile = blockIdx.x;
+    const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+    const int x = tx0 + (int)threadIdx.x % tw;
+    const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
+    const float px = (float)x + 0.5f;
+    // pixel rows of this warp (uniform): used to skip splats that miss them
+    const int rows_per_warp = 32 / tw * PPT;
+    const float wy0 = (float)(ty0 + ((int)threadIdx.x >> 5) * rows_per_warp) + 0.5f;
+    const float wy1 = wy0 + (float)(rows_per_warp - 1);
+    const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
+    const uint2 rg = ranges[tile];
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t live = 0;   // bit j: pixel j still compositing
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+        T[j] = 1.f;
+        C0[j] = C1[j] = C2[j] = 0.f;
+        if (x < W && y0 + j < H) live |= 1u << j;
+    }
+    for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
+        if (__syncthreads_count(live != 0) == 0) break;
+        const int nb = stage_batch<true, false>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
+                                                Y1, s0, s1, s2, nullptr, nullptr, s_wcnt);
+        for (int e = 0; e < nb && live; e++) {
+            const float4 r0 = s0[e];
+            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
+            const float dx = __fsub_rn(r0.x, px);
+            if (fabsf(dx) > r0.z) continue;                          // square test on x: shared by the column
+            const float4 r1 = s1[e], c = s2[e];
+#pragma unroll
+            for (int j = 0; j < PPT; j++) {
+                float dy, G;
                 bool cl;
-                float a = splat_alpha(s0[j], s1[j], px, py, dx, dy, G, cl);
-                if (a == 0.f) continue;
-                float Tn = T * (1.f - a);
-                if (Tn < T_STOP) {
-                    done = true;
-                    break;
-                }
-                float4 c = s2[j];
-                float aT = a * T;
-                C0 += c.x * aT;
-                C1 += c.y * aT;
-                C2 += c.z * aT;
-                T = Tn;
+                float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                a = ((live >> j) & 1u) ? a : 0.f;
+                const float Tn = T[j] * (1.f - a);
+                const bool stop = (a > 0.f) && (Tn < T_STOP);
+                a = stop ? 0.f : a;
+                live &= stop ? ~(1u << j) : ~0u;
+                const float aT = a * T[j];
+                C0[j] += c.x * aT;
+                C1[j] += c.y * aT;
+                C2[j] += c.z * aT;
+                T[j] = stop ? T[j] : Tn;
             }
         }
     }
-    const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+    const int64_t HW = (int64_t)W * H;
+    const float inv = 1.f / (float)(3 * HW);
     float part = 0.f;
-    if (inside) {
-        image[pix] = C0;
-        image[HW + pix] = C1;
-        image[2 * HW + pix] = C2;
-        if (target) {
-            float inv = 1.f / (float)(3 * HW);
-            float d0 = C0 - target[pix], d1 = C1 - target[HW + pix], d2 = C2 - target[2 * HW + pix];
-            dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
-            dimage[HW + pix] = (d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f));
-            dimage[2 * HW + pix] = (d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f));
-            part = (fabsf(d0) + fabsf(d1) + fabsf(d2)) * inv;
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+        const int y = y0 + j;
+        if (x < W && y < H) {
+            const int64_t pix = (int64_t)y * W + x;
+            image[pix] = C0[j];
+            image[HW + pix] = C1[j];
+            image[2 * HW + pix] = C2[j];
+            if (target) {
+                float d0 = C0[j] - target[pix], d1 = C1[j] - target[HW + pix], d2 = C2[j] - target[2 * HW + pix];
+                dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
+                dimage[HW + pix] = (d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f));
+                dimage[2 * HW + pix] = (d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f));
+                part += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * inv;
+            }
         }
     }
     if (target) {
@@ -234,136 +344,205 @@ __global__ void __launch_bounds__(RB) k_raster_fwd(const uint2 *__restrict__ ran
     }
 }
 
-__device__ __forceinline__ float warp_sum(float x)
+// Sum of v[0..7] over the 32 lanes, transposed: after 4 + 2 + 1 exchanges each
+// lane holds one index summed over 8 lanes, two more finish the sum.  Lanes
+// with (lane & 3) == 0 end with the total of index (lane >> 2).
+__device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
 {
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+    for (int i = 0; i < 4; i++) {
+        float send = b4 ? v[i] : v[i + 4], keep = b4 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        float send = b3 ? v[i] : v[i + 2], keep = b3 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        float send = b2 ? v[0] : v[1], keep = b2 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float r = v[0];
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
 }
 
-__global__ void __launch_bounds__(RB) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
-                                                   const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                   const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                   int view, const float *__restrict__ dimage, float *__restrict__ g9,
-                                                   int64_t gcap)
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
+                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                                                    const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
+                                                    int view, const float *__restrict__ dimage, float *__restrict__ g9,
+                                                    int64_t gcap)
 {
-    __shared__ float4 s0[RB], s1[RB], s2[RB];
-    __shared__ uint32_t s_k[RB];
+    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
+    __shared__ uint32_t s_k[BATCH];
+    __shared__ int s_gi[BATCH];
+    __shared__ int s_wcnt[8];
     __shared__ int s_end;
     const DevCam &cam = args->cam[view];
-    const int W = cam.width, H = cam.height, tw = cam.tile_w, tiles_x = cam.tiles_x;
+    const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tile = blockIdx.x;
-    const int x = (tile % tiles_x) * tw + (int)threadIdx.x % tw;
-    const int y = (tile / tiles_x) * cam.tile_h + (int)threadIdx.x / tw;
-    const bool inside = x < W && y < H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+    const int x = tx0 + (int)threadIdx.x % tw;
+    const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
+    const float px = (float)x + 0.5f;
+    const int rows_per_warp = 32 / tw * PPT;
+    const float wy0 = (float)(ty0 + ((int)threadIdx.x >> 5) * rows_per_warp) + 0.5f;
+    const float wy1 = wy0 + (float)(rows_per_warp - 1);
+    const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
-    const int nt = blockDim.x;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_end = (int)rg.x;
-    // phase 1: forward replay -> final transmittance and last contributor
-    float T = 1.f;
-    int last = -1;
-    bool done = !inside;
-    for (uint32_t b = rg.x; b < rg.y; b += nt) {
-        if (__syncthreads_count(!done) == 0) break;
-        uint32_t idx = b + threadIdx.x;
-        if (idx < rg.y) {
-            uint32_t k = svals[idx];
-            s0[threadIdx.x] = rec0[k];
-            s1[threadIdx.x] = rec1[k];
-        }
-        __syncthreads();
-        int nb = min(nt, (int)(rg.y - b));
-        if (!done) {
-            for (int j = 0; j < nb; j++) {
-                float dx, dy, G;
+    // phase 1: forward replay -> final transmittance and last contributor of each pixel
+    float T[PPT];
+    int last[PPT];
+    uint32_t live = 0;
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+        T[j] = 1.f;
+        last[j] = -1;
+        if (x < W && y0 + j < H) live |= 1u << j;
+    }
+    for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
+        if (__syncthreads_count(live != 0) == 0) break;
+        const int nb = stage_batch<false, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
+                                                Y1, s0, s1, s2, s_k, s_gi, s_wcnt);
+        for (int e = 0; e < nb && live; e++) {
+            const float4 r0 = s0[e];
+            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;
+            const float dx = __fsub_rn(r0.x, px);
+            if (fabsf(dx) > r0.z) continue;
+            const float4 r1 = s1[e];
+            const int gi = s_gi[e];
+#pragma unroll
+            for (int j = 0; j < PPT; j++) {
+                float dy, G;
                 bool cl;
-                float a = splat_alpha(s0[j], s1[j], px, py, dx, dy, G, cl);
-                if (a == 0.f) continue;
-                float Tn = T * (1.f - a);
-                if (Tn < T_STOP) {
-                    done = true;
-                    break;
-                }
-                T = Tn;
-                last = (int)(b + j);
+                float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                a = ((live >> j) & 1u) ? a : 0.f;
+                const float Tn = T[j] * (1.f - a);
+                const bool stop = (a > 0.f) && (Tn < T_STOP);
+                live &= stop ? ~(1u << j) : ~0u;
+                const bool used = (a > 0.f) && !stop;
+                T[j] = used ? Tn : T[j];
+                last[j] = used ? gi : last[j];
             }
         }
     }
+    int my_last = -1;
+#pragma unroll
+    for (int j = 0; j < PPT; j++) my_last = max(my_last, last[j]);
     __syncthreads();
-    if (last >= 0) atomicMax(&s_end, last + 1);
+    if (my_last >= 0) atomicMax(&s_end, my_last + 1);
     __syncthreads();
     const int end = s_end;
     // phase 2: back to front
-    const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (inside) {
-        g0 = dimage[pix];
-        g1 = dimage[HW + pix];
-        g2 = dimage[2 * HW + pix];
-    }
-    float R0 = 0.f, R1 = 0.f, R2 = 0.f;          // colour behind the current splat (background 0)
-    float la = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
-    float Tc = T;
-    for (int bend = end; bend > (int)rg.x; bend -= nt) {
-        int bstart = max((int)rg.x, bend - nt);
-        __syncthreads();
-        int idx = bstart + (int)threadIdx.x;
-        if (idx < bend) {
-            uint32_t k = svals[idx];
-            s_k[threadIdx.x] = k;
-            s0[threadIdx.x] = rec0[k];
-            s1[threadIdx.x] = rec1[k];
-            s2[threadIdx.x] = rec2[k];
+    const int64_t HW = (int64_t)W * H;
+    float g0[PPT], g1[PPT], g2[PPT], R0[PPT], R1[PPT], R2[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+        g0[j] = g1[j] = g2[j] = 0.f;
+        R0[j] = R1[j] = R2[j] = 0.f;       // colour behind the current splat (background 0)
+        if (x < W && y0 + j < H) {
+            const int64_t pix = (int64_t)(y0 + j) * W + x;
+            g0[j] = dimage[pix];
+            g1[j] = dimage[HW + pix];
+            g2[j] = dimage[2 * HW + pix];
         }
+    }
+    for (int bend = end; bend > (int)rg.x; bend -= BATCH) {
+        const int bstart = max((int)rg.x, bend - BATCH);
         __syncthreads();
-        for (int j = bend - bstart - 1; j >= 0; j--) {
-            const int gi = bstart + j;
+        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, (uint32_t)bstart, bend - bstart, X0, X1, Y0,
+                                               Y1, s0, s1, s2, s_k, s_gi, s_wcnt);
+        for (int e = nb - 1; e >= 0; e--) {
+            const int gi = s_gi[e];
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-            if (gi <= last) {
-                float dx, dy, G;
-                bool cl;
-                float4 r0 = s0[j], r1 = s1[j];
-                float a = splat_alpha(r0, r1, px, py, dx, dy, G, cl);
-                if (a != 0.f) {
-                    contrib = true;
-                    Tc = Tc / (1.f - a);
-                    float4 c = s2[j];
-                    R0 = la * lc0 + (1.f - la) * R0;
-                    R1 = la * lc1 + (1.f - la) * R1;
-                    R2 = la * lc2 + (1.f - la) * R2;
-                    float dLda = Tc * (g0 * (c.x - R0) + g1 * (c.y - R1) + g2 * (c.z - R2));
-                    float aT = a * Tc;
-                    v[6] = g0 * aT;
-                    v[7] = g1 * aT;
-                    v[8] = g2 * aT;
-                    if (!cl) {
-                        v[5] = G * dLda;
-                        float ds = -a * dLda;
-                        v[0] = ds * (r1.x * dx + r1.y * dy);
-                        v[1] = ds * (r1.y * dx + r1.z * dy);
-                        v[2] = 0.5f * ds * dx * dx;
-                        v[3] = ds * dx * dy;
-                        v[4] = 0.5f * ds * dy * dy;
-                    }
-                    la = a;
-                    lc0 = c.x;
-                    lc1 = c.y;
-                    lc2 = c.z;
+            const float4 r0 = s0[e];
+            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+            const float dx = __fsub_rn(r0.x, px);
+            if (gi <= my_last && fabsf(dx) <= r0.z) {
+                const float4 r1 = s1[e], c = s2[e];
+#pragma unroll
+                for (int j = 0; j < PPT; j++) {
+                    float dy, G;
+                    bool cl;
+                    float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                    a = (gi <= last[j]) ? a : 0.f;
+                    const bool on = a > 0.f;
+                    contrib |= on;
+                    T[j] = T[j] / (1.f - a);                 // transmittance in front of this splat (a = 0: unchanged)
+                    const float dLda = T[j] * (g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]));
+                    const float aT = a * T[j];
+                    v[6] += g0[j] * aT;
+                    v[7] += g1[j] * aT;
+                    v[8] += g2[j] * aT;
+                    const bool grad_a = on && !cl;           // the 0.999 clamp has no derivative
+                    const float ds = grad_a ? -a * dLda : 0.f;
+                    v[5] += grad_a ? G * dLda : 0.f;
+                    v[0] += ds * (r1.x * dx + r1.y * dy);
+                    v[1] += ds * (r1.y * dx + r1.z * dy);
+                    v[2] += 0.5f * ds * dx * dx;
+                    v[3] += ds * dx * dy;
+                    v[4] += 0.5f * ds * dy * dy;
+                    R0[j] = a * c.x + (1.f - a) * R0[j];
+                    R1[j] = a * c.y + (1.f - a) * R1[j];
+                    R2[j] = a * c.z + (1.f - a) * R2[j];
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const uint32_t k = s_k[j];
+                const uint32_t k = s_k[e];
+                float s8 = v[8];
 #pragma unroll
-                for (int f = 0; f < 9; f++) {
-                    float s = warp_sum(v[f]);
-                    if (lane == 0 && s != 0.f) atomicAdd(g9 + f * gcap + k, s);
-                }
+                for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+                float sum = warp_transpose_sum8(v, lane);
+                if ((lane & 3) == 0 && sum != 0.f) atomicAdd(g9 + (lane >> 2) * gcap + k, sum);
+                if (lane == 0 && s8 != 0.f) atomicAdd(g9 + 8 * gcap + k, s8);
             }
         }
     }
+}
+
+typedef void (*RasterFwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
+                            const DevArgs *, int, float *, int, float *, float *);
+typedef void (*RasterBwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
+                            const DevArgs *, int, const float *, float *, int64_t);
+
+// Variant v: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128.
+static RasterFwdFn fwd_variant(int v)
+{
+    switch (v) {
+    case 0: return k_raster_fwd<1, 128>;
+    case 1: return k_raster_fwd<1, 256>;
+    case 2: return k_raster_fwd<2, 128>;
+    case 3: return k_raster_fwd<2, 256>;
+    case 4: return k_raster_fwd<4, 128>;
+    default: return k_raster_fwd<4, 256>;
+    }
+}
+
+static RasterBwdFn bwd_variant(int v)
+{
+    switch (v) {
+    case 0: return k_raster_bwd<1, 128>;
+    case 1: return k_raster_bwd<1, 256>;
+    case 2: return k_raster_bwd<2, 128>;
+    case 3: return k_raster_bwd<2, 256>;
+    case 4: return k_raster_bwd<4, 128>;
+    default: return k_raster_bwd<4, 256>;
+    }
+}
+
+bool raster_variant_ok(int v, int tile_w, int tile_h)
+{
+    if (v < 0 || v >= N_RASTER_VARIANTS) return false;
+    const int ppt = 1 << (v >> 1);
+    const int threads = tile_w * tile_h / ppt;
+    return tile_h % ppt == 0 && threads >= 32 && threads <= 256 && threads % 32 == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -598,8 +777,10 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
                     Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
-    k_gather_project<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
-        sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1, rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect);
+    auto gp = sc.deg == 3 ? k_gather_project<3> : sc.deg == 2 ? k_gather_project<2>
+            : sc.deg == 1 ? k_gather_project<1> : k_gather_project<0>;
+    gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
+                                                          rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect);
     // depth order of the visible set (stable: ties keep ascending index)
     int dcur = radix_sort(rb.dk[0], rb.dv[0], rb.dk[1], rb.dv[1], n_vis, cap, 32, w, s);
     const uint32_t *dsorted = rb.dv[dcur];
@@ -615,8 +796,9 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
     rb.sorted_keys = rb.tk[tcur];
     rb.sorted_vals = rb.tv[tcur];
     rb.tiles = tiles;
-    k_raster_fwd<<<tiles, cam.tile_w * cam.tile_h, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args,
-                                                           view, image, use_target ? 1 : 0, dimage, loss);
+    const int ppt = 1 << (rb.variant >> 1);
+    fwd_variant(rb.variant)<<<tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
+        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, image, use_target ? 1 : 0, dimage, loss);
 }
 
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
@@ -625,8 +807,9 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
 {
     const int cap = (int)rb.cap;
     launch_zero_rows(rb.g9, 9, cap, n_vis, cap, w, s);
-    k_raster_bwd<<<rb.tiles, cam.tile_w * cam.tile_h, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2,
-                                                              args, view, dimage, rb.g9, cap);
+    const int ppt = 1 << (rb.variant >> 1);
+    bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
+        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap);
     k_project_bwd<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9,
                                                                      grad, gcap, ids, remap_mask, remap_prefix,
                                                                      accumulate ? 1 : 0, w.status);

@@ -268,7 +268,9 @@ def cfg_diff_check(n=200_000, width=512):
 def cfg_aerial(n=10_000_000, n_views=16, width=1920, height=1080, seed_views=2, scale=5.0,
                n_clusters=200):
     """Aerial heightfield: the 1M generator scaled x5 in x,y (1x1 km), 20 m
-    amplitude, 200 clusters; nadir-oblique views at 150-300 m altitude."""
+    amplitude, 200 clusters; nadir-oblique views at 150-300 m altitude.  A
+    smaller n with scale 5 sqrt(n / 10M) and 200 n / 10M clusters keeps the 10M
+    scene's density, hence the same per-view raster load."""
     he = 100.0 * scale
     scene = heightfield_scene(n, seed=0, half_extent=he, amplitude=20.0,
                               wavelength=(20.0 * scale, 25.0 * scale), n_clusters=n_clusters)

@@ -164,6 +164,43 @@ def test_render_backward_parity(gs, orc, name):
     assert max(errs.values()) <= 1e-4, errs
 
 
+@pytest.mark.parametrize("name,tile", [("cube_offaxis_sh3", (16, 16)), ("ragged_tiles", (16, 16)),
+                                       ("tile32x8", (32, 8)), ("cube10k", (8, 8)), ("cube10k", (16, 8))])
+def test_raster_variants_agree(gs, orc, name, tile):
+    """Every rasterizer variant (pixels per thread, batch) the tile shape allows
+    renders the same image bit for bit, and its gradients match the oracle."""
+    P, cam, deg, _ = _case(name)
+    camf = cam_f32(cam)
+    n, D = P.shape[1], P.shape[0]
+    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=tile)
+    scene = gs.GaussianScene(P, deg)
+    ids, nv = ctx.cull(scene, camf)
+    r = orc.render(f32(P), deg, camf, tile)
+    dimg = np.random.default_rng(2).normal(size=r["image"].shape)
+    g_ref, _ = orc.backward(f32(P), deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], dimg)
+    dimg_t = torch.as_tensor(dimg, dtype=torch.float32, device="cuda")
+    images, tried = [], 0
+    for v in range(6):
+        try:
+            ctx.set_raster_variant(v)
+        except Exception:
+            continue
+        tried += 1
+        img = ctx.render_fwd(scene, camf, ids, nv)
+        gc = ctx.render_bwd(dimg_t, D)
+        full = ctx.grad_scatter(scene, ids, nv, gc)
+        ctx.sync_status()
+        images.append(img.cpu().numpy())
+        g_gpu = full[:, :n].cpu().numpy().astype(np.float64)
+        errs = {k: rel_group_error(g_gpu, g_ref, sl) for k, sl in GROUPS.items() if g_ref[sl].size}
+        assert max(errs.values()) <= 1e-4, (v, errs)
+    assert tried >= 2
+    for im in images[1:]:
+        np.testing.assert_array_equal(im, images[0])
+    chosen, ms = ctx.autotune(scene, camf)
+    assert ms[chosen] is not None and ms[chosen] == min(t for t in ms if t is not None)
+
+
 def test_loss_l1_kernel(gs):
     ctx = make_ctx(gs, 64, 40, 30)
     rng = np.random.default_rng(0)
@@ -272,6 +309,49 @@ def test_materialize_parity(gs, orc):
     gw = wo[:, :n].cpu().numpy().astype(np.float64)
     bound = 16 * u * (np.abs(f32(w)) + np.abs(W - f32(w)))
     assert np.all(np.abs(gw - W) <= bound + 1e-30), np.max(np.abs(gw - W) / (bound + 1e-30))
+
+
+def test_restore_directions(gs):
+    """The stored restore directions equal m / (sqrt(v) + eps) after refresh and
+    after optimizer steps, and culling / rendering through them is bit-identical
+    to recomputing the restore from m and v."""
+    rng = np.random.default_rng(12)
+    n, deg = 6000, 1
+    P = scenes.uniform_cube_scene(n, seed=12, sh_degree=deg, log_scale_mean=-3.0)
+    scene = gs.GaussianScene(P, deg)
+    D = scene.D
+    scene.m[:, :n] = torch.as_tensor(rng.normal(size=(D, n)) * 1e-2, dtype=torch.float32, device="cuda")
+    scene.v[:, :n] = torch.as_tensor(rng.uniform(1e-8, 1e-5, (D, n)), dtype=torch.float32, device="cuda")
+    scene.counter[:n] = torch.as_tensor(rng.integers(0, 16, n), dtype=torch.uint8, device="cuda")
+    scene.step = 30
+    adam = gs.adam_struct(lr=1e-2, eps=1e-15)
+    cam = scenes.camera_lookat((0.3, -0.2, -3.0), (0.0, 0.0, 0.0), 96, 64, 60.0, up=(0, -1, 0))
+    ctx = make_ctx(gs, n, 96, 64, deg=deg)
+    ctx.refresh_rdir(scene, adam)
+    eps32 = np.float32(1e-15)
+
+    def expected(sc):
+        m = sc.m[:, :n].cpu().numpy()
+        v = sc.v[:, :n].cpu().numpy()
+        return m / (np.sqrt(v) + eps32)
+
+    np.testing.assert_array_equal(scene.rdir[:, :n].cpu().numpy(), expected(scene))
+    ids_a, nv_a = ctx.cull(scene, cam, adam)
+    img_a = ctx.render_fwd(scene, cam, ids_a, nv_a, adam)
+    rdir = scene.rdir
+    scene.rdir = None                                   # recompute from m and v
+    ids_b, nv_b = ctx.cull(scene, cam, adam)
+    img_b = ctx.render_fwd(scene, cam, ids_b, nv_b, adam)
+    ctx.sync_status()
+    assert nv_a.item() == nv_b.item() > 0
+    assert torch.equal(ids_a[:nv_a.item()], ids_b[:nv_b.item()])
+    assert torch.equal(img_a, img_b)
+    scene.rdir = rdir
+    gc = torch.as_tensor(rng.normal(size=(D, ctx.max_visible)) * 1e-3, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ctx.adam_deferred(scene, ids_a, nv_a, gc, adam)
+    ctx.sync_status()
+    np.testing.assert_array_equal(scene.rdir[:, :n].cpu().numpy(), expected(scene))
 
 
 def test_deferred_trajectory_tracks_eager(gs, orc):

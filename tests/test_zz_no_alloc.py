@@ -40,6 +40,7 @@ def test_noalloc_cull_matches_context_cull_twice():
             scenes.camera_lookat((-1.5, 0.4, -2.5), (0.3, 0.0, 0.5), 128, 96, 75.0, up=(0, -1, 0))]
     ctx = gs.Context(max_gaussians=n, max_visible=n, max_keys=10 * n, max_width=128, max_height=96, tile=tile,
                      max_sh_degree=deg)
+    ctx.refresh_rdir(scene, adam)                    # m and v were set directly
     for cam, ad in ((cams[0], None), (cams[1], adam)):           # two calls in a row, the second with restore
         ids_ref, nv_ref = ctx.cull(scene, cam, ad)
         ids = torch.full((n,), -1, dtype=torch.int32, device="cuda")
