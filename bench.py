@@ -132,8 +132,9 @@ def run_ours(args):
     D = 11 + 3 * (deg + 1) ** 2
     H, W = cams[0].height, cams[0].width
 
-    ctx = gs.Context(max_gaussians=N, max_visible=int(N * 0.6), max_keys=80_000_000, max_width=W, max_height=H,
-                     tile=(16, 16), max_views=1, max_sh_degree=deg, device=local)
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    ctx = gs.Context(max_gaussians=N, max_visible=int(N * 0.6), max_keys=160_000_000, max_width=W, max_height=H,
+                     tile=tile, max_views=1, max_sh_degree=deg, device=local)
     # targets: the seed-1 scene rendered by the same library (setup, untimed)
     tscene = gs.GaussianScene(tgt_params, deg, device=dev, with_optimizer=False)
     del tgt_params
@@ -262,7 +263,7 @@ def run_ours(args):
         "ms_per_step": round(ms_total / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
         "config": {"workload": cfg_note, "gaussians": N, "image": f"{W}x{H}", "sh_degree": deg,
-                   "views_per_step": 1, "form": "plain_fp32", "adam": "deferred", "tile": "16x16",
+                   "views_per_step": 1, "form": "plain_fp32", "adam": "deferred", "tile": args.tile,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (parameters+moments 7.1 GB), no flush",
                    "visible_per_view": round(n_vis), "keys_per_view": round(n_keys), "update_set": round(n_upd),
@@ -375,6 +376,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--density-of", type=int, default=None,
                     help="scale the scene area so that --gaussians keeps the density of this many (profiling cases)")
+    ap.add_argument("--tile", default="8x8", help="raster tile WxH (W in 4..64, W*H in 64, 128, 256)")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:

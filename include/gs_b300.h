@@ -116,7 +116,7 @@ typedef struct {
     int64_t max_visible;     /* capacity of the compact visible set per view */
     int64_t max_keys;        /* capacity of (tile, Gaussian) keys per view */
     int32_t max_width, max_height;
-    int32_t tile_w, tile_h;  /* raster tile: tile_w in {4, 8, 16, 32, 64}, tile_w * tile_h in {64, 128, 256} */
+    int32_t tile_w, tile_h;  /* raster tile: tile_w in {4, 8, 16, 32, 64}, tile_w * tile_h in {32, 64, 128, 256} */
     int32_t max_views;       /* views per gs_step, 1..8 */
     int32_t max_sh_degree;   /* 0..3 */
 } gs_config;

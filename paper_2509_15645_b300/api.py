@@ -100,7 +100,7 @@ class GaussianScene:
 class Context:
     """One gs_ctx: scratch workspace (a torch allocation) and the hot-path calls."""
 
-    def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(16, 16), max_views=1,
+    def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
                  max_sh_degree=3, device=0):
         self.lib = L.load()
         cfg = L.Config()

@@ -32,6 +32,7 @@ struct DevLut {
     float mom[LUT_N], var[LUT_N];   // b1^(d+1), b2^(d+1)
     float step_size[N_GROUPS];      // lr / (1 - b1^t)
     float bias_corr;                // sqrt(1 - b2^t)
+    float inv_bias_corr;            // 1 / sqrt(1 - b2^t)
     float omb1, omb2, eps;          // 1 - b1, 1 - b2, eps
     float b1, b2;
     int max_defer;
@@ -71,7 +72,7 @@ __host__ __device__ __forceinline__ int lr_group(int row)
 // optimizer (the scene's rdir planes) so that the restore is one FMA; the two
 // helpers below are the only places either quantity is formed, so a stored
 // direction and a recomputed one give the same restored value bit for bit.
-__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return m / (sqrtf(v) + eps); }
+__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return __fdividef(m, sqrtf(v) + eps); }
 
 __device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, int d)
 {

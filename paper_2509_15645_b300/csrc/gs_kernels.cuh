@@ -37,7 +37,8 @@ struct Work {
 void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *total_out, int total_cap,
                     cudaStream_t s);
 void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
-                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s);
+                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s, uint8_t *counter = nullptr,
+                  uint8_t *delay = nullptr);
 int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
                Work &w, cudaStream_t s);
 
@@ -67,7 +68,7 @@ void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w,
 // k_adam.cu
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                           const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
-                          int *n_upd, Work &w, cudaStream_t s);
+                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s);
 void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s);
 void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s);

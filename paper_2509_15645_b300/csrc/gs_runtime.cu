@@ -54,6 +54,7 @@ struct gs_ctx {
     uint32_t *mask = nullptr, *wprefix = nullptr, *chunk = nullptr;
     uint32_t *umask = nullptr, *uchunk = nullptr;
     int32_t *uids = nullptr;
+    uint8_t *udelay = nullptr;
     uint32_t *amask = nullptr, *aprefix = nullptr, *achunk = nullptr;
     uint32_t *vmask[MAX_VIEWS] = {nullptr};
     uint32_t *vprefix[MAX_VIEWS] = {nullptr};
@@ -125,7 +126,8 @@ static bool valid_cfg(const gs_config *c)
     int tp = c->tile_w * c->tile_h;
     return c->max_gaussians > 0 && c->max_gaussians < (1ll << 31) - CHUNK && c->max_visible > 0 &&
            c->max_visible < (1ll << 31) && c->max_keys > 0 && c->max_keys < (1ll << 32) - 1 && c->max_width > 0 &&
-           c->max_height > 0 && c->tile_w >= 4 && c->tile_h > 0 && 64 % c->tile_w == 0 && (tp == 64 || tp == 128 || tp == 256) &&
+           c->max_height > 0 && c->tile_w >= 4 && c->tile_h > 0 && 64 % c->tile_w == 0 &&
+           (tp == 32 || tp == 64 || tp == 128 || tp == 256) &&
            c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h;
 }
@@ -152,6 +154,7 @@ static void carve(gs_ctx *c, char *base)
     c->umask = k.take<uint32_t>(NW);
     c->uchunk = k.take<uint32_t>(NC);
     c->uids = k.take<int32_t>(N);
+    c->udelay = k.take<uint8_t>(N);
     c->amask = k.take<uint32_t>(NW);
     c->aprefix = k.take<uint32_t>(NW);
     c->achunk = k.take<uint32_t>(NC);
@@ -244,6 +247,7 @@ static DevLut make_lut(const gs_adam_cfg *a, int t, bool restore)
         L.var[i] = (float)std::pow(b2, i + 1);
     }
     L.bias_corr = (float)std::sqrt(1.0 - std::pow(b2, t));
+    L.inv_bias_corr = (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t)));
     L.omb1 = (float)(1.0 - b1);
     L.omb2 = (float)(1.0 - b2);
     L.eps = a->eps;
@@ -475,7 +479,7 @@ gs_status gs_adam_deferred(gs_ctx *c, gs_scene *scene, const int32_t *ids, const
     compact_mask(c->amask, sv.n, c->achunk, false, nullptr, c->aprefix, (int)sv.n, c->n_tmp, c->w, s);
     if (adam->mode == GS_ADAM_DEFERRED)
         launch_adam_deferred(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->umask, c->uchunk,
-                             c->uids, &c->cnt->n_upd, c->w, s);
+                             c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
     else
         launch_adam_eager(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->w, s);
     st = cuda_check(c, "gs_adam_deferred");
@@ -693,8 +697,8 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
     }
     c->w.mark(TP_ADAM0, s);
     if (mode == GS_ADAM_DEFERRED)
-        launch_adam_deferred(sv, args, gmask, gprefix, c->grad_u, gcap, c->umask, c->uchunk, c->uids, &c->cnt->n_upd,
-                             c->w, s);
+        launch_adam_deferred(sv, args, gmask, gprefix, c->grad_u, gcap, c->umask, c->uchunk, c->uids, c->udelay,
+                             &c->cnt->n_upd, c->w, s);
     else
         launch_adam_eager(sv, args, gmask, gprefix, c->grad_u, gcap, c->w, s);
     c->w.mark(TP_ADAM1, s);

@@ -64,7 +64,7 @@ struct SLut {
     float param[N_GROUPS][LUT_N];
     float mom[LUT_N], var[LUT_N];
     float step_size[N_GROUPS];
-    float bias_corr, omb1, omb2, eps;
+    float bias_corr, inv_bias_corr, omb1, omb2, eps;
 };
 
 __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
@@ -73,20 +73,28 @@ __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
     if (t < N_GROUPS * LUT_N) s.param[t / LUT_N][t % LUT_N] = L.param[t / LUT_N][t % LUT_N];
     if (t < LUT_N) { s.mom[t] = L.mom[t]; s.var[t] = L.var[t]; }
     if (t < N_GROUPS) s.step_size[t] = L.step_size[t];
-    if (t == 0) { s.bias_corr = L.bias_corr; s.omb1 = L.omb1; s.omb2 = L.omb2; s.eps = L.eps; }
+    if (t == 0) {
+        s.bias_corr = L.bias_corr;
+        s.inv_bias_corr = L.inv_bias_corr;
+        s.omb1 = L.omb1;
+        s.omb2 = L.omb2;
+        s.eps = L.eps;
+    }
     __syncthreads();
 }
 
 // Restore (delay d) + Eq. 1 for one value.  d = 0 is the plain Adam step.
-__device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
+// Returns the new restore direction m_new / (sqrt(v_new) + eps).
+__device__ __forceinline__ float adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
 {
     float m_new = L.mom[d] * m + L.omb1 * g;
     float v_new = L.var[d] * v + L.omb2 * g * g;
     float wr = restore_param(w, m, v, L.param[grp][d], d, L.eps);
-    float denom = sqrtf(v_new) / L.bias_corr + L.eps;
-    w = wr - L.step_size[grp] * m_new / denom;
+    float denom = sqrtf(v_new) * L.inv_bias_corr + L.eps;
+    w = wr - L.step_size[grp] * __fdividef(m_new, denom);
     m = m_new;
     v = v_new;
+    return restore_dir(m_new, v_new, L.eps);
 }
 
 __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask, const uint32_t *__restrict__ vprefix,
@@ -121,22 +129,62 @@ __device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__rest
         for (int u = 0; u < UNROLL; u++) {
             int r = r0 + u;
             if (r < D) {
-                adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
+                const float dir = adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
                 float *wp = r < N_GEO ? geo + r * pitch + i : sh + (r - N_GEO) * pitch + i;
                 *wp = w_[u];
                 m[r * pitch + i] = m_[u];
                 v[r * pitch + i] = v_[u];
-                if (rdir) rdir[r * pitch + i] = restore_dir(m_[u], v_[u], L.eps);
+                if (rdir) rdir[r * pitch + i] = dir;
             }
+        }
+    }
+}
+
+// One thread per (update-set member, group of RG planes), blockIdx.y selects
+// the plane group.  The loads of a thread's next member are issued before the
+// current member's arithmetic, so every warp keeps memory requests in flight
+// while it computes.  The member's delay comes from the compaction (which
+// already cleared its counter).
+constexpr int RG = 4;
+
+struct AdamRows {
+    float w[RG], m[RG], v[RG], g[RG];
+    int64_t i;
+    int d;
+};
+
+__device__ __forceinline__ float *plane(float *geo, float *sh, int64_t pitch, int r)
+{
+    return r < N_GEO ? geo + r * pitch : sh + (r - N_GEO) * pitch;
+}
+
+__device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__restrict__ uids,
+                                           const uint8_t *__restrict__ udelay, const uint32_t *__restrict__ vmask,
+                                           const uint32_t *__restrict__ vprefix, float *geo, float *sh,
+                                           const float *__restrict__ m, const float *__restrict__ v,
+                                           const float *__restrict__ grad, int64_t gcap, int64_t pitch, int D, int r0)
+{
+    a.i = uids[u];
+    a.d = udelay[u];
+    int k = compact_index(vmask, vprefix, a.i);
+    if (k >= gcap) k = -1;     // outside the caller's gradient buffer: treated as zero gradient
+#pragma unroll
+    for (int j = 0; j < RG; j++) {
+        const int r = r0 + j;
+        if (r < D) {
+            a.w[j] = plane(geo, sh, pitch, r)[a.i];
+            a.m[j] = m[r * pitch + a.i];
+            a.v[j] = v[r * pitch + a.i];
+            a.g[j] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
         }
     }
 }
 
 __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ geo, float *__restrict__ sh,
                                                            float *__restrict__ m, float *__restrict__ v,
-                                                           float *__restrict__ rdir,
-                                                           uint8_t *__restrict__ counter, int64_t pitch, int D,
-                                                           const int32_t *__restrict__ uids, const int *n_upd_p,
+                                                           float *__restrict__ rdir, int64_t pitch, int D,
+                                                           const int32_t *__restrict__ uids,
+                                                           const uint8_t *__restrict__ udelay, const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
                                                            const float *__restrict__ grad, int64_t gcap,
@@ -145,28 +193,47 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ g
     __shared__ SLut L;
     load_slut(L, args->lut);
     const int n_upd = *n_upd_p;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_upd; u += gridDim.x * blockDim.x) {
-        int64_t i = uids[u];
-        int d = counter[i];
-        int k = compact_index(vmask, vprefix, i);
-        if (k >= gcap) k = -1;     // outside the caller's gradient buffer: treated as zero gradient
-        adam_rows<4>(geo, sh, m, v, rdir, pitch, D, i, k, grad, gcap, d, L);
-        counter[i] = 0;
+    const int r0 = blockIdx.y * RG;
+    const int stride = gridDim.x * blockDim.x;
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_upd) return;
+    AdamRows cur, nxt;
+    adam_fetch(cur, u, uids, udelay, vmask, vprefix, geo, sh, m, v, grad, gcap, pitch, D, r0);
+    while (true) {
+        const int un = u + stride;
+        const bool more = un < n_upd;
+        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, geo, sh, m, v, grad, gcap, pitch, D, r0);
+#pragma unroll
+        for (int j = 0; j < RG; j++) {
+            const int r = r0 + j;
+            if (r < D) {
+                float w_ = cur.w[j], m_ = cur.m[j], v_ = cur.v[j];
+                const float dir = adam_value(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
+                plane(geo, sh, pitch, r)[cur.i] = w_;
+                m[r * pitch + cur.i] = m_;
+                v[r * pitch + cur.i] = v_;
+                if (rdir) rdir[r * pitch + cur.i] = dir;
+            }
+        }
+        if (!more) break;
+        cur = nxt;
+        u = un;
     }
 }
 
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                           const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
-                          int *n_upd, Work &w, cudaStream_t s)
+                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s)
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     k_adam_select<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.counter, vmask, sc.n, args, umask,
                                                                                 uchunk);
-    compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s);
+    compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s, sc.counter, udelay);
+    const int groups = (sc.D + RG - 1) / RG;
+    dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
     w.mark(TP_APPLY0, s);
-    k_adam_apply<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.counter,
-                                                               sc.pitch, sc.D, uids, n_upd, vmask, vprefix, grad,
-                                                               gcap, args);
+    k_adam_apply<<<grid, ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.pitch, sc.D, uids, udelay, n_upd,
+                                             vmask, vprefix, grad, gcap, args);
     w.mark(TP_APPLY1, s);
 }
 

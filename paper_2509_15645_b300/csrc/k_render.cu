@@ -275,9 +275,10 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
     const int x = tx0 + (int)threadIdx.x % tw;
     const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
     const float px = (float)x + 0.5f;
-    // pixel rows of this warp (uniform): used to skip splats that miss them
-    const int rows_per_warp = 32 / tw * PPT;
-    const float wy0 = (float)(ty0 + ((int)threadIdx.x >> 5) * rows_per_warp) + 0.5f;
+    // pixel rows covered by this warp (uniform): its first thread's row set plus
+    // the further thread rows its 32 lanes span
+    const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
+    const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
     const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
@@ -298,22 +299,25 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
             const float dx = __fsub_rn(r0.x, px);
             if (fabsf(dx) > r0.z) continue;                          // square test on x: shared by the column
-            const float4 r1 = s1[e], c = s2[e];
+            const float4 r1 = s1[e];
 #pragma unroll
             for (int j = 0; j < PPT; j++) {
+                if (!((live >> j) & 1u)) continue;
                 float dy, G;
                 bool cl;
-                float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
-                a = ((live >> j) & 1u) ? a : 0.f;
+                const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                if (a == 0.f) continue;
                 const float Tn = T[j] * (1.f - a);
-                const bool stop = (a > 0.f) && (Tn < T_STOP);
-                a = stop ? 0.f : a;
-                live &= stop ? ~(1u << j) : ~0u;
+                if (Tn < T_STOP) {
+                    live &= ~(1u << j);
+                    continue;
+                }
+                const float4 c = s2[e];
                 const float aT = a * T[j];
                 C0[j] += c.x * aT;
                 C1[j] += c.y * aT;
                 C2[j] += c.z * aT;
-                T[j] = stop ? T[j] : Tn;
+                T[j] = Tn;
             }
         }
     }
@@ -389,8 +393,10 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     const int x = tx0 + (int)threadIdx.x % tw;
     const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
     const float px = (float)x + 0.5f;
-    const int rows_per_warp = 32 / tw * PPT;
-    const float wy0 = (float)(ty0 + ((int)threadIdx.x >> 5) * rows_per_warp) + 0.5f;
+    // pixel rows covered by this warp (uniform): its first thread's row set plus
+    // the further thread rows its 32 lanes span
+    const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
+    const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
     const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
@@ -419,16 +425,18 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
             const int gi = s_gi[e];
 #pragma unroll
             for (int j = 0; j < PPT; j++) {
+                if (!((live >> j) & 1u)) continue;
                 float dy, G;
                 bool cl;
-                float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
-                a = ((live >> j) & 1u) ? a : 0.f;
+                const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                if (a == 0.f) continue;
                 const float Tn = T[j] * (1.f - a);
-                const bool stop = (a > 0.f) && (Tn < T_STOP);
-                live &= stop ? ~(1u << j) : ~0u;
-                const bool used = (a > 0.f) && !stop;
-                T[j] = used ? Tn : T[j];
-                last[j] = used ? gi : last[j];
+                if (Tn < T_STOP) {
+                    live &= ~(1u << j);
+                    continue;
+                }
+                T[j] = Tn;
+                last[j] = gi;
             }
         }
     }
@@ -459,36 +467,38 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
         const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, (uint32_t)bstart, bend - bstart, X0, X1, Y0,
                                                Y1, s0, s1, s2, s_k, s_gi, s_wcnt);
         for (int e = nb - 1; e >= 0; e--) {
-            const int gi = s_gi[e];
-            float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool contrib = false;
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+            const int gi = s_gi[e];
             const float dx = __fsub_rn(r0.x, px);
+            float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contrib = false;
             if (gi <= my_last && fabsf(dx) <= r0.z) {
-                const float4 r1 = s1[e], c = s2[e];
+                const float4 r1 = s1[e];
 #pragma unroll
                 for (int j = 0; j < PPT; j++) {
+                    if (gi > last[j]) continue;
                     float dy, G;
                     bool cl;
-                    float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
-                    a = (gi <= last[j]) ? a : 0.f;
-                    const bool on = a > 0.f;
-                    contrib |= on;
-                    T[j] = T[j] / (1.f - a);                 // transmittance in front of this splat (a = 0: unchanged)
+                    const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                    if (a == 0.f) continue;
+                    contrib = true;
+                    const float4 c = s2[e];
+                    T[j] = __fdividef(T[j], 1.f - a);        // transmittance in front of this splat
                     const float dLda = T[j] * (g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]));
                     const float aT = a * T[j];
                     v[6] += g0[j] * aT;
                     v[7] += g1[j] * aT;
                     v[8] += g2[j] * aT;
-                    const bool grad_a = on && !cl;           // the 0.999 clamp has no derivative
-                    const float ds = grad_a ? -a * dLda : 0.f;
-                    v[5] += grad_a ? G * dLda : 0.f;
-                    v[0] += ds * (r1.x * dx + r1.y * dy);
-                    v[1] += ds * (r1.y * dx + r1.z * dy);
-                    v[2] += 0.5f * ds * dx * dx;
-                    v[3] += ds * dx * dy;
-                    v[4] += 0.5f * ds * dy * dy;
+                    if (!cl) {                                   // the 0.999 clamp has no derivative
+                        const float ds = -a * dLda;
+                        v[5] += G * dLda;
+                        v[0] += ds * (r1.x * dx + r1.y * dy);
+                        v[1] += ds * (r1.y * dx + r1.z * dy);
+                        v[2] += 0.5f * ds * dx * dx;
+                        v[3] += ds * dx * dy;
+                        v[4] += 0.5f * ds * dy * dy;
+                    }
                     R0[j] = a * c.x + (1.f - a) * R0[j];
                     R1[j] = a * c.y + (1.f - a) * R1[j];
                     R2[j] = a * c.z + (1.f - a) * R2[j];

@@ -128,7 +128,7 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *
 // exclusive scan of per-chunk popcounts.  Writes ids (ascending, only those
 // below cap) and word_prefix[w] = number of set bits before word w.
 __global__ void k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords, const uint32_t *__restrict__ chunk_ofs,
-                               int32_t *ids, uint32_t *word_prefix, int cap)
+                               int32_t *ids, uint32_t *word_prefix, int cap, uint8_t *counter, uint8_t *delay)
 {
     __shared__ uint32_t s_pref[CHUNK_WORDS];
     __shared__ uint32_t s_warp[33];
@@ -151,7 +151,12 @@ __global__ void k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords
             uint32_t m = mask[w0 + j];
             if ((m >> lane) & 1u) {
                 uint32_t pos = s_pref[j] + __popc(m & ((1u << lane) - 1u));
-                if (ids && (int)pos < cap) ids[pos] = (int32_t)((w0 + j) * 32 + lane);
+                const int64_t id = (w0 + j) * 32 + lane;
+                if (ids && (int)pos < cap) ids[pos] = (int32_t)id;
+                if (counter && (int)pos < cap) {       // optimizer update set: record the delay, clear the counter
+                    delay[pos] = counter[id];
+                    counter[id] = 0;
+                }
             }
         }
         __syncthreads();
@@ -176,7 +181,8 @@ __global__ void k_chunk_counts(const uint32_t *__restrict__ mask, int64_t nwords
 }
 
 void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
-                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s)
+                  uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s, uint8_t *counter,
+                  uint8_t *delay)
 {
     int64_t nwords = (n + 31) / 32;
     int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
@@ -184,7 +190,8 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
         k_chunk_counts<<<w.grid(nchunks * 32, 256), 256, 0, s>>>(mask, nwords, chunk_cnt);
     ScanLen L{nullptr, 1, 1, 0, (int)nchunks, 0};
     scan_exclusive(chunk_cnt, chunk_cnt, L, w, count_out, cap, s);
-    k_compact_mask<<<w.grid(nchunks * 256, 256), 256, 0, s>>>(mask, nwords, chunk_cnt, ids, word_prefix, cap);
+    k_compact_mask<<<w.grid(nchunks * 256, 256), 256, 0, s>>>(mask, nwords, chunk_cnt, ids, word_prefix, cap, counter,
+                                                              delay);
 }
 
 // ---------------------------------------------------------------------------

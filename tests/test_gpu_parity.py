@@ -165,7 +165,8 @@ def test_render_backward_parity(gs, orc, name):
 
 
 @pytest.mark.parametrize("name,tile", [("cube_offaxis_sh3", (16, 16)), ("ragged_tiles", (16, 16)),
-                                       ("tile32x8", (32, 8)), ("cube10k", (8, 8)), ("cube10k", (16, 8))])
+                                       ("tile32x8", (32, 8)), ("cube10k", (8, 8)), ("cube10k", (16, 8)),
+                                       ("cube10k", (64, 4)), ("cube_offaxis_sh3", (8, 4)), ("ragged_tiles", (4, 8))])
 def test_raster_variants_agree(gs, orc, name, tile):
     """Every rasterizer variant (pixels per thread, batch) the tile shape allows
     renders the same image bit for bit, and its gradients match the oracle."""
@@ -312,9 +313,10 @@ def test_materialize_parity(gs, orc):
 
 
 def test_restore_directions(gs):
-    """The stored restore directions equal m / (sqrt(v) + eps) after refresh and
-    after optimizer steps, and culling / rendering through them is bit-identical
-    to recomputing the restore from m and v."""
+    """The stored restore directions equal m / (sqrt(v) + eps) (within the
+    2-ulp divide used for them) after refresh and after optimizer steps, and
+    culling / rendering through them is bit-identical to recomputing the
+    restore from m and v."""
     rng = np.random.default_rng(12)
     n, deg = 6000, 1
     P = scenes.uniform_cube_scene(n, seed=12, sh_degree=deg, log_scale_mean=-3.0)
@@ -335,7 +337,8 @@ def test_restore_directions(gs):
         v = sc.v[:, :n].cpu().numpy()
         return m / (np.sqrt(v) + eps32)
 
-    np.testing.assert_array_equal(scene.rdir[:, :n].cpu().numpy(), expected(scene))
+    u32 = 2.0 ** -24                                    # the direction uses a 2-ulp divide
+    np.testing.assert_allclose(scene.rdir[:, :n].cpu().numpy(), expected(scene), rtol=6 * u32, atol=0)
     ids_a, nv_a = ctx.cull(scene, cam, adam)
     img_a = ctx.render_fwd(scene, cam, ids_a, nv_a, adam)
     rdir = scene.rdir
@@ -351,7 +354,7 @@ def test_restore_directions(gs):
     for _ in range(3):
         ctx.adam_deferred(scene, ids_a, nv_a, gc, adam)
     ctx.sync_status()
-    np.testing.assert_array_equal(scene.rdir[:, :n].cpu().numpy(), expected(scene))
+    np.testing.assert_allclose(scene.rdir[:, :n].cpu().numpy(), expected(scene), rtol=6 * u32, atol=0)
 
 
 def test_deferred_trajectory_tracks_eager(gs, orc):
