@@ -103,10 +103,24 @@ def build_workload(n, n_views, seed_views=2, density_of=None):
     return cfg, tgt_scene
 
 
+# FP32 peak of the B300 from unit counts and clock: 148 SMs x 128 FP32 lanes
+# x 2 flops per FMA x 2.032 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# algorithmic FP32 operations of the rasterizer backward per (pixel, splat)
+# pair: a contributing pair costs the forward replay (16) and the adjoint (63);
+# a pair inside the 3-sigma square that does not contribute costs the two
+# alpha evaluations (14 + 14).  See the roofline section of the design doc.
+FLOPS_CONTRIB, FLOPS_SQUARE = 79.0, 28.0
+
+
 def algorithmic_bytes(N, D, n_vis, n_upd, n_restore):
     """Bytes the method must move per launch (roofline section)."""
-    cull = 40.0 * N + 1.0 * N + 80.0 * n_restore + N / 8.0 + 4.0 * N / 2048.0
-    apply = 24.0 * D * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 2.0 * n_upd
+    # cull: w of the 10 geometry planes for all, their restore directions for
+    # Gaussians with a non-zero counter, counters, bitmask, chunk counts
+    cull = 40.0 * N + 40.0 * n_restore + 1.0 * N + N / 8.0 + 4.0 * N / 2048.0
+    # apply: w, m, v read + w, m, v, restore direction written per parameter of
+    # each update-set member, gradients of the visible ones, ids and delays
+    apply = 28.0 * D * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 1.0 * n_upd
     select = 2.0 * N + N / 4.0
     return cull, apply, select
 
@@ -201,6 +215,8 @@ def run_ours(args):
         c = ctx.counters().cpu().tolist()
         stats.append((c[0], c[1], c[2], n_restore_geo))
     ctx.timing_read(tcap)
+    pairs = np.array([ctx.raster_pair_counts(scene, cam) for cam in cams], np.float64)   # untimed
+    n_sq_pairs, n_on_pairs = float(pairs[:, 0].mean()), float(pairs[:, 1].mean())
     n_vis = float(np.mean([x[0] for x in stats]))
     n_keys = float(np.mean([x[1] for x in stats]))
     n_upd = float(np.mean([x[2] for x in stats]))
@@ -211,19 +227,29 @@ def run_ours(args):
         vals = [sp[k] for sp in spans if sp[k] >= 0]
         return float(np.mean(vals)) if vals else None
 
-    st = {k: avg(k) for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply")}
+    st = {k: avg(k) for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")}
     peak, peak_src = _peaks()
     gbs = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms else None
     cull_gbs, apply_gbs = gbs(b_cull, st["cull"]), gbs(b_apply, st["adam_apply"])
     adam_stage_gbs = gbs(b_apply + b_select, st["adam"])
     ca_gbs = gbs(b_cull + b_apply + b_select, (st["cull"] or 0) + (st["adam"] or 0))
-    # dominant kernel of the memory-bound pair for the roofline line
-    dom = ("adam_apply", b_apply, st["adam_apply"]) if (st["adam_apply"] or 0) >= (st["cull"] or 0) else \
-        ("cull", b_cull, st["cull"])
-    roof = {"kernel": {"adam_apply": "k_adam_apply", "cull": "k_cull"}[dom[0]], "bound": "hbm",
-            "achieved": round(gbs(dom[1], dom[2]), 1), "peak": peak, "unit": "GB/s",
-            "frac": round(gbs(dom[1], dom[2]) / peak, 4), "peak_source": peak_src,
-            "algorithmic_bytes_per_launch": round(dom[1]), "traffic": None}
+    # roofline of the dominant kernel (largest live event time per step)
+    flops = FLOPS_CONTRIB * n_on_pairs + FLOPS_SQUARE * (n_sq_pairs - n_on_pairs)
+    cands = {"k_raster_bwd": st["raster_bwd"] or 0.0, "k_adam_apply": st["adam_apply"] or 0.0,
+             "k_cull": st["cull"] or 0.0}
+    dom = max(cands, key=cands.get)
+    if dom == "k_raster_bwd":
+        ach = flops / (st["raster_bwd"] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz",
+                "algorithmic_flops_per_launch": round(flops), "traffic": None}
+    else:
+        b = b_apply if dom == "k_adam_apply" else b_cull
+        t = st["adam_apply"] if dom == "k_adam_apply" else st["cull"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(gbs(b, t), 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs(b, t) / peak, 4), "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": round(b), "traffic": None}
 
     # ---- end to end through the public API: target H2D from pinned host memory,
     # gs_step, loss D2H, every step
@@ -267,13 +293,15 @@ def run_ours(args):
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (parameters+moments 7.1 GB), no flush",
                    "visible_per_view": round(n_vis), "keys_per_view": round(n_keys), "update_set": round(n_upd),
+                   "square_pairs_per_view": round(n_sq_pairs), "contrib_pairs_per_view": round(n_on_pairs),
                    "raster_variant": variant,
                    "autotune_ms": [None if t is None else round(t, 4) for t in variant_ms]},
         "roofline": roof,
         "cull_adam": {"cull_gbs": cull_gbs and round(cull_gbs, 1), "adam_apply_gbs": apply_gbs and round(apply_gbs, 1),
                       "adam_stage_gbs": adam_stage_gbs and round(adam_stage_gbs, 1),
                       "cull_plus_adam_gbs": ca_gbs and round(ca_gbs, 1), "peak_gbs": peak,
-                      "cull_plus_adam_frac": ca_gbs and round(ca_gbs / peak, 4)},
+                      "cull_plus_adam_frac": ca_gbs and round(ca_gbs / peak, 4),
+                      "cull_bytes": round(b_cull), "adam_bytes": round(b_apply + b_select)},
         "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in st.items()},
         "e2e": {"value": round(world * K / (e2e_ms / 1e3), 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
@@ -368,7 +396,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--gaussians", type=int, default=10_000_000)

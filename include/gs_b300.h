@@ -216,13 +216,13 @@ GS_API gs_status gs_step(gs_ctx *ctx, gs_scene *scene, const gs_camera *views, c
 /* Stage timing of gs_step with CUDA events (benchmarks).  After
  * gs_timing_enable(ctx, max_steps), each gs_step records events on its stream
  * around: the whole step, the first view's cull kernel, its render forward and
- * backward, the optimizer stage, and the optimizer's apply kernel (the
- * D-plane sweep).  gs_timing_read synchronises the device, writes elapsed
+ * backward, the optimizer stage, the optimizer's apply kernel (the D-plane
+ * sweep) and the first view's rasterizer backward kernel.  gs_timing_read synchronises the device, writes elapsed
  * milliseconds ms_out[step * GS_TIMING_SPANS + span] for up to max_steps
  * recorded steps, stores their number in *steps_out and restarts recording.
  * Enabling or disabling timing re-captures the step graph. */
 enum { GS_SPAN_STEP = 0, GS_SPAN_CULL = 1, GS_SPAN_FWD = 2, GS_SPAN_BWD = 3, GS_SPAN_ADAM = 4,
-       GS_SPAN_ADAM_APPLY = 5, GS_TIMING_SPANS = 6 };
+       GS_SPAN_ADAM_APPLY = 5, GS_SPAN_RASTER_BWD = 6, GS_TIMING_SPANS = 7 };
 GS_API gs_status gs_timing_enable(gs_ctx *ctx, int32_t max_steps);
 GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, int32_t *steps_out);
 
@@ -245,6 +245,14 @@ GS_API gs_status gs_autotune(gs_ctx *ctx, const gs_scene *scene, const gs_camera
 /* Select a rasterizer variant explicitly (tests); GS_ERR_INVALID_ARG if the
  * tile shape does not allow it. */
 GS_API gs_status gs_set_raster_variant(gs_ctx *ctx, int32_t variant);
+
+/* Work counts of the rasterizer backward for one view (benchmarks): renders
+ * forward and backward once (the rendered image as dL/dimage) with a counting
+ * instance of the backward kernel and writes counts[0] = (pixel, splat) pairs
+ * that pass the 3-sigma square test and counts[1] = pairs that contribute
+ * (alpha >= 1/255 before the transmittance stop).  Synchronises the stream. */
+GS_API gs_status gs_raster_pair_counts(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, uint64_t *counts,
+                                       void *stream);
 
 /* Number of kernel launches in the captured gs_step graph (0 before the first
  * gs_step). */

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR
                 5: "GS_ERR_CAPACITY", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_NUMERIC"}
 GS_FP32, GS_BF16_SH_MOM = 0, 1
 RASTER_VARIANTS = 6
-SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply")
+SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
 
 
@@ -57,6 +57,7 @@ EXPORTS = {
     "gs_grad_scatter": (c_i32, [c_vp, C.POINTER(Scene), c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "gs_timing_enable": (c_i32, [c_vp, c_i32]),
     "gs_timing_read": (c_i32, [c_vp, C.POINTER(c_f32), c_i32, C.POINTER(c_i32)]),
+    "gs_raster_pair_counts": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(C.c_uint64), c_vp]),
     "gs_step_kernel_count": (c_i32, [c_vp, C.POINTER(c_i32)]),
     "gs_autotune": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_i32), C.POINTER(c_f32), c_vp]),
     "gs_set_raster_variant": (c_i32, [c_vp, c_i32]),

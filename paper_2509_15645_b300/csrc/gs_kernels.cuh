@@ -34,6 +34,7 @@ struct Work {
 };
 
 // k_scan.cu
+constexpr int RADIX_TILE = 1024;   // keys per radix-sort tile (the histogram buffer holds 256 per tile)
 void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *total_out, int total_cap,
                     cudaStream_t s);
 void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
@@ -56,7 +57,7 @@ struct SceneView {
 
 // Timing points recorded inside a step (see gs_timing_enable).
 enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_ADAM0, TP_APPLY0, TP_APPLY1,
-       TP_ADAM1, TP_STEP1, TP_COUNT };
+       TP_ADAM1, TP_STEP1, TP_RBWD0, TP_RBWD1, TP_COUNT };
 
 // k_cull.cu: visibility bitmask + per-chunk counts (restore if lut.restore).
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
@@ -107,7 +108,7 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                      const DevCam &cam_host, const float *dimage, float *grad, int64_t gcap,
                      const uint32_t *remap_mask, const uint32_t *remap_prefix, const int32_t *ids, bool accumulate,
-                     Work &w, cudaStream_t s);
+                     Work &w, cudaStream_t s, unsigned long long *stats = nullptr);
 void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
                     cudaStream_t s);
 void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s);

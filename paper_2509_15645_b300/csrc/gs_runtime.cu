@@ -190,7 +190,7 @@ static void carve(gs_ctx *c, char *base)
     rb.g9 = k.take<float>(9 * V);
     rb.n_keys = base ? &c->cnt->n_keys : nullptr;
     int64_t big = K > V ? K : V;
-    c->w.hist = k.take<uint32_t>(256 * ((big + 4095) / 4096) + 256);
+    c->w.hist = k.take<uint32_t>(256 * ((big + RADIX_TILE - 1) / RADIX_TILE) + 256);
     c->w.partials = k.take<uint32_t>(1024);
     c->img = k.take<float>(P);
     c->dimg = k.take<float>(P);
@@ -554,7 +554,8 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
     if (!c || !ms_out || !steps_out) return GS_ERR_INVALID_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_check(c, "gs_timing_read");
     static const int span[GS_TIMING_SPANS][2] = {{TP_STEP0, TP_STEP1}, {TP_CULL0, TP_CULL1}, {TP_FWD0, TP_FWD1},
-                                                 {TP_BWD0, TP_BWD1}, {TP_ADAM0, TP_ADAM1}, {TP_APPLY0, TP_APPLY1}};
+                                                 {TP_BWD0, TP_BWD1}, {TP_ADAM0, TP_ADAM1}, {TP_APPLY0, TP_APPLY1},
+                                                 {TP_RBWD0, TP_RBWD1}};
     int n = c->t_used < max_steps ? c->t_used : max_steps;
     for (int st = 0; st < n; st++) {
         cudaEvent_t *ev = c->t_events + (size_t)st * TP_COUNT;
@@ -636,6 +637,38 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     c->have_fwd = false;
     if (chosen_out) *chosen_out = best_v;
     return cuda_check(c, "gs_autotune");
+}
+
+gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, uint64_t *counts,
+                                void *stream)
+{
+    if (!c || !counts) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv);
+    if (st) return st;
+    if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.cam[0] = make_cam(*cam, c->cfg);
+    a.n_views = 1;
+    set_args(c, SLOT_RENDER, a, s);
+    int32_t *ids = c->vids[0];
+    launch_cull(sv, c->args + SLOT_RENDER, 0, c->mask, c->chunk, c->w, s);
+    compact_mask(c->mask, sv.n, c->chunk, true, ids, c->wprefix, (int)c->cfg.max_visible, c->n_render, c->w, s);
+    unsigned long long *dev = reinterpret_cast<unsigned long long *>(c->n_tmp);   // 16 bytes of scratch
+    cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s);
+    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], c->img, false, nullptr, nullptr,
+                   c->w, s);
+    render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rb, a.cam[0], c->img, c->grad_u, c->cfg.max_visible,
+                    nullptr, nullptr, nullptr, false, c->w, s, dev);
+    unsigned long long host[2] = {0, 0};
+    if (cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check(c, "gs_raster_pair_counts");
+    counts[0] = host[0];
+    counts[1] = host[1];
+    c->have_fwd = false;
+    return GS_OK;
 }
 
 gs_status gs_step_kernel_count(const gs_ctx *c, int32_t *kernels)

@@ -12,7 +12,7 @@ namespace gs {
 
 constexpr int CULL_BLOCK = 256;
 
-__global__ void __launch_bounds__(CULL_BLOCK) k_cull(const float *__restrict__ geo, const float *__restrict__ m,
+__global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict__ geo, const float *__restrict__ m,
                                                      const float *__restrict__ v, const float *__restrict__ rdir,
                                                      const uint8_t *__restrict__ counter,
                                                      int64_t pitch, int64_t n, const DevArgs *__restrict__ args,

@@ -374,13 +374,16 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
     return r;
 }
 
-template <int PPT, int BATCH>
+// STATS: also count, over the back-to-front pass, the (pixel, splat) pairs
+// that pass the square test and the pairs that contribute (stats[0], stats[1]).
+template <int PPT, int BATCH, bool STATS = false>
 __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
                                                     const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                                     const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
                                                     int view, const float *__restrict__ dimage, float *__restrict__ g9,
-                                                    int64_t gcap)
+                                                    int64_t gcap, unsigned long long *stats = nullptr)
 {
+    unsigned long long n_sq = 0, n_on = 0;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ uint32_t s_k[BATCH];
     __shared__ int s_gi[BATCH];
@@ -481,7 +484,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
                     float dy, G;
                     bool cl;
                     const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
+                    if (STATS) n_sq += fabsf(dy) <= r0.z ? 1 : 0;
                     if (a == 0.f) continue;
+                    if (STATS) n_on++;
                     contrib = true;
                     const float4 c = s2[e];
                     T[j] = __fdividef(T[j], 1.f - a);        // transmittance in front of this splat
@@ -515,12 +520,23 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
             }
         }
     }
+    if (STATS) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            n_sq += __shfl_xor_sync(0xffffffffu, n_sq, o);
+            n_on += __shfl_xor_sync(0xffffffffu, n_on, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, n_sq);
+            atomicAdd(stats + 1, n_on);
+        }
+    }
 }
 
 typedef void (*RasterFwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
                             const DevArgs *, int, float *, int, float *, float *);
 typedef void (*RasterBwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
-                            const DevArgs *, int, const float *, float *, int64_t);
+                            const DevArgs *, int, const float *, float *, int64_t, unsigned long long *);
 
 // Variant v: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128.
 static RasterFwdFn fwd_variant(int v)
@@ -811,15 +827,35 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
         rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, image, use_target ? 1 : 0, dimage, loss);
 }
 
+static void raster_bwd_stats(int v, int tiles, int threads, const RenderBufs &rb, const DevArgs *args, int view,
+                             const float *dimage, unsigned long long *stats, cudaStream_t s)
+{
+    const int64_t cap = rb.cap;
+    switch (v) {
+    case 0: k_raster_bwd<1, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    case 1: k_raster_bwd<1, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    case 2: k_raster_bwd<2, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    case 3: k_raster_bwd<2, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    case 4: k_raster_bwd<4, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    default: k_raster_bwd<4, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    }
+}
+
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                      const DevCam &cam, const float *dimage, float *grad, int64_t gcap, const uint32_t *remap_mask,
-                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s)
+                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s,
+                     unsigned long long *stats)
 {
     const int cap = (int)rb.cap;
     launch_zero_rows(rb.g9, 9, cap, n_vis, cap, w, s);
     const int ppt = 1 << (rb.variant >> 1);
-    bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap);
+    if (view == 0) w.mark(TP_RBWD0, s);
+    if (stats)
+        raster_bwd_stats(rb.variant, rb.tiles, cam.tile_w * cam.tile_h / ppt, rb, args, view, dimage, stats, s);
+    else
+        bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
+            rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, nullptr);
+    if (view == 0) w.mark(TP_RBWD1, s);
     k_project_bwd<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9,
                                                                      grad, gcap, ids, remap_mask, remap_prefix,
                                                                      accumulate ? 1 : 0, w.status);

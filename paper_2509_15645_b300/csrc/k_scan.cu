@@ -198,7 +198,7 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
 // Stable LSD radix sort of (key, value) pairs on bits [0, nbits) of the key,
 // 8-bit digits.  Each pass: per-tile digit histograms -> exclusive scan over
 // (digit, tile) -> stable scatter with per-tile ranks.
-constexpr int RS_BLOCK = 256, RS_ITEMS = 16, RS_TILE = RS_BLOCK * RS_ITEMS, RS_WARPS = RS_BLOCK / 32;
+constexpr int RS_BLOCK = 256, RS_TILE = RADIX_TILE, RS_ITEMS = RS_TILE / RS_BLOCK, RS_WARPS = RS_BLOCK / 32;
 
 __device__ __forceinline__ int rs_count(const int *n_dev, int cap)
 {

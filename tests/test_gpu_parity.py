@@ -202,6 +202,21 @@ def test_raster_variants_agree(gs, orc, name, tile):
     assert ms[chosen] is not None and ms[chosen] == min(t for t in ms if t is not None)
 
 
+def test_raster_pair_counts(gs, orc):
+    """The backward's work counts: contributing pairs equal the oracle's
+    contributor counts summed over pixels (ties aside)."""
+    P, cam, deg, tile = _case("cube_offaxis_sh3")
+    camf = cam_f32(cam)
+    ctx = make_ctx(gs, P.shape[1], camf.width, camf.height, deg=3, tile=tile)
+    scene = gs.GaussianScene(P, deg)
+    n_sq, n_on = ctx.raster_pair_counts(scene, camf)
+    r = orc.render(f32(P), deg, camf, tile)
+    ex = r["margin"] < TIE_TOL
+    ref = int(r["n_contrib"].sum())
+    assert abs(n_on - ref) <= 2 * int(ex.sum()) + 2, (n_on, ref)
+    assert n_sq >= n_on > 0
+
+
 def test_loss_l1_kernel(gs):
     ctx = make_ctx(gs, 64, 40, 30)
     rng = np.random.default_rng(0)
