@@ -109,18 +109,23 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # algorithmic FP32 operations of the rasterizer backward per (pixel, splat)
 # pair: a contributing pair costs the forward replay (16) and the adjoint (63);
 # a pair inside the 3-sigma square that does not contribute costs the two
-# alpha evaluations (14 + 14).  See the roofline section of the design doc.
+# alpha evaluations (14 + 14).
 FLOPS_CONTRIB, FLOPS_SQUARE = 79.0, 28.0
 
 
-def algorithmic_bytes(N, D, n_vis, n_upd, n_restore):
-    """Bytes the method must move per launch (roofline section)."""
+def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False):
+    """Bytes the method must move per launch: the cull, the optimizer's apply
+    sweep and its select pass (the minimum traffic of each, every byte read or
+    written once)."""
     # cull: w of the 10 geometry planes for all, their restore directions for
     # Gaussians with a non-zero counter, counters, bitmask, chunk counts
     cull = 40.0 * N + 40.0 * n_restore + 1.0 * N + N / 8.0 + 4.0 * N / 2048.0
     # apply: w, m, v read + w, m, v, restore direction written per parameter of
-    # each update-set member, gradients of the visible ones, ids and delays
-    apply = 28.0 * D * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 1.0 * n_upd
+    # each update-set member, gradients of the visible ones, ids and delays.
+    # bf16 forms: the 11 geometry planes keep fp32 w and restore directions
+    # with bf16 m, v (20 B); SH planes hold bf16 w, m, v and direction (14 B)
+    per_member = (20.0 * 11 + 14.0 * (D - 11)) if bf16 else 28.0 * D
+    apply = per_member * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 1.0 * n_upd
     select = 2.0 * N + N / 4.0
     return cull, apply, select
 
@@ -158,155 +163,187 @@ def run_ours(args):
         targets.append(ctx.render_fwd(tscene, cam, ids, nv).clone())
     ctx.sync_status()
     del tscene
-    scene = gs.GaussianScene(cfg["scene"], deg, device=dev)
-    del cfg["scene"]
+    P0 = cfg.pop("scene")
     torch.cuda.empty_cache()
-    variant, variant_ms = ctx.autotune(scene, cams[0])     # rasterizer variant for this workload (untimed)
-    if args.raster_variant is not None:
-        ctx.set_raster_variant(args.raster_variant)
-        variant = args.raster_variant
-    adam = gs.adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15)
+    adam = gs.adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, seed=1)
     loss = torch.zeros(1, device=dev)
     stream = torch.cuda.current_stream()
-
     K, Wm = args.steps, args.warmup
     tcap = max(Wm + K, 16) + 8
-    ctx.timing_enable(tcap)
-    for s in range(Wm):
-        v = s % len(cams)
-        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
-    ctx.sync_status()
-    ctx.timing_read(tcap)            # discard warm-up timings
-
-    # ---- timed region: inputs resident in HBM (params 2.4 GB > L2: no flush needed)
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
-    e0.record(stream)
-    for s in range(K):
-        v = (Wm + s) % len(cams)
-        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
-    e1.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms_total = e0.elapsed_time(e1)
-    spans = ctx.timing_read(tcap)
-    ctx.sync_status()
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * K / (ms_total / 1e3)
-    kernels = ctx.step_kernel_count()
-
-    # ---- counts per view (untimed pass over the same views) for the algorithmic bytes
-    stats = []
-    for s in range(len(cams)):
-        v = (Wm + K + s) % len(cams)
-        n_restore_geo = int((scene.counter[:N] > 0).sum().item())
-        ctx.step(scene, [cams[v]], [targets[v]], adam, loss=loss)
-        c = ctx.counters().cpu().tolist()
-        stats.append((c[0], c[1], c[2], n_restore_geo))
-    ctx.timing_read(tcap)
-    pairs = np.array([ctx.raster_pair_counts(scene, cam) for cam in cams], np.float64)   # untimed
-    n_sq_pairs, n_on_pairs = float(pairs[:, 0].mean()), float(pairs[:, 1].mean())
-    n_vis = float(np.mean([x[0] for x in stats]))
-    n_keys = float(np.mean([x[1] for x in stats]))
-    n_upd = float(np.mean([x[2] for x in stats]))
-    n_rest = float(np.mean([x[3] for x in stats]))
-    b_cull, b_apply, b_select = algorithmic_bytes(N, D, n_vis, n_upd, n_rest)
-
-    def avg(k):
-        vals = [sp[k] for sp in spans if sp[k] >= 0]
-        return float(np.mean(vals)) if vals else None
-
-    st = {k: avg(k) for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")}
     peak, peak_src = _peaks()
     gbs = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms else None
-    cull_gbs, apply_gbs = gbs(b_cull, st["cull"]), gbs(b_apply, st["adam_apply"])
-    adam_stage_gbs = gbs(b_apply + b_select, st["adam"])
-    ca_gbs = gbs(b_cull + b_apply + b_select, (st["cull"] or 0) + (st["adam"] or 0))
-    # roofline of the dominant kernel (largest live event time per step)
-    flops = FLOPS_CONTRIB * n_on_pairs + FLOPS_SQUARE * (n_sq_pairs - n_on_pairs)
-    cands = {"k_raster_bwd": st["raster_bwd"] or 0.0, "k_adam_apply": st["adam_apply"] or 0.0,
-             "k_cull": st["cull"] or 0.0}
-    dom = max(cands, key=cands.get)
-    if dom == "k_raster_bwd":
-        ach = flops / (st["raster_bwd"] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz",
-                "algorithmic_flops_per_launch": round(flops), "traffic": None}
-    else:
-        b = b_apply if dom == "k_adam_apply" else b_cull
+
+    def timed_steps(sc):
+        """W warm-up steps, then K steps between CUDA events on the launching
+        stream (barrier + synchronize on both sides), clocks sampled meanwhile.
+        Returns (ms over the K steps, max over ranks; per-step stage spans; clocks)."""
+        ctx.timing_enable(tcap)
+        for s in range(Wm):
+            v = s % len(cams)
+            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+        ctx.sync_status()
+        ctx.timing_read(tcap)            # discard warm-up timings
+        clocks = ClockSampler(local)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(stream)
+        for s in range(K):
+            v = (Wm + s) % len(cams)
+            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        sp = ctx.timing_read(tcap)
+        ctx.sync_status()
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, sp, clk
+
+    def measure(precision):
+        """Autotune, time K steps of one precision form, then an untimed pass
+        over the views for the counts behind the algorithmic bytes and flops."""
+        sc = gs.GaussianScene(P0, deg, device=dev, precision=precision)
+        variant, variant_ms = ctx.autotune(sc, cams[0])     # rasterizer variant for this workload (untimed)
+        if args.raster_variant is not None:
+            ctx.set_raster_variant(args.raster_variant)
+            variant = args.raster_variant
+        ms_total, spans, clk = timed_steps(sc)
+        stats = []
+        ctx.timing_enable(tcap)
+        for s in range(len(cams)):
+            v = (Wm + K + s) % len(cams)
+            n_restore_geo = int((sc.counter[:N] > 0).sum().item())
+            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+            c = ctx.counters().cpu().tolist()
+            stats.append((c[0], c[1], c[2], n_restore_geo, c[6]))
+        ctx.timing_read(tcap)
+        pairs = np.array([ctx.raster_pair_counts(sc, cam) for cam in cams], np.float64)   # untimed
+        st = {}
+        for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd"):
+            vals = [x[k] for x in spans if x[k] >= 0]
+            st[k] = float(np.mean(vals)) if vals else None
+        m = {"sc": sc, "ms": ms_total, "clk": clk, "st": st, "variant": variant, "variant_ms": variant_ms,
+             "n_vis": float(np.mean([x[0] for x in stats])), "n_keys": float(np.mean([x[1] for x in stats])),
+             "n_upd": float(np.mean([x[2] for x in stats])), "n_rest": float(np.mean([x[3] for x in stats])),
+             "n_fp64": float(np.mean([x[4] for x in stats])),
+             "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
+             "kernels": ctx.step_kernel_count()}
+        b_cull, b_apply, b_select = algorithmic_bytes(N, D, m["n_vis"], m["n_upd"], m["n_rest"],
+                                                      bf16=precision != gs.GS_FP32)
+        m.update(b_cull=b_cull, b_apply=b_apply, b_select=b_select)
+        m["cull_adam"] = {
+            "cull_gbs": gbs(b_cull, st["cull"]), "adam_apply_gbs": gbs(b_apply, st["adam_apply"]),
+            "adam_stage_gbs": gbs(b_apply + b_select, st["adam"]),
+            "cull_plus_adam_gbs": gbs(b_cull + b_apply + b_select, (st["cull"] or 0) + (st["adam"] or 0)),
+            "peak_gbs": peak, "cull_bytes": round(b_cull), "adam_bytes": round(b_apply + b_select)}
+        ca = m["cull_adam"]
+        ca["cull_plus_adam_frac"] = ca["cull_plus_adam_gbs"] and ca["cull_plus_adam_gbs"] / peak
+        for k in list(ca):
+            if isinstance(ca[k], float):
+                ca[k] = round(ca[k], 4 if k.endswith("frac") else 1)
+        return m
+
+    def roofline(m):
+        """Roofline entry of the kernel with the largest live event time per step."""
+        st = m["st"]
+        flops = FLOPS_CONTRIB * m["on_pairs"] + FLOPS_SQUARE * (m["sq_pairs"] - m["on_pairs"])
+        cands = {"k_raster_bwd": st["raster_bwd"] or 0.0, "k_adam_apply": st["adam_apply"] or 0.0,
+                 "k_cull": st["cull"] or 0.0}
+        dom = max(cands, key=cands.get)
+        if dom == "k_raster_bwd":
+            ach = flops / (st["raster_bwd"] * 1e-3) / 1e12
+            return {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz",
+                    "algorithmic_flops_per_launch": round(flops), "traffic": None}
+        b = m["b_apply"] if dom == "k_adam_apply" else m["b_cull"]
         t = st["adam_apply"] if dom == "k_adam_apply" else st["cull"]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(gbs(b, t), 1), "peak": peak, "unit": "GB/s",
+        return {"kernel": dom, "bound": "hbm", "achieved": round(gbs(b, t), 1), "peak": peak, "unit": "GB/s",
                 "frac": round(gbs(b, t) / peak, 4), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": round(b), "traffic": None}
 
-    # ---- end to end through the public API: target H2D from pinned host memory,
-    # gs_step, loss D2H, every step
-    host_t = [t.cpu().pin_memory() for t in targets]
-    dev_t = torch.empty_like(targets[0])
-    host_loss = torch.zeros(1).pin_memory()
-    for s in range(2):
-        dev_t.copy_(host_t[s % len(cams)], non_blocking=True)
-        ctx.step(scene, [cams[s % len(cams)]], [dev_t], adam, loss=loss)
-        host_loss.copy_(loss, non_blocking=True)
-    torch.cuda.synchronize()
-    ctx.timing_read(tcap)
-    ctx.timing_enable(0)
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.step(scene, [cams[0]], [dev_t], adam, loss=loss)        # re-capture without timing nodes
-    torch.cuda.synchronize()
-    f0.record(stream)
-    for s in range(K):
-        v = s % len(cams)
-        dev_t.copy_(host_t[v], non_blocking=True)
-        ctx.step(scene, [cams[v]], [dev_t], adam, loss=loss)
-        host_loss.copy_(loss, non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    ctx.sync_status()
+    def e2e(sc):
+        """Steps/s through the public API with the step's target copied from
+        pinned host memory and the loss read back, every step."""
+        host_t = [t.cpu().pin_memory() for t in targets]
+        dev_t = torch.empty_like(targets[0])
+        host_loss = torch.zeros(1).pin_memory()
+        ctx.timing_enable(0)
+        for s in range(max(Wm, 3)):
+            dev_t.copy_(host_t[s % len(cams)], non_blocking=True)
+            ctx.step(sc, [cams[s % len(cams)]], [dev_t], adam, loss=loss)
+            host_loss.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for s in range(K):
+            v = s % len(cams)
+            dev_t.copy_(host_t[v], non_blocking=True)
+            ctx.step(sc, [cams[v]], [dev_t], adam, loss=loss)
+            host_loss.copy_(loss, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms = f0.elapsed_time(f1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        ctx.sync_status()
+        return {"value": round(world * K / (ms / 1e3), 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4}
+
+    main_prec = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
+    m = measure(main_prec)
+    e2e_main = e2e(m["sc"])
+    bf16 = None
+    if not args.bf16_only and not args.no_bf16:
+        # the precision form: bf16 SH coefficients and moments, fp32 geometry
+        # (same initial parameters, views and targets; its own warm-up and timed steps)
+        del m["sc"]
+        torch.cuda.empty_cache()
+        mb = measure(gs.GS_BF16_SH_MOM)
+        del mb["sc"]
+        bf16 = {"form": "bf16_sh_mom (bf16 SH and moments, stochastic rounding; fp32 geometry and compositing)",
+                "value": round(world * K / (mb["ms"] / 1e3), 4), "unit": UNIT, "ms_per_step": round(mb["ms"] / K, 4),
+                "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in mb["st"].items()},
+                "cull_adam": mb["cull_adam"], "roofline": roofline(mb), "clocks": mb["clk"],
+                "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 * 2 + D * 2 * 2 + 1}
     if args.density_of:
         cfg_note = f"aerial{N / 1e6:g}m_at_density_of_{args.density_of / 1e6:g}m_1080p_sh3"
     else:
         cfg_note = WORKLOAD
+    K_ms = m["ms"]
     out = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
-        "ms_per_step": round(ms_total / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
+        "metric": METRIC, "value": round(world * K / (K_ms / 1e3), 4), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": round(K_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
         "config": {"workload": cfg_note, "gaussians": N, "image": f"{W}x{H}", "sh_degree": deg,
-                   "views_per_step": 1, "form": "plain_fp32", "adam": "deferred", "tile": args.tile,
+                   "views_per_step": 1, "form": "bf16_sh_mom" if args.bf16_only else "plain_fp32",
+                   "adam": "deferred", "tile": args.tile,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (parameters+moments 7.1 GB), no flush",
-                   "visible_per_view": round(n_vis), "keys_per_view": round(n_keys), "update_set": round(n_upd),
-                   "square_pairs_per_view": round(n_sq_pairs), "contrib_pairs_per_view": round(n_on_pairs),
-                   "raster_variant": variant,
-                   "autotune_ms": [None if t is None else round(t, 4) for t in variant_ms]},
-        "roofline": roof,
-        "cull_adam": {"cull_gbs": cull_gbs and round(cull_gbs, 1), "adam_apply_gbs": apply_gbs and round(apply_gbs, 1),
-                      "adam_stage_gbs": adam_stage_gbs and round(adam_stage_gbs, 1),
-                      "cull_plus_adam_gbs": ca_gbs and round(ca_gbs, 1), "peak_gbs": peak,
-                      "cull_plus_adam_frac": ca_gbs and round(ca_gbs / peak, 4),
-                      "cull_bytes": round(b_cull), "adam_bytes": round(b_apply + b_select)},
-        "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in st.items()},
-        "e2e": {"value": round(world * K / (e2e_ms / 1e3), 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
-        "clocks": clk,
-        "gpu_launches": int(kernels * K),
+                   "visible_per_view": round(m["n_vis"]), "keys_per_view": round(m["n_keys"]),
+                   "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
+                   "square_pairs_per_view": round(m["sq_pairs"]), "contrib_pairs_per_view": round(m["on_pairs"]),
+                   "raster_variant": m["variant"],
+                   "autotune_ms": [None if t is None else round(t, 4) for t in m["variant_ms"]]},
+        "roofline": roofline(m),
+        "cull_adam": m["cull_adam"],
+        "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in m["st"].items()},
+        "e2e": e2e_main,
+        "clocks": m["clk"],
+        "gpu_launches": int(m["kernels"] * K),
+        "bf16_form": bf16,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, sample_frac=0.1)
@@ -402,6 +439,9 @@ def main():
     ap.add_argument("--gaussians", type=int, default=10_000_000)
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the bf16 precision-form measurement")
+    ap.add_argument("--bf16-only", action="store_true",
+                    help="time only the bf16 precision form (profiling); the JSON line then describes it")
     ap.add_argument("--density-of", type=int, default=None,
                     help="scale the scene area so that --gaussians keeps the density of this many (profiling cases)")
     ap.add_argument("--tile", default="8x8", help="raster tile WxH (W in 4..64, W*H in 64, 128, 256)")

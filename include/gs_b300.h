@@ -61,8 +61,13 @@ typedef enum {
     GS_ERR_NUMERIC = 7     /* non-finite loss */
 } gs_status;
 
-/* Storage precision of SH planes and of the moments m, v. */
-enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1 };
+/* Storage precision of SH planes and of the moments m, v.  The BF16 forms keep
+ * the 11 geometry/opacity planes in fp32 (the "master" copy), store SH planes
+ * and all moments in bf16, and compute everything in fp32.  GS_BF16_SH_MOM
+ * rounds every bf16 store stochastically (deterministic counter-based hash of
+ * seed, step, plane, index), which keeps small Adam updates and the 0.999
+ * decay of v from being rounded away; GS_BF16_SH_MOM_RN rounds to nearest. */
+enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
 
 /* Adam variants: deferred with the restore tables of Fig. 10 (the method) or
  * eager (Eq. 1 on every Gaussian each step: the baseline the paper improves). */
@@ -86,15 +91,17 @@ typedef struct {
     int64_t n;             /* number of Gaussians (< 2^31) */
     int64_t pitch;         /* elements between planes, >= n, multiple of 4 */
     int32_t sh_degree;     /* 0..3 */
-    int32_t precision;     /* GS_FP32 or GS_BF16_SH_MOM (sh, m, v stored as bf16) */
+    int32_t precision;     /* GS_FP32, GS_BF16_SH_MOM or GS_BF16_SH_MOM_RN (sh, m, v stored as bf16) */
     float *geo;            /* [11][pitch] fp32 */
     void *sh;              /* [3 (L+1)^2][pitch] fp32 or bf16 */
     void *m;               /* [D][pitch] fp32 or bf16, NULL = no optimizer state (render only) */
     void *v;               /* [D][pitch] */
-    float *rdir;           /* [D][pitch] fp32 restore direction m / (sqrt(v) + eps) of each parameter, kept
-                              by the optimizer so a deferred restore is one multiply-add; must equal that
-                              expression (all zero when m = v = 0; see gs_refresh_rdir).  NULL: the
-                              kernels recompute it from m and v */
+    float *rdir;           /* restore direction m / (sqrt(v) + eps) of each parameter, kept by the optimizer
+                              so a deferred restore is one multiply-add: [11][pitch] fp32 for the geometry
+                              planes followed by [D-11][pitch] of the SH storage type (so [D][pitch] fp32 in
+                              GS_FP32; 44 + 2 (D-11) bytes per pitch element in the BF16 forms).  Must equal
+                              that expression, rounded to the plane's type (all zero when m = v = 0; see
+                              gs_refresh_rdir).  NULL: the kernels recompute it from m and v */
     uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
     int32_t step;          /* optimizer steps completed; the next step is step + 1 */
     int32_t reserved;
@@ -107,7 +114,7 @@ typedef struct {
     float beta1, beta2, eps;
     int32_t max_defer;     /* MAX of the counter, at most 15 (4-bit counter) */
     int32_t mode;          /* GS_ADAM_DEFERRED or GS_ADAM_EAGER */
-    int32_t reserved;
+    int32_t seed;          /* stochastic-rounding seed of the BF16 form */
 } gs_adam_cfg;
 
 /* Context capacities, fixed at creation. */
@@ -141,9 +148,10 @@ GS_API const char *gs_last_error(const gs_ctx *ctx);
  * device since the last call (GS_OK if none). */
 GS_API gs_status gs_sync_status(gs_ctx *ctx, void *stream);
 
-/* Device pointer to the context's int32 counters: [0] visible count of the
+/* Device pointer to the context's 8 int32 counters: [0] visible count of the
  * last gs_cull, [1] key count of the last render, [2] update-set size of the
- * last deferred Adam step. */
+ * last deferred Adam step, [3] latched status, [6] Gaussians of the last
+ * render whose 2D covariance went through the FP64 chain. */
 GS_API const int32_t *gs_device_counters(const gs_ctx *ctx);
 
 /* ------------------------------------------------------------------ hot path */
@@ -285,6 +293,15 @@ GS_API gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, co
  * *n_keys the count K, *ranges[2 * tiles] the [begin, end) of each tile. */
 GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key, const uint32_t **splat_of_key,
                                  const int32_t **n_keys, const uint32_t **ranges);
+
+/* Inspection of the last gs_render_fwd: the projected splats of the visible
+ * set in compact order (entry k belongs to ids[k]), device pointers owned by
+ * the context and valid until the next render.  *geom[4 * k + 0..3] = (mean2d
+ * x, mean2d y, pixel radius, opacity), *conic[4 * k + 0..3] = (inverse 2D
+ * covariance entries A, B, C, camera depth) (§2.4 steps 1-2); *n_vis is the
+ * device count.  Gaussians that were not kept have radius 0 or an empty tile
+ * rectangle. */
+GS_API gs_status gs_render_splats(const gs_ctx *ctx, const float **geom, const float **conic, const int32_t **n_vis);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ c_i32, c_i64, c_f32, c_vp = C.c_int32, C.c_int64, C.c_float, C.c_void_p
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_BUDGET, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_NUMERIC = range(8)
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR_CUDA", 4: "GS_ERR_BUDGET",
                 5: "GS_ERR_CAPACITY", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_NUMERIC"}
-GS_FP32, GS_BF16_SH_MOM = 0, 1
+GS_FP32, GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN = 0, 1, 2
 RASTER_VARIANTS = 6
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
@@ -31,7 +31,7 @@ class Scene(C.Structure):
 
 class AdamCfg(C.Structure):
     _fields_ = [("lr", c_f32 * 6), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32), ("max_defer", c_i32),
-                ("mode", c_i32), ("reserved", c_i32)]
+                ("mode", c_i32), ("seed", c_i32)]
 
 
 class Config(C.Structure):
@@ -64,6 +64,7 @@ EXPORTS = {
     "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
                                 c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
+    "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
 }

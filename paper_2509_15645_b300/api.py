@@ -23,10 +23,11 @@ def _ptr(t):
 
 
 class _DeviceArray:
-    """Exposes a raw device int32 array to torch through __cuda_array_interface__."""
+    """Exposes a raw device array (int32 unless typestr says otherwise) to torch
+    through __cuda_array_interface__."""
 
-    def __init__(self, ptr, n):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (int(ptr), False), "version": 3}
+    def __init__(self, ptr, n, typestr="<i4"):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), False), "version": 3}
 
 
 def _stream(stream=None):
@@ -49,52 +50,84 @@ def camera_struct(cam) -> L.Camera:
     return c
 
 
-def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L.GS_ADAM_DEFERRED) -> L.AdamCfg:
+def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L.GS_ADAM_DEFERRED,
+                seed=0) -> L.AdamCfg:
     a = L.AdamCfg()
     lrs = [lr] * 6 if isinstance(lr, (int, float)) else list(lr)
     for k in range(6):
         a.lr[k] = float(lrs[k])
-    a.beta1, a.beta2, a.eps, a.max_defer, a.mode = beta1, beta2, eps, max_defer, mode
+    a.beta1, a.beta2, a.eps, a.max_defer, a.mode, a.seed = beta1, beta2, eps, max_defer, mode, seed
     return a
 
 
 class GaussianScene:
     """A Gaussian set on the device with its optimizer state.
 
-    ``w`` is one [D][pitch] float32 tensor (geometry planes then SH planes),
-    ``m``/``v`` the Adam moments, ``counter`` the defer counters."""
+    precision GS_FP32: ``w`` is one [D][pitch] float32 tensor (geometry planes
+    then SH planes; ``geo`` and ``sh`` are views of it), m / v float32, and
+    ``rdir`` [D][pitch] float32 restore directions.  BF16 forms: ``geo``
+    [11][pitch] float32 (master copy), ``sh`` [D-11][pitch] bfloat16, m / v
+    bfloat16; restore directions ``rdir_geo`` [11][pitch] float32 and
+    ``rdir_sh`` [D-11][pitch] bfloat16 (one buffer, in that order)."""
 
-    def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True):
+    def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True,
+                 precision=L.GS_FP32):
         D, n = params.shape
         assert D == n_params(sh_degree)
-        self.n, self.sh_degree, self.D = n, sh_degree, D
+        self.n, self.sh_degree, self.D, self.precision = n, sh_degree, D, precision
         self.pitch = (n + 3) // 4 * 4
-        self.w = torch.zeros(D, self.pitch, dtype=torch.float32, device=device)
-        self.w[:, :n] = torch.as_tensor(params, dtype=torch.float32).to(device)
-        if with_optimizer:
-            self.m = torch.zeros_like(self.w)
-            self.v = torch.zeros_like(self.w)
-            self.counter = torch.zeros(self.pitch, dtype=torch.uint8, device=device)
-            # restore directions m / (sqrt(v) + eps): zero while m = v = 0
-            self.rdir = torch.zeros_like(self.w) if with_rdir else None
+        src = torch.as_tensor(params, dtype=torch.float32).to(device)
+        if precision == L.GS_FP32:
+            self.w = torch.zeros(D, self.pitch, dtype=torch.float32, device=device)
+            self.w[:, :n] = src
+            self.geo, self.sh = self.w[:11], self.w[11:]
+            mdtype = torch.float32
         else:
-            self.m = self.v = self.counter = self.rdir = None
+            self.w = None
+            self.geo = torch.zeros(11, self.pitch, dtype=torch.float32, device=device)
+            self.sh = torch.zeros(D - 11, self.pitch, dtype=torch.bfloat16, device=device)
+            self.geo[:, :n] = src[:11]
+            self.sh[:, :n] = src[11:].to(torch.bfloat16)
+            mdtype = torch.bfloat16
+        self.rdir = self.rdir_geo = self.rdir_sh = None
+        if with_optimizer:
+            self.m = torch.zeros(D, self.pitch, dtype=mdtype, device=device)
+            self.v = torch.zeros(D, self.pitch, dtype=mdtype, device=device)
+            self.counter = torch.zeros(self.pitch, dtype=torch.uint8, device=device)
+            if with_rdir:
+                # restore directions m / (sqrt(v) + eps), zero while m = v = 0:
+                # fp32 rows for the geometry planes, then rows of the SH type
+                gbytes = 11 * self.pitch * 4
+                buf = torch.zeros(gbytes + (D - 11) * self.pitch * mdtype.itemsize, dtype=torch.uint8, device=device)
+                self._rdir_buf = buf
+                self.rdir_geo = buf[:gbytes].view(torch.float32).view(11, self.pitch)
+                self.rdir_sh = buf[gbytes:].view(mdtype).view(D - 11, self.pitch)
+                self.rdir = buf.view(torch.float32).view(D, self.pitch) if precision == L.GS_FP32 else None
+        else:
+            self.m = self.v = self.counter = None
         self.step = 0
 
     def struct(self) -> L.Scene:
         s = L.Scene()
-        s.n, s.pitch, s.sh_degree, s.precision = self.n, self.pitch, self.sh_degree, L.GS_FP32
-        s.geo = self.w.data_ptr()
-        s.sh = self.w.data_ptr() + 11 * self.pitch * 4
+        s.n, s.pitch, s.sh_degree, s.precision = self.n, self.pitch, self.sh_degree, self.precision
+        if self.w is not None:
+            s.geo = self.w.data_ptr()
+            s.sh = self.w.data_ptr() + 11 * self.pitch * 4
+        else:
+            s.geo = self.geo.data_ptr()
+            s.sh = self.sh.data_ptr()
         s.m = self.m.data_ptr() if self.m is not None else None
         s.v = self.v.data_ptr() if self.v is not None else None
-        s.rdir = self.rdir.data_ptr() if getattr(self, "rdir", None) is not None else None
+        s.rdir = self.rdir_geo.data_ptr() if self.rdir_geo is not None else None
         s.counter = self.counter.data_ptr() if self.counter is not None else None
         s.step = self.step
         return s
 
     def params(self):
-        return self.w[:, :self.n]
+        """Stored parameters as float32 [D][n]."""
+        if self.w is not None:
+            return self.w[:, :self.n]
+        return torch.cat([self.geo[:, :self.n], self.sh[:, :self.n].float()])
 
 
 class Context:
@@ -142,7 +175,8 @@ class Context:
     def counters(self):
         """The context's device counters (a torch view, no copy): [0] visible
         count of the last cull, [1] keys of the last render, [2] update-set size
-        of the last deferred Adam step, [3] latched status."""
+        of the last deferred Adam step, [3] latched status, [6] Gaussians of
+        the last render projected through the FP64 covariance chain."""
         p = self.lib.gs_device_counters(self.h)
         return torch.as_tensor(_DeviceArray(p, 8), device=self.device)
 
@@ -156,6 +190,17 @@ class Context:
         vals = torch.as_tensor(_DeviceArray(kv.value, max(n, 1)), device=self.device)[:n]
         ranges = torch.as_tensor(_DeviceArray(rg.value, 2 * tiles), device=self.device).view(tiles, 2)
         return keys, vals, ranges
+
+    def render_splats(self):
+        """Projected splats of the last render, float32 [n_vis][4] each (torch
+        views of context memory): (mean2d x, mean2d y, radius, opacity) and
+        (conic A, B, C, depth)."""
+        g, c, nv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self._check(self.lib.gs_render_splats(self.h, C.byref(g), C.byref(c), C.byref(nv)), "splats")
+        n = int(torch.as_tensor(_DeviceArray(nv.value, 1), device=self.device).item())
+        geom = torch.as_tensor(_DeviceArray(g.value, 4 * max(n, 1), "<f4"), device=self.device)[:4 * n].view(n, 4)
+        conic = torch.as_tensor(_DeviceArray(c.value, 4 * max(n, 1), "<f4"), device=self.device)[:4 * n].view(n, 4)
+        return geom, conic
 
     def cull(self, scene: GaussianScene, cam, adam=None, stream=None):
         ids = torch.empty(self.max_visible, dtype=torch.int32, device=self.device)
@@ -204,9 +249,7 @@ class Context:
         self._check(self.lib.gs_refresh_rdir(self.h, C.byref(sc), C.byref(adam), _stream(stream)), "gs_refresh_rdir")
 
     def materialize(self, scene: GaussianScene, adam, stream=None):
-        w = torch.empty_like(scene.w)
-        m = torch.empty_like(scene.w)
-        v = torch.empty_like(scene.w)
+        w, m, v = (torch.empty(scene.D, scene.pitch, dtype=torch.float32, device=self.device) for _ in range(3))
         sc = scene.struct()
         st = self.lib.gs_adam_materialize(self.h, C.byref(sc), C.byref(adam), _ptr(w), _ptr(m), _ptr(v),
                                           _stream(stream))
@@ -214,7 +257,7 @@ class Context:
         return w, m, v
 
     def grad_scatter(self, scene: GaussianScene, ids, n_vis, grad_compact, stream=None):
-        full = torch.empty_like(scene.w)
+        full = torch.empty(scene.D, scene.pitch, dtype=torch.float32, device=self.device)
         sc = scene.struct()
         st = self.lib.gs_grad_scatter(self.h, C.byref(sc), _ptr(ids), _ptr(n_vis), _ptr(grad_compact),
                                       grad_compact.shape[1], _ptr(full), _stream(stream))

@@ -3,6 +3,7 @@
 // arXiv 2509.15645, §2.4 steps 1-6 and §4.3).  Everything here is FP32.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,8 @@ struct DevCam {
 // Restore tables of the deferred update (Fig. 10, §4.3.2) for one step t.
 struct DevLut {
     float param[N_GROUPS][LUT_N];   // param_lut[d] (contains lr)
+    uint32_t seed;                  // stochastic-rounding seed (BF16 storage)
+    int stochastic;                 // 1: BF16 stores round stochastically
     float mom[LUT_N], var[LUT_N];   // b1^(d+1), b2^(d+1)
     float step_size[N_GROUPS];      // lr / (1 - b1^t)
     float bias_corr;                // sqrt(1 - b2^t)
@@ -55,7 +58,8 @@ struct Counters {
     int status;       // first latched gs_status
     float loss;       // last loss
     int n_union;      // gs_step: union of the views' visible sets
-    int pad[2];
+    int n_fix;        // last render: Gaussians projected through the FP64 chain
+    int pad;
 };
 
 __device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status, 0, code); }
@@ -63,6 +67,60 @@ __device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status,
 __host__ __device__ __forceinline__ int lr_group(int row)
 {
     return row < 3 ? 0 : row < 6 ? 1 : row < 10 ? 2 : row == 10 ? 3 : row < 14 ? 4 : 5;
+}
+
+// ---------------------------------------------------------------------------
+// Storage of SH planes and moments: fp32, or bf16 (precision form).  Loads
+// widen to fp32; bf16 stores round to nearest or stochastically with a
+// counter-based hash of (seed, step, plane, index), so a run is reproducible.
+__device__ __forceinline__ float ld_val(const float *p) { return *p; }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+// 32-bit integer finaliser (xor-shift / multiply rounds; the "lowbias32"
+// constants published by C. Wellons): a counter-based source of the random
+// bits of stochastic rounding.
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Random bits of the stores of parameter plane `plane` at Gaussian i in one
+// step: sr_bits(sr_plane_key(seed, step, plane), i).  The low 16 bits round m,
+// the high 16 bits v, and sr_w_bits() of them the weight.
+__device__ __forceinline__ uint32_t sr_plane_key(uint32_t seed, uint32_t step, uint32_t plane)
+{
+    return mix32(plane * 0x85ebca77u ^ mix32(step * 0xc2b2ae3du ^ seed));
+}
+__device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t i) { return mix32(i * 0x9e3779b1u ^ key); }
+__device__ __forceinline__ uint32_t sr_w_bits(uint32_t bits) { return (bits * 0x2c1b3c6du) >> 16; }
+
+// Stores return the value as stored (after rounding).
+__device__ __forceinline__ float st_val(float *p, float x, bool, uint32_t)
+{
+    *p = x;
+    return x;
+}
+
+// Stochastic rounding: adding 16 random bits below the kept mantissa carries
+// into it with probability equal to the dropped fraction (same for both signs,
+// the format being sign-magnitude).
+__device__ __forceinline__ float st_val(__nv_bfloat16 *p, float x, bool stochastic, uint32_t rnd)
+{
+    uint32_t u = __float_as_uint(x);
+    __nv_bfloat16 b;
+    if (!stochastic || (u & 0x7f800000u) == 0x7f800000u) {
+        b = __float2bfloat16_rn(x);
+    } else {
+        u += rnd & 0xffffu;
+        b = __ushort_as_bfloat16((unsigned short)(u >> 16));
+    }
+    *p = b;
+    return __bfloat162float(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -100,6 +158,7 @@ struct Proj {
     int cu, cw;            // guard-band clamps
     int rect[4];
     int keep;
+    int fp64;              // 2D covariance taken from the FP64 chain
 };
 
 __device__ __forceinline__ void quat_rot(const float q[4], float R[9])
@@ -111,9 +170,167 @@ __device__ __forceinline__ void quat_rot(const float q[4], float R[9])
 }
 
 // g[0..9] = mean(3), log-scale(3), quaternion(4).
+// ---------------------------------------------------------------------------
+// FP64 covariance chain for badly conditioned Gaussians (see project_gaussian).
+// Used by the fix-up kernels only, so the FP32 kernels keep their register
+// budget; both take the FP32 inputs (mean, log-scale, quaternion) and the view.
+struct Cov64 {
+    double Rq[9], s[3], qh[4], qn, S3[9], T[6], p[3], a, b, c;
+    int cu, cw;
+};
+struct Geo10 {
+    float v[10];
+};
+struct Sym2d {
+    double a, b, c;
+};
+struct CovGrad {
+    float gp[3], gls[3], gq[4];
+};
+
+static __device__ __forceinline__ void cov_chain_fp64(const Geo10 &G, const DevCam &cam, Cov64 &C)
+{
+    const float *g = G.v;
+    for (int k = 0; k < 3; k++) C.s[k] = exp((double)g[3 + k]);
+    double q[4] = {g[6], g[7], g[8], g[9]};
+    const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (qq > 0.0) {
+        C.qn = sqrt(qq);
+        for (int k = 0; k < 4; k++) C.qh[k] = q[k] / C.qn;
+    } else {
+        C.qn = 1.0; C.qh[0] = 1.0; C.qh[1] = C.qh[2] = C.qh[3] = 0.0;
+    }
+    const double w = C.qh[0], x = C.qh[1], y = C.qh[2], z = C.qh[3];
+    const double Rq[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                          2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                          2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    for (int k = 0; k < 9; k++) C.Rq[k] = Rq[k];
+    double M[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) M[r * 3 + c] = Rq[r * 3 + c] * C.s[c];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++)
+            C.S3[r * 3 + c] = M[r * 3 + 0] * M[c * 3 + 0] + M[r * 3 + 1] * M[c * 3 + 1] + M[r * 3 + 2] * M[c * 3 + 2];
+    const float *R = cam.R;
+    for (int r = 0; r < 3; r++)
+        C.p[r] = (double)R[r * 3 + 0] * g[0] + (double)R[r * 3 + 1] * g[1] + (double)R[r * 3 + 2] * g[2] + (double)cam.t[r];
+    const double iz = 1.0 / C.p[2];
+    const double u = C.p[0] * iz, v = C.p[1] * iz;
+    C.cu = (u < -(double)cam.limx) || (u > (double)cam.limx);
+    C.cw = (v < -(double)cam.limy) || (v > (double)cam.limy);
+    const double tu = fmin((double)cam.limx, fmax(-(double)cam.limx, u));
+    const double tv = fmin((double)cam.limy, fmax(-(double)cam.limy, v));
+    const double J00 = cam.fx * iz, J02 = -cam.fx * tu * iz, J11 = cam.fy * iz, J12 = -cam.fy * tv * iz;
+    for (int c = 0; c < 3; c++) {
+        C.T[c] = J00 * R[c] + J02 * R[6 + c];
+        C.T[3 + c] = J11 * R[3 + c] + J12 * R[6 + c];
+    }
+    double U[6];               // S3 T^T, columns for the two rows of T
+    for (int r = 0; r < 3; r++) {
+        U[r] = C.S3[r * 3 + 0] * C.T[0] + C.S3[r * 3 + 1] * C.T[1] + C.S3[r * 3 + 2] * C.T[2];
+        U[3 + r] = C.S3[r * 3 + 0] * C.T[3] + C.S3[r * 3 + 1] * C.T[4] + C.S3[r * 3 + 2] * C.T[5];
+    }
+    C.a = C.T[0] * U[0] + C.T[1] * U[1] + C.T[2] * U[2] + 0.3;
+    C.b = C.T[0] * U[3] + C.T[1] * U[4] + C.T[2] * U[5];
+    C.c = C.T[3] * U[3] + C.T[4] * U[4] + C.T[5] * U[5] + 0.3;
+}
+
+static __device__ __forceinline__ Sym2d cov2d_fp64(const Geo10 G, const DevCam &cam)
+{
+    Cov64 C;
+    cov_chain_fp64(G, cam, C);
+    return Sym2d{C.a, C.b, C.c};
+}
+
+// Adjoint of the chain in FP64: from the gradient of the conic (A, B, C) to
+// the camera-space mean (through J only), the log-scales and the quaternion.
+static __device__ __forceinline__ CovGrad cov_chain_bwd_fp64(const Geo10 G, const DevCam &cam, float gA, float gB,
+                                                          float gC)
+{
+    CovGrad out;
+    float *gp = out.gp, *gls = out.gls, *gq = out.gq;
+    Cov64 C;
+    cov_chain_fp64(G, cam, C);
+    const double a = C.a, b = C.b, c = C.c, det = a * c - b * b, id2 = 1.0 / (det * det);
+    const double ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
+    const double gb = (2.0 * b * c * gA - (a * c + b * b) * gB + 2.0 * a * b * gC) * id2;
+    const double gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+    const double hb = 0.5 * gb;
+    const double *T = C.T;
+    double gS[9];
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++)
+            gS[r * 3 + q] = ga * T[r] * T[q] + hb * (T[r] * T[3 + q] + T[3 + r] * T[q]) + gc * T[3 + r] * T[3 + q];
+    double e0[3], e1[3], gT[6];
+    for (int q = 0; q < 3; q++) {
+        e0[q] = 2.0 * (ga * T[q] + hb * T[3 + q]);
+        e1[q] = 2.0 * (hb * T[q] + gc * T[3 + q]);
+    }
+    for (int q = 0; q < 3; q++) {
+        gT[q] = e0[0] * C.S3[q] + e0[1] * C.S3[3 + q] + e0[2] * C.S3[6 + q];
+        gT[3 + q] = e1[0] * C.S3[q] + e1[1] * C.S3[3 + q] + e1[2] * C.S3[6 + q];
+    }
+    const float *R = cam.R;
+    const double gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
+    const double gJ02 = gT[0] * R[6] + gT[1] * R[7] + gT[2] * R[8];
+    const double gJ11 = gT[3] * R[3] + gT[4] * R[4] + gT[5] * R[5];
+    const double gJ12 = gT[3] * R[6] + gT[4] * R[7] + gT[5] * R[8];
+    const double iz = 1.0 / C.p[2], iz2 = iz * iz, iz3 = iz2 * iz;
+    const double fx = cam.fx, fy = cam.fy;
+    double p0 = 0.0, p1 = 0.0, p2 = -(gJ00 * fx + gJ11 * fy) * iz2;
+    if (!C.cu) {
+        p0 += -gJ02 * fx * iz2;
+        p2 += 2.0 * gJ02 * fx * C.p[0] * iz3;
+    } else {
+        p2 += gJ02 * fx * (C.p[0] > 0.0 ? (double)cam.limx : -(double)cam.limx) * iz2;
+    }
+    if (!C.cw) {
+        p1 += -gJ12 * fy * iz2;
+        p2 += 2.0 * gJ12 * fy * C.p[1] * iz3;
+    } else {
+        p2 += gJ12 * fy * (C.p[1] > 0.0 ? (double)cam.limy : -(double)cam.limy) * iz2;
+    }
+    gp[0] = (float)p0; gp[1] = (float)p1; gp[2] = (float)p2;
+    double M[9], gR[9];
+    for (int r = 0; r < 3; r++)
+        for (int q = 0; q < 3; q++) M[r * 3 + q] = C.Rq[r * 3 + q] * C.s[q];
+    for (int q = 0; q < 3; q++) {
+        double gsc = 0.0;
+        for (int r = 0; r < 3; r++) {
+            const double gm = 2.0 * (gS[r * 3 + 0] * M[q] + gS[r * 3 + 1] * M[3 + q] + gS[r * 3 + 2] * M[6 + q]);
+            gsc += gm * C.Rq[r * 3 + q];
+            gR[r * 3 + q] = gm * C.s[q];
+        }
+        gls[q] = (float)(gsc * C.s[q]);
+    }
+    const double qw = C.qh[0], qx = C.qh[1], qy = C.qh[2], qz = C.qh[3];
+    const double dw = -2 * qz * gR[1] + 2 * qy * gR[2] + 2 * qz * gR[3] - 2 * qx * gR[5] - 2 * qy * gR[6] + 2 * qx * gR[7];
+    const double dx = 2 * qy * gR[1] + 2 * qz * gR[2] + 2 * qy * gR[3] - 4 * qx * gR[4] - 2 * qw * gR[5] +
+                      2 * qz * gR[6] + 2 * qw * gR[7] - 4 * qx * gR[8];
+    const double dy = -4 * qy * gR[0] + 2 * qx * gR[1] + 2 * qw * gR[2] + 2 * qx * gR[3] + 2 * qz * gR[5] -
+                      2 * qw * gR[6] + 2 * qz * gR[7] - 4 * qy * gR[8];
+    const double dz = -4 * qz * gR[0] - 2 * qw * gR[1] + 2 * qx * gR[2] + 2 * qw * gR[3] - 4 * qz * gR[4] +
+                      2 * qy * gR[5] + 2 * qx * gR[6] + 2 * qy * gR[7];
+    const double dq = dw * qw + dx * qx + dy * qy + dz * qz;
+    gq[0] = (float)((dw - qw * dq) / C.qn);
+    gq[1] = (float)((dx - qx * dq) / C.qn);
+    gq[2] = (float)((dy - qy * dq) / C.qn);
+    gq[3] = (float)((dz - qz * dq) / C.qn);
+    return out;
+}
+
+// Conditioning bound above which the 2D covariance is recomputed in FP64.
+constexpr float COND_FP64 = 64.f;
+
+// FP64 = false: the FP32 chain only, P.fp64 flags a Gaussian that needs the
+// FP64 one (the cull, whose keep decision is set by the large eigenvalue, and
+// the first pass of the gather and of the adjoint, which hand flagged
+// Gaussians to a fix-up pass); FP64 = true: the fix-up pass itself.
+template <bool FP64 = false>
 __device__ __forceinline__ void project_gaussian(const float g[10], const DevCam &cam, Proj &P)
 {
     P.keep = 0;
+    P.fp64 = 0;
     P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
     const float *R = cam.R;
     P.p[0] = R[0] * g[0] + R[1] * g[1] + R[2] * g[2] + cam.t[0];
@@ -170,9 +387,35 @@ __device__ __forceinline__ void project_gaussian(const float g[10], const DevCam
     P.b = P.T[0] * v0 + P.T[1] * v1 + P.T[2] * v2;
     P.c = P.T[3] * v0 + P.T[4] * v1 + P.T[5] * v2 + 0.3f;
     P.det = P.a * P.c - P.b * P.b;
-    if (!(P.det > 0.f)) return;
-    float idet = 1.f / P.det;
-    P.conA = P.c * idet; P.conB = -P.b * idet; P.conC = P.a * idet;
+    // Rounding in the chain leaves an absolute error of about u * tr(Sigma3) *
+    // |T|_F^2 in a, b and c, so the relative error of det (and of the conic)
+    // is about u * (a + c) * tr(Sigma3) * |T|_F^2 / det: large for a
+    // near-singular Sigma2 and for a needle seen end-on.  Above 64 (a relative
+    // error of a few 1e-6) the chain is redone in FP64 from the FP32 inputs.
+    const float tr3 = P.S3[0] + P.S3[3] + P.S3[5];
+    const float tn = P.T[0] * P.T[0] + P.T[1] * P.T[1] + P.T[2] * P.T[2] + P.T[3] * P.T[3] + P.T[4] * P.T[4] +
+                     P.T[5] * P.T[5];
+    P.fp64 = !(P.det * COND_FP64 > (P.a + P.c) * tr3 * tn);
+    if (FP64 && P.fp64) {
+        Geo10 G;
+#pragma unroll
+        for (int k = 0; k < 10; k++) G.v[k] = g[k];
+        const Sym2d S2 = cov2d_fp64(G, cam);
+        const double S2d[3] = {S2.a, S2.b, S2.c};
+        const double detd = S2d[0] * S2d[2] - S2d[1] * S2d[1];
+        P.a = (float)S2d[0];
+        P.b = (float)S2d[1];
+        P.c = (float)S2d[2];
+        P.det = (float)detd;
+        if (!(detd > 0.0)) return;
+        P.conA = (float)(S2d[2] / detd);
+        P.conB = (float)(-S2d[1] / detd);
+        P.conC = (float)(S2d[0] / detd);
+    } else {
+        if (!(P.det > 0.f)) return;
+        float idet = 1.f / P.det;
+        P.conA = P.c * idet; P.conB = -P.b * idet; P.conC = P.a * idet;
+    }
     float mid = 0.5f * (P.a + P.c);
     float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - P.det));
     P.radius = ceilf(3.f * sqrtf(lam));

@@ -45,14 +45,15 @@ int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int
 
 // Scene pointers as the kernels take them.
 struct SceneView {
-    float *geo;
-    float *sh;
-    float *m;
-    float *v;
-    float *rdir;          // restore directions, or nullptr
+    float *geo;           // [11][pitch] fp32
+    void *sh;             // [D - 11][pitch] fp32 or bf16 (prec)
+    void *m;              // [D][pitch] fp32 or bf16
+    void *v;
+    float *rdir;          // restore directions: [11][pitch] fp32, then [D-11][pitch] of the SH type; or nullptr
     uint8_t *counter;
     int64_t n, pitch;
     int deg, D;
+    int prec;             // GS_FP32, GS_BF16_SH_MOM or GS_BF16_SH_MOM_RN
 };
 
 // Timing points recorded inside a step (see gs_timing_enable).
@@ -92,6 +93,9 @@ struct RenderBufs {
     uint2 *ranges;           // [tiles]
     float *g9;               // [9][cap] screen-space gradient sums
     int *n_keys;             // device
+    int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
+    int32_t *fix_idx;        // [cap] their visible-set indices
+    uint8_t *fix_flag;       // [cap] 1 for those, else 0
     int variant;             // rasterizer variant (pixels per thread, batch), see raster_variant_ok
     // filled by render_fwd
     const uint32_t *sorted_keys;

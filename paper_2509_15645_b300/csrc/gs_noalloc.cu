@@ -86,7 +86,8 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     if (tile_w <= 0 || tile_h <= 0 || cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f) ||
         !(cam->far_z > cam->near_z) || cam->width >= 65536 * tile_w || cam->height >= 65536 * tile_h)
         return GS_ERR_INVALID_ARG;
-    if (scene->precision != GS_FP32) return GS_ERR_INVALID_ARG;
+    if (scene->precision != GS_FP32 && scene->precision != GS_BF16_SH_MOM && scene->precision != GS_BF16_SH_MOM_RN)
+        return GS_ERR_INVALID_ARG;
     const bool restore = adam && adam->mode == GS_ADAM_DEFERRED && scene->m && scene->v && scene->counter;
     if (adam && (adam->max_defer < 1 || adam->max_defer > LUT_N - 1)) return GS_ERR_INVALID_ARG;
 
@@ -146,9 +147,10 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
 
     SceneView sv{};
     sv.geo = scene->geo;
-    sv.sh = (float *)scene->sh;
-    sv.m = (float *)scene->m;
-    sv.v = (float *)scene->v;
+    sv.sh = scene->sh;
+    sv.m = scene->m;
+    sv.v = scene->v;
+    sv.prec = scene->precision;
     sv.rdir = (scene->m && scene->v) ? scene->rdir : nullptr;
     sv.counter = scene->counter;
     sv.n = scene->n;

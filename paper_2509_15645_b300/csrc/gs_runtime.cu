@@ -27,7 +27,7 @@ struct GraphCache {
     float *rdir = nullptr;
     uint8_t *counter = nullptr;
     int64_t n = 0, pitch = 0;
-    int deg = -1, n_views = 0, mode = -1;
+    int deg = -1, n_views = 0, mode = -1, prec = -1;
     int W[MAX_VIEWS] = {0}, H[MAX_VIEWS] = {0};
     float *loss = nullptr;
     bool timed = false;
@@ -189,6 +189,9 @@ static void carve(gs_ctx *c, char *base)
     rb.ranges = k.take<uint2>(tiles);
     rb.g9 = k.take<float>(9 * V);
     rb.n_keys = base ? &c->cnt->n_keys : nullptr;
+    rb.n_fix = base ? &c->cnt->n_fix : nullptr;
+    rb.fix_idx = k.take<int32_t>(V);
+    rb.fix_flag = k.take<uint8_t>(V);
     int64_t big = K > V ? K : V;
     c->w.hist = k.take<uint32_t>(256 * ((big + RADIX_TILE - 1) / RADIX_TILE) + 256);
     c->w.partials = k.take<uint32_t>(1024);
@@ -222,11 +225,13 @@ static DevCam make_cam(const gs_camera &a, const gs_config &g)
 
 // Tables of the deferred update (Fig. 10, §4.3.2) for step t, computed in
 // double and rounded to float.  Entries with delay >= t are never used.
-static DevLut make_lut(const gs_adam_cfg *a, int t, bool restore)
+static DevLut make_lut(const gs_adam_cfg *a, int t, bool restore, int precision = GS_FP32)
 {
     DevLut L{};
     L.restore = 0;
     if (!a) return L;
+    L.seed = (uint32_t)a->seed;
+    L.stochastic = precision == GS_BF16_SH_MOM ? 1 : 0;
     const double b1 = a->beta1, b2 = a->beta2;
     const double scale = b1 / std::sqrt(b2);
     for (int g = 0; g < N_GROUPS; g++) {
@@ -284,14 +289,16 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     if (s->n <= 0 || s->n > c->cfg.max_gaussians) return fail(c, GS_ERR_INVALID_ARG, "scene n=%lld out of range", (long long)s->n);
     if (s->pitch < s->n || (s->pitch & 3)) return fail(c, GS_ERR_INVALID_ARG, "pitch must be >= n and a multiple of 4");
     if (s->sh_degree < 0 || s->sh_degree > c->cfg.max_sh_degree) return fail(c, GS_ERR_INVALID_ARG, "sh_degree out of range");
-    if (s->precision != GS_FP32) return fail(c, GS_ERR_INVALID_ARG, "precision form not supported by this build");
+    if (s->precision != GS_FP32 && s->precision != GS_BF16_SH_MOM && s->precision != GS_BF16_SH_MOM_RN)
+        return fail(c, GS_ERR_INVALID_ARG, "unknown precision form");
     if (!s->geo || !s->sh) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
     if (need_opt && (!s->m || !s->v || !s->counter)) return fail(c, GS_ERR_INVALID_ARG, "optimizer state is NULL");
     sv.geo = s->geo;
-    sv.sh = (float *)s->sh;
-    sv.m = (float *)s->m;
-    sv.v = (float *)s->v;
+    sv.sh = s->sh;
+    sv.m = s->m;
+    sv.v = s->v;
     sv.rdir = (s->m && s->v) ? s->rdir : nullptr;
+    sv.prec = s->precision;
     sv.counter = s->counter;
     sv.n = s->n;
     sv.pitch = s->pitch;
@@ -471,7 +478,7 @@ gs_status gs_adam_deferred(gs_ctx *c, gs_scene *scene, const int32_t *ids, const
     if (!ids || !n_vis || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
-    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED);
+    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED, scene->precision);
     a.n_views = 0;
     set_args(c, SLOT_ADAM, a, s);
     int icap = (int)(cap < c->cfg.max_visible ? cap : c->cfg.max_visible);
@@ -535,6 +542,14 @@ gs_status gs_grad_scatter(gs_ctx *c, const gs_scene *scene, const int32_t *ids, 
 gs_status gs_timing_enable(gs_ctx *c, int32_t max_steps)
 {
     if (!c || max_steps < 0 || max_steps > 1000000) return GS_ERR_INVALID_ARG;
+    // the cached step graph records into the events freed here: drop it (once
+    // no replay is in flight) so the next gs_step captures a graph for the new
+    // events, or none
+    if (c->graph.exec && cudaDeviceSynchronize() != cudaSuccess) return cuda_check(c, "gs_timing_enable");
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    if (c->graph.graph) cudaGraphDestroy(c->graph.graph);
+    c->graph.exec = nullptr;
+    c->graph.graph = nullptr;
     timing_free(c);
     if (max_steps == 0) return GS_OK;
     c->t_events = (cudaEvent_t *)calloc((size_t)max_steps * TP_COUNT, sizeof(cudaEvent_t));
@@ -689,6 +704,15 @@ gs_status gs_render_lists(const gs_ctx *c, const uint32_t **tile_of_key, const u
     return GS_OK;
 }
 
+gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **conic, const int32_t **n_vis)
+{
+    if (!c || !c->have_fwd || !geom || !conic || !n_vis) return GS_ERR_INVALID_ARG;
+    *geom = reinterpret_cast<const float *>(c->rb.rec0);
+    *conic = reinterpret_cast<const float *>(c->rb.rec1);
+    *n_vis = c->n_render;
+    return GS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // gs_step: the whole iteration enqueued on one stream; captured once into a
 // CUDA graph and replayed, with only the argument block (cameras, targets,
@@ -742,7 +766,8 @@ static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_came
                           float *loss, bool timed, int variant)
 {
     if (!g.exec || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
-        g.rdir != sc->rdir || g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree || g.n_views != n_views || g.mode != mode ||
+        g.rdir != sc->rdir || g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree ||
+        g.prec != sc->precision || g.n_views != n_views || g.mode != mode ||
         g.loss != loss || g.timed != timed || g.variant != variant)
         return false;
     for (int v = 0; v < n_views; v++)
@@ -766,7 +791,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         a.cam[v] = make_cam(views[v], c->cfg);
         a.target[v] = targets[v];
     }
-    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED);
+    a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED, scene->precision);
     a.n_views = n_views;
     cudaStream_t s = (cudaStream_t)stream;
     GraphCache &g = c->graph;
@@ -839,6 +864,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         g.geo = scene->geo; g.sh = scene->sh; g.m = scene->m; g.v = scene->v; g.counter = scene->counter;
         g.rdir = scene->rdir;
         g.n = scene->n; g.pitch = scene->pitch; g.deg = scene->sh_degree; g.n_views = n_views; g.mode = adam->mode;
+        g.prec = scene->precision;
         g.loss = loss_out;
         g.timed = timed;
         g.variant = c->rb.variant;

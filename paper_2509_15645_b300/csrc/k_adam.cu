@@ -8,9 +8,11 @@
 //   k_adam_select  -- counters (1 B) + visibility mask: update-set bitmask,
 //                     counters of non-members incremented in place;
 //   k_compact      -- ordered id list of the update set (k_scan.cu);
-//   k_adam_apply   -- one thread per member, all D planes of w, m, v (+ g):
-//                     28 B read/written per parameter, coalesced because the
-//                     Gaussians are stored in Morton order and views see runs.
+//   k_adam_apply   -- one thread per (member, 4 planes), w, m, v (+ g) and the
+//                     restore direction: 28 B read/written per parameter in
+//                     the fp32 form, 14 B per SH parameter in the bf16 form;
+//                     coalesced because the Gaussians are stored in Morton
+//                     order and views see runs.
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -65,6 +67,8 @@ struct SLut {
     float mom[LUT_N], var[LUT_N];
     float step_size[N_GROUPS];
     float bias_corr, inv_bias_corr, omb1, omb2, eps;
+    uint32_t seed, step;
+    int stochastic;
 };
 
 __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
@@ -79,13 +83,15 @@ __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
         s.omb1 = L.omb1;
         s.omb2 = L.omb2;
         s.eps = L.eps;
+        s.seed = L.seed;
+        s.step = (uint32_t)L.step;
+        s.stochastic = L.stochastic;
     }
     __syncthreads();
 }
 
 // Restore (delay d) + Eq. 1 for one value.  d = 0 is the plain Adam step.
-// Returns the new restore direction m_new / (sqrt(v_new) + eps).
-__device__ __forceinline__ float adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
+__device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
 {
     float m_new = L.mom[d] * m + L.omb1 * g;
     float v_new = L.var[d] * v + L.omb2 * g * g;
@@ -94,7 +100,6 @@ __device__ __forceinline__ float adam_value(float &w, float &m, float &v, float 
     w = wr - L.step_size[grp] * __fdividef(m_new, denom);
     m = m_new;
     v = v_new;
-    return restore_dir(m_new, v_new, L.eps);
 }
 
 __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask, const uint32_t *__restrict__ vprefix,
@@ -106,22 +111,55 @@ __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask,
     return (int)(vprefix[i >> 5] + __popc(word & ((1u << bit) - 1u)));
 }
 
-template <int UNROLL>
-__device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__restrict__ sh, float *__restrict__ m,
-                                          float *__restrict__ v, float *__restrict__ rdir, int64_t pitch, int D,
-                                          int64_t i, int k, const float *__restrict__ grad, int64_t gcap, int d,
-                                          const SLut &L)
+// Parameter plane r of Gaussian i: geometry planes are fp32, SH planes of
+// type T; restore directions likewise (fp32 for the 11 geometry planes, then
+// type T for the SH planes, so [D][pitch] fp32 in the fp32 form).
+template <typename T> struct Planes {
+    float *geo;
+    T *sh;
+    T *m, *v;
+    float *rdir;
+    int64_t pitch;
+    __device__ __forceinline__ float ldw(int r, int64_t i) const
+    {
+        return r < N_GEO ? geo[r * pitch + i] : ld_val(sh + (r - N_GEO) * pitch + i);
+    }
+    __device__ __forceinline__ T *rdir_sh() const { return (T *)(rdir + N_GEO * pitch); }
+    // Store the updated w, m, v of plane r (rounded per the storage; `key` is
+    // sr_plane_key of this plane and step) and the restore direction of what
+    // was stored.
+    __device__ __forceinline__ void store(int r, int64_t i, float w, float mm, float vv, const SLut &L,
+                                          uint32_t key) const
+    {
+        const bool st = L.stochastic != 0;
+        const uint32_t bits = st ? sr_bits(key, (uint32_t)i) : 0u;
+        const float ms = st_val(m + r * pitch + i, mm, st, bits);
+        const float vs = st_val(v + r * pitch + i, vv, st, bits >> 16);
+        const float dir = restore_dir(ms, vs, L.eps);
+        if (r < N_GEO) {
+            geo[r * pitch + i] = w;
+            if (rdir) rdir[r * pitch + i] = dir;
+        } else {
+            st_val(sh + (r - N_GEO) * pitch + i, w, st, sr_w_bits(bits));
+            if (rdir) st_val(rdir_sh() + (r - N_GEO) * pitch + i, dir, false, 0u);
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, int k, const float *__restrict__ grad,
+                                          int64_t gcap, int d, const SLut &L)
 {
+    constexpr int UNROLL = 4;
     for (int r0 = 0; r0 < D; r0 += UNROLL) {
         float w_[UNROLL], m_[UNROLL], v_[UNROLL], g_[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
             int r = r0 + u;
             if (r < D) {
-                const float *wp = r < N_GEO ? geo + r * pitch + i : sh + (r - N_GEO) * pitch + i;
-                w_[u] = *wp;
-                m_[u] = m[r * pitch + i];
-                v_[u] = v[r * pitch + i];
+                w_[u] = P.ldw(r, i);
+                m_[u] = ld_val(P.m + r * P.pitch + i);
+                v_[u] = ld_val(P.v + r * P.pitch + i);
                 g_[u] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
             }
         }
@@ -129,12 +167,8 @@ __device__ __forceinline__ void adam_rows(float *__restrict__ geo, float *__rest
         for (int u = 0; u < UNROLL; u++) {
             int r = r0 + u;
             if (r < D) {
-                const float dir = adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
-                float *wp = r < N_GEO ? geo + r * pitch + i : sh + (r - N_GEO) * pitch + i;
-                *wp = w_[u];
-                m[r * pitch + i] = m_[u];
-                v[r * pitch + i] = v_[u];
-                if (rdir) rdir[r * pitch + i] = dir;
+                adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
+                P.store(r, i, w_[u], m_[u], v_[u], L, L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)r) : 0u);
             }
         }
     }
@@ -153,16 +187,11 @@ struct AdamRows {
     int d;
 };
 
-__device__ __forceinline__ float *plane(float *geo, float *sh, int64_t pitch, int r)
-{
-    return r < N_GEO ? geo + r * pitch : sh + (r - N_GEO) * pitch;
-}
-
+template <typename T>
 __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__restrict__ uids,
                                            const uint8_t *__restrict__ udelay, const uint32_t *__restrict__ vmask,
-                                           const uint32_t *__restrict__ vprefix, float *geo, float *sh,
-                                           const float *__restrict__ m, const float *__restrict__ v,
-                                           const float *__restrict__ grad, int64_t gcap, int64_t pitch, int D, int r0)
+                                           const uint32_t *__restrict__ vprefix, const Planes<T> &P,
+                                           const float *__restrict__ grad, int64_t gcap, int D, int r0)
 {
     a.i = uids[u];
     a.d = udelay[u];
@@ -172,18 +201,16 @@ __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__
     for (int j = 0; j < RG; j++) {
         const int r = r0 + j;
         if (r < D) {
-            a.w[j] = plane(geo, sh, pitch, r)[a.i];
-            a.m[j] = m[r * pitch + a.i];
-            a.v[j] = v[r * pitch + a.i];
+            a.w[j] = P.ldw(r, a.i);
+            a.m[j] = ld_val(P.m + r * P.pitch + a.i);
+            a.v[j] = ld_val(P.v + r * P.pitch + a.i);
             a.g[j] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
         }
     }
 }
 
-__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ geo, float *__restrict__ sh,
-                                                           float *__restrict__ m, float *__restrict__ v,
-                                                           float *__restrict__ rdir, int64_t pitch, int D,
-                                                           const int32_t *__restrict__ uids,
+template <typename T>
+__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(Planes<T> P, int D, const int32_t *__restrict__ uids,
                                                            const uint8_t *__restrict__ udelay, const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
@@ -197,28 +224,40 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(float *__restrict__ g
     const int stride = gridDim.x * blockDim.x;
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_upd) return;
+    uint32_t key[RG];          // stochastic-rounding keys of this thread's planes
+#pragma unroll
+    for (int j = 0; j < RG; j++) key[j] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + j)) : 0u;
     AdamRows cur, nxt;
-    adam_fetch(cur, u, uids, udelay, vmask, vprefix, geo, sh, m, v, grad, gcap, pitch, D, r0);
+    adam_fetch(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
     while (true) {
         const int un = u + stride;
         const bool more = un < n_upd;
-        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, geo, sh, m, v, grad, gcap, pitch, D, r0);
+        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
 #pragma unroll
         for (int j = 0; j < RG; j++) {
             const int r = r0 + j;
             if (r < D) {
                 float w_ = cur.w[j], m_ = cur.m[j], v_ = cur.v[j];
-                const float dir = adam_value(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
-                plane(geo, sh, pitch, r)[cur.i] = w_;
-                m[r * pitch + cur.i] = m_;
-                v[r * pitch + cur.i] = v_;
-                if (rdir) rdir[r * pitch + cur.i] = dir;
+                adam_value(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
+                P.store(r, cur.i, w_, m_, v_, L, key[j]);
             }
         }
         if (!more) break;
         cur = nxt;
         u = un;
     }
+}
+
+template <typename T> static Planes<T> planes_of(const SceneView &sc)
+{
+    Planes<T> P;
+    P.geo = sc.geo;
+    P.sh = (T *)sc.sh;
+    P.m = (T *)sc.m;
+    P.v = (T *)sc.v;
+    P.rdir = sc.rdir;
+    P.pitch = sc.pitch;
+    return P;
 }
 
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
@@ -232,17 +271,20 @@ void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32
     const int groups = (sc.D + RG - 1) / RG;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
     w.mark(TP_APPLY0, s);
-    k_adam_apply<<<grid, ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.pitch, sc.D, uids, udelay, n_upd,
-                                             vmask, vprefix, grad, gcap, args);
+    if (sc.prec == GS_FP32)
+        k_adam_apply<float><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, uids, udelay, n_upd, vmask, vprefix,
+                                                        grad, gcap, args);
+    else
+        k_adam_apply<__nv_bfloat16><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, uids, udelay,
+                                                                n_upd, vmask, vprefix, grad, gcap, args);
     w.mark(TP_APPLY1, s);
 }
 
 // Eager Adam (Eq. 1 for every Gaussian, every step): the baseline the
 // deferred update removes; counters are left alone.
-__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(float *__restrict__ geo, float *__restrict__ sh,
-                                                           float *__restrict__ m, float *__restrict__ v,
-                                                           float *__restrict__ rdir, int64_t pitch,
-                                                           int64_t n, int D, const uint32_t *__restrict__ vmask,
+template <typename T>
+__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(Planes<T> P, int64_t n, int D,
+                                                           const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
                                                            const float *__restrict__ grad, int64_t gcap,
                                                            const DevArgs *__restrict__ args)
@@ -252,7 +294,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(float *__restrict__ g
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int k = compact_index(vmask, vprefix, i);
         if (k >= gcap) k = -1;
-        adam_rows<4>(geo, sh, m, v, rdir, pitch, D, i, k, grad, gcap, 0, L);
+        adam_rows<T>(P, D, i, k, grad, gcap, 0, L);
     }
 }
 
@@ -260,40 +302,54 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s)
 {
     w.mark(TP_APPLY0, s);
-    k_adam_eager<<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.rdir, sc.pitch, sc.n,
-                                                               sc.D, vmask, vprefix, grad, gcap, args);
+    if (sc.prec == GS_FP32)
+        k_adam_eager<float><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.n, sc.D, vmask,
+                                                                          vprefix, grad, gcap, args);
+    else
+        k_adam_eager<__nv_bfloat16><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.n,
+                                                                                  sc.D, vmask, vprefix, grad, gcap,
+                                                                                  args);
     w.mark(TP_APPLY1, s);
 }
 
-// rdir = m / (sqrt(v) + eps) for every parameter.
-__global__ void k_refresh_rdir(const float *__restrict__ m, const float *__restrict__ v, float *__restrict__ rdir,
-                               int64_t pitch, int64_t n, int D, const DevArgs *__restrict__ args)
+// rdir = m / (sqrt(v) + eps) for every plane that keeps a restore direction.
+template <typename T>
+__global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__restrict__ args)
 {
     const float eps = args->lut.eps;
-    const int64_t total = (int64_t)D * pitch;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-        if (e % pitch < n) rdir[e] = restore_dir(m[e], v[e], eps);
+    const int64_t total = (int64_t)D * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n);
+        const int64_t i = e - (int64_t)r * n, o = r * P.pitch + i;
+        const float dir = restore_dir(ld_val(P.m + o), ld_val(P.v + o), eps);
+        if (r < N_GEO) P.rdir[o] = dir;
+        else st_val(P.rdir_sh() + (r - N_GEO) * P.pitch + i, dir, false, 0u);
+    }
 }
 
 void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s)
 {
     if (!sc.rdir) return;
-    k_refresh_rdir<<<w.grid((int64_t)sc.D * sc.pitch, 256, 4), 256, 0, s>>>(sc.m, sc.v, sc.rdir, sc.pitch, sc.n, sc.D,
-                                                                          args);
+    const int g = w.grid((int64_t)sc.D * sc.n, 256, 4);
+    if (sc.prec == GS_FP32)
+        k_refresh_rdir<float><<<g, 256, 0, s>>>(planes_of<float>(sc), sc.D, sc.n, args);
+    else
+        k_refresh_rdir<__nv_bfloat16><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, sc.n, args);
 }
 
 // Catch-up without a step: m b1^c, v b2^c, w - param_lut[c] m / (sqrt(v) + eps).
-__global__ void k_materialize(const float *__restrict__ geo, const float *__restrict__ sh, const float *__restrict__ m,
-                              const float *__restrict__ v, const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
-                              int D, const DevArgs *__restrict__ args, float *w_out, float *m_out, float *v_out)
+template <typename T>
+__global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, int64_t n, int D,
+                              const DevArgs *__restrict__ args, float *w_out, float *m_out, float *v_out)
 {
     __shared__ SLut L;
     load_slut(L, args->lut);
+    const int64_t pitch = P.pitch;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int d = counter ? counter[i] : 0;
         for (int r = 0; r < D; r++) {
-            float w = r < N_GEO ? geo[r * pitch + i] : sh[(r - N_GEO) * pitch + i];
-            float mm = m[r * pitch + i], vv = v[r * pitch + i];
+            float w = P.ldw(r, i);
+            float mm = ld_val(P.m + r * pitch + i), vv = ld_val(P.v + r * pitch + i);
             if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[lr_group(r)][d], d, L.eps);
             if (m_out) m_out[r * pitch + i] = d ? L.mom[d - 1] * mm : mm;
             if (v_out) v_out[r * pitch + i] = d ? L.var[d - 1] * vv : vv;
@@ -304,8 +360,12 @@ __global__ void k_materialize(const float *__restrict__ geo, const float *__rest
 void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
                         Work &w, cudaStream_t s)
 {
-    k_materialize<<<w.grid(sc.n, 256), 256, 0, s>>>(sc.geo, sc.sh, sc.m, sc.v, sc.counter, sc.pitch, sc.n, sc.D, args,
-                                                   w_out, m_out, v_out);
+    if (sc.prec == GS_FP32)
+        k_materialize<float><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<float>(sc), sc.counter, sc.n, sc.D, args, w_out,
+                                                             m_out, v_out);
+    else
+        k_materialize<__nv_bfloat16><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.counter, sc.n,
+                                                                     sc.D, args, w_out, m_out, v_out);
 }
 
 __global__ void k_grad_scatter(const int32_t *__restrict__ ids, const int *n_dev, int cap,

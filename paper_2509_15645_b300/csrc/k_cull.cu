@@ -12,8 +12,9 @@ namespace gs {
 
 constexpr int CULL_BLOCK = 256;
 
-__global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict__ geo, const float *__restrict__ m,
-                                                     const float *__restrict__ v, const float *__restrict__ rdir,
+template <typename MT>
+__global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict__ geo, const MT *__restrict__ m,
+                                                     const MT *__restrict__ v, const float *__restrict__ rdir,
                                                      const uint8_t *__restrict__ counter,
                                                      int64_t pitch, int64_t n, const DevArgs *__restrict__ args,
                                                      int view, uint32_t *__restrict__ mask,
@@ -58,8 +59,8 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                     float mm[10], vv[10];
 #pragma unroll
                     for (int r = 0; r < 10; r++) {
-                        mm[r] = __ldg(m + r * pitch + i);
-                        vv[r] = __ldg(v + r * pitch + i);
+                        mm[r] = ld_val(m + r * pitch + i);
+                        vv[r] = ld_val(v + r * pitch + i);
                     }
                     const int d = counter[i];
 #pragma unroll
@@ -91,8 +92,14 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (view == 0) w.mark(TP_CULL0, s);
-    k_cull<<<w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8), CULL_BLOCK, 0, s>>>(sc.geo, sc.m, sc.v, sc.rdir, sc.counter,
-                                                                           sc.pitch, sc.n, args, view, mask, chunk_cnt);
+    const int g = w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8);
+    if (sc.prec == GS_FP32)
+        k_cull<float><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const float *)sc.m, (const float *)sc.v, sc.rdir, sc.counter,
+                                               sc.pitch, sc.n, args, view, mask, chunk_cnt);
+    else
+        k_cull<__nv_bfloat16><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const __nv_bfloat16 *)sc.m, (const __nv_bfloat16 *)sc.v,
+                                                       sc.rdir, sc.counter, sc.pitch, sc.n, args, view, mask,
+                                                       chunk_cnt);
     if (view == 0) w.mark(TP_CULL1, s);
 }
 

@@ -30,14 +30,16 @@ struct SLutR {
     int restore;
 };
 
-template <int DEG>
+template <int DEG, typename T>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
                                                                const int *n_vis_p, int cap,
                                                                const DevArgs *__restrict__ args, int view,
                                                                float *__restrict__ compact, float4 *__restrict__ rec0,
                                                                float4 *__restrict__ rec1, float4 *__restrict__ rec2,
                                                                uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
-                                                               uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect)
+                                                               uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect,
+                                                               int *__restrict__ n_fix, int32_t *__restrict__ fix_idx,
+                                                               uint8_t *__restrict__ fix_flag)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     constexpr int D = N_GEO + 3 * NK;
@@ -63,30 +65,41 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
             dval[k] = (uint32_t)k;
             tcnt[k] = 0u;
             rect[k] = make_uint2(0u, 0u);
+            fix_flag[k] = 0;
             for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = 0.f;
             continue;
         }
         // gather all D planes (with m, v when restoring) before any arithmetic
+        const T *sh = (const T *)sc.sh, *mp = (const T *)sc.m, *vp = (const T *)sc.v;
         float w[D];
 #pragma unroll
-        for (int r = 0; r < D; r++) w[r] = __ldg((r < N_GEO ? sc.geo + r * pitch : sc.sh + (r - N_GEO) * pitch) + i);
+        for (int r = 0; r < D; r++) w[r] = r < N_GEO ? __ldg(sc.geo + r * pitch + i) : ld_val(sh + (r - N_GEO) * pitch + i);
         if (L.restore) {
             const int d = sc.counter[i];
-            if (d && sc.rdir) {
+            if (d) {
+                // restore directions: fp32 for the geometry planes, the SH
+                // storage type for the SH planes
+                if (sc.rdir) {
+                    const T *rsh = (const T *)(sc.rdir + N_GEO * pitch);
 #pragma unroll
-                for (int r = 0; r < D; r++)
-                    w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d], d);
-            } else if (d) {
+                    for (int r = 0; r < D; r++) {
+                        const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * pitch + i);
+                        w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], d);
+                    }
+                } else {
 #pragma unroll
-                for (int r = 0; r < D; r++)
-                    w[r] = restore_param(w[r], __ldg(sc.m + r * pitch + i), __ldg(sc.v + r * pitch + i),
-                                         L.param[lr_group(r)][d], d, L.eps);
+                    for (int r = 0; r < D; r++)
+                        w[r] = restore_param(w[r], ld_val(mp + r * pitch + i), ld_val(vp + r * pitch + i),
+                                             L.param[lr_group(r)][d], d, L.eps);
+                }
             }
         }
 #pragma unroll
         for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = w[r];
         Proj P;
         project_gaussian(w, s_cam, P);
+        fix_flag[k] = (uint8_t)P.fp64;
+        if (P.fp64) fix_idx[atomicAdd(n_fix, 1)] = k;      // conic, radius and rect redone in FP64
         float vx = w[0] - s_cam.campos[0], vy = w[1] - s_cam.campos[1], vz = w[2] - s_cam.campos[2];
         float ivn = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
         float Y[16];
@@ -106,6 +119,36 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         dval[k] = (uint32_t)k;
         uint32_t cnt = P.keep ? (uint32_t)((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2])) : 0u;
         tcnt[k] = cnt;
+        rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
+    }
+}
+
+// FP64 fix-up of the Gaussians the gather flagged (badly conditioned 2D
+// covariance): conic, radius, tile rectangle and key count from the FP64
+// chain, before the keys are counted.  Opacity, colour and depth are unchanged.
+__global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restrict__ compact, int cap,
+                                                            const int *__restrict__ n_fix,
+                                                            const int32_t *__restrict__ fix_idx,
+                                                            const DevArgs *__restrict__ args, int view, float4 *rec0,
+                                                            float4 *rec1, uint32_t *tcnt, uint2 *rect)
+{
+    __shared__ DevCam s_cam;
+    if (threadIdx.x < sizeof(DevCam) / 4)
+        ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
+    __syncthreads();
+    const int nf = min(*n_fix, cap);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+        const int k = fix_idx[j];
+        float g[N_GEO];
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) g[r] = compact[r * (int64_t)cap + k];
+        Proj P;
+        P.conA = P.conB = P.conC = 0.f;
+        project_gaussian<true>(g, s_cam, P);
+        const float o = rec0[k].w;
+        rec0[k] = make_float4(P.mx, P.my, P.radius, o);
+        rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
+        tcnt[k] = P.keep ? (uint32_t)((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2])) : 0u;
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
 }
@@ -573,13 +616,19 @@ bool raster_variant_ok(int v, int tile_w, int tile_h)
 
 // ---------------------------------------------------------------------------
 // Chain rule of the projection (FP32 counterpart of the adjoint in §2.4 step 5).
+// FIX = false: every visible Gaussian except those the gather flagged for the
+// FP64 chain; FIX = true: the flagged ones, with the adjoint of the 2D
+// covariance in FP64.
+template <bool FIX>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restrict__ compact, int cap, int deg,
                                                             const int *n_vis_p, const DevArgs *__restrict__ args, int view,
                                                             const float *__restrict__ g9, float *__restrict__ grad,
                                                             int64_t gcap, const int32_t *__restrict__ ids,
                                                             const uint32_t *__restrict__ rmask,
                                                             const uint32_t *__restrict__ rprefix, int accumulate,
-                                                            int *status)
+                                                            int *status, const int *__restrict__ n_fix,
+                                                            const int32_t *__restrict__ fix_idx,
+                                                            const uint8_t *__restrict__ fix_flag)
 {
     __shared__ DevCam s_cam;
     if (threadIdx.x < sizeof(DevCam) / 4)
@@ -589,7 +638,10 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
     const int nk = (deg + 1) * (deg + 1);
     const int D = N_GEO + 3 * nk;
     const DevCam &cam = s_cam;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_vis; k += gridDim.x * blockDim.x) {
+    const int n_items = FIX ? min(*n_fix, n_vis) : n_vis;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_items; j += gridDim.x * blockDim.x) {
+        const int k = FIX ? fix_idx[j] : j;
+        if (!FIX && fix_flag[k]) continue;
         int64_t kk = k;
         if (rmask) {
             int64_t i = ids[k];
@@ -608,7 +660,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
 #pragma unroll
         for (int f = 0; f < 9; f++) gs[f] = g9[f * (int64_t)cap + k];
         Proj P;
-        project_gaussian(g, cam, P);
+        project_gaussian<FIX>(g, cam, P);   // as in the forward (FIX: the FP64 chain)
         float out[N_GEO];
 #pragma unroll
         for (int r = 0; r < N_GEO; r++) out[r] = 0.f;
@@ -647,61 +699,104 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
             // ---- opacity logit
             float o = 1.f / (1.f + expf(-g[ROW_OPAC]));
             out[ROW_OPAC] = gs[5] * o * (1.f - o);
-            // ---- conic -> covariance (a, b, c)
-            float a = P.a, b = P.b, c = P.c;
-            float id2 = 1.f / (P.det * P.det);
-            float gA = gs[2], gB = gs[3], gC = gs[4];
-            float ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
-            float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * id2;
-            float gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
-            float hb = 0.5f * gb;
-            // ---- Sigma2 = T Sigma3 T^T + 0.3 I
-            const float *T = P.T;
-            // gS3 = ga t0 t0^T + hb (t0 t1^T + t1 t0^T) + gc t1 t1^T (symmetric)
-            float gS[9];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int q = 0; q < 3; q++)
-                    gS[r * 3 + q] = ga * T[r] * T[q] + hb * (T[r] * T[3 + q] + T[3 + r] * T[q]) + gc * T[3 + r] * T[3 + q];
-            // gT = 2 G2 T Sigma3
-            float S3f[9] = {P.S3[0], P.S3[1], P.S3[2], P.S3[1], P.S3[3], P.S3[4], P.S3[2], P.S3[4], P.S3[5]};
-            float e0[3], e1[3];
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                e0[q] = 2.f * (ga * T[q] + hb * T[3 + q]);
-                e1[q] = 2.f * (hb * T[q] + gc * T[3 + q]);
-            }
-            float gT[6];
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                gT[q] = e0[0] * S3f[0 * 3 + q] + e0[1] * S3f[1 * 3 + q] + e0[2] * S3f[2 * 3 + q];
-                gT[3 + q] = e1[0] * S3f[0 * 3 + q] + e1[1] * S3f[1 * 3 + q] + e1[2] * S3f[2 * 3 + q];
-            }
-            // gJ = gT W^T (entries 00, 02, 11, 12)
-            const float *R = cam.R;
-            float gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
-            float gJ02 = gT[0] * R[6] + gT[1] * R[7] + gT[2] * R[8];
-            float gJ11 = gT[3] * R[3] + gT[4] * R[4] + gT[5] * R[5];
-            float gJ12 = gT[3] * R[6] + gT[4] * R[7] + gT[5] * R[8];
-            float pxc = P.p[0], pyc = P.p[1], pz = P.p[2];
-            float iz = 1.f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
-            float fx = cam.fx, fy = cam.fy;
             float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
-            gp2 += -(gJ00 * fx + gJ11 * fy) * iz2;
-            if (!P.cu) {
-                gp0 += -gJ02 * fx * iz2;
-                gp2 += 2.f * gJ02 * fx * pxc * iz3;
+            const float *R = cam.R;
+            float pxc = P.p[0], pyc = P.p[1], pz = P.p[2];
+            float iz = 1.f / pz, iz2 = iz * iz;
+            float fx = cam.fx, fy = cam.fy;
+            if (FIX) {
+                Geo10 G;
+#pragma unroll
+                for (int k = 0; k < 10; k++) G.v[k] = g[k];
+                const CovGrad cg = cov_chain_bwd_fp64(G, cam, gs[2], gs[3], gs[4]);
+                gp0 = cg.gp[0]; gp1 = cg.gp[1]; gp2 = cg.gp[2];
+#pragma unroll
+                for (int k = 0; k < 3; k++) out[ROW_LS + k] = cg.gls[k];
+#pragma unroll
+                for (int k = 0; k < 4; k++) out[ROW_QUAT + k] = cg.gq[k];
             } else {
-                float lim = pxc > 0.f ? cam.limx : -cam.limx;
-                gp2 += gJ02 * fx * lim * iz2;
-            }
-            if (!P.cw) {
-                gp1 += -gJ12 * fy * iz2;
-                gp2 += 2.f * gJ12 * fy * pyc * iz3;
-            } else {
-                float lim = pyc > 0.f ? cam.limy : -cam.limy;
-                gp2 += gJ12 * fy * lim * iz2;
+                // ---- conic -> covariance (a, b, c)
+                float a = P.a, b = P.b, c = P.c;
+                float id2 = 1.f / (P.det * P.det);
+                float gA = gs[2], gB = gs[3], gC = gs[4];
+                float ga = (-c * c * gA + b * c * gB - b * b * gC) * id2;
+                float gb = (2.f * b * c * gA - (a * c + b * b) * gB + 2.f * a * b * gC) * id2;
+                float gc = (-b * b * gA + a * b * gB - a * a * gC) * id2;
+                float hb = 0.5f * gb;
+                // ---- Sigma2 = T Sigma3 T^T + 0.3 I
+                const float *T = P.T;
+                // gS3 = ga t0 t0^T + hb (t0 t1^T + t1 t0^T) + gc t1 t1^T (symmetric)
+                float gS[9];
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int q = 0; q < 3; q++)
+                        gS[r * 3 + q] = ga * T[r] * T[q] + hb * (T[r] * T[3 + q] + T[3 + r] * T[q]) + gc * T[3 + r] * T[3 + q];
+                // gT = 2 G2 T Sigma3
+                float S3f[9] = {P.S3[0], P.S3[1], P.S3[2], P.S3[1], P.S3[3], P.S3[4], P.S3[2], P.S3[4], P.S3[5]};
+                float e0[3], e1[3];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    e0[q] = 2.f * (ga * T[q] + hb * T[3 + q]);
+                    e1[q] = 2.f * (hb * T[q] + gc * T[3 + q]);
+                }
+                float gT[6];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    gT[q] = e0[0] * S3f[0 * 3 + q] + e0[1] * S3f[1 * 3 + q] + e0[2] * S3f[2 * 3 + q];
+                    gT[3 + q] = e1[0] * S3f[0 * 3 + q] + e1[1] * S3f[1 * 3 + q] + e1[2] * S3f[2 * 3 + q];
+                }
+                // gJ = gT W^T (entries 00, 02, 11, 12)
+                float gJ00 = gT[0] * R[0] + gT[1] * R[1] + gT[2] * R[2];
+                float gJ02 = gT[0] * R[6] + gT[1] * R[7] + gT[2] * R[8];
+                float gJ11 = gT[3] * R[3] + gT[4] * R[4] + gT[5] * R[5];
+                float gJ12 = gT[3] * R[6] + gT[4] * R[7] + gT[5] * R[8];
+                float iz3 = iz2 * iz;
+                gp2 += -(gJ00 * fx + gJ11 * fy) * iz2;
+                if (!P.cu) {
+                    gp0 += -gJ02 * fx * iz2;
+                    gp2 += 2.f * gJ02 * fx * pxc * iz3;
+                } else {
+                    float lim = pxc > 0.f ? cam.limx : -cam.limx;
+                    gp2 += gJ02 * fx * lim * iz2;
+                }
+                if (!P.cw) {
+                    gp1 += -gJ12 * fy * iz2;
+                    gp2 += 2.f * gJ12 * fy * pyc * iz3;
+                } else {
+                    float lim = pyc > 0.f ? cam.limy : -cam.limy;
+                    gp2 += gJ12 * fy * lim * iz2;
+                }
+                // Sigma3 = M M^T, M = Rq diag(s): gM = 2 gS M
+                float M[9];
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int q = 0; q < 3; q++) M[r * 3 + q] = P.Rq[r * 3 + q] * P.s[q];
+                float gR[9];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    float gsc = 0.f;
+#pragma unroll
+                    for (int r = 0; r < 3; r++) {
+                        float gm = 2.f * (gS[r * 3 + 0] * M[0 * 3 + q] + gS[r * 3 + 1] * M[1 * 3 + q] + gS[r * 3 + 2] * M[2 * 3 + q]);
+                        gsc += gm * P.Rq[r * 3 + q];
+                        gR[r * 3 + q] = gm * P.s[q];
+                    }
+                    out[ROW_LS + q] = gsc * P.s[q];
+                }
+                // rotation -> normalised quaternion -> quaternion
+                float qw = P.qh[0], qx = P.qh[1], qy = P.qh[2], qz = P.qh[3];
+                float gw = -2.f * qz * gR[1] + 2.f * qy * gR[2] + 2.f * qz * gR[3] - 2.f * qx * gR[5] - 2.f * qy * gR[6] + 2.f * qx * gR[7];
+                float gx = 2.f * qy * gR[1] + 2.f * qz * gR[2] + 2.f * qy * gR[3] - 4.f * qx * gR[4] - 2.f * qw * gR[5] + 2.f * qz * gR[6] + 2.f * qw * gR[7] - 4.f * qx * gR[8];
+                float gy = -4.f * qy * gR[0] + 2.f * qx * gR[1] + 2.f * qw * gR[2] + 2.f * qx * gR[3] + 2.f * qz * gR[5] - 2.f * qw * gR[6] + 2.f * qz * gR[7] - 4.f * qy * gR[8];
+                float gz = -4.f * qz * gR[0] - 2.f * qw * gR[1] + 2.f * qx * gR[2] + 2.f * qw * gR[3] - 4.f * qz * gR[4] + 2.f * qy * gR[5] + 2.f * qx * gR[6] + 2.f * qy * gR[7];
+                float dq = gw * qw + gx * qx + gy * qy + gz * qz;
+                float iqn = 1.f / P.qn;
+                out[ROW_QUAT + 0] = (gw - qw * dq) * iqn;
+                out[ROW_QUAT + 1] = (gx - qx * dq) * iqn;
+                out[ROW_QUAT + 2] = (gy - qy * dq) * iqn;
+                out[ROW_QUAT + 3] = (gz - qz * dq) * iqn;
             }
             // mean2d
             gp0 += gs[0] * fx * iz;
@@ -711,36 +806,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
             gmu[0] += R[0] * gp0 + R[3] * gp1 + R[6] * gp2;
             gmu[1] += R[1] * gp0 + R[4] * gp1 + R[7] * gp2;
             gmu[2] += R[2] * gp0 + R[5] * gp1 + R[8] * gp2;
-            // Sigma3 = M M^T, M = Rq diag(s): gM = 2 gS M
-            float M[9];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int q = 0; q < 3; q++) M[r * 3 + q] = P.Rq[r * 3 + q] * P.s[q];
-            float gR[9];
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                float gsc = 0.f;
-#pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    float gm = 2.f * (gS[r * 3 + 0] * M[0 * 3 + q] + gS[r * 3 + 1] * M[1 * 3 + q] + gS[r * 3 + 2] * M[2 * 3 + q]);
-                    gsc += gm * P.Rq[r * 3 + q];
-                    gR[r * 3 + q] = gm * P.s[q];
-                }
-                out[ROW_LS + q] = gsc * P.s[q];
-            }
-            // rotation -> normalised quaternion -> quaternion
-            float qw = P.qh[0], qx = P.qh[1], qy = P.qh[2], qz = P.qh[3];
-            float gw = -2.f * qz * gR[1] + 2.f * qy * gR[2] + 2.f * qz * gR[3] - 2.f * qx * gR[5] - 2.f * qy * gR[6] + 2.f * qx * gR[7];
-            float gx = 2.f * qy * gR[1] + 2.f * qz * gR[2] + 2.f * qy * gR[3] - 4.f * qx * gR[4] - 2.f * qw * gR[5] + 2.f * qz * gR[6] + 2.f * qw * gR[7] - 4.f * qx * gR[8];
-            float gy = -4.f * qy * gR[0] + 2.f * qx * gR[1] + 2.f * qw * gR[2] + 2.f * qx * gR[3] + 2.f * qz * gR[5] - 2.f * qw * gR[6] + 2.f * qz * gR[7] - 4.f * qy * gR[8];
-            float gz = -4.f * qz * gR[0] - 2.f * qw * gR[1] + 2.f * qx * gR[2] + 2.f * qw * gR[3] - 4.f * qz * gR[4] + 2.f * qy * gR[5] + 2.f * qx * gR[6] + 2.f * qy * gR[7];
-            float dq = gw * qw + gx * qx + gy * qy + gz * qz;
-            float iqn = 1.f / P.qn;
-            out[ROW_QUAT + 0] = (gw - qw * dq) * iqn;
-            out[ROW_QUAT + 1] = (gx - qx * dq) * iqn;
-            out[ROW_QUAT + 2] = (gy - qy * dq) * iqn;
-            out[ROW_QUAT + 3] = (gz - qz * dq) * iqn;
         }
         out[0] = ok ? gmu[0] : 0.f;
         out[1] = ok ? gmu[1] : 0.f;
@@ -803,10 +868,17 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
                     Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
-    auto gp = sc.deg == 3 ? k_gather_project<3> : sc.deg == 2 ? k_gather_project<2>
-            : sc.deg == 1 ? k_gather_project<1> : k_gather_project<0>;
+    auto gp = sc.prec == GS_FP32
+                  ? (sc.deg == 3 ? k_gather_project<3, float> : sc.deg == 2 ? k_gather_project<2, float>
+                     : sc.deg == 1 ? k_gather_project<1, float> : k_gather_project<0, float>)
+                  : (sc.deg == 3 ? k_gather_project<3, __nv_bfloat16> : sc.deg == 2 ? k_gather_project<2, __nv_bfloat16>
+                     : sc.deg == 1 ? k_gather_project<1, __nv_bfloat16> : k_gather_project<0, __nv_bfloat16>);
+    cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
-                                                          rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect);
+                                                          rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect, rb.n_fix,
+                                                          rb.fix_idx, rb.fix_flag);
+    k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
+                                                    rb.tcnt, rb.rect);
     // depth order of the visible set (stable: ties keep ascending index)
     int dcur = radix_sort(rb.dk[0], rb.dv[0], rb.dk[1], rb.dv[1], n_vis, cap, 32, w, s);
     const uint32_t *dsorted = rb.dv[dcur];
@@ -856,9 +928,12 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
         bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
             rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, nullptr);
     if (view == 0) w.mark(TP_RBWD1, s);
-    k_project_bwd<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9,
-                                                                     grad, gcap, ids, remap_mask, remap_prefix,
-                                                                     accumulate ? 1 : 0, w.status);
+    k_project_bwd<false><<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
+        rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix,
+        accumulate ? 1 : 0, w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
+    k_project_bwd<true><<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap,
+                                                          ids, remap_mask, remap_prefix, accumulate ? 1 : 0, w.status,
+                                                          rb.n_fix, rb.fix_idx, rb.fix_flag);
 }
 
 }  // namespace gs

@@ -48,6 +48,15 @@ def _case(name):
     if name == "degenerate":
         c = scenes.cfg_diff_check(n=8000, width=96)
         return c["scene"], c["cams"][0], 3, (16, 16)
+    if name == "needles":
+        # long thin Gaussians at random orientations: a near-singular 2D
+        # covariance (diagonal in the image) or a needle seen end-on, where the
+        # FP32 covariance chain loses 10+ bits and the FP64 path takes over
+        P = scenes.uniform_cube_scene(1200, seed=12, sh_degree=1, log_scale_mean=-3.0)
+        P[3] = -0.8
+        P[4:6] = -7.5
+        cam = scenes.camera_lookat((0.2, -0.3, -3.2), (0.0, 0.0, 0.0), 96, 72, 60.0, up=(0, -1, 0))
+        return P, cam, 1, (16, 16)
     raise KeyError(name)
 
 
@@ -73,24 +82,28 @@ def _run_fwd(gs, orc, name):
 def _pixel_exclusions(r, gpu_ids=None):
     """Pixels whose value may legitimately differ between FP32 and FP64: a
     near-tie among the decisions that can change the pixel (square test of a
-    contributing Gaussian, the 1/255 floor, the transmittance stop), or inside
-    the 3-sigma square of a Gaussian whose integer radius or keep decision is a
-    near-tie."""
+    contributing Gaussian, the 1/255 floor, the transmittance stop), the ring
+    of pixels where a Gaussian's 3-sigma square test flips when its integer
+    radius is a near-tie, or the whole square of a Gaussian whose keep decision
+    differs (a near-tie of the cull)."""
     ex = r["margin"] < TIE_TOL
     sp = r["splats"]
     H, W = ex.shape
-    flagged = (sp["radius_margin"] < TIE_TOL) & (sp["keep"] == 1)
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    ring = (sp["radius_margin"] < TIE_TOL) & (sp["keep"] == 1)
+    whole = np.zeros_like(ring)
     if gpu_ids is not None:
-        diff = np.setxor1d(gpu_ids, np.nonzero(sp["keep"])[0])
-        flagged[diff] = True
-    for i in np.nonzero(flagged)[0]:
+        whole[np.setxor1d(gpu_ids, np.nonzero(sp["keep"])[0])] = True
+    for i in np.nonzero(ring | whole)[0]:
         mx, my = sp["mean2d"][i]
-        rr = sp["radius"][i] + 1
-        if not (np.isfinite(mx) and np.isfinite(my) and rr > 1):
+        rr = sp["radius"][i]
+        if not (np.isfinite(mx) and np.isfinite(my) and rr > 0):
             continue
-        x0, x1 = int(max(0, np.floor(mx - rr))), int(min(W, np.ceil(mx + rr)))
-        y0, y1 = int(max(0, np.floor(my - rr))), int(min(H, np.ceil(my + rr)))
-        ex[y0:y1, x0:x1] = True
+        dist = np.maximum(np.abs(xs - mx), np.abs(ys - my))
+        if whole[i]:
+            ex |= dist <= rr + 1.5
+        else:
+            ex |= np.abs(dist - rr) <= 1.01
     return ex
 
 
@@ -139,6 +152,53 @@ def test_render_forward_parity(gs, orc, name):
     assert ex.mean() < 0.03, f"too many tie pixels: {ex.mean()}"
     assert err[ok].max() <= 1e-5, (err[ok].max(), np.unravel_index(np.argmax(np.where(ok, err, 0)), err.shape))
     assert ref.max() > 0.05
+    n_fp64 = int(d["ctx"].counters()[6].item())
+    assert n_fp64 <= 0.01 * len(d["gids"]), n_fp64        # rare on moderately anisotropic scenes
+
+
+def test_fp64_covariance_needles(gs, orc):
+    """Long thin Gaussians (one axis 0.45, two 5.5e-4) at random orientations:
+    the FP32 covariance chain would leave a relative conic error of about
+    u * (a + c) * tr(Sigma3) * |T|^2 / det, here up to 1.5e-4, so every one of
+    them goes through the FP64 chain, whose conic must agree with the FP64
+    oracle to FP32 rounding.  The image and the gradients are then bounded by
+    what FP32 compositing allows: sigma at a pixel sums terms of up to
+    sigma_abs = (|A| + 2|B| + |C|) r^2 / 2 that cancel, so alpha and its
+    derivatives carry a relative error of up to about 8 u sigma_abs."""
+    d = _run_fwd(gs, orc, "needles")
+    r, ctx, gids = d["r"], d["ctx"], d["gids"]
+    sp = r["splats"]
+    geom, conic = ctx.render_splats()
+    geom = geom.cpu().numpy().astype(np.float64)
+    conic = conic.cpu().numpy().astype(np.float64)
+    n_fp64 = int(ctx.counters()[6].item())
+    kept = sp["keep"][gids] == 1
+    assert n_fp64 >= 0.9 * len(gids) and kept.sum() > 0.9 * len(gids), (n_fp64, len(gids))
+    ref_c = sp["conic"][gids][kept]
+    scale = np.abs(ref_c[:, 0]) + np.abs(ref_c[:, 2])
+    cerr = np.abs(conic[kept, :3] - ref_c) / scale[:, None]
+    assert cerr.max() <= 4e-7, cerr.max()
+    assert np.abs(geom[kept, :2] - sp["mean2d"][gids][kept]).max() <= 1e-4
+    tie = sp["radius_margin"][gids][kept] < TIE_TOL
+    assert np.all((geom[kept, 2] == sp["radius"][gids][kept]) | tie)
+    # image and gradients within the FP32-compositing bound
+    con, rad = sp["conic"][sp["keep"] == 1], sp["radius"][sp["keep"] == 1]
+    sabs = 0.5 * (np.abs(con[:, 0]) + 2 * np.abs(con[:, 1]) + np.abs(con[:, 2])) * rad ** 2
+    bound = 8 * 2.0 ** -24 * sabs.max()
+    ex = _pixel_exclusions(r, gids)
+    assert ex.mean() < 0.1, ex.mean()
+    err = np.abs(d["img"] - r["image"])[:, ~ex]
+    assert err.max() <= bound, (err.max(), bound)
+    P, cam, deg, tile = d["P"], d["cam"], d["deg"], d["tile"]
+    target = _target(orc, P, cam, deg, tile, seed=11)
+    _, dimg = orc.loss_l1(r["image"], target)
+    g_ref, _ = orc.backward(f32(P), deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], dimg)
+    gc = ctx.render_bwd(torch.as_tensor(dimg, dtype=torch.float32, device="cuda"), P.shape[0])
+    full = ctx.grad_scatter(d["scene"], d["ids"], d["nv"], gc)
+    ctx.sync_status()
+    g_gpu = full[:, :P.shape[1]].cpu().numpy().astype(np.float64)
+    errs = {k: rel_group_error(g_gpu, g_ref, s) for k, s in GROUPS.items() if g_ref[s].size}
+    assert max(errs.values()) <= bound, (errs, bound)
 
 
 def _target(orc, P_like, cam, deg, tile, seed):
@@ -327,18 +387,21 @@ def test_materialize_parity(gs, orc):
     assert np.all(np.abs(gw - W) <= bound + 1e-30), np.max(np.abs(gw - W) / (bound + 1e-30))
 
 
-def test_restore_directions(gs):
-    """The stored restore directions equal m / (sqrt(v) + eps) (within the
-    2-ulp divide used for them) after refresh and after optimizer steps, and
-    culling / rendering through them is bit-identical to recomputing the
-    restore from m and v."""
+@pytest.mark.parametrize("bf16", [False, True])
+def test_restore_directions(gs, bf16):
+    """The kept restore directions equal m / (sqrt(v) + eps) (rounded to the
+    plane's type: fp32 geometry planes, SH planes in the SH type) after a
+    refresh and after optimizer steps, and restoring through them gives the
+    same cull and (fp32 form) the same image as recomputing from m and v."""
+    from paper_2509_15645_b300 import _lib
     rng = np.random.default_rng(12)
     n, deg = 6000, 1
     P = scenes.uniform_cube_scene(n, seed=12, sh_degree=deg, log_scale_mean=-3.0)
-    scene = gs.GaussianScene(P, deg)
+    scene = gs.GaussianScene(P, deg, precision=_lib.GS_BF16_SH_MOM if bf16 else _lib.GS_FP32)
     D = scene.D
-    scene.m[:, :n] = torch.as_tensor(rng.normal(size=(D, n)) * 1e-2, dtype=torch.float32, device="cuda")
-    scene.v[:, :n] = torch.as_tensor(rng.uniform(1e-8, 1e-5, (D, n)), dtype=torch.float32, device="cuda")
+    mdt = scene.m.dtype
+    scene.m[:, :n] = torch.as_tensor(rng.normal(size=(D, n)) * 1e-2, dtype=torch.float32, device="cuda").to(mdt)
+    scene.v[:, :n] = torch.as_tensor(rng.uniform(1e-8, 1e-5, (D, n)), dtype=torch.float32, device="cuda").to(mdt)
     scene.counter[:n] = torch.as_tensor(rng.integers(0, 16, n), dtype=torch.uint8, device="cuda")
     scene.step = 30
     adam = gs.adam_struct(lr=1e-2, eps=1e-15)
@@ -346,30 +409,117 @@ def test_restore_directions(gs):
     ctx = make_ctx(gs, n, 96, 64, deg=deg)
     ctx.refresh_rdir(scene, adam)
     eps32 = np.float32(1e-15)
-
-    def expected(sc):
-        m = sc.m[:, :n].cpu().numpy()
-        v = sc.v[:, :n].cpu().numpy()
-        return m / (np.sqrt(v) + eps32)
-
     u32 = 2.0 ** -24                                    # the direction uses a 2-ulp divide
-    np.testing.assert_allclose(scene.rdir[:, :n].cpu().numpy(), expected(scene), rtol=6 * u32, atol=0)
+
+    def check(sc):
+        m = sc.m[:, :n].float().cpu().numpy()
+        v = sc.v[:, :n].float().cpu().numpy()
+        ref = m / (np.sqrt(v) + eps32)
+        np.testing.assert_allclose(sc.rdir_geo[:, :n].cpu().numpy(), ref[:11], rtol=6 * u32, atol=0)
+        rtol_sh = 2.0 ** -8 if bf16 else 6 * u32           # bf16: round to nearest of the fp32 quotient
+        np.testing.assert_allclose(sc.rdir_sh[:, :n].float().cpu().numpy(), ref[11:], rtol=rtol_sh, atol=0)
+
+    check(scene)
     ids_a, nv_a = ctx.cull(scene, cam, adam)
     img_a = ctx.render_fwd(scene, cam, ids_a, nv_a, adam)
-    rdir = scene.rdir
-    scene.rdir = None                                   # recompute from m and v
+    kept = scene.rdir_geo
+    scene.rdir_geo = None                               # recompute from m and v
     ids_b, nv_b = ctx.cull(scene, cam, adam)
     img_b = ctx.render_fwd(scene, cam, ids_b, nv_b, adam)
     ctx.sync_status()
+    scene.rdir_geo = kept
     assert nv_a.item() == nv_b.item() > 0
     assert torch.equal(ids_a[:nv_a.item()], ids_b[:nv_b.item()])
-    assert torch.equal(img_a, img_b)
-    scene.rdir = rdir
+    if bf16:   # SH restored through a bf16-rounded direction: a 2^-9 relative change of the restore step
+        assert (img_a - img_b).abs().max().item() < 1e-3
+    else:
+        assert torch.equal(img_a, img_b)
     gc = torch.as_tensor(rng.normal(size=(D, ctx.max_visible)) * 1e-3, dtype=torch.float32, device="cuda")
     for _ in range(3):
         ctx.adam_deferred(scene, ids_a, nv_a, gc, adam)
     ctx.sync_status()
-    np.testing.assert_allclose(scene.rdir[:, :n].cpu().numpy(), expected(scene), rtol=6 * u32, atol=0)
+    check(scene)
+
+
+def test_bf16_stochastic_rounding_keeps_decay(gs):
+    """With zero gradients each eager step multiplies v by 0.999, which is
+    below half a bf16 ulp: round-to-nearest rounds it back to v forever, while
+    stochastic rounding decays v by 0.999 per step on average."""
+    from paper_2509_15645_b300 import _lib
+    n, deg, steps = 200_000, 0, 60
+    rng = np.random.default_rng(4)
+    P = scenes.uniform_cube_scene(n, seed=4, sh_degree=deg)
+    ctx = make_ctx(gs, n, 32, 32, deg=deg)
+    out = {}
+    for prec in (_lib.GS_BF16_SH_MOM_RN, _lib.GS_BF16_SH_MOM):
+        scene = gs.GaussianScene(P, deg, precision=prec)
+        v0 = torch.as_tensor(rng.uniform(1.0, 2.0, (scene.D, n)), dtype=torch.float32, device="cuda")
+        scene.v[:, :n] = v0.to(torch.bfloat16)
+        v0 = scene.v[:, :n].float().clone()
+        scene.m.zero_()
+        ctx.refresh_rdir(scene, gs.adam_struct())
+        ids = torch.zeros(1, dtype=torch.int32, device="cuda")
+        nv = torch.zeros(1, dtype=torch.int32, device="cuda")
+        gc = torch.zeros(scene.D, 8, device="cuda")
+        for _ in range(steps):
+            ctx.adam_deferred(scene, ids, nv, gc, gs.adam_struct(mode=_lib.GS_ADAM_EAGER, seed=7))
+        ctx.sync_status()
+        out[prec] = (scene.v[:, :n].float() / v0).mean().item()
+    assert out[_lib.GS_BF16_SH_MOM_RN] == 1.0
+    assert abs(out[_lib.GS_BF16_SH_MOM] - 0.999 ** steps) < 2e-4, out
+
+
+def test_bf16_form_step_parity(gs, orc):
+    """A whole step of the precision form (bf16 SH coefficients and moments,
+    fp32 geometry and compositing, stochastic rounding of the stores) against
+    the FP64 oracle step from the same stored state, three steps in a row.  The
+    bf16 stores may differ from the exact values by less than one bf16 ulp
+    (2^-7 relative); everything held in fp32 keeps the FP32 bounds."""
+    from paper_2509_15645_b300 import _lib
+    c = scenes.cfg_small_step()
+    deg, tile = 3, (16, 16)
+    P = scenes.uniform_cube_scene(c["scene"].shape[1], seed=8, sh_degree=deg, log_scale_mean=-2.8)
+    cam = cam_f32(c["cams"][0])
+    n, D = P.shape[1], P.shape[0]
+    target = orc.render(f32(scenes.uniform_cube_scene(n, seed=9, sh_degree=deg, log_scale_mean=-2.8)), deg, cam,
+                        tile)["image"]
+    tgt = torch.as_tensor(target, dtype=torch.float32, device="cuda")
+    scene = gs.GaussianScene(P, deg, precision=_lib.GS_BF16_SH_MOM)
+    ctx = make_ctx(gs, n, cam.width, cam.height, deg=deg)
+    lr = 1e-3
+    adam = gs.adam_struct(lr=lr, eps=1e-15, seed=3)
+    hp = hp32(orc, lr=lr, eps=1e-15)
+    ub = 2.0 ** -7
+    for t in (1, 2, 3):
+        W = scene.params().cpu().numpy().astype(np.float64)
+        M = scene.m[:, :n].float().cpu().numpy().astype(np.float64)
+        V = scene.v[:, :n].float().cpu().numpy().astype(np.float64)
+        Cn = scene.counter[:n].cpu().numpy().copy()
+        W0 = W.copy()
+        Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)
+        rr = orc.render_loss_backward(Wcur, deg, cam, target, tile)
+        loss = ctx.step(scene, [cam], [tgt], adam)
+        ctx.sync_status()
+        assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
+        kept = np.nonzero(rr["splats"]["keep"])[0].astype(np.int32)
+        orc.adam_deferred(W, M, V, Cn, kept, rr["grad"][:, kept], t, hp)
+        np.testing.assert_array_equal(scene.counter[:n].cpu().numpy(), Cn)
+        gw = scene.params().cpu().numpy().astype(np.float64)
+        gm = scene.m[:, :n].float().cpu().numpy().astype(np.float64)
+        gv = scene.v[:, :n].float().cpu().numpy().astype(np.float64)
+        for k, s in GROUPS.items():
+            if not M[s].size:
+                continue
+            scale_m, scale_v = np.abs(M[s]).max(), np.abs(V[s]).max()
+            assert np.all(np.abs(gm[s] - M[s]) <= ub * np.abs(M[s]) + 2e-4 * scale_m), (t, k, "m")
+            assert np.all(np.abs(gv[s] - V[s]) <= ub * np.abs(V[s]) + 4e-4 * scale_v), (t, k, "v")
+        # geometry (fp32): the FP32 form's bound; SH (bf16): one ulp of the
+        # stored value plus a 2^-6 relative error of the step lr * m/sqrt(v)
+        assert np.max(np.abs(gw[:11] - W[:11])) <= 2e-3 * lr + 1e-6, t
+        err = np.abs(gw[11:] - W[11:])
+        assert np.all(err <= ub * np.abs(W[11:]) + 2 * ub * lr * (t + 1) + 1e-7), (t, np.max(err))
+        moved = np.abs(W[11:] - W0[11:]) > 0
+        assert moved.mean() > 0.1                      # the steps did update SH coefficients
 
 
 def test_deferred_trajectory_tracks_eager(gs, orc):
@@ -437,6 +587,32 @@ def test_step_parity(gs, orc):
             if M[s].size:
                 assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
         assert np.max(np.abs(gw - W)) <= 2e-3 * 1e-3 + 1e-6
+
+
+def test_step_timing_spans(gs):
+    """Stage timing inside gs_step: every span recorded, nested spans inside
+    the step, and timing re-enabled between steps (a new event set) works."""
+    c = scenes.cfg_small_step()
+    P, cam = c["scene"], cam_f32(c["cams"][0])
+    n = P.shape[1]
+    scene = gs.GaussianScene(P, 0)
+    ctx = make_ctx(gs, n, cam.width, cam.height, deg=0)
+    tgt = torch.zeros(3, cam.height, cam.width, device="cuda")
+    adam = gs.adam_struct()
+    for rounds in range(2):
+        ctx.timing_enable(4)
+        for _ in range(3):
+            ctx.step(scene, [cam], [tgt], adam)
+        sp = ctx.timing_read(4)
+        assert len(sp) == 3
+        for x in sp:
+            assert all(v >= 0 for v in x.values()), x
+            assert x["cull"] + x["fwd"] + x["bwd"] + x["adam"] <= x["step"] * 1.01 + 1e-3
+            assert x["adam_apply"] <= x["adam"] + 1e-3 and x["raster_bwd"] <= x["bwd"] + 1e-3
+    ctx.timing_enable(0)
+    ctx.step(scene, [cam], [tgt], adam)
+    ctx.sync_status()
+    assert scene.step == 7
 
 
 # ---------------------------------------------------------------------------- autograd
