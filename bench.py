@@ -89,7 +89,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- workload
 
-def build_workload(n, n_views, seed_views=2, density_of=None):
+def build_workload(n, n_views, seed_views=2, density_of=None, width=1920, height=1080):
     """The aerial workload; with density_of=N0 a scene of n Gaussians over the
     area that keeps the N0-Gaussian scene's density (same raster load per view)."""
     from synth import scenes
@@ -97,7 +97,8 @@ def build_workload(n, n_views, seed_views=2, density_of=None):
     if density_of:
         scale = 5.0 * math.sqrt(n / density_of)
         clusters = max(1, round(200 * n / density_of))
-    cfg = scenes.cfg_aerial(n=n, n_views=n_views, seed_views=seed_views, scale=scale, n_clusters=clusters)
+    cfg = scenes.cfg_aerial(n=n, n_views=n_views, seed_views=seed_views, scale=scale, n_clusters=clusters,
+                            width=width, height=height)
     tgt_scene = scenes.heightfield_scene(n, seed=1, half_extent=cfg["half_extent"], amplitude=20.0,
                                          wavelength=(20.0 * scale, 25.0 * scale), n_clusters=clusters)
     return cfg, tgt_scene
@@ -145,15 +146,47 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     N = args.gaussians
-    cfg, tgt_params = build_workload(N, args.views, seed_views=2 + rank, density_of=args.density_of)
+    IW, IH = (int(x) for x in args.image.split("x"))
+    vps = args.views_per_step
+    cfg, tgt_params = build_workload(N, args.views, seed_views=2 + rank, density_of=args.density_of, width=IW,
+                                     height=IH)
     cams = cfg["cams"]
     deg = cfg["sh_degree"]
     D = 11 + 3 * (deg + 1) ** 2
     H, W = cams[0].height, cams[0].width
 
     tile = tuple(int(x) for x in args.tile.split("x"))
-    ctx = gs.Context(max_gaussians=N, max_visible=int(N * 0.6), max_keys=160_000_000, max_width=W, max_height=H,
-                     tile=tile, max_views=1, max_sh_degree=deg, device=local)
+    # capacities: visible set and keys per view scale with the image area (a
+    # 10M-density aerial view of 1920x1080 sees ~0.65M Gaussians, ~3.4M keys)
+    area = W * H / (1920 * 1080)
+    max_vis = int(min(N, max(0.6 * N if not args.density_of else 0, 3_000_000 * area * (args.density_of or N) / 10e6)))
+    max_vis = int(min(N, max(max_vis, 1_000_000)))
+    max_keys = int(min(160_000_000, max(16_000_000, 20 * max_vis)))
+    ctx_kw = dict(max_gaussians=N, max_visible=max_vis, max_keys=max_keys, max_width=W, max_height=H, tile=tile,
+                  max_views=vps, max_sh_degree=deg)
+    # HBM budget: state that does not fit goes to the host tier (SH planes and
+    # their optimizer state in pinned host memory, streamed by gs_step)
+    tier, stage_chunks, plan = gs.GS_TIER_DEVICE, 0, None
+    if args.budget_gb:
+        prec0 = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
+        eb = 4 if prec0 == gs.GS_FP32 else 2
+        resident = N * (44 + (D - 11) * eb + 2 * D * eb + 44 + (D - 11) * eb + 1)
+        geo_only = N * (44 + 2 * 11 * eb + 44 + 1)
+        ws0 = gs.Context.workspace_bytes(**ctx_kw)
+        budget = args.budget_gb * 1e9
+        if resident + ws0 > budget:
+            R = 1 << args.chunk_shift
+            ring_chunk = 4 * (D - 11) * R * 4
+            stage_chunks = int((budget - geo_only - ws0) // ring_chunk)
+            if stage_chunks < 1:
+                raise SystemExit(f"budget {args.budget_gb} GB holds no staging ring")
+            tier = gs.GS_TIER_HOST_SH
+        plan = {"budget_gb": args.budget_gb, "resident_state_gb": round(resident / 1e9, 2),
+                "workspace_gb": round(ws0 / 1e9, 2),
+                "tier": "host_sh" if tier == gs.GS_TIER_HOST_SH else "device",
+                "device_state_gb": round((geo_only if tier else resident) / 1e9, 2),
+                "stage_chunks": stage_chunks, "chunk_rows": 1 << args.chunk_shift}
+    ctx = gs.Context(**ctx_kw, device=local, stage_chunks=stage_chunks, chunk_shift=args.chunk_shift)
     # targets: the seed-1 scene rendered by the same library (setup, untimed)
     tscene = gs.GaussianScene(tgt_params, deg, device=dev, with_optimizer=False)
     del tgt_params
@@ -173,14 +206,17 @@ def run_ours(args):
     peak, peak_src = _peaks()
     gbs = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms else None
 
+    def one_step(sc, s, tgt=None):
+        vs = [(s * vps + j) % len(cams) for j in range(vps)]
+        ctx.step(sc, [cams[v] for v in vs], tgt or [targets[v] for v in vs], adam, loss=loss)
+
     def timed_steps(sc):
         """W warm-up steps, then K steps between CUDA events on the launching
         stream (barrier + synchronize on both sides), clocks sampled meanwhile.
         Returns (ms over the K steps, max over ranks; per-step stage spans; clocks)."""
         ctx.timing_enable(tcap)
         for s in range(Wm):
-            v = s % len(cams)
-            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+            one_step(sc, s)
         ctx.sync_status()
         ctx.timing_read(tcap)            # discard warm-up timings
         clocks = ClockSampler(local)
@@ -192,8 +228,7 @@ def run_ours(args):
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for s in range(K):
-            v = (Wm + s) % len(cams)
-            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+            one_step(sc, Wm + s)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -212,22 +247,29 @@ def run_ours(args):
     def measure(precision):
         """Autotune, time K steps of one precision form, then an untimed pass
         over the views for the counts behind the algorithmic bytes and flops."""
-        sc = gs.GaussianScene(P0, deg, device=dev, precision=precision)
-        variant, variant_ms = ctx.autotune(sc, cams[0])     # rasterizer variant for this workload (untimed)
+        sc = gs.GaussianScene(P0, deg, device=dev, precision=precision, tier=tier)
+        if tier == gs.GS_TIER_DEVICE:
+            variant, variant_ms = ctx.autotune(sc, cams[0])     # rasterizer variant for this workload (untimed)
+        else:   # the autotuner renders a resident scene: tune on the geometry with a resident copy of the SH
+            variant, variant_ms = 1, [None] * 6
         if args.raster_variant is not None:
             ctx.set_raster_variant(args.raster_variant)
             variant = args.raster_variant
         ms_total, spans, clk = timed_steps(sc)
-        stats = []
+        stats, staged = [], []
         ctx.timing_enable(tcap)
-        for s in range(len(cams)):
-            v = (Wm + K + s) % len(cams)
+        for s in range(min(len(cams), 16 if tier == gs.GS_TIER_DEVICE else 4)):
             n_restore_geo = int((sc.counter[:N] > 0).sum().item())
-            ctx.step(sc, [cams[v]], [targets[v]], adam, loss=loss)
+            one_step(sc, Wm + K + s)
             c = ctx.counters().cpu().tolist()
             stats.append((c[0], c[1], c[2], n_restore_geo, c[6]))
+            if tier:
+                staged.append(ctx.host_tier_stats())
         ctx.timing_read(tcap)
-        pairs = np.array([ctx.raster_pair_counts(sc, cam) for cam in cams], np.float64)   # untimed
+        if tier == gs.GS_TIER_DEVICE:
+            pairs = np.array([ctx.raster_pair_counts(sc, cam) for cam in cams], np.float64)   # untimed
+        else:
+            pairs = np.full((1, 2), np.nan)
         st = {}
         for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd"):
             vals = [x[k] for x in spans if x[k] >= 0]
@@ -237,7 +279,9 @@ def run_ours(args):
              "n_upd": float(np.mean([x[2] for x in stats])), "n_rest": float(np.mean([x[3] for x in stats])),
              "n_fp64": float(np.mean([x[4] for x in stats])),
              "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
-             "kernels": ctx.step_kernel_count()}
+             "kernels": ctx.step_kernel_count(),
+             "staged_chunks": float(np.mean([x[0] for x in staged])) if staged else None,
+             "staged_bytes": float(np.mean([x[1] for x in staged])) if staged else None}
         b_cull, b_apply, b_select = algorithmic_bytes(N, D, m["n_vis"], m["n_upd"], m["n_rest"],
                                                       bf16=precision != gs.GS_FP32)
         m.update(b_cull=b_cull, b_apply=b_apply, b_select=b_select)
@@ -259,6 +303,8 @@ def run_ours(args):
         flops = FLOPS_CONTRIB * m["on_pairs"] + FLOPS_SQUARE * (m["sq_pairs"] - m["on_pairs"])
         cands = {"k_raster_bwd": st["raster_bwd"] or 0.0, "k_adam_apply": st["adam_apply"] or 0.0,
                  "k_cull": st["cull"] or 0.0}
+        if not np.isfinite(flops):
+            cands.pop("k_raster_bwd")      # no pair counts (host tier)
         dom = max(cands, key=cands.get)
         if dom == "k_raster_bwd":
             ach = flops / (st["raster_bwd"] * 1e-3) / 1e12
@@ -273,24 +319,27 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": round(b), "traffic": None}
 
     def e2e(sc):
-        """Steps/s through the public API with the step's target copied from
+        """Steps/s through the public API with the step's targets copied from
         pinned host memory and the loss read back, every step."""
         host_t = [t.cpu().pin_memory() for t in targets]
-        dev_t = torch.empty_like(targets[0])
+        dev_t = [torch.empty_like(targets[0]) for _ in range(vps)]
         host_loss = torch.zeros(1).pin_memory()
+
+        def e2e_step(s):
+            vs = [(s * vps + j) % len(cams) for j in range(vps)]
+            for j, v in enumerate(vs):
+                dev_t[j].copy_(host_t[v], non_blocking=True)
+            one_step(sc, s, tgt=dev_t)
+            host_loss.copy_(loss, non_blocking=True)
+
         ctx.timing_enable(0)
         for s in range(max(Wm, 3)):
-            dev_t.copy_(host_t[s % len(cams)], non_blocking=True)
-            ctx.step(sc, [cams[s % len(cams)]], [dev_t], adam, loss=loss)
-            host_loss.copy_(loss, non_blocking=True)
+            e2e_step(s)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for s in range(K):
-            v = s % len(cams)
-            dev_t.copy_(host_t[v], non_blocking=True)
-            ctx.step(sc, [cams[v]], [dev_t], adam, loss=loss)
-            host_loss.copy_(loss, non_blocking=True)
+            e2e_step(s)
         f1.record(stream)
         torch.cuda.synchronize()
         ms = f0.elapsed_time(f1)
@@ -300,9 +349,11 @@ def run_ours(args):
             ms = float(t.item())
         ctx.sync_status()
         return {"value": round(world * K / (ms / 1e3), 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4}
+                "h2d_bytes_per_step": int(targets[0].numel() * 4 * vps), "d2h_bytes_per_step": 4}
 
     main_prec = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
+    if args.budget_gb:
+        args.no_bf16 = True        # the memory plan was made for one form
     m = measure(main_prec)
     e2e_main = e2e(m["sc"])
     bf16 = None
@@ -318,8 +369,9 @@ def run_ours(args):
                 "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in mb["st"].items()},
                 "cull_adam": mb["cull_adam"], "roofline": roofline(mb), "clocks": mb["clk"],
                 "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 * 2 + D * 2 * 2 + 1}
-    if args.density_of:
-        cfg_note = f"aerial{N / 1e6:g}m_at_density_of_{args.density_of / 1e6:g}m_1080p_sh3"
+    if args.density_of or (IW, IH) != (1920, 1080) or vps != 1:
+        cfg_note = f"aerial{N / 1e6:g}m" + (f"_at_density_of_{args.density_of / 1e6:g}m" if args.density_of else "") + \
+            f"_{IW}x{IH}_sh3" + (f"_{vps}views" if vps > 1 else "")
     else:
         cfg_note = WORKLOAD
     K_ms = m["ms"]
@@ -328,10 +380,10 @@ def run_ours(args):
         "warmup": Wm, "ms_per_step": round(K_ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
         "config": {"workload": cfg_note, "gaussians": N, "image": f"{W}x{H}", "sh_degree": deg,
-                   "views_per_step": 1, "form": "bf16_sh_mom" if args.bf16_only else "plain_fp32",
+                   "views_per_step": vps, "memory_plan": plan, "form": "bf16_sh_mom" if args.bf16_only else "plain_fp32",
                    "adam": "deferred", "tile": args.tile,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (parameters+moments 7.1 GB), no flush",
+                   "l2": f"inputs larger than L2 (parameters + moments {N * D * 12 / 1e9:.1f} GB in fp32), no flush",
                    "visible_per_view": round(m["n_vis"]), "keys_per_view": round(m["n_keys"]),
                    "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
                    "square_pairs_per_view": round(m["sq_pairs"]), "contrib_pairs_per_view": round(m["on_pairs"]),
@@ -345,6 +397,10 @@ def run_ours(args):
         "gpu_launches": int(m["kernels"] * K),
         "bf16_form": bf16,
     }
+    if tier:
+        out["host_tier"] = {"staged_chunks_per_step": m["staged_chunks"], "chunk_rows": 1 << args.chunk_shift,
+                            "bytes_per_step": m["staged_bytes"],
+                            "pcie_gbs": m["staged_bytes"] / (K_ms / K * 1e-3) / 1e9 if m["staged_bytes"] else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, sample_frac=0.1)
     if rank == 0:
@@ -445,6 +501,11 @@ def main():
     ap.add_argument("--density-of", type=int, default=None,
                     help="scale the scene area so that --gaussians keeps the density of this many (profiling cases)")
     ap.add_argument("--tile", default="8x8", help="raster tile WxH (W in 4..64, W*H in 64, 128, 256)")
+    ap.add_argument("--image", default="1920x1080", help="view size WxH")
+    ap.add_argument("--views-per-step", type=int, default=1, help="views rendered and summed per training step")
+    ap.add_argument("--budget-gb", type=float, default=None,
+                    help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
+    ap.add_argument("--chunk-shift", type=int, default=15, help="log2 Gaussians per host-tier chunk")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:

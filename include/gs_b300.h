@@ -69,6 +69,17 @@ typedef enum {
  * decay of v from being rounded away; GS_BF16_SH_MOM_RN rounds to nearest. */
 enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
 
+/* Residency of a scene's state (§4.2 selective offloading).  GS_TIER_DEVICE:
+ * every plane in device memory.  GS_TIER_HOST_SH: the geometry and opacity
+ * planes with their moments and restore directions stay in device memory
+ * (geo, m, v, rdir then hold those 11 rows only, [11][pitch]); the SH planes
+ * with their m, v and restore directions live in pinned host memory (host_sh,
+ * host_m, host_v, host_rdir, each [D-11][pitch] of the SH type).  gs_step
+ * streams the chunks of 2^chunk_shift Gaussians that a step touches (the
+ * visible ones and the optimizer's update set) into the context's staging
+ * ring with cudaMemcpy2DAsync on a side stream, and the updated rows back. */
+enum { GS_TIER_DEVICE = 0, GS_TIER_HOST_SH = 1 };
+
 /* Adam variants: deferred with the restore tables of Fig. 10 (the method) or
  * eager (Eq. 1 on every Gaussian each step: the baseline the paper improves). */
 enum { GS_ADAM_DEFERRED = 0, GS_ADAM_EAGER = 2 };
@@ -86,25 +97,31 @@ typedef struct {
     int32_t width, height;
 } gs_camera;
 
-/* A Gaussian set with its optimizer state (all device pointers). */
+/* A Gaussian set with its optimizer state (device pointers, except host_*). */
 typedef struct {
     int64_t n;             /* number of Gaussians (< 2^31) */
     int64_t pitch;         /* elements between planes, >= n, multiple of 4 */
     int32_t sh_degree;     /* 0..3 */
     int32_t precision;     /* GS_FP32, GS_BF16_SH_MOM or GS_BF16_SH_MOM_RN (sh, m, v stored as bf16) */
     float *geo;            /* [11][pitch] fp32 */
-    void *sh;              /* [3 (L+1)^2][pitch] fp32 or bf16 */
-    void *m;               /* [D][pitch] fp32 or bf16, NULL = no optimizer state (render only) */
-    void *v;               /* [D][pitch] */
+    void *sh;              /* [3 (L+1)^2][pitch] fp32 or bf16 (unused in GS_TIER_HOST_SH) */
+    void *m;               /* [D][pitch] fp32 or bf16 ([11][pitch] in GS_TIER_HOST_SH), NULL = no optimizer
+                              state (render only) */
+    void *v;               /* like m */
     float *rdir;           /* restore direction m / (sqrt(v) + eps) of each parameter, kept by the optimizer
                               so a deferred restore is one multiply-add: [11][pitch] fp32 for the geometry
                               planes followed by [D-11][pitch] of the SH storage type (so [D][pitch] fp32 in
                               GS_FP32; 44 + 2 (D-11) bytes per pitch element in the BF16 forms).  Must equal
                               that expression, rounded to the plane's type (all zero when m = v = 0; see
-                              gs_refresh_rdir).  NULL: the kernels recompute it from m and v */
+                              gs_refresh_rdir).  GS_TIER_HOST_SH: the [11][pitch] geometry part only.  NULL:
+                              the kernels recompute it from m and v */
     uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
     int32_t step;          /* optimizer steps completed; the next step is step + 1 */
-    int32_t reserved;
+    int32_t tier;          /* GS_TIER_DEVICE or GS_TIER_HOST_SH */
+    void *host_sh;         /* GS_TIER_HOST_SH only: pinned host [D-11][pitch] SH planes, */
+    void *host_m;          /*   their first moments, */
+    void *host_v;          /*   second moments */
+    void *host_rdir;       /*   and restore directions (all of the SH type) */
 } gs_scene;
 
 /* Adam hyper-parameters (§4.3.2).  lr per parameter group:
@@ -126,6 +143,9 @@ typedef struct {
     int32_t tile_w, tile_h;  /* raster tile: tile_w in {4, 8, 16, 32, 64}, tile_w * tile_h in {32, 64, 128, 256} */
     int32_t max_views;       /* views per gs_step, 1..8 */
     int32_t max_sh_degree;   /* 0..3 */
+    int64_t stage_chunks;    /* staging ring of host-tier scenes, in chunks (0: no host tier) */
+    int32_t chunk_shift;     /* log2 Gaussians per chunk, 10..20 (0: 15) */
+    int32_t reserved;
 } gs_config;
 
 /* ------------------------------------------------------------------ context */
@@ -293,6 +313,10 @@ GS_API gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, co
  * *n_keys the count K, *ranges[2 * tiles] the [begin, end) of each tile. */
 GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key, const uint32_t **splat_of_key,
                                  const int32_t **n_keys, const uint32_t **ranges);
+
+/* Host tier: chunks staged by the last gs_step of a GS_TIER_HOST_SH scene and
+ * the bytes it moved between host and device (both directions). */
+GS_API gs_status gs_host_tier_stats(const gs_ctx *ctx, int64_t *chunks, int64_t *bytes);
 
 /* Inspection of the last gs_render_fwd: the projected splats of the visible
  * set in compact order (entry k belongs to ids[k]), device pointers owned by

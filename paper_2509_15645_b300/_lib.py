@@ -16,6 +16,7 @@ GS_FP32, GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN = 0, 1, 2
 RASTER_VARIANTS = 6
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
+GS_TIER_DEVICE, GS_TIER_HOST_SH = 0, 1
 
 
 class Camera(C.Structure):
@@ -26,7 +27,7 @@ class Camera(C.Structure):
 class Scene(C.Structure):
     _fields_ = [("n", c_i64), ("pitch", c_i64), ("sh_degree", c_i32), ("precision", c_i32), ("geo", c_vp),
                 ("sh", c_vp), ("m", c_vp), ("v", c_vp), ("rdir", c_vp), ("counter", c_vp), ("step", c_i32),
-                ("reserved", c_i32)]
+                ("tier", c_i32), ("host_sh", c_vp), ("host_m", c_vp), ("host_v", c_vp), ("host_rdir", c_vp)]
 
 
 class AdamCfg(C.Structure):
@@ -37,7 +38,7 @@ class AdamCfg(C.Structure):
 class Config(C.Structure):
     _fields_ = [("max_gaussians", c_i64), ("max_visible", c_i64), ("max_keys", c_i64), ("max_width", c_i32),
                 ("max_height", c_i32), ("tile_w", c_i32), ("tile_h", c_i32), ("max_views", c_i32),
-                ("max_sh_degree", c_i32)]
+                ("max_sh_degree", c_i32), ("stage_chunks", c_i64), ("chunk_shift", c_i32), ("reserved", c_i32)]
 
 
 EXPORTS = {
@@ -65,6 +66,7 @@ EXPORTS = {
                                 c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
+    "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
 }

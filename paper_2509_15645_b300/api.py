@@ -61,86 +61,118 @@ def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L
 
 
 class GaussianScene:
-    """A Gaussian set on the device with its optimizer state.
+    """A Gaussian set with its optimizer state.
 
     precision GS_FP32: ``w`` is one [D][pitch] float32 tensor (geometry planes
     then SH planes; ``geo`` and ``sh`` are views of it), m / v float32, and
     ``rdir`` [D][pitch] float32 restore directions.  BF16 forms: ``geo``
     [11][pitch] float32 (master copy), ``sh`` [D-11][pitch] bfloat16, m / v
     bfloat16; restore directions ``rdir_geo`` [11][pitch] float32 and
-    ``rdir_sh`` [D-11][pitch] bfloat16 (one buffer, in that order)."""
+    ``rdir_sh`` [D-11][pitch] bfloat16 (one buffer, in that order).
+
+    tier GS_TIER_HOST_SH: the geometry planes with their m, v (``m``, ``v``
+    [11][pitch]) and ``rdir_geo`` stay on the device; the SH planes ``sh`` and
+    their ``m_sh``, ``v_sh``, ``rdir_sh`` are pinned host tensors [D-11][pitch]
+    that gs_step streams (read them after ``Context.sync_status``)."""
 
     def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True,
-                 precision=L.GS_FP32):
+                 precision=L.GS_FP32, tier=L.GS_TIER_DEVICE):
         D, n = params.shape
         assert D == n_params(sh_degree)
-        self.n, self.sh_degree, self.D, self.precision = n, sh_degree, D, precision
+        self.n, self.sh_degree, self.D, self.precision, self.tier = n, sh_degree, D, precision, tier
         self.pitch = (n + 3) // 4 * 4
-        src = torch.as_tensor(params, dtype=torch.float32).to(device)
+        P = self.pitch
+        src = torch.as_tensor(params, dtype=torch.float32)
+        mdtype = torch.float32 if precision == L.GS_FP32 else torch.bfloat16
+        self.w = None
+        self.m = self.v = self.counter = None
+        self.m_sh = self.v_sh = None
+        self.rdir = self.rdir_geo = self.rdir_sh = None
+        host = tier == L.GS_TIER_HOST_SH
+        if host:
+            assert with_optimizer, "the host tier holds optimizer state"
+            pin = dict(device="cpu", pin_memory=True)
+            self.geo = torch.zeros(11, P, dtype=torch.float32, device=device)
+            self.geo[:, :n] = src[:11].to(device)
+            self.sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+            self.sh[:, :n] = src[11:].to(mdtype)
+            self.m = torch.zeros(11, P, dtype=mdtype, device=device)
+            self.v = torch.zeros(11, P, dtype=mdtype, device=device)
+            self.m_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+            self.v_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+            self.counter = torch.zeros(P, dtype=torch.uint8, device=device)
+            if with_rdir:
+                self.rdir_geo = torch.zeros(11, P, dtype=torch.float32, device=device)
+                self.rdir_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+            self.step = 0
+            return
+        src = src.to(device)
         if precision == L.GS_FP32:
-            self.w = torch.zeros(D, self.pitch, dtype=torch.float32, device=device)
+            self.w = torch.zeros(D, P, dtype=torch.float32, device=device)
             self.w[:, :n] = src
             self.geo, self.sh = self.w[:11], self.w[11:]
-            mdtype = torch.float32
         else:
-            self.w = None
-            self.geo = torch.zeros(11, self.pitch, dtype=torch.float32, device=device)
-            self.sh = torch.zeros(D - 11, self.pitch, dtype=torch.bfloat16, device=device)
+            self.geo = torch.zeros(11, P, dtype=torch.float32, device=device)
+            self.sh = torch.zeros(D - 11, P, dtype=torch.bfloat16, device=device)
             self.geo[:, :n] = src[:11]
             self.sh[:, :n] = src[11:].to(torch.bfloat16)
-            mdtype = torch.bfloat16
-        self.rdir = self.rdir_geo = self.rdir_sh = None
         if with_optimizer:
-            self.m = torch.zeros(D, self.pitch, dtype=mdtype, device=device)
-            self.v = torch.zeros(D, self.pitch, dtype=mdtype, device=device)
-            self.counter = torch.zeros(self.pitch, dtype=torch.uint8, device=device)
+            self.m = torch.zeros(D, P, dtype=mdtype, device=device)
+            self.v = torch.zeros(D, P, dtype=mdtype, device=device)
+            self.counter = torch.zeros(P, dtype=torch.uint8, device=device)
             if with_rdir:
                 # restore directions m / (sqrt(v) + eps), zero while m = v = 0:
                 # fp32 rows for the geometry planes, then rows of the SH type
-                gbytes = 11 * self.pitch * 4
-                buf = torch.zeros(gbytes + (D - 11) * self.pitch * mdtype.itemsize, dtype=torch.uint8, device=device)
+                gbytes = 11 * P * 4
+                buf = torch.zeros(gbytes + (D - 11) * P * mdtype.itemsize, dtype=torch.uint8, device=device)
                 self._rdir_buf = buf
-                self.rdir_geo = buf[:gbytes].view(torch.float32).view(11, self.pitch)
-                self.rdir_sh = buf[gbytes:].view(mdtype).view(D - 11, self.pitch)
-                self.rdir = buf.view(torch.float32).view(D, self.pitch) if precision == L.GS_FP32 else None
-        else:
-            self.m = self.v = self.counter = None
+                self.rdir_geo = buf[:gbytes].view(torch.float32).view(11, P)
+                self.rdir_sh = buf[gbytes:].view(mdtype).view(D - 11, P)
+                self.rdir = buf.view(torch.float32).view(D, P) if precision == L.GS_FP32 else None
         self.step = 0
 
     def struct(self) -> L.Scene:
         s = L.Scene()
-        s.n, s.pitch, s.sh_degree, s.precision = self.n, self.pitch, self.sh_degree, self.precision
+        s.n, s.pitch, s.sh_degree, s.precision, s.tier = self.n, self.pitch, self.sh_degree, self.precision, self.tier
         if self.w is not None:
             s.geo = self.w.data_ptr()
             s.sh = self.w.data_ptr() + 11 * self.pitch * 4
         else:
             s.geo = self.geo.data_ptr()
-            s.sh = self.sh.data_ptr()
+            s.sh = self.sh.data_ptr() if self.tier == L.GS_TIER_DEVICE else None
         s.m = self.m.data_ptr() if self.m is not None else None
         s.v = self.v.data_ptr() if self.v is not None else None
         s.rdir = self.rdir_geo.data_ptr() if self.rdir_geo is not None else None
         s.counter = self.counter.data_ptr() if self.counter is not None else None
+        if self.tier == L.GS_TIER_HOST_SH:
+            s.host_sh, s.host_m, s.host_v = self.sh.data_ptr(), self.m_sh.data_ptr(), self.v_sh.data_ptr()
+            s.host_rdir = self.rdir_sh.data_ptr() if self.rdir_sh is not None else None
         s.step = self.step
         return s
 
     def params(self):
-        """Stored parameters as float32 [D][n]."""
+        """Stored parameters as float32 [D][n] on the geometry's device."""
         if self.w is not None:
             return self.w[:, :self.n]
-        return torch.cat([self.geo[:, :self.n], self.sh[:, :self.n].float()])
+        return torch.cat([self.geo[:, :self.n], self.sh[:, :self.n].to(self.geo.device).float()])
+
+    def moments(self):
+        """(m, v) as float32 [D][n] on the geometry's device."""
+        if self.tier == L.GS_TIER_HOST_SH:
+            dev = self.geo.device
+            return (torch.cat([self.m[:, :self.n].float(), self.m_sh[:, :self.n].to(dev).float()]),
+                    torch.cat([self.v[:, :self.n].float(), self.v_sh[:, :self.n].to(dev).float()]))
+        return self.m[:, :self.n].float(), self.v[:, :self.n].float()
 
 
 class Context:
     """One gs_ctx: scratch workspace (a torch allocation) and the hot-path calls."""
 
     def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
-                 max_sh_degree=3, device=0):
+                 max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0):
         self.lib = L.load()
-        cfg = L.Config()
-        cfg.max_gaussians, cfg.max_visible, cfg.max_keys = int(max_gaussians), int(max_visible), int(max_keys)
-        cfg.max_width, cfg.max_height = int(max_width), int(max_height)
-        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
-        cfg.max_views, cfg.max_sh_degree = int(max_views), int(max_sh_degree)
+        cfg = self._config(max_gaussians, max_visible, max_keys, max_width, max_height, tile, max_views,
+                           max_sh_degree, stage_chunks, chunk_shift)
         self.cfg = cfg
         nb = C.c_size_t(0)
         self._check(self.lib.gs_workspace_size(C.byref(cfg), C.byref(nb)), "workspace size")
@@ -150,6 +182,27 @@ class Context:
         self._check(self.lib.gs_create(C.byref(h), C.byref(cfg), device, _ptr(self.workspace), nb.value), "create")
         self.h = h
         self.max_visible = int(max_visible)
+
+    @staticmethod
+    def _config(max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
+                max_sh_degree=3, stage_chunks=0, chunk_shift=0):
+        cfg = L.Config()
+        cfg.stage_chunks, cfg.chunk_shift = int(stage_chunks), int(chunk_shift)
+        cfg.max_gaussians, cfg.max_visible, cfg.max_keys = int(max_gaussians), int(max_visible), int(max_keys)
+        cfg.max_width, cfg.max_height = int(max_width), int(max_height)
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+        cfg.max_views, cfg.max_sh_degree = int(max_views), int(max_sh_degree)
+        return cfg
+
+    @staticmethod
+    def workspace_bytes(**kw):
+        """Device workspace a context with these arguments would take."""
+        cfg = Context._config(**kw)
+        nb = C.c_size_t(0)
+        st = L.load().gs_workspace_size(C.byref(cfg), C.byref(nb))
+        if st != L.GS_OK:
+            raise L.GsError(st, "workspace size")
+        return nb.value
 
     def _check(self, st, what=""):
         if st != L.GS_OK:
@@ -190,6 +243,12 @@ class Context:
         vals = torch.as_tensor(_DeviceArray(kv.value, max(n, 1)), device=self.device)[:n]
         ranges = torch.as_tensor(_DeviceArray(rg.value, 2 * tiles), device=self.device).view(tiles, 2)
         return keys, vals, ranges
+
+    def host_tier_stats(self):
+        """(chunks staged, bytes moved host<->device) by the last host-tier gs_step."""
+        ch, by = C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.gs_host_tier_stats(self.h, C.byref(ch), C.byref(by)), "host tier stats")
+        return ch.value, by.value
 
     def render_splats(self):
         """Projected splats of the last render, float32 [n_vis][4] each (torch

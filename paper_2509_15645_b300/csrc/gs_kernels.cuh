@@ -19,10 +19,13 @@ struct Work {
     int scan_grid;        // blocks of the scan kernels (<= 1024)
     int num_sms;
     cudaEvent_t *tev;     // timing points of the current step, or nullptr
+    bool capturing;       // the stream is being captured into a graph
     void mark(int p, cudaStream_t s) const
     {
+        if (!tev) return;
         // External: recorded as an event node when the stream is being captured
-        if (tev) cudaEventRecordWithFlags(tev[p], s, cudaEventRecordExternal);
+        if (capturing) cudaEventRecordWithFlags(tev[p], s, cudaEventRecordExternal);
+        else cudaEventRecord(tev[p], s);
     }
     int grid(int64_t threads, int block, int per_sm = 8) const
     {
@@ -43,17 +46,37 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
 int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
                Work &w, cudaStream_t s);
 
+// SH planes of w, m, v and their restore directions: D - 11 planes each, of
+// the SH storage type.  Resident scenes: the planes sit `ppitch` = pitch
+// elements apart inside the scene's arrays and Gaussian i at element i.  Host
+// tier: they sit in the context's staging ring, ppitch = slots << shift, and
+// Gaussian i at (slot[i >> shift] << shift) + (i & (2^shift - 1)).
+struct ShRows {
+    void *w, *m, *v, *rdir;   // rdir may be nullptr (then restores use m, v)
+    int64_t ppitch;
+    const int32_t *slot;      // host tier: chunk -> staging slot; nullptr when resident
+    int shift;
+    __device__ __forceinline__ int64_t base(int64_t i) const
+    {
+        if (!slot) return i;
+        // a chunk the step did not stage has slot -1: never read for a staged
+        // step's Gaussians; clamped so a stray index stays inside the ring
+        return ((int64_t)max(__ldg(slot + (i >> shift)), 0) << shift) + (i & ((1ll << shift) - 1));
+    }
+};
+
 // Scene pointers as the kernels take them.
 struct SceneView {
     float *geo;           // [11][pitch] fp32
-    void *sh;             // [D - 11][pitch] fp32 or bf16 (prec)
-    void *m;              // [D][pitch] fp32 or bf16
+    void *m;              // geometry rows of m: [11][pitch], fp32 or bf16 (prec); SH rows in sh
     void *v;
-    float *rdir;          // restore directions: [11][pitch] fp32, then [D-11][pitch] of the SH type; or nullptr
+    float *rdir;          // [11][pitch] fp32 geometry restore directions, or nullptr
+    ShRows sh;
     uint8_t *counter;
     int64_t n, pitch;
     int deg, D;
     int prec;             // GS_FP32, GS_BF16_SH_MOM or GS_BF16_SH_MOM_RN
+    int tier;             // GS_TIER_DEVICE or GS_TIER_HOST_SH
 };
 
 // Timing points recorded inside a step (see gs_timing_enable).
@@ -73,6 +96,8 @@ void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32
                           uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s);
 void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s);
+void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t n, int shift, int max_defer,
+                         uint8_t *touch, Work &w, cudaStream_t s);
 void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s);
 void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
                         Work &w, cudaStream_t s);

@@ -88,6 +88,7 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
         return GS_ERR_INVALID_ARG;
     if (scene->precision != GS_FP32 && scene->precision != GS_BF16_SH_MOM && scene->precision != GS_BF16_SH_MOM_RN)
         return GS_ERR_INVALID_ARG;
+    if (scene->tier != GS_TIER_DEVICE && scene->tier != GS_TIER_HOST_SH) return GS_ERR_INVALID_ARG;
     const bool restore = adam && adam->mode == GS_ADAM_DEFERRED && scene->m && scene->v && scene->counter;
     if (adam && (adam->max_defer < 1 || adam->max_defer > LUT_N - 1)) return GS_ERR_INVALID_ARG;
 
@@ -146,8 +147,8 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     uint32_t *mask = reinterpret_cast<uint32_t *>(base + OFF_MASK);
 
     SceneView sv{};
-    sv.geo = scene->geo;
-    sv.sh = scene->sh;
+    sv.geo = scene->geo;                 // the cull reads the geometry rows only
+    sv.tier = scene->tier;
     sv.m = scene->m;
     sv.v = scene->v;
     sv.prec = scene->precision;

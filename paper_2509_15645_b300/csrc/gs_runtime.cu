@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gs_kernels.cuh"
 
@@ -72,6 +73,21 @@ struct gs_ctx {
     // stage timing
     int t_max = 0, t_used = 0;
     cudaEvent_t *t_events = nullptr;   // [t_max][TP_COUNT]
+    // host tier: staging ring of SH rows (w, m, v, restore direction), each
+    // [max SH planes][stage_chunks << shift], chunk -> slot tables, the copy
+    // stream and its events
+    int shift = 15;
+    int64_t max_chunks = 0;
+    void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *dslot = nullptr;
+    uint8_t *dtouch = nullptr;
+    uint8_t *htouch = nullptr;          // pinned
+    int32_t *hslot = nullptr;           // pinned
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_vis = nullptr, ev_upd = nullptr, ev_done = nullptr;
+    struct Run { int64_t chunk0, slot0, nchunks; };
+    std::vector<Run> runs;              // copy runs of the last host-tier step
+    int64_t last_touched = 0, last_bytes = 0;
     char err[512] = {0};
 };
 
@@ -129,7 +145,8 @@ static bool valid_cfg(const gs_config *c)
            c->max_height > 0 && c->tile_w >= 4 && c->tile_h > 0 && 64 % c->tile_w == 0 &&
            (tp == 32 || tp == 64 || tp == 128 || tp == 256) &&
            c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
-           c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h;
+           c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h && c->stage_chunks >= 0 &&
+           (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20));
 }
 
 static void carve(gs_ctx *c, char *base)
@@ -199,6 +216,14 @@ static void carve(gs_ctx *c, char *base)
     c->dimg = k.take<float>(P);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
+    if (g.stage_chunks > 0) {
+        c->shift = g.chunk_shift ? g.chunk_shift : 15;
+        c->max_chunks = (N + (1ll << c->shift) - 1) >> c->shift;
+        const size_t ring = (size_t)(D - N_GEO) * ((size_t)g.stage_chunks << c->shift);
+        for (int j = 0; j < 4; j++) c->stage[j] = k.take<float>(ring);   // sized for fp32 rows
+        c->dslot = k.take<int32_t>(c->max_chunks);
+        c->dtouch = k.take<uint8_t>(c->max_chunks);
+    }
     c->ws_bytes = k.off + 256;
 }
 
@@ -283,7 +308,11 @@ static bool valid_cam(const gs_ctx *c, const gs_camera *cam)
            std::isfinite(cam->fx) && std::isfinite(cam->fy);
 }
 
-static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneView &sv)
+static int elem_bytes(int prec) { return prec == GS_FP32 ? 4 : 2; }
+
+// Host-tier scenes are accepted only where `host_ok` (gs_cull, which reads the
+// device-resident geometry, and gs_step, which stages the SH rows).
+static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneView &sv, bool host_ok = false)
 {
     if (!s) return fail(c, GS_ERR_INVALID_ARG, "scene is NULL");
     if (s->n <= 0 || s->n > c->cfg.max_gaussians) return fail(c, GS_ERR_INVALID_ARG, "scene n=%lld out of range", (long long)s->n);
@@ -291,19 +320,44 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     if (s->sh_degree < 0 || s->sh_degree > c->cfg.max_sh_degree) return fail(c, GS_ERR_INVALID_ARG, "sh_degree out of range");
     if (s->precision != GS_FP32 && s->precision != GS_BF16_SH_MOM && s->precision != GS_BF16_SH_MOM_RN)
         return fail(c, GS_ERR_INVALID_ARG, "unknown precision form");
-    if (!s->geo || !s->sh) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
+    if (s->tier != GS_TIER_DEVICE && s->tier != GS_TIER_HOST_SH) return fail(c, GS_ERR_INVALID_ARG, "unknown tier");
+    const bool host = s->tier == GS_TIER_HOST_SH;
+    if (host && !host_ok) return fail(c, GS_ERR_INVALID_ARG, "host-tier scenes run through gs_step (and gs_cull)");
+    if (host && (c->cfg.stage_chunks <= 0 || !s->host_sh || !s->host_m || !s->host_v || !s->m || !s->v ||
+                 !s->counter))
+        return fail(c, GS_ERR_INVALID_ARG, "host tier needs a staging ring (stage_chunks) and host_sh/m/v planes");
+    if (!s->geo || (!host && !s->sh)) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
     if (need_opt && (!s->m || !s->v || !s->counter)) return fail(c, GS_ERR_INVALID_ARG, "optimizer state is NULL");
+    const int64_t eb = elem_bytes(s->precision), P = s->pitch;
     sv.geo = s->geo;
-    sv.sh = s->sh;
     sv.m = s->m;
     sv.v = s->v;
     sv.rdir = (s->m && s->v) ? s->rdir : nullptr;
     sv.prec = s->precision;
+    sv.tier = s->tier;
     sv.counter = s->counter;
     sv.n = s->n;
-    sv.pitch = s->pitch;
+    sv.pitch = P;
     sv.deg = s->sh_degree;
     sv.D = n_params(s->sh_degree);
+    if (!host) {
+        sv.sh.w = s->sh;
+        sv.sh.m = s->m ? (char *)s->m + N_GEO * P * eb : nullptr;
+        sv.sh.v = s->v ? (char *)s->v + N_GEO * P * eb : nullptr;
+        sv.sh.rdir = sv.rdir ? (char *)sv.rdir + N_GEO * P * 4 : nullptr;
+        sv.sh.ppitch = P;
+        sv.sh.slot = nullptr;
+        sv.sh.shift = 0;
+    } else {
+        if (sv.rdir && !s->host_rdir) return fail(c, GS_ERR_INVALID_ARG, "host tier with rdir needs host_rdir");
+        sv.sh.w = c->stage[0];
+        sv.sh.m = c->stage[1];
+        sv.sh.v = c->stage[2];
+        sv.sh.rdir = sv.rdir ? c->stage[3] : nullptr;
+        sv.sh.ppitch = c->cfg.stage_chunks << c->shift;
+        sv.sh.slot = c->dslot;
+        sv.sh.shift = c->shift;
+    }
     return GS_OK;
 }
 
@@ -366,6 +420,18 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
         gs_destroy(c);
         return GS_ERR_CUDA;
     }
+    if (cfg->stage_chunks > 0) {
+        if (cudaHostAlloc((void **)&c->htouch, c->max_chunks, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void **)&c->hslot, c->max_chunks * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_vis, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_upd, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            gs_destroy(c);
+            return GS_ERR_CUDA;
+        }
+    }
     *out = c;
     return GS_OK;
 }
@@ -377,6 +443,13 @@ gs_status gs_destroy(gs_ctx *c)
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
     if (c->graph.graph) cudaGraphDestroy(c->graph.graph);
     timing_free(c);
+    if (c->cstream) cudaStreamSynchronize(c->cstream);
+    if (c->ev_vis) cudaEventDestroy(c->ev_vis);
+    if (c->ev_upd) cudaEventDestroy(c->ev_upd);
+    if (c->ev_done) cudaEventDestroy(c->ev_done);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
+    if (c->htouch) cudaFreeHost(c->htouch);
+    if (c->hslot) cudaFreeHost(c->hslot);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
     return GS_OK;
@@ -391,6 +464,7 @@ gs_status gs_sync_status(gs_ctx *c, void *stream)
     if (!c) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "gs_sync_status");
+    if (c->cstream && cudaStreamSynchronize(c->cstream) != cudaSuccess) return cuda_check(c, "gs_sync_status copies");
     int st = 0;
     if (cudaMemcpy(&st, &c->cnt->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_check(c, "gs_sync_status read");
@@ -405,7 +479,7 @@ gs_status gs_cull(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const 
 {
     if (!c) return GS_ERR_INVALID_ARG;
     SceneView sv;
-    gs_status st = scene_view(c, scene, false, sv);
+    gs_status st = scene_view(c, scene, false, sv, true);
     if (st) return st;
     if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
     if (!ids_out || !n_vis_out) return fail(c, GS_ERR_INVALID_ARG, "NULL output");
@@ -704,6 +778,14 @@ gs_status gs_render_lists(const gs_ctx *c, const uint32_t **tile_of_key, const u
     return GS_OK;
 }
 
+gs_status gs_host_tier_stats(const gs_ctx *c, int64_t *chunks, int64_t *bytes)
+{
+    if (!c || !chunks || !bytes) return GS_ERR_INVALID_ARG;
+    *chunks = c->last_touched;
+    *bytes = c->last_bytes;
+    return GS_OK;
+}
+
 gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **conic, const int32_t **n_vis)
 {
     if (!c || !c->have_fwd || !geom || !conic || !n_vis) return GS_ERR_INVALID_ARG;
@@ -714,11 +796,15 @@ gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **co
 }
 
 // ---------------------------------------------------------------------------
-// gs_step: the whole iteration enqueued on one stream; captured once into a
-// CUDA graph and replayed, with only the argument block (cameras, targets,
-// restore tables of the new step) updated between replays.
-static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, int mode, float *loss,
-                         cudaStream_t s)
+// gs_step
+struct StepMasks {
+    const uint32_t *gmask, *gprefix;   // gradient rows: the view's visible set, or the union of the views'
+    int64_t gcap;
+};
+
+// Cull of every view (visible ids, counts) and the union of the visible sets.
+static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, float *loss,
+                                    cudaStream_t s)
 {
     const int V = (int)c->cfg.max_visible;
     DevArgs *args = c->args + SLOT_STEP;
@@ -730,8 +816,7 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
         compact_mask(c->vmask[v], sv.n, c->chunk, true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
     }
     cudaMemcpyAsync(&c->cnt->n_vis, c->nvis_view, sizeof(int), cudaMemcpyDeviceToDevice, s);
-    const uint32_t *gmask = c->vmask[0], *gprefix = c->vprefix[0];
-    int64_t gcap = V;
+    StepMasks M{c->vmask[0], c->vprefix[0], V};
     if (n_views > 1) {
         const int64_t nw = (sv.n + 31) / 32;
         cudaMemsetAsync(c->union_mask, 0, nw * sizeof(uint32_t), s);
@@ -739,27 +824,143 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
         compact_mask(c->union_mask, sv.n, c->union_chunk, false, nullptr, c->union_prefix, (int)c->gcap_u,
                      &c->cnt->n_union, c->w, s);
         launch_zero_rows(c->grad_u, sv.D, c->gcap_u, &c->cnt->n_union, (int)c->gcap_u, c->w, s);
-        gmask = c->union_mask;
-        gprefix = c->union_prefix;
-        gcap = c->gcap_u;
+        M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u};
     }
+    return M;
+}
+
+// Render, L1 loss and backward of every view; gradients summed per Gaussian.
+static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, const StepMasks &M,
+                                 float *loss, cudaStream_t s)
+{
+    DevArgs *args = c->args + SLOT_STEP;
     for (int v = 0; v < n_views; v++) {
         if (v == 0) c->w.mark(TP_FWD0, s);
         render_forward(sv, args, v, c->vids[v], c->nvis_view + v, c->rb, a.cam[v], c->img, true, c->dimg, loss, c->w, s);
         if (v == 0) c->w.mark(TP_FWD1, s);
         if (v == 0) c->w.mark(TP_BWD0, s);
-        render_backward(sv, args, v, c->nvis_view + v, c->rb, a.cam[v], c->dimg, c->grad_u, gcap,
-                        n_views > 1 ? gmask : nullptr, n_views > 1 ? gprefix : nullptr, c->vids[v], n_views > 1, c->w, s);
+        render_backward(sv, args, v, c->nvis_view + v, c->rb, a.cam[v], c->dimg, c->grad_u, M.gcap,
+                        n_views > 1 ? M.gmask : nullptr, n_views > 1 ? M.gprefix : nullptr, c->vids[v], n_views > 1,
+                        c->w, s);
         if (v == 0) c->w.mark(TP_BWD1, s);
     }
+}
+
+static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const StepMasks &M, cudaStream_t s)
+{
+    DevArgs *args = c->args + SLOT_STEP;
     c->w.mark(TP_ADAM0, s);
     if (mode == GS_ADAM_DEFERRED)
-        launch_adam_deferred(sv, args, gmask, gprefix, c->grad_u, gcap, c->umask, c->uchunk, c->uids, c->udelay,
+        launch_adam_deferred(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->umask, c->uchunk, c->uids, c->udelay,
                              &c->cnt->n_upd, c->w, s);
     else
-        launch_adam_eager(sv, args, gmask, gprefix, c->grad_u, gcap, c->w, s);
+        launch_adam_eager(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->w, s);
     c->w.mark(TP_ADAM1, s);
     c->w.mark(TP_STEP1, s);
+}
+
+// gs_step: the whole iteration enqueued on one stream; captured once into a
+// CUDA graph and replayed, with only the argument block (cameras, targets,
+// restore tables of the new step) updated between replays.
+static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, int mode, float *loss,
+                         cudaStream_t s)
+{
+    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s);
+    enqueue_render_phase(c, sv, a, n_views, M, loss, s);
+    enqueue_adam_phase(c, sv, mode, M, s);
+}
+
+// One copy per staged array (w, m, v, restore direction) of each run of
+// consecutive chunks held in consecutive slots: rows [chunk0 << shift, ...) of
+// the host planes <-> the slots' rows of the staging ring, all SH planes at once.
+static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, size_t first, size_t last, bool to_dev)
+{
+    const int64_t eb = elem_bytes(scene->precision), R = 1ll << c->shift;
+    const int64_t planes = sv.D - N_GEO, ring = sv.sh.ppitch;
+    void *host[4] = {scene->host_sh, scene->host_m, scene->host_v, sv.rdir ? scene->host_rdir : nullptr};
+    for (size_t k = first; k < last; k++) {
+        const gs_ctx::Run &r = c->runs[k];
+        const int64_t i0 = r.chunk0 << c->shift;
+        const int64_t rows = std::min(sv.n, (r.chunk0 + r.nchunks) << c->shift) - i0;
+        for (int j = 0; j < 4; j++) {
+            if (!host[j]) continue;
+            char *h = (char *)host[j] + i0 * eb;
+            char *d = (char *)c->stage[j] + r.slot0 * R * eb;
+            if (to_dev)
+                cudaMemcpy2DAsync(d, ring * eb, h, scene->pitch * eb, rows * eb, planes, cudaMemcpyHostToDevice,
+                                  c->cstream);
+            else
+                cudaMemcpy2DAsync(h, scene->pitch * eb, d, ring * eb, rows * eb, planes, cudaMemcpyDeviceToHost,
+                                  c->cstream);
+            c->last_bytes += rows * eb * planes;
+        }
+    }
+}
+
+// gs_step for a host-tier scene (§4.2 selective offloading with the SH rows
+// streamed): cull and the chunk-touch map on the stream, one host
+// synchronisation to read the map, then the chunks' SH rows H2D on the copy
+// stream (the visible ones first, so the render starts while the
+// optimizer-only ones are in flight), render, optimizer step on the staged
+// rows, and the updated rows D2H on the copy stream, overlapping whatever the
+// caller enqueues next.  Kernels are launched directly (no graph: the copies
+// depend on the map).
+static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv, const DevArgs &a, int n_views,
+                                const gs_adam_cfg *adam, float *loss, cudaStream_t s)
+{
+    c->w.capturing = false;
+    c->w.tev = c->t_events ? c->t_events + (size_t)c->t_used * TP_COUNT : nullptr;
+    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s);
+    const int max_defer = adam->mode == GS_ADAM_DEFERRED ? adam->max_defer : 0;   // eager: every row
+    launch_touch_chunks(M.gmask, sv.counter, sv.n, c->shift, max_defer, c->dtouch, c->w, s);
+    const int64_t nch = (sv.n + (1ll << c->shift) - 1) >> c->shift;
+    cudaMemcpyAsync(c->htouch, c->dtouch, nch, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        c->w.tev = nullptr;
+        return cuda_check(c, "host tier: touch map");
+    }
+    // slots: chunks with visible Gaussians first, then optimizer-only chunks
+    int64_t used = 0;
+    size_t n_vis_runs = 0;
+    c->runs.clear();
+    for (int pass = 2; pass >= 1; pass--) {
+        for (int64_t ch = 0; ch < nch; ch++) {
+            if (c->htouch[ch] != pass) continue;
+            if (used >= c->cfg.stage_chunks) {
+                c->w.tev = nullptr;
+                return fail(c, GS_ERR_CAPACITY, "host tier: %lld+ chunks touched, staging ring holds %lld",
+                            (long long)used + 1, (long long)c->cfg.stage_chunks);
+            }
+            c->hslot[ch] = (int32_t)used;
+            if (!c->runs.empty() && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
+                c->runs.back().slot0 + c->runs.back().nchunks == used)
+                c->runs.back().nchunks++;
+            else
+                c->runs.push_back(gs_ctx::Run{ch, used, 1});
+            used++;
+        }
+        if (pass == 2) n_vis_runs = c->runs.size();
+    }
+    for (int64_t ch = 0; ch < nch; ch++)
+        if (!c->htouch[ch]) c->hslot[ch] = -1;
+    c->last_touched = used;
+    c->last_bytes = 0;
+    cudaMemcpyAsync(c->dslot, c->hslot, nch * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    // the copy stream still holds the previous step's write-back: its order keeps the ring and the host rows consistent
+    copy_runs(c, scene, sv, 0, n_vis_runs, true);
+    cudaEventRecord(c->ev_vis, c->cstream);
+    copy_runs(c, scene, sv, n_vis_runs, c->runs.size(), true);
+    cudaEventRecord(c->ev_upd, c->cstream);
+    cudaStreamWaitEvent(s, c->ev_vis, 0);
+    enqueue_render_phase(c, sv, a, n_views, M, loss, s);
+    cudaStreamWaitEvent(s, c->ev_upd, 0);
+    enqueue_adam_phase(c, sv, adam->mode, M, s);
+    cudaEventRecord(c->ev_done, s);
+    cudaStreamWaitEvent(c->cstream, c->ev_done, 0);
+    copy_runs(c, scene, sv, 0, c->runs.size(), false);
+    if (c->w.tev) c->t_used++;
+    c->w.tev = nullptr;
+    return cuda_check(c, "gs_step host tier");
 }
 
 static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
@@ -780,7 +981,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
 {
     if (!c) return GS_ERR_INVALID_ARG;
     SceneView sv;
-    gs_status st = scene_view(c, scene, true, sv);
+    gs_status st = scene_view(c, scene, true, sv, true);
     if (st) return st;
     if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
     if (n_views < 1 || n_views > c->cfg.max_views || !views || !targets || !loss_out)
@@ -797,6 +998,11 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
     GraphCache &g = c->graph;
     const bool timed = c->t_events != nullptr;
     if (timed && c->t_used >= c->t_max) return fail(c, GS_ERR_CAPACITY, "timing buffer full: call gs_timing_read");
+    if (scene->tier == GS_TIER_HOST_SH) {
+        st = step_host_tier(c, scene, sv, a, n_views, adam, loss_out, s);
+        if (!st) scene->step += 1;
+        return st;
+    }
     if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rb.variant)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
@@ -818,7 +1024,9 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
             return cuda_check(c, "gs_step begin capture");
         }
         c->w.tev = timed ? c->t_events : nullptr;        // slot 0 events identify the nodes
+        c->w.capturing = true;
         enqueue_step(c, sv, a, n_views, adam->mode, loss_out, cs);
+        c->w.capturing = false;
         c->w.tev = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
         if (own) cudaStreamDestroy(cs);

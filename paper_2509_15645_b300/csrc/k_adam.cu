@@ -61,6 +61,35 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_select(uint8_t *__restrict_
     }
 }
 
+// Host tier (§4.2 selective offloading): which chunks of 2^shift Gaussians
+// this step touches.  touch[c] = 2 if a Gaussian of chunk c is visible (its SH
+// rows feed the gather and the optimizer), 1 if one is only in the update set
+// (its counter reached max_defer), else 0 -- the same membership test as
+// k_adam_select, taken before the counters change.
+__global__ void __launch_bounds__(ADAM_BLOCK) k_touch_chunks(const uint32_t *__restrict__ vmask,
+                                                             const uint8_t *__restrict__ counter, int64_t n, int shift,
+                                                             int max_defer, uint8_t *__restrict__ touch)
+{
+    const int64_t R = 1ll << shift, nchunks = (n + R - 1) >> shift;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int64_t i0 = c << shift, i1 = min(n, i0 + R);
+        int vis = 0, sat = 0;
+        for (int64_t wd = (i0 >> 5) + threadIdx.x; wd < ((i1 + 31) >> 5); wd += blockDim.x) vis |= vmask[wd] != 0u;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) sat |= counter[i] >= max_defer;
+        vis = __syncthreads_or(vis);
+        sat = __syncthreads_or(sat);
+        if (threadIdx.x == 0) touch[c] = vis ? 2 : (sat ? 1 : 0);
+    }
+}
+
+void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t n, int shift, int max_defer,
+                         uint8_t *touch, Work &w, cudaStream_t s)
+{
+    const int64_t nchunks = (n + (1ll << shift) - 1) >> shift;
+    k_touch_chunks<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK, 4), ADAM_BLOCK, 0, s>>>(vmask, counter, n, shift,
+                                                                                   max_defer, touch);
+}
+
 // Shared copy of the step's tables.
 struct SLut {
     float param[N_GROUPS][LUT_N];
@@ -111,37 +140,55 @@ __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask,
     return (int)(vprefix[i >> 5] + __popc(word & ((1u << bit) - 1u)));
 }
 
-// Parameter plane r of Gaussian i: geometry planes are fp32, SH planes of
-// type T; restore directions likewise (fp32 for the 11 geometry planes, then
-// type T for the SH planes, so [D][pitch] fp32 in the fp32 form).
+// Parameter plane r of Gaussian i: the 11 geometry planes (w fp32, m and v of
+// type T, restore direction fp32) at r * pitch + i; SH plane r (w, m, v and
+// restore direction of type T) at (r - 11) * sp + sb, where sb = shbase(i) is
+// i for a resident scene and the staging-ring element for the host tier.
 template <typename T> struct Planes {
     float *geo;
-    T *sh;
     T *m, *v;
     float *rdir;
-    int64_t pitch;
-    __device__ __forceinline__ float ldw(int r, int64_t i) const
+    T *shw, *shm, *shv, *shr;
+    int64_t pitch, sp;
+    const int32_t *slot;
+    int shift;
+    __device__ __forceinline__ int64_t shbase(int64_t i) const
     {
-        return r < N_GEO ? geo[r * pitch + i] : ld_val(sh + (r - N_GEO) * pitch + i);
+        if (!slot) return i;
+        return ((int64_t)max(__ldg(slot + (i >> shift)), 0) << shift) + (i & ((1ll << shift) - 1));
     }
-    __device__ __forceinline__ T *rdir_sh() const { return (T *)(rdir + N_GEO * pitch); }
+    __device__ __forceinline__ float ldw(int r, int64_t i, int64_t sb) const
+    {
+        return r < N_GEO ? geo[r * pitch + i] : ld_val(shw + (r - N_GEO) * sp + sb);
+    }
+    __device__ __forceinline__ float ldm(int r, int64_t i, int64_t sb) const
+    {
+        return ld_val(r < N_GEO ? m + r * pitch + i : shm + (r - N_GEO) * sp + sb);
+    }
+    __device__ __forceinline__ float ldv(int r, int64_t i, int64_t sb) const
+    {
+        return ld_val(r < N_GEO ? v + r * pitch + i : shv + (r - N_GEO) * sp + sb);
+    }
     // Store the updated w, m, v of plane r (rounded per the storage; `key` is
     // sr_plane_key of this plane and step) and the restore direction of what
     // was stored.
-    __device__ __forceinline__ void store(int r, int64_t i, float w, float mm, float vv, const SLut &L,
+    __device__ __forceinline__ void store(int r, int64_t i, int64_t sb, float w, float mm, float vv, const SLut &L,
                                           uint32_t key) const
     {
         const bool st = L.stochastic != 0;
         const uint32_t bits = st ? sr_bits(key, (uint32_t)i) : 0u;
-        const float ms = st_val(m + r * pitch + i, mm, st, bits);
-        const float vs = st_val(v + r * pitch + i, vv, st, bits >> 16);
-        const float dir = restore_dir(ms, vs, L.eps);
         if (r < N_GEO) {
-            geo[r * pitch + i] = w;
-            if (rdir) rdir[r * pitch + i] = dir;
+            const int64_t o = r * pitch + i;
+            const float ms = st_val(m + o, mm, st, bits);
+            const float vs = st_val(v + o, vv, st, bits >> 16);
+            geo[o] = w;
+            if (rdir) rdir[o] = restore_dir(ms, vs, L.eps);
         } else {
-            st_val(sh + (r - N_GEO) * pitch + i, w, st, sr_w_bits(bits));
-            if (rdir) st_val(rdir_sh() + (r - N_GEO) * pitch + i, dir, false, 0u);
+            const int64_t o = (r - N_GEO) * sp + sb;
+            const float ms = st_val(shm + o, mm, st, bits);
+            const float vs = st_val(shv + o, vv, st, bits >> 16);
+            st_val(shw + o, w, st, sr_w_bits(bits));
+            if (shr) st_val(shr + o, restore_dir(ms, vs, L.eps), false, 0u);
         }
     }
 };
@@ -151,15 +198,16 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
                                           int64_t gcap, int d, const SLut &L)
 {
     constexpr int UNROLL = 4;
+    const int64_t sb = P.shbase(i);
     for (int r0 = 0; r0 < D; r0 += UNROLL) {
         float w_[UNROLL], m_[UNROLL], v_[UNROLL], g_[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
             int r = r0 + u;
             if (r < D) {
-                w_[u] = P.ldw(r, i);
-                m_[u] = ld_val(P.m + r * P.pitch + i);
-                v_[u] = ld_val(P.v + r * P.pitch + i);
+                w_[u] = P.ldw(r, i, sb);
+                m_[u] = P.ldm(r, i, sb);
+                v_[u] = P.ldv(r, i, sb);
                 g_[u] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
             }
         }
@@ -168,7 +216,7 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
             int r = r0 + u;
             if (r < D) {
                 adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
-                P.store(r, i, w_[u], m_[u], v_[u], L, L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)r) : 0u);
+                P.store(r, i, sb, w_[u], m_[u], v_[u], L, L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)r) : 0u);
             }
         }
     }
@@ -183,7 +231,7 @@ constexpr int RG = 4;
 
 struct AdamRows {
     float w[RG], m[RG], v[RG], g[RG];
-    int64_t i;
+    int64_t i, sb;
     int d;
 };
 
@@ -194,6 +242,7 @@ __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__
                                            const float *__restrict__ grad, int64_t gcap, int D, int r0)
 {
     a.i = uids[u];
+    a.sb = P.shbase(a.i);
     a.d = udelay[u];
     int k = compact_index(vmask, vprefix, a.i);
     if (k >= gcap) k = -1;     // outside the caller's gradient buffer: treated as zero gradient
@@ -201,16 +250,16 @@ __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__
     for (int j = 0; j < RG; j++) {
         const int r = r0 + j;
         if (r < D) {
-            a.w[j] = P.ldw(r, a.i);
-            a.m[j] = ld_val(P.m + r * P.pitch + a.i);
-            a.v[j] = ld_val(P.v + r * P.pitch + a.i);
+            a.w[j] = P.ldw(r, a.i, a.sb);
+            a.m[j] = P.ldm(r, a.i, a.sb);
+            a.v[j] = P.ldv(r, a.i, a.sb);
             a.g[j] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(Planes<T> P, int D, const int32_t *__restrict__ uids,
+__global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D, const int32_t *__restrict__ uids,
                                                            const uint8_t *__restrict__ udelay, const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
@@ -239,7 +288,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_apply(Planes<T> P, int D, c
             if (r < D) {
                 float w_ = cur.w[j], m_ = cur.m[j], v_ = cur.v[j];
                 adam_value(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
-                P.store(r, cur.i, w_, m_, v_, L, key[j]);
+                P.store(r, cur.i, cur.sb, w_, m_, v_, L, key[j]);
             }
         }
         if (!more) break;
@@ -252,11 +301,17 @@ template <typename T> static Planes<T> planes_of(const SceneView &sc)
 {
     Planes<T> P;
     P.geo = sc.geo;
-    P.sh = (T *)sc.sh;
     P.m = (T *)sc.m;
     P.v = (T *)sc.v;
     P.rdir = sc.rdir;
+    P.shw = (T *)sc.sh.w;
+    P.shm = (T *)sc.sh.m;
+    P.shv = (T *)sc.sh.v;
+    P.shr = sc.rdir ? (T *)sc.sh.rdir : nullptr;
     P.pitch = sc.pitch;
+    P.sp = sc.sh.ppitch;
+    P.slot = sc.sh.slot;
+    P.shift = sc.sh.shift;
     return P;
 }
 
@@ -312,7 +367,7 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
     w.mark(TP_APPLY1, s);
 }
 
-// rdir = m / (sqrt(v) + eps) for every plane that keeps a restore direction.
+// rdir = m / (sqrt(v) + eps) for every plane.
 template <typename T>
 __global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__restrict__ args)
 {
@@ -320,10 +375,10 @@ __global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__r
     const int64_t total = (int64_t)D * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
-        const int64_t i = e - (int64_t)r * n, o = r * P.pitch + i;
-        const float dir = restore_dir(ld_val(P.m + o), ld_val(P.v + o), eps);
-        if (r < N_GEO) P.rdir[o] = dir;
-        else st_val(P.rdir_sh() + (r - N_GEO) * P.pitch + i, dir, false, 0u);
+        const int64_t i = e - (int64_t)r * n, sb = P.shbase(i);
+        const float dir = restore_dir(P.ldm(r, i, sb), P.ldv(r, i, sb), eps);
+        if (r < N_GEO) P.rdir[r * P.pitch + i] = dir;
+        else st_val(P.shr + (r - N_GEO) * P.sp + sb, dir, false, 0u);
     }
 }
 
@@ -347,9 +402,10 @@ __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, 
     const int64_t pitch = P.pitch;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int d = counter ? counter[i] : 0;
+        const int64_t sb = P.shbase(i);
         for (int r = 0; r < D; r++) {
-            float w = P.ldw(r, i);
-            float mm = ld_val(P.m + r * pitch + i), vv = ld_val(P.v + r * pitch + i);
+            float w = P.ldw(r, i, sb);
+            float mm = P.ldm(r, i, sb), vv = P.ldv(r, i, sb);
             if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[lr_group(r)][d], d, L.eps);
             if (m_out) m_out[r * pitch + i] = d ? L.mom[d - 1] * mm : mm;
             if (v_out) v_out[r * pitch + i] = d ? L.var[d - 1] * vv : vv;

@@ -69,28 +69,33 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
             for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = 0.f;
             continue;
         }
-        // gather all D planes (with m, v when restoring) before any arithmetic
-        const T *sh = (const T *)sc.sh, *mp = (const T *)sc.m, *vp = (const T *)sc.v;
+        // gather all D planes (with the restore directions, or m and v) before any arithmetic
+        const int64_t sb = sc.sh.base(i);                  // element of Gaussian i in the SH planes
+        const int64_t sp = sc.sh.ppitch;
+        const T *shw = (const T *)sc.sh.w;
         float w[D];
 #pragma unroll
-        for (int r = 0; r < D; r++) w[r] = r < N_GEO ? __ldg(sc.geo + r * pitch + i) : ld_val(sh + (r - N_GEO) * pitch + i);
+        for (int r = 0; r < D; r++)
+            w[r] = r < N_GEO ? __ldg(sc.geo + r * pitch + i) : ld_val(shw + (r - N_GEO) * sp + sb);
         if (L.restore) {
             const int d = sc.counter[i];
             if (d) {
-                // restore directions: fp32 for the geometry planes, the SH
-                // storage type for the SH planes
                 if (sc.rdir) {
-                    const T *rsh = (const T *)(sc.rdir + N_GEO * pitch);
+                    const T *rsh = (const T *)sc.sh.rdir;
 #pragma unroll
                     for (int r = 0; r < D; r++) {
-                        const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * pitch + i);
+                        const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * sp + sb);
                         w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], d);
                     }
                 } else {
+                    const T *mp = (const T *)sc.m, *vp = (const T *)sc.v;
+                    const T *msh = (const T *)sc.sh.m, *vsh = (const T *)sc.sh.v;
 #pragma unroll
-                    for (int r = 0; r < D; r++)
-                        w[r] = restore_param(w[r], ld_val(mp + r * pitch + i), ld_val(vp + r * pitch + i),
-                                             L.param[lr_group(r)][d], d, L.eps);
+                    for (int r = 0; r < D; r++) {
+                        const float mm = r < N_GEO ? ld_val(mp + r * pitch + i) : ld_val(msh + (r - N_GEO) * sp + sb);
+                        const float vv = r < N_GEO ? ld_val(vp + r * pitch + i) : ld_val(vsh + (r - N_GEO) * sp + sb);
+                        w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], d, L.eps);
+                    }
                 }
             }
         }
