@@ -96,6 +96,12 @@ void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32
                           uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s);
 void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s);
+void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, uint32_t *umask,
+                        uint32_t *uchunk, int32_t *uids, uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s);
+void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, const int32_t *uids, const uint8_t *udelay,
+                       const int *u_range, const int *n_upd, Work &w, cudaStream_t s);
+void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s);
 void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t n, int shift, int max_defer,
                          uint8_t *touch, Work &w, cudaStream_t s);
 void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s);

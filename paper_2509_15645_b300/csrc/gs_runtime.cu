@@ -897,69 +897,114 @@ static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, siz
     }
 }
 
-// gs_step for a host-tier scene (§4.2 selective offloading with the SH rows
-// streamed): cull and the chunk-touch map on the stream, one host
-// synchronisation to read the map, then the chunks' SH rows H2D on the copy
-// stream (the visible ones first, so the render starts while the
-// optimizer-only ones are in flight), render, optimizer step on the staged
-// rows, and the updated rows D2H on the copy stream, overlapping whatever the
-// caller enqueues next.  Kernels are launched directly (no graph: the copies
-// depend on the map).
+// gs_step for a host-tier scene (§4.2 selective offloading, SH rows
+// streamed).  On the stream: cull and the chunk-touch map, then one host
+// synchronisation to read the map.  Chunks with visible Gaussians take the
+// first slots of the staging ring for the whole step; the optimizer-only
+// chunks (counters at the bound) go through the remaining slots in rounds,
+// each round covering a range of chunk ids.  Copy stream: H2D of the visible
+// chunks (the render waits for these only), then per round the write-back of
+// the previous round's chunks and the H2D of this round's; stream: render,
+// the optimizer's select, and per round the apply over the members whose ids
+// fall in the round's range.  The updated rows go back D2H on the copy stream,
+// overlapping whatever the caller enqueues next.  Kernels are launched
+// directly (no graph: the copies depend on the map).
 static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv, const DevArgs &a, int n_views,
                                 const gs_adam_cfg *adam, float *loss, cudaStream_t s)
 {
+    if (adam->mode != GS_ADAM_DEFERRED) return fail(c, GS_ERR_INVALID_ARG, "host tier runs the deferred optimizer");
     c->w.capturing = false;
     c->w.tev = c->t_events ? c->t_events + (size_t)c->t_used * TP_COUNT : nullptr;
+    struct TevReset {
+        gs_ctx *c;
+        ~TevReset() { c->w.tev = nullptr; }
+    } tev_reset{c};
     const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s);
-    const int max_defer = adam->mode == GS_ADAM_DEFERRED ? adam->max_defer : 0;   // eager: every row
-    launch_touch_chunks(M.gmask, sv.counter, sv.n, c->shift, max_defer, c->dtouch, c->w, s);
+    launch_touch_chunks(M.gmask, sv.counter, sv.n, c->shift, adam->max_defer, c->dtouch, c->w, s);
     const int64_t nch = (sv.n + (1ll << c->shift) - 1) >> c->shift;
     cudaMemcpyAsync(c->htouch, c->dtouch, nch, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        c->w.tev = nullptr;
-        return cuda_check(c, "host tier: touch map");
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "host tier: touch map");
+
+    // plan: visible chunks -> slots [0, nv); optimizer-only chunks -> slots
+    // [nv, ring) in rounds of at most `cap` chunks, cut at chunk-id boundaries
+    int64_t nv = 0, nu = 0;
+    for (int64_t ch = 0; ch < nch; ch++) {
+        if (c->htouch[ch] == 2) c->hslot[ch] = (int32_t)nv++;
+        else if (c->htouch[ch] == 1) nu++;
+        else c->hslot[ch] = -1;
     }
-    // slots: chunks with visible Gaussians first, then optimizer-only chunks
-    int64_t used = 0;
-    size_t n_vis_runs = 0;
+    const int64_t cap = c->cfg.stage_chunks - nv;
+    if (nv > c->cfg.stage_chunks || (nu > 0 && cap < 1))
+        return fail(c, GS_ERR_CAPACITY, "host tier: %lld chunks of visible Gaussians, staging ring holds %lld",
+                    (long long)nv + (nu > 0), (long long)c->cfg.stage_chunks);
+    struct Round { int64_t ch_lo, ch_hi; size_t run_lo, run_hi; };
+    std::vector<Round> rounds;
     c->runs.clear();
-    for (int pass = 2; pass >= 1; pass--) {
-        for (int64_t ch = 0; ch < nch; ch++) {
-            if (c->htouch[ch] != pass) continue;
-            if (used >= c->cfg.stage_chunks) {
-                c->w.tev = nullptr;
-                return fail(c, GS_ERR_CAPACITY, "host tier: %lld+ chunks touched, staging ring holds %lld",
-                            (long long)used + 1, (long long)c->cfg.stage_chunks);
-            }
-            c->hslot[ch] = (int32_t)used;
-            if (!c->runs.empty() && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
-                c->runs.back().slot0 + c->runs.back().nchunks == used)
-                c->runs.back().nchunks++;
-            else
-                c->runs.push_back(gs_ctx::Run{ch, used, 1});
-            used++;
-        }
-        if (pass == 2) n_vis_runs = c->runs.size();
-    }
+    auto add_run = [&](int64_t ch, int64_t slot) {
+        if (!c->runs.empty() && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
+            c->runs.back().slot0 + c->runs.back().nchunks == slot)
+            c->runs.back().nchunks++;
+        else
+            c->runs.push_back(gs_ctx::Run{ch, slot, 1});
+    };
     for (int64_t ch = 0; ch < nch; ch++)
-        if (!c->htouch[ch]) c->hslot[ch] = -1;
-    c->last_touched = used;
+        if (c->htouch[ch] == 2) add_run(ch, c->hslot[ch]);
+    const size_t n_vis_runs = c->runs.size();
+    {
+        Round r{0, nch, n_vis_runs, n_vis_runs};
+        int64_t in_round = 0;
+        for (int64_t ch = 0; ch < nch; ch++) {
+            if (c->htouch[ch] != 1) continue;
+            if (in_round == cap) {           // close the round before this chunk
+                r.ch_hi = ch;
+                r.run_hi = c->runs.size();
+                rounds.push_back(r);
+                r = Round{ch, nch, c->runs.size(), c->runs.size()};
+                in_round = 0;
+            }
+            c->hslot[ch] = (int32_t)(nv + in_round);
+            add_run(ch, nv + in_round);
+            in_round++;
+        }
+        r.run_hi = c->runs.size();
+        rounds.push_back(r);
+    }
+    c->last_touched = nv + nu;
     c->last_bytes = 0;
     cudaMemcpyAsync(c->dslot, c->hslot, nch * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    // the copy stream still holds the previous step's write-back: its order keeps the ring and the host rows consistent
+    // the copy stream still holds the previous step's write-backs: its order
+    // keeps the ring and the host rows consistent
     copy_runs(c, scene, sv, 0, n_vis_runs, true);
     cudaEventRecord(c->ev_vis, c->cstream);
-    copy_runs(c, scene, sv, n_vis_runs, c->runs.size(), true);
-    cudaEventRecord(c->ev_upd, c->cstream);
     cudaStreamWaitEvent(s, c->ev_vis, 0);
     enqueue_render_phase(c, sv, a, n_views, M, loss, s);
-    cudaStreamWaitEvent(s, c->ev_upd, 0);
-    enqueue_adam_phase(c, sv, adam->mode, M, s);
-    cudaEventRecord(c->ev_done, s);
+    DevArgs *args = c->args + SLOT_STEP;
+    c->w.mark(TP_ADAM0, s);
+    launch_adam_select(sv, args, M.gmask, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+    int *u_range = c->n_tmp + 2;
+    const int64_t R = 1ll << c->shift;
+    for (size_t k = 0; k < rounds.size(); k++) {
+        const Round &r = rounds[k];
+        if (k > 0) {                          // the ring slots of the previous round go back first
+            cudaStreamWaitEvent(c->cstream, c->ev_done, 0);
+            copy_runs(c, scene, sv, rounds[k - 1].run_lo, rounds[k - 1].run_hi, false);
+        }
+        copy_runs(c, scene, sv, r.run_lo, r.run_hi, true);
+        cudaEventRecord(c->ev_upd, c->cstream);
+        cudaStreamWaitEvent(s, c->ev_upd, 0);
+        launch_uid_range(c->uids, &c->cnt->n_upd, r.ch_lo * R, r.ch_hi * R, u_range, s);
+        if (k == 0) c->w.mark(TP_APPLY0, s);
+        launch_adam_apply(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->uids, c->udelay, u_range,
+                          &c->cnt->n_upd, c->w, s);
+        if (k == 0) c->w.mark(TP_APPLY1, s);
+        cudaEventRecord(c->ev_done, s);
+    }
+    c->w.mark(TP_ADAM1, s);
+    c->w.mark(TP_STEP1, s);
     cudaStreamWaitEvent(c->cstream, c->ev_done, 0);
-    copy_runs(c, scene, sv, 0, c->runs.size(), false);
+    copy_runs(c, scene, sv, rounds.back().run_lo, rounds.back().run_hi, false);
+    copy_runs(c, scene, sv, 0, n_vis_runs, false);
     if (c->w.tev) c->t_used++;
-    c->w.tev = nullptr;
     return cuda_check(c, "gs_step host tier");
 }
 

@@ -260,7 +260,8 @@ __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__
 
 template <typename T>
 __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D, const int32_t *__restrict__ uids,
-                                                           const uint8_t *__restrict__ udelay, const int *n_upd_p,
+                                                           const uint8_t *__restrict__ udelay, const int *u_range,
+                                                           const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
                                                            const float *__restrict__ grad, int64_t gcap,
@@ -268,10 +269,11 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D
 {
     __shared__ SLut L;
     load_slut(L, args->lut);
-    const int n_upd = *n_upd_p;
+    // members [u_range[0], u_range[1]) of the update set, or all of them
+    const int n_upd = u_range ? u_range[1] : *n_upd_p;
     const int r0 = blockIdx.y * RG;
     const int stride = gridDim.x * blockDim.x;
-    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int u = (u_range ? u_range[0] : 0) + blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n_upd) return;
     uint32_t key[RG];          // stochastic-rounding keys of this thread's planes
 #pragma unroll
@@ -315,24 +317,58 @@ template <typename T> static Planes<T> planes_of(const SceneView &sc)
     return P;
 }
 
-void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
-                          const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
-                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s)
+void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, uint32_t *umask,
+                        uint32_t *uchunk, int32_t *uids, uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s)
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     k_adam_select<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.counter, vmask, sc.n, args, umask,
                                                                                 uchunk);
     compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s, sc.counter, udelay);
+}
+
+void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, const int32_t *uids, const uint8_t *udelay,
+                       const int *u_range, const int *n_upd, Work &w, cudaStream_t s)
+{
     const int groups = (sc.D + RG - 1) / RG;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
-    w.mark(TP_APPLY0, s);
     if (sc.prec == GS_FP32)
-        k_adam_apply<float><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, uids, udelay, n_upd, vmask, vprefix,
-                                                        grad, gcap, args);
+        k_adam_apply<float><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, uids, udelay, u_range, n_upd, vmask,
+                                                        vprefix, grad, gcap, args);
     else
         k_adam_apply<__nv_bfloat16><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, uids, udelay,
-                                                                n_upd, vmask, vprefix, grad, gcap, args);
+                                                                u_range, n_upd, vmask, vprefix, grad, gcap, args);
+}
+
+void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                          const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
+                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s)
+{
+    launch_adam_select(sc, args, vmask, umask, uchunk, uids, udelay, n_upd, w, s);
+    w.mark(TP_APPLY0, s);
+    launch_adam_apply(sc, args, vmask, vprefix, grad, gcap, uids, udelay, nullptr, n_upd, w, s);
     w.mark(TP_APPLY1, s);
+}
+
+// [first, end) of the update-set members with ids in [id_lo, id_hi): the ids
+// are ascending, so two binary searches.
+__global__ void k_uid_range(const int32_t *__restrict__ uids, const int *n_upd_p, int64_t id_lo, int64_t id_hi,
+                            int *range)
+{
+    if (threadIdx.x >= 2) return;
+    const int64_t key = threadIdx.x == 0 ? id_lo : id_hi;
+    int lo = 0, hi = *n_upd_p;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (uids[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    range[threadIdx.x] = lo;
+}
+
+void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s)
+{
+    k_uid_range<<<1, 32, 0, s>>>(uids, n_upd, id_lo, id_hi, range);
 }
 
 // Eager Adam (Eq. 1 for every Gaussian, every step): the baseline the
