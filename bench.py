@@ -114,6 +114,11 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FLOPS_CONTRIB, FLOPS_SQUARE = 79.0, 28.0
 
 
+def _int(x):
+    """round() that maps a missing count (NaN) to None."""
+    return None if x is None or not np.isfinite(x) else round(x)
+
+
 def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False):
     """Bytes the method must move per launch: the cull, the optimizer's apply
     sweep and its select pass (the minimum traffic of each, every byte read or
@@ -386,7 +391,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (parameters + moments {N * D * 12 / 1e9:.1f} GB in fp32), no flush",
                    "visible_per_view": round(m["n_vis"]), "keys_per_view": round(m["n_keys"]),
                    "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
-                   "square_pairs_per_view": round(m["sq_pairs"]), "contrib_pairs_per_view": round(m["on_pairs"]),
+                   "square_pairs_per_view": _int(m["sq_pairs"]), "contrib_pairs_per_view": _int(m["on_pairs"]),
                    "raster_variant": m["variant"],
                    "autotune_ms": [None if t is None else round(t, 4) for t in m["variant_ms"]]},
         "roofline": roofline(m),
