@@ -124,6 +124,7 @@ struct RenderBufs {
     uint2 *ranges;           // [tiles]
     float *g9;               // [9][cap] screen-space gradient sums
     int *n_keys;             // device
+    float *cfinal;           // [3][H][W] final colour of the last forward render (for the backward)
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0

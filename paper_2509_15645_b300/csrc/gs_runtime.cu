@@ -207,6 +207,7 @@ static void carve(gs_ctx *c, char *base)
     rb.g9 = k.take<float>(9 * V);
     rb.n_keys = base ? &c->cnt->n_keys : nullptr;
     rb.n_fix = base ? &c->cnt->n_fix : nullptr;
+    rb.cfinal = k.take<float>(P);
     rb.fix_idx = k.take<int32_t>(V);
     rb.fix_flag = k.take<uint8_t>(V);
     int64_t big = K > V ? K : V;

@@ -296,7 +296,7 @@ __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, c
             if (COLOR) s2[pos] = a2;
             if (INDEX) {
                 s_k[pos] = k;
-                s_gi[pos] = (int)b + e;
+                if (s_gi) s_gi[pos] = (int)b + e;
             }
         }
         base += tot;
@@ -309,8 +309,9 @@ template <int PPT, int BATCH>
 __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
                                                     const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                                     const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                    int view, float *__restrict__ image, int use_target,
-                                                    float *__restrict__ dimage, float *__restrict__ loss)
+                                                    int view, float *__restrict__ image, float *__restrict__ cfinal,
+                                                    int use_target, float *__restrict__ dimage,
+                                                    float *__restrict__ loss)
 {
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ int s_wcnt[8];
@@ -380,6 +381,11 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
             image[pix] = C0[j];
             image[HW + pix] = C1[j];
             image[2 * HW + pix] = C2[j];
+            if (cfinal) {                    // kept for the backward pass
+                cfinal[pix] = C0[j];
+                cfinal[HW + pix] = C1[j];
+                cfinal[2 * HW + pix] = C2[j];
+            }
             if (target) {
                 float d0 = C0[j] - target[pix], d1 = C1[j] - target[HW + pix], d2 = C2[j] - target[2 * HW + pix];
                 dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
@@ -422,21 +428,29 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
     return r;
 }
 
-// STATS: also count, over the back-to-front pass, the (pixel, splat) pairs
-// that pass the square test and the pairs that contribute (stats[0], stats[1]).
+// Backward of the compositing (§2.4 step 5), one front-to-back pass per tile
+// that recomputes each pixel's transmittance T_i exactly as the forward did
+// (same list, same tests, same operations) together with the colour
+// accumulated so far, A_i = sum_{j<=i} c_j a_j T_j.  With the forward's final
+// colour F (kept per pixel), the colour behind splat i seen through it is
+// T_i R_i = (F - A_i) / (1 - a_i), so
+//   dL/da_i = g . (T_i c_i - (F - A_i) / (1 - a_i)),   dL/dc_i = g a_i T_i,
+// and nothing is replayed or divided back out of T.  A warp sums its lanes'
+// contributions to each splat and issues the atomic adds into g9.
+// STATS: also count the (pixel, splat) pairs that pass the square test and the
+// pairs that contribute (stats[0], stats[1]).
 template <int PPT, int BATCH, bool STATS = false>
 __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
                                                     const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                                                     const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                    int view, const float *__restrict__ dimage, float *__restrict__ g9,
+                                                    int view, const float *__restrict__ cfinal,
+                                                    const float *__restrict__ dimage, float *__restrict__ g9,
                                                     int64_t gcap, unsigned long long *stats = nullptr)
 {
     unsigned long long n_sq = 0, n_on = 0;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ uint32_t s_k[BATCH];
-    __shared__ int s_gi[BATCH];
     __shared__ int s_wcnt[8];
-    __shared__ int s_end;
     const DevCam &cam = args->cam[view];
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tile = blockIdx.x;
@@ -452,94 +466,59 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_end = (int)rg.x;
-    // phase 1: forward replay -> final transmittance and last contributor of each pixel
-    float T[PPT];
-    int last[PPT];
+    const int64_t HW = (int64_t)W * H;
+    float T[PPT], A0[PPT], A1[PPT], A2[PPT], F0[PPT], F1[PPT], F2[PPT], g0[PPT], g1[PPT], g2[PPT];
     uint32_t live = 0;
 #pragma unroll
     for (int j = 0; j < PPT; j++) {
         T[j] = 1.f;
-        last[j] = -1;
-        if (x < W && y0 + j < H) live |= 1u << j;
-    }
-    for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
-        if (__syncthreads_count(live != 0) == 0) break;
-        const int nb = stage_batch<false, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
-                                                Y1, s0, s1, s2, s_k, s_gi, s_wcnt);
-        for (int e = 0; e < nb && live; e++) {
-            const float4 r0 = s0[e];
-            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;
-            const float dx = __fsub_rn(r0.x, px);
-            if (fabsf(dx) > r0.z) continue;
-            const float4 r1 = s1[e];
-            const int gi = s_gi[e];
-#pragma unroll
-            for (int j = 0; j < PPT; j++) {
-                if (!((live >> j) & 1u)) continue;
-                float dy, G;
-                bool cl;
-                const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
-                if (a == 0.f) continue;
-                const float Tn = T[j] * (1.f - a);
-                if (Tn < T_STOP) {
-                    live &= ~(1u << j);
-                    continue;
-                }
-                T[j] = Tn;
-                last[j] = gi;
-            }
-        }
-    }
-    int my_last = -1;
-#pragma unroll
-    for (int j = 0; j < PPT; j++) my_last = max(my_last, last[j]);
-    __syncthreads();
-    if (my_last >= 0) atomicMax(&s_end, my_last + 1);
-    __syncthreads();
-    const int end = s_end;
-    // phase 2: back to front
-    const int64_t HW = (int64_t)W * H;
-    float g0[PPT], g1[PPT], g2[PPT], R0[PPT], R1[PPT], R2[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; j++) {
-        g0[j] = g1[j] = g2[j] = 0.f;
-        R0[j] = R1[j] = R2[j] = 0.f;       // colour behind the current splat (background 0)
+        A0[j] = A1[j] = A2[j] = 0.f;
+        F0[j] = F1[j] = F2[j] = g0[j] = g1[j] = g2[j] = 0.f;
         if (x < W && y0 + j < H) {
+            live |= 1u << j;
             const int64_t pix = (int64_t)(y0 + j) * W + x;
+            F0[j] = cfinal[pix];
+            F1[j] = cfinal[HW + pix];
+            F2[j] = cfinal[2 * HW + pix];
             g0[j] = dimage[pix];
             g1[j] = dimage[HW + pix];
             g2[j] = dimage[2 * HW + pix];
         }
     }
-    for (int bend = end; bend > (int)rg.x; bend -= BATCH) {
-        const int bstart = max((int)rg.x, bend - BATCH);
-        __syncthreads();
-        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, (uint32_t)bstart, bend - bstart, X0, X1, Y0,
-                                               Y1, s0, s1, s2, s_k, s_gi, s_wcnt);
-        for (int e = nb - 1; e >= 0; e--) {
+    for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
+        if (__syncthreads_count(live != 0) == 0) break;
+        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
+                                               Y1, s0, s1, s2, s_k, nullptr, s_wcnt);
+        for (int e = 0; e < nb; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
-            const int gi = s_gi[e];
             const float dx = __fsub_rn(r0.x, px);
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-            if (gi <= my_last && fabsf(dx) <= r0.z) {
+            if (live && fabsf(dx) <= r0.z) {
                 const float4 r1 = s1[e];
 #pragma unroll
                 for (int j = 0; j < PPT; j++) {
-                    if (gi > last[j]) continue;
+                    if (!((live >> j) & 1u)) continue;
                     float dy, G;
                     bool cl;
                     const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
                     if (STATS) n_sq += fabsf(dy) <= r0.z ? 1 : 0;
                     if (a == 0.f) continue;
+                    const float Tn = T[j] * (1.f - a);
+                    if (Tn < T_STOP) {
+                        live &= ~(1u << j);
+                        continue;
+                    }
                     if (STATS) n_on++;
                     contrib = true;
                     const float4 c = s2[e];
-                    T[j] = __fdividef(T[j], 1.f - a);        // transmittance in front of this splat
-                    const float dLda = T[j] * (g0[j] * (c.x - R0[j]) + g1[j] * (c.y - R1[j]) + g2[j] * (c.z - R2[j]));
                     const float aT = a * T[j];
+                    A0[j] += c.x * aT;                   // as the forward accumulates C
+                    A1[j] += c.y * aT;
+                    A2[j] += c.z * aT;
+                    const float behind = g0[j] * (F0[j] - A0[j]) + g1[j] * (F1[j] - A1[j]) + g2[j] * (F2[j] - A2[j]);
+                    const float dLda = T[j] * (g0[j] * c.x + g1[j] * c.y + g2[j] * c.z) - __fdividef(behind, 1.f - a);
                     v[6] += g0[j] * aT;
                     v[7] += g1[j] * aT;
                     v[8] += g2[j] * aT;
@@ -552,9 +531,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
                         v[3] += ds * dx * dy;
                         v[4] += 0.5f * ds * dy * dy;
                     }
-                    R0[j] = a * c.x + (1.f - a) * R0[j];
-                    R1[j] = a * c.y + (1.f - a) * R1[j];
-                    R2[j] = a * c.z + (1.f - a) * R2[j];
+                    T[j] = Tn;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -582,9 +559,10 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
 }
 
 typedef void (*RasterFwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
-                            const DevArgs *, int, float *, int, float *, float *);
+                            const DevArgs *, int, float *, float *, int, float *, float *);
 typedef void (*RasterBwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
-                            const DevArgs *, int, const float *, float *, int64_t, unsigned long long *);
+                            const DevArgs *, int, const float *, const float *, float *, int64_t,
+                            unsigned long long *);
 
 // Variant v: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128.
 static RasterFwdFn fwd_variant(int v)
@@ -901,7 +879,8 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
     rb.tiles = tiles;
     const int ppt = 1 << (rb.variant >> 1);
     fwd_variant(rb.variant)<<<tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, image, use_target ? 1 : 0, dimage, loss);
+        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, image, image == rb.cfinal ? nullptr : rb.cfinal,
+        use_target ? 1 : 0, dimage, loss);
 }
 
 static void raster_bwd_stats(int v, int tiles, int threads, const RenderBufs &rb, const DevArgs *args, int view,
@@ -909,12 +888,12 @@ static void raster_bwd_stats(int v, int tiles, int threads, const RenderBufs &rb
 {
     const int64_t cap = rb.cap;
     switch (v) {
-    case 0: k_raster_bwd<1, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
-    case 1: k_raster_bwd<1, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
-    case 2: k_raster_bwd<2, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
-    case 3: k_raster_bwd<2, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
-    case 4: k_raster_bwd<4, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
-    default: k_raster_bwd<4, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, stats); break;
+    case 0: k_raster_bwd<1, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    case 1: k_raster_bwd<1, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    case 2: k_raster_bwd<2, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    case 3: k_raster_bwd<2, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    case 4: k_raster_bwd<4, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    default: k_raster_bwd<4, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
     }
 }
 
@@ -931,7 +910,7 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
         raster_bwd_stats(rb.variant, rb.tiles, cam.tile_w * cam.tile_h / ppt, rb, args, view, dimage, stats, s);
     else
         bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-            rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, dimage, rb.g9, cap, nullptr);
+            rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, nullptr);
     if (view == 0) w.mark(TP_RBWD1, s);
     k_project_bwd<false><<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
         rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix,

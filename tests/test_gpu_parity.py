@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error
+from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, sign_undetermined
 from synth import scenes
 
 pytestmark = pytest.mark.gpu
@@ -515,9 +515,16 @@ def test_bf16_form_step_parity(gs, orc):
             assert np.all(np.abs(gv[s] - V[s]) <= ub * np.abs(V[s]) + 4e-4 * scale_v), (t, k, "v")
         # geometry (fp32): the FP32 form's bound; SH (bf16): one ulp of the
         # stored value plus a 2^-6 relative error of the step lr * m/sqrt(v)
-        assert np.max(np.abs(gw[:11] - W[:11])) <= 2e-3 * lr + 1e-6, t
+        g_full = np.zeros((D, n))
+        g_full[:, kept] = rr["grad"][:, kept]
+        und_all = sign_undetermined(g_full)
+        und = und_all[:11]
+        gerr = np.abs(gw[:11] - W[:11])
+        assert np.all(gerr[~und] <= 2e-3 * lr + 1e-6), (t, np.max(gerr[~und]))
+        assert np.all(gerr[und] <= 2 * lr + 1e-6), t
         err = np.abs(gw[11:] - W[11:])
-        assert np.all(err <= ub * np.abs(W[11:]) + 2 * ub * lr * (t + 1) + 1e-7), (t, np.max(err))
+        bound = ub * np.abs(W[11:]) + 2 * ub * lr * (t + 1) + 1e-7 + np.where(und_all[11:], 2 * lr, 0.0)
+        assert np.all(err <= bound), (t, np.max(err / bound))
         moved = np.abs(W[11:] - W0[11:]) > 0
         assert moved.mean() > 0.1                      # the steps did update SH coefficients
 
@@ -586,7 +593,12 @@ def test_step_parity(gs, orc):
         for k, s in GROUPS.items():
             if M[s].size:
                 assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
-        assert np.max(np.abs(gw - W)) <= 2e-3 * 1e-3 + 1e-6
+        g_full = np.zeros((D, n))
+        g_full[:, kept] = rr["grad"][:, kept]
+        und = sign_undetermined(g_full)
+        err = np.abs(gw - W)
+        assert np.all(err[~und] <= 2e-3 * 1e-3 + 1e-6), np.max(err[~und])
+        assert np.all(err[und] <= 2 * 1e-3 + 1e-6)
 
 
 def test_step_timing_spans(gs):
