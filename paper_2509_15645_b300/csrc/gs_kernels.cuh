@@ -111,6 +111,11 @@ void launch_grad_scatter(const int32_t *ids, const int *n_dev, int cap, const fl
                          float *gfull, int64_t pitch, Work &w, cudaStream_t s);
 
 // k_render.cu
+// Per-splat record of the rasterizer backward's sums: d/d(mean2d x, y), d/d(conic
+// A, B, C), d/d(opacity), d/d(rgb), padded to 12 floats so that a warp adds
+// them with two 16-byte vector atomics and one scalar.
+constexpr int G9_STRIDE = 12;
+
 struct RenderBufs {
     float *compact;          // [D][cap] restored parameters of the visible set
     int64_t cap;             // visible capacity
@@ -122,7 +127,7 @@ struct RenderBufs {
     uint32_t *tk[2], *tv[2]; // tile sort buffers
     int64_t kcap;            // key capacity
     uint2 *ranges;           // [tiles]
-    float *g9;               // [9][cap] screen-space gradient sums
+    float *g9;               // [cap][G9_STRIDE] screen-space gradient sums per splat (9 used)
     int *n_keys;             // device
     float *cfinal;           // [3][H][W] final colour of the last forward render (for the backward)
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
@@ -147,6 +152,7 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
                      Work &w, cudaStream_t s, unsigned long long *stats = nullptr);
 void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
                     cudaStream_t s);
-void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s);
+void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s,
+                      bool aos = false);
 
 }  // namespace gs

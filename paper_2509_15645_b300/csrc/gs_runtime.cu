@@ -204,7 +204,7 @@ static void carve(gs_ctx *c, char *base)
         rb.tv[j] = k.take<uint32_t>(K);
     }
     rb.ranges = k.take<uint2>(tiles);
-    rb.g9 = k.take<float>(9 * V);
+    rb.g9 = k.take<float>(G9_STRIDE * V);
     rb.n_keys = base ? &c->cnt->n_keys : nullptr;
     rb.n_fix = base ? &c->cnt->n_fix : nullptr;
     rb.cfinal = k.take<float>(P);

@@ -539,9 +539,15 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
                 float s8 = v[8];
 #pragma unroll
                 for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
-                float sum = warp_transpose_sum8(v, lane);
-                if ((lane & 3) == 0 && sum != 0.f) atomicAdd(g9 + (lane >> 2) * gcap + k, sum);
-                if (lane == 0 && s8 != 0.f) atomicAdd(g9 + 8 * gcap + k, s8);
+                // lane 4q holds the sum of index q; lanes 0 and 16 gather 0..3 and 4..7
+                const float sum = warp_transpose_sum8(v, lane);
+                const float q1 = __shfl_down_sync(0xffffffffu, sum, 4);
+                const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
+                const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
+                float *row = g9 + (int64_t)k * G9_STRIDE;
+                if ((lane & 15) == 0)
+                    atomicAdd(reinterpret_cast<float4 *>(row + (lane >> 2)), make_float4(sum, q1, q2, q3));
+                if (lane == 0 && s8 != 0.f) atomicAdd(row + 8, s8);
             }
         }
     }
@@ -640,8 +646,13 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
 #pragma unroll
         for (int r = 0; r < N_GEO; r++) g[r] = compact[r * (int64_t)cap + k];
         float gs[9];
-#pragma unroll
-        for (int f = 0; f < 9; f++) gs[f] = g9[f * (int64_t)cap + k];
+        {
+            const float4 *row = reinterpret_cast<const float4 *>(g9 + (int64_t)k * G9_STRIDE);
+            const float4 a = row[0], b = row[1];
+            gs[0] = a.x; gs[1] = a.y; gs[2] = a.z; gs[3] = a.w;
+            gs[4] = b.x; gs[5] = b.y; gs[6] = b.z; gs[7] = b.w;
+            gs[8] = g9[(int64_t)k * G9_STRIDE + 8];
+        }
         Proj P;
         project_gaussian<FIX>(g, cam, P);   // as in the forward (FIX: the FP64 chain)
         float out[N_GEO];
@@ -803,19 +814,26 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap)
+// Zero rows x n entries (n = min(*n_dev, cap)) of a [rows][pitch] array, or,
+// with aos, the first n records of `rows` floats each.
+__global__ void k_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, int aos)
 {
     int n = n_dev ? min(*n_dev, cap) : cap;
     int64_t total = (int64_t)rows * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / n, k = e - r * n;
-        buf[r * pitch + k] = 0.f;
+        if (aos) {
+            buf[e] = 0.f;
+        } else {
+            int64_t r = e / n, k = e - r * n;
+            buf[r * pitch + k] = 0.f;
+        }
     }
 }
 
-void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s)
+void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s,
+                      bool aos)
 {
-    k_zero_rows<<<w.grid((int64_t)rows * cap, 256), 256, 0, s>>>(buf, rows, pitch, n_dev, cap);
+    k_zero_rows<<<w.grid((int64_t)rows * cap, 256), 256, 0, s>>>(buf, rows, pitch, n_dev, cap, aos ? 1 : 0);
 }
 
 __global__ void k_loss_l1(const float *__restrict__ image, const float *__restrict__ target, int64_t count,
@@ -903,7 +921,7 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
                      unsigned long long *stats)
 {
     const int cap = (int)rb.cap;
-    launch_zero_rows(rb.g9, 9, cap, n_vis, cap, w, s);
+    launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
     const int ppt = 1 << (rb.variant >> 1);
     if (view == 0) w.mark(TP_RBWD0, s);
     if (stats)
