@@ -254,12 +254,13 @@ def run_ours(args):
         over the views for the counts behind the algorithmic bytes and flops."""
         sc = gs.GaussianScene(P0, deg, device=dev, precision=precision, tier=tier)
         if tier == gs.GS_TIER_DEVICE:
-            variant, variant_ms = ctx.autotune(sc, cams[0])     # rasterizer variant for this workload (untimed)
-        else:   # the autotuner renders a resident scene: tune on the geometry with a resident copy of the SH
-            variant, variant_ms = 1, [None] * 6
+            variant, ms_f, ms_b = ctx.autotune(sc, cams[0])     # rasterizer variants for this workload (untimed)
+            variant_ms = {"fwd_stage": ms_f, "bwd_stage": ms_b}
+        else:   # the autotuner renders through the resident path
+            variant, variant_ms = (1, 1), {}
         if args.raster_variant is not None:
             ctx.set_raster_variant(args.raster_variant)
-            variant = args.raster_variant
+            variant = (args.raster_variant, args.raster_variant)
         ms_total, spans, clk = timed_steps(sc)
         stats, staged = [], []
         ctx.timing_enable(tcap)
@@ -392,8 +393,9 @@ def run_ours(args):
                    "visible_per_view": round(m["n_vis"]), "keys_per_view": round(m["n_keys"]),
                    "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
                    "square_pairs_per_view": _int(m["sq_pairs"]), "contrib_pairs_per_view": _int(m["on_pairs"]),
-                   "raster_variant": m["variant"],
-                   "autotune_ms": [None if t is None else round(t, 4) for t in m["variant_ms"]]},
+                   "raster_variant": {"fwd": m["variant"][0], "bwd": m["variant"][1]},
+                   "autotune_ms": {k: [None if t is None else round(t, 4) for t in v]
+                                   for k, v in m["variant_ms"].items()}},
         "roofline": roofline(m),
         "cull_adam": m["cull_adam"],
         "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in m["st"].items()},

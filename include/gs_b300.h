@@ -262,11 +262,13 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
 #define GS_RASTER_VARIANTS 6
 
 /* Autotuner: time every variant the context's tile shape allows on this scene
- * and view (cull, render forward, backward; CUDA events, best of three) and
- * keep the fastest for this context.  Synchronises the stream; call it outside
- * stream capture.  *chosen_out (host, may be NULL) receives the variant,
- * ms_out (host, GS_RASTER_VARIANTS floats, may be NULL) the forward+backward
- * milliseconds of each (-1 where not allowed). */
+ * and view (render forward and backward separately; CUDA events, best of
+ * three) and keep the fastest forward and the fastest backward for this
+ * context.  Synchronises the stream; call it outside stream capture.
+ * chosen_out (host, 2 ints, may be NULL) receives the forward and the backward
+ * variant, ms_out (host, 2 * GS_RASTER_VARIANTS floats, may be NULL) the
+ * forward stage's milliseconds of each variant, then the backward stage's (-1
+ * where not allowed).  gs_set_raster_variant sets both. */
 GS_API gs_status gs_autotune(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, int32_t *chosen_out,
                              float *ms_out, void *stream);
 

@@ -324,15 +324,18 @@ class Context:
         return full
 
     def autotune(self, scene: GaussianScene, cam, stream=None):
-        """Time the rasterizer variants on this scene and view; keep the fastest.
-        Returns (chosen variant, per-variant ms or None where not allowed)."""
-        chosen = C.c_int32(-1)
-        ms = (C.c_float * L.RASTER_VARIANTS)()
+        """Time the rasterizer variants on this scene and view; keep the fastest
+        forward and backward.  Returns ((forward variant, backward variant),
+        per-variant forward ms, per-variant backward ms; None where not allowed)."""
+        chosen = (C.c_int32 * 2)(-1, -1)
+        ms = (C.c_float * (2 * L.RASTER_VARIANTS))()
         sc = scene.struct()
         cs = camera_struct(cam)
-        self._check(self.lib.gs_autotune(self.h, C.byref(sc), C.byref(cs), C.byref(chosen), ms, _stream(stream)),
+        self._check(self.lib.gs_autotune(self.h, C.byref(sc), C.byref(cs), chosen, ms, _stream(stream)),
                     "gs_autotune")
-        return chosen.value, [None if t < 0 else t for t in ms]
+        V = L.RASTER_VARIANTS
+        conv = [None if t < 0 else t for t in ms]
+        return (chosen[0], chosen[1]), conv[:V], conv[V:]
 
     def set_raster_variant(self, v):
         self._check(self.lib.gs_set_raster_variant(self.h, int(v)), "gs_set_raster_variant")

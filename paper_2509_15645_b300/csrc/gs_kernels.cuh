@@ -133,7 +133,8 @@ struct RenderBufs {
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0
-    int variant;             // rasterizer variant (pixels per thread, batch), see raster_variant_ok
+    int variant;             // forward rasterizer variant (pixels per thread, batch), see raster_variant_ok
+    int variant_bwd;         // backward rasterizer variant
     // filled by render_fwd
     const uint32_t *sorted_keys;
     const uint32_t *sorted_vals;

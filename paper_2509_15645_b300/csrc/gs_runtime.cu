@@ -416,6 +416,7 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
     c->w.num_sms = c->num_sms;
     c->rb.variant = 1;
     if (!raster_variant_ok(c->rb.variant, cfg->tile_w, cfg->tile_h)) c->rb.variant = 0;
+    c->rb.variant_bwd = c->rb.variant;
     c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
     if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         gs_destroy(c);
@@ -666,7 +667,7 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
 gs_status gs_set_raster_variant(gs_ctx *c, int32_t variant)
 {
     if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h)) return GS_ERR_INVALID_ARG;
-    c->rb.variant = variant;
+    c->rb.variant = c->rb.variant_bwd = variant;
     return GS_OK;
 }
 
@@ -686,46 +687,63 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     int32_t *ids = c->vids[0];
     launch_cull(sv, c->args + SLOT_RENDER, 0, c->mask, c->chunk, c->w, s);
     compact_mask(c->mask, sv.n, c->chunk, true, ids, c->wprefix, (int)c->cfg.max_visible, c->n_render, c->w, s);
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int keep = c->rb.variant;
-    float best = 1e30f;
-    int best_v = keep;
-    for (int v = 0; v < N_RASTER_VARIANTS; v++) {
-        if (ms_out) ms_out[v] = -1.f;
+    cudaEventCreate(&e2);
+    const int keep = c->rb.variant, keep_b = c->rb.variant_bwd;
+    float best_f = 1e30f, best_b = 1e30f;
+    int best_vf = keep, best_vb = keep_b;
+    gs_status res = GS_OK;
+    for (int v = 0; v < N_RASTER_VARIANTS && res == GS_OK; v++) {
+        if (ms_out) ms_out[v] = ms_out[N_RASTER_VARIANTS + v] = -1.f;
         if (!raster_variant_ok(v, c->cfg.tile_w, c->cfg.tile_h)) continue;
-        c->rb.variant = v;
-        float vbest = 1e30f;
+        c->rb.variant = c->rb.variant_bwd = v;
+        float fbest = 1e30f, bbest = 1e30f;
         for (int rep = 0; rep < 4; rep++) {
             cudaEventRecord(e0, s);
             render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], c->img, false, nullptr,
                            nullptr, c->w, s);
+            cudaEventRecord(e1, s);
             // the rendered image itself serves as a dense dL/dimage
             render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rb, a.cam[0], c->img, c->grad_u,
                             c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                c->rb.variant = keep;
-                return cuda_check(c, "gs_autotune");
+            cudaEventRecord(e2, s);
+            if (cudaEventSynchronize(e2) != cudaSuccess) {
+                res = cuda_check(c, "gs_autotune");
+                break;
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0 && ms < vbest) vbest = ms;      // the first run warms caches and clocks
+            float fms = 0.f, bms = 0.f;
+            cudaEventElapsedTime(&fms, e0, e1);
+            cudaEventElapsedTime(&bms, e1, e2);
+            if (rep > 0) {                                 // the first run warms caches and clocks
+                fbest = fminf(fbest, fms);
+                bbest = fminf(bbest, bms);
+            }
         }
-        if (ms_out) ms_out[v] = vbest;
-        if (vbest < best) {
-            best = vbest;
-            best_v = v;
+        if (res != GS_OK) break;
+        if (ms_out) {
+            ms_out[v] = fbest;
+            ms_out[N_RASTER_VARIANTS + v] = bbest;
         }
+        if (fbest < best_f) { best_f = fbest; best_vf = v; }
+        if (bbest < best_b) { best_b = bbest; best_vb = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->rb.variant = best_v;
+    cudaEventDestroy(e2);
+    if (res != GS_OK) {
+        c->rb.variant = keep;
+        c->rb.variant_bwd = keep_b;
+        return res;
+    }
+    c->rb.variant = best_vf;
+    c->rb.variant_bwd = best_vb;
     c->have_fwd = false;
-    if (chosen_out) *chosen_out = best_v;
+    if (chosen_out) {
+        chosen_out[0] = best_vf;
+        chosen_out[1] = best_vb;
+    }
     return cuda_check(c, "gs_autotune");
 }
 
@@ -1049,7 +1067,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         if (!st) scene->step += 1;
         return st;
     }
-    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rb.variant)) {
+    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rb.variant * 16 + c->rb.variant_bwd)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1121,7 +1139,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         g.prec = scene->precision;
         g.loss = loss_out;
         g.timed = timed;
-        g.variant = c->rb.variant;
+        g.variant = c->rb.variant * 16 + c->rb.variant_bwd;
         for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
     }
     if (timed) {

@@ -922,12 +922,12 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
 {
     const int cap = (int)rb.cap;
     launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
-    const int ppt = 1 << (rb.variant >> 1);
+    const int ppt = 1 << (rb.variant_bwd >> 1);
     if (view == 0) w.mark(TP_RBWD0, s);
     if (stats)
-        raster_bwd_stats(rb.variant, rb.tiles, cam.tile_w * cam.tile_h / ppt, rb, args, view, dimage, stats, s);
+        raster_bwd_stats(rb.variant_bwd, rb.tiles, cam.tile_w * cam.tile_h / ppt, rb, args, view, dimage, stats, s);
     else
-        bwd_variant(rb.variant)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
+        bwd_variant(rb.variant_bwd)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
             rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, nullptr);
     if (view == 0) w.mark(TP_RBWD1, s);
     k_project_bwd<false><<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(

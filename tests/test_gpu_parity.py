@@ -258,8 +258,9 @@ def test_raster_variants_agree(gs, orc, name, tile):
     assert tried >= 2
     for im in images[1:]:
         np.testing.assert_array_equal(im, images[0])
-    chosen, ms = ctx.autotune(scene, camf)
-    assert ms[chosen] is not None and ms[chosen] == min(t for t in ms if t is not None)
+    (vf, vb), ms_f, ms_b = ctx.autotune(scene, camf)
+    assert ms_f[vf] is not None and ms_f[vf] == min(t for t in ms_f if t is not None)
+    assert ms_b[vb] is not None and ms_b[vb] == min(t for t in ms_b if t is not None)
 
 
 def test_raster_pair_counts(gs, orc):
