@@ -107,11 +107,12 @@ def build_workload(n, n_views, seed_views=2, density_of=None, width=1920, height
 # FP32 peak of the B300 from unit counts and clock: 148 SMs x 128 FP32 lanes
 # x 2 flops per FMA x 2.032 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# algorithmic FP32 operations of the rasterizer backward per (pixel, splat)
-# pair: a contributing pair costs the forward replay (16) and the adjoint (63);
-# a pair inside the 3-sigma square that does not contribute costs the two
-# alpha evaluations (14 + 14).
-FLOPS_CONTRIB, FLOPS_SQUARE = 79.0, 28.0
+# algorithmic FP32 operations of the rasterizer backward (one front-to-back
+# pass) per (pixel, splat) pair: a contributing pair costs alpha (14), the
+# transmittance and colour accumulation (8), the colour behind it and dL/dalpha
+# (19), the colour gradients (6) and the conic / mean / opacity gradients (21);
+# a pair inside the 3-sigma square that does not contribute costs alpha alone.
+FLOPS_CONTRIB, FLOPS_SQUARE = 68.0, 14.0
 
 
 def _int(x):
