@@ -133,6 +133,9 @@ struct RenderBufs {
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0
+    int *n_big;              // device [2]: sizes of the two large-rectangle lists
+    int32_t *big_idx;        // [cap] splats whose tiles k_big_counts counts
+    int32_t *big_rank;       // [cap] depth ranks whose keys k_big_emit writes
     int variant;             // forward rasterizer variant (pixels per thread, batch), see raster_variant_ok
     int variant_bwd;         // backward rasterizer variant
     // filled by render_fwd

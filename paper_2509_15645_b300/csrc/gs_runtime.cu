@@ -210,6 +210,9 @@ static void carve(gs_ctx *c, char *base)
     rb.cfinal = k.take<float>(P);
     rb.fix_idx = k.take<int32_t>(V);
     rb.fix_flag = k.take<uint8_t>(V);
+    rb.n_big = k.take<int>(2);
+    rb.big_idx = k.take<int32_t>(V);
+    rb.big_rank = k.take<int32_t>(V);
     int64_t big = K > V ? K : V;
     c->w.hist = k.take<uint32_t>(256 * ((big + RADIX_TILE - 1) / RADIX_TILE) + 256);
     c->w.partials = k.take<uint32_t>(1024);

@@ -30,6 +30,73 @@ struct SLutR {
     int restore;
 };
 
+// Can splat (r0, r1) reach alpha >= 1/255 at any pixel centre of the box
+// [X0, X1] x [Y0, Y1]?  Intersects the box with the splat's square (widened
+// by a small margin), takes the minimum of sigma over the remaining rectangle
+// (zero if the mean is inside, otherwise on an edge, where sigma is a 1-D
+// quadratic) and compares o exp(-sigma_min) with the floor, with 0.1% slack.
+// It only ever says "no" when no pixel can pass the per-pixel tests, so
+// dropping such splats leaves every pixel's result unchanged.
+__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
+{
+    const float margin = 1e-3f;
+    const float x0 = fmaxf(X0, r0.x - r0.z - margin), x1 = fminf(X1, r0.x + r0.z + margin);
+    const float y0 = fmaxf(Y0, r0.y - r0.z - margin), y1 = fminf(Y1, r0.y + r0.z + margin);
+    if (x0 > x1 || y0 > y1) return false;
+    // d = mean - p over the rectangle
+    const float dxl = r0.x - x1, dxh = r0.x - x0, dyl = r0.y - y1, dyh = r0.y - y0;
+    const float A = r1.x, B = r1.y, C = r1.z;
+    float smin = 0.f;
+    if (!(dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f)) {
+        smin = 3.4e38f;
+        // edges dx = const: minimiser dy = -B dx / C
+        const float dxs[2] = {dxl, dxh};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float dx = dxs[k];
+            const float dy = fminf(fmaxf(-B * dx / C, dyl), dyh);
+            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+        }
+        const float dys[2] = {dyl, dyh};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float dy = dys[k];
+            const float dx = fminf(fmaxf(-B * dy / A, dxl), dxh);
+            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+        }
+        smin = fmaxf(smin, 0.f);
+    }
+    return r0.w * __expf(-smin) >= ALPHA_MIN * 0.999f;
+}
+
+// Pixel-centre box of tile (t_x, t_y).
+__device__ __forceinline__ void tile_box(const DevCam &cam, int t_x, int t_y, float &X0, float &X1, float &Y0,
+                                         float &Y1)
+{
+    X0 = (float)(t_x * cam.tile_w) + 0.5f;
+    X1 = X0 + (float)(cam.tile_w - 1);
+    Y0 = (float)(t_y * cam.tile_h) + 0.5f;
+    Y1 = Y0 + (float)(cam.tile_h - 1);
+}
+
+// Rectangles of more tiles than this are counted and emitted by a warp
+// (k_big_counts, k_big_emit); smaller ones by the splat's own thread.
+constexpr int BIG_RECT = 32;
+
+// Number of tiles of [x0, x1) x [y0, y1) that splat (r0, r1) reaches, row-major.
+__device__ __forceinline__ uint32_t count_reach(float4 r0, float4 r1, int x0, int x1, int y0, int y1,
+                                                const DevCam &cam)
+{
+    uint32_t c = 0;
+    for (int ty = y0; ty < y1; ty++)
+        for (int tx = x0; tx < x1; tx++) {
+            float X0, X1, Y0, Y1;
+            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+            c += splat_reaches_box(r0, r1, X0, X1, Y0, Y1) ? 1u : 0u;
+        }
+    return c;
+}
+
 template <int DEG, typename T>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
                                                                const int *n_vis_p, int cap,
@@ -39,7 +106,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                                                                uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
                                                                uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect,
                                                                int *__restrict__ n_fix, int32_t *__restrict__ fix_idx,
-                                                               uint8_t *__restrict__ fix_flag)
+                                                               uint8_t *__restrict__ fix_flag, int *__restrict__ n_big,
+                                                               int32_t *__restrict__ big_idx)
 {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     constexpr int D = N_GEO + 3 * NK;
@@ -117,12 +185,21 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
 #pragma unroll
         for (int c = 0; c < 3; c++) rgb[c] = fmaxf(rgb[c] + 0.5f, 0.f);
         float o = 1.f / (1.f + expf(-w[ROW_OPAC]));
-        rec0[k] = make_float4(P.mx, P.my, P.radius, o);
-        rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
+        const float4 r0v = make_float4(P.mx, P.my, P.radius, o), r1v = make_float4(P.conA, P.conB, P.conC, P.p[2]);
+        rec0[k] = r0v;
+        rec1[k] = r1v;
         rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
         dkey[k] = __float_as_uint(P.p[2]);
         dval[k] = (uint32_t)k;
-        uint32_t cnt = P.keep ? (uint32_t)((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2])) : 0u;
+        // tiles the splat reaches (the list filter); FP64-flagged splats and
+        // large rectangles are counted by k_big_counts
+        uint32_t cnt = 0;
+        if (P.keep && !P.fp64) {
+            if ((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2]) <= BIG_RECT)
+                cnt = count_reach(r0v, r1v, P.rect[0], P.rect[1], P.rect[2], P.rect[3], s_cam);
+            else
+                big_idx[atomicAdd(n_big, 1)] = k;
+        }
         tcnt[k] = cnt;
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
@@ -135,7 +212,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restr
                                                             const int *__restrict__ n_fix,
                                                             const int32_t *__restrict__ fix_idx,
                                                             const DevArgs *__restrict__ args, int view, float4 *rec0,
-                                                            float4 *rec1, uint32_t *tcnt, uint2 *rect)
+                                                            float4 *rec1, uint32_t *tcnt, uint2 *rect, int *n_big,
+                                                            int32_t *big_idx)
 {
     __shared__ DevCam s_cam;
     if (threadIdx.x < sizeof(DevCam) / 4)
@@ -153,10 +231,12 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restr
         const float o = rec0[k].w;
         rec0[k] = make_float4(P.mx, P.my, P.radius, o);
         rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
-        tcnt[k] = P.keep ? (uint32_t)((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2])) : 0u;
+        tcnt[k] = 0u;
+        if (P.keep) big_idx[atomicAdd(n_big, 1)] = k;        // counted by k_big_counts
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
 }
+
 
 __global__ void k_rank_counts(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ tcnt,
                               const int *n_vis_p, int cap, uint32_t *rank_cnt)
@@ -166,25 +246,118 @@ __global__ void k_rank_counts(const uint32_t *__restrict__ sorted_vals, const ui
         rank_cnt[r] = tcnt[sorted_vals[r]];
 }
 
-__global__ void k_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
-                       const uint2 *__restrict__ rect, const int *n_vis_p, int cap, int64_t kcap,
-                       const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval)
+
+// Tiles reached by the splats of the big list (large rectangles, FP64-fixed
+// splats): one warp per splat, lanes over the rectangle's tiles.
+__global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                             const uint2 *__restrict__ rect, const int *__restrict__ n_big,
+                             const int32_t *__restrict__ big_idx, int cap, const DevArgs *__restrict__ args, int view,
+                             uint32_t *__restrict__ tcnt)
 {
-    int n = min(*n_vis_p, cap);
-    int tiles_x = args->cam[view].tiles_x;
+    const int nb = min(*n_big, cap);
+    const DevCam &cam = args->cam[view];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nwarps) {
+        const int k = big_idx[j];
+        const uint2 rc = rect[k];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
+        uint32_t cnt = 0;
+        if (cnt_all > 0) {
+            const float4 r0 = rec0[k], r1 = rec1[k];
+            for (int t = lane; t < cnt_all; t += 32) {
+                float X0, X1, Y0, Y1;
+                tile_box(cam, x0 + t % wdt, y0 + t / wdt, X0, X1, Y0, Y1);
+                cnt += splat_reaches_box(r0, r1, X0, X1, Y0, Y1) ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) tcnt[k] = cnt;
+    }
+}
+
+// Keys of the splats in depth order: the splat of rank r writes (tile, k) for
+// each tile it reaches, in row-major tile order, from offset ofs[r].  Small
+// rectangles by the rank's thread; large ones go to a list for k_big_emit.
+__global__ void k_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
+                       const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
+                       const float4 *__restrict__ rec1, const int *n_vis_p, int cap, int64_t kcap,
+                       const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval, int *n_big_emit,
+                       int32_t *big_rank)
+{
+    const int n = min(*n_vis_p, cap);
+    const DevCam &cam = args->cam[view];
+    const int tiles_x = cam.tiles_x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        uint32_t k = sorted_vals[r];
+        const uint32_t k = sorted_vals[r];
+        const uint2 rc = rect[k];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const int area = (x1 - x0) * (y1 - y0);
+        if (area <= 0) continue;
+        if (area > BIG_RECT) {
+            big_rank[atomicAdd(n_big_emit, 1)] = r;
+            continue;
+        }
         int64_t o = ofs[r];
-        uint2 rc = rect[k];
-        int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const float4 r0 = rec0[k], r1 = rec1[k];
         for (int ty = y0; ty < y1; ty++)
             for (int tx = x0; tx < x1; tx++) {
+                float X0, X1, Y0, Y1;
+                tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+                if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
                 if (o < kcap) {
                     tkey[o] = (uint32_t)(ty * tiles_x + tx);
                     tval[o] = k;
                 }
                 o++;
             }
+    }
+}
+
+// The large rectangles of k_emit: one warp per splat, a ballot orders the
+// lanes' keys.
+__global__ void k_big_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
+                           const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
+                           const float4 *__restrict__ rec1, const int *__restrict__ n_big_emit,
+                           const int32_t *__restrict__ big_rank, int cap, int64_t kcap,
+                           const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval)
+{
+    const int nb = min(*n_big_emit, cap);
+    const DevCam &cam = args->cam[view];
+    const int tiles_x = cam.tiles_x;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nwarps) {
+        const int r = big_rank[j];
+        const uint32_t k = sorted_vals[r];
+        int64_t o = ofs[r];
+        const uint2 rc = rect[k];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
+        const float4 r0 = rec0[k], r1 = rec1[k];
+        for (int t0 = 0; t0 < cnt_all; t0 += 32) {
+            const int t = t0 + lane;
+            bool hit = false;
+            int tx = 0, ty = 0;
+            if (t < cnt_all) {
+                tx = x0 + t % wdt;
+                ty = y0 + t / wdt;
+                float X0, X1, Y0, Y1;
+                tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+                hit = splat_reaches_box(r0, r1, X0, X1, Y0, Y1);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int64_t p = o + __popc(bal & ((1u << lane) - 1u));
+                if (p < kcap) {
+                    tkey[p] = (uint32_t)(ty * tiles_x + tx);
+                    tval[p] = k;
+                }
+            }
+            o += __popc(bal);
+        }
     }
 }
 
@@ -218,91 +391,23 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
     return t;
 }
 
-// Can splat (r0, r1) reach alpha >= 1/255 at any pixel centre of the box
-// [X0, X1] x [Y0, Y1]?  Intersects the box with the splat's square (widened
-// by a small margin), takes the minimum of sigma over the remaining rectangle
-// (zero if the mean is inside, otherwise on an edge, where sigma is a 1-D
-// quadratic) and compares o exp(-sigma_min) with the floor, with 0.1% slack.
-// It only ever says "no" when no pixel can pass the per-pixel tests, so
-// dropping such splats leaves every pixel's result unchanged.
-__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
-{
-    const float margin = 1e-3f;
-    const float x0 = fmaxf(X0, r0.x - r0.z - margin), x1 = fminf(X1, r0.x + r0.z + margin);
-    const float y0 = fmaxf(Y0, r0.y - r0.z - margin), y1 = fminf(Y1, r0.y + r0.z + margin);
-    if (x0 > x1 || y0 > y1) return false;
-    // d = mean - p over the rectangle
-    const float dxl = r0.x - x1, dxh = r0.x - x0, dyl = r0.y - y1, dyh = r0.y - y0;
-    const float A = r1.x, B = r1.y, C = r1.z;
-    float smin = 0.f;
-    if (!(dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f)) {
-        smin = 3.4e38f;
-        // edges dx = const: minimiser dy = -B dx / C
-        const float dxs[2] = {dxl, dxh};
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const float dx = dxs[k];
-            const float dy = fminf(fmaxf(-B * dx / C, dyl), dyh);
-            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
-        }
-        const float dys[2] = {dyl, dyh};
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const float dy = dys[k];
-            const float dx = fminf(fmaxf(-B * dy / A, dxl), dxh);
-            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
-        }
-        smin = fmaxf(smin, 0.f);
-    }
-    return r0.w * __expf(-smin) >= ALPHA_MIN * 0.999f;
-}
 
-// Stage the tile's list entries [b, b + cnt) into shared memory, keeping, in
-// list order, only the splats that can reach some pixel of the tile.  Returns
-// the number kept.  s_gi receives each kept entry's position in the list.
+// Stage the tile's list entries [b, b + cnt) into shared memory (the lists
+// hold only splats that can reach the tile: k_tile_counts / k_emit).
 template <bool COLOR, bool INDEX>
 __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
                                            const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
-                                           uint32_t b, int cnt, float X0, float X1, float Y0, float Y1, float4 *s0,
-                                           float4 *s1, float4 *s2, uint32_t *s_k, int *s_gi, int *s_wcnt)
+                                           uint32_t b, int cnt, float4 *s0, float4 *s1, float4 *s2, uint32_t *s_k)
 {
-    const int nt = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = nt >> 5;
-    int base = 0;
-    for (int r0 = 0; r0 < cnt; r0 += nt) {
-        const int e = r0 + (int)threadIdx.x;
-        bool keep = false;
-        float4 a0, a1, a2;
-        uint32_t k = 0;
-        if (e < cnt) {
-            k = svals[b + e];
-            a0 = rec0[k];
-            a1 = rec1[k];
-            keep = splat_reaches_box(a0, a1, X0, X1, Y0, Y1);
-            if (COLOR && keep) a2 = rec2[k];
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) s_wcnt[wid] = __popc(bal);
-        __syncthreads();
-        int off = base, tot = 0;
-        for (int w = 0; w < nw; w++) {
-            const int c = s_wcnt[w];
-            off += w < wid ? c : 0;
-            tot += c;
-        }
-        if (keep) {
-            const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            s0[pos] = a0;
-            s1[pos] = a1;
-            if (COLOR) s2[pos] = a2;
-            if (INDEX) {
-                s_k[pos] = k;
-                if (s_gi) s_gi[pos] = (int)b + e;
-            }
-        }
-        base += tot;
-        __syncthreads();
+    for (int e = (int)threadIdx.x; e < cnt; e += blockDim.x) {
+        const uint32_t k = svals[b + e];
+        s0[e] = rec0[k];
+        s1[e] = rec1[k];
+        if (COLOR) s2[e] = rec2[k];
+        if (INDEX) s_k[e] = k;
     }
-    return base;
+    __syncthreads();
+    return cnt;
 }
 
 template <int PPT, int BATCH>
@@ -314,7 +419,6 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
                                                     float *__restrict__ loss)
 {
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
-    __shared__ int s_wcnt[8];
     __shared__ float s_red[8];
     const DevCam &cam = args->cam[view];
     const float *target = use_target ? args->target[view] : nullptr;
@@ -329,7 +433,6 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
     const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
     const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
-    const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t live = 0;   // bit j: pixel j still compositing
@@ -341,8 +444,8 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
     }
     for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
         if (__syncthreads_count(live != 0) == 0) break;
-        const int nb = stage_batch<true, false>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
-                                                Y1, s0, s1, s2, nullptr, nullptr, s_wcnt);
+        const int nb = stage_batch<true, false>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1, s2,
+                                                nullptr);
         for (int e = 0; e < nb && live; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
@@ -450,7 +553,6 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     unsigned long long n_sq = 0, n_on = 0;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ uint32_t s_k[BATCH];
-    __shared__ int s_wcnt[8];
     const DevCam &cam = args->cam[view];
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tile = blockIdx.x;
@@ -463,7 +565,6 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
     const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
-    const float X0 = (float)tx0 + 0.5f, X1 = X0 + (float)(tw - 1), Y0 = (float)ty0 + 0.5f, Y1 = Y0 + (float)(th - 1);
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
     const int64_t HW = (int64_t)W * H;
@@ -487,8 +588,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     }
     for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
         if (__syncthreads_count(live != 0) == 0) break;
-        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), X0, X1, Y0,
-                                               Y1, s0, s1, s2, s_k, nullptr, s_wcnt);
+        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1, s2,
+                                               s_k);
         for (int e = 0; e < nb; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
@@ -875,19 +976,24 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
                   : (sc.deg == 3 ? k_gather_project<3, __nv_bfloat16> : sc.deg == 2 ? k_gather_project<2, __nv_bfloat16>
                      : sc.deg == 1 ? k_gather_project<1, __nv_bfloat16> : k_gather_project<0, __nv_bfloat16>);
     cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
+    cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
                                                           rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect, rb.n_fix,
-                                                          rb.fix_idx, rb.fix_flag);
+                                                          rb.fix_idx, rb.fix_flag, rb.n_big, rb.big_idx);
     k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
-                                                    rb.tcnt, rb.rect);
+                                                    rb.tcnt, rb.rect, rb.n_big, rb.big_idx);
+    k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
+                                               rb.tcnt);
     // depth order of the visible set (stable: ties keep ascending index)
     int dcur = radix_sort(rb.dk[0], rb.dv[0], rb.dk[1], rb.dv[1], n_vis, cap, 32, w, s);
     const uint32_t *dsorted = rb.dv[dcur];
     k_rank_counts<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.tcnt, n_vis, cap, rb.rank_cnt);
     ScanLen L{n_vis, 1, 1, 0, 0, cap};
     scan_exclusive(rb.rank_cnt, rb.rank_cnt, L, w, rb.n_keys, (int)rb.kcap, s);
-    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, n_vis, cap, rb.kcap, args, view, rb.tk[0],
-                                            rb.tv[0]);
+    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, rb.rec0, rb.rec1, n_vis, cap, rb.kcap, args,
+                                            view, rb.tk[0], rb.tv[0], rb.n_big + 1, rb.big_rank);
+    k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, rb.rec0, rb.rec1, rb.n_big + 1, rb.big_rank,
+                                             cap, rb.kcap, args, view, rb.tk[0], rb.tv[0]);
     const int tiles = cam.tiles_x * cam.tiles_y;
     int tcur = radix_sort(rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_keys, (int)rb.kcap, bits_for(tiles), w, s);
     cudaMemsetAsync(rb.ranges, 0, (size_t)tiles * sizeof(uint2), s);

@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, sign_undetermined
+from helpers import (GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, sign_undetermined,
+                     splat_max_alpha_in_tile)
 from synth import scenes
 
 pytestmark = pytest.mark.gpu
@@ -132,7 +133,18 @@ def test_key_lists_parity(gs, orc, name):
     sp = r["splats"]
     exclude = np.nonzero(sp["margin"] < TIE_TOL)[0]
     dbits = sp["depth"].astype(np.float32).view(np.uint32)
-    swaps = check_lists(keys, gpu_gid, r["key_tile"].astype(np.int64), r["key_gid"], dbits, exclude)
+    # the GPU lists drop (tile, splat) pairs the splat cannot reach with alpha >=
+    # 1/255 at any pixel centre of the tile; the rest is the oracle's sequence
+    ot, og = r["key_tile"].astype(np.int64), r["key_gid"].astype(np.int64)
+    gpu_pairs = set(zip(keys.tolist(), gpu_gid.tolist()))
+    kept = np.array([(t, g) in gpu_pairs for t, g in zip(ot.tolist(), og.tolist())], bool)
+    tie = np.isin(og, exclude)
+    assert len(gpu_pairs - set(zip(ot.tolist(), og.tolist()))) == 0 or np.all(np.isin(
+        [g for (t, g) in gpu_pairs - set(zip(ot.tolist(), og.tolist()))], exclude))
+    for t, g in zip(ot[~kept & ~tie].tolist(), og[~kept & ~tie].tolist()):
+        amax = splat_max_alpha_in_tile(sp, g, t, tx, d["tile"][0], d["tile"][1])
+        assert amax < (1.0 / 255.0) * (1.0 + 1e-3), (t, g, amax)
+    swaps = check_lists(keys, gpu_gid, ot[kept | tie], og[kept | tie], dbits, exclude)
     assert swaps <= 4
     # ranges delimit each tile's run
     rg = ranges.cpu().numpy().astype(np.int64)
