@@ -130,7 +130,17 @@ __device__ __forceinline__ float st_val(__nv_bfloat16 *p, float x, bool stochast
 // optimizer (the scene's rdir planes) so that the restore is one FMA; the two
 // helpers below are the only places either quantity is formed, so a stored
 // direction and a recomputed one give the same restored value bit for bit.
-__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return __fdividef(m, sqrtf(v) + eps); }
+// Square root by the hardware approximation (PTX sqrt.approx.f32, a few ulps;
+// no denormal flush): the optimizer's divisors sqrt(v) + eps need no IEEE
+// rounding, and one helper keeps every restore direction the same bit for bit.
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return __fdividef(m, sqrt_fast(v) + eps); }
 
 __device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, int d)
 {

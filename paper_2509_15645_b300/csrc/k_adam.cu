@@ -125,7 +125,7 @@ __device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g
     float m_new = L.mom[d] * m + L.omb1 * g;
     float v_new = L.var[d] * v + L.omb2 * g * g;
     float wr = restore_param(w, m, v, L.param[grp][d], d, L.eps);
-    float denom = sqrtf(v_new) * L.inv_bias_corr + L.eps;
+    float denom = sqrt_fast(v_new) * L.inv_bias_corr + L.eps;
     w = wr - L.step_size[grp] * __fdividef(m_new, denom);
     m = m_new;
     v = v_new;
