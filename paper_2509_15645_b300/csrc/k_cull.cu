@@ -87,13 +87,145 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
     }
 }
 
+// The same cull with the planes staged in shared memory by the TMA engine:
+// tiles of CT Gaussians, each the CT-element segments of the 10 geometry
+// planes and (restoring) their 10 restore-direction planes, in a ring of
+// CSTAGES buffers, so HBM streams independently of how many warps are
+// resident.  Thread 0 issues the bulk copies CSTAGES - 1 tiles ahead; every
+// thread waits on the tile's barrier (bounded: on a timeout the block latches
+// GS_ERR_TIMEOUT and stops after draining what it issued).
+constexpr int CT = 256, CSTAGES = 3, CPLANES = 10;
+struct CullStage {
+    float geo[CPLANES][CT];
+    float dir[CPLANES][CT];
+};
+constexpr size_t CULL_SMEM = sizeof(CullStage) * CSTAGES;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+__global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
+                                                   const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
+                                                   const DevArgs *__restrict__ args, int view,
+                                                   uint32_t *__restrict__ mask, uint32_t *__restrict__ chunk_cnt,
+                                                   int *status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    CullStage *st = reinterpret_cast<CullStage *>(smem);
+    __shared__ __align__(8) uint64_t bar[CSTAGES];
+    __shared__ DevCam s_cam;
+    __shared__ float s_plut[3][LUT_N];
+    __shared__ uint32_t s_cnt[CT / 32];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid < sizeof(DevCam) / 4) ((uint32_t *)&s_cam)[tid] = ((const uint32_t *)&args->cam[view])[tid];
+    if (tid < 3 * LUT_N) s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
+    const bool restore = args->lut.restore && rdir != nullptr && counter != nullptr;
+    if (tid == 0) {
+        s_abort = 0;
+        for (int k = 0; k < CSTAGES; k++) mbar_init(&bar[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    constexpr int PER_CHUNK = CHUNK / CT;
+    const int64_t ntiles = (n + CT - 1) / CT, nchunks = (n + CHUNK - 1) / CHUNK;
+    // q-th tile of this block (chunks blockIdx.x, + gridDim.x, ...), or -1
+    auto tile_of = [&](int64_t q) -> int64_t {
+        const int64_t c = blockIdx.x + (q / PER_CHUNK) * gridDim.x;
+        if (c >= nchunks) return -1;
+        const int64_t t = c * PER_CHUNK + q % PER_CHUNK;
+        return t < ntiles ? t : -1;
+    };
+    auto issue = [&](int64_t q) {                  // thread 0 only
+        const int64_t t = tile_of(q);
+        if (t < 0) return;
+        const int s = (int)(q % CSTAGES);
+        const int64_t i0 = t * CT;
+        const int64_t rows = min((int64_t)CT, n - i0);
+        const uint32_t bytes = (uint32_t)(((rows + 3) & ~3ll) * 4);   // within the plane: pitch >= n, a multiple of 4
+        mbar_expect_tx(&bar[s], bytes * CPLANES * (restore ? 2u : 1u));
+        for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].geo[r], geo + r * pitch + i0, bytes, &bar[s]);
+        if (restore)
+            for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].dir[r], rdir + r * pitch + i0, bytes, &bar[s]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < CSTAGES - 1; q++) issue(q);
+    int64_t issued_to = CSTAGES - 1;               // tiles [0, issued_to) issued (thread 0's view)
+    int64_t q_stop = 0;                            // first tile not consumed when the loop ends
+    uint32_t cnt = 0;
+    for (int64_t q = 0;; q++) {
+        q_stop = q;
+        const int64_t c = blockIdx.x + (q / PER_CHUNK) * gridDim.x;
+        if (c >= nchunks) break;
+        if (tid == 0) {
+            issue(q + CSTAGES - 1);                // into the buffer freed at the end of tile q - 1
+            issued_to = q + CSTAGES;
+        }
+        const int64_t t = tile_of(q);
+        int keep = 0;
+        if (t >= 0) {
+            const int s = (int)(q % CSTAGES);
+            if (!mbar_wait_bounded(&bar[s], (uint32_t)((q / CSTAGES) & 1), WAIT_LIMIT)) s_abort = 1;
+            const int64_t i = t * CT + tid;
+            if (i < n && !s_abort) {
+                float g[CPLANES];
+#pragma unroll
+                for (int r = 0; r < CPLANES; r++) g[r] = st[s].geo[r][tid];
+                if (restore) {
+                    const int d = counter[i];
+#pragma unroll
+                    for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
+                }
+                Proj P;
+                project_gaussian(g, s_cam, P);
+                keep = P.keep;
+            }
+            const uint32_t word = __ballot_sync(0xffffffffu, keep);
+            const int64_t wbase = t * CT + wid * 32;
+            if (lane == 0 && wbase < n) {
+                mask[wbase >> 5] = word;
+                cnt += __popc(word);
+            }
+        }
+        __syncthreads();                           // buffer q % CSTAGES is free again
+        if (s_abort) break;                        // q_stop = q: its copy may still be landing
+        if (q % PER_CHUNK == PER_CHUNK - 1) {
+            if (lane == 0) s_cnt[wid] = cnt;
+            cnt = 0;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t tot = 0;
+                for (int k = 0; k < CT / 32; k++) tot += s_cnt[k];
+                chunk_cnt[c] = tot;
+            }
+        }
+    }
+    if (s_abort && tid == 0) {
+        latch(status, GS_ERR_TIMEOUT);
+        // let the copies this block issued and did not consume land before its
+        // shared memory goes away (at most CSTAGES - 1 tiles)
+        for (int64_t q = q_stop; q < issued_to; q++)
+            if (tile_of(q) >= 0) mbar_wait_bounded(&bar[q % CSTAGES], (uint32_t)((q / CSTAGES) & 1), WAIT_LIMIT);
+    }
+}
+
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
                  cudaStream_t s)
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (view == 0) w.mark(TP_CULL0, s);
     const int g = w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8);
-    if (sc.prec == GS_FP32)
+    const bool restore_dir_path = sc.rdir != nullptr || !(sc.m && sc.v && sc.counter);
+    const bool aligned = ((uintptr_t)sc.geo & 15) == 0 && ((uintptr_t)sc.rdir & 15) == 0;   // bulk-copy rule
+    if (restore_dir_path && aligned) {
+        // geometry (and restore directions) staged by the TMA engine
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_cull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
+            attr_set = true;
+        }
+        const int gt = w.grid(nchunks * CT, CT, 3);
+        k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view, mask, chunk_cnt,
+                                              w.status);
+    } else if (sc.prec == GS_FP32)
         k_cull<float><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const float *)sc.m, (const float *)sc.v, sc.rdir, sc.counter,
                                                sc.pitch, sc.n, args, view, mask, chunk_cnt);
     else
