@@ -144,47 +144,49 @@ __device__ __forceinline__ int compact_index(const uint32_t *__restrict__ vmask,
 // type T, restore direction fp32) at r * pitch + i; SH plane r (w, m, v and
 // restore direction of type T) at (r - 11) * sp + sb, where sb = shbase(i) is
 // i for a resident scene and the staging-ring element for the host tier.
-template <typename T> struct Planes {
+template <typename T, typename IX = int64_t> struct Planes {
     float *geo;
     T *m, *v;
     float *rdir;
     T *shw, *shm, *shv, *shr;
-    int64_t pitch, sp;
+    IX pitch, sp;
     const int32_t *slot;
     int shift;
-    __device__ __forceinline__ int64_t shbase(int64_t i) const
+    __device__ __forceinline__ IX shbase(IX i) const
     {
         if (!slot) return i;
-        return ((int64_t)max(__ldg(slot + (i >> shift)), 0) << shift) + (i & ((1ll << shift) - 1));
+        return ((IX)max(__ldg(slot + (i >> shift)), 0) << shift) + (i & (((IX)1 << shift) - 1));
     }
-    __device__ __forceinline__ float ldw(int r, int64_t i, int64_t sb) const
+    __device__ __forceinline__ IX go(int r, IX i) const { return (IX)r * pitch + i; }
+    __device__ __forceinline__ IX so(int r, IX sb) const { return (IX)(r - N_GEO) * sp + sb; }
+    __device__ __forceinline__ float ldw(int r, IX i, IX sb) const
     {
-        return r < N_GEO ? geo[r * pitch + i] : ld_val(shw + (r - N_GEO) * sp + sb);
+        return r < N_GEO ? geo[go(r, i)] : ld_val(shw + so(r, sb));
     }
-    __device__ __forceinline__ float ldm(int r, int64_t i, int64_t sb) const
+    __device__ __forceinline__ float ldm(int r, IX i, IX sb) const
     {
-        return ld_val(r < N_GEO ? m + r * pitch + i : shm + (r - N_GEO) * sp + sb);
+        return ld_val(r < N_GEO ? m + go(r, i) : shm + so(r, sb));
     }
-    __device__ __forceinline__ float ldv(int r, int64_t i, int64_t sb) const
+    __device__ __forceinline__ float ldv(int r, IX i, IX sb) const
     {
-        return ld_val(r < N_GEO ? v + r * pitch + i : shv + (r - N_GEO) * sp + sb);
+        return ld_val(r < N_GEO ? v + go(r, i) : shv + so(r, sb));
     }
     // Store the updated w, m, v of plane r (rounded per the storage; `key` is
     // sr_plane_key of this plane and step) and the restore direction of what
     // was stored.
-    __device__ __forceinline__ void store(int r, int64_t i, int64_t sb, float w, float mm, float vv, const SLut &L,
+    __device__ __forceinline__ void store(int r, IX i, IX sb, float w, float mm, float vv, const SLut &L,
                                           uint32_t key) const
     {
         const bool st = L.stochastic != 0;
         const uint32_t bits = st ? sr_bits(key, (uint32_t)i) : 0u;
         if (r < N_GEO) {
-            const int64_t o = r * pitch + i;
+            const IX o = go(r, i);
             const float ms = st_val(m + o, mm, st, bits);
             const float vs = st_val(v + o, vv, st, bits >> 16);
             geo[o] = w;
             if (rdir) rdir[o] = restore_dir(ms, vs, L.eps);
         } else {
-            const int64_t o = (r - N_GEO) * sp + sb;
+            const IX o = so(r, sb);
             const float ms = st_val(shm + o, mm, st, bits);
             const float vs = st_val(shv + o, vv, st, bits >> 16);
             st_val(shw + o, w, st, sr_w_bits(bits));
@@ -229,19 +231,19 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
 // already cleared its counter).
 constexpr int RG = 4;
 
-struct AdamRows {
+template <typename IX> struct AdamRows {
     float w[RG], m[RG], v[RG], g[RG];
-    int64_t i, sb;
+    IX i, sb;
     int d;
 };
 
-template <typename T>
-__device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__restrict__ uids,
+template <typename T, typename IX>
+__device__ __forceinline__ void adam_fetch(AdamRows<IX> &a, int u, const int32_t *__restrict__ uids,
                                            const uint8_t *__restrict__ udelay, const uint32_t *__restrict__ vmask,
-                                           const uint32_t *__restrict__ vprefix, const Planes<T> &P,
+                                           const uint32_t *__restrict__ vprefix, const Planes<T, IX> &P,
                                            const float *__restrict__ grad, int64_t gcap, int D, int r0)
 {
-    a.i = uids[u];
+    a.i = (IX)uids[u];
     a.sb = P.shbase(a.i);
     a.d = udelay[u];
     int k = compact_index(vmask, vprefix, a.i);
@@ -258,8 +260,8 @@ __device__ __forceinline__ void adam_fetch(AdamRows &a, int u, const int32_t *__
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D, const int32_t *__restrict__ uids,
+template <typename T, typename IX>
+__global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T, IX> P, int D, const int32_t *__restrict__ uids,
                                                            const uint8_t *__restrict__ udelay, const int *u_range,
                                                            const int *n_upd_p,
                                                            const uint32_t *__restrict__ vmask,
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D
     uint32_t key[RG];          // stochastic-rounding keys of this thread's planes
 #pragma unroll
     for (int j = 0; j < RG; j++) key[j] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + j)) : 0u;
-    AdamRows cur, nxt;
+    AdamRows<IX> cur, nxt;
     adam_fetch(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
     while (true) {
         const int un = u + stride;
@@ -299,9 +301,9 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T> P, int D
     }
 }
 
-template <typename T> static Planes<T> planes_of(const SceneView &sc)
+template <typename T, typename IX = int64_t> static Planes<T, IX> planes_of(const SceneView &sc)
 {
-    Planes<T> P;
+    Planes<T, IX> P;
     P.geo = sc.geo;
     P.m = (T *)sc.m;
     P.v = (T *)sc.v;
@@ -310,11 +312,19 @@ template <typename T> static Planes<T> planes_of(const SceneView &sc)
     P.shm = (T *)sc.sh.m;
     P.shv = (T *)sc.sh.v;
     P.shr = sc.rdir ? (T *)sc.sh.rdir : nullptr;
-    P.pitch = sc.pitch;
-    P.sp = sc.sh.ppitch;
+    P.pitch = (IX)sc.pitch;
+    P.sp = (IX)sc.sh.ppitch;
     P.slot = sc.sh.slot;
     P.shift = sc.sh.shift;
     return P;
+}
+
+// 32-bit element offsets when every plane offset fits (D * pitch and the
+// staging ring below 2^32): one multiply-add per address instead of 64-bit math.
+static bool offsets_fit_u32(const SceneView &sc)
+{
+    const uint64_t lim = 1ull << 32;
+    return (uint64_t)sc.D * (uint64_t)sc.pitch < lim && (uint64_t)(sc.D - N_GEO) * (uint64_t)sc.sh.ppitch < lim;
 }
 
 void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, uint32_t *umask,
@@ -332,12 +342,24 @@ void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t 
 {
     const int groups = (sc.D + RG - 1) / RG;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
-    if (sc.prec == GS_FP32)
-        k_adam_apply<float><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, uids, udelay, u_range, n_upd, vmask,
-                                                        vprefix, grad, gcap, args);
-    else
-        k_adam_apply<__nv_bfloat16><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, uids, udelay,
-                                                                u_range, n_upd, vmask, vprefix, grad, gcap, args);
+    const bool u32 = offsets_fit_u32(sc);
+    if (sc.prec == GS_FP32) {
+        if (u32)
+            k_adam_apply<float, uint32_t><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float, uint32_t>(sc), sc.D, uids, udelay,
+                                                                      u_range, n_upd, vmask, vprefix, grad, gcap, args);
+        else
+            k_adam_apply<float, int64_t><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float, int64_t>(sc), sc.D, uids, udelay,
+                                                                     u_range, n_upd, vmask, vprefix, grad, gcap, args);
+    } else {
+        if (u32)
+            k_adam_apply<__nv_bfloat16, uint32_t><<<grid, ADAM_BLOCK, 0, s>>>(
+                planes_of<__nv_bfloat16, uint32_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap,
+                args);
+        else
+            k_adam_apply<__nv_bfloat16, int64_t><<<grid, ADAM_BLOCK, 0, s>>>(
+                planes_of<__nv_bfloat16, int64_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap,
+                args);
+    }
 }
 
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,

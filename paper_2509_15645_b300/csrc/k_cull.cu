@@ -98,6 +98,7 @@ constexpr int CT = 256, CSTAGES = 3, CPLANES = 10;
 struct CullStage {
     float geo[CPLANES][CT];
     float dir[CPLANES][CT];
+    uint8_t cnt[CT];      // counters of a full tile (the last, partial tile reads them directly)
 };
 constexpr size_t CULL_SMEM = sizeof(CullStage) * CSTAGES;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
@@ -141,10 +142,13 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         const int64_t i0 = t * CT;
         const int64_t rows = min((int64_t)CT, n - i0);
         const uint32_t bytes = (uint32_t)(((rows + 3) & ~3ll) * 4);   // within the plane: pitch >= n, a multiple of 4
-        mbar_expect_tx(&bar[s], bytes * CPLANES * (restore ? 2u : 1u));
+        const bool cnt_bulk = restore && rows == CT;
+        mbar_expect_tx(&bar[s], bytes * CPLANES * (restore ? 2u : 1u) + (cnt_bulk ? (uint32_t)CT : 0u));
         for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].geo[r], geo + r * pitch + i0, bytes, &bar[s]);
-        if (restore)
+        if (restore) {
             for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].dir[r], rdir + r * pitch + i0, bytes, &bar[s]);
+            if (cnt_bulk) bulk_g2s(st[s].cnt, counter + i0, CT, &bar[s]);
+        }
     };
     if (tid == 0)
         for (int q = 0; q < CSTAGES - 1; q++) issue(q);
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
 #pragma unroll
                 for (int r = 0; r < CPLANES; r++) g[r] = st[s].geo[r][tid];
                 if (restore) {
-                    const int d = counter[i];
+                    const int d = (t * CT + CT <= n) ? st[s].cnt[tid] : counter[i];
 #pragma unroll
                     for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
                 }
@@ -214,7 +218,8 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
     if (view == 0) w.mark(TP_CULL0, s);
     const int g = w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8);
     const bool restore_dir_path = sc.rdir != nullptr || !(sc.m && sc.v && sc.counter);
-    const bool aligned = ((uintptr_t)sc.geo & 15) == 0 && ((uintptr_t)sc.rdir & 15) == 0;   // bulk-copy rule
+    const bool aligned = ((uintptr_t)sc.geo & 15) == 0 && ((uintptr_t)sc.rdir & 15) == 0 &&
+                         ((uintptr_t)sc.counter & 15) == 0;   // bulk-copy rule
     if (restore_dir_path && aligned) {
         // geometry (and restore directions) staged by the TMA engine
         static bool attr_set = false;
