@@ -144,16 +144,45 @@ struct RenderBufs {
     int tiles;
 };
 
+// The rasterizer's work over one or several views: (view, tile) items
+// [tile_ofs[v], tile_ofs[v + 1]) belong to view v; persistent blocks take items
+// from a work counter (zeroed before each launch) until all are done.
+struct RasterJob {
+    int n_views;
+    int tile_ofs[MAX_VIEWS + 1];
+    const uint2 *ranges[MAX_VIEWS];
+    const uint32_t *svals[MAX_VIEWS];
+    const float4 *rec0[MAX_VIEWS], *rec1[MAX_VIEWS], *rec2[MAX_VIEWS];
+    float *image[MAX_VIEWS];     // forward: image out
+    float *cfinal[MAX_VIEWS];    // forward: final colour kept for the backward (or null); backward: read
+    float *dimage[MAX_VIEWS];    // forward: dL/dimage out (with targets); backward: read
+    float *g9[MAX_VIEWS];        // backward: per-splat sums out
+    int *work;
+};
+
 constexpr int N_RASTER_VARIANTS = 6;
 bool raster_variant_ok(int v, int tile_w, int tile_h);
 
 void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
                     RenderBufs &rb, const DevCam &cam_host, float *image, bool use_target, float *dimage,
-                    float *loss, Work &w, cudaStream_t s);
+                    float *loss, Work &w, cudaStream_t s, int *work);
+// The stages of render_forward / render_backward, for steps over several views:
+// per view prepare_view (gather, projection, keys, sorts); one forward and one
+// backward rasterizer launch over all views; per view project_backward.
+void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
+                  RenderBufs &rb, const DevCam &cam_host, Work &w, cudaStream_t s);
+void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
+                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s);
+void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
+                     const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
+                     unsigned long long *stats = nullptr);
+void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
+                      float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
+                      const int32_t *ids, bool accumulate, Work &w, cudaStream_t s);
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                      const DevCam &cam_host, const float *dimage, float *grad, int64_t gcap,
                      const uint32_t *remap_mask, const uint32_t *remap_prefix, const int32_t *ids, bool accumulate,
-                     Work &w, cudaStream_t s, unsigned long long *stats = nullptr);
+                     Work &w, cudaStream_t s, int *work, unsigned long long *stats = nullptr);
 void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
                     cudaStream_t s);
 void launch_zero_rows(float *buf, int rows, int64_t pitch, const int *n_dev, int cap, Work &w, cudaStream_t s,

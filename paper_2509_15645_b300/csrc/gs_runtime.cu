@@ -61,9 +61,10 @@ struct gs_ctx {
     uint32_t *vprefix[MAX_VIEWS] = {nullptr};
     int32_t *vids[MAX_VIEWS] = {nullptr};
     uint32_t *union_mask = nullptr, *union_prefix = nullptr, *union_chunk = nullptr;
-    float *img = nullptr, *dimg = nullptr, *grad_u = nullptr;
+    float *imgs[MAX_VIEWS] = {nullptr}, *dimgs[MAX_VIEWS] = {nullptr}, *grad_u = nullptr;
+    int *work = nullptr;                // rasterizer work counters
     int64_t gcap_u = 0;
-    RenderBufs rb{};
+    RenderBufs rbs[MAX_VIEWS]{};
     Work w{};
     // state kept from the last gs_render_fwd for gs_render_bwd
     bool have_fwd = false;
@@ -185,39 +186,44 @@ static void carve(gs_ctx *c, char *base)
         c->union_prefix = k.take<uint32_t>(NW);
         c->union_chunk = k.take<uint32_t>(NC);
     }
-    RenderBufs &rb = c->rb;
-    rb.cap = V;
-    rb.kcap = K;
-    rb.compact = k.take<float>((size_t)D * V);
-    rb.rec0 = k.take<float4>(V);
-    rb.rec1 = k.take<float4>(V);
-    rb.rec2 = k.take<float4>(V);
-    rb.tcnt = k.take<uint32_t>(V);
-    rb.rect = k.take<uint2>(V);
-    for (int j = 0; j < 2; j++) {
-        rb.dk[j] = k.take<uint32_t>(V);
-        rb.dv[j] = k.take<uint32_t>(V);
+    // render buffers of each view a step may hold at once
+    for (int v = 0; v < g.max_views; v++) {
+        RenderBufs &rb = c->rbs[v];
+        rb.cap = V;
+        rb.kcap = K;
+        rb.compact = k.take<float>((size_t)D * V);
+        rb.rec0 = k.take<float4>(V);
+        rb.rec1 = k.take<float4>(V);
+        rb.rec2 = k.take<float4>(V);
+        rb.tcnt = k.take<uint32_t>(V);
+        rb.rect = k.take<uint2>(V);
+        for (int j = 0; j < 2; j++) {
+            rb.dk[j] = k.take<uint32_t>(V);
+            rb.dv[j] = k.take<uint32_t>(V);
+        }
+        rb.rank_cnt = k.take<uint32_t>(V + 1);
+        for (int j = 0; j < 2; j++) {
+            rb.tk[j] = k.take<uint32_t>(K);
+            rb.tv[j] = k.take<uint32_t>(K);
+        }
+        rb.ranges = k.take<uint2>(tiles);
+        rb.g9 = k.take<float>(G9_STRIDE * V);
+        int *ctr = k.take<int>(2);
+        rb.n_keys = v == 0 ? (base ? &c->cnt->n_keys : nullptr) : ctr;
+        rb.n_fix = v == 0 ? (base ? &c->cnt->n_fix : nullptr) : ctr + 1;
+        rb.cfinal = k.take<float>(P);
+        rb.fix_idx = k.take<int32_t>(V);
+        rb.fix_flag = k.take<uint8_t>(V);
+        rb.n_big = k.take<int>(2);
+        rb.big_idx = k.take<int32_t>(V);
+        rb.big_rank = k.take<int32_t>(V);
+        c->imgs[v] = k.take<float>(P);
+        c->dimgs[v] = k.take<float>(P);
     }
-    rb.rank_cnt = k.take<uint32_t>(V + 1);
-    for (int j = 0; j < 2; j++) {
-        rb.tk[j] = k.take<uint32_t>(K);
-        rb.tv[j] = k.take<uint32_t>(K);
-    }
-    rb.ranges = k.take<uint2>(tiles);
-    rb.g9 = k.take<float>(G9_STRIDE * V);
-    rb.n_keys = base ? &c->cnt->n_keys : nullptr;
-    rb.n_fix = base ? &c->cnt->n_fix : nullptr;
-    rb.cfinal = k.take<float>(P);
-    rb.fix_idx = k.take<int32_t>(V);
-    rb.fix_flag = k.take<uint8_t>(V);
-    rb.n_big = k.take<int>(2);
-    rb.big_idx = k.take<int32_t>(V);
-    rb.big_rank = k.take<int32_t>(V);
+    c->work = k.take<int>(4);
     int64_t big = K > V ? K : V;
     c->w.hist = k.take<uint32_t>(256 * ((big + RADIX_TILE - 1) / RADIX_TILE) + 256);
     c->w.partials = k.take<uint32_t>(1024);
-    c->img = k.take<float>(P);
-    c->dimg = k.take<float>(P);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
     if (g.stage_chunks > 0) {
@@ -417,9 +423,9 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
     carve(c, (char *)c->ws);
     c->w.status = &c->cnt->status;
     c->w.num_sms = c->num_sms;
-    c->rb.variant = 1;
-    if (!raster_variant_ok(c->rb.variant, cfg->tile_w, cfg->tile_h)) c->rb.variant = 0;
-    c->rb.variant_bwd = c->rb.variant;
+    c->rbs[0].variant = 1;
+    if (!raster_variant_ok(c->rbs[0].variant, cfg->tile_w, cfg->tile_h)) c->rbs[0].variant = 0;
+    c->rbs[0].variant_bwd = c->rbs[0].variant;
     c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
     if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         gs_destroy(c);
@@ -518,8 +524,8 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, 
     a.n_views = 1;
     set_args(c, SLOT_RENDER, a, s);
     cudaMemcpyAsync(c->n_render, n_vis, sizeof(int), cudaMemcpyDeviceToDevice, s);
-    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], image_out, false, nullptr,
-                   nullptr, c->w, s);
+    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], image_out, false, nullptr,
+                   nullptr, c->w, s, c->work);
     c->have_fwd = true;
     c->fwd_sc = sv;
     c->fwd_cam = a.cam[0];
@@ -532,8 +538,8 @@ gs_status gs_render_bwd(gs_ctx *c, const float *dL_dimage, float *grad_compact, 
     if (!c->have_fwd) return fail(c, GS_ERR_INVALID_ARG, "gs_render_bwd without a gs_render_fwd");
     if (!dL_dimage || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
     cudaStream_t s = (cudaStream_t)stream;
-    render_backward(c->fwd_sc, c->args + SLOT_RENDER, 0, c->n_render, c->rb, c->fwd_cam, dL_dimage, grad_compact, cap,
-                    nullptr, nullptr, nullptr, false, c->w, s);
+    render_backward(c->fwd_sc, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], c->fwd_cam, dL_dimage, grad_compact, cap,
+                    nullptr, nullptr, nullptr, false, c->w, s, c->work);
     return cuda_check(c, "gs_render_bwd");
 }
 
@@ -670,7 +676,7 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
 gs_status gs_set_raster_variant(gs_ctx *c, int32_t variant)
 {
     if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h)) return GS_ERR_INVALID_ARG;
-    c->rb.variant = c->rb.variant_bwd = variant;
+    c->rbs[0].variant = c->rbs[0].variant_bwd = variant;
     return GS_OK;
 }
 
@@ -694,23 +700,23 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventCreate(&e2);
-    const int keep = c->rb.variant, keep_b = c->rb.variant_bwd;
+    const int keep = c->rbs[0].variant, keep_b = c->rbs[0].variant_bwd;
     float best_f = 1e30f, best_b = 1e30f;
     int best_vf = keep, best_vb = keep_b;
     gs_status res = GS_OK;
     for (int v = 0; v < N_RASTER_VARIANTS && res == GS_OK; v++) {
         if (ms_out) ms_out[v] = ms_out[N_RASTER_VARIANTS + v] = -1.f;
         if (!raster_variant_ok(v, c->cfg.tile_w, c->cfg.tile_h)) continue;
-        c->rb.variant = c->rb.variant_bwd = v;
+        c->rbs[0].variant = c->rbs[0].variant_bwd = v;
         float fbest = 1e30f, bbest = 1e30f;
         for (int rep = 0; rep < 4; rep++) {
             cudaEventRecord(e0, s);
-            render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], c->img, false, nullptr,
-                           nullptr, c->w, s);
+            render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], false, nullptr,
+                           nullptr, c->w, s, c->work);
             cudaEventRecord(e1, s);
             // the rendered image itself serves as a dense dL/dimage
-            render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rb, a.cam[0], c->img, c->grad_u,
-                            c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s);
+            render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u,
+                            c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s, c->work);
             cudaEventRecord(e2, s);
             if (cudaEventSynchronize(e2) != cudaSuccess) {
                 res = cuda_check(c, "gs_autotune");
@@ -736,12 +742,14 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
     if (res != GS_OK) {
-        c->rb.variant = keep;
-        c->rb.variant_bwd = keep_b;
+        c->rbs[0].variant = keep;
+        c->rbs[0].variant_bwd = keep_b;
         return res;
     }
-    c->rb.variant = best_vf;
-    c->rb.variant_bwd = best_vb;
+    for (int v = 0; v < MAX_VIEWS; v++) {
+        c->rbs[v].variant = best_vf;
+        c->rbs[v].variant_bwd = best_vb;
+    }
     c->have_fwd = false;
     if (chosen_out) {
         chosen_out[0] = best_vf;
@@ -768,10 +776,10 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
     compact_mask(c->mask, sv.n, c->chunk, true, ids, c->wprefix, (int)c->cfg.max_visible, c->n_render, c->w, s);
     unsigned long long *dev = reinterpret_cast<unsigned long long *>(c->n_tmp);   // 16 bytes of scratch
     cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s);
-    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rb, a.cam[0], c->img, false, nullptr, nullptr,
-                   c->w, s);
-    render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rb, a.cam[0], c->img, c->grad_u, c->cfg.max_visible,
-                    nullptr, nullptr, nullptr, false, c->w, s, dev);
+    render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], false, nullptr, nullptr,
+                   c->w, s, c->work);
+    render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u, c->cfg.max_visible,
+                    nullptr, nullptr, nullptr, false, c->w, s, c->work, dev);
     unsigned long long host[2] = {0, 0};
     if (cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -793,10 +801,10 @@ gs_status gs_render_lists(const gs_ctx *c, const uint32_t **tile_of_key, const u
                           const int32_t **n_keys, const uint32_t **ranges)
 {
     if (!c || !c->have_fwd || !tile_of_key || !splat_of_key || !n_keys || !ranges) return GS_ERR_INVALID_ARG;
-    *tile_of_key = c->rb.sorted_keys;
-    *splat_of_key = c->rb.sorted_vals;
-    *n_keys = c->rb.n_keys;
-    *ranges = reinterpret_cast<const uint32_t *>(c->rb.ranges);
+    *tile_of_key = c->rbs[0].sorted_keys;
+    *splat_of_key = c->rbs[0].sorted_vals;
+    *n_keys = c->rbs[0].n_keys;
+    *ranges = reinterpret_cast<const uint32_t *>(c->rbs[0].ranges);
     return GS_OK;
 }
 
@@ -811,8 +819,8 @@ gs_status gs_host_tier_stats(const gs_ctx *c, int64_t *chunks, int64_t *bytes)
 gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **conic, const int32_t **n_vis)
 {
     if (!c || !c->have_fwd || !geom || !conic || !n_vis) return GS_ERR_INVALID_ARG;
-    *geom = reinterpret_cast<const float *>(c->rb.rec0);
-    *conic = reinterpret_cast<const float *>(c->rb.rec1);
+    *geom = reinterpret_cast<const float *>(c->rbs[0].rec0);
+    *conic = reinterpret_cast<const float *>(c->rbs[0].rec1);
     *n_vis = c->n_render;
     return GS_OK;
 }
@@ -852,20 +860,30 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
 }
 
 // Render, L1 loss and backward of every view; gradients summed per Gaussian.
+// Each view's lists are prepared on its own buffers; one forward and one
+// backward rasterizer launch then cover the tiles of all views.
 static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, const StepMasks &M,
                                  float *loss, cudaStream_t s)
 {
     DevArgs *args = c->args + SLOT_STEP;
+    RenderBufs *rbs[MAX_VIEWS];
+    const int *nv[MAX_VIEWS];
+    const float *dimg_c[MAX_VIEWS];
     for (int v = 0; v < n_views; v++) {
-        if (v == 0) c->w.mark(TP_FWD0, s);
-        render_forward(sv, args, v, c->vids[v], c->nvis_view + v, c->rb, a.cam[v], c->img, true, c->dimg, loss, c->w, s);
-        if (v == 0) c->w.mark(TP_FWD1, s);
-        if (v == 0) c->w.mark(TP_BWD0, s);
-        render_backward(sv, args, v, c->nvis_view + v, c->rb, a.cam[v], c->dimg, c->grad_u, M.gcap,
-                        n_views > 1 ? M.gmask : nullptr, n_views > 1 ? M.gprefix : nullptr, c->vids[v], n_views > 1,
-                        c->w, s);
-        if (v == 0) c->w.mark(TP_BWD1, s);
+        rbs[v] = &c->rbs[v];
+        nv[v] = c->nvis_view + v;
+        dimg_c[v] = c->dimgs[v];
     }
+    c->w.mark(TP_FWD0, s);
+    for (int v = 0; v < n_views; v++) prepare_view(sv, args, v, c->vids[v], c->nvis_view + v, c->rbs[v], a.cam[v], c->w, s);
+    raster_forward(args, n_views, rbs, a.cam, c->imgs, true, c->dimgs, loss, c->work, c->w, s);
+    c->w.mark(TP_FWD1, s);
+    c->w.mark(TP_BWD0, s);
+    raster_backward(args, n_views, rbs, a.cam, dimg_c, nv, c->work + 1, c->w, s);
+    for (int v = 0; v < n_views; v++)
+        project_backward(sv, args, v, c->nvis_view + v, c->rbs[v], c->grad_u, M.gcap, n_views > 1 ? M.gmask : nullptr,
+                         n_views > 1 ? M.gprefix : nullptr, c->vids[v], n_views > 1, c->w, s);
+    c->w.mark(TP_BWD1, s);
 }
 
 static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const StepMasks &M, cudaStream_t s)
@@ -1070,7 +1088,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         if (!st) scene->step += 1;
         return st;
     }
-    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rb.variant * 16 + c->rb.variant_bwd)) {
+    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rbs[0].variant * 16 + c->rbs[0].variant_bwd)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1142,7 +1160,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         g.prec = scene->precision;
         g.loss = loss_out;
         g.timed = timed;
-        g.variant = c->rb.variant * 16 + c->rb.variant_bwd;
+        g.variant = c->rbs[0].variant * 16 + c->rbs[0].variant_bwd;
         for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
     }
     if (timed) {

@@ -18,6 +18,8 @@
 //                     atomics into the per-splat screen-space gradients
 //   k_project_bwd     chain rule to mean, log-scale, quaternion, opacity logit
 //                     and SH coefficients
+#include <algorithm>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -410,20 +412,36 @@ __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, c
     return cnt;
 }
 
+// Next (view, tile) item of a persistent rasterizer block, or false when done.
+__device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &view, int &tile)
+{
+    __syncthreads();                                   // the previous item's shared data is no longer read
+    if (threadIdx.x == 0) *s_item = atomicAdd(J.work, 1);
+    __syncthreads();
+    const int item = *s_item;
+    if (item >= J.tile_ofs[J.n_views]) return false;
+    view = 0;
+    while (item >= J.tile_ofs[view + 1]) view++;
+    tile = item - J.tile_ofs[view];
+    return true;
+}
+
 template <int PPT, int BATCH>
-__global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
-                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                    const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                    int view, float *__restrict__ image, float *__restrict__ cfinal,
-                                                    int use_target, float *__restrict__ dimage,
-                                                    float *__restrict__ loss)
+__global__ void __launch_bounds__(256) k_raster_fwd(const RasterJob J, const DevArgs *__restrict__ args,
+                                                    int use_target, float *__restrict__ loss)
 {
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ float s_red[8];
+    __shared__ int s_item;
+    int view, tile;
+    while (next_item(J, &s_item, view, tile)) {
+    const uint2 *__restrict__ ranges = J.ranges[view];
+    const uint32_t *__restrict__ svals = J.svals[view];
+    const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
+    float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
     const DevCam &cam = args->cam[view];
     const float *target = use_target ? args->target[view] : nullptr;
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
-    const int tile = blockIdx.x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
     const int x = tx0 + (int)threadIdx.x % tw;
     const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
@@ -503,6 +521,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const uint2 *__restrict__ ra
         float t = block_sum(part, s_red);
         if (threadIdx.x == 0) atomicAdd(loss, t);
     }
+    }
 }
 
 // Sum of v[0..7] over the 32 lanes, transposed: after 4 + 2 + 1 exchanges each
@@ -543,19 +562,22 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
 // STATS: also count the (pixel, splat) pairs that pass the square test and the
 // pairs that contribute (stats[0], stats[1]).
 template <int PPT, int BATCH, bool STATS = false>
-__global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ svals,
-                                                    const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                                                    const float4 *__restrict__ rec2, const DevArgs *__restrict__ args,
-                                                    int view, const float *__restrict__ cfinal,
-                                                    const float *__restrict__ dimage, float *__restrict__ g9,
-                                                    int64_t gcap, unsigned long long *stats = nullptr)
+__global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const DevArgs *__restrict__ args,
+                                                    unsigned long long *stats = nullptr)
 {
     unsigned long long n_sq = 0, n_on = 0;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ uint32_t s_k[BATCH];
+    __shared__ int s_item;
+    int view, tile;
+    while (next_item(J, &s_item, view, tile)) {
+    const uint2 *__restrict__ ranges = J.ranges[view];
+    const uint32_t *__restrict__ svals = J.svals[view];
+    const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
+    const float *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
+    float *__restrict__ g9 = J.g9[view];
     const DevCam &cam = args->cam[view];
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
-    const int tile = blockIdx.x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
     const int x = tx0 + (int)threadIdx.x % tw;
     const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
@@ -652,7 +674,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
             }
         }
     }
+    }
     if (STATS) {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             n_sq += __shfl_xor_sync(0xffffffffu, n_sq, o);
@@ -665,11 +689,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const uint2 *__restrict__ ra
     }
 }
 
-typedef void (*RasterFwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
-                            const DevArgs *, int, float *, float *, int, float *, float *);
-typedef void (*RasterBwdFn)(const uint2 *, const uint32_t *, const float4 *, const float4 *, const float4 *,
-                            const DevArgs *, int, const float *, const float *, float *, int64_t,
-                            unsigned long long *);
+typedef void (*RasterFwdFn)(const RasterJob, const DevArgs *, int, float *);
+typedef void (*RasterBwdFn)(const RasterJob, const DevArgs *, unsigned long long *);
 
 // Variant v: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128.
 static RasterFwdFn fwd_variant(int v)
@@ -684,15 +705,21 @@ static RasterFwdFn fwd_variant(int v)
     }
 }
 
-static RasterBwdFn bwd_variant(int v)
+static RasterBwdFn bwd_variant(int v, bool stats)
 {
-    switch (v) {
-    case 0: return k_raster_bwd<1, 128>;
-    case 1: return k_raster_bwd<1, 256>;
-    case 2: return k_raster_bwd<2, 128>;
-    case 3: return k_raster_bwd<2, 256>;
-    case 4: return k_raster_bwd<4, 128>;
-    default: return k_raster_bwd<4, 256>;
+    switch (v * 2 + (stats ? 1 : 0)) {
+    case 0: return k_raster_bwd<1, 128, false>;
+    case 1: return k_raster_bwd<1, 128, true>;
+    case 2: return k_raster_bwd<1, 256, false>;
+    case 3: return k_raster_bwd<1, 256, true>;
+    case 4: return k_raster_bwd<2, 128, false>;
+    case 5: return k_raster_bwd<2, 128, true>;
+    case 6: return k_raster_bwd<2, 256, false>;
+    case 7: return k_raster_bwd<2, 256, true>;
+    case 8: return k_raster_bwd<4, 128, false>;
+    case 9: return k_raster_bwd<4, 128, true>;
+    case 10: return k_raster_bwd<4, 256, false>;
+    default: return k_raster_bwd<4, 256, true>;
     }
 }
 
@@ -965,9 +992,8 @@ static int bits_for(int n)
     return b;
 }
 
-void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
-                    RenderBufs &rb, const DevCam &cam, float *image, bool use_target, float *dimage, float *loss,
-                    Work &w, cudaStream_t s)
+void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
+                  RenderBufs &rb, const DevCam &cam, Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
     auto gp = sc.prec == GS_FP32
@@ -1001,47 +1027,122 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
     rb.sorted_keys = rb.tk[tcur];
     rb.sorted_vals = rb.tv[tcur];
     rb.tiles = tiles;
-    const int ppt = 1 << (rb.variant >> 1);
-    fwd_variant(rb.variant)<<<tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-        rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, image, image == rb.cfinal ? nullptr : rb.cfinal,
-        use_target ? 1 : 0, dimage, loss);
 }
 
-static void raster_bwd_stats(int v, int tiles, int threads, const RenderBufs &rb, const DevArgs *args, int view,
-                             const float *dimage, unsigned long long *stats, cudaStream_t s)
+static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
 {
-    const int64_t cap = rb.cap;
-    switch (v) {
-    case 0: k_raster_bwd<1, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
-    case 1: k_raster_bwd<1, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
-    case 2: k_raster_bwd<2, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
-    case 3: k_raster_bwd<2, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
-    case 4: k_raster_bwd<4, 128, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
-    default: k_raster_bwd<4, 256, true><<<tiles, threads, 0, s>>>(rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, stats); break;
+    RasterJob J{};
+    J.n_views = n_views;
+    J.tile_ofs[0] = 0;
+    for (int v = 0; v < n_views; v++) {
+        const RenderBufs &rb = *rbs[v];
+        J.tile_ofs[v + 1] = J.tile_ofs[v] + rb.tiles;
+        J.ranges[v] = rb.ranges;
+        J.svals[v] = rb.sorted_vals;
+        J.rec0[v] = rb.rec0;
+        J.rec1[v] = rb.rec1;
+        J.rec2[v] = rb.rec2;
+        J.cfinal[v] = rb.cfinal;
+        J.g9[v] = rb.g9;
     }
+    J.work = work;
+    return J;
 }
 
-void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
-                     const DevCam &cam, const float *dimage, float *grad, int64_t gcap, const uint32_t *remap_mask,
-                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s,
+// Persistent blocks: enough to fill the GPU, never more than the items.
+static int persistent_grid(int items, const Work &w) { return std::max(1, std::min(items, w.num_sms * 32)); }
+
+void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
+                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s)
+{
+    RasterJob J = make_job(n_views, rbs, work);
+    for (int v = 0; v < n_views; v++) {
+        J.image[v] = images[v];
+        if (images[v] == rbs[v]->cfinal) J.cfinal[v] = nullptr;
+        J.dimage[v] = use_target ? dimages[v] : nullptr;
+    }
+    const RenderBufs &rb0 = *rbs[0];
+    const int ppt = 1 << (rb0.variant >> 1);
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    fwd_variant(rb0.variant)<<<persistent_grid(J.tile_ofs[n_views], w), cams[0].tile_w * cams[0].tile_h / ppt, 0, s>>>(
+        J, args, use_target ? 1 : 0, loss);
+}
+
+// A job over one view of the argument block: slots 0..view, only `view` with items.
+static RasterJob single_view_job(int view, RenderBufs &rb, int *work)
+{
+    RenderBufs *rbs[MAX_VIEWS] = {nullptr};
+    for (int v = 0; v <= view; v++) rbs[v] = &rb;
+    RasterJob J = make_job(view + 1, rbs, work);
+    for (int v = 0; v <= view; v++) J.tile_ofs[v + 1] = v < view ? 0 : rb.tiles;
+    return J;
+}
+
+void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
+                    RenderBufs &rb, const DevCam &cam, float *image, bool use_target, float *dimage, float *loss,
+                    Work &w, cudaStream_t s, int *work)
+{
+    prepare_view(sc, args, view, ids, n_vis, rb, cam, w, s);
+    RasterJob J = single_view_job(view, rb, work);
+    for (int v = 0; v <= view; v++) {
+        J.image[v] = image;
+        J.cfinal[v] = image == rb.cfinal ? nullptr : rb.cfinal;
+        J.dimage[v] = use_target ? dimage : nullptr;
+    }
+    const int ppt = 1 << (rb.variant >> 1);
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    fwd_variant(rb.variant)<<<persistent_grid(rb.tiles, w), cam.tile_w * cam.tile_h / ppt, 0, s>>>(
+        J, args, use_target ? 1 : 0, loss);
+}
+
+void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
+                     const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
                      unsigned long long *stats)
 {
+    for (int v = 0; v < n_views; v++) {
+        const int cap = (int)rbs[v]->cap;
+        launch_zero_rows(rbs[v]->g9, G9_STRIDE, cap, n_vis[v], cap, w, s, true);
+    }
+    RasterJob J = make_job(n_views, rbs, work);
+    for (int v = 0; v < n_views; v++) J.dimage[v] = const_cast<float *>(dimages[v]);
+    const RenderBufs &rb0 = *rbs[0];
+    const int ppt = 1 << (rb0.variant_bwd >> 1);
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    w.mark(TP_RBWD0, s);
+    bwd_variant(rb0.variant_bwd, stats != nullptr)<<<persistent_grid(J.tile_ofs[n_views], w),
+                                                     cams[0].tile_w * cams[0].tile_h / ppt, 0, s>>>(J, args, stats);
+    w.mark(TP_RBWD1, s);
+}
+
+void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
+                      float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
+                      const int32_t *ids, bool accumulate, Work &w, cudaStream_t s)
+{
     const int cap = (int)rb.cap;
-    launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
-    const int ppt = 1 << (rb.variant_bwd >> 1);
-    if (view == 0) w.mark(TP_RBWD0, s);
-    if (stats)
-        raster_bwd_stats(rb.variant_bwd, rb.tiles, cam.tile_w * cam.tile_h / ppt, rb, args, view, dimage, stats, s);
-    else
-        bwd_variant(rb.variant_bwd)<<<rb.tiles, cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-            rb.ranges, rb.sorted_vals, rb.rec0, rb.rec1, rb.rec2, args, view, rb.cfinal, dimage, rb.g9, cap, nullptr);
-    if (view == 0) w.mark(TP_RBWD1, s);
     k_project_bwd<false><<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
         rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix,
         accumulate ? 1 : 0, w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
     k_project_bwd<true><<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap,
                                                           ids, remap_mask, remap_prefix, accumulate ? 1 : 0, w.status,
                                                           rb.n_fix, rb.fix_idx, rb.fix_flag);
+}
+
+void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
+                     const DevCam &cam, const float *dimage, float *grad, int64_t gcap, const uint32_t *remap_mask,
+                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s,
+                     int *work, unsigned long long *stats)
+{
+    const int cap = (int)rb.cap;
+    launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
+    RasterJob J = single_view_job(view, rb, work);
+    for (int v = 0; v <= view; v++) J.dimage[v] = const_cast<float *>(dimage);
+    const int ppt = 1 << (rb.variant_bwd >> 1);
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    if (view == 0) w.mark(TP_RBWD0, s);
+    bwd_variant(rb.variant_bwd, stats != nullptr)<<<persistent_grid(rb.tiles, w), cam.tile_w * cam.tile_h / ppt, 0,
+                                                    s>>>(J, args, stats);
+    if (view == 0) w.mark(TP_RBWD1, s);
+    project_backward(sc, args, view, n_vis, rb, grad, gcap, remap_mask, remap_prefix, ids, accumulate, w, s);
 }
 
 }  // namespace gs

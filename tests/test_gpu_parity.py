@@ -640,6 +640,44 @@ def test_step_timing_spans(gs):
     assert scene.step == 7
 
 
+def test_step_two_views_parity(gs, orc):
+    """gs_step over two views (one fused rasterizer launch per direction): the
+    loss is the sum of the views' L1 losses, the gradient of a Gaussian the sum
+    of its views' gradients, and one optimizer step covers the union of the
+    visible sets (§2.4 steps 1-6 with several views per iteration)."""
+    P = scenes.uniform_cube_scene(6000, seed=41, sh_degree=1, log_scale_mean=-3.0)
+    deg, tile = 1, (16, 16)
+    n, D = P.shape[1], P.shape[0]
+    cams = [cam_f32(scenes.camera_lookat((0.6, -0.2, -2.8), (0.3, 0.0, 0.0), 80, 60, 55.0, up=(0, -1, 0))),
+            cam_f32(scenes.camera_lookat((-0.7, 0.3, -2.6), (-0.4, 0.1, 0.0), 72, 56, 60.0, up=(0, -1, 0)))]
+    T = f32(scenes.uniform_cube_scene(n, seed=42, sh_degree=deg, log_scale_mean=-3.0))
+    targets = [orc.render(T, deg, c, tile)["image"] for c in cams]
+    scene = gs.GaussianScene(P, deg)
+    ctx = make_ctx(gs, n, 80, 60, deg=deg, tile=tile, views=2)
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    hp = hp32(orc, lr=1e-3, eps=1e-15)
+    loss = ctx.step(scene, cams, [torch.as_tensor(t, dtype=torch.float32, device="cuda") for t in targets], adam)
+    ctx.sync_status()
+    W, M, V, Cn = f32(P), np.zeros((D, n)), np.zeros((D, n)), np.zeros(n, np.uint8)
+    g = np.zeros((D, n))
+    vis = np.zeros(n, bool)
+    ref_loss = 0.0
+    for c, t in zip(cams, targets):
+        rr = orc.render_loss_backward(W, deg, c, t, tile)
+        kept = rr["splats"]["keep"] == 1
+        g[:, kept] += rr["grad"][:, kept]
+        vis |= kept
+        ref_loss += rr["loss"]
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    ids = np.nonzero(vis)[0].astype(np.int32)
+    orc.adam_deferred(W, M, V, Cn, ids, g[:, ids], 1, hp)
+    np.testing.assert_array_equal(scene.counter[:n].cpu().numpy(), Cn)
+    gm = scene.m[:, :n].cpu().numpy().astype(np.float64)
+    for k, sl in GROUPS.items():
+        if M[sl].size:
+            assert rel_group_error(gm, M, sl) <= 2e-4, (k, rel_group_error(gm, M, sl))
+
+
 # ---------------------------------------------------------------------------- autograd
 
 def test_autograd_function(gs, orc):
