@@ -86,6 +86,9 @@ enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_
 // k_cull.cu: visibility bitmask + per-chunk counts (restore if lut.restore).
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
                  cudaStream_t s);
+// All views of a step in one sweep over the geometry (per-view masks and chunk counts).
+void launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
+                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s);
 void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t *mask, int64_t n, Work &w,
                         cudaStream_t s);
 void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s);

@@ -58,6 +58,7 @@ struct gs_ctx {
     uint8_t *udelay = nullptr;
     uint32_t *amask = nullptr, *aprefix = nullptr, *achunk = nullptr;
     uint32_t *vmask[MAX_VIEWS] = {nullptr};
+    uint32_t *vchunk[MAX_VIEWS] = {nullptr};
     uint32_t *vprefix[MAX_VIEWS] = {nullptr};
     int32_t *vids[MAX_VIEWS] = {nullptr};
     uint32_t *union_mask = nullptr, *union_prefix = nullptr, *union_chunk = nullptr;
@@ -178,6 +179,7 @@ static void carve(gs_ctx *c, char *base)
     c->achunk = k.take<uint32_t>(NC);
     for (int v = 0; v < g.max_views; v++) {
         c->vmask[v] = k.take<uint32_t>(NW);
+        c->vchunk[v] = k.take<uint32_t>(NC);
         c->vprefix[v] = k.take<uint32_t>(NW);
         c->vids[v] = k.take<int32_t>(V);
     }
@@ -841,10 +843,9 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
     c->w.mark(TP_STEP0, s);
     set_args(c, SLOT_STEP, a, s);
     cudaMemsetAsync(loss, 0, sizeof(float), s);
-    for (int v = 0; v < n_views; v++) {
-        launch_cull(sv, args, v, c->vmask[v], c->chunk, c->w, s);
-        compact_mask(c->vmask[v], sv.n, c->chunk, true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
-    }
+    launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s);
+    for (int v = 0; v < n_views; v++)
+        compact_mask(c->vmask[v], sv.n, c->vchunk[v], true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
     cudaMemcpyAsync(&c->cnt->n_vis, c->nvis_view, sizeof(int), cudaMemcpyDeviceToDevice, s);
     StepMasks M{c->vmask[0], c->vprefix[0], V};
     if (n_views > 1) {

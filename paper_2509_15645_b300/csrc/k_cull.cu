@@ -103,21 +103,31 @@ struct CullStage {
 constexpr size_t CULL_SMEM = sizeof(CullStage) * CSTAGES;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
+// Views [view0, view0 + nv) of the argument block in one sweep: the planes
+// are read and restored once and projected into every view.
+struct CullOut {
+    uint32_t *mask[MAX_VIEWS];
+    uint32_t *chunk[MAX_VIEWS];
+};
+
 __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
                                                    const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
-                                                   const DevArgs *__restrict__ args, int view,
-                                                   uint32_t *__restrict__ mask, uint32_t *__restrict__ chunk_cnt,
-                                                   int *status)
+                                                   const DevArgs *__restrict__ args, int view0, int nv,
+                                                   const CullOut out, int *status)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     CullStage *st = reinterpret_cast<CullStage *>(smem);
     __shared__ __align__(8) uint64_t bar[CSTAGES];
-    __shared__ DevCam s_cam;
+    __shared__ DevCam s_cam[MAX_VIEWS];
     __shared__ float s_plut[3][LUT_N];
-    __shared__ uint32_t s_cnt[CT / 32];
+    __shared__ uint32_t s_cnt[MAX_VIEWS][CT / 32];
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid < sizeof(DevCam) / 4) ((uint32_t *)&s_cam)[tid] = ((const uint32_t *)&args->cam[view])[tid];
+    for (int e = tid; e < nv * (int)(sizeof(DevCam) / 4); e += CT) {
+        const int v = e / (int)(sizeof(DevCam) / 4), o = e % (int)(sizeof(DevCam) / 4);
+        ((uint32_t *)&s_cam[v])[o] = ((const uint32_t *)&args->cam[view0 + v])[o];
+    }
+    if (tid < MAX_VIEWS * (CT / 32)) s_cnt[tid / (CT / 32)][tid % (CT / 32)] = 0;
     if (tid < 3 * LUT_N) s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
     const bool restore = args->lut.restore && rdir != nullptr && counter != nullptr;
     if (tid == 0) {
@@ -154,7 +164,6 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         for (int q = 0; q < CSTAGES - 1; q++) issue(q);
     int64_t issued_to = CSTAGES - 1;               // tiles [0, issued_to) issued (thread 0's view)
     int64_t q_stop = 0;                            // first tile not consumed when the loop ends
-    uint32_t cnt = 0;
     for (int64_t q = 0;; q++) {
         q_stop = q;
         const int64_t c = blockIdx.x + (q / PER_CHUNK) * gridDim.x;
@@ -164,42 +173,46 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
             issued_to = q + CSTAGES;
         }
         const int64_t t = tile_of(q);
-        int keep = 0;
         if (t >= 0) {
             const int s = (int)(q % CSTAGES);
             if (!mbar_wait_bounded(&bar[s], (uint32_t)((q / CSTAGES) & 1), WAIT_LIMIT)) s_abort = 1;
             const int64_t i = t * CT + tid;
-            if (i < n && !s_abort) {
-                float g[CPLANES];
+            const bool live = i < n && !s_abort;
+            float g[CPLANES];
 #pragma unroll
-                for (int r = 0; r < CPLANES; r++) g[r] = st[s].geo[r][tid];
-                if (restore) {
-                    const int d = (t * CT + CT <= n) ? st[s].cnt[tid] : counter[i];
+            for (int r = 0; r < CPLANES; r++) g[r] = live ? st[s].geo[r][tid] : 0.f;
+            if (restore && live) {
+                const int d = (t * CT + CT <= n) ? st[s].cnt[tid] : counter[i];
 #pragma unroll
-                    for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
-                }
-                Proj P;
-                project_gaussian(g, s_cam, P);
-                keep = P.keep;
+                for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
             }
-            const uint32_t word = __ballot_sync(0xffffffffu, keep);
             const int64_t wbase = t * CT + wid * 32;
-            if (lane == 0 && wbase < n) {
-                mask[wbase >> 5] = word;
-                cnt += __popc(word);
+            for (int v = 0; v < nv; v++) {
+                int keep = 0;
+                if (live) {
+                    Proj P;
+                    project_gaussian(g, s_cam[v], P);
+                    keep = P.keep;
+                }
+                const uint32_t word = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0 && wbase < n) {
+                    out.mask[v][wbase >> 5] = word;
+                    s_cnt[v][wid] += __popc(word);
+                }
             }
         }
         __syncthreads();                           // buffer q % CSTAGES is free again
         if (s_abort) break;                        // q_stop = q: its copy may still be landing
-        if (q % PER_CHUNK == PER_CHUNK - 1) {
-            if (lane == 0) s_cnt[wid] = cnt;
-            cnt = 0;
-            __syncthreads();
-            if (tid == 0) {
+        if (q % PER_CHUNK == PER_CHUNK - 1) {      // the chunk's counts (s_cnt settled by the barrier above)
+            if (tid < nv) {
                 uint32_t tot = 0;
-                for (int k = 0; k < CT / 32; k++) tot += s_cnt[k];
-                chunk_cnt[c] = tot;
+                for (int k = 0; k < CT / 32; k++) {
+                    tot += s_cnt[tid][k];
+                    s_cnt[tid][k] = 0;
+                }
+                out.chunk[tid][c] = tot;
             }
+            __syncthreads();                       // counts cleared before the next tile adds to them
         }
     }
     if (s_abort && tid == 0) {
@@ -211,25 +224,39 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
     }
 }
 
+static bool cull_tma_ok(const SceneView &sc)
+{
+    const bool restore_dir_path = sc.rdir != nullptr || !(sc.m && sc.v && sc.counter);
+    const bool aligned = ((uintptr_t)sc.geo & 15) == 0 && ((uintptr_t)sc.rdir & 15) == 0 &&
+                         ((uintptr_t)sc.counter & 15) == 0;   // bulk-copy rule
+    return restore_dir_path && aligned;
+}
+
+static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0, int nv, const CullOut &out, Work &w,
+                            cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
+        attr_set = true;
+    }
+    const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
+    const int gt = w.grid(nchunks * CT, CT, 3);
+    k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status);
+}
+
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
                  cudaStream_t s)
 {
     int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (view == 0) w.mark(TP_CULL0, s);
     const int g = w.grid(nchunks * CULL_BLOCK, CULL_BLOCK, 8);
-    const bool restore_dir_path = sc.rdir != nullptr || !(sc.m && sc.v && sc.counter);
-    const bool aligned = ((uintptr_t)sc.geo & 15) == 0 && ((uintptr_t)sc.rdir & 15) == 0 &&
-                         ((uintptr_t)sc.counter & 15) == 0;   // bulk-copy rule
-    if (restore_dir_path && aligned) {
+    if (cull_tma_ok(sc)) {
         // geometry (and restore directions) staged by the TMA engine
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_cull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
-            attr_set = true;
-        }
-        const int gt = w.grid(nchunks * CT, CT, 3);
-        k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view, mask, chunk_cnt,
-                                              w.status);
+        CullOut out{};
+        out.mask[0] = mask;
+        out.chunk[0] = chunk_cnt;
+        launch_cull_tma(sc, args, view, 1, out, w, s);
     } else if (sc.prec == GS_FP32)
         k_cull<float><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const float *)sc.m, (const float *)sc.v, sc.rdir, sc.counter,
                                                sc.pitch, sc.n, args, view, mask, chunk_cnt);
@@ -238,6 +265,23 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
                                                        sc.rdir, sc.counter, sc.pitch, sc.n, args, view, mask,
                                                        chunk_cnt);
     if (view == 0) w.mark(TP_CULL1, s);
+}
+
+void launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
+                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s)
+{
+    if (n_views == 1 || !cull_tma_ok(sc)) {
+        for (int v = 0; v < n_views; v++) launch_cull(sc, args, v, masks[v], chunk_cnts[v], w, s);
+        return;
+    }
+    w.mark(TP_CULL0, s);
+    CullOut out{};
+    for (int v = 0; v < n_views; v++) {
+        out.mask[v] = masks[v];
+        out.chunk[v] = chunk_cnts[v];
+    }
+    launch_cull_tma(sc, args, 0, n_views, out, w, s);
+    w.mark(TP_CULL1, s);
 }
 
 // Build a bitmask from an id list (ids < n).
