@@ -375,6 +375,35 @@ static __device__ __forceinline__ CovGrad cov_chain_bwd_fp64(const Geo10 G, cons
     return out;
 }
 
+// Cheap conservative pre-test of project_gaussian's keep decision: false only
+// when the full projection would reject the Gaussian.  The largest eigenvalue
+// of Sigma2 = T Sigma3 T^T + 0.3 I is at most |T|_F^2 max(s)^2 + 0.3, and the
+// radius formula adds at most sqrt(0.1) to it, so the pixel radius is at most
+// 3 sqrt(|T|_F^2 max(s)^2 + 0.62) + 1; a square of that half-width around the
+// projected mean that misses the tiled image (with a pixel of slack for
+// rounding) cannot overlap it.  Same depth test, same Jacobian as
+// project_gaussian.
+__device__ __forceinline__ bool maybe_visible(const float g[10], const DevCam &cam)
+{
+    const float *R = cam.R;
+    const float px = R[0] * g[0] + R[1] * g[1] + R[2] * g[2] + cam.t[0];
+    const float py = R[3] * g[0] + R[4] * g[1] + R[5] * g[2] + cam.t[1];
+    const float pz = R[6] * g[0] + R[7] * g[1] + R[8] * g[2] + cam.t[2];
+    if (!(pz > cam.near_z && pz < cam.far_z)) return false;
+    const float iz = __fdividef(1.f, pz);
+    const float u = px * iz, w = py * iz;
+    const float tu = fminf(cam.limx, fmaxf(-cam.limx, u));
+    const float tw = fminf(cam.limy, fmaxf(-cam.limy, w));
+    // |T|_F^2 = (fx/z)^2 (1 + tu^2) + (fy/z)^2 (1 + tw^2) for T = J W, W a rotation
+    const float fxz = cam.fx * iz, fyz = cam.fy * iz;
+    const float tn = fxz * fxz * (1.f + tu * tu) + fyz * fyz * (1.f + tw * tw);
+    const float smax = __expf(fmaxf(g[3], fmaxf(g[4], g[5])));
+    const float rb = 3.f * sqrt_fast(1.001f * (tn * smax * smax) + 0.62f) + 2.f;
+    const float mx = cam.fx * u + cam.cx, my = cam.fy * w + cam.cy;
+    const float Wt = (float)(cam.tiles_x * cam.tile_w), Ht = (float)(cam.tiles_y * cam.tile_h);
+    return mx + rb > -1.f && mx - rb < Wt + 1.f && my + rb > -1.f && my - rb < Ht + 1.f;
+}
+
 // Conditioning bound above which the 2D covariance is recomputed in FP64.
 constexpr float COND_FP64 = 64.f;
 
@@ -394,11 +423,13 @@ __device__ __forceinline__ void project_gaussian(const float g[10], const DevCam
     P.p[2] = R[6] * g[0] + R[7] * g[1] + R[8] * g[2] + cam.t[2];
     float pz = P.p[2];
     if (!(pz > cam.near_z && pz < cam.far_z)) return;
-    P.s[0] = expf(g[3]); P.s[1] = expf(g[4]); P.s[2] = expf(g[5]);
+    // hardware approximations (a few ulps) for the transcendental steps: every
+    // kernel projects through this one function, so their decisions agree
+    P.s[0] = __expf(g[3]); P.s[1] = __expf(g[4]); P.s[2] = __expf(g[5]);
     float qn2 = g[6] * g[6] + g[7] * g[7] + g[8] * g[8] + g[9] * g[9];
     if (qn2 > 0.f) {
-        P.qn = sqrtf(qn2);
-        float inv = 1.f / P.qn;
+        const float inv = rsqrtf(qn2);
+        P.qn = qn2 * inv;
         P.qh[0] = g[6] * inv; P.qh[1] = g[7] * inv; P.qh[2] = g[8] * inv; P.qh[3] = g[9] * inv;
     } else {
         P.qn = 1.f; P.qh[0] = 1.f; P.qh[1] = P.qh[2] = P.qh[3] = 0.f;
@@ -416,7 +447,7 @@ __device__ __forceinline__ void project_gaussian(const float g[10], const DevCam
     P.S3[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
     P.S3[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     P.S3[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-    float iz = 1.f / pz;
+    float iz = __fdividef(1.f, pz);
     float u = P.p[0] * iz, w = P.p[1] * iz;
     float tu = fminf(cam.limx, fmaxf(-cam.limx, u));
     float tw = fminf(cam.limy, fmaxf(-cam.limy, w));
@@ -469,12 +500,12 @@ __device__ __forceinline__ void project_gaussian(const float g[10], const DevCam
         P.conC = (float)(S2d[0] / detd);
     } else {
         if (!(P.det > 0.f)) return;
-        float idet = 1.f / P.det;
+        float idet = __fdividef(1.f, P.det);
         P.conA = P.c * idet; P.conB = -P.b * idet; P.conC = P.a * idet;
     }
     float mid = 0.5f * (P.a + P.c);
-    float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - P.det));
-    P.radius = ceilf(3.f * sqrtf(lam));
+    float lam = mid + sqrt_fast(fmaxf(0.1f, mid * mid - P.det));
+    P.radius = ceilf(3.f * sqrt_fast(lam));
     P.mx = cam.fx * u + cam.cx;
     P.my = cam.fy * w + cam.cy;
     float itw = 1.f / (float)cam.tile_w, ith = 1.f / (float)cam.tile_h;

@@ -66,9 +66,11 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
 #pragma unroll
                     for (int r = 0; r < 10; r++) g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], d, s_eps);
                 }
-                Proj P;
-                project_gaussian(g, s_cam, P);
-                keep = P.keep;
+                if (maybe_visible(g, s_cam)) {
+                    Proj P;
+                    project_gaussian(g, s_cam, P);
+                    keep = P.keep;
+                }
             }
             uint32_t word = __ballot_sync(0xffffffffu, keep);
             if (lane == 0 && wbase < n) {
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
             const int64_t wbase = t * CT + wid * 32;
             for (int v = 0; v < nv; v++) {
                 int keep = 0;
-                if (live) {
+                if (live && maybe_visible(g, s_cam[v])) {   // most Gaussians leave here
                     Proj P;
                     project_gaussian(g, s_cam[v], P);
                     keep = P.keep;
