@@ -87,8 +87,11 @@ enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
                  cudaStream_t s);
 // All views of a step in one sweep over the geometry (per-view masks and chunk counts).
-void launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
-                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s);
+// With umask, the same sweep also takes the deferred optimizer's select
+// (returns true; false if it fell back to per-view sweeps without it).
+bool launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
+                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s, uint32_t *umask = nullptr,
+                       uint32_t *uchunk = nullptr, int max_defer = 0);
 void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t *mask, int64_t n, Work &w,
                         cudaStream_t s);
 void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s);
@@ -104,6 +107,10 @@ void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t
 void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, const int32_t *uids, const uint8_t *udelay,
                        const int *u_range, const int *n_upd, Work &w, cudaStream_t s);
+void launch_adam_compact(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, int32_t *uids, uint8_t *udelay,
+                         int *n_upd, Work &w, cudaStream_t s);
+void launch_touch_from_masks(const uint32_t *vmask, const uint32_t *umask, int64_t n, int shift, uint8_t *touch,
+                             Work &w, cudaStream_t s);
 void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s);
 void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t n, int shift, int max_defer,
                          uint8_t *touch, Work &w, cudaStream_t s);

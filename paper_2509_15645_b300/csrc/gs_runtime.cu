@@ -832,22 +832,26 @@ gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **co
 struct StepMasks {
     const uint32_t *gmask, *gprefix;   // gradient rows: the view's visible set, or the union of the views'
     int64_t gcap;
+    bool selected;                     // the optimizer's select ran inside the cull sweep
 };
 
 // Cull of every view (visible ids, counts) and the union of the visible sets.
 static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, float *loss,
-                                    cudaStream_t s)
+                                    cudaStream_t s, int select_max_defer = -1)
 {
     const int V = (int)c->cfg.max_visible;
     DevArgs *args = c->args + SLOT_STEP;
     c->w.mark(TP_STEP0, s);
     set_args(c, SLOT_STEP, a, s);
     cudaMemsetAsync(loss, 0, sizeof(float), s);
-    launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s);
+    const bool selected = select_max_defer >= 0 &&
+                          launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s, c->umask, c->uchunk,
+                                            select_max_defer);
+    if (select_max_defer < 0) launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s);
     for (int v = 0; v < n_views; v++)
         compact_mask(c->vmask[v], sv.n, c->vchunk[v], true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
     cudaMemcpyAsync(&c->cnt->n_vis, c->nvis_view, sizeof(int), cudaMemcpyDeviceToDevice, s);
-    StepMasks M{c->vmask[0], c->vprefix[0], V};
+    StepMasks M{c->vmask[0], c->vprefix[0], V, selected};
     if (n_views > 1) {
         const int64_t nw = (sv.n + 31) / 32;
         cudaMemsetAsync(c->union_mask, 0, nw * sizeof(uint32_t), s);
@@ -855,7 +859,7 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
         compact_mask(c->union_mask, sv.n, c->union_chunk, false, nullptr, c->union_prefix, (int)c->gcap_u,
                      &c->cnt->n_union, c->w, s);
         launch_zero_rows(c->grad_u, sv.D, c->gcap_u, &c->cnt->n_union, (int)c->gcap_u, c->w, s);
-        M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u};
+        M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u, selected};
     }
     return M;
 }
@@ -891,7 +895,13 @@ static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const S
 {
     DevArgs *args = c->args + SLOT_STEP;
     c->w.mark(TP_ADAM0, s);
-    if (mode == GS_ADAM_DEFERRED)
+    if (mode == GS_ADAM_DEFERRED && M.selected) {
+        launch_adam_compact(sv, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+        c->w.mark(TP_APPLY0, s);
+        launch_adam_apply(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->uids, c->udelay, nullptr,
+                          &c->cnt->n_upd, c->w, s);
+        c->w.mark(TP_APPLY1, s);
+    } else if (mode == GS_ADAM_DEFERRED)
         launch_adam_deferred(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->umask, c->uchunk, c->uids, c->udelay,
                              &c->cnt->n_upd, c->w, s);
     else
@@ -906,7 +916,8 @@ static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const S
 static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, int mode, float *loss,
                          cudaStream_t s)
 {
-    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s);
+    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s,
+                                           mode == GS_ADAM_DEFERRED ? a.lut.max_defer : -1);
     enqueue_render_phase(c, sv, a, n_views, M, loss, s);
     enqueue_adam_phase(c, sv, mode, M, s);
 }
@@ -960,8 +971,11 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
         gs_ctx *c;
         ~TevReset() { c->w.tev = nullptr; }
     } tev_reset{c};
-    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s);
-    launch_touch_chunks(M.gmask, sv.counter, sv.n, c->shift, adam->max_defer, c->dtouch, c->w, s);
+    const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s, adam->max_defer);
+    if (M.selected)
+        launch_touch_from_masks(M.gmask, c->umask, sv.n, c->shift, c->dtouch, c->w, s);
+    else
+        launch_touch_chunks(M.gmask, sv.counter, sv.n, c->shift, adam->max_defer, c->dtouch, c->w, s);
     const int64_t nch = (sv.n + (1ll << c->shift) - 1) >> c->shift;
     cudaMemcpyAsync(c->htouch, c->dtouch, nch, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "host tier: touch map");
@@ -1021,7 +1035,10 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     enqueue_render_phase(c, sv, a, n_views, M, loss, s);
     DevArgs *args = c->args + SLOT_STEP;
     c->w.mark(TP_ADAM0, s);
-    launch_adam_select(sv, args, M.gmask, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+    if (M.selected)
+        launch_adam_compact(sv, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+    else
+        launch_adam_select(sv, args, M.gmask, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
     int *u_range = c->n_tmp + 2;
     const int64_t R = 1ll << c->shift;
     for (size_t k = 0; k < rounds.size(); k++) {

@@ -336,6 +336,41 @@ void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t
     compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s, sc.counter, udelay);
 }
 
+// The update-set compaction alone (when the select ran inside the cull sweep).
+void launch_adam_compact(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, int32_t *uids, uint8_t *udelay,
+                         int *n_upd, Work &w, cudaStream_t s)
+{
+    compact_mask(umask, sc.n, uchunk, true, uids, nullptr, (int)sc.n, n_upd, w, s, sc.counter, udelay);
+}
+
+// Host tier: chunk touch map from the step's masks -- 2 = a Gaussian visible in
+// some view, 1 = only update-set members (counter at the bound), else 0.
+__global__ void __launch_bounds__(ADAM_BLOCK) k_touch_from_masks(const uint32_t *__restrict__ vmask,
+                                                                 const uint32_t *__restrict__ umask, int64_t n,
+                                                                 int shift, uint8_t *__restrict__ touch)
+{
+    const int64_t R = 1ll << shift, nchunks = (n + R - 1) >> shift;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int64_t w0 = (c << shift) >> 5, w1 = (min(n, (c + 1) << shift) + 31) >> 5;
+        int vis = 0, upd = 0;
+        for (int64_t wd = w0 + threadIdx.x; wd < w1; wd += blockDim.x) {
+            vis |= vmask[wd] != 0u;
+            upd |= umask[wd] != 0u;
+        }
+        vis = __syncthreads_or(vis);
+        upd = __syncthreads_or(upd);
+        if (threadIdx.x == 0) touch[c] = vis ? 2 : (upd ? 1 : 0);
+    }
+}
+
+void launch_touch_from_masks(const uint32_t *vmask, const uint32_t *umask, int64_t n, int shift, uint8_t *touch,
+                             Work &w, cudaStream_t s)
+{
+    const int64_t nchunks = (n + (1ll << shift) - 1) >> shift;
+    k_touch_from_masks<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK, 4), ADAM_BLOCK, 0, s>>>(vmask, umask, n, shift,
+                                                                                       touch);
+}
+
 void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, const int32_t *uids, const uint8_t *udelay,
                        const int *u_range, const int *n_upd, Work &w, cudaStream_t s)

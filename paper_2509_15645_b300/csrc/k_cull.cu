@@ -110,6 +110,13 @@ constexpr uint32_t WAIT_LIMIT = 1u << 24;
 struct CullOut {
     uint32_t *mask[MAX_VIEWS];
     uint32_t *chunk[MAX_VIEWS];
+    // optional, inside a training step: the deferred optimizer's select of
+    // Fig. 10 on the same sweep -- update-set mask (visible in some view, or
+    // counter at max_defer), per-chunk member counts, counters of the other
+    // Gaussians incremented
+    uint32_t *umask;
+    uint32_t *uchunk;
+    uint8_t *counter_rw;
 };
 
 __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
@@ -132,6 +139,8 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
     if (tid < MAX_VIEWS * (CT / 32)) s_cnt[tid / (CT / 32)][tid % (CT / 32)] = 0;
     if (tid < 3 * LUT_N) s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
     const bool restore = args->lut.restore && rdir != nullptr && counter != nullptr;
+    const bool select = out.umask != nullptr;
+    const bool need_cnt = restore || select;
     if (tid == 0) {
         s_abort = 0;
         for (int k = 0; k < CSTAGES; k++) mbar_init(&bar[k], 1);
@@ -154,13 +163,12 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         const int64_t i0 = t * CT;
         const int64_t rows = min((int64_t)CT, n - i0);
         const uint32_t bytes = (uint32_t)(((rows + 3) & ~3ll) * 4);   // within the plane: pitch >= n, a multiple of 4
-        const bool cnt_bulk = restore && rows == CT;
+        const bool cnt_bulk = need_cnt && rows == CT;
         mbar_expect_tx(&bar[s], bytes * CPLANES * (restore ? 2u : 1u) + (cnt_bulk ? (uint32_t)CT : 0u));
         for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].geo[r], geo + r * pitch + i0, bytes, &bar[s]);
-        if (restore) {
+        if (restore)
             for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].dir[r], rdir + r * pitch + i0, bytes, &bar[s]);
-            if (cnt_bulk) bulk_g2s(st[s].cnt, counter + i0, CT, &bar[s]);
-        }
+        if (cnt_bulk) bulk_g2s(st[s].cnt, counter + i0, CT, &bar[s]);
     };
     if (tid == 0)
         for (int q = 0; q < CSTAGES - 1; q++) issue(q);
@@ -183,12 +191,13 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
             float g[CPLANES];
 #pragma unroll
             for (int r = 0; r < CPLANES; r++) g[r] = live ? st[s].geo[r][tid] : 0.f;
+            const int d = (need_cnt && live) ? ((t * CT + CT <= n) ? st[s].cnt[tid] : counter[i]) : 0;
             if (restore && live) {
-                const int d = (t * CT + CT <= n) ? st[s].cnt[tid] : counter[i];
 #pragma unroll
                 for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
             }
             const int64_t wbase = t * CT + wid * 32;
+            bool any_view = false;
             for (int v = 0; v < nv; v++) {
                 int keep = 0;
                 if (live && maybe_visible(g, s_cam[v])) {   // most Gaussians leave here
@@ -196,10 +205,20 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
                     project_gaussian(g, s_cam[v], P);
                     keep = P.keep;
                 }
+                any_view |= keep != 0;
                 const uint32_t word = __ballot_sync(0xffffffffu, keep);
                 if (lane == 0 && wbase < n) {
                     out.mask[v][wbase >> 5] = word;
                     s_cnt[v][wid] += __popc(word);
+                }
+            }
+            if (select) {
+                const bool in_u = live && (any_view || d >= args->lut.max_defer);
+                if (live && !in_u) out.counter_rw[i] = (uint8_t)(d + 1);
+                const uint32_t uword = __ballot_sync(0xffffffffu, in_u);
+                if (lane == 0 && wbase < n) {
+                    out.umask[wbase >> 5] = uword;
+                    if (uword) atomicAdd(&out.uchunk[t / PER_CHUNK], (uint32_t)__popc(uword));
                 }
             }
         }
@@ -243,6 +262,7 @@ static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0,
         attr_set = true;
     }
     const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
+    if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics
     const int gt = w.grid(nchunks * CT, CT, 3);
     k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status);
 }
@@ -269,12 +289,13 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
     if (view == 0) w.mark(TP_CULL1, s);
 }
 
-void launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
-                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s)
+bool launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
+                       uint32_t *const *chunk_cnts, Work &w, cudaStream_t s, uint32_t *umask, uint32_t *uchunk,
+                       int max_defer)
 {
-    if (n_views == 1 || !cull_tma_ok(sc)) {
+    if (!cull_tma_ok(sc)) {
         for (int v = 0; v < n_views; v++) launch_cull(sc, args, v, masks[v], chunk_cnts[v], w, s);
-        return;
+        return false;                              // the optimizer's select stays a pass of its own
     }
     w.mark(TP_CULL0, s);
     CullOut out{};
@@ -282,8 +303,15 @@ void launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, ui
         out.mask[v] = masks[v];
         out.chunk[v] = chunk_cnts[v];
     }
+    if (umask && sc.counter) {
+        out.umask = umask;
+        out.uchunk = uchunk;
+        out.counter_rw = sc.counter;
+        (void)max_defer;                           // the kernel reads the step's bound from the argument block
+    }
     launch_cull_tma(sc, args, 0, n_views, out, w, s);
     w.mark(TP_CULL1, s);
+    return out.umask != nullptr;
 }
 
 // Build a bitmask from an id list (ids < n).
