@@ -590,22 +590,21 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
     const int64_t HW = (int64_t)W * H;
-    float T[PPT], A0[PPT], A1[PPT], A2[PPT], F0[PPT], F1[PPT], F2[PPT], g0[PPT], g1[PPT], g2[PPT];
+    // per pixel: T, g . F (F the forward's final colour), g . A (A the colour
+    // accumulated so far, kept only as its product with g)
+    float T[PPT], gF[PPT], gA[PPT], g0[PPT], g1[PPT], g2[PPT];
     uint32_t live = 0;
 #pragma unroll
     for (int j = 0; j < PPT; j++) {
         T[j] = 1.f;
-        A0[j] = A1[j] = A2[j] = 0.f;
-        F0[j] = F1[j] = F2[j] = g0[j] = g1[j] = g2[j] = 0.f;
+        gF[j] = gA[j] = g0[j] = g1[j] = g2[j] = 0.f;
         if (x < W && y0 + j < H) {
             live |= 1u << j;
             const int64_t pix = (int64_t)(y0 + j) * W + x;
-            F0[j] = cfinal[pix];
-            F1[j] = cfinal[HW + pix];
-            F2[j] = cfinal[2 * HW + pix];
             g0[j] = dimage[pix];
             g1[j] = dimage[HW + pix];
             g2[j] = dimage[2 * HW + pix];
+            gF[j] = g0[j] * cfinal[pix] + g1[j] * cfinal[HW + pix] + g2[j] * cfinal[2 * HW + pix];
         }
     }
     for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
@@ -616,6 +615,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
             const float dx = __fsub_rn(r0.x, px);
+            // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
+            // G dL/da, g_r aT, g_g aT, g_b aT (ds = -a dL/da); the mean and conic
+            // gradients are formed from them once per (warp, splat)
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (live && fabsf(dx) <= r0.z) {
@@ -637,22 +639,22 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     contrib = true;
                     const float4 c = s2[e];
                     const float aT = a * T[j];
-                    A0[j] += c.x * aT;                   // as the forward accumulates C
-                    A1[j] += c.y * aT;
-                    A2[j] += c.z * aT;
-                    const float behind = g0[j] * (F0[j] - A0[j]) + g1[j] * (F1[j] - A1[j]) + g2[j] * (F2[j] - A2[j]);
-                    const float dLda = T[j] * (g0[j] * c.x + g1[j] * c.y + g2[j] * c.z) - __fdividef(behind, 1.f - a);
+                    const float gc = g0[j] * c.x + g1[j] * c.y + g2[j] * c.z;
+                    gA[j] += aT * gc;
+                    // dL/da = g . (T c - (F - A)/(1 - a)), A through this splat
+                    const float dLda = T[j] * gc - __fdividef(gF[j] - gA[j], 1.f - a);
                     v[6] += g0[j] * aT;
                     v[7] += g1[j] * aT;
                     v[8] += g2[j] * aT;
                     if (!cl) {                                   // the 0.999 clamp has no derivative
                         const float ds = -a * dLda;
                         v[5] += G * dLda;
-                        v[0] += ds * (r1.x * dx + r1.y * dy);
-                        v[1] += ds * (r1.y * dx + r1.z * dy);
-                        v[2] += 0.5f * ds * dx * dx;
-                        v[3] += ds * dx * dy;
-                        v[4] += 0.5f * ds * dy * dy;
+                        const float sdx = ds * dx, sdy = ds * dy;
+                        v[0] += sdx;
+                        v[1] += sdy;
+                        v[2] += sdx * dx;
+                        v[3] += sdx * dy;
+                        v[4] += sdy * dy;
                     }
                     T[j] = Tn;
                 }
@@ -668,9 +670,15 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                 const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
                 const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
                 float *row = g9 + (int64_t)k * G9_STRIDE;
-                if ((lane & 15) == 0)
-                    atomicAdd(reinterpret_cast<float4 *>(row + (lane >> 2)), make_float4(sum, q1, q2, q3));
-                if (lane == 0 && s8 != 0.f) atomicAdd(row + 8, s8);
+                if (lane == 0) {
+                    // d/d mean = conic (sum ds d), d/d conic = (sum ds dx^2 / 2, sum ds dx dy, .)
+                    const float4 cn = s1[e];
+                    atomicAdd(reinterpret_cast<float4 *>(row),
+                              make_float4(cn.x * sum + cn.y * q1, cn.y * sum + cn.z * q1, 0.5f * q2, q3));
+                    if (s8 != 0.f) atomicAdd(row + 8, s8);
+                } else if (lane == 16) {
+                    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+                }
             }
         }
     }
