@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import re
 import math
 import os
 import statistics
@@ -172,7 +173,7 @@ def run_ours(args):
                   max_views=vps, max_sh_degree=deg)
     # HBM budget: state that does not fit goes to the host tier (SH planes and
     # their optimizer state in pinned host memory, streamed by gs_step)
-    tier, stage_chunks, plan = gs.GS_TIER_DEVICE, 0, None
+    tier, stage_chunks, plan, eb = gs.GS_TIER_DEVICE, 0, None, 4
     if args.budget_gb:
         prec0 = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
         eb = 4 if prec0 == gs.GS_FP32 else 2
@@ -182,7 +183,7 @@ def run_ours(args):
         budget = args.budget_gb * 1e9
         if resident + ws0 > budget:
             R = 1 << args.chunk_shift
-            ring_chunk = 4 * (D - 11) * R * 4
+            ring_chunk = 3 * (D - 11) * R * eb          # w, m, v rows of the SH type
             stage_chunks = int((budget - geo_only - ws0) // ring_chunk)
             if stage_chunks < 1:
                 raise SystemExit(f"budget {args.budget_gb} GB holds no staging ring")
@@ -192,7 +193,8 @@ def run_ours(args):
                 "tier": "host_sh" if tier == gs.GS_TIER_HOST_SH else "device",
                 "device_state_gb": round((geo_only if tier else resident) / 1e9, 2),
                 "stage_chunks": stage_chunks, "chunk_rows": 1 << args.chunk_shift}
-    ctx = gs.Context(**ctx_kw, device=local, stage_chunks=stage_chunks, chunk_shift=args.chunk_shift)
+    ctx = gs.Context(**ctx_kw, device=local, stage_chunks=stage_chunks, chunk_shift=args.chunk_shift,
+                     stage_elem_bytes=eb if stage_chunks else 0)
     # targets: the seed-1 scene rendered by the same library (setup, untimed)
     tscene = gs.GaussianScene(tgt_params, deg, device=dev, with_optimizer=False)
     del tgt_params
@@ -216,6 +218,61 @@ def run_ours(args):
         vs = [(s * vps + j) % len(cams) for j in range(vps)]
         ctx.step(sc, [cams[v] for v in vs], tgt or [targets[v] for v in vs], adam, loss=loss)
 
+    def link_rates(nbytes=1 << 30, reps=4):
+        """Host<->device copy rates of this GPU's link from pinned memory (GB/s):
+        H2D alone, D2H alone, and both directions at once (their sum), untimed
+        setup measurements for the host tier."""
+        h = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        d = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+        st = [torch.cuda.Stream(device=dev) for _ in range(2)]
+
+        def run(up, down):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                if up:
+                    with torch.cuda.stream(st[0]):
+                        d[0].copy_(h[0], non_blocking=True)
+                if down:
+                    with torch.cuda.stream(st[1]):
+                        h[1].copy_(d[1], non_blocking=True)
+            torch.cuda.synchronize()
+            return round(reps * nbytes * (up + down) / (time.perf_counter() - t) / 1e9, 1)
+
+        run(1, 1)
+        out = {"h2d": run(1, 0), "d2h": run(0, 1), "both_directions": run(1, 1)}
+        del h, d
+        return out
+
+    def trace_step(sc, s):
+        """One extra untimed step under the CUDA activity trace: the kernels of
+        this library it launches (for steps that run without a captured graph,
+        e.g. the host tier) and, per copy direction, the bytes, the summed copy
+        durations and the span from the first copy's start to the last's end."""
+        try:
+            import tempfile
+            from torch.profiler import profile, ProfilerActivity
+            torch.cuda.synchronize()
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                one_step(sc, s)
+                torch.cuda.synchronize()
+            with tempfile.NamedTemporaryFile(suffix=".json") as f:
+                prof.export_chrome_trace(f.name)
+                ev = json.load(open(f.name)).get("traceEvents", [])
+            kernels = sum(1 for e in ev if e.get("cat") == "kernel" and re.search(r"(^|[\s:])k_\w+", e.get("name", "")))
+            copies = {}
+            for d, key in (("HtoD", "h2d"), ("DtoH", "d2h")):
+                cs = [e for e in ev if e.get("cat") == "gpu_memcpy" and d in e.get("name", "")]
+                if cs:
+                    nb = sum(float(e.get("args", {}).get("bytes", 0)) for e in cs)
+                    busy = sum(float(e["dur"]) for e in cs) * 1e-3
+                    span = (max(e["ts"] + e["dur"] for e in cs) - min(e["ts"] for e in cs)) * 1e-3
+                    copies[key] = {"copies": len(cs), "bytes": nb, "busy_ms": round(busy, 3),
+                                   "span_ms": round(span, 3), "gbs_while_busy": round(nb / busy * 1e-6, 1)}
+            return kernels, copies
+        except Exception as e:
+            return None, {"error": repr(e)[:200]}
+
     def timed_steps(sc):
         """W warm-up steps, then K steps between CUDA events on the launching
         stream (barrier + synchronize on both sides), clocks sampled meanwhile.
@@ -233,8 +290,12 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
+        staged = []
         for s in range(K):
             one_step(sc, Wm + s)
+            if tier:     # host-side counters of the step just enqueued (no synchronisation)
+                staged.append(ctx.host_tier_stats())
+        ctx.wait_copies()                # the last step's write-backs to host memory are timed too
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -248,7 +309,7 @@ def run_ours(args):
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        return ms, sp, clk
+        return ms, sp, clk, staged
 
     def measure(precision):
         """Autotune, time K steps of one precision form, then an untimed pass
@@ -262,17 +323,19 @@ def run_ours(args):
         if args.raster_variant is not None:
             ctx.set_raster_variant(args.raster_variant)
             variant = (args.raster_variant, args.raster_variant)
-        ms_total, spans, clk = timed_steps(sc)
-        stats, staged = [], []
+        ms_total, spans, clk, staged = timed_steps(sc)
+        stats = []
         ctx.timing_enable(tcap)
         for s in range(min(len(cams), 16 if tier == gs.GS_TIER_DEVICE else 4)):
             n_restore_geo = int((sc.counter[:N] > 0).sum().item())
             one_step(sc, Wm + K + s)
             c = ctx.counters().cpu().tolist()
             stats.append((c[0], c[1], c[2], n_restore_geo, c[6]))
-            if tier:
-                staged.append(ctx.host_tier_stats())
         ctx.timing_read(tcap)
+        kernels = ctx.step_kernel_count()    # kernel nodes of the captured step graph
+        copy_trace = None
+        if not kernels:
+            kernels, copy_trace = trace_step(sc, Wm + K + 16)
         if tier == gs.GS_TIER_DEVICE:
             pairs = np.array([ctx.raster_pair_counts(sc, cam) for cam in cams], np.float64)   # untimed
         else:
@@ -286,7 +349,7 @@ def run_ours(args):
              "n_upd": float(np.mean([x[2] for x in stats])), "n_rest": float(np.mean([x[3] for x in stats])),
              "n_fp64": float(np.mean([x[4] for x in stats])),
              "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
-             "kernels": ctx.step_kernel_count(),
+             "kernels": kernels, "copy_trace": copy_trace,
              "staged_chunks": float(np.mean([x[0] for x in staged])) if staged else None,
              "staged_bytes": float(np.mean([x[1] for x in staged])) if staged else None}
         b_cull, b_apply, b_select = algorithmic_bytes(N, D, m["n_vis"], m["n_upd"], m["n_rest"],
@@ -347,6 +410,7 @@ def run_ours(args):
         f0.record(stream)
         for s in range(K):
             e2e_step(s)
+        ctx.wait_copies()
         f1.record(stream)
         torch.cuda.synchronize()
         ms = f0.elapsed_time(f1)
@@ -402,13 +466,19 @@ def run_ours(args):
         "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in m["st"].items()},
         "e2e": e2e_main,
         "clocks": m["clk"],
-        "gpu_launches": int(m["kernels"] * K),
+        "gpu_launches": int(m["kernels"] * K) if m["kernels"] else None,
         "bf16_form": bf16,
     }
     if tier:
         out["host_tier"] = {"staged_chunks_per_step": m["staged_chunks"], "chunk_rows": 1 << args.chunk_shift,
                             "bytes_per_step": m["staged_bytes"],
-                            "pcie_gbs": m["staged_bytes"] / (K_ms / K * 1e-3) / 1e9 if m["staged_bytes"] else None}
+                            "pcie_gbs": m["staged_bytes"] / (K_ms / K * 1e-3) / 1e9 if m["staged_bytes"] else None,
+                            "copy_trace": m["copy_trace"], "link_gbs": link_rates()}
+        # the counts behind the kernels' algorithmic bytes come from untimed steps at
+        # another point of the deferral cycle than the timed ones: no kernel roofline here
+        out["roofline"] = {"bound": "pcie", "note": "host tier: the step is bound by its host<->device copies; "
+                           "kernel rooflines are measured on the resident workloads"}
+        out["cull_adam"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, sample_frac=0.1)
     if rank == 0:
@@ -513,7 +583,7 @@ def main():
     ap.add_argument("--views-per-step", type=int, default=1, help="views rendered and summed per training step")
     ap.add_argument("--budget-gb", type=float, default=None,
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
-    ap.add_argument("--chunk-shift", type=int, default=15, help="log2 Gaussians per host-tier chunk")
+    ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:

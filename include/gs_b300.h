@@ -13,8 +13,9 @@
  *    buffer it passes; the context owns only its scratch workspace.
  *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
  *    void*; NULL = legacy default stream) and never synchronises, except
- *    gs_sync_status and gs_create/gs_destroy.  A context must be driven from
- *    one stream at a time.
+ *    gs_sync_status, gs_create/gs_destroy, gs_timing_read and gs_step on a
+ *    host-tier scene (which waits once for its chunk-touch map).  A context
+ *    must be driven from one stream at a time.
  *  - Invalid arguments return GS_ERR_INVALID_ARG before anything is launched;
  *    a failed launch returns GS_ERR_CUDA.  Errors found on the device (a
  *    capacity overflow, a non-finite loss) are latched in a device status word
@@ -73,11 +74,16 @@ enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
  * every plane in device memory.  GS_TIER_HOST_SH: the geometry and opacity
  * planes with their moments and restore directions stay in device memory
  * (geo, m, v, rdir then hold those 11 rows only, [11][pitch]); the SH planes
- * with their m, v and restore directions live in pinned host memory (host_sh,
- * host_m, host_v, host_rdir, each [D-11][pitch] of the SH type).  gs_step
- * streams the chunks of 2^chunk_shift Gaussians that a step touches (the
- * visible ones and the optimizer's update set) into the context's staging
- * ring with cudaMemcpy2DAsync on a side stream, and the updated rows back. */
+ * with their m and v live in pinned host memory (host_sh, host_m, host_v, each
+ * [D-11][pitch] of the SH type; their restore directions are recomputed from
+ * m, v on the device instead of being streamed).  gs_step streams the chunks
+ * of 2^chunk_shift Gaussians that a step touches (the visible ones and the
+ * optimizer's update set) into the context's staging ring with
+ * cudaMemcpy2DAsync on one side stream and the updated rows back on another,
+ * so both PCIe directions run at once.  The last write-backs of a step run
+ * on past the end of its work on `stream` (overlapping the next step's cull);
+ * gs_wait_copies makes a stream wait for them, gs_sync_status waits for them
+ * on the host, and the next gs_step orders its own copies after them. */
 enum { GS_TIER_DEVICE = 0, GS_TIER_HOST_SH = 1 };
 
 /* Adam variants: deferred with the restore tables of Fig. 10 (the method) or
@@ -120,8 +126,8 @@ typedef struct {
     int32_t tier;          /* GS_TIER_DEVICE or GS_TIER_HOST_SH */
     void *host_sh;         /* GS_TIER_HOST_SH only: pinned host [D-11][pitch] SH planes, */
     void *host_m;          /*   their first moments, */
-    void *host_v;          /*   second moments */
-    void *host_rdir;       /*   and restore directions (all of the SH type) */
+    void *host_v;          /*   and second moments (all of the SH type) */
+    void *host_rdir;       /*   unused (SH restore directions are recomputed from m, v on the device); may be NULL */
 } gs_scene;
 
 /* Adam hyper-parameters (§4.3.2).  lr per parameter group:
@@ -144,8 +150,8 @@ typedef struct {
     int32_t max_views;       /* views per gs_step, 1..8 */
     int32_t max_sh_degree;   /* 0..3 */
     int64_t stage_chunks;    /* staging ring of host-tier scenes, in chunks (0: no host tier) */
-    int32_t chunk_shift;     /* log2 Gaussians per chunk, 10..20 (0: 15) */
-    int32_t reserved;
+    int32_t chunk_shift;     /* log2 Gaussians per chunk, 10..20 (0: 11) */
+    int32_t stage_elem_bytes;/* element size of the staged SH rows: 4 (0: 4) serves every form, 2 only the bf16 forms */
 } gs_config;
 
 /* ------------------------------------------------------------------ context */
@@ -167,6 +173,12 @@ GS_API const char *gs_last_error(const gs_ctx *ctx);
 /* Synchronise `stream`, then return and clear the first error latched on the
  * device since the last call (GS_OK if none). */
 GS_API gs_status gs_sync_status(gs_ctx *ctx, void *stream);
+
+/* Make `stream` wait (without blocking the host) for the host-tier copies
+ * the context has in flight: the write-backs of its last gs_step.  Work
+ * enqueued on `stream` afterwards sees the updated host planes.  A no-op for
+ * contexts without a staging ring. */
+GS_API gs_status gs_wait_copies(gs_ctx *ctx, void *stream);
 
 /* Device pointer to the context's 8 int32 counters: [0] visible count of the
  * last gs_cull, [1] key count of the last render, [2] update-set size of the

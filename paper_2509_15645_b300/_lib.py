@@ -38,7 +38,7 @@ class AdamCfg(C.Structure):
 class Config(C.Structure):
     _fields_ = [("max_gaussians", c_i64), ("max_visible", c_i64), ("max_keys", c_i64), ("max_width", c_i32),
                 ("max_height", c_i32), ("tile_w", c_i32), ("tile_h", c_i32), ("max_views", c_i32),
-                ("max_sh_degree", c_i32), ("stage_chunks", c_i64), ("chunk_shift", c_i32), ("reserved", c_i32)]
+                ("max_sh_degree", c_i32), ("stage_chunks", c_i64), ("chunk_shift", c_i32), ("stage_elem_bytes", c_i32)]
 
 
 EXPORTS = {
@@ -47,6 +47,7 @@ EXPORTS = {
     "gs_destroy": (c_i32, [c_vp]),
     "gs_last_error": (C.c_char_p, [c_vp]),
     "gs_sync_status": (c_i32, [c_vp, c_vp]),
+    "gs_wait_copies": (c_i32, [c_vp, c_vp]),
     "gs_device_counters": (c_vp, [c_vp]),
     "gs_cull": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_vp, c_vp, c_vp]),
     "gs_render_fwd": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_vp, c_vp, c_vp, c_vp]),

@@ -72,8 +72,9 @@ class GaussianScene:
 
     tier GS_TIER_HOST_SH: the geometry planes with their m, v (``m``, ``v``
     [11][pitch]) and ``rdir_geo`` stay on the device; the SH planes ``sh`` and
-    their ``m_sh``, ``v_sh``, ``rdir_sh`` are pinned host tensors [D-11][pitch]
-    that gs_step streams (read them after ``Context.sync_status``)."""
+    their ``m_sh``, ``v_sh`` are pinned host tensors [D-11][pitch] that gs_step
+    streams (read them after ``Context.sync_status``, or from work enqueued on a
+    stream after ``Context.wait_copies``)."""
 
     def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True,
                  precision=L.GS_FP32, tier=L.GS_TIER_DEVICE):
@@ -101,9 +102,8 @@ class GaussianScene:
             self.m_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
             self.v_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
             self.counter = torch.zeros(P, dtype=torch.uint8, device=device)
-            if with_rdir:
+            if with_rdir:     # geometry directions only: the SH ones are recomputed on the device
                 self.rdir_geo = torch.zeros(11, P, dtype=torch.float32, device=device)
-                self.rdir_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
             self.step = 0
             return
         src = src.to(device)
@@ -146,7 +146,7 @@ class GaussianScene:
         s.counter = self.counter.data_ptr() if self.counter is not None else None
         if self.tier == L.GS_TIER_HOST_SH:
             s.host_sh, s.host_m, s.host_v = self.sh.data_ptr(), self.m_sh.data_ptr(), self.v_sh.data_ptr()
-            s.host_rdir = self.rdir_sh.data_ptr() if self.rdir_sh is not None else None
+            s.host_rdir = None
         s.step = self.step
         return s
 
@@ -169,10 +169,10 @@ class Context:
     """One gs_ctx: scratch workspace (a torch allocation) and the hot-path calls."""
 
     def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
-                 max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0):
+                 max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0):
         self.lib = L.load()
         cfg = self._config(max_gaussians, max_visible, max_keys, max_width, max_height, tile, max_views,
-                           max_sh_degree, stage_chunks, chunk_shift)
+                           max_sh_degree, stage_chunks, chunk_shift, stage_elem_bytes)
         self.cfg = cfg
         nb = C.c_size_t(0)
         self._check(self.lib.gs_workspace_size(C.byref(cfg), C.byref(nb)), "workspace size")
@@ -185,9 +185,10 @@ class Context:
 
     @staticmethod
     def _config(max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
-                max_sh_degree=3, stage_chunks=0, chunk_shift=0):
+                max_sh_degree=3, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0):
         cfg = L.Config()
         cfg.stage_chunks, cfg.chunk_shift = int(stage_chunks), int(chunk_shift)
+        cfg.stage_elem_bytes = int(stage_elem_bytes)
         cfg.max_gaussians, cfg.max_visible, cfg.max_keys = int(max_gaussians), int(max_visible), int(max_keys)
         cfg.max_width, cfg.max_height = int(max_width), int(max_height)
         cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
@@ -224,6 +225,10 @@ class Context:
     def sync_status(self, stream=None):
         st = self.lib.gs_sync_status(self.h, _stream(stream))
         self._check(st, "device status")
+
+    def wait_copies(self, stream=None):
+        """The stream waits for the host tier's write-backs still in flight."""
+        self._check(self.lib.gs_wait_copies(self.h, _stream(stream)), "gs_wait_copies")
 
     def counters(self):
         """The context's device counters (a torch view, no copy): [0] visible

@@ -80,13 +80,15 @@ struct gs_ctx {
     // stream and its events
     int shift = 15;
     int64_t max_chunks = 0;
-    void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    void *stage[3] = {nullptr, nullptr, nullptr};
     int32_t *dslot = nullptr;
     uint8_t *dtouch = nullptr;
     uint8_t *htouch = nullptr;          // pinned
     int32_t *hslot = nullptr;           // pinned
-    cudaStream_t cstream = nullptr;
-    cudaEvent_t ev_vis = nullptr, ev_upd = nullptr, ev_done = nullptr;
+    cudaStream_t cstream = nullptr;     // host -> device copies
+    cudaStream_t dstream = nullptr;     // device -> host copies (the other PCIe direction, concurrently)
+    cudaEvent_t ev_vis = nullptr, ev_upd = nullptr, ev_done = nullptr, ev_end = nullptr;
+    cudaEvent_t ev_down[2] = {nullptr, nullptr};
     struct Run { int64_t chunk0, slot0, nchunks; };
     std::vector<Run> runs;              // copy runs of the last host-tier step
     int64_t last_touched = 0, last_bytes = 0;
@@ -148,8 +150,11 @@ static bool valid_cfg(const gs_config *c)
            (tp == 32 || tp == 64 || tp == 128 || tp == 256) &&
            c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h && c->stage_chunks >= 0 &&
-           (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20));
+           (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20)) &&
+           (c->stage_elem_bytes == 0 || c->stage_elem_bytes == 2 || c->stage_elem_bytes == 4);
 }
+
+static int stage_eb(const gs_config &g) { return g.stage_elem_bytes ? g.stage_elem_bytes : 4; }
 
 static void carve(gs_ctx *c, char *base)
 {
@@ -229,10 +234,10 @@ static void carve(gs_ctx *c, char *base)
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
     if (g.stage_chunks > 0) {
-        c->shift = g.chunk_shift ? g.chunk_shift : 15;
+        c->shift = g.chunk_shift ? g.chunk_shift : 11;
         c->max_chunks = (N + (1ll << c->shift) - 1) >> c->shift;
-        const size_t ring = (size_t)(D - N_GEO) * ((size_t)g.stage_chunks << c->shift);
-        for (int j = 0; j < 4; j++) c->stage[j] = k.take<float>(ring);   // sized for fp32 rows
+        const size_t ring = (size_t)(D - N_GEO) * ((size_t)g.stage_chunks << c->shift) * stage_eb(g);
+        for (int j = 0; j < 3; j++) c->stage[j] = k.take<char>(ring);    // w, m, v
         c->dslot = k.take<int32_t>(c->max_chunks);
         c->dtouch = k.take<uint8_t>(c->max_chunks);
     }
@@ -338,6 +343,9 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     if (host && (c->cfg.stage_chunks <= 0 || !s->host_sh || !s->host_m || !s->host_v || !s->m || !s->v ||
                  !s->counter))
         return fail(c, GS_ERR_INVALID_ARG, "host tier needs a staging ring (stage_chunks) and host_sh/m/v planes");
+    if (host && elem_bytes(s->precision) > stage_eb(c->cfg))
+        return fail(c, GS_ERR_INVALID_ARG, "staging ring holds %d-byte rows, the scene's SH rows have %d bytes",
+                    stage_eb(c->cfg), (int)elem_bytes(s->precision));
     if (!s->geo || (!host && !s->sh)) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
     if (need_opt && (!s->m || !s->v || !s->counter)) return fail(c, GS_ERR_INVALID_ARG, "optimizer state is NULL");
     const int64_t eb = elem_bytes(s->precision), P = s->pitch;
@@ -361,11 +369,11 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
         sv.sh.slot = nullptr;
         sv.sh.shift = 0;
     } else {
-        if (sv.rdir && !s->host_rdir) return fail(c, GS_ERR_INVALID_ARG, "host tier with rdir needs host_rdir");
+        // SH restore directions are not streamed: the kernels recompute them from the staged m, v
         sv.sh.w = c->stage[0];
         sv.sh.m = c->stage[1];
         sv.sh.v = c->stage[2];
-        sv.sh.rdir = sv.rdir ? c->stage[3] : nullptr;
+        sv.sh.rdir = nullptr;
         sv.sh.ppitch = c->cfg.stage_chunks << c->shift;
         sv.sh.slot = c->dslot;
         sv.sh.shift = c->shift;
@@ -437,9 +445,13 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
         if (cudaHostAlloc((void **)&c->htouch, c->max_chunks, cudaHostAllocDefault) != cudaSuccess ||
             cudaHostAlloc((void **)&c->hslot, c->max_chunks * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
             cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_vis, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_upd, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_down[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_down[1], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             gs_destroy(c);
             return GS_ERR_CUDA;
@@ -457,10 +469,11 @@ gs_status gs_destroy(gs_ctx *c)
     if (c->graph.graph) cudaGraphDestroy(c->graph.graph);
     timing_free(c);
     if (c->cstream) cudaStreamSynchronize(c->cstream);
-    if (c->ev_vis) cudaEventDestroy(c->ev_vis);
-    if (c->ev_upd) cudaEventDestroy(c->ev_upd);
-    if (c->ev_done) cudaEventDestroy(c->ev_done);
+    if (c->dstream) cudaStreamSynchronize(c->dstream);
+    for (cudaEvent_t e : {c->ev_vis, c->ev_upd, c->ev_done, c->ev_end, c->ev_down[0], c->ev_down[1]})
+        if (e) cudaEventDestroy(e);
     if (c->cstream) cudaStreamDestroy(c->cstream);
+    if (c->dstream) cudaStreamDestroy(c->dstream);
     if (c->htouch) cudaFreeHost(c->htouch);
     if (c->hslot) cudaFreeHost(c->hslot);
     if (c->own_ws && c->ws) cudaFree(c->ws);
@@ -472,12 +485,21 @@ const char *gs_last_error(const gs_ctx *c) { return c ? c->err : "null context";
 
 const int32_t *gs_device_counters(const gs_ctx *c) { return c ? reinterpret_cast<const int32_t *>(c->cnt) : nullptr; }
 
+gs_status gs_wait_copies(gs_ctx *c, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->dstream) return GS_OK;
+    if (cudaStreamWaitEvent((cudaStream_t)stream, c->ev_end, 0) != cudaSuccess) return cuda_check(c, "gs_wait_copies");
+    return GS_OK;
+}
+
 gs_status gs_sync_status(gs_ctx *c, void *stream)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "gs_sync_status");
     if (c->cstream && cudaStreamSynchronize(c->cstream) != cudaSuccess) return cuda_check(c, "gs_sync_status copies");
+    if (c->dstream && cudaStreamSynchronize(c->dstream) != cudaSuccess) return cuda_check(c, "gs_sync_status copies");
     int st = 0;
     if (cudaMemcpy(&st, &c->cnt->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_check(c, "gs_sync_status read");
@@ -922,20 +944,19 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
     enqueue_adam_phase(c, sv, mode, M, s);
 }
 
-// One copy per staged array (w, m, v, restore direction) of each run of
-// consecutive chunks held in consecutive slots: rows [chunk0 << shift, ...) of
-// the host planes <-> the slots' rows of the staging ring, all SH planes at once.
+// One copy per staged array (w, m, v) of each run of consecutive chunks held
+// in consecutive slots: rows [chunk0 << shift, ...) of the host planes <-> the
+// slots' rows of the staging ring, all SH planes at once.
 static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, size_t first, size_t last, bool to_dev)
 {
     const int64_t eb = elem_bytes(scene->precision), R = 1ll << c->shift;
     const int64_t planes = sv.D - N_GEO, ring = sv.sh.ppitch;
-    void *host[4] = {scene->host_sh, scene->host_m, scene->host_v, sv.rdir ? scene->host_rdir : nullptr};
+    void *host[3] = {scene->host_sh, scene->host_m, scene->host_v};
     for (size_t k = first; k < last; k++) {
         const gs_ctx::Run &r = c->runs[k];
         const int64_t i0 = r.chunk0 << c->shift;
         const int64_t rows = std::min(sv.n, (r.chunk0 + r.nchunks) << c->shift) - i0;
-        for (int j = 0; j < 4; j++) {
-            if (!host[j]) continue;
+        for (int j = 0; j < 3; j++) {
             char *h = (char *)host[j] + i0 * eb;
             char *d = (char *)c->stage[j] + r.slot0 * R * eb;
             if (to_dev)
@@ -943,7 +964,7 @@ static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, siz
                                   c->cstream);
             else
                 cudaMemcpy2DAsync(h, scene->pitch * eb, d, ring * eb, rows * eb, planes, cudaMemcpyDeviceToHost,
-                                  c->cstream);
+                                  c->dstream);
             c->last_bytes += rows * eb * planes;
         }
     }
@@ -954,13 +975,17 @@ static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, siz
 // synchronisation to read the map.  Chunks with visible Gaussians take the
 // first slots of the staging ring for the whole step; the optimizer-only
 // chunks (counters at the bound) go through the remaining slots in rounds,
-// each round covering a range of chunk ids.  Copy stream: H2D of the visible
-// chunks (the render waits for these only), then per round the write-back of
-// the previous round's chunks and the H2D of this round's; stream: render,
-// the optimizer's select, and per round the apply over the members whose ids
-// fall in the round's range.  The updated rows go back D2H on the copy stream,
-// overlapping whatever the caller enqueues next.  Kernels are launched
-// directly (no graph: the copies depend on the map).
+// each round covering a range of chunk ids, alternating between the two
+// halves of that part of the ring.  Three streams: the H2D copy stream brings
+// the visible chunks (the render waits for these only), then each round's
+// chunks once the half it fills has been written back; the stream renders,
+// takes the optimizer's select, and per round applies Adam to the members
+// whose ids fall in the round's range; the D2H copy stream writes back, after
+// each round's apply, that round's chunks and the visible chunks of its id
+// range (final from then on).  So the two PCIe directions run at the same
+// time.  The last write-backs overlap the next step's cull; that step's
+// copies wait for them (ev_end).  Kernels are launched directly (no graph:
+// the copies depend on the map).
 static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv, const DevArgs &a, int n_views,
                                 const gs_adam_cfg *adam, float *loss, cudaStream_t s)
 {
@@ -980,8 +1005,9 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     cudaMemcpyAsync(c->htouch, c->dtouch, nch, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "host tier: touch map");
 
-    // plan: visible chunks -> slots [0, nv); optimizer-only chunks -> slots
-    // [nv, ring) in rounds of at most `cap` chunks, cut at chunk-id boundaries
+    // plan: visible chunks -> slots [0, nv); optimizer-only chunks -> rounds of
+    // at most `rcap` chunks, cut at chunk-id boundaries, round k in slots
+    // nv + (k % nbuf) * rcap + [0, rcap)
     int64_t nv = 0, nu = 0;
     for (int64_t ch = 0; ch < nch; ch++) {
         if (c->htouch[ch] == 2) c->hslot[ch] = (int32_t)nv++;
@@ -992,43 +1018,54 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     if (nv > c->cfg.stage_chunks || (nu > 0 && cap < 1))
         return fail(c, GS_ERR_CAPACITY, "host tier: %lld chunks of visible Gaussians, staging ring holds %lld",
                     (long long)nv + (nu > 0), (long long)c->cfg.stage_chunks);
-    struct Round { int64_t ch_lo, ch_hi; size_t run_lo, run_hi; };
+    const int64_t nbuf = cap >= 2 ? 2 : 1, rcap = nu > 0 ? cap / nbuf : 1;
+    struct Round { int64_t ch_lo, ch_hi; size_t vis_lo, vis_hi, upd_lo, upd_hi; };
     std::vector<Round> rounds;
+    {
+        Round r{0, nch, 0, 0, 0, 0};
+        int64_t in_round = 0;
+        for (int64_t ch = 0; ch < nch; ch++) {
+            if (c->htouch[ch] != 1) continue;
+            if (in_round == rcap) {           // close the round before this chunk
+                r.ch_hi = ch;
+                rounds.push_back(r);
+                r = Round{ch, nch, 0, 0, 0, 0};
+                in_round = 0;
+            }
+            c->hslot[ch] = (int32_t)(nv + ((int64_t)rounds.size() % nbuf) * rcap + in_round);
+            in_round++;
+        }
+        rounds.push_back(r);
+    }
     c->runs.clear();
-    auto add_run = [&](int64_t ch, int64_t slot) {
-        if (!c->runs.empty() && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
+    auto add_run = [&](int64_t ch, size_t first) {
+        const int64_t slot = c->hslot[ch];
+        if (c->runs.size() > first && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
             c->runs.back().slot0 + c->runs.back().nchunks == slot)
             c->runs.back().nchunks++;
         else
             c->runs.push_back(gs_ctx::Run{ch, slot, 1});
     };
-    for (int64_t ch = 0; ch < nch; ch++)
-        if (c->htouch[ch] == 2) add_run(ch, c->hslot[ch]);
+    for (Round &r : rounds) {             // visible chunks, runs split at round boundaries
+        r.vis_lo = c->runs.size();
+        for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
+            if (c->htouch[ch] == 2) add_run(ch, r.vis_lo);
+        r.vis_hi = c->runs.size();
+    }
     const size_t n_vis_runs = c->runs.size();
-    {
-        Round r{0, nch, n_vis_runs, n_vis_runs};
-        int64_t in_round = 0;
-        for (int64_t ch = 0; ch < nch; ch++) {
-            if (c->htouch[ch] != 1) continue;
-            if (in_round == cap) {           // close the round before this chunk
-                r.ch_hi = ch;
-                r.run_hi = c->runs.size();
-                rounds.push_back(r);
-                r = Round{ch, nch, c->runs.size(), c->runs.size()};
-                in_round = 0;
-            }
-            c->hslot[ch] = (int32_t)(nv + in_round);
-            add_run(ch, nv + in_round);
-            in_round++;
-        }
-        r.run_hi = c->runs.size();
-        rounds.push_back(r);
+    for (Round &r : rounds) {             // optimizer-only chunks
+        r.upd_lo = c->runs.size();
+        for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
+            if (c->htouch[ch] == 1) add_run(ch, r.upd_lo);
+        r.upd_hi = c->runs.size();
     }
     c->last_touched = nv + nu;
     c->last_bytes = 0;
     cudaMemcpyAsync(c->dslot, c->hslot, nch * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    // the copy stream still holds the previous step's write-backs: its order
-    // keeps the ring and the host rows consistent
+    // after the previous step's write-backs (also when it ran on another
+    // stream): the ring and the host rows are free and current.  The render
+    // needs all three arrays (its deferred restore of SH rows reads m and v).
+    cudaStreamWaitEvent(c->cstream, c->ev_end, 0);
     copy_runs(c, scene, sv, 0, n_vis_runs, true);
     cudaEventRecord(c->ev_vis, c->cstream);
     cudaStreamWaitEvent(s, c->ev_vis, 0);
@@ -1043,11 +1080,9 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     const int64_t R = 1ll << c->shift;
     for (size_t k = 0; k < rounds.size(); k++) {
         const Round &r = rounds[k];
-        if (k > 0) {                          // the ring slots of the previous round go back first
-            cudaStreamWaitEvent(c->cstream, c->ev_done, 0);
-            copy_runs(c, scene, sv, rounds[k - 1].run_lo, rounds[k - 1].run_hi, false);
-        }
-        copy_runs(c, scene, sv, r.run_lo, r.run_hi, true);
+        // the ring half this round fills was written back by round k - nbuf
+        if ((int64_t)k >= nbuf) cudaStreamWaitEvent(c->cstream, c->ev_down[k % nbuf], 0);
+        copy_runs(c, scene, sv, r.upd_lo, r.upd_hi, true);
         cudaEventRecord(c->ev_upd, c->cstream);
         cudaStreamWaitEvent(s, c->ev_upd, 0);
         launch_uid_range(c->uids, &c->cnt->n_upd, r.ch_lo * R, r.ch_hi * R, u_range, s);
@@ -1056,12 +1091,14 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
                           &c->cnt->n_upd, c->w, s);
         if (k == 0) c->w.mark(TP_APPLY1, s);
         cudaEventRecord(c->ev_done, s);
+        cudaStreamWaitEvent(c->dstream, c->ev_done, 0);
+        copy_runs(c, scene, sv, r.upd_lo, r.upd_hi, false);
+        copy_runs(c, scene, sv, r.vis_lo, r.vis_hi, false);
+        cudaEventRecord(c->ev_down[k % nbuf], c->dstream);
     }
     c->w.mark(TP_ADAM1, s);
     c->w.mark(TP_STEP1, s);
-    cudaStreamWaitEvent(c->cstream, c->ev_done, 0);
-    copy_runs(c, scene, sv, rounds.back().run_lo, rounds.back().run_hi, false);
-    copy_runs(c, scene, sv, 0, n_vis_runs, false);
+    cudaEventRecord(c->ev_end, c->dstream);
     if (c->w.tev) c->t_used++;
     return cuda_check(c, "gs_step host tier");
 }

@@ -150,12 +150,24 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         if (L.restore) {
             const int d = sc.counter[i];
             if (d) {
-                if (sc.rdir) {
+                if (sc.rdir && sc.sh.rdir) {
                     const T *rsh = (const T *)sc.sh.rdir;
 #pragma unroll
                     for (int r = 0; r < D; r++) {
                         const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * sp + sb);
                         w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], d);
+                    }
+                } else if (sc.rdir) {
+                    // host tier: geometry directions kept, SH directions recomputed from the staged m, v
+                    const T *msh = (const T *)sc.sh.m, *vsh = (const T *)sc.sh.v;
+#pragma unroll
+                    for (int r = 0; r < D; r++) {
+                        if (r < N_GEO) {
+                            w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d], d);
+                        } else {
+                            const float mm = ld_val(msh + (r - N_GEO) * sp + sb), vv = ld_val(vsh + (r - N_GEO) * sp + sb);
+                            w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], d, L.eps);
+                        }
                     }
                 } else {
                     const T *mp = (const T *)sc.m, *vp = (const T *)sc.v;

@@ -37,11 +37,14 @@ def _scene(n, deg, seed):
                                     n_clusters=2, cluster_size=2000, sh_degree=deg)
 
 
-def _run(gs, P, deg, prec, tier, steps, n_views=1, stage_chunks=64, shift=10):
+def _run(gs, P, deg, prec, tier, steps, n_views=1, stage_chunks=64, shift=10, ring_eb=None):
     n = P.shape[1]
     cams = _views()
+    if ring_eb is None:      # bf16 scenes stage through a ring of 2-byte rows
+        ring_eb = 4 if prec == gs.GS_FP32 else 2
     ctx = gs.Context(max_gaussians=n, max_visible=n, max_keys=64 * n, max_width=96, max_height=72, tile=(8, 8),
-                     max_views=2, max_sh_degree=deg, stage_chunks=stage_chunks if tier else 0, chunk_shift=shift)
+                     max_views=2, max_sh_degree=deg, stage_chunks=stage_chunks if tier else 0, chunk_shift=shift,
+                     stage_elem_bytes=ring_eb if tier else 0)
     tgt = [torch.full((3, 72, 96), 0.3 + 0.1 * k, device="cuda") for k in range(len(cams))]
     scene = gs.GaussianScene(P, deg, precision=prec, tier=tier)
     adam = gs.adam_struct(lr=[1e-3, 1e-2, 1e-2, 1.0, 10.0, 10.0], eps=1.0, seed=5)
@@ -51,12 +54,15 @@ def _run(gs, P, deg, prec, tier, steps, n_views=1, stage_chunks=64, shift=10):
         ctx.step(scene, [cams[v] for v in vs], [tgt[v] for v in vs], adam)
         if tier:
             staged.append(ctx.host_tier_stats()[0])
-    ctx.sync_status()
+    if tier:     # the stream waits for the write-backs; only the stream is synchronised
+        ctx.wait_copies()
+        torch.cuda.current_stream().synchronize()
+    else:
+        ctx.sync_status()
     m, v = scene.moments()
     out = dict(w=scene.params().cpu().numpy(), m=m.cpu().numpy(), v=v.cpu().numpy(),
                counter=scene.counter[:n].cpu().numpy(), staged=staged)
-    if scene.rdir_sh is not None:
-        out["rdir_sh"] = scene.rdir_sh[:, :n].float().cpu().numpy()
+    ctx.sync_status()
     return out
 
 
@@ -78,9 +84,8 @@ def test_host_tier_matches_resident(gs, prec_name, n_views, ring):
     assert np.mean(a["counter"] != b["counter"]) <= 1e-3
     # storage ulp: 2^-23 (fp32) or 2^-7 (bf16, stochastic rounding may pick the other neighbour)
     ulp = 2.0 ** -23 if prec == gs.GS_FP32 else 2.0 ** -7
-    for k in ("w", "m", "v", "rdir_sh"):
+    for k in ("w", "m", "v"):
         x, y = a[k], b[k]
-        rows = slice(11, None) if k != "rdir_sh" else slice(None)
         scale = np.abs(x).max(axis=1, keepdims=True) + 1e-30
         if k == "w":                                    # geometry stays fp32 in every form
             bound = np.where(np.arange(x.shape[0])[:, None] < 11, 4 * 2.0 ** -23 * np.abs(x),
@@ -100,3 +105,12 @@ def test_host_tier_reports_a_small_ring(gs):
     with pytest.raises(_lib.GsError) as e:       # a view's visible chunks alone exceed the ring
         _run(gs, P, deg, gs.GS_FP32, gs.GS_TIER_HOST_SH, 1, stage_chunks=2)
     assert e.value.status == _lib.GS_ERR_CAPACITY
+
+
+def test_host_tier_refuses_fp32_rows_in_a_bf16_ring(gs):
+    from paper_2509_15645_b300 import _lib
+    n, deg = 40_000, 1
+    P = _scene(n, deg, 33)
+    with pytest.raises(_lib.GsError) as e:
+        _run(gs, P, deg, gs.GS_FP32, gs.GS_TIER_HOST_SH, 1, ring_eb=2)
+    assert e.value.status == _lib.GS_ERR_INVALID_ARG
