@@ -121,13 +121,19 @@ def _int(x):
     return None if x is None or not np.isfinite(x) else round(x)
 
 
-def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False):
+def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False, n_cand=None):
     """Bytes the method must move per launch: the cull, the optimizer's apply
     sweep and its select pass (the minimum traffic of each, every byte read or
     written once)."""
-    # cull: w of the 10 geometry planes for all, their restore directions for
-    # Gaussians with a non-zero counter, counters, bitmask, chunk counts
-    cull = 40.0 * N + 40.0 * n_restore + 1.0 * N + N / 8.0 + 4.0 * N / 2048.0
+    # cull: w of the mean and scale planes (0-5) for all, their restore
+    # directions for Gaussians with a non-zero counter; the rotation planes
+    # (6-9, w and direction) for the n_cand Gaussians that pass the
+    # conservative pre-test; counters, bitmask, chunk counts
+    if n_cand is None:
+        n_cand = N
+    restore_frac = n_restore / max(N, 1)
+    cull = (24.0 * N + 24.0 * n_restore + n_cand * (16.0 + 16.0 * restore_frac)
+            + 1.0 * N + N / 8.0 + 4.0 * N / 2048.0)
     # apply: w, m, v read + w, m, v, restore direction written per parameter of
     # each update-set member, gradients of the visible ones, ids and delays.
     # bf16 forms: the 11 geometry planes keep fp32 w and restore directions
@@ -330,7 +336,7 @@ def run_ours(args):
             n_restore_geo = int((sc.counter[:N] > 0).sum().item())
             one_step(sc, Wm + K + s)
             c = ctx.counters().cpu().tolist()
-            stats.append((c[0], c[1], c[2], n_restore_geo, c[6]))
+            stats.append((c[0], c[1], c[2], n_restore_geo, c[6], c[7]))
         ctx.timing_read(tcap)
         kernels = ctx.step_kernel_count()    # kernel nodes of the captured step graph
         copy_trace = None
@@ -347,13 +353,13 @@ def run_ours(args):
         m = {"sc": sc, "ms": ms_total, "clk": clk, "st": st, "variant": variant, "variant_ms": variant_ms,
              "n_vis": float(np.mean([x[0] for x in stats])), "n_keys": float(np.mean([x[1] for x in stats])),
              "n_upd": float(np.mean([x[2] for x in stats])), "n_rest": float(np.mean([x[3] for x in stats])),
-             "n_fp64": float(np.mean([x[4] for x in stats])),
+             "n_fp64": float(np.mean([x[4] for x in stats])), "n_cand": float(np.mean([x[5] for x in stats])),
              "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
              "kernels": kernels, "copy_trace": copy_trace,
              "staged_chunks": float(np.mean([x[0] for x in staged])) if staged else None,
              "staged_bytes": float(np.mean([x[1] for x in staged])) if staged else None}
         b_cull, b_apply, b_select = algorithmic_bytes(N, D, m["n_vis"], m["n_upd"], m["n_rest"],
-                                                      bf16=precision != gs.GS_FP32)
+                                                      bf16=precision != gs.GS_FP32, n_cand=m["n_cand"])
         m.update(b_cull=b_cull, b_apply=b_apply, b_select=b_select)
         m["cull_adam"] = {
             "cull_gbs": gbs(b_cull, st["cull"]), "adam_apply_gbs": gbs(b_apply, st["adam_apply"]),
@@ -457,6 +463,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (parameters + moments {N * D * 12 / 1e9:.1f} GB in fp32), no flush",
                    "visible_per_view": round(m["n_vis"]), "keys_per_view": round(m["n_keys"]),
                    "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
+                   "cull_pretest_survivors": round(m["n_cand"]),
                    "square_pairs_per_view": _int(m["sq_pairs"]), "contrib_pairs_per_view": _int(m["on_pairs"]),
                    "raster_variant": {"fwd": m["variant"][0], "bwd": m["variant"][1]},
                    "autotune_ms": {k: [None if t is None else round(t, 4) for t in v]

@@ -183,7 +183,9 @@ GS_API gs_status gs_wait_copies(gs_ctx *ctx, void *stream);
 /* Device pointer to the context's 8 int32 counters: [0] visible count of the
  * last gs_cull, [1] key count of the last render, [2] update-set size of the
  * last deferred Adam step, [3] latched status, [6] Gaussians of the last
- * render whose 2D covariance went through the FP64 chain. */
+ * render whose 2D covariance went through the FP64 chain, [7] Gaussians that
+ * passed the cull's conservative pre-test in the last gs_step (the cull reads
+ * their rotation planes; the others leave after the mean and scale planes). */
 GS_API const int32_t *gs_device_counters(const gs_ctx *ctx);
 
 /* ------------------------------------------------------------------ hot path */

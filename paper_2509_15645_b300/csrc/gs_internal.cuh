@@ -59,7 +59,7 @@ struct Counters {
     float loss;       // last loss
     int n_union;      // gs_step: union of the views' visible sets
     int n_fix;        // last render: Gaussians projected through the FP64 chain
-    int pad;
+    int n_cand;       // last gs_step cull: Gaussians that passed the visibility pre-test
 };
 
 __device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status, 0, code); }
@@ -383,25 +383,50 @@ static __device__ __forceinline__ CovGrad cov_chain_bwd_fp64(const Geo10 G, cons
 // projected mean that misses the tiled image (with a pixel of slack for
 // rounding) cannot overlap it.  Same depth test, same Jacobian as
 // project_gaussian.
-__device__ __forceinline__ bool maybe_visible(const float g[10], const DevCam &cam)
+// The camera as the conservative pre-test reads it: six 16-byte vectors in
+// shared memory instead of ~24 scalar loads per Gaussian.
+struct __align__(16) CullCam {
+    float R[9], t[3];
+    float near_z, far_z, limx, limy;
+    float fx, fy, cx, cy;
+    float xmax, ymax, pad0, pad1;   // tiles_x * tile_w + 1, tiles_y * tile_h + 1
+};
+
+__device__ __forceinline__ void make_cull_cam(const DevCam &c, CullCam &cc)
 {
-    const float *R = cam.R;
-    const float px = R[0] * g[0] + R[1] * g[1] + R[2] * g[2] + cam.t[0];
-    const float py = R[3] * g[0] + R[4] * g[1] + R[5] * g[2] + cam.t[1];
-    const float pz = R[6] * g[0] + R[7] * g[1] + R[8] * g[2] + cam.t[2];
-    if (!(pz > cam.near_z && pz < cam.far_z)) return false;
+    for (int k = 0; k < 9; k++) cc.R[k] = c.R[k];
+    for (int k = 0; k < 3; k++) cc.t[k] = c.t[k];
+    cc.near_z = c.near_z; cc.far_z = c.far_z; cc.limx = c.limx; cc.limy = c.limy;
+    cc.fx = c.fx; cc.fy = c.fy; cc.cx = c.cx; cc.cy = c.cy;
+    cc.xmax = (float)(c.tiles_x * c.tile_w) + 1.f;
+    cc.ymax = (float)(c.tiles_y * c.tile_h) + 1.f;
+    cc.pad0 = cc.pad1 = 0.f;
+}
+
+// Conservative visibility pre-test on the mean and the largest scale (planes
+// 0-5 only): false only if the Gaussian's 3-sigma square, under an upper
+// bound of its largest screen-space eigenvalue, misses the tile grid.
+__device__ __forceinline__ bool maybe_visible(const float g[6], const CullCam &cc)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(&cc);
+    const float4 a = q[0], b = q[1], c = q[2];
+    const float px = a.x * g[0] + a.y * g[1] + a.z * g[2] + c.y;
+    const float py = a.w * g[0] + b.x * g[1] + b.y * g[2] + c.z;
+    const float pz = b.z * g[0] + b.w * g[1] + c.x * g[2] + c.w;
+    const float4 d = q[3];
+    if (!(pz > d.x && pz < d.y)) return false;
+    const float4 e = q[4], f = q[5];
     const float iz = __fdividef(1.f, pz);
     const float u = px * iz, w = py * iz;
-    const float tu = fminf(cam.limx, fmaxf(-cam.limx, u));
-    const float tw = fminf(cam.limy, fmaxf(-cam.limy, w));
+    const float tu = fminf(d.z, fmaxf(-d.z, u));
+    const float tw = fminf(d.w, fmaxf(-d.w, w));
     // |T|_F^2 = (fx/z)^2 (1 + tu^2) + (fy/z)^2 (1 + tw^2) for T = J W, W a rotation
-    const float fxz = cam.fx * iz, fyz = cam.fy * iz;
+    const float fxz = e.x * iz, fyz = e.y * iz;
     const float tn = fxz * fxz * (1.f + tu * tu) + fyz * fyz * (1.f + tw * tw);
     const float smax = __expf(fmaxf(g[3], fmaxf(g[4], g[5])));
     const float rb = 3.f * sqrt_fast(1.001f * (tn * smax * smax) + 0.62f) + 2.f;
-    const float mx = cam.fx * u + cam.cx, my = cam.fy * w + cam.cy;
-    const float Wt = (float)(cam.tiles_x * cam.tile_w), Ht = (float)(cam.tiles_y * cam.tile_h);
-    return mx + rb > -1.f && mx - rb < Wt + 1.f && my + rb > -1.f && my - rb < Ht + 1.f;
+    const float mx = e.x * u + e.z, my = e.y * w + e.w;
+    return mx + rb > -1.f && mx - rb < f.x && my + rb > -1.f && my - rb < f.y;
 }
 
 // Conditioning bound above which the 2D covariance is recomputed in FP64.

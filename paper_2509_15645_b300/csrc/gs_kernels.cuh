@@ -89,9 +89,11 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
 // All views of a step in one sweep over the geometry (per-view masks and chunk counts).
 // With umask, the same sweep also takes the deferred optimizer's select
 // (returns true; false if it fell back to per-view sweeps without it).
+// n_cand (optional) receives the number of Gaussians that passed the
+// pre-test in some view (their rotation planes were read).
 bool launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
                        uint32_t *const *chunk_cnts, Work &w, cudaStream_t s, uint32_t *umask = nullptr,
-                       uint32_t *uchunk = nullptr, int max_defer = 0);
+                       uint32_t *uchunk = nullptr, int max_defer = 0, int *n_cand = nullptr);
 void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t *mask, int64_t n, Work &w,
                         cudaStream_t s);
 void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s);

@@ -868,8 +868,9 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
     cudaMemsetAsync(loss, 0, sizeof(float), s);
     const bool selected = select_max_defer >= 0 &&
                           launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s, c->umask, c->uchunk,
-                                            select_max_defer);
-    if (select_max_defer < 0) launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s);
+                                            select_max_defer, &c->cnt->n_cand);
+    if (select_max_defer < 0)
+        launch_cull_views(sv, args, n_views, c->vmask, c->vchunk, c->w, s, nullptr, nullptr, 0, &c->cnt->n_cand);
     for (int v = 0; v < n_views; v++)
         compact_mask(c->vmask[v], sv.n, c->vchunk[v], true, c->vids[v], c->vprefix[v], V, c->nvis_view + v, c->w, s);
     cudaMemcpyAsync(&c->cnt->n_vis, c->nvis_view, sizeof(int), cudaMemcpyDeviceToDevice, s);

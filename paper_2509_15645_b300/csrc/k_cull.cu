@@ -21,12 +21,14 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                                                      uint32_t *__restrict__ chunk_cnt)
 {
     __shared__ DevCam s_cam;
+    __shared__ CullCam s_cc;
     __shared__ float s_plut[3][LUT_N];
     __shared__ float s_eps;
     __shared__ int s_restore;
     __shared__ uint32_t s_cnt[CULL_BLOCK / 32];
     if (threadIdx.x < sizeof(DevCam) / 4)
         ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
+    if (threadIdx.x == 0) make_cull_cam(args->cam[view], s_cc);
     if (threadIdx.x < 3 * LUT_N) s_plut[threadIdx.x / LUT_N][threadIdx.x % LUT_N] = args->lut.param[threadIdx.x / LUT_N][threadIdx.x % LUT_N];
     if (threadIdx.x == 0) {
         s_eps = args->lut.eps;
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
 #pragma unroll
                     for (int r = 0; r < 10; r++) g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], d, s_eps);
                 }
-                if (maybe_visible(g, s_cam)) {
+                if (maybe_visible(g, s_cc)) {
                     Proj P;
                     project_gaussian(g, s_cam, P);
                     keep = P.keep;
@@ -96,11 +98,19 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
 // resident.  Thread 0 issues the bulk copies CSTAGES - 1 tiles ahead; every
 // thread waits on the tile's barrier (bounded: on a timeout the block latches
 // GS_ERR_TIMEOUT and stops after draining what it issued).
-constexpr int CT = 256, CSTAGES = 3, CPLANES = 10;
+// The stages hold the planes every Gaussian needs (mean and log-scale, 0-5)
+// with their restore directions; the rotation planes (6-9) are read directly
+// for the Gaussians that pass the pre-test.  A tile is TT = 512 Gaussians; each
+// of the CT = 256 threads takes two of them (tid and tid + 256), so the tile's
+// fixed costs are shared by twice the work and the two chains interleave.  The
+// kernel is bound by latency, not bandwidth: two stages (one tile landing while
+// the other is consumed) leave room for four blocks (32 warps) per SM, which
+// measured faster than three stages at two or three blocks.
+constexpr int CT = 256, CG = 2, TT = CT * CG, CSTAGES = 2, CPLANES = 10, CPRE = 6;
 struct CullStage {
-    float geo[CPLANES][CT];
-    float dir[CPLANES][CT];
-    uint8_t cnt[CT];      // counters of a full tile (the last, partial tile reads them directly)
+    float geo[CPRE][TT];
+    float dir[CPRE][TT];
+    uint8_t cnt[TT];      // counters of a full tile (the last, partial tile reads them directly)
 };
 constexpr size_t CULL_SMEM = sizeof(CullStage) * CSTAGES;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
@@ -117,9 +127,10 @@ struct CullOut {
     uint32_t *umask;
     uint32_t *uchunk;
     uint8_t *counter_rw;
+    int *n_cand;          // optional: number of Gaussians whose rotation planes were read
 };
 
-__global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
+__global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
                                                    const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
                                                    const DevArgs *__restrict__ args, int view0, int nv,
                                                    const CullOut out, int *status)
@@ -128,6 +139,7 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
     CullStage *st = reinterpret_cast<CullStage *>(smem);
     __shared__ __align__(8) uint64_t bar[CSTAGES];
     __shared__ DevCam s_cam[MAX_VIEWS];
+    __shared__ CullCam s_cc[MAX_VIEWS];
     __shared__ float s_plut[3][LUT_N];
     __shared__ uint32_t s_cnt[MAX_VIEWS][CT / 32];
     __shared__ int s_abort;
@@ -136,19 +148,22 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         const int v = e / (int)(sizeof(DevCam) / 4), o = e % (int)(sizeof(DevCam) / 4);
         ((uint32_t *)&s_cam[v])[o] = ((const uint32_t *)&args->cam[view0 + v])[o];
     }
+    if (tid < nv) make_cull_cam(args->cam[view0 + tid], s_cc[tid]);
     if (tid < MAX_VIEWS * (CT / 32)) s_cnt[tid / (CT / 32)][tid % (CT / 32)] = 0;
     if (tid < 3 * LUT_N) s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
     const bool restore = args->lut.restore && rdir != nullptr && counter != nullptr;
     const bool select = out.umask != nullptr;
     const bool need_cnt = restore || select;
+    const int max_defer = args->lut.max_defer;
     if (tid == 0) {
         s_abort = 0;
         for (int k = 0; k < CSTAGES; k++) mbar_init(&bar[k], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    constexpr int PER_CHUNK = CHUNK / CT;
-    const int64_t ntiles = (n + CT - 1) / CT, nchunks = (n + CHUNK - 1) / CHUNK;
+    constexpr int PER_CHUNK = CHUNK / TT;
+    static_assert(CHUNK % TT == 0, "a chunk is a whole number of tiles");
+    const int64_t ntiles = (n + TT - 1) / TT, nchunks = (n + CHUNK - 1) / CHUNK;
     // q-th tile of this block (chunks blockIdx.x, + gridDim.x, ...), or -1
     auto tile_of = [&](int64_t q) -> int64_t {
         const int64_t c = blockIdx.x + (q / PER_CHUNK) * gridDim.x;
@@ -160,20 +175,21 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         const int64_t t = tile_of(q);
         if (t < 0) return;
         const int s = (int)(q % CSTAGES);
-        const int64_t i0 = t * CT;
-        const int64_t rows = min((int64_t)CT, n - i0);
+        const int64_t i0 = t * TT;
+        const int64_t rows = min((int64_t)TT, n - i0);
         const uint32_t bytes = (uint32_t)(((rows + 3) & ~3ll) * 4);   // within the plane: pitch >= n, a multiple of 4
-        const bool cnt_bulk = need_cnt && rows == CT;
-        mbar_expect_tx(&bar[s], bytes * CPLANES * (restore ? 2u : 1u) + (cnt_bulk ? (uint32_t)CT : 0u));
-        for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].geo[r], geo + r * pitch + i0, bytes, &bar[s]);
+        const bool cnt_bulk = need_cnt && rows == TT;
+        mbar_expect_tx(&bar[s], bytes * CPRE * (restore ? 2u : 1u) + (cnt_bulk ? (uint32_t)TT : 0u));
+        for (int r = 0; r < CPRE; r++) bulk_g2s(st[s].geo[r], geo + r * pitch + i0, bytes, &bar[s]);
         if (restore)
-            for (int r = 0; r < CPLANES; r++) bulk_g2s(st[s].dir[r], rdir + r * pitch + i0, bytes, &bar[s]);
-        if (cnt_bulk) bulk_g2s(st[s].cnt, counter + i0, CT, &bar[s]);
+            for (int r = 0; r < CPRE; r++) bulk_g2s(st[s].dir[r], rdir + r * pitch + i0, bytes, &bar[s]);
+        if (cnt_bulk) bulk_g2s(st[s].cnt, counter + i0, TT, &bar[s]);
     };
     if (tid == 0)
         for (int q = 0; q < CSTAGES - 1; q++) issue(q);
     int64_t issued_to = CSTAGES - 1;               // tiles [0, issued_to) issued (thread 0's view)
     int64_t q_stop = 0;                            // first tile not consumed when the loop ends
+    uint32_t n_full = 0;                           // Gaussians of this thread whose rotation planes were read
     for (int64_t q = 0;; q++) {
         q_stop = q;
         const int64_t c = blockIdx.x + (q / PER_CHUNK) * gridDim.x;
@@ -186,39 +202,80 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
         if (t >= 0) {
             const int s = (int)(q % CSTAGES);
             if (!mbar_wait_bounded(&bar[s], (uint32_t)((q / CSTAGES) & 1), WAIT_LIMIT)) s_abort = 1;
-            const int64_t i = t * CT + tid;
-            const bool live = i < n && !s_abort;
-            float g[CPLANES];
+            const bool full_tile = t * TT + TT <= n;
+            // planes 0-5 (mean, log-scale) of both Gaussians from the stage: the
+            // pre-test needs only those; the rotation planes are read for its survivors
+            float g[CG][CPLANES];
+            int d[CG];
+            bool live[CG], full[CG], any_view[CG];
 #pragma unroll
-            for (int r = 0; r < CPLANES; r++) g[r] = live ? st[s].geo[r][tid] : 0.f;
-            const int d = (need_cnt && live) ? ((t * CT + CT <= n) ? st[s].cnt[tid] : counter[i]) : 0;
-            if (restore && live) {
+            for (int e = 0; e < CG; e++) {
+                const int k = tid + e * CT;
+                const int64_t i = t * TT + k;
+                live[e] = i < n && !s_abort;
+                full[e] = false;
+                any_view[e] = false;
 #pragma unroll
-                for (int r = 0; r < CPLANES; r++) g[r] = restore_with_dir(g[r], st[s].dir[r][tid], s_plut[lr_group(r)][d], d);
+                for (int r = 0; r < CPRE; r++) g[e][r] = live[e] ? st[s].geo[r][k] : 0.f;
+                d[e] = (need_cnt && live[e]) ? (full_tile ? st[s].cnt[k] : counter[i]) : 0;
             }
-            const int64_t wbase = t * CT + wid * 32;
-            bool any_view = false;
-            for (int v = 0; v < nv; v++) {
-                int keep = 0;
-                if (live && maybe_visible(g, s_cam[v])) {   // most Gaussians leave here
-                    Proj P;
-                    project_gaussian(g, s_cam[v], P);
-                    keep = P.keep;
+            if (restore) {
+#pragma unroll
+                for (int e = 0; e < CG; e++) {
+                    const int k = tid + e * CT;
+#pragma unroll
+                    for (int r = 0; r < CPRE; r++)
+                        if (live[e]) g[e][r] = restore_with_dir(g[e][r], st[s].dir[r][k], s_plut[lr_group(r)][d[e]], d[e]);
                 }
-                any_view |= keep != 0;
-                const uint32_t word = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0 && wbase < n) {
-                    out.mask[v][wbase >> 5] = word;
-                    s_cnt[v][wid] += __popc(word);
+            }
+            for (int v = 0; v < nv; v++) {
+                bool mv[CG];
+#pragma unroll
+                for (int e = 0; e < CG; e++) mv[e] = live[e] && maybe_visible(g[e], s_cc[v]);   // most leave here
+#pragma unroll
+                for (int e = 0; e < CG; e++) {
+                    int keep = 0;
+                    const int64_t i = t * TT + tid + e * CT;
+                    if (mv[e]) {
+                        if (!full[e]) {
+#pragma unroll
+                            for (int r = CPRE; r < CPLANES; r++) g[e][r] = __ldg(geo + r * pitch + i);
+                            if (restore && d[e]) {
+                                float dd[CPLANES - CPRE];
+#pragma unroll
+                                for (int r = CPRE; r < CPLANES; r++) dd[r - CPRE] = __ldg(rdir + r * pitch + i);
+#pragma unroll
+                                for (int r = CPRE; r < CPLANES; r++)
+                                    g[e][r] = restore_with_dir(g[e][r], dd[r - CPRE], s_plut[lr_group(r)][d[e]], d[e]);
+                            }
+                            full[e] = true;
+                            n_full++;
+                        }
+                        Proj P;
+                        project_gaussian(g[e], s_cam[v], P);
+                        keep = P.keep;
+                    }
+                    any_view[e] |= keep != 0;
+                    const uint32_t word = __ballot_sync(0xffffffffu, keep);
+                    const int64_t wbase = t * TT + e * CT + wid * 32;
+                    if (lane == 0 && wbase < n) {
+                        out.mask[v][wbase >> 5] = word;
+                        s_cnt[v][wid] += __popc(word);
+                    }
                 }
             }
             if (select) {
-                const bool in_u = live && (any_view || d >= args->lut.max_defer);
-                if (live && !in_u) out.counter_rw[i] = (uint8_t)(d + 1);
-                const uint32_t uword = __ballot_sync(0xffffffffu, in_u);
-                if (lane == 0 && wbase < n) {
-                    out.umask[wbase >> 5] = uword;
-                    if (uword) atomicAdd(&out.uchunk[t / PER_CHUNK], (uint32_t)__popc(uword));
+#pragma unroll
+                for (int e = 0; e < CG; e++) {
+                    const int64_t i = t * TT + tid + e * CT;
+                    const bool in_u = live[e] && (any_view[e] || d[e] >= max_defer);
+                    if (live[e] && !in_u) out.counter_rw[i] = (uint8_t)(d[e] + 1);
+                    const uint32_t uword = __ballot_sync(0xffffffffu, in_u);
+                    const int64_t wbase = t * TT + e * CT + wid * 32;
+                    if (lane == 0 && wbase < n) {
+                        out.umask[wbase >> 5] = uword;
+                        if (uword) atomicAdd(&out.uchunk[t / PER_CHUNK], (uint32_t)__popc(uword));
+                    }
                 }
             }
         }
@@ -235,6 +292,11 @@ __global__ void __launch_bounds__(CT, 3) k_cull_tma(const float *__restrict__ ge
             }
             __syncthreads();                       // counts cleared before the next tile adds to them
         }
+    }
+    if (out.n_cand) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
+        if (lane == 0 && n_full) atomicAdd(out.n_cand, (int)n_full);
     }
     if (s_abort && tid == 0) {
         latch(status, GS_ERR_TIMEOUT);
@@ -263,7 +325,8 @@ static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0,
     }
     const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics
-    const int gt = w.grid(nchunks * CT, CT, 3);
+    if (out.n_cand) cudaMemsetAsync(out.n_cand, 0, sizeof(int), s);
+    const int gt = w.grid(nchunks * CT, CT, 4);
     k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status);
 }
 
@@ -291,7 +354,7 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
 
 bool launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, uint32_t *const *masks,
                        uint32_t *const *chunk_cnts, Work &w, cudaStream_t s, uint32_t *umask, uint32_t *uchunk,
-                       int max_defer)
+                       int max_defer, int *n_cand)
 {
     if (!cull_tma_ok(sc)) {
         for (int v = 0; v < n_views; v++) launch_cull(sc, args, v, masks[v], chunk_cnts[v], w, s);
@@ -303,6 +366,7 @@ bool launch_cull_views(const SceneView &sc, const DevArgs *args, int n_views, ui
         out.mask[v] = masks[v];
         out.chunk[v] = chunk_cnts[v];
     }
+    out.n_cand = n_cand;
     if (umask && sc.counter) {
         out.umask = umask;
         out.uchunk = uchunk;

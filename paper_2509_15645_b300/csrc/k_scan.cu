@@ -124,38 +124,95 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *
 }
 
 // ---------------------------------------------------------------------------
-// Ordered compaction of a bitmask (bit i of word i/32).  chunk_ofs holds the
-// exclusive scan of per-chunk popcounts.  Writes ids (ascending, only those
-// below cap) and word_prefix[w] = number of set bits before word w.
-__global__ void k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords, const uint32_t *__restrict__ chunk_ofs,
-                               int32_t *ids, uint32_t *word_prefix, int cap, uint8_t *counter, uint8_t *delay)
+// Exclusive scan of up to SMALL_SCAN_MAX chunk counts in place, by one block
+// (one launch instead of the three of scan_exclusive): each thread scans a
+// contiguous segment, the block scans the segment sums.  Writes the total to
+// total_out (clamped to total_cap, GS_ERR_CAPACITY latched above it).
+constexpr int SMALL_SCAN_THREADS = 1024;
+constexpr int64_t SMALL_SCAN_MAX = 64 * SMALL_SCAN_THREADS;
+
+__global__ void __launch_bounds__(SMALL_SCAN_THREADS) k_scan_small(uint32_t *v, int len, int *total_out,
+                                                                   int total_cap, int *status)
+{
+    __shared__ uint32_t s_warp[33];
+    const int seg = (len + SMALL_SCAN_THREADS - 1) / SMALL_SCAN_THREADS;
+    const int lo = threadIdx.x * seg, hi = min(len, lo + seg);
+    uint32_t sum = 0;
+    for (int k = lo; k < hi; k++) sum += v[k];
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(sum, &tot, s_warp);
+    for (int k = lo; k < hi; k++) {
+        const uint32_t x = v[k];
+        v[k] = ex;
+        ex += x;
+    }
+    if (threadIdx.x == 0 && total_out) {
+        int t = (int)tot;
+        if (total_cap > 0 && t > total_cap) {
+            if (status) latch(status, GS_ERR_CAPACITY);
+            t = total_cap;
+        }
+        *total_out = t;
+    }
+}
+
+// Ordered compaction of a bitmask (bit i of word i/32), one 256-thread block
+// per chunk of CHUNK_WORDS words at a time; warp k takes words k, k + 8, ...
+// and a lane the bit of its index.  chunk_ofs holds the exclusive scan of
+// per-chunk popcounts.  Writes ids (ascending, only those below cap) and
+// word_prefix[w] = number of set bits before word w.  A warp issues all its
+// mask words and (for the optimizer's update set) all its members' counter
+// reads before the first store, so a chunk costs one memory latency.
+constexpr int COMPACT_BLOCK = 256, COMPACT_WPW = CHUNK_WORDS / (COMPACT_BLOCK / 32);
+
+__global__ void __launch_bounds__(COMPACT_BLOCK) k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords,
+                                                                const uint32_t *__restrict__ chunk_ofs, int32_t *ids,
+                                                                uint32_t *word_prefix, int cap, uint8_t *counter,
+                                                                uint8_t *delay)
 {
     __shared__ uint32_t s_pref[CHUNK_WORDS];
     __shared__ uint32_t s_warp[33];
-    int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        int64_t w0 = c * CHUNK_WORDS;
+        const int64_t w0 = c * CHUNK_WORDS;
+        uint32_t mw[COMPACT_WPW];
+#pragma unroll
+        for (int k = 0; k < COMPACT_WPW; k++) {
+            const int64_t wd = w0 + wid + k * (COMPACT_BLOCK / 32);
+            mw[k] = wd < nwords ? __ldg(mask + wd) : 0u;
+        }
+        uint8_t cv[COMPACT_WPW];
+        if (counter) {
+#pragma unroll
+            for (int k = 0; k < COMPACT_WPW; k++) {
+                const int64_t id = (w0 + wid + k * (COMPACT_BLOCK / 32)) * 32 + lane;
+                cv[k] = ((mw[k] >> lane) & 1u) ? counter[id] : (uint8_t)0;
+            }
+        }
         uint32_t word = 0;
-        if (threadIdx.x < CHUNK_WORDS && w0 + threadIdx.x < nwords) word = mask[w0 + threadIdx.x];
-        uint32_t cnt = threadIdx.x < CHUNK_WORDS ? __popc(word) : 0u;
-        uint32_t ex = block_excl_scan(cnt, nullptr, s_warp);
-        uint32_t base = chunk_ofs[c];
+        if (threadIdx.x < CHUNK_WORDS && w0 + threadIdx.x < nwords) word = __ldg(mask + w0 + threadIdx.x);
+        const uint32_t cnt = threadIdx.x < CHUNK_WORDS ? __popc(word) : 0u;
+        const uint32_t ex = block_excl_scan(cnt, nullptr, s_warp);
+        const uint32_t base = __ldg(chunk_ofs + c);
         if (threadIdx.x < CHUNK_WORDS) {
             s_pref[threadIdx.x] = base + ex;
             if (w0 + threadIdx.x < nwords && word_prefix) word_prefix[w0 + threadIdx.x] = base + ex;
         }
         __syncthreads();
-        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int j = wid; j < CHUNK_WORDS; j += nw) {
-            if (w0 + j >= nwords) break;
-            uint32_t m = mask[w0 + j];
+#pragma unroll
+        for (int k = 0; k < COMPACT_WPW; k++) {
+            const int j = wid + k * (COMPACT_BLOCK / 32);
+            const uint32_t m = mw[k];
             if ((m >> lane) & 1u) {
-                uint32_t pos = s_pref[j] + __popc(m & ((1u << lane) - 1u));
+                const uint32_t pos = s_pref[j] + __popc(m & ((1u << lane) - 1u));
                 const int64_t id = (w0 + j) * 32 + lane;
-                if (ids && (int)pos < cap) ids[pos] = (int32_t)id;
-                if (counter && (int)pos < cap) {       // optimizer update set: record the delay, clear the counter
-                    delay[pos] = counter[id];
-                    counter[id] = 0;
+                if ((int)pos < cap) {
+                    if (ids) ids[pos] = (int32_t)id;
+                    if (counter) {           // optimizer update set: record the delay, clear the counter
+                        delay[pos] = cv[k];
+                        counter[id] = 0;
+                    }
                 }
             }
         }
@@ -188,10 +245,14 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
     int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
     if (!have_counts)
         k_chunk_counts<<<w.grid(nchunks * 32, 256), 256, 0, s>>>(mask, nwords, chunk_cnt);
-    ScanLen L{nullptr, 1, 1, 0, (int)nchunks, 0};
-    scan_exclusive(chunk_cnt, chunk_cnt, L, w, count_out, cap, s);
-    k_compact_mask<<<w.grid(nchunks * 256, 256), 256, 0, s>>>(mask, nwords, chunk_cnt, ids, word_prefix, cap, counter,
-                                                              delay);
+    if (nchunks <= SMALL_SCAN_MAX) {
+        k_scan_small<<<1, SMALL_SCAN_THREADS, 0, s>>>(chunk_cnt, (int)nchunks, count_out, cap, w.status);
+    } else {
+        ScanLen L{nullptr, 1, 1, 0, (int)nchunks, 0};
+        scan_exclusive(chunk_cnt, chunk_cnt, L, w, count_out, cap, s);
+    }
+    k_compact_mask<<<w.grid(nchunks * COMPACT_BLOCK, COMPACT_BLOCK), COMPACT_BLOCK, 0, s>>>(
+        mask, nwords, chunk_cnt, ids, word_prefix, cap, counter, delay);
 }
 
 // ---------------------------------------------------------------------------
