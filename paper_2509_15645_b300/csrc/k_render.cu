@@ -756,8 +756,8 @@ bool raster_variant_ok(int v, int tile_w, int tile_h)
 // FIX = false: every visible Gaussian except those the gather flagged for the
 // FP64 chain; FIX = true: the flagged ones, with the adjoint of the 2D
 // covariance in FP64.
-template <bool FIX>
-__global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restrict__ compact, int cap, int deg,
+template <bool FIX, int DEG>
+__global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restrict__ compact, int cap,
                                                             const int *n_vis_p, const DevArgs *__restrict__ args, int view,
                                                             const float *__restrict__ g9, float *__restrict__ grad,
                                                             int64_t gcap, const int32_t *__restrict__ ids,
@@ -772,8 +772,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
     __syncthreads();
     const int n_vis = min(*n_vis_p, cap);
-    const int nk = (deg + 1) * (deg + 1);
-    const int D = N_GEO + 3 * nk;
+    constexpr int deg = DEG, nk = (DEG + 1) * (DEG + 1);   // compile-time: Y and h stay in registers
     const DevCam &cam = s_cam;
     const int n_items = FIX ? min(*n_fix, n_vis) : n_vis;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_items; j += gridDim.x * blockDim.x) {
@@ -814,6 +813,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         float Y[16];
         sh_basis(deg, dir[0], dir[1], dir[2], Y);
         float raw[3] = {0.f, 0.f, 0.f};
+#pragma unroll
         for (int q = 0; q < nk; q++)
 #pragma unroll
             for (int c = 0; c < 3; c++) raw[c] += Y[q] * compact[(N_GEO + 3 * q + c) * (int64_t)cap + k];
@@ -821,6 +821,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
 #pragma unroll
         for (int c = 0; c < 3; c++) grgb[c] = (ok && raw[c] + 0.5f >= 0.f) ? gs[6 + c] : 0.f;
         float h[16];
+#pragma unroll
         for (int q = 0; q < nk; q++) {
             float acc = 0.f;
 #pragma unroll
@@ -957,7 +958,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
             float *dst = grad + r * gcap + kk;
             if (accumulate) *dst += out[r]; else *dst = out[r];
         }
-        (void)D;
     }
 }
 
@@ -1134,17 +1134,31 @@ void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, c
     w.mark(TP_RBWD1, s);
 }
 
+typedef void (*ProjBwdFn)(const float *, int, const int *, const DevArgs *, int, const float *, float *, int64_t,
+                          const int32_t *, const uint32_t *, const uint32_t *, int, int *, const int *, const int32_t *,
+                          const uint8_t *);
+
+template <bool FIX> static ProjBwdFn pbwd_for(int deg)
+{
+    switch (deg) {
+    case 0: return k_project_bwd<FIX, 0>;
+    case 1: return k_project_bwd<FIX, 1>;
+    case 2: return k_project_bwd<FIX, 2>;
+    default: return k_project_bwd<FIX, 3>;
+    }
+}
+
 void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                       float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
                       const int32_t *ids, bool accumulate, Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
-    k_project_bwd<false><<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
-        rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix,
-        accumulate ? 1 : 0, w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
-    k_project_bwd<true><<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, sc.deg, n_vis, args, view, rb.g9, grad, gcap,
-                                                          ids, remap_mask, remap_prefix, accumulate ? 1 : 0, w.status,
-                                                          rb.n_fix, rb.fix_idx, rb.fix_flag);
+    pbwd_for<false>(sc.deg)<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
+        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, accumulate ? 1 : 0,
+        w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
+    pbwd_for<true>(sc.deg)<<<w.num_sms, PROJ_BLOCK, 0, s>>>(
+        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, accumulate ? 1 : 0,
+        w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
 }
 
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
