@@ -585,7 +585,7 @@ def main():
                     help="time only the bf16 precision form (profiling); the JSON line then describes it")
     ap.add_argument("--density-of", type=int, default=None,
                     help="scale the scene area so that --gaussians keeps the density of this many (profiling cases)")
-    ap.add_argument("--tile", default="8x8", help="raster tile WxH (W in 4..64, W*H in 64, 128, 256)")
+    ap.add_argument("--tile", default="8x4", help="raster tile WxH (W in 4..64, W*H in 32, 64, 128, 256)")
     ap.add_argument("--image", default="1920x1080", help="view size WxH")
     ap.add_argument("--views-per-step", type=int, default=1, help="views rendered and summed per training step")
     ap.add_argument("--budget-gb", type=float, default=None,

@@ -268,12 +268,14 @@ enum { GS_SPAN_STEP = 0, GS_SPAN_CULL = 1, GS_SPAN_FWD = 2, GS_SPAN_BWD = 3, GS_
 GS_API gs_status gs_timing_enable(gs_ctx *ctx, int32_t max_steps);
 GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, int32_t *steps_out);
 
-/* Rasterizer variants: pixels per thread 1 << (v >> 1) and a shared-memory
- * splat batch of (v & 1 ? 256 : 128) records.  Every variant computes the same
- * image bit for bit; they differ only in speed.  A tile shape allows a variant
- * when tile_h is a multiple of its pixels per thread and the block has 32 to
- * 256 threads. */
-#define GS_RASTER_VARIANTS 6
+/* Rasterizer variants.  v < 6: one tile per block, pixels per thread
+ * 1 << (v >> 1) and a shared-memory splat batch of (v & 1 ? 256 : 128)
+ * records; a tile shape allows them when tile_h is a multiple of the pixels
+ * per thread and the block has 32 to 256 threads.  v = 6, 7 (32-pixel tiles
+ * only): one tile per warp, 4 warps per block with batches of 64 records, or
+ * 8 warps with batches of 32.  Every variant computes the same image bit for
+ * bit; they differ only in speed. */
+#define GS_RASTER_VARIANTS 8
 
 /* Autotuner: time every variant the context's tile shape allows on this scene
  * and view (render forward and backward separately; CUDA events, best of

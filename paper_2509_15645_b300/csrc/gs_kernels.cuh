@@ -172,7 +172,7 @@ struct RasterJob {
     int *work;
 };
 
-constexpr int N_RASTER_VARIANTS = 6;
+constexpr int N_RASTER_VARIANTS = 8;
 bool raster_variant_ok(int v, int tile_w, int tile_h);
 
 void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,

@@ -408,29 +408,41 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
 
 // Stage the tile's list entries [b, b + cnt) into shared memory (the lists
 // hold only splats that can reach the tile: k_tile_counts / k_emit).
-template <bool COLOR, bool INDEX>
+// WT: the staging belongs to one warp (warp-tile rasterizers), else to the block.
+template <bool COLOR, bool INDEX, bool WT = false>
 __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
                                            const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
                                            uint32_t b, int cnt, float4 *s0, float4 *s1, float4 *s2, uint32_t *s_k)
 {
-    for (int e = (int)threadIdx.x; e < cnt; e += blockDim.x) {
+    const int t0 = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x, nt = WT ? 32 : (int)blockDim.x;
+    for (int e = t0; e < cnt; e += nt) {
         const uint32_t k = svals[b + e];
         s0[e] = rec0[k];
         s1[e] = rec1[k];
         if (COLOR) s2[e] = rec2[k];
         if (INDEX) s_k[e] = k;
     }
-    __syncthreads();
+    if (WT) __syncwarp();
+    else __syncthreads();
     return cnt;
 }
 
 // Next (view, tile) item of a persistent rasterizer block, or false when done.
+// WT: each warp takes its own items (warp-tile rasterizers).
+template <bool WT = false>
 __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &view, int &tile)
 {
-    __syncthreads();                                   // the previous item's shared data is no longer read
-    if (threadIdx.x == 0) *s_item = atomicAdd(J.work, 1);
-    __syncthreads();
-    const int item = *s_item;
+    int item;
+    if (WT) {
+        __syncwarp();                                  // the previous item's staged records are no longer read
+        if ((threadIdx.x & 31) == 0) item = atomicAdd(J.work, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+    } else {
+        __syncthreads();                               // the previous item's shared data is no longer read
+        if (threadIdx.x == 0) *s_item = atomicAdd(J.work, 1);
+        __syncthreads();
+        item = *s_item;
+    }
     if (item >= J.tile_ofs[J.n_views]) return false;
     view = 0;
     while (item >= J.tile_ofs[view + 1]) view++;
@@ -438,15 +450,27 @@ __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &
     return true;
 }
 
-template <int PPT, int BATCH>
-__global__ void __launch_bounds__(256) k_raster_fwd(const RasterJob J, const DevArgs *__restrict__ args,
+// NW > 0: warp tiles -- a tile is exactly 32 threads (tile pixels / PPT = 32)
+// and each of the block's NW warps takes its own tiles and staging slot, with
+// warp-level synchronisation only (one-warp tiles would otherwise be one-warp
+// blocks, of which an SM holds at most 32).  Their register budget is set for
+// five blocks per SM (measured faster; the backward kept its own budget, as a
+// cap there spills).
+template <int PPT, int BATCH, int NW = 0>
+__global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob J, const DevArgs *__restrict__ args,
                                                     int use_target, float *__restrict__ loss)
 {
-    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
+    constexpr bool WT = NW > 0;
+    constexpr int NS = WT ? NW : 1;
+    __shared__ float4 s0_[NS][BATCH], s1_[NS][BATCH], s2_[NS][BATCH];
     __shared__ float s_red[8];
     __shared__ int s_item;
+    const int slot = WT ? (int)(threadIdx.x >> 5) : 0;
+    const int tl = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;   // thread within the tile
+    float4 *s0 = s0_[slot], *s1 = s1_[slot], *s2 = s2_[slot];
+    float loss_part = 0.f;
     int view, tile;
-    while (next_item(J, &s_item, view, tile)) {
+    while (next_item<WT>(J, &s_item, view, tile)) {
     const uint2 *__restrict__ ranges = J.ranges[view];
     const uint32_t *__restrict__ svals = J.svals[view];
     const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
@@ -455,13 +479,13 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const RasterJob J, const Dev
     const float *target = use_target ? args->target[view] : nullptr;
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
-    const int x = tx0 + (int)threadIdx.x % tw;
-    const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
+    const int x = tx0 + tl % tw;
+    const int y0 = ty0 + (tl / tw) * PPT;
     const float px = (float)x + 0.5f;
     // pixel rows covered by this warp (uniform): its first thread's row set plus
     // the further thread rows its 32 lanes span
     const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
-    const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
+    const float wy0 = (float)(ty0 + (((tl >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
     const uint2 rg = ranges[tile];
     float T[PPT], C0[PPT], C1[PPT], C2[PPT];
@@ -473,9 +497,14 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const RasterJob J, const Dev
         if (x < W && y0 + j < H) live |= 1u << j;
     }
     for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
-        if (__syncthreads_count(live != 0) == 0) break;
-        const int nb = stage_batch<true, false>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1, s2,
-                                                nullptr);
+        if (WT) {
+            if (!__any_sync(0xffffffffu, live != 0)) break;
+            __syncwarp();                            // the previous batch is no longer read
+        } else if (__syncthreads_count(live != 0) == 0) {
+            break;
+        }
+        const int nb = stage_batch<true, false, WT>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1,
+                                                    s2, nullptr);
         for (int e = 0; e < nb && live; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
@@ -528,11 +557,19 @@ __global__ void __launch_bounds__(256) k_raster_fwd(const RasterJob J, const Dev
             }
         }
     }
-    if (target) {
-        __syncthreads();
-        float t = block_sum(part, s_red);
-        if (threadIdx.x == 0) atomicAdd(loss, t);
+    loss_part += part;
     }
+    // the loss: one sum per warp (warp tiles) or per block, after the last item
+    if (use_target) {
+        if (WT) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
+            if ((threadIdx.x & 31) == 0 && loss_part != 0.f) atomicAdd(loss, loss_part);
+        } else {
+            __syncthreads();
+            const float t = block_sum(loss_part, s_red);
+            if (threadIdx.x == 0 && t != 0.f) atomicAdd(loss, t);
+        }
     }
 }
 
@@ -573,16 +610,22 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
 // contributions to each splat and issues the atomic adds into g9.
 // STATS: also count the (pixel, splat) pairs that pass the square test and the
 // pairs that contribute (stats[0], stats[1]).
-template <int PPT, int BATCH, bool STATS = false>
+template <int PPT, int BATCH, bool STATS = false, int NW = 0>
 __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const DevArgs *__restrict__ args,
                                                     unsigned long long *stats = nullptr)
 {
+    constexpr bool WT = NW > 0;
+    constexpr int NS = WT ? NW : 1;
     unsigned long long n_sq = 0, n_on = 0;
-    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
-    __shared__ uint32_t s_k[BATCH];
+    __shared__ float4 s0_[NS][BATCH], s1_[NS][BATCH], s2_[NS][BATCH];
+    __shared__ uint32_t s_k_[NS][BATCH];
     __shared__ int s_item;
+    const int slot = WT ? (int)(threadIdx.x >> 5) : 0;
+    const int tl = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;   // thread within the tile
+    float4 *s0 = s0_[slot], *s1 = s1_[slot], *s2 = s2_[slot];
+    uint32_t *s_k = s_k_[slot];
     int view, tile;
-    while (next_item(J, &s_item, view, tile)) {
+    while (next_item<WT>(J, &s_item, view, tile)) {
     const uint2 *__restrict__ ranges = J.ranges[view];
     const uint32_t *__restrict__ svals = J.svals[view];
     const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
@@ -591,13 +634,13 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
     const DevCam &cam = args->cam[view];
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
-    const int x = tx0 + (int)threadIdx.x % tw;
-    const int y0 = ty0 + ((int)threadIdx.x / tw) * PPT;
+    const int x = tx0 + tl % tw;
+    const int y0 = ty0 + (tl / tw) * PPT;
     const float px = (float)x + 0.5f;
     // pixel rows covered by this warp (uniform): its first thread's row set plus
     // the further thread rows its 32 lanes span
     const int rows_per_warp = (tw >= 32 ? 1 : 32 / tw) * PPT;
-    const float wy0 = (float)(ty0 + ((((int)threadIdx.x >> 5) << 5) / tw) * PPT) + 0.5f;
+    const float wy0 = (float)(ty0 + (((tl >> 5) << 5) / tw) * PPT) + 0.5f;
     const float wy1 = wy0 + (float)(rows_per_warp - 1);
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
@@ -620,9 +663,14 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
         }
     }
     for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
-        if (__syncthreads_count(live != 0) == 0) break;
-        const int nb = stage_batch<true, true>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1, s2,
-                                               s_k);
+        if (WT) {
+            if (!__any_sync(0xffffffffu, live != 0)) break;
+            __syncwarp();                            // the previous batch is no longer read
+        } else if (__syncthreads_count(live != 0) == 0) {
+            break;
+        }
+        const int nb = stage_batch<true, true, WT>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1,
+                                                   s2, s_k);
         for (int e = 0; e < nb; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
@@ -712,7 +760,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
 typedef void (*RasterFwdFn)(const RasterJob, const DevArgs *, int, float *);
 typedef void (*RasterBwdFn)(const RasterJob, const DevArgs *, unsigned long long *);
 
-// Variant v: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128.
+// Variant v < 6: PPT = 1 << (v >> 1), BATCH = (v & 1) ? 256 : 128, one tile
+// per block.  v = 6, 7: warp tiles (32-pixel tiles, PPT 1), 4 warps with
+// batches of 64 or 8 warps with batches of 32 per block.
 static RasterFwdFn fwd_variant(int v)
 {
     switch (v) {
@@ -721,7 +771,9 @@ static RasterFwdFn fwd_variant(int v)
     case 2: return k_raster_fwd<2, 128>;
     case 3: return k_raster_fwd<2, 256>;
     case 4: return k_raster_fwd<4, 128>;
-    default: return k_raster_fwd<4, 256>;
+    case 5: return k_raster_fwd<4, 256>;
+    case 6: return k_raster_fwd<1, 64, 4>;
+    default: return k_raster_fwd<1, 32, 8>;
     }
 }
 
@@ -739,13 +791,21 @@ static RasterBwdFn bwd_variant(int v, bool stats)
     case 8: return k_raster_bwd<4, 128, false>;
     case 9: return k_raster_bwd<4, 128, true>;
     case 10: return k_raster_bwd<4, 256, false>;
-    default: return k_raster_bwd<4, 256, true>;
+    case 11: return k_raster_bwd<4, 256, true>;
+    case 12: return k_raster_bwd<1, 64, false, 4>;
+    case 13: return k_raster_bwd<1, 64, true, 4>;
+    case 14: return k_raster_bwd<1, 32, false, 8>;
+    default: return k_raster_bwd<1, 32, true, 8>;
     }
 }
+
+// Warps per block of a warp-tile variant, else 0.
+static int warp_tile_warps(int v) { return v == 6 ? 4 : v == 7 ? 8 : 0; }
 
 bool raster_variant_ok(int v, int tile_w, int tile_h)
 {
     if (v < 0 || v >= N_RASTER_VARIANTS) return false;
+    if (warp_tile_warps(v)) return tile_w * tile_h == 32;
     const int ppt = 1 << (v >> 1);
     const int threads = tile_w * tile_h / ppt;
     return tile_h % ppt == 0 && threads >= 32 && threads <= 256 && threads % 32 == 0;
@@ -1069,8 +1129,18 @@ static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
     return J;
 }
 
-// Persistent blocks: enough to fill the GPU, never more than the items.
-static int persistent_grid(int items, const Work &w) { return std::max(1, std::min(items, w.num_sms * 32)); }
+// Launch shape of variant v: persistent blocks, enough to fill the GPU and
+// never more than the items (warp tiles: an item per warp).
+struct RasterShape {
+    int grid, block;
+};
+static RasterShape raster_shape(int v, int items, int tile_w, int tile_h, const Work &w)
+{
+    const int nw = warp_tile_warps(v);
+    if (nw) return {std::max(1, std::min((items + nw - 1) / nw, w.num_sms * 64 / nw)), 32 * nw};
+    const int ppt = 1 << (v >> 1);
+    return {std::max(1, std::min(items, w.num_sms * 32)), tile_w * tile_h / ppt};
+}
 
 void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
                     bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s)
@@ -1082,10 +1152,9 @@ void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, co
         J.dimage[v] = use_target ? dimages[v] : nullptr;
     }
     const RenderBufs &rb0 = *rbs[0];
-    const int ppt = 1 << (rb0.variant >> 1);
+    const RasterShape sh = raster_shape(rb0.variant, J.tile_ofs[n_views], cams[0].tile_w, cams[0].tile_h, w);
     cudaMemsetAsync(work, 0, sizeof(int), s);
-    fwd_variant(rb0.variant)<<<persistent_grid(J.tile_ofs[n_views], w), cams[0].tile_w * cams[0].tile_h / ppt, 0, s>>>(
-        J, args, use_target ? 1 : 0, loss);
+    fwd_variant(rb0.variant)<<<sh.grid, sh.block, 0, s>>>(J, args, use_target ? 1 : 0, loss);
 }
 
 // A job over one view of the argument block: slots 0..view, only `view` with items.
@@ -1109,10 +1178,9 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
         J.cfinal[v] = image == rb.cfinal ? nullptr : rb.cfinal;
         J.dimage[v] = use_target ? dimage : nullptr;
     }
-    const int ppt = 1 << (rb.variant >> 1);
+    const RasterShape sh = raster_shape(rb.variant, rb.tiles, cam.tile_w, cam.tile_h, w);
     cudaMemsetAsync(work, 0, sizeof(int), s);
-    fwd_variant(rb.variant)<<<persistent_grid(rb.tiles, w), cam.tile_w * cam.tile_h / ppt, 0, s>>>(
-        J, args, use_target ? 1 : 0, loss);
+    fwd_variant(rb.variant)<<<sh.grid, sh.block, 0, s>>>(J, args, use_target ? 1 : 0, loss);
 }
 
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
@@ -1126,11 +1194,10 @@ void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, c
     RasterJob J = make_job(n_views, rbs, work);
     for (int v = 0; v < n_views; v++) J.dimage[v] = const_cast<float *>(dimages[v]);
     const RenderBufs &rb0 = *rbs[0];
-    const int ppt = 1 << (rb0.variant_bwd >> 1);
+    const RasterShape sh = raster_shape(rb0.variant_bwd, J.tile_ofs[n_views], cams[0].tile_w, cams[0].tile_h, w);
     cudaMemsetAsync(work, 0, sizeof(int), s);
     w.mark(TP_RBWD0, s);
-    bwd_variant(rb0.variant_bwd, stats != nullptr)<<<persistent_grid(J.tile_ofs[n_views], w),
-                                                     cams[0].tile_w * cams[0].tile_h / ppt, 0, s>>>(J, args, stats);
+    bwd_variant(rb0.variant_bwd, stats != nullptr)<<<sh.grid, sh.block, 0, s>>>(J, args, stats);
     w.mark(TP_RBWD1, s);
 }
 
@@ -1170,11 +1237,10 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
     launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
     RasterJob J = single_view_job(view, rb, work);
     for (int v = 0; v <= view; v++) J.dimage[v] = const_cast<float *>(dimage);
-    const int ppt = 1 << (rb.variant_bwd >> 1);
+    const RasterShape sh = raster_shape(rb.variant_bwd, rb.tiles, cam.tile_w, cam.tile_h, w);
     cudaMemsetAsync(work, 0, sizeof(int), s);
     if (view == 0) w.mark(TP_RBWD0, s);
-    bwd_variant(rb.variant_bwd, stats != nullptr)<<<persistent_grid(rb.tiles, w), cam.tile_w * cam.tile_h / ppt, 0,
-                                                    s>>>(J, args, stats);
+    bwd_variant(rb.variant_bwd, stats != nullptr)<<<sh.grid, sh.block, 0, s>>>(J, args, stats);
     if (view == 0) w.mark(TP_RBWD1, s);
     project_backward(sc, args, view, n_vis, rb, grad, gcap, remap_mask, remap_prefix, ids, accumulate, w, s);
 }

@@ -46,6 +46,11 @@ def _case(name):
         P = scenes.uniform_cube_scene(3000, seed=5, sh_degree=2, log_scale_mean=-3.0)
         cam = scenes.camera_lookat((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 80, 64, 60.0, up=(0, -1, 0))
         return P, cam, 2, (32, 8)
+    if name == "tile8x4_ragged":
+        # the benchmark's tile shape (one warp per tile), ragged in both directions
+        P = scenes.uniform_cube_scene(3000, seed=6, sh_degree=3, log_scale_mean=-3.0)
+        cam = scenes.camera_lookat((0.3, -0.2, -2.8), (0.0, 0.1, 0.0), 90, 70, 65.0, up=(0, -1, 0))
+        return P, cam, 3, (8, 4)
     if name == "degenerate":
         c = scenes.cfg_diff_check(n=8000, width=96)
         return c["scene"], c["cams"][0], 3, (16, 16)
@@ -61,7 +66,7 @@ def _case(name):
     raise KeyError(name)
 
 
-CASES = ["cube10k", "cube_offaxis_sh3", "ragged_tiles", "tile32x8", "degenerate"]
+CASES = ["cube10k", "cube_offaxis_sh3", "ragged_tiles", "tile32x8", "tile8x4_ragged", "degenerate"]
 
 
 def _run_fwd(gs, orc, name):
@@ -252,8 +257,9 @@ def test_raster_variants_agree(gs, orc, name, tile):
     dimg = np.random.default_rng(2).normal(size=r["image"].shape)
     g_ref, _ = orc.backward(f32(P), deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], dimg)
     dimg_t = torch.as_tensor(dimg, dtype=torch.float32, device="cuda")
+    from paper_2509_15645_b300 import _lib
     images, tried = [], 0
-    for v in range(6):
+    for v in range(_lib.RASTER_VARIANTS):
         try:
             ctx.set_raster_variant(v)
         except Exception:
