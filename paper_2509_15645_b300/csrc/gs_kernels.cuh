@@ -14,7 +14,6 @@ struct ScanLen {
 
 struct Work {
     uint32_t *partials;   // >= 1024 scan partials
-    uint32_t *hist;       // radix histograms
     int *status;          // device status word
     int scan_grid;        // blocks of the scan kernels (<= 1024)
     int num_sms;
@@ -37,14 +36,15 @@ struct Work {
 };
 
 // k_scan.cu
-constexpr int RADIX_TILE = 1024;   // keys per radix-sort tile (the histogram buffer holds 256 per tile)
 void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *total_out, int total_cap,
                     cudaStream_t s);
+// Exclusive scan of len counts in place (one block when len <= 65536, else
+// scan_exclusive); the total goes to total_out, clamped to cap with
+// GS_ERR_CAPACITY latched above it.
+void scan_counts(uint32_t *v, int64_t len, int *total_out, int cap, Work &w, cudaStream_t s);
 void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
                   uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s, uint8_t *counter = nullptr,
                   uint8_t *delay = nullptr);
-int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
-               Work &w, cudaStream_t s);
 
 // SH planes of w, m, v and their restore directions: D - 11 planes each, of
 // the SH storage type.  Resident scenes: the planes sit `ppitch` = pitch
@@ -132,11 +132,12 @@ struct RenderBufs {
     float *compact;          // [D][cap] restored parameters of the visible set
     int64_t cap;             // visible capacity
     float4 *rec0, *rec1, *rec2;
-    uint32_t *dkey, *tcnt;
     uint2 *rect;
-    uint32_t *dk[2], *dv[2]; // depth sort buffers
-    uint32_t *rank_cnt;      // [cap + 1]
-    uint32_t *tk[2], *tv[2]; // tile sort buffers
+    uint32_t *depth;         // [cap] depth of each visible splat (f32 bits: positive, so ordered as integers)
+    uint32_t *tile_cnt;      // [tiles + 1] keys per tile, then (scanned in place) each tile's first key
+    uint32_t *tile_cur;      // [tiles] emission cursors
+    int32_t *long_tiles;     // [tiles] tiles whose lists are sorted by k_tile_sort_long
+    uint32_t *tk[2], *tv[2]; // keys: [0] per tile, unsorted (depth, splat); [1] sorted (tile, splat)
     int64_t kcap;            // key capacity
     uint2 *ranges;           // [tiles]
     float *g9;               // [cap][G9_STRIDE] screen-space gradient sums per splat (9 used)
@@ -145,9 +146,8 @@ struct RenderBufs {
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0
-    int *n_big;              // device [2]: sizes of the two large-rectangle lists
-    int32_t *big_idx;        // [cap] splats whose tiles k_big_counts counts
-    int32_t *big_rank;       // [cap] depth ranks whose keys k_big_emit writes
+    int *n_big;              // device [2]: [0] splats of the large-rectangle list, [1] long tiles
+    int32_t *big_idx;        // [cap] splats whose tiles a warp counts and emits (k_big_counts, k_big_emit)
     int variant;             // forward rasterizer variant (pixels per thread, batch), see raster_variant_ok
     int variant_bwd;         // backward rasterizer variant
     // filled by render_fwd
@@ -169,6 +169,7 @@ struct RasterJob {
     float *cfinal[MAX_VIEWS];    // forward: final colour kept for the backward (or null); backward: read
     float *dimage[MAX_VIEWS];    // forward: dL/dimage out (with targets); backward: read
     float *g9[MAX_VIEWS];        // backward: per-splat sums out
+    uint32_t cap[MAX_VIEWS];     // visible capacity (list entries index records below it)
     int *work;
 };
 

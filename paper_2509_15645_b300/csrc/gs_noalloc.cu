@@ -138,7 +138,6 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     int *status = reinterpret_cast<int *>(base + OFF_STATUS);
     Work w{};
     w.partials = reinterpret_cast<uint32_t *>(base + OFF_PARTIALS);
-    w.hist = nullptr;
     w.status = status;
     w.num_sms = sms;
     w.scan_grid = sms * 2 > 1024 ? 1024 : sms * 2;

@@ -202,13 +202,11 @@ static void carve(gs_ctx *c, char *base)
         rb.rec0 = k.take<float4>(V);
         rb.rec1 = k.take<float4>(V);
         rb.rec2 = k.take<float4>(V);
-        rb.tcnt = k.take<uint32_t>(V);
         rb.rect = k.take<uint2>(V);
-        for (int j = 0; j < 2; j++) {
-            rb.dk[j] = k.take<uint32_t>(V);
-            rb.dv[j] = k.take<uint32_t>(V);
-        }
-        rb.rank_cnt = k.take<uint32_t>(V + 1);
+        rb.depth = k.take<uint32_t>(V);
+        rb.tile_cnt = k.take<uint32_t>(tiles + 1);
+        rb.tile_cur = k.take<uint32_t>(tiles);
+        rb.long_tiles = k.take<int32_t>(tiles);
         for (int j = 0; j < 2; j++) {
             rb.tk[j] = k.take<uint32_t>(K);
             rb.tv[j] = k.take<uint32_t>(K);
@@ -223,13 +221,10 @@ static void carve(gs_ctx *c, char *base)
         rb.fix_flag = k.take<uint8_t>(V);
         rb.n_big = k.take<int>(2);
         rb.big_idx = k.take<int32_t>(V);
-        rb.big_rank = k.take<int32_t>(V);
         c->imgs[v] = k.take<float>(P);
         c->dimgs[v] = k.take<float>(P);
     }
     c->work = k.take<int>(4);
-    int64_t big = K > V ? K : V;
-    c->w.hist = k.take<uint32_t>(256 * ((big + RADIX_TILE - 1) / RADIX_TILE) + 256);
     c->w.partials = k.take<uint32_t>(1024);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);

@@ -39,14 +39,26 @@ struct SLutR {
 // quadratic) and compares o exp(-sigma_min) with the floor, with 0.1% slack.
 // It only ever says "no" when no pixel can pass the per-pixel tests, so
 // dropping such splats leaves every pixel's result unchanged.
+// Every operation is an explicitly rounded intrinsic (no contraction into FMAs
+// that could differ between the kernels that inline it): the key counting and
+// the key emission, in different kernels, must take the same decisions.
+__device__ __forceinline__ float q_sigma(float A, float B, float C, float dx, float dy)
+{
+    // 0.5 (A dx^2 + C dy^2) + B dx dy
+    const float a = __fmul_rn(__fmul_rn(A, dx), dx), c = __fmul_rn(__fmul_rn(C, dy), dy);
+    return __fadd_rn(__fmul_rn(0.5f, __fadd_rn(a, c)), __fmul_rn(__fmul_rn(B, dx), dy));
+}
+
 __device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
 {
     const float margin = 1e-3f;
-    const float x0 = fmaxf(X0, r0.x - r0.z - margin), x1 = fminf(X1, r0.x + r0.z + margin);
-    const float y0 = fmaxf(Y0, r0.y - r0.z - margin), y1 = fminf(Y1, r0.y + r0.z + margin);
+    const float ext = __fadd_rn(r0.z, margin);
+    const float x0 = fmaxf(X0, __fsub_rn(r0.x, ext)), x1 = fminf(X1, __fadd_rn(r0.x, ext));
+    const float y0 = fmaxf(Y0, __fsub_rn(r0.y, ext)), y1 = fminf(Y1, __fadd_rn(r0.y, ext));
     if (x0 > x1 || y0 > y1) return false;
     // d = mean - p over the rectangle
-    const float dxl = r0.x - x1, dxh = r0.x - x0, dyl = r0.y - y1, dyh = r0.y - y0;
+    const float dxl = __fsub_rn(r0.x, x1), dxh = __fsub_rn(r0.x, x0);
+    const float dyl = __fsub_rn(r0.y, y1), dyh = __fsub_rn(r0.y, y0);
     const float A = r1.x, B = r1.y, C = r1.z;
     float smin = 0.f;
     if (!(dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f)) {
@@ -56,19 +68,19 @@ __device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const float dx = dxs[k];
-            const float dy = fminf(fmaxf(-B * dx / C, dyl), dyh);
-            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+            const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dx), C), dyl), dyh);
+            smin = fminf(smin, q_sigma(A, B, C, dx, dy));
         }
         const float dys[2] = {dyl, dyh};
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const float dy = dys[k];
-            const float dx = fminf(fmaxf(-B * dy / A, dxl), dxh);
-            smin = fminf(smin, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+            const float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dy), A), dxl), dxh);
+            smin = fminf(smin, q_sigma(A, B, C, dx, dy));
         }
         smin = fmaxf(smin, 0.f);
     }
-    return r0.w * __expf(-smin) >= ALPHA_MIN * 0.999f;
+    return __fmul_rn(r0.w, __expf(-smin)) >= ALPHA_MIN * 0.999f;
 }
 
 // Pixel-centre box of tile (t_x, t_y).
@@ -85,18 +97,16 @@ __device__ __forceinline__ void tile_box(const DevCam &cam, int t_x, int t_y, fl
 // (k_big_counts, k_big_emit); smaller ones by the splat's own thread.
 constexpr int BIG_RECT = 32;
 
-// Number of tiles of [x0, x1) x [y0, y1) that splat (r0, r1) reaches, row-major.
-__device__ __forceinline__ uint32_t count_reach(float4 r0, float4 r1, int x0, int x1, int y0, int y1,
-                                                const DevCam &cam)
+// One more key for every tile of [x0, x1) x [y0, y1) that splat (r0, r1) reaches.
+__device__ __forceinline__ void count_tiles(float4 r0, float4 r1, int x0, int x1, int y0, int y1, const DevCam &cam,
+                                            uint32_t *tile_cnt)
 {
-    uint32_t c = 0;
     for (int ty = y0; ty < y1; ty++)
         for (int tx = x0; tx < x1; tx++) {
             float X0, X1, Y0, Y1;
             tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            c += splat_reaches_box(r0, r1, X0, X1, Y0, Y1) ? 1u : 0u;
+            if (splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
         }
-    return c;
 }
 
 template <int DEG, typename T>
@@ -105,8 +115,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                                                                const DevArgs *__restrict__ args, int view,
                                                                float *__restrict__ compact, float4 *__restrict__ rec0,
                                                                float4 *__restrict__ rec1, float4 *__restrict__ rec2,
-                                                               uint32_t *__restrict__ dkey, uint32_t *__restrict__ dval,
-                                                               uint32_t *__restrict__ tcnt, uint2 *__restrict__ rect,
+                                                               uint32_t *__restrict__ depth,
+                                                               uint32_t *__restrict__ tile_cnt, uint2 *__restrict__ rect,
                                                                int *__restrict__ n_fix, int32_t *__restrict__ fix_idx,
                                                                uint8_t *__restrict__ fix_flag, int *__restrict__ n_big,
                                                                int32_t *__restrict__ big_idx)
@@ -131,9 +141,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
             rec0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             rec1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             rec2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            dkey[k] = 0u;
-            dval[k] = (uint32_t)k;
-            tcnt[k] = 0u;
+            depth[k] = 0u;
             rect[k] = make_uint2(0u, 0u);
             fix_flag[k] = 0;
             for (int r = 0; r < D; r++) compact[r * (int64_t)cap + k] = 0.f;
@@ -203,31 +211,31 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         rec0[k] = r0v;
         rec1[k] = r1v;
         rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
-        dkey[k] = __float_as_uint(P.p[2]);
-        dval[k] = (uint32_t)k;
-        // tiles the splat reaches (the list filter); FP64-flagged splats and
-        // large rectangles are counted by k_big_counts
-        uint32_t cnt = 0;
+        depth[k] = __float_as_uint(P.p[2]);
+        // the key count of each tile the splat reaches (the list filter);
+        // FP64-flagged splats and large rectangles are counted by k_big_counts.
+        // A splat that is not kept gets an empty rectangle, so that counting
+        // and emission (k_emit) see the same partition.
+        if (!P.keep) P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
         if (P.keep && !P.fp64) {
             if ((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2]) <= BIG_RECT)
-                cnt = count_reach(r0v, r1v, P.rect[0], P.rect[1], P.rect[2], P.rect[3], s_cam);
+                count_tiles(r0v, r1v, P.rect[0], P.rect[1], P.rect[2], P.rect[3], s_cam, tile_cnt);
             else
                 big_idx[atomicAdd(n_big, 1)] = k;
         }
-        tcnt[k] = cnt;
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
 }
 
 // FP64 fix-up of the Gaussians the gather flagged (badly conditioned 2D
-// covariance): conic, radius, tile rectangle and key count from the FP64
-// chain, before the keys are counted.  Opacity, colour and depth are unchanged.
+// covariance): conic, radius and tile rectangle from the FP64 chain, before
+// their keys are counted (k_big_counts).  Opacity, colour and depth are
+// unchanged.
 __global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restrict__ compact, int cap,
                                                             const int *__restrict__ n_fix,
                                                             const int32_t *__restrict__ fix_idx,
                                                             const DevArgs *__restrict__ args, int view, float4 *rec0,
-                                                            float4 *rec1, uint32_t *tcnt, uint2 *rect, int *n_big,
-                                                            int32_t *big_idx)
+                                                            float4 *rec1, uint2 *rect, int *n_big, int32_t *big_idx)
 {
     __shared__ DevCam s_cam;
     if (threadIdx.x < sizeof(DevCam) / 4)
@@ -245,19 +253,10 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restr
         const float o = rec0[k].w;
         rec0[k] = make_float4(P.mx, P.my, P.radius, o);
         rec1[k] = make_float4(P.conA, P.conB, P.conC, P.p[2]);
-        tcnt[k] = 0u;
         if (P.keep) big_idx[atomicAdd(n_big, 1)] = k;        // counted by k_big_counts
+        else P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
-}
-
-
-__global__ void k_rank_counts(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ tcnt,
-                              const int *n_vis_p, int cap, uint32_t *rank_cnt)
-{
-    int n = min(*n_vis_p, cap);
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-        rank_cnt[r] = tcnt[sorted_vals[r]];
 }
 
 
@@ -266,7 +265,7 @@ __global__ void k_rank_counts(const uint32_t *__restrict__ sorted_vals, const ui
 __global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
                              const uint2 *__restrict__ rect, const int *__restrict__ n_big,
                              const int32_t *__restrict__ big_idx, int cap, const DevArgs *__restrict__ args, int view,
-                             uint32_t *__restrict__ tcnt)
+                             uint32_t *__restrict__ tile_cnt)
 {
     const int nb = min(*n_big, cap);
     const DevCam &cam = args->cam[view];
@@ -277,111 +276,266 @@ __global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__re
         const uint2 rc = rect[k];
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
-        uint32_t cnt = 0;
-        if (cnt_all > 0) {
-            const float4 r0 = rec0[k], r1 = rec1[k];
-            for (int t = lane; t < cnt_all; t += 32) {
-                float X0, X1, Y0, Y1;
-                tile_box(cam, x0 + t % wdt, y0 + t / wdt, X0, X1, Y0, Y1);
-                cnt += splat_reaches_box(r0, r1, X0, X1, Y0, Y1) ? 1u : 0u;
-            }
+        if (cnt_all <= 0) continue;
+        const float4 r0 = rec0[k], r1 = rec1[k];
+        for (int t = lane; t < cnt_all; t += 32) {
+            const int tx = x0 + t % wdt, ty = y0 + t / wdt;
+            float X0, X1, Y0, Y1;
+            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+            if (splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) tcnt[k] = cnt;
     }
 }
 
-// Keys of the splats in depth order: the splat of rank r writes (tile, k) for
-// each tile it reaches, in row-major tile order, from offset ofs[r].  Small
-// rectangles by the rank's thread; large ones go to a list for k_big_emit.
-__global__ void k_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
-                       const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                       const float4 *__restrict__ rec1, const int *n_vis_p, int cap, int64_t kcap,
-                       const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval, int *n_big_emit,
-                       int32_t *big_rank)
+// Keys of the visible splats into their tiles' lists: for each tile t the
+// splat reaches, (depth, k) goes to slot tile_off[t] + (a cursor of t), so a
+// tile's list is complete but unordered until k_tile_sort.  Small rectangles
+// by the splat's thread (the partition of k_gather_project's counting: kept,
+// not FP64-flagged, at most BIG_RECT tiles); the big list by k_big_emit.
+__global__ void k_emit(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
+                       const float4 *__restrict__ rec1, const uint32_t *__restrict__ depth,
+                       const uint8_t *__restrict__ fix_flag, const int *n_vis_p, int cap, int64_t kcap,
+                       const DevArgs *__restrict__ args, int view, const uint32_t *__restrict__ tile_off,
+                       uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
 {
     const int n = min(*n_vis_p, cap);
     const DevCam &cam = args->cam[view];
     const int tiles_x = cam.tiles_x;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const uint32_t k = sorted_vals[r];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (fix_flag[k]) continue;
         const uint2 rc = rect[k];
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const int area = (x1 - x0) * (y1 - y0);
-        if (area <= 0) continue;
-        if (area > BIG_RECT) {
-            big_rank[atomicAdd(n_big_emit, 1)] = r;
-            continue;
-        }
-        int64_t o = ofs[r];
+        if (area <= 0 || area > BIG_RECT) continue;
         const float4 r0 = rec0[k], r1 = rec1[k];
+        const uint32_t dk = depth[k];
         for (int ty = y0; ty < y1; ty++)
             for (int tx = x0; tx < x1; tx++) {
                 float X0, X1, Y0, Y1;
                 tile_box(cam, tx, ty, X0, X1, Y0, Y1);
                 if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
-                if (o < kcap) {
-                    tkey[o] = (uint32_t)(ty * tiles_x + tx);
-                    tval[o] = k;
+                const int t = ty * tiles_x + tx;
+                const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
+                if (p < kcap) {
+                    bkey[p] = dk;
+                    bval[p] = (uint32_t)k;
                 }
-                o++;
             }
     }
 }
 
-// The large rectangles of k_emit: one warp per splat, a ballot orders the
-// lanes' keys.
-__global__ void k_big_emit(const uint32_t *__restrict__ sorted_vals, const uint32_t *__restrict__ ofs,
-                           const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                           const float4 *__restrict__ rec1, const int *__restrict__ n_big_emit,
-                           const int32_t *__restrict__ big_rank, int cap, int64_t kcap,
-                           const DevArgs *__restrict__ args, int view, uint32_t *tkey, uint32_t *tval)
+// The keys of the big list: one warp per splat, lanes over its tiles.
+__global__ void k_big_emit(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
+                           const float4 *__restrict__ rec1, const uint32_t *__restrict__ depth,
+                           const int *__restrict__ n_big, const int32_t *__restrict__ big_idx, int cap, int64_t kcap,
+                           const DevArgs *__restrict__ args, int view, const uint32_t *__restrict__ tile_off,
+                           uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
 {
-    const int nb = min(*n_big_emit, cap);
+    const int nb = min(*n_big, cap);
     const DevCam &cam = args->cam[view];
-    const int tiles_x = cam.tiles_x;
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nwarps) {
-        const int r = big_rank[j];
-        const uint32_t k = sorted_vals[r];
-        int64_t o = ofs[r];
+        const int k = big_idx[j];
         const uint2 rc = rect[k];
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
+        if (cnt_all <= 0) continue;
         const float4 r0 = rec0[k], r1 = rec1[k];
-        for (int t0 = 0; t0 < cnt_all; t0 += 32) {
-            const int t = t0 + lane;
-            bool hit = false;
-            int tx = 0, ty = 0;
-            if (t < cnt_all) {
-                tx = x0 + t % wdt;
-                ty = y0 + t / wdt;
-                float X0, X1, Y0, Y1;
-                tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-                hit = splat_reaches_box(r0, r1, X0, X1, Y0, Y1);
+        const uint32_t dk = depth[k];
+        for (int tt = lane; tt < cnt_all; tt += 32) {
+            const int tx = x0 + tt % wdt, ty = y0 + tt / wdt;
+            float X0, X1, Y0, Y1;
+            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+            if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
+            const int t = ty * cam.tiles_x + tx;
+            const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
+            if (p < kcap) {
+                bkey[p] = dk;
+                bval[p] = (uint32_t)k;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int64_t p = o + __popc(bal & ((1u << lane) - 1u));
-                if (p < kcap) {
-                    tkey[p] = (uint32_t)(ty * tiles_x + tx);
-                    tval[p] = k;
-                }
-            }
-            o += __popc(bal);
         }
     }
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ tkey, const int *n_keys_p, int64_t kcap, uint2 *ranges)
+// ---------------------------------------------------------------------------
+// Per-tile sort of the lists into front-to-back order: by depth, ties by the
+// splat's index (ascending ids: the visible set is compacted in id order), the
+// order of one global sort on (tile, depth, id).  Keys are (depth bits << 32 |
+// splat): depths are positive, so their bits order as unsigned integers.  All
+// sorts are bitonic networks whose every comparator puts the minimum at the
+// lower index (the first step of each merge compares mirrored positions), so
+// a list padded with +inf needs no direction changes.
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
+
+// N keys in a warp (N = 32, 64, 128 or 256): element e = 32 r + lane held in
+// v[r].  Pairs within a row are exchanged through shuffles, pairs across rows
+// stay in the lane's registers.
+template <int N>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[N / 32], int lane)
 {
-    int n = (int)min((int64_t)*n_keys_p, kcap);
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        uint32_t t = tkey[p];
-        if (p == 0 || tkey[p - 1] != t) ranges[t].x = (uint32_t)p;
-        if (p == n - 1 || tkey[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    constexpr int R = N / 32;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+        // first step of the merge: e pairs with its mirror in the block of k
+        if (k <= 32) {
+            const bool lower = (lane & (k >> 1)) == 0;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], k - 1);
+                v[r] = lower ? umin64(v[r], p) : umax64(v[r], p);
+            }
+        } else {
+            const int rm = (k >> 5) - 1;                  // mirror: row r ^ rm, lane ^ 31
+            unsigned long long p[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) p[r] = __shfl_xor_sync(0xffffffffu, v[r ^ rm], 31);
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                // the lower element of the pair is the one in the lower half of the block of k
+                const bool lower = ((r * 32) & (k >> 1)) == 0;
+                v[r] = lower ? umin64(v[r], p[r]) : umax64(v[r], p[r]);
+            }
+        }
+        // then pairs at distance j = k/4, ..., 1
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int rj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if ((r & rj) == 0) {
+                        const unsigned long long x = v[r], y = v[r | rj];
+                        v[r] = umin64(x, y);
+                        v[r | rj] = umax64(x, y);
+                    }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    v[r] = lower ? umin64(v[r], p) : umax64(v[r], p);
+                }
+            }
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void warp_sort_list(const uint32_t *__restrict__ bkey, const uint32_t *__restrict__ bval,
+                                               int64_t lo, int L, uint32_t t, uint32_t *skey, uint32_t *sval, int lane)
+{
+    unsigned long long v[N / 32];
+#pragma unroll
+    for (int r = 0; r < N / 32; r++) {
+        const int e = r * 32 + lane;
+        v[r] = e < L ? ((unsigned long long)bkey[lo + e] << 32 | bval[lo + e]) : ~0ull;
+    }
+    warp_bitonic<N>(v, lane);
+#pragma unroll
+    for (int r = 0; r < N / 32; r++) {
+        const int e = r * 32 + lane;
+        if (e < L) {
+            skey[lo + e] = t;
+            sval[lo + e] = (uint32_t)v[r];
+        }
+    }
+}
+
+constexpr int SORT_WARP_MAX = 256;       // lists up to this length: one warp, in registers
+constexpr int SORT_SMEM_MAX = 8192;      // longer ones up to this: one block, in shared memory
+
+// One warp per tile: the tile's range, and its list sorted into (tile, splat)
+// order when it has at most SORT_WARP_MAX keys; longer lists are queued for
+// k_tile_sort_long.
+__global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ tile_off, int tiles, int64_t kcap,
+                                                   const uint32_t *__restrict__ bkey,
+                                                   const uint32_t *__restrict__ bval, uint32_t *skey, uint32_t *sval,
+                                                   uint2 *ranges, int *n_long, int32_t *long_tiles)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += nwarps) {
+        const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
+        const int L = (int)(hi - lo);
+        if (lane == 0) ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
+        if (L <= 0) continue;
+        if (L <= 32) warp_sort_list<32>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
+        else if (L <= 64) warp_sort_list<64>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
+        else if (L <= 128) warp_sort_list<128>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
+        else if (L <= SORT_WARP_MAX) warp_sort_list<256>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
+        else if (lane == 0) long_tiles[atomicAdd(n_long, 1)] = t;
+    }
+}
+
+// Compare-exchange of positions i < j of a list of length L (positions >= L
+// hold +inf and stay untouched).
+__device__ __forceinline__ void cmpx_smem(unsigned long long *v, int i, int j)
+{
+    const unsigned long long x = v[i], y = v[j];
+    if (y < x) {
+        v[i] = y;
+        v[j] = x;
+    }
+}
+__device__ __forceinline__ void cmpx_global(uint32_t *key, uint32_t *val, int64_t lo, int L, int i, int j)
+{
+    if (j >= L) return;
+    const unsigned long long x = (unsigned long long)key[lo + i] << 32 | val[lo + i];
+    const unsigned long long y = (unsigned long long)key[lo + j] << 32 | val[lo + j];
+    if (y < x) {
+        key[lo + i] = (uint32_t)(y >> 32);
+        val[lo + i] = (uint32_t)y;
+        key[lo + j] = (uint32_t)(x >> 32);
+        val[lo + j] = (uint32_t)x;
+    }
+}
+
+// One block per long list: a bitonic sort in shared memory (up to
+// SORT_SMEM_MAX keys, padded to a power of two with +inf), else in place in
+// the unsorted key arrays (positions past the list act as +inf).
+__global__ void __launch_bounds__(256) k_tile_sort_long(const uint32_t *__restrict__ tile_off, int64_t kcap,
+                                                        uint32_t *bkey, uint32_t *bval, uint32_t *skey,
+                                                        uint32_t *sval, const int *n_long,
+                                                        const int32_t *__restrict__ long_tiles)
+{
+    extern __shared__ unsigned long long sv[];
+    const int nl = *n_long;
+    for (int q = blockIdx.x; q < nl; q += gridDim.x) {
+        const int t = long_tiles[q];
+        const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
+        const int L = (int)(hi - lo);
+        int P = 1;
+        while (P < L) P <<= 1;
+        const bool in_smem = P <= SORT_SMEM_MAX;
+        if (in_smem)
+            for (int e = threadIdx.x; e < P; e += blockDim.x)
+                sv[e] = e < L ? ((unsigned long long)bkey[lo + e] << 32 | bval[lo + e]) : ~0ull;
+        __syncthreads();
+        for (int lk = 1; (1 << lk) <= P; lk++) {        // blocks of k = 2^lk
+            const int k = 1 << lk;
+            for (int e = threadIdx.x; e < P / 2; e += blockDim.x) {      // mirrored pairs within blocks of k
+                const int i = ((e >> (lk - 1)) << lk) | (e & ((k >> 1) - 1)), j = i ^ (k - 1);
+                if (in_smem) cmpx_smem(sv, i, j);
+                else cmpx_global(bkey, bval, lo, L, i, j);
+            }
+            __syncthreads();
+            for (int ld = lk - 2; ld >= 0; ld--) {       // then pairs at distance 2^ld
+                for (int e = threadIdx.x; e < P / 2; e += blockDim.x) {
+                    const int i = ((e >> ld) << (ld + 1)) | (e & ((1 << ld) - 1)), j = i + (1 << ld);
+                    if (in_smem) cmpx_smem(sv, i, j);
+                    else cmpx_global(bkey, bval, lo, L, i, j);
+                }
+                __syncthreads();
+            }
+        }
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            skey[lo + e] = (uint32_t)t;
+            sval[lo + e] = in_smem ? (uint32_t)sv[e] : bval[lo + e];
+        }
+        __syncthreads();                                  // sv is reused by the next list
     }
 }
 
@@ -412,11 +566,19 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
 template <bool COLOR, bool INDEX, bool WT = false>
 __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
                                            const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
-                                           uint32_t b, int cnt, float4 *s0, float4 *s1, float4 *s2, uint32_t *s_k)
+                                           uint32_t b, int cnt, float4 *s0, float4 *s1, float4 *s2, uint32_t *s_k,
+                                           uint32_t kcap_vis)
 {
     const int t0 = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x, nt = WT ? 32 : (int)blockDim.x;
     for (int e = t0; e < cnt; e += nt) {
         const uint32_t k = svals[b + e];
+        if (k >= kcap_vis) {            // never for a consistent list; an empty splat rather than a stray read
+            s0[e] = make_float4(0.f, 0.f, -1.f, 0.f);
+            s1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (COLOR) s2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (INDEX) s_k[e] = 0u;
+            continue;
+        }
         s0[e] = rec0[k];
         s1[e] = rec1[k];
         if (COLOR) s2[e] = rec2[k];
@@ -504,7 +666,7 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
             break;
         }
         const int nb = stage_batch<true, false, WT>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1,
-                                                    s2, nullptr);
+                                                    s2, nullptr, J.cap[view]);
         for (int e = 0; e < nb && live; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
@@ -670,7 +832,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
             break;
         }
         const int nb = stage_batch<true, true, WT>(svals, rec0, rec1, rec2, b, min(BATCH, (int)(rg.y - b)), s0, s1,
-                                                   s2, s_k);
+                                                   s2, s_k, J.cap[view]);
         for (int e = 0; e < nb; e++) {
             const float4 r0 = s0[e];
             if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
@@ -1065,13 +1227,6 @@ void launch_loss_l1(const float *image, const float *target, int64_t count, floa
     k_loss_l1<<<w.grid(count, 256, 4), 256, 0, s>>>(image, target, count, loss, dimage);
 }
 
-static int bits_for(int n)
-{
-    int b = 1;
-    while ((1 << b) < n) b++;
-    return b;
-}
-
 void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
                   RenderBufs &rb, const DevCam &cam, Work &w, cudaStream_t s)
 {
@@ -1081,31 +1236,39 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
                      : sc.deg == 1 ? k_gather_project<1, float> : k_gather_project<0, float>)
                   : (sc.deg == 3 ? k_gather_project<3, __nv_bfloat16> : sc.deg == 2 ? k_gather_project<2, __nv_bfloat16>
                      : sc.deg == 1 ? k_gather_project<1, __nv_bfloat16> : k_gather_project<0, __nv_bfloat16>);
+    const int tiles = cam.tiles_x * cam.tiles_y;
     cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
     cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);
+    cudaMemsetAsync(rb.tile_cnt, 0, (size_t)(tiles + 1) * sizeof(uint32_t), s);
+    cudaMemsetAsync(rb.tile_cur, 0, (size_t)tiles * sizeof(uint32_t), s);
+    // gather, projection, and the key count of every tile (small rectangles)
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
-                                                          rb.rec2, rb.dk[0], rb.dv[0], rb.tcnt, rb.rect, rb.n_fix,
+                                                          rb.rec2, rb.depth, rb.tile_cnt, rb.rect, rb.n_fix,
                                                           rb.fix_idx, rb.fix_flag, rb.n_big, rb.big_idx);
     k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
-                                                    rb.tcnt, rb.rect, rb.n_big, rb.big_idx);
+                                                    rb.rect, rb.n_big, rb.big_idx);
     k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
-                                               rb.tcnt);
-    // depth order of the visible set (stable: ties keep ascending index)
-    int dcur = radix_sort(rb.dk[0], rb.dv[0], rb.dk[1], rb.dv[1], n_vis, cap, 32, w, s);
-    const uint32_t *dsorted = rb.dv[dcur];
-    k_rank_counts<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.tcnt, n_vis, cap, rb.rank_cnt);
-    ScanLen L{n_vis, 1, 1, 0, 0, cap};
-    scan_exclusive(rb.rank_cnt, rb.rank_cnt, L, w, rb.n_keys, (int)rb.kcap, s);
-    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, rb.rec0, rb.rec1, n_vis, cap, rb.kcap, args,
-                                            view, rb.tk[0], rb.tv[0], rb.n_big + 1, rb.big_rank);
-    k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(dsorted, rb.rank_cnt, rb.rect, rb.rec0, rb.rec1, rb.n_big + 1, rb.big_rank,
-                                             cap, rb.kcap, args, view, rb.tk[0], rb.tv[0]);
-    const int tiles = cam.tiles_x * cam.tiles_y;
-    int tcur = radix_sort(rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_keys, (int)rb.kcap, bits_for(tiles), w, s);
-    cudaMemsetAsync(rb.ranges, 0, (size_t)tiles * sizeof(uint2), s);
-    k_tile_ranges<<<w.grid(rb.kcap, 256), 256, 0, s>>>(rb.tk[tcur], rb.n_keys, rb.kcap, rb.ranges);
-    rb.sorted_keys = rb.tk[tcur];
-    rb.sorted_vals = rb.tv[tcur];
+                                               rb.tile_cnt);
+    // each tile's first key (and the key total), then the keys into their tiles' lists
+    scan_counts(rb.tile_cnt, tiles + 1, rb.n_keys, (int)rb.kcap, w, s);
+    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
+                                            view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
+    k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.n_big, rb.big_idx, cap, rb.kcap,
+                                             args, view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
+    // front-to-back order within each tile, and the tiles' ranges
+    k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
+                                                                  rb.tk[1], rb.tv[1], rb.ranges, rb.n_big + 1,
+                                                                  rb.long_tiles);
+    static bool long_attr = false;
+    if (!long_attr) {
+        cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(SORT_SMEM_MAX * sizeof(unsigned long long)));
+        long_attr = true;
+    }
+    k_tile_sort_long<<<w.num_sms * 2, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
+        rb.tile_cnt, rb.kcap, rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_big + 1, rb.long_tiles);
+    rb.sorted_keys = rb.tk[1];
+    rb.sorted_vals = rb.tv[1];
     rb.tiles = tiles;
 }
 
@@ -1124,6 +1287,7 @@ static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
         J.rec2[v] = rb.rec2;
         J.cfinal[v] = rb.cfinal;
         J.g9[v] = rb.g9;
+        J.cap[v] = (uint32_t)rb.cap;
     }
     J.work = work;
     return J;

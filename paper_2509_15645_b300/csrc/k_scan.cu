@@ -1,6 +1,6 @@
-// k_scan.cu -- device-wide exclusive scan, ordered compaction of a bitmask,
-// and a stable LSD radix sort, all with data-dependent lengths read from
-// device memory so that callers never synchronise (graph capture).
+// k_scan.cu -- device-wide exclusive scan and ordered compaction of a
+// bitmask, with data-dependent lengths read from device memory so that callers
+// never synchronise (graph capture).
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -129,7 +129,7 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *
 // contiguous segment, the block scans the segment sums.  Writes the total to
 // total_out (clamped to total_cap, GS_ERR_CAPACITY latched above it).
 constexpr int SMALL_SCAN_THREADS = 1024;
-constexpr int64_t SMALL_SCAN_MAX = 64 * SMALL_SCAN_THREADS;
+constexpr int64_t SMALL_SCAN_MAX = 8 * SMALL_SCAN_THREADS;   // longer scans: three kernels (the one-block scan walks its segments serially)
 
 __global__ void __launch_bounds__(SMALL_SCAN_THREADS) k_scan_small(uint32_t *v, int len, int *total_out,
                                                                    int total_cap, int *status)
@@ -153,6 +153,16 @@ __global__ void __launch_bounds__(SMALL_SCAN_THREADS) k_scan_small(uint32_t *v, 
             t = total_cap;
         }
         *total_out = t;
+    }
+}
+
+void scan_counts(uint32_t *v, int64_t len, int *total_out, int cap, Work &w, cudaStream_t s)
+{
+    if (len <= SMALL_SCAN_MAX) {
+        k_scan_small<<<1, SMALL_SCAN_THREADS, 0, s>>>(v, (int)len, total_out, cap, w.status);
+    } else {
+        ScanLen L{nullptr, 1, 1, 0, (int)len, 0};
+        scan_exclusive(v, v, L, w, total_out, cap, s);
     }
 }
 
@@ -245,114 +255,9 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
     int64_t nchunks = (nwords + CHUNK_WORDS - 1) / CHUNK_WORDS;
     if (!have_counts)
         k_chunk_counts<<<w.grid(nchunks * 32, 256), 256, 0, s>>>(mask, nwords, chunk_cnt);
-    if (nchunks <= SMALL_SCAN_MAX) {
-        k_scan_small<<<1, SMALL_SCAN_THREADS, 0, s>>>(chunk_cnt, (int)nchunks, count_out, cap, w.status);
-    } else {
-        ScanLen L{nullptr, 1, 1, 0, (int)nchunks, 0};
-        scan_exclusive(chunk_cnt, chunk_cnt, L, w, count_out, cap, s);
-    }
+    scan_counts(chunk_cnt, nchunks, count_out, cap, w, s);
     k_compact_mask<<<w.grid(nchunks * COMPACT_BLOCK, COMPACT_BLOCK), COMPACT_BLOCK, 0, s>>>(
         mask, nwords, chunk_cnt, ids, word_prefix, cap, counter, delay);
-}
-
-// ---------------------------------------------------------------------------
-// Stable LSD radix sort of (key, value) pairs on bits [0, nbits) of the key,
-// 8-bit digits.  Each pass: per-tile digit histograms -> exclusive scan over
-// (digit, tile) -> stable scatter with per-tile ranks.
-constexpr int RS_BLOCK = 256, RS_TILE = RADIX_TILE, RS_ITEMS = RS_TILE / RS_BLOCK, RS_WARPS = RS_BLOCK / 32;
-
-__device__ __forceinline__ int rs_count(const int *n_dev, int cap)
-{
-    int n = *n_dev;
-    return n > cap ? cap : n;
-}
-
-__global__ void __launch_bounds__(RS_BLOCK) k_radix_hist(const uint32_t *__restrict__ keys, const int *n_dev, int cap,
-                                                         int shift, uint32_t dmask, uint32_t *hist)
-{
-    __shared__ uint32_t s_h[256];
-    int n = rs_count(n_dev, cap);
-    int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        s_h[threadIdx.x] = 0;
-        __syncthreads();
-        int base = t * RS_TILE;
-#pragma unroll 4
-        for (int j = 0; j < RS_ITEMS; j++) {
-            int idx = base + j * RS_BLOCK + threadIdx.x;
-            if (idx < n) atomicAdd(&s_h[(keys[idx] >> shift) & dmask], 1u);
-        }
-        __syncthreads();
-        hist[threadIdx.x * ntiles + t] = s_h[threadIdx.x];
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(RS_BLOCK) k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                                                            uint32_t *kout, uint32_t *vout, const int *n_dev, int cap,
-                                                            int shift, uint32_t dmask, const uint32_t *__restrict__ hist)
-{
-    __shared__ uint32_t s_ofs[256];
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_wc[RS_WARPS][256];
-    int n = rs_count(n_dev, cap);
-    int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t lt = (1u << lane) - 1u;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        s_ofs[threadIdx.x] = hist[threadIdx.x * ntiles + t];
-        s_run[threadIdx.x] = 0;
-        int base = t * RS_TILE;
-        for (int j = 0; j < RS_ITEMS; j++) {
-#pragma unroll
-            for (int w = 0; w < RS_WARPS; w++) s_wc[w][threadIdx.x] = 0;
-            __syncthreads();
-            int idx = base + j * RS_BLOCK + threadIdx.x;
-            bool valid = idx < n;
-            uint32_t key = valid ? kin[idx] : 0u, val = valid ? vin[idx] : 0u;
-            uint32_t d = (key >> shift) & dmask;
-            uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
-            uint32_t wrank = __popc(peers & lt);
-            if (valid && wrank == 0) s_wc[wid][d] = __popc(peers);
-            __syncthreads();
-            {
-                uint32_t run = s_run[threadIdx.x];
-#pragma unroll
-                for (int w = 0; w < RS_WARPS; w++) {
-                    uint32_t c = s_wc[w][threadIdx.x];
-                    s_wc[w][threadIdx.x] = run;
-                    run += c;
-                }
-                s_run[threadIdx.x] = run;
-            }
-            __syncthreads();
-            if (valid) {
-                uint32_t pos = s_ofs[d] + s_wc[wid][d] + wrank;
-                kout[pos] = key;
-                vout[pos] = val;
-            }
-            __syncthreads();
-        }
-    }
-}
-
-int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *n_dev, int cap, int nbits,
-               Work &w, cudaStream_t s)
-{
-    int cur = 0;
-    uint32_t *K[2] = {k0, k1}, *V[2] = {v0, v1};
-    int ntiles_cap = (cap + RS_TILE - 1) / RS_TILE;
-    int g = w.grid((int64_t)ntiles_cap * RS_BLOCK, RS_BLOCK);
-    for (int shift = 0; shift < nbits; shift += 8) {
-        int bits = nbits - shift < 8 ? nbits - shift : 8;
-        uint32_t dmask = (1u << bits) - 1u;
-        k_radix_hist<<<g, RS_BLOCK, 0, s>>>(K[cur], n_dev, cap, shift, dmask, w.hist);
-        ScanLen L{n_dev, 256, RS_TILE, 0, 0, cap};
-        scan_exclusive(w.hist, w.hist, L, w, nullptr, 0, s);
-        k_radix_scatter<<<g, RS_BLOCK, 0, s>>>(K[cur], V[cur], K[cur ^ 1], V[cur ^ 1], n_dev, cap, shift, dmask, w.hist);
-        cur ^= 1;
-    }
-    return cur;
 }
 
 }  // namespace gs
