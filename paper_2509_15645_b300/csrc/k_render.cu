@@ -4,18 +4,21 @@
 //   k_gather_project  gather of the visible Gaussians' D planes with the
 //                     deferred restore (parameter forwarding of §4.2.2 done in
 //                     place), EWA projection, SH colour, opacity -> 48 B splat
-//                     record, depth key and tile count per Gaussian
-//   depth sort        stable radix sort of the visible set by float depth bits
-//   k_emit            (tile id, Gaussian) keys in depth order
-//   tile sort         stable radix sort by tile id: per-tile depth order with
-//                     ties in ascending Gaussian id
-//   k_raster_fwd      one block per tile, one thread per pixel; the tile's
-//                     splats are staged through shared memory in batches and
-//                     composited front to back
-//   k_raster_bwd      recomputes each pixel's transmittance by a forward replay
-//                     over the tile (nothing stored per pixel), then walks the
-//                     list back to front; warp-shuffle reduction before the
-//                     atomics into the per-splat screen-space gradients
+//                     record, depth and tile rectangle per Gaussian
+//   k_tiles_small,    the tiles each splat reaches (the list filter): a count
+//   k_big_counts      per tile, scanned into each tile's first key
+//   k_tiles_small,    (depth, Gaussian) keys into the tiles' lists through
+//   k_big_emit        per-tile cursors
+//   k_tile_sort(_long) each list sorted front to back (depth, ties in
+//                     ascending Gaussian id) by bitonic networks per tile
+//   k_raster_fwd      one tile per block or per warp; the tile's splats are
+//                     staged through shared memory in batches and composited
+//                     front to back
+//   k_raster_bwd      one front-to-back pass per tile that recomputes each
+//                     pixel's transmittance (nothing stored per pixel) and the
+//                     colour behind each splat from the forward's final colour;
+//                     warp-shuffle reductions before the atomics into the
+//                     per-splat screen-space gradients
 //   k_project_bwd     chain rule to mean, log-scale, quaternion, opacity logit
 //                     and SH coefficients
 #include <algorithm>
@@ -97,26 +100,13 @@ __device__ __forceinline__ void tile_box(const DevCam &cam, int t_x, int t_y, fl
 // (k_big_counts, k_big_emit); smaller ones by the splat's own thread.
 constexpr int BIG_RECT = 32;
 
-// One more key for every tile of [x0, x1) x [y0, y1) that splat (r0, r1) reaches.
-__device__ __forceinline__ void count_tiles(float4 r0, float4 r1, int x0, int x1, int y0, int y1, const DevCam &cam,
-                                            uint32_t *tile_cnt)
-{
-    for (int ty = y0; ty < y1; ty++)
-        for (int tx = x0; tx < x1; tx++) {
-            float X0, X1, Y0, Y1;
-            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
-        }
-}
-
 template <int DEG, typename T>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
                                                                const int *n_vis_p, int cap,
                                                                const DevArgs *__restrict__ args, int view,
                                                                float *__restrict__ compact, float4 *__restrict__ rec0,
                                                                float4 *__restrict__ rec1, float4 *__restrict__ rec2,
-                                                               uint32_t *__restrict__ depth,
-                                                               uint32_t *__restrict__ tile_cnt, uint2 *__restrict__ rect,
+                                                               uint32_t *__restrict__ depth, uint2 *__restrict__ rect,
                                                                int *__restrict__ n_fix, int32_t *__restrict__ fix_idx,
                                                                uint8_t *__restrict__ fix_flag, int *__restrict__ n_big,
                                                                int32_t *__restrict__ big_idx)
@@ -212,17 +202,13 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         rec1[k] = r1v;
         rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
         depth[k] = __float_as_uint(P.p[2]);
-        // the key count of each tile the splat reaches (the list filter);
-        // FP64-flagged splats and large rectangles are counted by k_big_counts.
-        // A splat that is not kept gets an empty rectangle, so that counting
-        // and emission (k_emit) see the same partition.
+        // tiles reached: small rectangles are counted and emitted by
+        // k_tiles_small; FP64-flagged splats and large rectangles go to the big
+        // list (k_big_counts, k_big_emit).  A splat that is not kept gets an
+        // empty rectangle, so that every pass sees the same partition.
         if (!P.keep) P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
-        if (P.keep && !P.fp64) {
-            if ((P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2]) <= BIG_RECT)
-                count_tiles(r0v, r1v, P.rect[0], P.rect[1], P.rect[2], P.rect[3], s_cam, tile_cnt);
-            else
-                big_idx[atomicAdd(n_big, 1)] = k;
-        }
+        if (P.keep && !P.fp64 && (P.rect[1] - P.rect[0]) * (P.rect[3] - P.rect[2]) > BIG_RECT)
+            big_idx[atomicAdd(n_big, 1)] = k;
         rect[k] = make_uint2((uint32_t)P.rect[0] | ((uint32_t)P.rect[1] << 16), (uint32_t)P.rect[2] | ((uint32_t)P.rect[3] << 16));
     }
 }
@@ -287,40 +273,83 @@ __global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__re
     }
 }
 
-// Keys of the visible splats into their tiles' lists: for each tile t the
-// splat reaches, (depth, k) goes to slot tile_off[t] + (a cursor of t), so a
-// tile's list is complete but unordered until k_tile_sort.  Small rectangles
-// by the splat's thread (the partition of k_gather_project's counting: kept,
-// not FP64-flagged, at most BIG_RECT tiles); the big list by k_big_emit.
-__global__ void k_emit(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                       const float4 *__restrict__ rec1, const uint32_t *__restrict__ depth,
-                       const uint8_t *__restrict__ fix_flag, const int *n_vis_p, int cap, int64_t kcap,
-                       const DevArgs *__restrict__ args, int view, const uint32_t *__restrict__ tile_off,
-                       uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
+// The small rectangles' (splat, tile) pairs, load-balanced over a warp: the
+// warp takes 32 splats (kept, not FP64-flagged, at most BIG_RECT tiles: the
+// partition k_gather_project leaves to it), scans their rectangle areas, and
+// its lanes walk the concatenated pairs 32 at a time, so that the atomics of
+// different pairs are in flight together.  EMIT = false: one more key for each
+// tile reached; EMIT = true: the key (depth, k) into the tile's list at slot
+// tile_off[t] + (a cursor of t), complete but unordered until k_tile_sort.
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
+                                                     const float4 *__restrict__ rec1,
+                                                     const uint32_t *__restrict__ depth,
+                                                     const uint8_t *__restrict__ fix_flag, const int *n_vis_p, int cap,
+                                                     int64_t kcap, const DevArgs *__restrict__ args, int view,
+                                                     uint32_t *tile_cnt, const uint32_t *__restrict__ tile_off,
+                                                     uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
 {
     const int n = min(*n_vis_p, cap);
     const DevCam &cam = args->cam[view];
     const int tiles_x = cam.tiles_x;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (fix_flag[k]) continue;
-        const uint2 rc = rect[k];
-        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
-        const int area = (x1 - x0) * (y1 - y0);
-        if (area <= 0 || area > BIG_RECT) continue;
-        const float4 r0 = rec0[k], r1 = rec1[k];
-        const uint32_t dk = depth[k];
-        for (int ty = y0; ty < y1; ty++)
-            for (int tx = x0; tx < x1; tx++) {
-                float X0, X1, Y0, Y1;
-                tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-                if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
-                const int t = ty * tiles_x + tx;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nwarps) {
+        const int k = g * 32 + lane;
+        uint2 rc = make_uint2(0u, 0u);
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        uint32_t dk = 0u;
+        int area = 0;
+        if (k < n && !fix_flag[k]) {
+            rc = rect[k];
+            area = (int)((rc.x >> 16) - (rc.x & 0xffff)) * (int)((rc.y >> 16) - (rc.y & 0xffff));
+            if (area > 0 && area <= BIG_RECT) {
+                r0 = rec0[k];
+                r1 = rec1[k];
+                if (EMIT) dk = depth[k];
+            } else {
+                area = 0;
+            }
+        }
+        int incl = area;                                  // inclusive scan of the areas over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int ex = incl - area, total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int q0 = 0; q0 < total; q0 += 32) {
+            const int q = q0 + lane;
+            int sl = 0;                                   // the last lane whose pairs start at or before q
+#pragma unroll
+            for (int st = 16; st; st >>= 1) {
+                const int c = sl + st;
+                if (__shfl_sync(0xffffffffu, ex, c) <= q) sl = c;
+            }
+            const uint32_t rcx = __shfl_sync(0xffffffffu, rc.x, sl), rcy = __shfl_sync(0xffffffffu, rc.y, sl);
+            const float4 a0 = make_float4(__shfl_sync(0xffffffffu, r0.x, sl), __shfl_sync(0xffffffffu, r0.y, sl),
+                                          __shfl_sync(0xffffffffu, r0.z, sl), __shfl_sync(0xffffffffu, r0.w, sl));
+            const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
+                                          __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
+            const int exs = __shfl_sync(0xffffffffu, ex, sl);
+            const uint32_t dks = EMIT ? __shfl_sync(0xffffffffu, dk, sl) : 0u;
+            if (q >= total) continue;
+            const int x0 = (int)(rcx & 0xffff), wdt = (int)(rcx >> 16) - x0, y0 = (int)(rcy & 0xffff);
+            const int j = q - exs, tx = x0 + j % wdt, ty = y0 + j / wdt;
+            float X0, X1, Y0, Y1;
+            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+            if (!splat_reaches_box(a0, a1, X0, X1, Y0, Y1)) continue;
+            const int t = ty * tiles_x + tx;
+            if (!EMIT) {
+                atomicAdd(tile_cnt + t, 1u);
+            } else {
                 const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
                 if (p < kcap) {
-                    bkey[p] = dk;
-                    bval[p] = (uint32_t)k;
+                    bkey[p] = dks;
+                    bval[p] = (uint32_t)(g * 32 + sl);
                 }
             }
+        }
     }
 }
 
@@ -445,7 +474,7 @@ __device__ __forceinline__ void warp_sort_list(const uint32_t *__restrict__ bkey
 }
 
 constexpr int SORT_WARP_MAX = 256;       // lists up to this length: one warp, in registers
-constexpr int SORT_SMEM_MAX = 8192;      // longer ones up to this: one block, in shared memory
+constexpr int SORT_SMEM_MAX = 2048;      // longer ones up to this: one block, in shared memory (16 KB)
 
 // One warp per tile: the tile's range, and its list sorted into (tile, splat)
 // order when it has at most SORT_WARP_MAX keys; longer lists are queued for
@@ -561,7 +590,7 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
 
 
 // Stage the tile's list entries [b, b + cnt) into shared memory (the lists
-// hold only splats that can reach the tile: k_tile_counts / k_emit).
+// hold only splats that can reach the tile: k_tiles_small / k_big_emit).
 // WT: the staging belongs to one warp (warp-tile rasterizers), else to the block.
 template <bool COLOR, bool INDEX, bool WT = false>
 __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
@@ -1241,18 +1270,22 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);
     cudaMemsetAsync(rb.tile_cnt, 0, (size_t)(tiles + 1) * sizeof(uint32_t), s);
     cudaMemsetAsync(rb.tile_cur, 0, (size_t)tiles * sizeof(uint32_t), s);
-    // gather, projection, and the key count of every tile (small rectangles)
+    // gather and projection
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
-                                                          rb.rec2, rb.depth, rb.tile_cnt, rb.rect, rb.n_fix,
-                                                          rb.fix_idx, rb.fix_flag, rb.n_big, rb.big_idx);
+                                                          rb.rec2, rb.depth, rb.rect, rb.n_fix, rb.fix_idx,
+                                                          rb.fix_flag, rb.n_big, rb.big_idx);
     k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
                                                     rb.rect, rb.n_big, rb.big_idx);
+    // the key count of every tile
+    const int gsm = w.grid((int64_t)(cap + 31) / 32 * 32, 256);
+    k_tiles_small<false><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
+                                             view, rb.tile_cnt, nullptr, nullptr, nullptr, nullptr);
     k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
                                                rb.tile_cnt);
     // each tile's first key (and the key total), then the keys into their tiles' lists
     scan_counts(rb.tile_cnt, tiles + 1, rb.n_keys, (int)rb.kcap, w, s);
-    k_emit<<<w.grid(cap, 256), 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
-                                            view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
+    k_tiles_small<true><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
+                                            view, nullptr, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
     k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.n_big, rb.big_idx, cap, rb.kcap,
                                              args, view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
     // front-to-back order within each tile, and the tiles' ranges
@@ -1265,7 +1298,7 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
                              (int)(SORT_SMEM_MAX * sizeof(unsigned long long)));
         long_attr = true;
     }
-    k_tile_sort_long<<<w.num_sms * 2, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
+    k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
         rb.tile_cnt, rb.kcap, rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_big + 1, rb.long_tiles);
     rb.sorted_keys = rb.tk[1];
     rb.sorted_vals = rb.tv[1];
