@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <array>
 #include <vector>
 
 #include "gs_kernels.cuh"
@@ -91,6 +92,16 @@ struct gs_ctx {
     cudaEvent_t ev_down[2] = {nullptr, nullptr};
     struct Run { int64_t chunk0, slot0, nchunks; };
     std::vector<Run> runs;              // copy runs of the last host-tier step
+    // ring halves between consecutive host-tier steps: the previous step's
+    // visible chunks (slot, or -1) and staged chunks, the half it used
+    std::vector<int32_t> pvslot;
+    std::vector<uint8_t> pstaged;
+    int parity = 0;
+    bool prev_full = true;              // the previous step used the whole ring (or there was none)
+    const void *pscene = nullptr;
+    int64_t pn = 0;
+    cudaEvent_t ev_half[2] = {nullptr, nullptr};   // write-backs of the last step that used half 0 / 1 done
+    cudaEvent_t ev_sdone = nullptr;     // the previous host-tier step's work on its stream done
     int64_t last_touched = 0, last_bytes = 0;
     char err[512] = {0};
 };
@@ -446,7 +457,10 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
             cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_down[0], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_down[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_down[1], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_half[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_half[1], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_sdone, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             gs_destroy(c);
             return GS_ERR_CUDA;
@@ -465,7 +479,8 @@ gs_status gs_destroy(gs_ctx *c)
     timing_free(c);
     if (c->cstream) cudaStreamSynchronize(c->cstream);
     if (c->dstream) cudaStreamSynchronize(c->dstream);
-    for (cudaEvent_t e : {c->ev_vis, c->ev_upd, c->ev_done, c->ev_end, c->ev_down[0], c->ev_down[1]})
+    for (cudaEvent_t e : {c->ev_vis, c->ev_upd, c->ev_done, c->ev_end, c->ev_down[0], c->ev_down[1], c->ev_half[0],
+                          c->ev_half[1], c->ev_sdone})
         if (e) cudaEventDestroy(e);
     if (c->cstream) cudaStreamDestroy(c->cstream);
     if (c->dstream) cudaStreamDestroy(c->dstream);
@@ -966,6 +981,21 @@ static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, siz
     }
 }
 
+// Device copies of staged chunks from the previous step's slots (w, m, v):
+// runs of chunks whose source and destination slots are both consecutive.
+static void copy_slots(gs_ctx *c, const gs_scene *scene, const SceneView &sv,
+                       const std::vector<std::array<int64_t, 3>> &druns, cudaStream_t s)
+{
+    const int64_t eb = elem_bytes(scene->precision), R = 1ll << c->shift;
+    const int64_t planes = sv.D - N_GEO, ring = sv.sh.ppitch;
+    for (const auto &r : druns)                  // {source slot, destination slot, chunks}
+        for (int j = 0; j < 3; j++) {
+            char *base = (char *)c->stage[j];
+            cudaMemcpy2DAsync(base + r[1] * R * eb, ring * eb, base + r[0] * R * eb, ring * eb, r[2] * R * eb, planes,
+                              cudaMemcpyDeviceToDevice, s);
+        }
+}
+
 // gs_step for a host-tier scene (§4.2 selective offloading, SH rows
 // streamed).  On the stream: cull and the chunk-touch map, then one host
 // synchronisation to read the map.  Chunks with visible Gaussians take the
@@ -1000,35 +1030,66 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     const int64_t nch = (sv.n + (1ll << c->shift) - 1) >> c->shift;
     cudaMemcpyAsync(c->htouch, c->dtouch, nch, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "host tier: touch map");
+    // the previous step's work is done (at once when it ran on this stream):
+    // its slot table copy has landed and its slots hold their final values
+    if (cudaEventSynchronize(c->ev_sdone) != cudaSuccess) return cuda_check(c, "host tier: previous step");
 
-    // plan: visible chunks -> slots [0, nv); optimizer-only chunks -> rounds of
-    // at most `rcap` chunks, cut at chunk-id boundaries, round k in slots
-    // nv + (k % nbuf) * rcap + [0, rcap)
+    // history of the previous host-tier step on this scene (reset otherwise)
+    if (c->pscene != scene->host_sh || c->pn != sv.n || (int64_t)c->pvslot.size() != nch) {
+        c->pvslot.assign(nch, -1);
+        c->pstaged.assign(nch, 0);
+        c->prev_full = true;
+        c->pscene = scene->host_sh;
+        c->pn = sv.n;
+    }
     int64_t nv = 0, nu = 0;
     for (int64_t ch = 0; ch < nch; ch++) {
-        if (c->htouch[ch] == 2) c->hslot[ch] = (int32_t)nv++;
+        if (c->htouch[ch] == 2) nv++;
         else if (c->htouch[ch] == 1) nu++;
-        else c->hslot[ch] = -1;
     }
-    const int64_t cap = c->cfg.stage_chunks - nv;
+    // Ring halves: a step whose chunks fit in half of the ring uses the half
+    // the previous step did not, so its H2D need not wait for the previous
+    // step's write-backs (only for those of the step before, normally long
+    // done).  Its chunks that the previous step had visible are copied from
+    // their slots on the device (the previous step's apply is ordered before
+    // this step on the stream); those the previous step staged only for the
+    // optimizer come from the host after the previous write-backs.  Otherwise
+    // the whole ring after every write-back, as for the first step.
+    const int64_t H = c->cfg.stage_chunks / 2;
+    const bool half = H >= 1 && nv <= H && (nu == 0 || H - nv >= 1);
+    const int p = half ? c->parity : 0;
+    const int64_t base = half ? p * H : 0, ring_chunks = half ? H : c->cfg.stage_chunks;
+    const bool reuse = half && !c->prev_full;      // device copies from the previous step's visible slots
+    // plan: visible chunks -> slots base + [0, nv); optimizer-only chunks ->
+    // rounds of at most `rcap` chunks, cut at chunk-id boundaries, round k in
+    // slots base + nv + (k % nbuf) * rcap + [0, rcap)
+    {
+        int64_t q = 0;
+        for (int64_t ch = 0; ch < nch; ch++) {
+            if (c->htouch[ch] == 2) c->hslot[ch] = (int32_t)(base + q++);
+            else c->hslot[ch] = -1;
+        }
+    }
+    const int64_t cap = ring_chunks - nv;
     if (nv > c->cfg.stage_chunks || (nu > 0 && cap < 1))
         return fail(c, GS_ERR_CAPACITY, "host tier: %lld chunks of visible Gaussians, staging ring holds %lld",
                     (long long)nv + (nu > 0), (long long)c->cfg.stage_chunks);
     const int64_t nbuf = cap >= 2 ? 2 : 1, rcap = nu > 0 ? cap / nbuf : 1;
-    struct Round { int64_t ch_lo, ch_hi; size_t vis_lo, vis_hi, upd_lo, upd_hi; };
+    struct Round { int64_t ch_lo, ch_hi; size_t vis_lo, vis_hi, upd_lo, upd_hi; bool late; };
     std::vector<Round> rounds;
     {
-        Round r{0, nch, 0, 0, 0, 0};
+        Round r{0, nch, 0, 0, 0, 0, false};
         int64_t in_round = 0;
         for (int64_t ch = 0; ch < nch; ch++) {
             if (c->htouch[ch] != 1) continue;
             if (in_round == rcap) {           // close the round before this chunk
                 r.ch_hi = ch;
                 rounds.push_back(r);
-                r = Round{ch, nch, 0, 0, 0, 0};
+                r = Round{ch, nch, 0, 0, 0, 0, false};
                 in_round = 0;
             }
-            c->hslot[ch] = (int32_t)(nv + ((int64_t)rounds.size() % nbuf) * rcap + in_round);
+            c->hslot[ch] = (int32_t)(base + nv + ((int64_t)rounds.size() % nbuf) * rcap + in_round);
+            r.late |= c->pstaged[ch] != 0;    // its host rows are current once the previous write-backs land
             in_round++;
         }
         rounds.push_back(r);
@@ -1042,13 +1103,35 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
         else
             c->runs.push_back(gs_ctx::Run{ch, slot, 1});
     };
-    for (Round &r : rounds) {             // visible chunks, runs split at round boundaries
+    // visible chunks by source: device copies, host rows now, host rows after
+    // the previous write-backs; their write-back runs are split at round
+    // boundaries
+    std::vector<std::array<int64_t, 3>> druns;
+    auto src_class = [&](int64_t ch) {
+        if (reuse && c->pvslot[ch] >= 0) return 0;
+        return c->pstaged[ch] ? 2 : 1;
+    };
+    for (int64_t ch = 0; ch < nch; ch++) {
+        if (c->htouch[ch] != 2 || src_class(ch) != 0) continue;
+        const int64_t src = c->pvslot[ch], dst = c->hslot[ch];
+        if (!druns.empty() && druns.back()[0] + druns.back()[2] == src && druns.back()[1] + druns.back()[2] == dst)
+            druns.back()[2]++;
+        else
+            druns.push_back({src, dst, 1});
+    }
+    const size_t now_lo = c->runs.size();
+    for (int64_t ch = 0; ch < nch; ch++)
+        if (c->htouch[ch] == 2 && src_class(ch) == 1) add_run(ch, now_lo);
+    const size_t late_lo = c->runs.size();
+    for (int64_t ch = 0; ch < nch; ch++)
+        if (c->htouch[ch] == 2 && src_class(ch) == 2) add_run(ch, late_lo);
+    const size_t late_hi = c->runs.size();
+    for (Round &r : rounds) {             // visible chunks again, for the write-backs
         r.vis_lo = c->runs.size();
         for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
             if (c->htouch[ch] == 2) add_run(ch, r.vis_lo);
         r.vis_hi = c->runs.size();
     }
-    const size_t n_vis_runs = c->runs.size();
     for (Round &r : rounds) {             // optimizer-only chunks
         r.upd_lo = c->runs.size();
         for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
@@ -1058,11 +1141,19 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     c->last_touched = nv + nu;
     c->last_bytes = 0;
     cudaMemcpyAsync(c->dslot, c->hslot, nch * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    // after the previous step's write-backs (also when it ran on another
-    // stream): the ring and the host rows are free and current.  The render
-    // needs all three arrays (its deferred restore of SH rows reads m and v).
-    cudaStreamWaitEvent(c->cstream, c->ev_end, 0);
-    copy_runs(c, scene, sv, 0, n_vis_runs, true);
+    cudaEvent_t prev_done = c->ev_end;            // the previous step's write-backs
+    if (half && !c->prev_full) {
+        // this half was last written back by the step before the previous one
+        cudaStreamWaitEvent(c->cstream, c->ev_half[p], 0);
+        cudaStreamWaitEvent(s, c->ev_half[p], 0);
+        copy_slots(c, scene, sv, druns, s);
+    } else {
+        cudaStreamWaitEvent(c->cstream, c->ev_end, 0);
+    }
+    copy_runs(c, scene, sv, now_lo, late_lo, true);
+    cudaStreamWaitEvent(c->cstream, prev_done, 0);
+    copy_runs(c, scene, sv, late_lo, late_hi, true);
+    // the render needs all three arrays (its deferred restore of SH rows reads m and v)
     cudaEventRecord(c->ev_vis, c->cstream);
     cudaStreamWaitEvent(s, c->ev_vis, 0);
     enqueue_render_phase(c, sv, a, n_views, M, loss, s);
@@ -1078,6 +1169,7 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
         const Round &r = rounds[k];
         // the ring half this round fills was written back by round k - nbuf
         if ((int64_t)k >= nbuf) cudaStreamWaitEvent(c->cstream, c->ev_down[k % nbuf], 0);
+        if (r.late) cudaStreamWaitEvent(c->cstream, prev_done, 0);
         copy_runs(c, scene, sv, r.upd_lo, r.upd_hi, true);
         cudaEventRecord(c->ev_upd, c->cstream);
         cudaStreamWaitEvent(s, c->ev_upd, 0);
@@ -1094,7 +1186,21 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     }
     c->w.mark(TP_ADAM1, s);
     c->w.mark(TP_STEP1, s);
+    cudaEventRecord(c->ev_sdone, s);
     cudaEventRecord(c->ev_end, c->dstream);
+    if (half) {
+        cudaEventRecord(c->ev_half[p], c->dstream);
+    } else {
+        cudaEventRecord(c->ev_half[0], c->dstream);
+        cudaEventRecord(c->ev_half[1], c->dstream);
+    }
+    // history for the next step
+    for (int64_t ch = 0; ch < nch; ch++) {
+        c->pvslot[ch] = c->htouch[ch] == 2 ? c->hslot[ch] : -1;
+        c->pstaged[ch] = c->htouch[ch] != 0;
+    }
+    c->prev_full = !half;
+    if (half) c->parity ^= 1;
     if (c->w.tev) c->t_used++;
     return cuda_check(c, "gs_step host tier");
 }
