@@ -80,7 +80,11 @@ enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
  * of 2^chunk_shift Gaussians that a step touches (the visible ones and the
  * optimizer's update set) into the context's staging ring with
  * cudaMemcpy2DAsync on one side stream and the updated rows back on another,
- * so both PCIe directions run at once.  The last write-backs of a step run
+ * so both PCIe directions run at once; consecutive steps alternate between the
+ * two halves of the ring when a step's chunks fit in one (a chunk the previous
+ * step had visible is then copied between the halves on the device).  A step
+ * synchronises the host once, for its chunk map, and waits for the previous
+ * step's work if that ran on another stream.  The last write-backs of a step run
  * on past the end of its work on `stream` (overlapping the next step's cull);
  * gs_wait_copies makes a stream wait for them, gs_sync_status waits for them
  * on the host, and the next gs_step orders its own copies after them. */
