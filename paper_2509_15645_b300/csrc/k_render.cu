@@ -535,7 +535,9 @@ __global__ void __launch_bounds__(256) k_tile_sort_long(const uint32_t *__restri
     for (int q = blockIdx.x; q < nl; q += gridDim.x) {
         const int t = long_tiles[q];
         const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
-        const int L = (int)(hi - lo);
+        const int64_t L64 = hi - lo;
+        if (L64 > (1 << 30)) continue;                   // beyond any workspace; the list stays unsorted
+        const int L = (int)L64;
         int P = 1;
         while (P < L) P <<= 1;
         const bool in_smem = P <= SORT_SMEM_MAX;
