@@ -208,8 +208,9 @@ GS_API gs_status gs_cull(gs_ctx *ctx, const gs_scene *scene, const gs_camera *ca
 
 /* Render one view (§2.4 steps 1-3) of the Gaussians ids[0..*n_vis) (device,
  * ascending, from gs_cull): gather with restore (as gs_cull), projection and
- * SH colour, tile keys, depth/tile sort, front-to-back compositing on a black
- * background.  image_out (device fp32 [3][H][W]).  The context keeps what the
+ * SH colour, each tile's list of the splats that can reach it sorted by depth
+ * (ties by Gaussian id), front-to-back compositing on a black background.
+ * image_out (device fp32 [3][H][W]).  The context keeps what the
  * backward needs (compact parameters, splats, sorted keys, tile ranges) until
  * the next gs_render_fwd. */
 GS_API gs_status gs_render_fwd(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
