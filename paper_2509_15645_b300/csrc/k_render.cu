@@ -318,6 +318,9 @@ __global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ r
             if (lane >= o) incl += y;
         }
         const int ex = incl - area, total = __shfl_sync(0xffffffffu, incl, 31);
+        // j / width as (j * ceil(2^16 / width)) >> 16: exact for j * width < 2^16 (here j < 32, width <= 32)
+        const int wd = area ? (int)((rc.x >> 16) - (rc.x & 0xffff)) : 1;
+        const uint32_t inv = (65536u + (uint32_t)wd - 1u) / (uint32_t)wd;
         for (int q0 = 0; q0 < total; q0 += 32) {
             const int q = q0 + lane;
             int sl = 0;                                   // the last lane whose pairs start at or before q
@@ -332,10 +335,12 @@ __global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ r
             const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
                                           __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
             const int exs = __shfl_sync(0xffffffffu, ex, sl);
+            const uint32_t invs = __shfl_sync(0xffffffffu, inv, sl);
             const uint32_t dks = EMIT ? __shfl_sync(0xffffffffu, dk, sl) : 0u;
             if (q >= total) continue;
             const int x0 = (int)(rcx & 0xffff), wdt = (int)(rcx >> 16) - x0, y0 = (int)(rcy & 0xffff);
-            const int j = q - exs, tx = x0 + j % wdt, ty = y0 + j / wdt;
+            const int j = q - exs, row = (int)(((uint32_t)j * invs) >> 16);
+            const int tx = x0 + (j - row * wdt), ty = y0 + row;
             float X0, X1, Y0, Y1;
             tile_box(cam, tx, ty, X0, X1, Y0, Y1);
             if (!splat_reaches_box(a0, a1, X0, X1, Y0, Y1)) continue;
