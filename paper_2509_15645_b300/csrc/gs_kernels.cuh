@@ -174,6 +174,13 @@ struct RasterJob {
 };
 
 constexpr int N_RASTER_VARIANTS = 8;
+
+// k_lists.cu: rectangles of more tiles than this are counted and emitted by a
+// warp each (the big list the gather fills); smaller ones by a warp's lanes
+// over the concatenated (splat, tile) pairs of 32 splats.
+constexpr int BIG_RECT = 32;
+void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBufs &rb, int tiles, Work &w,
+                      cudaStream_t s);
 bool raster_variant_ok(int v, int tile_w, int tile_h);
 
 void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,

@@ -5,12 +5,8 @@
 //                     deferred restore (parameter forwarding of §4.2.2 done in
 //                     place), EWA projection, SH colour, opacity -> 48 B splat
 //                     record, depth and tile rectangle per Gaussian
-//   k_tiles_small,    the tiles each splat reaches (the list filter): a count
-//   k_big_counts      per tile, scanned into each tile's first key
-//   k_tiles_small,    (depth, Gaussian) keys into the tiles' lists through
-//   k_big_emit        per-tile cursors
-//   k_tile_sort(_long) each list sorted front to back (depth, ties in
-//                     ascending Gaussian id) by bitonic networks per tile
+//   (k_lists.cu)      each tile's list of the splats that can reach it,
+//                     sorted front to back
 //   k_raster_fwd      one tile per block or per warp; the tile's splats are
 //                     staged through shared memory in batches and composited
 //                     front to back
@@ -34,71 +30,6 @@ struct SLutR {
     float eps;
     int restore;
 };
-
-// Can splat (r0, r1) reach alpha >= 1/255 at any pixel centre of the box
-// [X0, X1] x [Y0, Y1]?  Intersects the box with the splat's square (widened
-// by a small margin), takes the minimum of sigma over the remaining rectangle
-// (zero if the mean is inside, otherwise on an edge, where sigma is a 1-D
-// quadratic) and compares o exp(-sigma_min) with the floor, with 0.1% slack.
-// It only ever says "no" when no pixel can pass the per-pixel tests, so
-// dropping such splats leaves every pixel's result unchanged.
-// Every operation is an explicitly rounded intrinsic (no contraction into FMAs
-// that could differ between the kernels that inline it): the key counting and
-// the key emission, in different kernels, must take the same decisions.
-__device__ __forceinline__ float q_sigma(float A, float B, float C, float dx, float dy)
-{
-    // 0.5 (A dx^2 + C dy^2) + B dx dy
-    const float a = __fmul_rn(__fmul_rn(A, dx), dx), c = __fmul_rn(__fmul_rn(C, dy), dy);
-    return __fadd_rn(__fmul_rn(0.5f, __fadd_rn(a, c)), __fmul_rn(__fmul_rn(B, dx), dy));
-}
-
-__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
-{
-    const float margin = 1e-3f;
-    const float ext = __fadd_rn(r0.z, margin);
-    const float x0 = fmaxf(X0, __fsub_rn(r0.x, ext)), x1 = fminf(X1, __fadd_rn(r0.x, ext));
-    const float y0 = fmaxf(Y0, __fsub_rn(r0.y, ext)), y1 = fminf(Y1, __fadd_rn(r0.y, ext));
-    if (x0 > x1 || y0 > y1) return false;
-    // d = mean - p over the rectangle
-    const float dxl = __fsub_rn(r0.x, x1), dxh = __fsub_rn(r0.x, x0);
-    const float dyl = __fsub_rn(r0.y, y1), dyh = __fsub_rn(r0.y, y0);
-    const float A = r1.x, B = r1.y, C = r1.z;
-    float smin = 0.f;
-    if (!(dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f)) {
-        smin = 3.4e38f;
-        // edges dx = const: minimiser dy = -B dx / C
-        const float dxs[2] = {dxl, dxh};
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const float dx = dxs[k];
-            const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dx), C), dyl), dyh);
-            smin = fminf(smin, q_sigma(A, B, C, dx, dy));
-        }
-        const float dys[2] = {dyl, dyh};
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const float dy = dys[k];
-            const float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dy), A), dxl), dxh);
-            smin = fminf(smin, q_sigma(A, B, C, dx, dy));
-        }
-        smin = fmaxf(smin, 0.f);
-    }
-    return __fmul_rn(r0.w, __expf(-smin)) >= ALPHA_MIN * 0.999f;
-}
-
-// Pixel-centre box of tile (t_x, t_y).
-__device__ __forceinline__ void tile_box(const DevCam &cam, int t_x, int t_y, float &X0, float &X1, float &Y0,
-                                         float &Y1)
-{
-    X0 = (float)(t_x * cam.tile_w) + 0.5f;
-    X1 = X0 + (float)(cam.tile_w - 1);
-    Y0 = (float)(t_y * cam.tile_h) + 0.5f;
-    Y1 = Y0 + (float)(cam.tile_h - 1);
-}
-
-// Rectangles of more tiles than this are counted and emitted by a warp
-// (k_big_counts, k_big_emit); smaller ones by the splat's own thread.
-constexpr int BIG_RECT = 32;
 
 template <int DEG, typename T>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
@@ -245,335 +176,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_fix_project(const float *__restr
     }
 }
 
-
-// Tiles reached by the splats of the big list (large rectangles, FP64-fixed
-// splats): one warp per splat, lanes over the rectangle's tiles.
-__global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
-                             const uint2 *__restrict__ rect, const int *__restrict__ n_big,
-                             const int32_t *__restrict__ big_idx, int cap, const DevArgs *__restrict__ args, int view,
-                             uint32_t *__restrict__ tile_cnt)
-{
-    const int nb = min(*n_big, cap);
-    const DevCam &cam = args->cam[view];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nwarps) {
-        const int k = big_idx[j];
-        const uint2 rc = rect[k];
-        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
-        const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
-        if (cnt_all <= 0) continue;
-        const float4 r0 = rec0[k], r1 = rec1[k];
-        for (int t = lane; t < cnt_all; t += 32) {
-            const int tx = x0 + t % wdt, ty = y0 + t / wdt;
-            float X0, X1, Y0, Y1;
-            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
-        }
-    }
-}
-
-// The small rectangles' (splat, tile) pairs, load-balanced over a warp: the
-// warp takes 32 splats (kept, not FP64-flagged, at most BIG_RECT tiles: the
-// partition k_gather_project leaves to it), scans their rectangle areas, and
-// its lanes walk the concatenated pairs 32 at a time, so that the atomics of
-// different pairs are in flight together.  EMIT = false: one more key for each
-// tile reached; EMIT = true: the key (depth, k) into the tile's list at slot
-// tile_off[t] + (a cursor of t), complete but unordered until k_tile_sort.
-template <bool EMIT>
-__global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                                                     const float4 *__restrict__ rec1,
-                                                     const uint32_t *__restrict__ depth,
-                                                     const uint8_t *__restrict__ fix_flag, const int *n_vis_p, int cap,
-                                                     int64_t kcap, const DevArgs *__restrict__ args, int view,
-                                                     uint32_t *tile_cnt, const uint32_t *__restrict__ tile_off,
-                                                     uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
-{
-    const int n = min(*n_vis_p, cap);
-    const DevCam &cam = args->cam[view];
-    const int tiles_x = cam.tiles_x;
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nwarps) {
-        const int k = g * 32 + lane;
-        uint2 rc = make_uint2(0u, 0u);
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        uint32_t dk = 0u;
-        int area = 0;
-        if (k < n && !fix_flag[k]) {
-            rc = rect[k];
-            area = (int)((rc.x >> 16) - (rc.x & 0xffff)) * (int)((rc.y >> 16) - (rc.y & 0xffff));
-            if (area > 0 && area <= BIG_RECT) {
-                r0 = rec0[k];
-                r1 = rec1[k];
-                if (EMIT) dk = depth[k];
-            } else {
-                area = 0;
-            }
-        }
-        int incl = area;                                  // inclusive scan of the areas over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int ex = incl - area, total = __shfl_sync(0xffffffffu, incl, 31);
-        // j / width as (j * ceil(2^16 / width)) >> 16: exact for j * width < 2^16 (here j < 32, width <= 32)
-        const int wd = area ? (int)((rc.x >> 16) - (rc.x & 0xffff)) : 1;
-        const uint32_t inv = (65536u + (uint32_t)wd - 1u) / (uint32_t)wd;
-        for (int q0 = 0; q0 < total; q0 += 32) {
-            const int q = q0 + lane;
-            int sl = 0;                                   // the last lane whose pairs start at or before q
-#pragma unroll
-            for (int st = 16; st; st >>= 1) {
-                const int c = sl + st;
-                if (__shfl_sync(0xffffffffu, ex, c) <= q) sl = c;
-            }
-            const uint32_t rcx = __shfl_sync(0xffffffffu, rc.x, sl), rcy = __shfl_sync(0xffffffffu, rc.y, sl);
-            const float4 a0 = make_float4(__shfl_sync(0xffffffffu, r0.x, sl), __shfl_sync(0xffffffffu, r0.y, sl),
-                                          __shfl_sync(0xffffffffu, r0.z, sl), __shfl_sync(0xffffffffu, r0.w, sl));
-            const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
-                                          __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
-            const int exs = __shfl_sync(0xffffffffu, ex, sl);
-            const uint32_t invs = __shfl_sync(0xffffffffu, inv, sl);
-            const uint32_t dks = EMIT ? __shfl_sync(0xffffffffu, dk, sl) : 0u;
-            if (q >= total) continue;
-            const int x0 = (int)(rcx & 0xffff), wdt = (int)(rcx >> 16) - x0, y0 = (int)(rcy & 0xffff);
-            const int j = q - exs, row = (int)(((uint32_t)j * invs) >> 16);
-            const int tx = x0 + (j - row * wdt), ty = y0 + row;
-            float X0, X1, Y0, Y1;
-            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (!splat_reaches_box(a0, a1, X0, X1, Y0, Y1)) continue;
-            const int t = ty * tiles_x + tx;
-            if (!EMIT) {
-                atomicAdd(tile_cnt + t, 1u);
-            } else {
-                const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
-                if (p < kcap) {
-                    bkey[p] = dks;
-                    bval[p] = (uint32_t)(g * 32 + sl);
-                }
-            }
-        }
-    }
-}
-
-// The keys of the big list: one warp per splat, lanes over its tiles.
-__global__ void k_big_emit(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                           const float4 *__restrict__ rec1, const uint32_t *__restrict__ depth,
-                           const int *__restrict__ n_big, const int32_t *__restrict__ big_idx, int cap, int64_t kcap,
-                           const DevArgs *__restrict__ args, int view, const uint32_t *__restrict__ tile_off,
-                           uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
-{
-    const int nb = min(*n_big, cap);
-    const DevCam &cam = args->cam[view];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nwarps) {
-        const int k = big_idx[j];
-        const uint2 rc = rect[k];
-        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
-        const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
-        if (cnt_all <= 0) continue;
-        const float4 r0 = rec0[k], r1 = rec1[k];
-        const uint32_t dk = depth[k];
-        for (int tt = lane; tt < cnt_all; tt += 32) {
-            const int tx = x0 + tt % wdt, ty = y0 + tt / wdt;
-            float X0, X1, Y0, Y1;
-            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
-            const int t = ty * cam.tiles_x + tx;
-            const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
-            if (p < kcap) {
-                bkey[p] = dk;
-                bval[p] = (uint32_t)k;
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Per-tile sort of the lists into front-to-back order: by depth, ties by the
-// splat's index (ascending ids: the visible set is compacted in id order), the
-// order of one global sort on (tile, depth, id).  Keys are (depth bits << 32 |
-// splat): depths are positive, so their bits order as unsigned integers.  All
-// sorts are bitonic networks whose every comparator puts the minimum at the
-// lower index (the first step of each merge compares mirrored positions), so
-// a list padded with +inf needs no direction changes.
-
-__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
-
-// N keys in a warp (N = 32, 64, 128 or 256): element e = 32 r + lane held in
-// v[r].  Pairs within a row are exchanged through shuffles, pairs across rows
-// stay in the lane's registers.
-template <int N>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[N / 32], int lane)
-{
-    constexpr int R = N / 32;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-        // first step of the merge: e pairs with its mirror in the block of k
-        if (k <= 32) {
-            const bool lower = (lane & (k >> 1)) == 0;
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], k - 1);
-                v[r] = lower ? umin64(v[r], p) : umax64(v[r], p);
-            }
-        } else {
-            const int rm = (k >> 5) - 1;                  // mirror: row r ^ rm, lane ^ 31
-            unsigned long long p[R];
-#pragma unroll
-            for (int r = 0; r < R; r++) p[r] = __shfl_xor_sync(0xffffffffu, v[r ^ rm], 31);
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                // the lower element of the pair is the one in the lower half of the block of k
-                const bool lower = ((r * 32) & (k >> 1)) == 0;
-                v[r] = lower ? umin64(v[r], p[r]) : umax64(v[r], p[r]);
-            }
-        }
-        // then pairs at distance j = k/4, ..., 1
-#pragma unroll
-        for (int j = k >> 2; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int rj = j >> 5;
-#pragma unroll
-                for (int r = 0; r < R; r++)
-                    if ((r & rj) == 0) {
-                        const unsigned long long x = v[r], y = v[r | rj];
-                        v[r] = umin64(x, y);
-                        v[r | rj] = umax64(x, y);
-                    }
-            } else {
-                const bool lower = (lane & j) == 0;
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    const unsigned long long p = __shfl_xor_sync(0xffffffffu, v[r], j);
-                    v[r] = lower ? umin64(v[r], p) : umax64(v[r], p);
-                }
-            }
-        }
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void warp_sort_list(const uint32_t *__restrict__ bkey, const uint32_t *__restrict__ bval,
-                                               int64_t lo, int L, uint32_t t, uint32_t *skey, uint32_t *sval, int lane)
-{
-    unsigned long long v[N / 32];
-#pragma unroll
-    for (int r = 0; r < N / 32; r++) {
-        const int e = r * 32 + lane;
-        v[r] = e < L ? ((unsigned long long)bkey[lo + e] << 32 | bval[lo + e]) : ~0ull;
-    }
-    warp_bitonic<N>(v, lane);
-#pragma unroll
-    for (int r = 0; r < N / 32; r++) {
-        const int e = r * 32 + lane;
-        if (e < L) {
-            skey[lo + e] = t;
-            sval[lo + e] = (uint32_t)v[r];
-        }
-    }
-}
-
-constexpr int SORT_WARP_MAX = 256;       // lists up to this length: one warp, in registers
-constexpr int SORT_SMEM_MAX = 2048;      // longer ones up to this: one block, in shared memory (16 KB)
-
-// One warp per tile: the tile's range, and its list sorted into (tile, splat)
-// order when it has at most SORT_WARP_MAX keys; longer lists are queued for
-// k_tile_sort_long.
-__global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ tile_off, int tiles, int64_t kcap,
-                                                   const uint32_t *__restrict__ bkey,
-                                                   const uint32_t *__restrict__ bval, uint32_t *skey, uint32_t *sval,
-                                                   uint2 *ranges, int *n_long, int32_t *long_tiles)
-{
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += nwarps) {
-        const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
-        const int L = (int)(hi - lo);
-        if (lane == 0) ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
-        if (L <= 0) continue;
-        if (L <= 32) warp_sort_list<32>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
-        else if (L <= 64) warp_sort_list<64>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
-        else if (L <= 128) warp_sort_list<128>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
-        else if (L <= SORT_WARP_MAX) warp_sort_list<256>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
-        else if (lane == 0) long_tiles[atomicAdd(n_long, 1)] = t;
-    }
-}
-
-// Compare-exchange of positions i < j of a list of length L (positions >= L
-// hold +inf and stay untouched).
-__device__ __forceinline__ void cmpx_smem(unsigned long long *v, int i, int j)
-{
-    const unsigned long long x = v[i], y = v[j];
-    if (y < x) {
-        v[i] = y;
-        v[j] = x;
-    }
-}
-__device__ __forceinline__ void cmpx_global(uint32_t *key, uint32_t *val, int64_t lo, int L, int i, int j)
-{
-    if (j >= L) return;
-    const unsigned long long x = (unsigned long long)key[lo + i] << 32 | val[lo + i];
-    const unsigned long long y = (unsigned long long)key[lo + j] << 32 | val[lo + j];
-    if (y < x) {
-        key[lo + i] = (uint32_t)(y >> 32);
-        val[lo + i] = (uint32_t)y;
-        key[lo + j] = (uint32_t)(x >> 32);
-        val[lo + j] = (uint32_t)x;
-    }
-}
-
-// One block per long list: a bitonic sort in shared memory (up to
-// SORT_SMEM_MAX keys, padded to a power of two with +inf), else in place in
-// the unsorted key arrays (positions past the list act as +inf).
-__global__ void __launch_bounds__(256) k_tile_sort_long(const uint32_t *__restrict__ tile_off, int64_t kcap,
-                                                        uint32_t *bkey, uint32_t *bval, uint32_t *skey,
-                                                        uint32_t *sval, const int *n_long,
-                                                        const int32_t *__restrict__ long_tiles)
-{
-    extern __shared__ unsigned long long sv[];
-    const int nl = *n_long;
-    for (int q = blockIdx.x; q < nl; q += gridDim.x) {
-        const int t = long_tiles[q];
-        const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
-        const int64_t L64 = hi - lo;
-        if (L64 > (1 << 30)) continue;                   // beyond any workspace; the list stays unsorted
-        const int L = (int)L64;
-        int P = 1;
-        while (P < L) P <<= 1;
-        const bool in_smem = P <= SORT_SMEM_MAX;
-        if (in_smem)
-            for (int e = threadIdx.x; e < P; e += blockDim.x)
-                sv[e] = e < L ? ((unsigned long long)bkey[lo + e] << 32 | bval[lo + e]) : ~0ull;
-        __syncthreads();
-        for (int lk = 1; (1 << lk) <= P; lk++) {        // blocks of k = 2^lk
-            const int k = 1 << lk;
-            for (int e = threadIdx.x; e < P / 2; e += blockDim.x) {      // mirrored pairs within blocks of k
-                const int i = ((e >> (lk - 1)) << lk) | (e & ((k >> 1) - 1)), j = i ^ (k - 1);
-                if (in_smem) cmpx_smem(sv, i, j);
-                else cmpx_global(bkey, bval, lo, L, i, j);
-            }
-            __syncthreads();
-            for (int ld = lk - 2; ld >= 0; ld--) {       // then pairs at distance 2^ld
-                for (int e = threadIdx.x; e < P / 2; e += blockDim.x) {
-                    const int i = ((e >> ld) << (ld + 1)) | (e & ((1 << ld) - 1)), j = i + (1 << ld);
-                    if (in_smem) cmpx_smem(sv, i, j);
-                    else cmpx_global(bkey, bval, lo, L, i, j);
-                }
-                __syncthreads();
-            }
-        }
-        for (int e = threadIdx.x; e < L; e += blockDim.x) {
-            skey[lo + e] = (uint32_t)t;
-            sval[lo + e] = in_smem ? (uint32_t)sv[e] : bval[lo + e];
-        }
-        __syncthreads();                                  // sv is reused by the next list
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Rasterizer blocks: one tile per block.  Each thread owns PPT vertically
@@ -1293,38 +895,13 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     const int tiles = cam.tiles_x * cam.tiles_y;
     cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
     cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);
-    cudaMemsetAsync(rb.tile_cnt, 0, (size_t)(tiles + 1) * sizeof(uint32_t), s);
-    cudaMemsetAsync(rb.tile_cur, 0, (size_t)tiles * sizeof(uint32_t), s);
     // gather and projection
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
                                                           rb.rec2, rb.depth, rb.rect, rb.n_fix, rb.fix_idx,
                                                           rb.fix_flag, rb.n_big, rb.big_idx);
     k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
                                                     rb.rect, rb.n_big, rb.big_idx);
-    // the key count of every tile
-    const int gsm = w.grid((int64_t)(cap + 31) / 32 * 32, 256);
-    k_tiles_small<false><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
-                                             view, rb.tile_cnt, nullptr, nullptr, nullptr, nullptr);
-    k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
-                                               rb.tile_cnt);
-    // each tile's first key (and the key total), then the keys into their tiles' lists
-    scan_counts(rb.tile_cnt, tiles + 1, rb.n_keys, (int)rb.kcap, w, s);
-    k_tiles_small<true><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
-                                            view, nullptr, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
-    k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.n_big, rb.big_idx, cap, rb.kcap,
-                                             args, view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
-    // front-to-back order within each tile, and the tiles' ranges
-    k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
-                                                                  rb.tk[1], rb.tv[1], rb.ranges, rb.n_big + 1,
-                                                                  rb.long_tiles);
-    static bool long_attr = false;
-    if (!long_attr) {
-        cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(SORT_SMEM_MAX * sizeof(unsigned long long)));
-        long_attr = true;
-    }
-    k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
-        rb.tile_cnt, rb.kcap, rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_big + 1, rb.long_tiles);
+    build_tile_lists(args, view, n_vis, rb, tiles, w, s);
     rb.sorted_keys = rb.tk[1];
     rb.sorted_vals = rb.tv[1];
     rb.tiles = tiles;
