@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "gs_kernels.cuh"
+#include "host_plan.hpp"
 
 using namespace gs;
 
@@ -90,14 +91,8 @@ struct gs_ctx {
     cudaStream_t dstream = nullptr;     // device -> host copies (the other PCIe direction, concurrently)
     cudaEvent_t ev_vis = nullptr, ev_upd = nullptr, ev_done = nullptr, ev_end = nullptr;
     cudaEvent_t ev_down[2] = {nullptr, nullptr};
-    struct Run { int64_t chunk0, slot0, nchunks; };
-    std::vector<Run> runs;              // copy runs of the last host-tier step
-    // ring halves between consecutive host-tier steps: the previous step's
-    // visible chunks (slot, or -1) and staged chunks, the half it used
-    std::vector<int32_t> pvslot;
-    std::vector<uint8_t> pstaged;
-    int parity = 0;
-    bool prev_full = true;              // the previous step used the whole ring (or there was none)
+    HostPlan plan;                      // the last host-tier step's slots, rounds and copy runs
+    HostHistory hist;                   // what that step leaves for the next (ring halves)
     const void *pscene = nullptr;
     int64_t pn = 0;
     cudaEvent_t ev_half[2] = {nullptr, nullptr};   // write-backs of the last step that used half 0 / 1 done
@@ -964,7 +959,7 @@ static void copy_runs(gs_ctx *c, const gs_scene *scene, const SceneView &sv, siz
     const int64_t planes = sv.D - N_GEO, ring = sv.sh.ppitch;
     void *host[3] = {scene->host_sh, scene->host_m, scene->host_v};
     for (size_t k = first; k < last; k++) {
-        const gs_ctx::Run &r = c->runs[k];
+        const HostRun &r = c->plan.runs[k];
         const int64_t i0 = r.chunk0 << c->shift;
         const int64_t rows = std::min(sv.n, (r.chunk0 + r.nchunks) << c->shift) - i0;
         for (int j = 0; j < 3; j++) {
@@ -1035,114 +1030,30 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     if (cudaEventSynchronize(c->ev_sdone) != cudaSuccess) return cuda_check(c, "host tier: previous step");
 
     // history of the previous host-tier step on this scene (reset otherwise)
-    if (c->pscene != scene->host_sh || c->pn != sv.n || (int64_t)c->pvslot.size() != nch) {
-        c->pvslot.assign(nch, -1);
-        c->pstaged.assign(nch, 0);
-        c->prev_full = true;
+    if (c->pscene != scene->host_sh || c->pn != sv.n || (int64_t)c->hist.pvslot.size() != nch) {
+        c->hist.reset(nch);
         c->pscene = scene->host_sh;
         c->pn = sv.n;
     }
-    int64_t nv = 0, nu = 0;
-    for (int64_t ch = 0; ch < nch; ch++) {
-        if (c->htouch[ch] == 2) nv++;
-        else if (c->htouch[ch] == 1) nu++;
-    }
-    // Ring halves: a step whose chunks fit in half of the ring uses the half
-    // the previous step did not, so its H2D need not wait for the previous
-    // step's write-backs (only for those of the step before, normally long
-    // done).  Its chunks that the previous step had visible are copied from
-    // their slots on the device (the previous step's apply is ordered before
-    // this step on the stream); those the previous step staged only for the
-    // optimizer come from the host after the previous write-backs.  Otherwise
-    // the whole ring after every write-back, as for the first step.
-    const int64_t H = c->cfg.stage_chunks / 2;
-    const bool half = H >= 1 && nv <= H && (nu == 0 || H - nv >= 1);
-    const int p = half ? c->parity : 0;
-    const int64_t base = half ? p * H : 0, ring_chunks = half ? H : c->cfg.stage_chunks;
-    const bool reuse = half && !c->prev_full;      // device copies from the previous step's visible slots
-    // plan: visible chunks -> slots base + [0, nv); optimizer-only chunks ->
-    // rounds of at most `rcap` chunks, cut at chunk-id boundaries, round k in
-    // slots base + nv + (k % nbuf) * rcap + [0, rcap)
-    {
-        int64_t q = 0;
-        for (int64_t ch = 0; ch < nch; ch++) {
-            if (c->htouch[ch] == 2) c->hslot[ch] = (int32_t)(base + q++);
-            else c->hslot[ch] = -1;
-        }
-    }
-    const int64_t cap = ring_chunks - nv;
-    if (nv > c->cfg.stage_chunks || (nu > 0 && cap < 1))
+    // the plan (host_plan.hpp): ring half, each touched chunk's slot and the
+    // source of its rows, the optimizer's rounds, the copy runs
+    c->plan = plan_host_step(c->htouch, nch, c->cfg.stage_chunks, c->hist);
+    const HostPlan &P = c->plan;
+    if (!P.ok)
         return fail(c, GS_ERR_CAPACITY, "host tier: %lld chunks of visible Gaussians, staging ring holds %lld",
-                    (long long)nv + (nu > 0), (long long)c->cfg.stage_chunks);
-    const int64_t nbuf = cap >= 2 ? 2 : 1, rcap = nu > 0 ? cap / nbuf : 1;
-    struct Round { int64_t ch_lo, ch_hi; size_t vis_lo, vis_hi, upd_lo, upd_hi; bool late; };
-    std::vector<Round> rounds;
-    {
-        Round r{0, nch, 0, 0, 0, 0, false};
-        int64_t in_round = 0;
-        for (int64_t ch = 0; ch < nch; ch++) {
-            if (c->htouch[ch] != 1) continue;
-            if (in_round == rcap) {           // close the round before this chunk
-                r.ch_hi = ch;
-                rounds.push_back(r);
-                r = Round{ch, nch, 0, 0, 0, 0, false};
-                in_round = 0;
-            }
-            c->hslot[ch] = (int32_t)(base + nv + ((int64_t)rounds.size() % nbuf) * rcap + in_round);
-            r.late |= c->pstaged[ch] != 0;    // its host rows are current once the previous write-backs land
-            in_round++;
-        }
-        rounds.push_back(r);
-    }
-    c->runs.clear();
-    auto add_run = [&](int64_t ch, size_t first) {
-        const int64_t slot = c->hslot[ch];
-        if (c->runs.size() > first && c->runs.back().chunk0 + c->runs.back().nchunks == ch &&
-            c->runs.back().slot0 + c->runs.back().nchunks == slot)
-            c->runs.back().nchunks++;
-        else
-            c->runs.push_back(gs_ctx::Run{ch, slot, 1});
-    };
-    // visible chunks by source: device copies, host rows now, host rows after
-    // the previous write-backs; their write-back runs are split at round
-    // boundaries
-    std::vector<std::array<int64_t, 3>> druns;
-    auto src_class = [&](int64_t ch) {
-        if (reuse && c->pvslot[ch] >= 0) return 0;
-        return c->pstaged[ch] ? 2 : 1;
-    };
-    for (int64_t ch = 0; ch < nch; ch++) {
-        if (c->htouch[ch] != 2 || src_class(ch) != 0) continue;
-        const int64_t src = c->pvslot[ch], dst = c->hslot[ch];
-        if (!druns.empty() && druns.back()[0] + druns.back()[2] == src && druns.back()[1] + druns.back()[2] == dst)
-            druns.back()[2]++;
-        else
-            druns.push_back({src, dst, 1});
-    }
-    const size_t now_lo = c->runs.size();
-    for (int64_t ch = 0; ch < nch; ch++)
-        if (c->htouch[ch] == 2 && src_class(ch) == 1) add_run(ch, now_lo);
-    const size_t late_lo = c->runs.size();
-    for (int64_t ch = 0; ch < nch; ch++)
-        if (c->htouch[ch] == 2 && src_class(ch) == 2) add_run(ch, late_lo);
-    const size_t late_hi = c->runs.size();
-    for (Round &r : rounds) {             // visible chunks again, for the write-backs
-        r.vis_lo = c->runs.size();
-        for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
-            if (c->htouch[ch] == 2) add_run(ch, r.vis_lo);
-        r.vis_hi = c->runs.size();
-    }
-    for (Round &r : rounds) {             // optimizer-only chunks
-        r.upd_lo = c->runs.size();
-        for (int64_t ch = r.ch_lo; ch < r.ch_hi; ch++)
-            if (c->htouch[ch] == 1) add_run(ch, r.upd_lo);
-        r.upd_hi = c->runs.size();
-    }
+                    (long long)P.nv + (P.nu > 0), (long long)c->cfg.stage_chunks);
+    const int64_t nv = P.nv, nu = P.nu, nbuf = P.nbuf;
+    const bool half = P.half;
+    const int p = P.p;
+    const std::vector<HostRound> &rounds = P.rounds;
+    const std::vector<std::array<int64_t, 3>> &druns = P.druns;
+    const size_t now_lo = P.now_lo, late_lo = P.late_lo, late_hi = P.late_hi;
+    std::memcpy(c->hslot, P.slot.data(), (size_t)nch * sizeof(int32_t));
     c->last_touched = nv + nu;
     c->last_bytes = 0;
     cudaMemcpyAsync(c->dslot, c->hslot, nch * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     cudaEvent_t prev_done = c->ev_end;            // the previous step's write-backs
-    if (half && !c->prev_full) {
+    if (P.reuse) {
         // this half was last written back by the step before the previous one
         cudaStreamWaitEvent(c->cstream, c->ev_half[p], 0);
         cudaStreamWaitEvent(s, c->ev_half[p], 0);
@@ -1166,7 +1077,7 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     int *u_range = c->n_tmp + 2;
     const int64_t R = 1ll << c->shift;
     for (size_t k = 0; k < rounds.size(); k++) {
-        const Round &r = rounds[k];
+        const HostRound &r = rounds[k];
         // the ring half this round fills was written back by round k - nbuf
         if ((int64_t)k >= nbuf) cudaStreamWaitEvent(c->cstream, c->ev_down[k % nbuf], 0);
         if (r.late) cudaStreamWaitEvent(c->cstream, prev_done, 0);
@@ -1194,13 +1105,7 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
         cudaEventRecord(c->ev_half[0], c->dstream);
         cudaEventRecord(c->ev_half[1], c->dstream);
     }
-    // history for the next step
-    for (int64_t ch = 0; ch < nch; ch++) {
-        c->pvslot[ch] = c->htouch[ch] == 2 ? c->hslot[ch] : -1;
-        c->pstaged[ch] = c->htouch[ch] != 0;
-    }
-    c->prev_full = !half;
-    if (half) c->parity ^= 1;
+    advance_host_history(c->hist, c->htouch, nch, P);
     if (c->w.tev) c->t_used++;
     return cuda_check(c, "gs_step host tier");
 }
