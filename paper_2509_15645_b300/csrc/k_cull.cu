@@ -6,6 +6,8 @@
 // applied to Gaussians whose counter is non-zero).  Output: one visibility bit
 // per Gaussian (warp ballot) and the number of visible Gaussians per
 // 2048-Gaussian chunk, from which k_scan.cu builds the ordered id list.
+#include <atomic>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -318,10 +320,15 @@ static bool cull_tma_ok(const SceneView &sc)
 static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0, int nv, const CullOut &out, Work &w,
                             cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the stages exceed the default dynamic shared-memory limit; the raised
+    // limit is a per-device setting, recorded per device
+    static std::atomic<uint64_t> attr_devices{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(attr_devices.load() & bit)) {
         cudaFuncSetAttribute(k_cull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
-        attr_set = true;
+        attr_devices.fetch_or(bit);
     }
     const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics

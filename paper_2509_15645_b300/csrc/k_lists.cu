@@ -427,12 +427,8 @@ void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBuf
     k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
                                                                   rb.tk[1], rb.tv[1], rb.ranges, rb.n_big + 1,
                                                                   rb.long_tiles);
-    static bool long_attr = false;
-    if (!long_attr) {
-        cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(SORT_SMEM_MAX * sizeof(unsigned long long)));
-        long_attr = true;
-    }
+    static_assert(SORT_SMEM_MAX * sizeof(unsigned long long) <= 48 * 1024,
+                  "the long-list buffer stays within the default dynamic shared-memory limit");
     k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
         rb.tile_cnt, rb.kcap, rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_big + 1, rb.long_tiles);
 }
