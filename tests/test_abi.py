@@ -97,3 +97,33 @@ def test_null_context_is_rejected(lib):
     h = C.c_void_p()
     c.tile_w = 7
     assert lib.gs_create(C.byref(h), C.byref(c), 0, None, 0) == _lib.GS_ERR_INVALID_ARG
+
+
+def test_staging_ring_configuration(lib):
+    """The host tier's staging ring: its size follows stage_chunks, the chunk
+    size and the element size of the staged rows (w, m, v of the 48 SH planes
+    at degree 3); out-of-range chunk shifts and element sizes are refused, and
+    the 32-pixel tiles of the warp-tile rasterizer are accepted."""
+    from paper_2509_15645_b300 import _lib
+
+    def size(**kw):
+        nb = C.c_size_t(0)
+        st = lib.gs_workspace_size(C.byref(_cfg(**kw)), C.byref(nb))
+        return st, nb.value
+
+    st0, base = size()
+    assert st0 == _lib.GS_OK
+    st, ring4 = size(stage_chunks=100, chunk_shift=11)
+    assert st == _lib.GS_OK
+    st, ring2 = size(stage_chunks=100, chunk_shift=11, stage_elem_bytes=2)
+    assert st == _lib.GS_OK
+    planes = 48
+    # the ring (3 arrays) plus chunk tables; allocations are 256-byte aligned
+    assert abs((ring4 - base) - 3 * planes * (100 << 11) * 4) < 4096 + 8 * (10_000_000 >> 11)
+    assert abs((ring2 - base) - 3 * planes * (100 << 11) * 2) < 4096 + 8 * (10_000_000 >> 11)
+    assert size(stage_chunks=100, chunk_shift=13)[1] > ring4
+    for bad in (dict(stage_chunks=10, chunk_shift=9), dict(stage_chunks=10, chunk_shift=21),
+                dict(stage_chunks=10, stage_elem_bytes=3), dict(stage_chunks=-1), dict(tile_w=32, tile_h=16)):
+        assert size(**bad)[0] == _lib.GS_ERR_INVALID_ARG, bad
+    for good in (dict(tile_w=8, tile_h=4), dict(tile_w=4, tile_h=8), dict(tile_w=64, tile_h=4)):
+        assert size(**good)[0] == _lib.GS_OK, good
