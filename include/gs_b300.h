@@ -247,6 +247,21 @@ GS_API gs_status gs_refresh_rdir(gs_ctx *ctx, const gs_scene *scene, const gs_ad
 GS_API gs_status gs_adam_materialize(gs_ctx *ctx, const gs_scene *scene, const gs_adam_cfg *adam, float *w_out,
                               float *m_out, float *v_out, void *stream);
 
+/* The tables the deferred update of optimizer step `step` (>= 1: the step a
+ * scene with scene->step == step - 1 takes next) hands to the kernels, fp32,
+ * computed in double from the hyper-parameters (Fig. 10, §4.3.2):
+ *   param     [6][16] row-major: per parameter group g and delay d, the
+ *             coefficient of the restore w -= param[g][d] m / (sqrt(v) + eps),
+ *             i.e. the sum over the d skipped steps of Eq. 3's weights;
+ *             0 for d = 0, d > max_defer and d >= step;
+ *   mom, var  [16]: beta1^(d+1), beta2^(d+1), the decay of m and v over the
+ *             d skipped steps and the current one;
+ *   step_size [6]: lr[g] / (1 - beta1^step);  bias_corr: sqrt(1 - beta2^step).
+ * Host arrays owned by the caller; any may be NULL.  Touches no device.
+ * GS_ERR_INVALID_ARG for a NULL adam, step < 1 or max_defer outside [1, 15]. */
+GS_API gs_status gs_adam_tables(const gs_adam_cfg *adam, int32_t step, float *param, float *mom, float *var,
+                                float *step_size, float *bias_corr);
+
 /* Scatter compact gradients to a full [D][pitch] array (zero elsewhere). */
 GS_API gs_status gs_grad_scatter(gs_ctx *ctx, const gs_scene *scene, const int32_t *ids, const int32_t *n_vis,
                           const float *grad_compact, int64_t cap, float *grad_full, void *stream);

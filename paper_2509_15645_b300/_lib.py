@@ -68,6 +68,8 @@ EXPORTS = {
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
+    "gs_adam_tables": (c_i32, [C.POINTER(AdamCfg), c_i32, C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32),
+                               C.POINTER(c_f32), C.POINTER(c_f32)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
 }

@@ -60,6 +60,18 @@ def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L
     return a
 
 
+def adam_tables(adam: L.AdamCfg, step: int) -> dict:
+    """The deferred update's tables for optimizer step ``step`` as the kernels
+    receive them (Fig. 10): ``param`` [6][16], ``mom`` [16], ``var`` [16],
+    ``step_size`` [6], ``bias_corr``.  Host only."""
+    param, mom, var, ss, bc = (C.c_float * 96)(), (C.c_float * 16)(), (C.c_float * 16)(), (C.c_float * 6)(), C.c_float()
+    st = L.load().gs_adam_tables(C.byref(adam), int(step), param, mom, var, ss, C.byref(bc))
+    if st != L.GS_OK:
+        raise L.GsError(st, "gs_adam_tables")
+    return {"param": [list(param[g * 16:(g + 1) * 16]) for g in range(6)], "mom": list(mom), "var": list(var),
+            "step_size": list(ss), "bias_corr": bc.value}
+
+
 class GaussianScene:
     """A Gaussian set with its optimizer state.
 

@@ -115,24 +115,7 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     c.tiles_x = (cam->width + tile_w - 1) / tile_w;
     c.tiles_y = (cam->height + tile_h - 1) / tile_h;
     a.n_views = 1;
-    if (restore) {
-        const int t = scene->step + 1;
-        const double b1 = adam->beta1, b2 = adam->beta2, scale = b1 / std::sqrt(b2);
-        for (int g = 0; g < N_GROUPS; g++) {
-            double prev = 0.0;
-            for (int i = 1; i < LUT_N; i++) {
-                if (i <= adam->max_defer && i <= t - 1) {
-                    prev = scale * prev + (adam->lr[g] * b1) /
-                                              (std::sqrt(b2 / (1.0 - std::pow(b2, t - i))) * (1.0 - std::pow(b1, t - i)));
-                    a.lut.param[g][i] = (float)prev;
-                }
-            }
-        }
-        a.lut.eps = adam->eps;
-        a.lut.max_defer = adam->max_defer;
-        a.lut.step = t;
-        a.lut.restore = 1;
-    }
+    if (restore) a.lut = make_lut(adam, scene->step + 1, true);
 
     DevArgs *args = reinterpret_cast<DevArgs *>(base + OFF_ARGS);
     int *status = reinterpret_cast<int *>(base + OFF_STATUS);

@@ -268,7 +268,7 @@ static DevCam make_cam(const gs_camera &a, const gs_config &g)
 
 // Tables of the deferred update (Fig. 10, §4.3.2) for step t, computed in
 // double and rounded to float.  Entries with delay >= t are never used.
-static DevLut make_lut(const gs_adam_cfg *a, int t, bool restore, int precision = GS_FP32)
+DevLut gs::make_lut(const gs_adam_cfg *a, int t, bool restore, int precision)
 {
     DevLut L{};
     L.restore = 0;
@@ -816,6 +816,24 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
     counts[0] = host[0];
     counts[1] = host[1];
     c->have_fwd = false;
+    return GS_OK;
+}
+
+gs_status gs_adam_tables(const gs_adam_cfg *adam, int32_t step, float *param, float *mom, float *var,
+                         float *step_size, float *bias_corr)
+{
+    if (!adam || step < 1 || adam->max_defer < 1 || adam->max_defer > LUT_N - 1) return GS_ERR_INVALID_ARG;
+    const DevLut L = make_lut(adam, step, true);
+    for (int g = 0; g < N_GROUPS; g++) {
+        for (int i = 0; i < LUT_N; i++)
+            if (param) param[g * LUT_N + i] = L.param[g][i];
+        if (step_size) step_size[g] = L.step_size[g];
+    }
+    for (int i = 0; i < LUT_N; i++) {
+        if (mom) mom[i] = L.mom[i];
+        if (var) var[i] = L.var[i];
+    }
+    if (bias_corr) *bias_corr = L.bias_corr;
     return GS_OK;
 }
 
