@@ -40,6 +40,25 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+# ---------------------------------------------------------------------------- replicas
+
+def max_over_ranks(ms, dist, dev):
+    """The slowest rank's time: the job ends when its last replica does.  With
+    no process group (one GPU) the local time."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, ms):
+    """Steps per second of the whole job: each of `world` replicas takes
+    `steps` steps, and all of them finish within `ms` milliseconds."""
+    return world * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -311,10 +330,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         sp = ctx.timing_read(tcap)
         ctx.sync_status()
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms, sp, clk, staged
 
     def measure(precision):
@@ -419,13 +435,9 @@ def run_ours(args):
         ctx.wait_copies()
         f1.record(stream)
         torch.cuda.synchronize()
-        ms = f0.elapsed_time(f1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
         ctx.sync_status()
-        return {"value": round(world * K / (ms / 1e3), 4), "unit": UNIT,
+        return {"value": round(job_rate(world, K, ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(targets[0].numel() * 4 * vps), "d2h_bytes_per_step": 4}
 
     main_prec = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
@@ -442,7 +454,7 @@ def run_ours(args):
         mb = measure(gs.GS_BF16_SH_MOM)
         del mb["sc"]
         bf16 = {"form": "bf16_sh_mom (bf16 SH and moments, stochastic rounding; fp32 geometry and compositing)",
-                "value": round(world * K / (mb["ms"] / 1e3), 4), "unit": UNIT, "ms_per_step": round(mb["ms"] / K, 4),
+                "value": round(job_rate(world, K, mb["ms"]), 4), "unit": UNIT, "ms_per_step": round(mb["ms"] / K, 4),
                 "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in mb["st"].items()},
                 "cull_adam": mb["cull_adam"], "roofline": roofline(mb), "clocks": mb["clk"],
                 "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 * 2 + D * 2 * 2 + 1}
@@ -453,7 +465,7 @@ def run_ours(args):
         cfg_note = WORKLOAD
     K_ms = m["ms"]
     out = {
-        "metric": METRIC, "value": round(world * K / (K_ms / 1e3), 4), "unit": UNIT, "n_gpus": world, "steps": K,
+        "metric": METRIC, "value": round(job_rate(world, K, K_ms), 4), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": round(K_ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded aerial heightfield, random-init Gaussians)",
         "config": {"workload": cfg_note, "gaussians": N, "image": f"{W}x{H}", "sh_degree": deg,

@@ -1,0 +1,68 @@
+"""The N > 1 benchmark path on the CPU: replicas (one per GPU, no collective on
+the data path) report the slowest rank's time and the whole job's rate; the
+reference arm runs on rank 0 alone.  Two `gloo` ranks stand in for two GPUs."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = [7.5, 20.25][rank]               # rank 1 is the slow replica
+        ms = bench.max_over_ranks(local_ms, dist, torch.device("cpu"))
+        dist.barrier()
+        q.put((rank, ms, bench.job_rate(world, 40, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_rate_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, ms, rate in got:
+        assert ms == 20.25                          # both ranks see the slowest time
+        assert rate == pytest.approx(2 * 40 / 0.02025)   # both replicas' steps over that time
+
+
+def test_single_process_keeps_local_time():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.25, None, None) == 3.25
+    assert bench.job_rate(1, 10, 20.0) == pytest.approx(500.0)
+
+
+def test_reference_arm_on_other_ranks_exits_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""                   # rank 0 alone prints the line
