@@ -101,6 +101,20 @@ __global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__re
     }
 }
 
+// Row of pair j in a rectangle of width w as (j * ceil(2^16 / w)) >> 16:
+// checked at compile time for every width and pair index a rectangle of at
+// most BIG_RECT tiles has.
+constexpr bool row_by_multiply_shift_exact(int max_area)
+{
+    for (int w = 1; w <= max_area; w++) {
+        const uint32_t inv = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
+        for (int j = 0; j < max_area; j++)
+            if ((int)(((uint32_t)j * inv) >> 16) != j / w) return false;
+    }
+    return true;
+}
+static_assert(row_by_multiply_shift_exact(BIG_RECT), "pair row index by multiply-shift is inexact at BIG_RECT");
+
 // The small rectangles' (splat, tile) pairs, load-balanced over a warp: the
 // warp takes 32 splats (kept, not FP64-flagged, at most BIG_RECT tiles: the
 // partition k_gather_project leaves to it), scans their rectangle areas, and
