@@ -116,6 +116,9 @@ void launch_touch_from_masks(const uint32_t *vmask, const uint32_t *umask, int64
 void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s);
 void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t n, int shift, int max_defer,
                          uint8_t *touch, Work &w, cudaStream_t s);
+// Device camera of a view: pinhole, the projection's guard band, the camera
+// centre and the tile grid.  Host only.
+DevCam make_cam(const gs_camera &a, int tile_w, int tile_h);
 // Deferred-update tables (Fig. 10) for optimizer step t; restore = 0 leaves the
 // cull's and gather's restore off.  Host only.
 DevLut make_lut(const gs_adam_cfg *a, int t, bool restore, int precision = GS_FP32);

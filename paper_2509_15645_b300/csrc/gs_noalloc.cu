@@ -14,7 +14,6 @@
 // last call's contents, so calls that overlap on the GPU (other streams,
 // other threads) race; every byte a call reads is written or cleared by that
 // same call first.
-#include <cmath>
 #include <mutex>
 
 #include "gs_kernels.cuh"
@@ -100,20 +99,7 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
 
     // argument block: the camera, and the restore tables of the coming step
     DevArgs a{};
-    DevCam &c = a.cam[0];
-    for (int k = 0; k < 9; k++) c.R[k] = cam->R[k];
-    for (int k = 0; k < 3; k++) c.t[k] = cam->t[k];
-    c.fx = cam->fx; c.fy = cam->fy; c.cx = cam->cx; c.cy = cam->cy;
-    c.near_z = cam->near_z; c.far_z = cam->far_z;
-    c.limx = (float)(1.3 * (0.5 * cam->width / (double)cam->fx));
-    c.limy = (float)(1.3 * (0.5 * cam->height / (double)cam->fy));
-    for (int i = 0; i < 3; i++)
-        c.campos[i] = (float)(-((double)cam->R[0 * 3 + i] * cam->t[0] + (double)cam->R[1 * 3 + i] * cam->t[1] +
-                                (double)cam->R[2 * 3 + i] * cam->t[2]));
-    c.width = cam->width; c.height = cam->height;
-    c.tile_w = tile_w; c.tile_h = tile_h;
-    c.tiles_x = (cam->width + tile_w - 1) / tile_w;
-    c.tiles_y = (cam->height + tile_h - 1) / tile_h;
+    a.cam[0] = make_cam(*cam, tile_w, tile_h);
     a.n_views = 1;
     if (restore) a.lut = make_lut(adam, scene->step + 1, true);
 

@@ -246,7 +246,7 @@ static void carve(gs_ctx *c, char *base)
 }
 
 // ---------------------------------------------------------------------------
-static DevCam make_cam(const gs_camera &a, const gs_config &g)
+DevCam gs::make_cam(const gs_camera &a, int tile_w, int tile_h)
 {
     DevCam c{};
     memcpy(c.R, a.R, sizeof(c.R));
@@ -259,10 +259,10 @@ static DevCam make_cam(const gs_camera &a, const gs_config &g)
         c.campos[i] = (float)(-((double)a.R[0 * 3 + i] * a.t[0] + (double)a.R[1 * 3 + i] * a.t[1] + (double)a.R[2 * 3 + i] * a.t[2]));
     c.width = a.width;
     c.height = a.height;
-    c.tile_w = g.tile_w;
-    c.tile_h = g.tile_h;
-    c.tiles_x = (a.width + g.tile_w - 1) / g.tile_w;
-    c.tiles_y = (a.height + g.tile_h - 1) / g.tile_h;
+    c.tile_w = tile_w;
+    c.tile_h = tile_h;
+    c.tiles_x = (a.width + tile_w - 1) / tile_w;
+    c.tiles_y = (a.height + tile_h - 1) / tile_h;
     return c;
 }
 
@@ -526,7 +526,7 @@ gs_status gs_cull(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const 
     if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
-    a.cam[0] = make_cam(*cam, c->cfg);
+    a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
     a.lut = make_lut(adam, scene->step + 1, adam && adam->mode == GS_ADAM_DEFERRED && sv.m && sv.v && sv.counter);
     a.n_views = 1;
     set_args(c, SLOT_CULL, a, s);
@@ -548,7 +548,7 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, 
     if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
-    a.cam[0] = make_cam(*cam, c->cfg);
+    a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
     a.lut = make_lut(adam, scene->step + 1, adam && adam->mode == GS_ADAM_DEFERRED && sv.m && sv.v && sv.counter);
     a.n_views = 1;
     set_args(c, SLOT_RENDER, a, s);
@@ -719,7 +719,7 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
-    a.cam[0] = make_cam(*cam, c->cfg);
+    a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
     a.n_views = 1;
     set_args(c, SLOT_RENDER, a, s);
     int32_t *ids = c->vids[0];
@@ -797,7 +797,7 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
     if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
-    a.cam[0] = make_cam(*cam, c->cfg);
+    a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
     a.n_views = 1;
     set_args(c, SLOT_RENDER, a, s);
     int32_t *ids = c->vids[0];
@@ -1154,7 +1154,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
     DevArgs a{};
     for (int v = 0; v < n_views; v++) {
         if (!valid_cam(c, &views[v]) || !targets[v]) return fail(c, GS_ERR_INVALID_ARG, "invalid view %d", v);
-        a.cam[v] = make_cam(views[v], c->cfg);
+        a.cam[v] = make_cam(views[v], c->cfg.tile_w, c->cfg.tile_h);
         a.target[v] = targets[v];
     }
     a.lut = make_lut(adam, scene->step + 1, adam->mode == GS_ADAM_DEFERRED, scene->precision);
