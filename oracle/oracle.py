@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  Arrays are
 numpy float64; parameters use the [D][n] structure-of-arrays layout of
 ``synth.scenes``.  Functions follow GS-Scale §2.4 (render steps 1-5), Eq. 1
-(eager Adam) and Eqs. 2-3 with the pseudocode of Fig. 10 (deferred Adam).
+(eager Adam), Eqs. 2-3 with the pseudocode of Fig. 10 (deferred Adam) and §4.4
+(balance-aware image splitting).
 """
 from __future__ import annotations
 
@@ -227,3 +228,41 @@ def depth_bits(depth_f64) -> np.ndarray:
     return np.asarray(depth_f64, np.float64).astype(np.float32).view(np.uint32)
 
 
+
+
+# ---------------------------------------------------------------------------- image splitting (§4.4)
+
+def split_counts(splats, axis: int, at: int):
+    """Visible-Gaussian counts of the two regions of a view split at tile
+    boundary ``at`` along ``axis`` (0: tile columns [0, at) and [at, tiles_x);
+    1: tile rows).  Each region culls on its own (§4.4): a Gaussian counts for
+    a region when it survives the view's cull and its tile rectangle (from
+    ``project``) reaches the region's tiles, so one that straddles the
+    boundary counts for both."""
+    keep = splats["keep"] == 1
+    first, last = splats["rect"][:, 2 * axis], splats["rect"][:, 2 * axis + 1]    # half-open tile range
+    return int(np.count_nonzero(keep & (first < at))), int(np.count_nonzero(keep & (last > at)))
+
+
+def balance_split(splats, oc: OrcCamera, axis: int, steps: int = 5):
+    """Balance-aware split point of §4.4 (the paper: 5 steps, once before
+    training).  Start at the middle tile boundary, cull both sides, and move
+    the boundary into the side with more visible Gaussians by halving the
+    remaining interval each step; boundaries stay inside (0, tiles).  Returns
+    (boundary in tiles, counts of both regions there)."""
+    tiles = tiles_of(oc)[axis]
+    assert tiles >= 2, "a split needs two tiles along the axis"
+
+    def inside(x):
+        return min(max(x, 1), tiles - 1)
+
+    lo, hi = 0, tiles
+    for _ in range(steps):
+        at = inside((lo + hi) // 2)
+        first, second = split_counts(splats, axis, at)
+        if first > second:
+            hi = at          # the first region is fuller: shrink it
+        else:
+            lo = at
+    at = inside((lo + hi) // 2)
+    return at, split_counts(splats, axis, at)
