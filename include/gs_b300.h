@@ -98,13 +98,27 @@ typedef struct gs_ctx gs_ctx;
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  R is the
  * world->camera rotation (row-major), t the translation: p_cam = R mu + t.
- * Pixel (i, j) has its centre at (i + 0.5, j + 0.5). */
+ * Pixel (i, j) has its centre at (i + 0.5, j + 0.5).
+ *
+ * Regions (image splitting, §4.4): with full_width = 0 (and x0 = y0 = 0) the
+ * camera renders its whole width x height image.  Otherwise it renders the
+ * region [x0, x0 + width) x [y0, y0 + height) of the full_width x full_height
+ * image of the same camera (fx, fy, cx, cy are the full image's): pixel (i, j)
+ * of the region is pixel (x0 + i, y0 + j) of the full image, the projection's
+ * guard band is the full image's, and the L1 loss of the region is normalised
+ * by the full image's 3 * full_width * full_height values, so the losses and
+ * gradients of a view's regions, summed, are the whole view's.  The cull keeps
+ * a Gaussian whose 3-sigma square overlaps the region's tiles; regions that
+ * start on a tile boundary of the full image keep the full image's tile grid,
+ * and the union of their visible sets is the whole view's. */
 typedef struct {
     float R[9];
     float t[3];
     float fx, fy, cx, cy;
     float near_z, far_z;
     int32_t width, height;
+    int32_t x0, y0;                   /* region origin in the full image */
+    int32_t full_width, full_height;  /* 0: the camera is the whole image */
 } gs_camera;
 
 /* A Gaussian set with its optimizer state (device pointers, except host_*). */
@@ -355,6 +369,25 @@ GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key
 /* Host tier: chunks staged by the last gs_step of a GS_TIER_HOST_SH scene and
  * the bytes it moved between host and device (both directions). */
 GS_API gs_status gs_host_tier_stats(const gs_ctx *ctx, int64_t *chunks, int64_t *bytes);
+
+/* Balance-aware split point of one view (§4.4): the tile boundary along
+ * `axis` (0: a vertical line, regions left | right; 1: a horizontal line,
+ * regions top | bottom) that divides the view into two regions of about equal
+ * visible-Gaussian counts.  Bisection over the tile boundaries 0 < s < tiles
+ * (tiles along the axis): lo = 0, hi = tiles; each of `steps` rounds culls
+ * both regions at s = clamp((lo + hi) / 2, 1, tiles - 1) in one sweep, then
+ * sets hi = s if the first region has more visible Gaussians than the second
+ * (the split moves into the fuller region, shrinking it), else lo = s.  The
+ * result is s = clamp((lo + hi) / 2, 1, tiles - 1); the paper takes 5 rounds.
+ * *split_out = the chosen boundary in pixels (a multiple of the tile size
+ * along the axis); counts_out[0..1] (may be NULL) = the two regions' visible
+ * counts at that split.  cam is a whole image (full_width = 0) with at least
+ * two tiles along the axis.  Culls with the deferred restore when the scene has
+ * optimizer state and adam is deferred, as gs_cull does.  Synchronises with
+ * the stream once per round (the counts are read on the host); uses the
+ * context's per-view cull buffers of views 0 and 1. */
+GS_API gs_status gs_split_point(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                                int32_t axis, int32_t steps, int32_t *split_out, int64_t *counts_out, void *stream);
 
 /* Inspection of the last gs_render_fwd: the projected splats of the visible
  * set in compact order (entry k belongs to ids[k]), device pointers owned by

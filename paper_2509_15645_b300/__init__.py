@@ -7,6 +7,7 @@ the library and fails if it has not been built.
 """
 from . import _lib
 from ._lib import GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN, GS_FP32, GS_TIER_DEVICE, GS_TIER_HOST_SH  # noqa: F401
-from .api import Context, GaussianScene, adam_struct, adam_tables, camera_struct, n_params, render  # noqa: F401
+from .api import (Context, GaussianScene, RegionCamera, adam_struct, adam_tables, camera_struct, n_params,  # noqa: F401
+                  render, split_regions)
 
 _lib.load()

@@ -21,7 +21,8 @@ GS_TIER_DEVICE, GS_TIER_HOST_SH = 0, 1
 
 class Camera(C.Structure):
     _fields_ = [("R", c_f32 * 9), ("t", c_f32 * 3), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
-                ("near_z", c_f32), ("far_z", c_f32), ("width", c_i32), ("height", c_i32)]
+                ("near_z", c_f32), ("far_z", c_f32), ("width", c_i32), ("height", c_i32), ("x0", c_i32),
+                ("y0", c_i32), ("full_width", c_i32), ("full_height", c_i32)]
 
 
 class Scene(C.Structure):
@@ -68,6 +69,8 @@ EXPORTS = {
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
+    "gs_split_point": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32,
+                               C.POINTER(c_i32), C.POINTER(c_i64), c_vp]),
     "gs_adam_tables": (c_i32, [C.POINTER(AdamCfg), c_i32, C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32),
                                C.POINTER(c_f32), C.POINTER(c_f32)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),

@@ -47,7 +47,38 @@ def camera_struct(cam) -> L.Camera:
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.near_z, c.far_z = float(getattr(cam, "near", 0.01)), float(getattr(cam, "far", 1e10))
     c.width, c.height = int(cam.width), int(cam.height)
+    if getattr(cam, "full_width", 0):
+        c.x0, c.y0 = int(cam.x0), int(cam.y0)
+        c.full_width, c.full_height = int(cam.full_width), int(cam.full_height)
     return c
+
+
+class RegionCamera:
+    """Part of a view (§4.4 image splitting): the region [x0, x0 + width) x
+    [y0, y0 + height) of ``cam``'s full image.  It culls, renders and steps like
+    a camera; the projection's guard band and the L1 normalisation are the full
+    image's, so the losses and gradients of a view's regions, summed, are the
+    whole view's."""
+
+    def __init__(self, cam, x0, y0, width, height):
+        self.R, self.t = cam.R, cam.t
+        self.fx, self.fy, self.cx, self.cy = cam.fx, cam.fy, cam.cx, cam.cy
+        self.near, self.far = getattr(cam, "near", 0.01), getattr(cam, "far", 1e10)
+        self.x0, self.y0, self.width, self.height = int(x0), int(y0), int(width), int(height)
+        self.full_width, self.full_height = int(cam.width), int(cam.height)
+
+    def crop(self, image):
+        """This region of a full-view [3][H][W] image, as a contiguous tensor."""
+        return image[:, self.y0:self.y0 + self.height, self.x0:self.x0 + self.width].contiguous()
+
+
+def split_regions(cam, axis: int, split: int):
+    """The two regions of ``cam`` split at pixel ``split``: axis 0 columns
+    [0, split) and [split, W), axis 1 rows [0, split) and [split, H)."""
+    W, H = int(cam.width), int(cam.height)
+    if axis == 0:
+        return [RegionCamera(cam, 0, 0, split, H), RegionCamera(cam, split, 0, W - split, H)]
+    return [RegionCamera(cam, 0, 0, W, split), RegionCamera(cam, 0, split, W, H - split)]
 
 
 def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L.GS_ADAM_DEFERRED,
@@ -287,6 +318,30 @@ class Context:
                               _ptr(ids), _ptr(n_vis), _stream(stream))
         self._check(st, "gs_cull")
         return ids, n_vis
+
+    def split_point(self, scene: GaussianScene, cam, adam=None, axis=None, steps=5, stream=None):
+        """Balance-aware split of one view (§4.4, gs_split_point): returns
+        (axis, split in pixels, (visible count of region 0, of region 1)).
+        axis None: split across the longer image side."""
+        if axis is None:
+            axis = 0 if int(cam.width) >= int(cam.height) else 1
+        sc = scene.struct()
+        cs = camera_struct(cam)
+        sp, cnt = C.c_int32(0), (C.c_int64 * 2)()
+        st = self.lib.gs_split_point(self.h, C.byref(sc), C.byref(cs), C.byref(adam) if adam is not None else None,
+                                     int(axis), int(steps), C.byref(sp), cnt, _stream(stream))
+        self._check(st, "gs_split_point")
+        return axis, sp.value, (cnt[0], cnt[1])
+
+    def plan_split(self, scene: GaussianScene, cam, adam=None, mem_limit=0.3, axis=None, steps=5, stream=None):
+        """§4.4: a view whose visible fraction of the scene exceeds
+        ``mem_limit`` is trained as two regions.  Returns None (train the view
+        whole) or the two RegionCamera objects of its balance-aware split."""
+        _, n_vis = self.cull(scene, cam, adam, stream)
+        if int(n_vis.item()) <= mem_limit * scene.n:
+            return None
+        ax, sp, _ = self.split_point(scene, cam, adam, axis, steps, stream)
+        return split_regions(cam, ax, sp)
 
     def render_fwd(self, scene: GaussianScene, cam, ids, n_vis, adam=None, stream=None):
         img = torch.empty(3, int(cam.height), int(cam.width), dtype=torch.float32, device=self.device)

@@ -25,7 +25,11 @@ struct DevCam {
     float limx, limy;            // guard band: 1.3 * tan(half fov)
     float campos[3];             // camera centre in world space
     int width, height, tile_w, tile_h, tiles_x, tiles_y;
+    float loss_inv;              // 1 / (3 W H) of the full image (a region's loss is part of it)
 };
+// Kernels copy a camera into shared memory one 32-bit word per thread, with
+// blocks of at least one warp.
+static_assert(sizeof(DevCam) % 4 == 0 && sizeof(DevCam) <= 32 * 4, "DevCam must fit one warp's word copy");
 
 // Restore tables of the deferred update (Fig. 10, §4.3.2) for one step t.
 struct DevLut {

@@ -119,6 +119,8 @@ void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t 
 // Device camera of a view: pinhole, the projection's guard band, the camera
 // centre and the tile grid.  Host only.
 DevCam make_cam(const gs_camera &a, int tile_w, int tile_h);
+// A camera's region fields describe a whole image or a region inside its full image.
+bool camera_region_ok(const gs_camera &a);
 // Deferred-update tables (Fig. 10) for optimizer step t; restore = 0 leaves the
 // cull's and gather's restore off.  Host only.
 DevLut make_lut(const gs_adam_cfg *a, int t, bool restore, int precision = GS_FP32);

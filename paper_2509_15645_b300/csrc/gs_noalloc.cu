@@ -83,7 +83,8 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     if (scene->n <= 0 || scene->pitch < scene->n || (scene->pitch & 3)) return GS_ERR_INVALID_ARG;
     if (scene->n > NA_MAX) return GS_ERR_CAPACITY;     // beyond the fixed scratch: refused, nothing launched
     if (tile_w <= 0 || tile_h <= 0 || cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f) ||
-        !(cam->far_z > cam->near_z) || cam->width >= 65536 * tile_w || cam->height >= 65536 * tile_h)
+        !(cam->far_z > cam->near_z) || cam->width >= 65536 * tile_w || cam->height >= 65536 * tile_h ||
+        !camera_region_ok(*cam))
         return GS_ERR_INVALID_ARG;
     if (scene->precision != GS_FP32 && scene->precision != GS_BF16_SH_MOM && scene->precision != GS_BF16_SH_MOM_RN)
         return GS_ERR_INVALID_ARG;

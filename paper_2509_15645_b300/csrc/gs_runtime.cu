@@ -246,15 +246,30 @@ static void carve(gs_ctx *c, char *base)
 }
 
 // ---------------------------------------------------------------------------
+// A region camera (§4.4 image splitting) renders part of the full image: its
+// principal point moves by the region's origin, while the guard band and the
+// loss normalisation stay the full image's.
+bool gs::camera_region_ok(const gs_camera &a)
+{
+    if (a.full_width == 0) return a.x0 == 0 && a.y0 == 0 && a.full_height == 0;
+    return a.full_width > 0 && a.full_height > 0 && a.x0 >= 0 && a.y0 >= 0 &&
+           (int64_t)a.x0 + a.width <= a.full_width && (int64_t)a.y0 + a.height <= a.full_height;
+}
+
 DevCam gs::make_cam(const gs_camera &a, int tile_w, int tile_h)
 {
     DevCam c{};
+    const bool region = a.full_width > 0;
+    const int FW = region ? a.full_width : a.width, FH = region ? a.full_height : a.height;
     memcpy(c.R, a.R, sizeof(c.R));
     memcpy(c.t, a.t, sizeof(c.t));
-    c.fx = a.fx; c.fy = a.fy; c.cx = a.cx; c.cy = a.cy;
+    c.fx = a.fx; c.fy = a.fy;
+    c.cx = region ? (float)((double)a.cx - a.x0) : a.cx;
+    c.cy = region ? (float)((double)a.cy - a.y0) : a.cy;
     c.near_z = a.near_z; c.far_z = a.far_z;
-    c.limx = (float)(1.3 * (0.5 * a.width / (double)a.fx));
-    c.limy = (float)(1.3 * (0.5 * a.height / (double)a.fy));
+    c.limx = (float)(1.3 * (0.5 * FW / (double)a.fx));
+    c.limy = (float)(1.3 * (0.5 * FH / (double)a.fy));
+    c.loss_inv = 1.f / (float)(3 * (int64_t)FW * FH);
     for (int i = 0; i < 3; i++)
         c.campos[i] = (float)(-((double)a.R[0 * 3 + i] * a.t[0] + (double)a.R[1 * 3 + i] * a.t[1] + (double)a.R[2 * 3 + i] * a.t[2]));
     c.width = a.width;
@@ -323,7 +338,7 @@ static bool valid_cam(const gs_ctx *c, const gs_camera *cam)
 {
     return cam && cam->width > 0 && cam->height > 0 && cam->width <= c->cfg.max_width &&
            cam->height <= c->cfg.max_height && cam->fx > 0.f && cam->fy > 0.f && cam->far_z > cam->near_z &&
-           std::isfinite(cam->fx) && std::isfinite(cam->fy);
+           std::isfinite(cam->fx) && std::isfinite(cam->fy) && camera_region_ok(*cam);
 }
 
 static int elem_bytes(int prec) { return prec == GS_FP32 ? 4 : 2; }
@@ -534,6 +549,75 @@ gs_status gs_cull(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const 
     compact_mask(c->mask, sv.n, c->chunk, true, ids_out, c->wprefix, (int)c->cfg.max_visible, &c->cnt->n_vis, c->w, s);
     cudaMemcpyAsync(n_vis_out, &c->cnt->n_vis, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     return cuda_check(c, "gs_cull");
+}
+
+gs_status gs_split_point(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,
+                         int32_t axis, int32_t steps, int32_t *split_out, int64_t *counts_out, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv;
+    gs_status st = scene_view(c, scene, false, sv, true);
+    if (st) return st;
+    if (!valid_cam(c, cam) || cam->full_width != 0) return fail(c, GS_ERR_INVALID_ARG, "invalid camera (a whole image)");
+    if (axis != 0 && axis != 1) return fail(c, GS_ERR_INVALID_ARG, "axis must be 0 (x) or 1 (y)");
+    if (steps < 0 || steps > 32 || !split_out) return fail(c, GS_ERR_INVALID_ARG, "steps out of range or NULL output");
+    if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (c->cfg.max_views < 2) return fail(c, GS_ERR_INVALID_ARG, "splitting needs a context with max_views >= 2");
+    const int T = axis == 0 ? c->cfg.tile_w : c->cfg.tile_h;
+    const int tiles = ((axis == 0 ? cam->width : cam->height) + T - 1) / T;
+    if (tiles < 2) return fail(c, GS_ERR_INVALID_ARG, "fewer than two tiles along the split axis");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool restore = adam && adam->mode == GS_ADAM_DEFERRED && sv.m && sv.v && sv.counter;
+    const int64_t nchunks = ((sv.n + 31) / 32 + CHUNK_WORDS - 1) / CHUNK_WORDS;
+    int32_t cnt[2] = {0, 0};
+    // visible counts of the two regions split at tile boundary `at`: one cull
+    // sweep over both, exact totals of the per-chunk counts (no capacity)
+    auto count = [&](int at) -> gs_status {
+        gs_camera r[2] = {*cam, *cam};
+        for (int v = 0; v < 2; v++) {
+            r[v].full_width = cam->width;
+            r[v].full_height = cam->height;
+        }
+        if (axis == 0) {
+            r[0].width = at * T;
+            r[1].x0 = at * T;
+            r[1].width = cam->width - at * T;
+        } else {
+            r[0].height = at * T;
+            r[1].y0 = at * T;
+            r[1].height = cam->height - at * T;
+        }
+        DevArgs a{};
+        for (int v = 0; v < 2; v++) a.cam[v] = make_cam(r[v], c->cfg.tile_w, c->cfg.tile_h);
+        a.lut = make_lut(adam, scene->step + 1, restore);
+        a.n_views = 2;
+        set_args(c, SLOT_CULL, a, s);
+        launch_cull_views(sv, c->args + SLOT_CULL, 2, c->vmask, c->vchunk, c->w, s);
+        for (int v = 0; v < 2; v++) scan_counts(c->vchunk[v], nchunks, c->nvis_view + v, 0, c->w, s);
+        cudaMemcpyAsync(cnt, c->nvis_view, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "gs_split_point");
+        int dev_st = 0;
+        if (cudaMemcpy(&dev_st, &c->cnt->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cuda_check(c, "gs_split_point status");
+        if (dev_st) return fail(c, (gs_status)dev_st, "device latched status %d during the split search", dev_st);
+        return GS_OK;
+    };
+    auto inner = [&](int x) { return x < 1 ? 1 : (x > tiles - 1 ? tiles - 1 : x); };
+    int lo = 0, hi = tiles;
+    for (int k = 0; k < steps; k++) {
+        const int at = inner((lo + hi) / 2);
+        if ((st = count(at)) != GS_OK) return st;
+        if (cnt[0] > cnt[1]) hi = at;
+        else lo = at;
+    }
+    const int at = inner((lo + hi) / 2);
+    if (counts_out) {
+        if ((st = count(at)) != GS_OK) return st;
+        counts_out[0] = cnt[0];
+        counts_out[1] = cnt[1];
+    }
+    *split_out = at * T;
+    return cuda_check(c, "gs_split_point");
 }
 
 gs_status gs_render_fwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam,

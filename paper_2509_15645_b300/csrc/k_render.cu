@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
         }
     }
     const int64_t HW = (int64_t)W * H;
-    const float inv = 1.f / (float)(3 * HW);
+    const float inv = cam.loss_inv;
     float part = 0.f;
 #pragma unroll
     for (int j = 0; j < PPT; j++) {

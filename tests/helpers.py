@@ -105,3 +105,31 @@ def splat_max_alpha_in_tile(sp, gid, tile, tiles_x, tile_w, tile_h):
         return 0.0
     sig = 0.5 * (A * dx * dx + C * dy * dy) + B * dx * dy
     return float(np.max(np.where(inside, o * np.exp(-np.maximum(sig, 0.0)), 0.0)))
+
+
+def pixel_exclusions(r, gpu_ids=None):
+    """Pixels whose value may legitimately differ between FP32 and FP64: a
+    near-tie among the decisions that can change the pixel (square test of a
+    contributing Gaussian, the 1/255 floor, the transmittance stop), the ring
+    of pixels where a Gaussian's 3-sigma square test flips when its integer
+    radius is a near-tie, or the whole square of a Gaussian whose keep decision
+    differs (a near-tie of the cull)."""
+    ex = r["margin"] < TIE_TOL
+    sp = r["splats"]
+    H, W = ex.shape
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    ring = (sp["radius_margin"] < TIE_TOL) & (sp["keep"] == 1)
+    whole = np.zeros_like(ring)
+    if gpu_ids is not None:
+        whole[np.setxor1d(gpu_ids, np.nonzero(sp["keep"])[0])] = True
+    for i in np.nonzero(ring | whole)[0]:
+        mx, my = sp["mean2d"][i]
+        rr = sp["radius"][i]
+        if not (np.isfinite(mx) and np.isfinite(my) and rr > 0):
+            continue
+        dist = np.maximum(np.abs(xs - mx), np.abs(ys - my))
+        if whole[i]:
+            ex |= dist <= rr + 1.5
+        else:
+            ex |= np.abs(dist - rr) <= 1.01
+    return ex

@@ -11,6 +11,7 @@ import torch
 
 from helpers import (GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, sign_undetermined,
                      splat_max_alpha_in_tile)
+from helpers import pixel_exclusions as _pixel_exclusions
 from synth import scenes
 
 pytestmark = pytest.mark.gpu
@@ -83,34 +84,6 @@ def _run_fwd(gs, orc, name):
     r = orc.render(f32(P), deg, camf, tile)
     return dict(P=P, cam=camf, deg=deg, tile=tile, ctx=ctx, scene=scene, ids=ids, nv=nv, gids=gids,
                 img=img.cpu().numpy().astype(np.float64), r=r)
-
-
-def _pixel_exclusions(r, gpu_ids=None):
-    """Pixels whose value may legitimately differ between FP32 and FP64: a
-    near-tie among the decisions that can change the pixel (square test of a
-    contributing Gaussian, the 1/255 floor, the transmittance stop), the ring
-    of pixels where a Gaussian's 3-sigma square test flips when its integer
-    radius is a near-tie, or the whole square of a Gaussian whose keep decision
-    differs (a near-tie of the cull)."""
-    ex = r["margin"] < TIE_TOL
-    sp = r["splats"]
-    H, W = ex.shape
-    ys, xs = np.mgrid[0:H, 0:W] + 0.5
-    ring = (sp["radius_margin"] < TIE_TOL) & (sp["keep"] == 1)
-    whole = np.zeros_like(ring)
-    if gpu_ids is not None:
-        whole[np.setxor1d(gpu_ids, np.nonzero(sp["keep"])[0])] = True
-    for i in np.nonzero(ring | whole)[0]:
-        mx, my = sp["mean2d"][i]
-        rr = sp["radius"][i]
-        if not (np.isfinite(mx) and np.isfinite(my) and rr > 0):
-            continue
-        dist = np.maximum(np.abs(xs - mx), np.abs(ys - my))
-        if whole[i]:
-            ex |= dist <= rr + 1.5
-        else:
-            ex |= np.abs(dist - rr) <= 1.01
-    return ex
 
 
 @pytest.mark.parametrize("name", CASES)
