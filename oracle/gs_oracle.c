@@ -776,6 +776,207 @@ void orc_adam_materialize(int64_t n, int D, int64_t pitch, const double *w, cons
     }
 }
 
+/* ---------------------------------------------------------------- AdamW, SGD with momentum
+ * §4.3 states that the deferral carries over to other momentum optimizers, naming
+ * SGD with momentum and AdamW, without formulas; the catch-ups below are derived
+ * the same way as Eqs. 2-3: a Gaussian last updated at step s = t - d - 1 whose
+ * gradient was zero for the d steps s+1..t-1.
+ *
+ * AdamW (decoupled decay lambda, rho = 1 - lr lambda): each zero-gradient step j
+ * takes w <- rho w, m <- b1 m, v <- b2 v, w <- w - lr mhat / (sqrt(vhat) + eps).
+ * With eps factored out of the k-th skipped step as in Eq. 3,
+ *   w_{s+d} = rho^d w_s - wlut[d] m_s / (sqrt(v_s) + eps),
+ *   wlut[d] = sum_{k=1..d} rho^(d-k) c_k,  c_k = lr b1^k sqrt((1-b2^j)/b2^k) / (1-b1^j), j = s + k.
+ * Written over i = t - j (i = 1..d) this is the recursion
+ *   wlut[i] = (b1/sqrt(b2)) wlut[i-1] + rho^(i-1) lr b1 / ( sqrt(b2/(1-b2^(t-i))) (1-b1^(t-i)) ),
+ * the Adam table of Fig. 10 with the i-th term weighted by rho^(i-1); decay[i] = rho^i.
+ * lambda = 0 gives the Adam tables exactly.
+ *
+ * SGD with momentum mu (no dampening, no weight decay; buffer b starts at 0):
+ * each step b <- mu b + g, w <- w - lr b.  Zero-gradient steps give, exactly,
+ *   b_{s+d} = mu^d b_s,  w_{s+d} = w_s - slut[d] b_s,  slut[d] = lr (mu + ... + mu^d),
+ * so slut[i] = mu slut[i-1] + lr mu and the update step takes b <- mu^(d+1) b + g. */
+static void adamw_one(double *w, double *m, double *v, double g, int t, double lr, double b1, double b2,
+                      double eps, double wd)
+{
+    *w *= 1 - lr * wd;      /* decoupled decay first, then the Adam step */
+    adam_one(w, m, v, g, t, lr, b1, b2, eps);
+}
+
+static void sgdm_one(double *w, double *b, double g, double lr, double mu)
+{
+    *b = mu * *b + g;
+    *w -= lr * *b;
+}
+
+void orc_adamw_lut(int t, double lr, double b1, double b2, double wd, int max_defer, double *wlut, double *decay)
+{
+    double scale = b1 / sqrt(b2), rho = 1 - lr * wd;
+    wlut[0] = 0;
+    decay[0] = 1;
+    for (int i = 1; i <= max_defer; i++) {
+        decay[i] = pow(rho, i);
+        if (i > t - 1) { wlut[i] = NAN; continue; }
+        wlut[i] = scale * wlut[i - 1] +
+                  pow(rho, i - 1) * (lr * b1) / (sqrt(b2 / (1 - pow(b2, t - i))) * (1 - pow(b1, t - i)));
+    }
+}
+
+void orc_sgdm_lut(double lr, double mu, int max_defer, double *slut, double *mom)
+{
+    slut[0] = 0;
+    mom[0] = mu;
+    for (int i = 1; i <= max_defer; i++) {
+        slut[i] = mu * slut[i - 1] + lr * mu;
+        mom[i] = pow(mu, i + 1);
+    }
+}
+
+void orc_adamw_eager(int64_t n, int D, int64_t pitch, double *w, double *m, double *v, const double *g, int t,
+                     const double *lr, double b1, double b2, double eps, double wd)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++)
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            adamw_one(&w[k], &m[k], &v[k], g[k], t, lr[row_group(r)], b1, b2, eps, wd);
+        }
+}
+
+void orc_sgdm_eager(int64_t n, int D, int64_t pitch, double *w, double *b, const double *g, const double *lr,
+                    double mu)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++)
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            sgdm_one(&w[k], &b[k], g[k], lr[row_group(r)], mu);
+        }
+}
+
+/* Deferred AdamW / momentum SGD at step t: update set = ids U {counter == MAX},
+ * as orc_adam_deferred.  mode 0: the tables above, then the step with the
+ * gradient; mode 1: replay of the d zero-gradient steps, then the step. */
+void orc_adamw_deferred(int64_t n, int D, int64_t pitch, double *w, double *m, double *v, uint8_t *counter,
+                        const int32_t *ids, int64_t n_ids, const double *gc, int t, const double *lr, double b1,
+                        double b2, double eps, double wd, int max_defer, int mode)
+{
+    double wlut[6][16], dec[6][16];
+    for (int gidx = 0; gidx < 6; gidx++) orc_adamw_lut(t, lr[gidx], b1, b2, wd, max_defer, wlut[gidx], dec[gidx]);
+    int64_t *slot = malloc((n ? n : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) slot[i] = -1;
+    for (int64_t k = 0; k < n_ids; k++) slot[ids[k]] = k;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        if (!(slot[i] >= 0 || counter[i] == max_defer)) continue;
+        int d = counter[i];
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            int grp = row_group(r);
+            double g = slot[i] >= 0 ? gc[r * n_ids + slot[i]] : 0.0;
+            if (mode == 1) {
+                for (int s = t - d; s < t; s++) adamw_one(&w[k], &m[k], &v[k], 0.0, s, lr[grp], b1, b2, eps, wd);
+            } else if (d > 0) {
+                w[k] = dec[grp][d] * w[k] - wlut[grp][d] * m[k] / (sqrt(v[k]) + eps);
+                m[k] *= pow(b1, d);
+                v[k] *= pow(b2, d);
+            }
+            adamw_one(&w[k], &m[k], &v[k], g, t, lr[grp], b1, b2, eps, wd);
+        }
+    }
+    for (int64_t i = 0; i < n; i++) {
+        int in_update = slot[i] >= 0 || counter[i] == max_defer;
+        counter[i] = in_update ? 0 : (uint8_t)(counter[i] + 1);
+    }
+    free(slot);
+}
+
+void orc_sgdm_deferred(int64_t n, int D, int64_t pitch, double *w, double *b, uint8_t *counter, const int32_t *ids,
+                       int64_t n_ids, const double *gc, const double *lr, double mu, int max_defer, int mode)
+{
+    double slut[6][16], mom[16];
+    for (int gidx = 0; gidx < 6; gidx++) orc_sgdm_lut(lr[gidx], mu, max_defer, slut[gidx], mom);
+    int64_t *slot = malloc((n ? n : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) slot[i] = -1;
+    for (int64_t k = 0; k < n_ids; k++) slot[ids[k]] = k;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        if (!(slot[i] >= 0 || counter[i] == max_defer)) continue;
+        int d = counter[i];
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            int grp = row_group(r);
+            double g = slot[i] >= 0 ? gc[r * n_ids + slot[i]] : 0.0;
+            if (mode == 1) {
+                for (int s = 0; s < d; s++) sgdm_one(&w[k], &b[k], 0.0, lr[grp], mu);
+                sgdm_one(&w[k], &b[k], g, lr[grp], mu);
+            } else {
+                w[k] -= slut[grp][d] * b[k];
+                b[k] = mom[d] * b[k] + g;
+                w[k] -= lr[grp] * b[k];
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; i++) {
+        int in_update = slot[i] >= 0 || counter[i] == max_defer;
+        counter[i] = in_update ? 0 : (uint8_t)(counter[i] + 1);
+    }
+    free(slot);
+}
+
+/* Current (eager-equivalent) AdamW / SGD state after t_done completed steps,
+ * stored state untouched (tables, or replay with mode 1). */
+void orc_adamw_materialize(int64_t n, int D, int64_t pitch, const double *w, const double *m, const double *v,
+                           const uint8_t *counter, int t_done, const double *lr, double b1, double b2, double eps,
+                           double wd, int max_defer, int mode, double *w_out, double *m_out, double *v_out)
+{
+    double wlut[6][16], dec[6][16];
+    for (int gidx = 0; gidx < 6; gidx++)
+        orc_adamw_lut(t_done + 1, lr[gidx], b1, b2, wd, max_defer, wlut[gidx], dec[gidx]);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int c = counter[i];
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            int grp = row_group(r);
+            double wk = w[k], mk = m[k], vk = v[k];
+            if (c > 0) {
+                if (mode == 1) {
+                    for (int s = t_done + 1 - c; s <= t_done; s++) adamw_one(&wk, &mk, &vk, 0.0, s, lr[grp], b1, b2, eps, wd);
+                } else {
+                    wk = dec[grp][c] * wk - wlut[grp][c] * mk / (sqrt(vk) + eps);
+                    mk *= pow(b1, c);
+                    vk *= pow(b2, c);
+                }
+            }
+            w_out[k] = wk; m_out[k] = mk; v_out[k] = vk;
+        }
+    }
+}
+
+void orc_sgdm_materialize(int64_t n, int D, int64_t pitch, const double *w, const double *b, const uint8_t *counter,
+                          const double *lr, double mu, int max_defer, int mode, double *w_out, double *b_out)
+{
+    double slut[6][16], mom[16];
+    for (int gidx = 0; gidx < 6; gidx++) orc_sgdm_lut(lr[gidx], mu, max_defer, slut[gidx], mom);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int c = counter[i];
+        for (int r = 0; r < D; r++) {
+            int64_t k = r * pitch + i;
+            int grp = row_group(r);
+            double wk = w[k], bk = b[k];
+            if (mode == 1) {
+                for (int s = 0; s < c; s++) sgdm_one(&wk, &bk, 0.0, lr[grp], mu);
+            } else if (c > 0) {
+                wk -= slut[grp][c] * bk;
+                bk *= pow(mu, c);
+            }
+            w_out[k] = wk; b_out[k] = bk;
+        }
+    }
+}
+
 int orc_splat_size(void) { return (int)sizeof(orc_splat); }
 
 int orc_num_threads(void)

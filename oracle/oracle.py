@@ -266,3 +266,77 @@ def balance_split(splats, oc: OrcCamera, axis: int, steps: int = 5):
             lo = at
     at = inside((lo + hi) // 2)
     return at, split_counts(splats, axis, at)
+
+
+# ---------------------------------------------------------------------------- AdamW, SGD with momentum (§4.3)
+
+def adamw_lut(t, lr, hp: AdamHyper, wd):
+    """AdamW restore tables at step t: (wlut [MAX+1], decay [MAX+1])."""
+    K = hp.max_defer + 1
+    wl, dec = np.zeros(K), np.zeros(K)
+    lib().orc_adamw_lut(C.c_int(t), c_dbl(lr), c_dbl(hp.beta1), c_dbl(hp.beta2), c_dbl(wd), C.c_int(hp.max_defer),
+                        _p(wl), _p(dec))
+    return wl, dec
+
+
+def sgdm_lut(lr, mu, max_defer=15):
+    """Momentum-SGD restore tables: (slut [MAX+1], mom [MAX+1] = mu^(d+1))."""
+    sl, mo = np.zeros(max_defer + 1), np.zeros(max_defer + 1)
+    lib().orc_sgdm_lut(c_dbl(lr), c_dbl(mu), C.c_int(max_defer), _p(sl), _p(mo))
+    return sl, mo
+
+
+def adamw_eager(w, m, v, g, t, hp: AdamHyper, wd):
+    """One AdamW step (decoupled weight decay wd) on every value (in place)."""
+    D, n = w.shape
+    lib().orc_adamw_eager(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v),
+                          _p(np.ascontiguousarray(g, np.float64)), C.c_int(t), _p(hp.lr), c_dbl(hp.beta1),
+                          c_dbl(hp.beta2), c_dbl(hp.eps), c_dbl(wd))
+
+
+def sgdm_eager(w, b, g, lr, mu):
+    """One step of SGD with momentum mu (buffer b, no dampening) on every value (in place)."""
+    D, n = w.shape
+    lr = np.full(6, lr, np.float64) if np.isscalar(lr) else np.asarray(lr, np.float64)
+    lib().orc_sgdm_eager(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(b), _p(np.ascontiguousarray(g, np.float64)),
+                         _p(lr), c_dbl(mu))
+
+
+def adamw_deferred(w, m, v, counter, ids, g_compact, t, hp: AdamHyper, wd, mode=0):
+    """Deferred AdamW at step t (in place); mode 0 tables, mode 1 replay."""
+    D, n = w.shape
+    ids = np.ascontiguousarray(ids, np.int32)
+    gc = np.ascontiguousarray(g_compact, np.float64).reshape(D, ids.shape[0])
+    assert counter.dtype == np.uint8
+    lib().orc_adamw_deferred(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v), _p(counter), _p(ids),
+                             c_i64(ids.shape[0]), _p(gc), C.c_int(t), _p(hp.lr), c_dbl(hp.beta1), c_dbl(hp.beta2),
+                             c_dbl(hp.eps), c_dbl(wd), C.c_int(hp.max_defer), C.c_int(mode))
+
+
+def sgdm_deferred(w, b, counter, ids, g_compact, lr, mu, max_defer=15, mode=0):
+    """Deferred momentum SGD (in place); mode 0 tables, mode 1 replay."""
+    D, n = w.shape
+    lr = np.full(6, lr, np.float64) if np.isscalar(lr) else np.asarray(lr, np.float64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    gc = np.ascontiguousarray(g_compact, np.float64).reshape(D, ids.shape[0])
+    assert counter.dtype == np.uint8
+    lib().orc_sgdm_deferred(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(b), _p(counter), _p(ids), c_i64(ids.shape[0]),
+                            _p(gc), _p(lr), c_dbl(mu), C.c_int(max_defer), C.c_int(mode))
+
+
+def adamw_materialize(w, m, v, counter, t_done, hp: AdamHyper, wd, mode=0):
+    D, n = w.shape
+    wo, mo, vo = np.zeros_like(w), np.zeros_like(m), np.zeros_like(v)
+    lib().orc_adamw_materialize(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(m), _p(v), _p(counter), C.c_int(t_done),
+                                _p(hp.lr), c_dbl(hp.beta1), c_dbl(hp.beta2), c_dbl(hp.eps), c_dbl(wd),
+                                C.c_int(hp.max_defer), C.c_int(mode), _p(wo), _p(mo), _p(vo))
+    return wo, mo, vo
+
+
+def sgdm_materialize(w, b, counter, lr, mu, max_defer=15, mode=0):
+    D, n = w.shape
+    lr = np.full(6, lr, np.float64) if np.isscalar(lr) else np.asarray(lr, np.float64)
+    wo, bo = np.zeros_like(w), np.zeros_like(b)
+    lib().orc_sgdm_materialize(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(b), _p(counter), _p(lr), c_dbl(mu),
+                               C.c_int(max_defer), C.c_int(mode), _p(wo), _p(bo))
+    return wo, bo
