@@ -340,3 +340,56 @@ def sgdm_materialize(w, b, counter, lr, mu, max_defer=15, mode=0):
     lib().orc_sgdm_materialize(c_i64(n), C.c_int(D), c_i64(n), _p(w), _p(b), _p(counter), _p(lr), c_dbl(mu),
                                C.c_int(max_defer), C.c_int(mode), _p(wo), _p(bo))
     return wo, bo
+
+
+# ---------------------------------------------------------------------------- densification (§2.4 step 7)
+
+def densify(w, m, v, counter, t_done, hp: AdamHyper, grad_accum, denom, extent, normals, grad_threshold=2e-4,
+            percent_dense=0.01, min_opacity=0.005, mode=0, geo_eager=False):
+    """Periodic densification (§2.4 step 7: clone or split Gaussians with large
+    accumulated gradients, prune low-opacity ones) on a deferred-Adam state
+    after t_done steps.  The paper names the step and defers to 3DGS; the rules
+    are 3DGS's: g = grad_accum / denom (mean view-space gradient norm, 0 where
+    never seen); g >= grad_threshold clones a Gaussian whose largest scale is at
+    most percent_dense * extent and splits a larger one into two children
+    (scales / 1.6, means mu + R(q) (s * z) for the standard normals
+    normals[j] [3][n_split] passed in); then every Gaussian whose opacity is
+    below min_opacity is pruned.  New Gaussians get zero moments.
+
+    Deferred state: every decision reads the current (caught-up) values; a
+    row that is copied or split is caught up first (counter 0); other rows keep
+    their deferred w, m, v and counter.  Order of the result: survivors in
+    their order, then clones, then the children of split 0, then of split 1 (3DGS's).
+    Returns (w, m, v, counter)."""
+    from scipy.spatial.transform import Rotation
+    D, n = w.shape
+    wc, mc, vc = adam_materialize(w, m, v, counter, t_done, hp, mode=mode, geo_eager=geo_eager)
+    g = np.where(denom > 0, grad_accum / np.where(denom > 0, denom, 1), 0.0)
+    smax = np.exp(wc[3:6]).max(axis=0)
+    big = g >= grad_threshold
+    clone = big & (smax <= percent_dense * extent)
+    split = big & (smax > percent_dense * extent)
+    wd_, md_, vd_, cd_ = w.copy(), m.copy(), v.copy(), counter.copy()
+    aff = clone | split
+    wd_[:, aff], md_[:, aff], vd_[:, aff], cd_[aff] = wc[:, aff], mc[:, aff], vc[:, aff], 0
+    ids_s = np.nonzero(split)[0]
+    q = wc[6:10, ids_s]                                            # (w, x, y, z)
+    R = Rotation.from_quat(np.stack([q[1], q[2], q[3], q[0]], axis=1)).as_matrix() if len(ids_s) else np.zeros((0, 3, 3))
+    s = np.exp(wc[3:6, ids_s])
+    parts_w = [wd_[:, ~split], wc[:, clone]]
+    cur_w = [wc[:, ~split], wc[:, clone]]                          # current values, for the prune decision
+    for j in range(2):
+        child = wc[:, ids_s].copy()
+        child[0:3] += np.einsum("kab,bk->ak", R, s * normals[j])
+        child[3:6] = np.log(s / 1.6)
+        parts_w.append(child)
+        cur_w.append(child)
+    n_new = int(clone.sum()) + 2 * len(ids_s)
+    W2 = np.concatenate(parts_w, axis=1)
+    M2 = np.concatenate([md_[:, ~split], np.zeros((D, n_new))], axis=1)
+    V2 = np.concatenate([vd_[:, ~split], np.zeros((D, n_new))], axis=1)
+    C2 = np.concatenate([cd_[~split], np.zeros(n_new, np.uint8)])
+    opac = 1.0 / (1.0 + np.exp(-np.concatenate(cur_w, axis=1)[10]))
+    keep = opac >= min_opacity
+    return (np.ascontiguousarray(W2[:, keep]), np.ascontiguousarray(M2[:, keep]),
+            np.ascontiguousarray(V2[:, keep]), np.ascontiguousarray(C2[keep]))
