@@ -127,3 +127,32 @@ def test_staging_ring_configuration(lib):
         assert size(**bad)[0] == _lib.GS_ERR_INVALID_ARG, bad
     for good in (dict(tile_w=8, tile_h=4), dict(tile_w=4, tile_h=8), dict(tile_w=64, tile_h=4)):
         assert size(**good)[0] == _lib.GS_OK, good
+
+
+def test_region_cameras_marshal_the_full_image():
+    """split_regions tiles the view; each region's struct carries the view's
+    intrinsics (the library moves the principal point), its origin and the
+    full image size; a whole-image camera leaves the region fields at 0."""
+    import numpy as np
+    import torch
+    from paper_2509_15645_b300 import api
+    from synth import scenes
+    cam = scenes.camera_lookat((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 120, 80, 60.0, up=(0, -1, 0))
+    whole = api.camera_struct(cam)
+    assert (whole.x0, whole.y0, whole.full_width, whole.full_height) == (0, 0, 0, 0)
+    img = torch.arange(3 * 80 * 120, dtype=torch.float32).view(3, 80, 120)
+    for axis, split in ((0, 48), (1, 32)):
+        regs = api.split_regions(cam, axis, split)
+        area = 0
+        for r in regs:
+            cs = api.camera_struct(r)
+            assert (cs.full_width, cs.full_height) == (120, 80)
+            assert (cs.x0, cs.y0, cs.width, cs.height) == (r.x0, r.y0, r.width, r.height)
+            assert cs.cx == whole.cx and cs.cy == whole.cy and cs.fx == whole.fx
+            crop = r.crop(img)
+            assert crop.is_contiguous() and tuple(crop.shape) == (3, r.height, r.width)
+            assert torch.equal(crop, img[:, r.y0:r.y0 + r.height, r.x0:r.x0 + r.width])
+            area += r.width * r.height
+        assert area == 120 * 80
+        assert (regs[1].x0, regs[1].y0) == ((split, 0) if axis == 0 else (0, split))
+    assert np.all(np.asarray(regs[0].R) == np.asarray(cam.R))
