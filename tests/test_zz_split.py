@@ -1,7 +1,9 @@
 """GPU parity of balance-aware image splitting (GS-Scale §4.4): the split
 search against the oracle's, region renders stitched against the whole view,
 and one training step over a view's two regions against the oracle's
-whole-view step (the paper's claim: the split is mathematically equivalent)."""
+whole-view step (the paper's claim: the split is mathematically equivalent).
+This file sorts last so that a run stopping at its first failure has already
+run every other test."""
 import numpy as np
 import pytest
 import torch
