@@ -58,11 +58,13 @@ def test_split_point_matches_oracle(gs, orc, axis):
     assert abs(counts[0] - ref[0]) <= ties and abs(counts[1] - ref[1]) <= ties, (counts, ref, ties)
 
 
-@pytest.mark.parametrize("axis,split", [(0, 56), (1, 48), (0, 8)])
+@pytest.mark.parametrize("axis,split", [(0, 56), (1, 48), (0, 8), (0, 61), (1, 37)])
 def test_region_renders_stitch_to_the_view(gs, orc, axis, split):
     """Each region culls and renders on its own; placed side by side their
-    images are the whole view's (oracle, FP64) and the union of their visible
-    sets is the whole view's."""
+    images are the whole view's (oracle, FP64).  With the split on a tile
+    boundary the union of their visible sets is the whole view's; elsewhere a
+    region's last tile reaches past its pixels and may keep Gaussians that
+    touch no pixel of it."""
     P = _scene()
     cam, n = _cam(), P.shape[1]
     ctx = _ctx(gs, n)
@@ -78,8 +80,10 @@ def test_region_renders_stitch_to_the_view(gs, orc, axis, split):
         vis.append(ids[:int(nv.item())].cpu().numpy())
     union = np.union1d(vis[0], vis[1])
     ties = np.nonzero(r["splats"]["margin"] < TIE_TOL)[0]
-    diff = np.setxor1d(union, np.nonzero(r["splats"]["keep"])[0])
-    assert np.all(np.isin(diff, ties)), diff
+    kept = np.nonzero(r["splats"]["keep"])[0]
+    assert np.all(np.isin(np.setdiff1d(kept, union), ties))           # nothing the view keeps is lost
+    if split % TILE[axis] == 0:
+        assert np.all(np.isin(np.setxor1d(union, kept), ties))
     ex = pixel_exclusions(r, union)
     ok = ~ex[None, :, :].repeat(3, 0)
     assert ex.mean() < 0.03, ex.mean()
