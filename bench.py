@@ -548,6 +548,59 @@ def cpu_baseline(args, sample_frac=0.1, steps=1):
             "seconds_per_sample_step": round(dt, 3)}
 
 
+def run_oracle_workloads(args):
+    """FP64 oracle timings on the host cores for every workload (a baseline for
+    context, never a target): full steps of the 10k and 200k cases, the first
+    three steps of the 1M orbit, one step of the 10M aerial workload and its
+    cull and deferred Adam alone; single-threaded and on every core.  The 40M
+    case is not run: its FP64 w, m, v alone need 57 GB.  One JSON line per
+    (workload, threads)."""
+    from oracle import oracle as orc
+    from synth import scenes
+    all_cores = orc.num_threads()
+    hp = orc.AdamHyper(lr=1e-3, eps=1e-15)
+
+    def cases():
+        c = scenes.cfg_small_step()
+        yield "cube10k_64px_sh0", c["scene"], c["target_scene"], c["cams"][:1], 0, False
+        c = scenes.cfg_diff_check()
+        yield "cube200k_512px_sh3", c["scene"], c["target_scene"], c["cams"][:1], 3, False
+        c = scenes.cfg_heightfield_1m(n_views=3)
+        yield "heightfield1m_1080p_sh3 (steps 1-3)", c["scene"], None, c["cams"][:3], 3, False
+        c = scenes.cfg_aerial(n_views=1)
+        yield WORKLOAD, c["scene"], None, c["cams"][:1], 3, True
+
+    for name, P32, T32, cams, deg, split_stages in cases():
+        P = np.ascontiguousarray(P32, np.float64)
+        n = P.shape[1]
+        for threads in (1, all_cores):
+            orc.set_num_threads(threads)
+            W_, M_, V_ = P.copy(), np.zeros_like(P), np.zeros_like(P)
+            C_ = np.zeros(n, np.uint8)
+            times, line = [], {"workload": name, "gaussians": n, "threads": threads, "impl": "reference",
+                               "kind": "oracle"}
+            for s, cam in enumerate(cams):
+                target = (orc.render(np.asarray(T32, np.float64), deg, cam)["image"] if T32 is not None
+                          else np.zeros((3, cam.height, cam.width)))
+                t0 = time.perf_counter()
+                _, n_vis = _oracle_step(orc, P, deg, cam, target, W_, M_, V_, C_, s + 1, hp)
+                times.append(time.perf_counter() - t0)
+            line.update(seconds_per_step=[round(t, 3) for t in times], visible=int(n_vis))
+            if split_stages:
+                # the cull (projection of every Gaussian) and the deferred update alone
+                t0 = time.perf_counter()
+                sp = orc.project(W_, deg, orc.camera(cams[0]))
+                t_cull = time.perf_counter() - t0
+                kept = np.nonzero(sp["keep"])[0].astype(np.int32)
+                g = np.zeros((P.shape[0], kept.size))
+                t0 = time.perf_counter()
+                orc.adam_deferred(W_, M_, V_, C_, kept, g, len(cams) + 1, hp)
+                t_adam = time.perf_counter() - t0
+                line.update(cull_seconds=round(t_cull, 3), adam_seconds=round(t_adam, 3))
+            print(json.dumps(line), flush=True)
+        del P
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -604,10 +657,14 @@ def main():
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
     ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
+    ap.add_argument("--oracle-workloads", action="store_true",
+                    help="with --impl reference: time the FP64 oracle on every workload, 1 thread and all cores")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.impl == "reference" and args.oracle_workloads:
+        run_oracle_workloads(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -13,8 +13,9 @@
  *    buffer it passes; the context owns only its scratch workspace.
  *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
  *    void*; NULL = legacy default stream) and never synchronises, except
- *    gs_sync_status, gs_create/gs_destroy, gs_timing_read and gs_step on a
- *    host-tier scene (which waits once for its chunk-touch map).  A context
+ *    gs_sync_status, gs_create/gs_destroy, gs_timing_read, gs_autotune,
+ *    gs_split_point (once per bisection round) and gs_step on a host-tier scene
+ *    (which waits once for its chunk-touch map).  A context
  *    must be driven from one stream at a time.
  *  - Invalid arguments return GS_ERR_INVALID_ARG before anything is launched;
  *    a failed launch returns GS_ERR_CUDA.  Errors found on the device (a
@@ -284,8 +285,10 @@ GS_API gs_status gs_grad_scatter(gs_ctx *ctx, const gs_scene *scene, const int32
  * view, render, L1 loss against targets[v] (device fp32 [3][H][W] each),
  * backward, gradients summed over the views, one optimizer step over the union
  * of the visible sets.  *loss_out (device) = sum over views of the L1 losses.
- * Replays a CUDA graph captured on the first call with the same scene
- * pointers, view count and image sizes.  Increments scene->step. */
+ * The views may be the regions of one split view (§4.4; targets[v] then holds
+ * the region's pixels): the step is then the whole view's.  Replays a CUDA
+ * graph captured on the first call with the same scene pointers, view count
+ * and image sizes.  Increments scene->step. */
 GS_API gs_status gs_step(gs_ctx *ctx, gs_scene *scene, const gs_camera *views, const float *const *targets,
                   int32_t n_views, const gs_adam_cfg *adam, float *loss_out, void *stream);
 

@@ -979,6 +979,15 @@ void orc_sgdm_materialize(int64_t n, int D, int64_t pitch, const double *w, cons
 
 int orc_splat_size(void) { return (int)sizeof(orc_splat); }
 
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

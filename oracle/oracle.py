@@ -224,6 +224,11 @@ def num_threads() -> int:
     return lib().orc_num_threads()
 
 
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls (timing only)."""
+    lib().orc_set_num_threads(C.c_int(int(n)))
+
+
 def depth_bits(depth_f64) -> np.ndarray:
     return np.asarray(depth_f64, np.float64).astype(np.float32).view(np.uint32)
 
