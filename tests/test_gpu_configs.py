@@ -26,7 +26,14 @@ def gs():
 
 
 def test_deferred_equals_eager_on_the_1m_orbit(gs):
-    c = scenes.cfg_heightfield_1m()
+    f = deferred_vs_eager_on_orbit(gs, orbit_radius=55.0)
+    assert 0.15 <= f <= 0.25, f                  # the orbit's mean visible fraction (oracle cull: 18.9%)
+
+
+def deferred_vs_eager_on_orbit(gs, orbit_radius):
+    """Deferred against eager Adam over the 100-view orbit of the given radius
+    (60 m altitude); returns the mean visible fraction."""
+    c = scenes.cfg_heightfield_1m(orbit_radius=orbit_radius)
     P, deg, cams = c["scene"], c["sh_degree"], [cam_f32(k) for k in c["cams"]]
     n, D = P.shape[1], P.shape[0]
     W, H = cams[0].width, cams[0].height
@@ -75,8 +82,7 @@ def test_deferred_equals_eager_on_the_1m_orbit(gs):
     assert worst <= 2e-5, worst
     touched = (B.m[:, :n] != 0).sum().item()
     assert eps_regime.sum().item() <= 0.02 * touched, (eps_regime.sum().item(), touched)
-    f = float(np.mean(fractions))
-    assert 0.05 <= f <= 0.6, f                   # the orbit sees a part of the scene per view
+    return float(np.mean(fractions))
 
 
 def test_gradients_at_200k_against_oracle_and_differences(gs, orc):
