@@ -205,6 +205,64 @@ def test_brute_force_equals_tiled(orc, seed):
     assert r["n_contrib"].max() > 3
 
 
+def _composite_untruncated(sp, P, W, H):
+    """Per pixel, every Gaussian that survives the 3D cull with a positive
+    determinant, in (FP32 depth, id) order, with the alpha floor, the 0.999
+    clamp and the transmittance stop but without the 3-sigma square (nor the
+    2D cull that follows from it).  Degree-0 colours and opacities straight
+    from the parameters.  Returns the image and, per pixel, the summed alpha of
+    the contributions the square test drops, and their largest alpha / o."""
+    ok = np.isfinite(sp["conic"][:, 0]) & (sp["depth"] > 0.01) & (sp["cov2d"][:, 0] * sp["cov2d"][:, 2] -
+                                                                  sp["cov2d"][:, 1] ** 2 > 0)
+    ids = np.nonzero(ok)[0]
+    order = ids[np.lexsort((ids, sp["depth_f32"][ids]))]
+    o = 1.0 / (1.0 + np.exp(-P[10]))
+    rgb = np.maximum(P[11:14] * C0 + 0.5, 0.0)
+    img = np.zeros((3, H, W))
+    dropped = np.zeros((H, W))
+    worst = 0.0
+    for py in range(H):
+        for px in range(W):
+            T = 1.0
+            for i in order:
+                dx, dy = px + 0.5 - sp["mean2d"][i, 0], py + 0.5 - sp["mean2d"][i, 1]
+                A, B, Cc = sp["conic"][i]
+                sig = 0.5 * (A * dx * dx + Cc * dy * dy) + B * dx * dy
+                if sig < 0:
+                    continue
+                a = min(0.999, o[i] * math.exp(-sig))
+                if a < 1 / 255:
+                    continue
+                if T * (1 - a) < 1e-4:
+                    break
+                r = sp["radius"][i]
+                if not (sp["keep"][i] and abs(dx) <= r and abs(dy) <= r):
+                    dropped[py, px] += a
+                    worst = max(worst, a / o[i])
+                img[:, py, px] += rgb[:, i] * a * T
+                T *= 1 - a
+    return img, dropped, worst
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_truncation_error_of_the_3sigma_square(orc, seed):
+    """Informational: the 3-sigma square drops contributions with sigma >= 4.5
+    (outside the square |d| > r >= 3 sqrt(lambda_max)), so each dropped alpha
+    is at most o e^-4.5, and the image moves by at most about twice the
+    colour-weighted sum of the dropped alphas (their own share plus the
+    transmittance they take from what lies behind) plus the stop tolerance."""
+    P, cam = _tiny_scene(seed, n=60, deg=0, W=24, H=16)
+    P[3:6] += 0.8                                   # larger splats: more of them reach past their squares
+    r = orc.render(P, 0, cam, tile=(8, 8))
+    img, dropped, worst = _composite_untruncated(r["splats"], P, cam.width, cam.height)
+    assert worst <= math.exp(-4.5) * (1 + 1e-12), worst
+    cmax = float(np.maximum(P[11:14] * C0 + 0.5, 0.0).max())
+    err = np.abs(img - r["image"]).max(axis=0)
+    assert np.all(err <= 2 * cmax * dropped + 2e-4 * cmax + 1e-12), float((err - 2 * cmax * dropped).max())
+    print(f"3-sigma truncation: max |untruncated - tiled| = {err.max():.3e}, pixels affected "
+          f"{np.mean(dropped > 0):.1%}")
+
+
 def test_sort_against_library_lexsort(orc):
     P, cam = _tiny_scene(5, n=200)
     r = orc.render(P, 0, cam, tile=(8, 8))
