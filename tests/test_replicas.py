@@ -66,3 +66,16 @@ def test_reference_arm_on_other_ranks_exits_quietly():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""                   # rank 0 alone prints the line
+
+
+def test_bench_command_line_contract():
+    """The driver's flags exist, and fewer than 3 warm-up steps are refused
+    before any work (argparse exit status 2)."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0
+    for flag in ("--gpus", "--steps", "--warmup", "--impl"):
+        assert flag in out.stdout
+    bad = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "2"],
+                         capture_output=True, text=True, timeout=120)
+    assert bad.returncode == 2 and "warmup" in bad.stderr
