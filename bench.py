@@ -163,6 +163,21 @@ def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False, n_cand=None):
     return cull, apply, select
 
 
+def method_bytes(N, D, n_vis, n_upd, bf16=False):
+    """The method's algorithmic bytes per step for the cull and the deferred
+    update, as planned from the paper's algorithm (restore reading w, m and v;
+    every Gaussian's geometry planes read once): cull 121 N + N/8 + 4 |V| in
+    fp32 (w, m, v of the 10 geometry planes and the counter), 81 N + ... with
+    bf16 moments; update 2 N (counters) + 28 D |U| (w, m, v read and written)
+    + 4 |V| in fp32, 2 N + (11 * 20 + (D - 11) * 16) |U| + 4 |V| with bf16 SH
+    and moments.  The kernels move less (restore directions instead of m and v,
+    rotation planes only for the pre-test's survivors): `algorithmic_bytes`."""
+    cull = (81.0 if bf16 else 121.0) * N + N / 8.0 + 4.0 * n_vis
+    per_member = (11 * 20.0 + (D - 11) * 16.0) if bf16 else 28.0 * D
+    adam = 2.0 * N + per_member * n_upd + 4.0 * n_vis
+    return cull, adam
+
+
 def run_ours(args):
     import torch
     import paper_2509_15645_b300 as gs
@@ -384,6 +399,10 @@ def run_ours(args):
             "peak_gbs": peak, "cull_bytes": round(b_cull), "adam_bytes": round(b_apply + b_select)}
         ca = m["cull_adam"]
         ca["cull_plus_adam_frac"] = ca["cull_plus_adam_gbs"] and ca["cull_plus_adam_gbs"] / peak
+        mb_cull, mb_adam = method_bytes(N, D, m["n_vis"], m["n_upd"], bf16=precision != gs.GS_FP32)
+        ca["method_bytes"] = round(mb_cull + mb_adam)
+        ca["cull_plus_adam_method_gbs"] = gbs(mb_cull + mb_adam, (st["cull"] or 0) + (st["adam"] or 0))
+        ca["cull_plus_adam_method_frac"] = ca["cull_plus_adam_method_gbs"] and ca["cull_plus_adam_method_gbs"] / peak
         for k in list(ca):
             if isinstance(ca[k], float):
                 ca[k] = round(ca[k], 4 if k.endswith("frac") else 1)

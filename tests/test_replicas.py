@@ -79,3 +79,20 @@ def test_bench_command_line_contract():
     bad = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "2"],
                          capture_output=True, text=True, timeout=120)
     assert bad.returncode == 2 and "warmup" in bad.stderr
+
+
+def test_method_bytes_per_step():
+    """The method's cull and deferred-update bytes at 10M Gaussians, SH degree
+    3, 20% visible and 25% in the update set: 121 N + N/8 + 4 |V| = 1.219 GB
+    and 2 N + 28 D |U| + 4 |V| = 4.158 GB in fp32; the bf16 form moves 81 N + ...
+    and 2 N + 988 |U| + ... ."""
+    sys.path.insert(0, ROOT)
+    import bench
+    N, D = 10_000_000, 59
+    cull, adam = bench.method_bytes(N, D, 0.2 * N, 0.25 * N)
+    assert cull == pytest.approx(1.21925e9) and adam == pytest.approx(4.158e9)
+    cull_b, adam_b = bench.method_bytes(N, D, 0.2 * N, 0.25 * N, bf16=True)
+    assert cull_b == pytest.approx(81e7 + 1.25e6 + 8e6) and adam_b == pytest.approx(2e7 + 988 * 2.5e6 + 8e6)
+    # the kernels' own traffic is below the method's: restore directions instead of m, v
+    k_cull, k_apply, k_select = bench.algorithmic_bytes(N, D, 0.2 * N, 0.25 * N, 0.1 * N, n_cand=0.07 * N)
+    assert k_cull < cull and k_apply + k_select < adam * 1.2
