@@ -292,7 +292,8 @@ void orc_project(int64_t n, int deg, const double *P, int64_t pitch, const orc_c
 }
 
 /* ---------------------------------------------------------------- keys and order
- * Step 2 of §2.4: one key per (tile in rect, Gaussian); key = tile id * 2^32 +
+ * Step 2 of §2.4: one key per (tile in rect that the Gaussian reaches, Gaussian);
+ * key = tile id * 2^32 +
  * bits of the float32 depth; ties broken by ascending Gaussian id. */
 typedef struct { uint64_t key; int64_t gid; } orc_key;
 
@@ -305,11 +306,80 @@ static int key_cmp(const void *pa, const void *pb)
     return a->gid < b->gid ? -1 : (a->gid > b->gid ? 1 : 0);
 }
 
-int64_t orc_count_keys(int64_t n, const orc_splat *sp)
+/* Reading of §2.4 step 2 (which tiles a Gaussian is binned into): the paper
+ * and 3DGS bin a Gaussian into every tile of its rectangle; here a (tile,
+ * Gaussian) pair is kept only if the Gaussian can reach alpha >= 1/255
+ * somewhere in the tile.  "Somewhere" is the rectangle spanned by the
+ * centres of the tile's tile_w x tile_h pixels (the whole tile of the grid,
+ * also past the image edge of a ragged last tile), intersected with the
+ * Gaussian's 3-sigma square widened by `ext` pixels.  Over that rectangle the
+ * largest value of o exp(-sigma) is taken exactly: sigma(d) = 1/2 (A dx^2 +
+ * C dy^2) + B dx dy with d = mean2d - p is a positive-definite quadratic
+ * (the conic of a kept Gaussian), so its minimum over a rectangle is 0 when
+ * d = 0 lies inside and otherwise lies on an edge, where sigma is a convex
+ * quadratic in one variable minimised at the clamped stationary point.  A
+ * dropped pair has no pixel centre with alpha >= 1/255, so no pixel changes.
+ * Returns 0 for an empty intersection. */
+static double sigma_at(const double *q, double dx, double dy)
+{
+    return 0.5 * (q[0] * dx * dx + q[2] * dy * dy) + q[1] * dx * dy;
+}
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+double orc_tile_reach(const orc_splat *g, const orc_camera *cam, int tx, int ty, double ext)
+{
+    const double X0 = tx * cam->tile_w + 0.5, X1 = X0 + cam->tile_w - 1;
+    const double Y0 = ty * cam->tile_h + 0.5, Y1 = Y0 + cam->tile_h - 1;
+    const double r = g->radius + ext;
+    const double x0 = dmax(X0, g->mean2d[0] - r), x1 = dmin(X1, g->mean2d[0] + r);
+    const double y0 = dmax(Y0, g->mean2d[1] - r), y1 = dmin(Y1, g->mean2d[1] + r);
+    if (x0 > x1 || y0 > y1) return 0.0;
+    /* d = mean2d - p ranges over [dx_lo, dx_hi] x [dy_lo, dy_hi] */
+    const double dx_lo = g->mean2d[0] - x1, dx_hi = g->mean2d[0] - x0;
+    const double dy_lo = g->mean2d[1] - y1, dy_hi = g->mean2d[1] - y0;
+    const double *q = g->conic;
+    double smin;
+    if (dx_lo <= 0 && dx_hi >= 0 && dy_lo <= 0 && dy_hi >= 0) {
+        smin = 0.0;
+    } else {
+        const double dxe[2] = {dx_lo, dx_hi}, dye[2] = {dy_lo, dy_hi};
+        smin = INFINITY;
+        for (int k = 0; k < 2; k++) {
+            /* edge dx = const: d sigma / d dy = C dy + B dx = 0 */
+            const double dy = clampd(-q[1] * dxe[k] / q[2], dy_lo, dy_hi);
+            smin = dmin(smin, sigma_at(q, dxe[k], dy));
+            /* edge dy = const: d sigma / d dx = A dx + B dy = 0 */
+            const double dx = clampd(-q[1] * dye[k] / q[0], dx_lo, dx_hi);
+            smin = dmin(smin, sigma_at(q, dx, dye[k]));
+        }
+        smin = dmax(smin, 0.0);
+    }
+    return g->opacity * exp(-smin);
+}
+
+static int pair_kept(const orc_splat *g, const orc_camera *cam, int tx, int ty)
+{
+    return orc_tile_reach(g, cam, tx, ty, 0.0) >= ALPHA_MIN;
+}
+
+/* orc_tile_reach for n pairs (gid[k], tile[k]). */
+void orc_tile_reach_many(int64_t n_pairs, const orc_splat *sp, const orc_camera *cam, const int64_t *gid,
+                         const int64_t *tile, double ext, double *out)
+{
+    const int tiles_x = (cam->width + cam->tile_w - 1) / cam->tile_w;
+    for (int64_t k = 0; k < n_pairs; k++)
+        out[k] = orc_tile_reach(&sp[gid[k]], cam, (int)(tile[k] % tiles_x), (int)(tile[k] / tiles_x), ext);
+}
+
+int64_t orc_count_keys(int64_t n, const orc_splat *sp, const orc_camera *cam)
 {
     int64_t K = 0;
-    for (int64_t i = 0; i < n; i++)
-        if (sp[i].keep) K += (int64_t)(sp[i].rect[1] - sp[i].rect[0]) * (sp[i].rect[3] - sp[i].rect[2]);
+    for (int64_t i = 0; i < n; i++) {
+        if (!sp[i].keep) continue;
+        for (int ty = sp[i].rect[2]; ty < sp[i].rect[3]; ty++)
+            for (int tx = sp[i].rect[0]; tx < sp[i].rect[1]; tx++) K += pair_kept(&sp[i], cam, tx, ty);
+    }
     return K;
 }
 
@@ -319,13 +389,14 @@ void orc_build_lists(int64_t n, const orc_splat *sp, const orc_camera *cam,
 {
     int tiles_x = (cam->width + cam->tile_w - 1) / cam->tile_w;
     int tiles_y = (cam->height + cam->tile_h - 1) / cam->tile_h;
-    int64_t K = orc_count_keys(n, sp);
+    int64_t K = orc_count_keys(n, sp, cam);
     orc_key *keys = malloc((K ? K : 1) * sizeof(orc_key));
     int64_t o = 0;
     for (int64_t i = 0; i < n; i++) {
         if (!sp[i].keep) continue;
         for (int ty = sp[i].rect[2]; ty < sp[i].rect[3]; ty++)
             for (int tx = sp[i].rect[0]; tx < sp[i].rect[1]; tx++) {
+                if (!pair_kept(&sp[i], cam, tx, ty)) continue;
                 keys[o].key = ((uint64_t)(ty * tiles_x + tx) << 32) | f32_bits(sp[i].depth);
                 keys[o].gid = i;
                 o++;

@@ -86,15 +86,29 @@ def project(params, deg: int, oc: OrcCamera) -> np.ndarray:
 
 
 def build_lists(splats: np.ndarray, oc: OrcCamera):
-    """Step 2 of §2.4: sorted (tile, Gaussian id) keys and per-tile ranges."""
+    """Step 2 of §2.4: sorted (tile, Gaussian id) keys and per-tile ranges.  A
+    pair is kept when the Gaussian reaches alpha >= 1/255 in the tile
+    (``tile_reach``)."""
     n = splats.shape[0]
-    K = lib().orc_count_keys(c_i64(n), _p(splats))
+    K = lib().orc_count_keys(c_i64(n), _p(splats), C.byref(oc))
     tx, ty = tiles_of(oc)
     key_tile = np.zeros(max(K, 1), np.int32)
     key_gid = np.zeros(max(K, 1), np.int64)
     ranges = np.zeros(2 * tx * ty, np.int64)
     lib().orc_build_lists(c_i64(n), _p(splats), C.byref(oc), _p(key_tile), _p(key_gid), _p(ranges))
     return key_tile[:K], key_gid[:K], ranges.reshape(-1, 2)
+
+
+def tile_reach(splats, oc: OrcCamera, gids, tiles, ext=0.0):
+    """Largest o exp(-sigma) of Gaussian gids[k] over the box of tile tiles[k]'s
+    pixel centres inside its 3-sigma square widened by ``ext`` pixels (0 where
+    they do not meet): the quantity the list filter compares with 1/255."""
+    g = np.ascontiguousarray(gids, np.int64).ravel()
+    t = np.ascontiguousarray(tiles, np.int64).ravel()
+    assert g.shape == t.shape
+    out = np.zeros(g.shape[0])
+    lib().orc_tile_reach_many(c_i64(g.shape[0]), _p(splats), C.byref(oc), _p(g), _p(t), c_dbl(ext), _p(out))
+    return out
 
 
 def composite(splats, oc: OrcCamera, key_gid, ranges, bg=(0.0, 0.0, 0.0)):

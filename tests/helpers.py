@@ -88,25 +88,6 @@ def check_lists(gpu_tiles, gpu_gids, oracle_tiles, oracle_gids, depth_bits, excl
     return len(bad)
 
 
-def splat_max_alpha_in_tile(sp, gid, tile, tiles_x, tile_w, tile_h):
-    """Largest opacity * exp(-sigma) over the pixel centres of `tile` inside
-    the splat's 3-sigma square, in FP64 from the oracle's splat (mean, conic,
-    radius, opacity): the bound a list filter may use to drop the tile."""
-    mx, my = sp["mean2d"][gid]
-    A, B, C = sp["conic"][gid]
-    r, o = sp["radius"][gid], sp["opacity"][gid]
-    tx, ty = tile % tiles_x, tile // tiles_x
-    xs = np.arange(tx * tile_w, (tx + 1) * tile_w) + 0.5
-    ys = np.arange(ty * tile_h, (ty + 1) * tile_h) + 0.5
-    dx = (mx - xs)[None, :]
-    dy = (my - ys)[:, None]
-    inside = (np.abs(dx) <= r) & (np.abs(dy) <= r)
-    if not inside.any():
-        return 0.0
-    sig = 0.5 * (A * dx * dx + C * dy * dy) + B * dx * dy
-    return float(np.max(np.where(inside, o * np.exp(-np.maximum(sig, 0.0)), 0.0)))
-
-
 def pixel_exclusions(r, gpu_ids=None):
     """Pixels whose value may legitimately differ between FP32 and FP64: a
     near-tie among the decisions that can change the pixel (square test of a

@@ -277,6 +277,10 @@ def test_sort_against_library_lexsort(orc):
                 bits.append(np.float32(sp["depth"][i]).view(np.uint32))
                 gids.append(i)
     tiles, bits, gids = map(np.asarray, (tiles, bits, gids))
+    # the pairs the Gaussian can reach (the list filter, pinned on its own below)
+    reach = orc.tile_reach(sp, r["cam"], gids, tiles) >= 1 / 255
+    assert 0 < reach.sum() < len(reach)
+    tiles, bits, gids = tiles[reach], bits[reach], gids[reach]
     order = np.lexsort((gids, bits, tiles))
     np.testing.assert_array_equal(r["key_tile"], tiles[order])
     np.testing.assert_array_equal(r["key_gid"], gids[order])
@@ -285,6 +289,84 @@ def test_sort_against_library_lexsort(orc):
         b, e = r["ranges"][t]
         assert np.all(r["key_tile"][b:e] == t)
         assert e - b == np.count_nonzero(tiles == t)
+
+
+def _reach_by_sampling(sp, i, tile, tiles_x, tw, th, ext, m=241):
+    """o exp(-sigma) maximised over an m x m grid of the box of the tile's pixel
+    centres cut to the (widened) 3-sigma square, plus its corners."""
+    mx, my = sp["mean2d"][i]
+    r = sp["radius"][i] + ext
+    X0 = (tile % tiles_x) * tw + 0.5
+    Y0 = (tile // tiles_x) * th + 0.5
+    x0, x1 = max(X0, mx - r), min(X0 + tw - 1, mx + r)
+    y0, y1 = max(Y0, my - r), min(Y0 + th - 1, my + r)
+    if x0 > x1 or y0 > y1:
+        return 0.0
+    xs, ys = np.linspace(x0, x1, m), np.linspace(y0, y1, m)
+    dx = (mx - xs)[None, :]
+    dy = (my - ys)[:, None]
+    A, B, Cc = sp["conic"][i]
+    sig = 0.5 * (A * dx * dx + Cc * dy * dy) + B * dx * dy
+    return float(sp["opacity"][i] * np.exp(-sig.min()))
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 4), (4, 8)])
+def test_tile_reach_against_sampling(orc, tile):
+    """The list filter's quantity -- the largest o exp(-sigma) over the part of
+    a tile that the Gaussian's square covers -- against a dense grid: never
+    below any sampled value, and within the grid's resolution of the largest.
+    Anisotropic splats near tile corners, where the minimiser lies inside an
+    edge, make a dropped or mis-signed cross term B visible."""
+    P, cam = _tiny_scene(7, n=200)
+    P[3:6] += np.random.default_rng(7).normal(0, 0.6, (3, P.shape[1]))
+    r = orc.render(P, 0, cam, tile=tile)
+    sp, oc = r["splats"], r["cam"]
+    tx, _ = orc.tiles_of(oc)
+    pairs = []
+    for i in np.nonzero(sp["keep"])[0]:
+        x0, x1, y0, y1 = sp["rect"][i]
+        for ty in range(y0, y1):
+            for txx in range(x0, x1):
+                pairs.append((i, ty * tx + txx))
+    pairs = np.asarray(pairs)
+    rng = np.random.default_rng(1)
+    pairs = pairs[rng.choice(len(pairs), size=min(400, len(pairs)), replace=False)]
+    for ext in (0.0, 0.7):
+        got = orc.tile_reach(sp, oc, pairs[:, 0], pairs[:, 1], ext=ext)
+        ref = np.array([_reach_by_sampling(sp, i, t, tx, tile[0], tile[1], ext) for i, t in pairs])
+        assert np.all(got >= ref * (1 - 1e-12)), np.max(ref - got)
+        assert np.all(got <= ref * (1 + 2e-3) + 1e-300), np.max(got / np.maximum(ref, 1e-300))
+        o = sp["opacity"][pairs[:, 0]]
+        assert np.any(got == o) and np.any((got > 0) & (got < o))   # mean inside the box, and outside
+
+
+def test_lists_hold_every_contributing_pair(orc):
+    """Every (tile, Gaussian) whose tile has a pixel centre where the per-pixel
+    rule lets the Gaussian contribute (square test, alpha >= 1/255) is in the
+    oracle's lists, found by brute force over all pixels; and the filter does
+    drop pairs of the rectangles (the rule has an effect here)."""
+    P, cam = _tiny_scene(8, n=200)
+    tile = (8, 4)
+    r = orc.render(P, 0, cam, tile=tile)
+    sp = r["splats"]
+    tx, _ = orc.tiles_of(r["cam"])
+    listed = set(zip(r["key_tile"].tolist(), r["key_gid"].tolist()))
+    H, W = cam.height, cam.width
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    n_rect = 0
+    for i in np.nonzero(sp["keep"])[0]:
+        mx, my = sp["mean2d"][i]
+        A, B, Cc = sp["conic"][i]
+        dx, dy = xs - mx, ys - my
+        sig = 0.5 * (A * dx * dx + Cc * dy * dy) + B * dx * dy
+        alpha = np.minimum(0.999, sp["opacity"][i] * np.exp(-sig))
+        rr = sp["radius"][i]
+        ok = (np.abs(dx) <= rr) & (np.abs(dy) <= rr) & (alpha >= 1 / 255)
+        for py, px in zip(*np.nonzero(ok)):
+            assert ((py // tile[1]) * tx + px // tile[0], i) in listed
+        x0, x1, y0, y1 = sp["rect"][i]
+        n_rect += (x1 - x0) * (y1 - y0)
+    assert len(listed) < n_rect
 
 
 def test_cull_rules_and_special_cases(orc):
