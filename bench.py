@@ -62,17 +62,56 @@ def job_rate(world, steps, ms):
 # ---------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML
+    polled every ~2 ms from a thread (a timed region of a few tens of ms still
+    gets samples), else nvidia-smi every 100 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
+    def __init__(self, index, pci_bus_id=None):
+        self.index, self.pci = index, pci_bus_id
+        self.proc = self.thread = None
+        self.samples = []
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        if self.pci:
+            try:
+                return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(self.pci)
+            except Exception:
+                pass
+        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
 
     def start(self):
+        import threading
+        try:
+            nv, h = self._nvml_handle()
+            bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
+                    "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
+                    "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
+                    "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
+            self.smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            self.stop_flag = threading.Event()
+
+            def loop():
+                while not self.stop_flag.is_set():
+                    try:
+                        mhz = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                        r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                        self.samples.append((mhz, [k for k, b in bits.items() if r & b]))
+                    except Exception:
+                        pass
+                    time.sleep(0.002)
+
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.thread = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -81,6 +120,13 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread:
+            self.stop_flag.set()
+            self.thread.join()
+            sm = [x[0] for x in self.samples]
+            reasons = sorted({r for x in self.samples for r in x[1]})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.smax, "reasons": reasons,
+                    "samples": len(sm), "source": "nvml, ~2 ms"}
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -90,7 +136,6 @@ class ClockSampler:
             self.proc.kill()
             out, _ = self.proc.communicate()
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 8:
@@ -100,11 +145,11 @@ class ClockSampler:
                 smax.append(float(f[1]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
+            for nm, v in zip(self.NAMES, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 100 ms"}
 
 
 # ---------------------------------------------------------------------------- workload
@@ -124,9 +169,12 @@ def build_workload(n, n_views, seed_views=2, density_of=None, width=1920, height
     return cfg, tgt_scene
 
 
-# FP32 peak of the B300 from unit counts and clock: 148 SMs x 128 FP32 lanes
-# x 2 flops per FMA x 2.032 GHz (maximum SM clock)
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+def fp32_peak_tflops(sms, sm_max_mhz):
+    """FP32 peak derived from unit counts and the clock: SMs (read from the
+    device) x 128 FP32 lanes x 2 flops per FMA x the maximum SM clock."""
+    return sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
 # algorithmic FP32 operations of the rasterizer backward (one front-to-back
 # pass) per (pixel, splat) pair: a contributing pair costs alpha (14), the
 # transmittance and colour accumulation (8), the colour behind it and dL/dalpha
@@ -252,6 +300,16 @@ def run_ours(args):
     K, Wm = args.steps, args.warmup
     tcap = max(Wm + K, 16) + 8
     peak, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sms = props.multi_processor_count
+    try:
+        sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        sm_max = 2032.0
+    fp32_peak = fp32_peak_tflops(n_sms, sm_max)
+    pci = getattr(props, "pci_bus_id", None)
+    pci = f"{getattr(props, 'pci_domain_id', 0):08x}:{pci:02x}:{getattr(props, 'pci_device_id', 0):02x}.0" \
+        if isinstance(pci, int) else None
     gbs = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms else None
 
     def one_step(sc, s, tgt=None):
@@ -322,7 +380,7 @@ def run_ours(args):
             one_step(sc, s)
         ctx.sync_status()
         ctx.timing_read(tcap)            # discard warm-up timings
-        clocks = ClockSampler(local)
+        clocks = ClockSampler(local, pci)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -419,9 +477,10 @@ def run_ours(args):
         dom = max(cands, key=cands.get)
         if dom == "k_raster_bwd":
             ach = flops / (st["raster_bwd"] * 1e-3) / 1e12
-            return {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz",
+            return {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                    "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                    "peak_source": f"derived: {n_sms} SMs (device attribute) x 128 FP32 lanes x 2 flop/FMA x "
+                                   f"{sm_max:g} MHz (maximum SM clock)",
                     "algorithmic_flops_per_launch": round(flops), "traffic": None}
         b = m["b_apply"] if dom == "k_adam_apply" else m["b_cull"]
         t = st["adam_apply"] if dom == "k_adam_apply" else st["cull"]
@@ -431,33 +490,55 @@ def run_ours(args):
 
     def e2e(sc):
         """Steps/s through the public API with the step's targets copied from
-        pinned host memory and the loss read back, every step."""
+        pinned host memory and the loss read back, every step.  The targets are
+        double-buffered: step s + 1's copy runs on a copy stream while step s
+        computes (events order each buffer's copy before its use and its reuse
+        after the step that read it), as a data loader would feed training."""
         host_t = [t.cpu().pin_memory() for t in targets]
-        dev_t = [torch.empty_like(targets[0]) for _ in range(vps)]
+        bufs = [[torch.empty_like(targets[0]) for _ in range(vps)] for _ in range(2)]
         host_loss = torch.zeros(1).pin_memory()
+        cstream = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
+        for e in used:
+            e.record(stream)
 
-        def e2e_step(s):
-            vs = [(s * vps + j) % len(cams) for j in range(vps)]
-            for j, v in enumerate(vs):
-                dev_t[j].copy_(host_t[v], non_blocking=True)
-            one_step(sc, s, tgt=dev_t)
+        def prefetch(s):
+            b = s % 2
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(used[b])              # the step that read this buffer is done
+                for j in range(vps):
+                    bufs[b][j].copy_(host_t[(s * vps + j) % len(cams)], non_blocking=True)
+                copied[b].record(cstream)
+
+        def e2e_step(s, last):
+            b = s % 2
+            stream.wait_event(copied[b])
+            one_step(sc, s, tgt=bufs[b])
+            used[b].record(stream)
             host_loss.copy_(loss, non_blocking=True)
+            if not last:
+                prefetch(s + 1)
 
         ctx.timing_enable(0)
+        prefetch(0)
         for s in range(max(Wm, 3)):
-            e2e_step(s)
+            e2e_step(s, False)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
+        cstream.wait_stream(stream)      # the timed region's first copy starts after f0
+        prefetch(0)
         for s in range(K):
-            e2e_step(s)
+            e2e_step(s, s == K - 1)
         ctx.wait_copies()
         f1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
         ctx.sync_status()
         return {"value": round(job_rate(world, K, ms), 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(targets[0].numel() * 4 * vps), "d2h_bytes_per_step": 4}
+                "h2d_bytes_per_step": int(targets[0].numel() * 4 * vps), "d2h_bytes_per_step": 4,
+                "copies": "targets double-buffered on a copy stream (step s+1's copy overlaps step s)"}
 
     main_prec = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
     if args.budget_gb:

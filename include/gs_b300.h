@@ -352,15 +352,31 @@ GS_API gs_status gs_step_kernel_count(const gs_ctx *ctx, int32_t *kernels);
  * arguments and results as gs_cull on a context with tile size tile_w x
  * tile_h: ids_out (device, room for scene->n ids) receives the visible
  * Gaussians in ascending order and *n_vis_out (device) their count.
+ * status_out (device, may be NULL) receives the status the kernels found on
+ * the device: GS_OK, or GS_ERR_TIMEOUT if a cull block gave up waiting for its
+ * own copies (*n_vis_out is then 0).
  * Its scratch is a fixed ~2.1 MB array of device memory inside the library,
  * held on every GPU that loads the library until the process exits.
  * Returns GS_ERR_CAPACITY, launching nothing, if scene->n exceeds
- * GS_CULL_NOALLOC_MAX_GAUSSIANS.  The first call on each device looks up that
- * array's address (with the device current) and should come before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race;
- * serialise them (one stream, or events). */
+ * GS_CULL_NOALLOC_MAX_GAUSSIANS, and GS_ERR_INVALID_ARG, launching nothing,
+ * for the arguments gs_cull rejects (sh_degree outside 0..3, a non-finite or
+ * non-positive focal length, unusable Adam hyper-parameters, ...).  The first
+ * call on each device looks up that array's address (with the device current)
+ * and should come before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU race; serialise them (one stream, or events). */
 GS_API gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, const gs_adam_cfg *adam, int32_t tile_w,
-                                 int32_t tile_h, int32_t *ids_out, int32_t *n_vis_out, void *stream);
+                                 int32_t tile_h, int32_t *ids_out, int32_t *n_vis_out, int32_t *status_out,
+                                 void *stream);
+
+/* Failure-path testing (no counterpart in the paper).  Every cull block waits
+ * on an mbarrier for the TMA copies it issued itself, each wait bounded; after
+ * `first_wait` polls (default 2^24) of a block's first wait it gives up:
+ * latches GS_ERR_TIMEOUT (gs_sync_status returns it), lets the copies it
+ * issued land (waiting for them with the default bound) and returns, so the
+ * context stays usable.  0 makes every block give up at once.  ctx = NULL
+ * sets the limit of gs_cull_noalloc (process-wide).  Host only; gs_step
+ * captures a new graph after a change. */
+GS_API gs_status gs_set_cull_wait_limit(gs_ctx *ctx, uint32_t first_wait);
 
 /* Inspection of the last gs_render_fwd (tests, debugging).  Device pointers,
  * owned by the context, valid until the next render: *tile_of_key[K] and

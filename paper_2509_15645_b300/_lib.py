@@ -65,7 +65,8 @@ EXPORTS = {
     "gs_autotune": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_i32), C.POINTER(c_f32), c_vp]),
     "gs_set_raster_variant": (c_i32, [c_vp, c_i32]),
     "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
-                                c_vp]),
+                                c_vp, c_vp]),
+    "gs_set_cull_wait_limit": (c_i32, [c_vp, C.c_uint32]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),

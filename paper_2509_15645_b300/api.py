@@ -409,6 +409,11 @@ class Context:
         conv = [None if t < 0 else t for t in ms]
         return (chosen[0], chosen[1]), conv[:V], conv[V:]
 
+    def set_cull_wait_limit(self, first_wait):
+        """Polls of each cull block's first wait on its own copies before it
+        gives up and latches GS_ERR_TIMEOUT (default 2^24; failure-path tests)."""
+        self._check(self.lib.gs_set_cull_wait_limit(self.h, int(first_wait)), "gs_set_cull_wait_limit")
+
     def set_raster_variant(self, v):
         self._check(self.lib.gs_set_raster_variant(self.h, int(v)), "gs_set_raster_variant")
 

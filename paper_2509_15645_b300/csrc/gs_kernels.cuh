@@ -12,6 +12,10 @@ struct ScanLen {
     int mul, div, add, fixed, cap;
 };
 
+// Polls of an mbarrier before a wait on the block's own TMA copies gives up
+// (the block then latches GS_ERR_TIMEOUT, lets its copies land and returns).
+constexpr uint32_t CULL_WAIT_LIMIT = 1u << 24;
+
 struct Work {
     uint32_t *partials;   // >= 1024 scan partials
     int *status;          // device status word
@@ -19,6 +23,7 @@ struct Work {
     int num_sms;
     cudaEvent_t *tev;     // timing points of the current step, or nullptr
     bool capturing;       // the stream is being captured into a graph
+    uint32_t cull_first_wait = CULL_WAIT_LIMIT;   // limit of each cull block's first wait (failure-path tests)
     void mark(int p, cudaStream_t s) const
     {
         if (!tev) return;
@@ -82,6 +87,12 @@ struct SceneView {
 // Timing points recorded inside a step (see gs_timing_enable).
 enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_ADAM0, TP_APPLY0, TP_APPLY1,
        TP_ADAM1, TP_STEP1, TP_RBWD0, TP_RBWD1, TP_COUNT };
+
+// gs_runtime.cu: the Adam hyper-parameters are usable (betas in [0, 1), eps >= 0,
+// max_defer in [1, 15], a known mode).  Host only.
+bool valid_adam(const gs_adam_cfg *a);
+// gs_noalloc.cu: the first-wait limit of gs_cull_noalloc's cull blocks.
+void set_noalloc_first_wait(uint32_t limit);
 
 // k_cull.cu: visibility bitmask + per-chunk counts (restore if lut.restore).
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,

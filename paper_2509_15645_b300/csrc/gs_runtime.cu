@@ -35,6 +35,7 @@ struct GraphCache {
     float *loss = nullptr;
     bool timed = false;
     int variant = -1;
+    uint32_t first_wait = 0;
     cudaGraphNode_t ev_node[TP_COUNT] = {nullptr};
     int kernels = 0;
 };
@@ -397,7 +398,7 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     return GS_OK;
 }
 
-static bool valid_adam(const gs_adam_cfg *a)
+bool gs::valid_adam(const gs_adam_cfg *a)
 {
     if (!a) return false;
     if (!(a->beta1 >= 0.f && a->beta1 < 1.f && a->beta2 >= 0.f && a->beta2 < 1.f && a->eps >= 0.f)) return false;
@@ -921,6 +922,16 @@ gs_status gs_adam_tables(const gs_adam_cfg *adam, int32_t step, float *param, fl
     return GS_OK;
 }
 
+gs_status gs_set_cull_wait_limit(gs_ctx *c, uint32_t first_wait)
+{
+    if (!c) {                            // the limit of gs_cull_noalloc (process-wide)
+        set_noalloc_first_wait(first_wait);
+        return GS_OK;
+    }
+    c->w.cull_first_wait = first_wait;   // gs_step re-captures its graph when this changes
+    return GS_OK;
+}
+
 gs_status gs_step_kernel_count(const gs_ctx *c, int32_t *kernels)
 {
     if (!c || !kernels) return GS_ERR_INVALID_ARG;
@@ -1213,9 +1224,9 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
 }
 
 static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
-                          float *loss, bool timed, int variant)
+                          float *loss, bool timed, int variant, uint32_t first_wait)
 {
-    if (!g.exec || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
+    if (!g.exec || g.first_wait != first_wait || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
         g.rdir != sc->rdir || g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree ||
         g.prec != sc->precision || g.n_views != n_views || g.mode != mode ||
         g.loss != loss || g.timed != timed || g.variant != variant)
@@ -1252,7 +1263,8 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         if (!st) scene->step += 1;
         return st;
     }
-    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rbs[0].variant * 16 + c->rbs[0].variant_bwd)) {
+    if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rbs[0].variant * 16 + c->rbs[0].variant_bwd,
+                       c->w.cull_first_wait)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1325,6 +1337,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         g.loss = loss_out;
         g.timed = timed;
         g.variant = c->rbs[0].variant * 16 + c->rbs[0].variant_bwd;
+        g.first_wait = c->w.cull_first_wait;
         for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
     }
     if (timed) {

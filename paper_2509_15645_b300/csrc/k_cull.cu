@@ -99,7 +99,10 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
 // CSTAGES buffers, so HBM streams independently of how many warps are
 // resident.  Thread 0 issues the bulk copies CSTAGES - 1 tiles ahead; every
 // thread waits on the tile's barrier (bounded: on a timeout the block latches
-// GS_ERR_TIMEOUT and stops after draining what it issued).
+// GS_ERR_TIMEOUT and stops after draining what it issued).  The first wait of
+// each block has its own limit `first_wait` (CULL_WAIT_LIMIT unless a test
+// lowers it to make the timeout path run; the drain always uses the full
+// limit, so the copies in flight land before the block exits).
 // The stages hold the planes every Gaussian needs (mean and log-scale, 0-5)
 // with their restore directions; the rotation planes (6-9) are read directly
 // for the Gaussians that pass the pre-test.  A tile is TT = 512 Gaussians; each
@@ -115,7 +118,7 @@ struct CullStage {
     uint8_t cnt[TT];      // counters of a full tile (the last, partial tile reads them directly)
 };
 constexpr size_t CULL_SMEM = sizeof(CullStage) * CSTAGES;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t WAIT_LIMIT = CULL_WAIT_LIMIT;
 
 // Views [view0, view0 + nv) of the argument block in one sweep: the planes
 // are read and restored once and projected into every view.
@@ -135,7 +138,7 @@ struct CullOut {
 __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
                                                    const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
                                                    const DevArgs *__restrict__ args, int view0, int nv,
-                                                   const CullOut out, int *status)
+                                                   const CullOut out, int *status, uint32_t first_wait)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     CullStage *st = reinterpret_cast<CullStage *>(smem);
@@ -203,7 +206,8 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
         const int64_t t = tile_of(q);
         if (t >= 0) {
             const int s = (int)(q % CSTAGES);
-            if (!mbar_wait_bounded(&bar[s], (uint32_t)((q / CSTAGES) & 1), WAIT_LIMIT)) s_abort = 1;
+            if (!mbar_wait_bounded(&bar[s], (uint32_t)((q / CSTAGES) & 1), q == 0 ? first_wait : WAIT_LIMIT))
+                s_abort = 1;
             const bool full_tile = t * TT + TT <= n;
             // planes 0-5 (mean, log-scale) of both Gaussians from the stage: the
             // pre-test needs only those; the rotation planes are read for its survivors
@@ -334,7 +338,8 @@ static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0,
     if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics
     if (out.n_cand) cudaMemsetAsync(out.n_cand, 0, sizeof(int), s);
     const int gt = w.grid(nchunks * CT, CT, 4);
-    k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status);
+    k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status,
+                                         w.cull_first_wait);
 }
 
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,

@@ -156,3 +156,34 @@ def test_region_cameras_marshal_the_full_image():
         assert area == 120 * 80
         assert (regs[1].x0, regs[1].y0) == ((split, 0) if axis == 0 else (0, split))
     assert np.all(np.asarray(regs[0].R) == np.asarray(cam.R))
+
+
+def test_noalloc_cull_rejects_before_any_launch(lib):
+    """gs_cull_noalloc refuses what gs_cull refuses, on the host, before any
+    CUDA call (so this runs without a GPU): an oversize scene, an SH degree
+    outside 0..3, a non-finite focal length, unusable Adam hyper-parameters."""
+
+    def scene(n=1000, deg=1):
+        sc = _lib.Scene()
+        sc.n, sc.pitch, sc.sh_degree = n, (n + 3) // 4 * 4, deg
+        sc.geo = 256                                 # never dereferenced: rejected on the host first
+        return sc
+
+    def cam(fx=50.0):
+        c = _lib.Camera()
+        c.width, c.height, c.fx, c.fy, c.near_z, c.far_z = 64, 64, fx, 50.0, 0.01, 100.0
+        return c
+
+    from paper_2509_15645_b300 import _lib
+    z = C.c_void_p(256)
+    call = lambda sc, cm, ad=None: lib.gs_cull_noalloc(C.byref(sc), C.byref(cm), C.byref(ad) if ad else None, 16, 16,
+                                                       z, z, None, None)
+    assert call(scene(n=(1 << 24) + 1), cam()) == _lib.GS_ERR_CAPACITY
+    assert call(scene(deg=4), cam()) == _lib.GS_ERR_INVALID_ARG
+    assert call(scene(deg=-1), cam()) == _lib.GS_ERR_INVALID_ARG
+    assert call(scene(), cam(fx=float("inf"))) == _lib.GS_ERR_INVALID_ARG
+    assert call(scene(), cam(fx=float("nan"))) == _lib.GS_ERR_INVALID_ARG
+    from paper_2509_15645_b300 import api
+    for bad in (dict(beta2=1.0), dict(beta1=-0.1), dict(eps=-1.0), dict(max_defer=16), dict(max_defer=0),
+                dict(mode=7)):
+        assert call(scene(), cam(), api.adam_struct(**bad)) == _lib.GS_ERR_INVALID_ARG, bad

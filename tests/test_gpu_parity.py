@@ -743,3 +743,34 @@ def test_capacity_overflow_is_reported(gs):
         ctx2.sync_status()
     assert e.value.status == _lib.GS_ERR_CAPACITY
     ctx2.sync_status()   # cleared
+
+
+def test_cull_timeout_is_reported_and_the_context_recovers(gs):
+    """The cull blocks' bounded waits on their own TMA copies: with the first
+    wait's limit at 0 every block gives up at once, lets its copies land and
+    returns; GS_ERR_TIMEOUT is latched (gs_cull and a whole gs_step) with no
+    fault, and with the default limit back the same context culls as before."""
+    from paper_2509_15645_b300 import _lib
+    c = scenes.cfg_small_step()
+    P, cam = c["scene"], cam_f32(c["cams"][0])
+    n = P.shape[1]
+    ctx = make_ctx(gs, n, 64, 64, deg=0)
+    scene = gs.GaussianScene(P, 0)
+    ids_ref, nv_ref = ctx.cull(scene, cam)
+    ctx.sync_status()
+    ref = ids_ref[:int(nv_ref.item())].clone()
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    tgt = torch.zeros(3, 64, 64, device="cuda")
+    ctx.set_cull_wait_limit(0)
+    ctx.cull(scene, cam)
+    with pytest.raises(_lib.GsError) as e:
+        ctx.sync_status()
+    assert e.value.status == _lib.GS_ERR_TIMEOUT
+    ctx.step(scene, [cam], [tgt], adam)
+    with pytest.raises(_lib.GsError) as e:
+        ctx.sync_status()
+    assert e.value.status == _lib.GS_ERR_TIMEOUT
+    ctx.set_cull_wait_limit(1 << 24)
+    ids, nv = ctx.cull(scene, cam)
+    ctx.sync_status()
+    assert torch.equal(ids[:int(nv.item())], ref)

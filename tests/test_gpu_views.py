@@ -1,0 +1,197 @@
+"""GPU parity of the deferred restore over changing views (§4.3.3 parameter
+forwarding with the Eq. 3 catch-up, §4.2.1 selective offloading).
+
+A training run cycles through views of one heightfield that overlap only in
+part, so each view sees Gaussians deferred for 0 to several steps, and (with
+a small counter bound) Gaussians that no view sees are caught up through the
+counter bound.  At every step the oracle is fed the GPU's stored state (one-
+step parity, since atomics make FP32 gradients run-dependent):
+
+* resident scenes: the GPU's cull, render and backward with the restore (the
+  gather restores each visible Gaussian on the fly) against the oracle's
+  render of the materialised parameters -- cull set, image, gradients -- then
+  the whole gs_step against the oracle's deferred Adam step;
+* host-tier scenes (SH rows streamed through the staging ring): the loss of
+  gs_step against the oracle's, and the stored state after the step.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import GROUPS, TIE_TOL, cam_f32, f32, hp32, pixel_exclusions, rel_group_error, sign_undetermined
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+N, DEG, TILE = 12_000, 3, (8, 8)
+LR = [1e-3, 2e-3, 2e-3, 1e-2, 5e-3, 1e-3]
+# the view of each step: overlapping views in an irregular order, so delays of 1 to 5 steps occur
+ORDER = [0, 1, 2, 3, 0, 2, 1, 3, 3, 0, 1, 2]
+
+
+@pytest.fixture(scope="module")
+def gs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2509_15645_b300 as gs
+    return gs
+
+
+def _views():
+    return [cam_f32(scenes.camera_aerial((9 * np.cos(a), 9 * np.sin(a), 35.0), a, -np.pi / 2 + 0.35, 96, 72, 55.0))
+            for a in np.linspace(0, 2 * np.pi, 5)[:4]]
+
+
+def _scene(seed):
+    return scenes.heightfield_scene(N, seed=seed, half_extent=50.0, amplitude=5.0, wavelength=(20.0, 25.0),
+                                    n_clusters=2, cluster_size=2000, sh_degree=DEG)
+
+
+def _targets(orc, cams):
+    T = f32(_scene(42))
+    return [orc.render(T, DEG, c, TILE)["image"] for c in cams]
+
+
+def _state(scene, n):
+    """The stored (w, m, v, counter) as float64 / uint8 arrays [D][n]."""
+    m, v = scene.moments()
+    return (scene.params().cpu().numpy().astype(np.float64), m.cpu().numpy().astype(np.float64),
+            v.cpu().numpy().astype(np.float64), scene.counter[:n].cpu().numpy().copy())
+
+
+def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr):
+    """The GPU's state after step t against the oracle's deferred step from the
+    stored state (W, M, V, Cn) with the GPU's visible set and the oracle's
+    gradients.  fp32: FP32 rounding of each update term; bf16 stores: one bf16
+    ulp (stochastic rounding picks either neighbour) plus the step's share."""
+    W0 = W.copy()
+    orc.adam_deferred(W, M, V, Cn, gids, grad[:, gids], t, hp)
+    gw, gm, gv, gc = _state(scene, n)
+    np.testing.assert_array_equal(gc, Cn)
+    D = W.shape[0]
+    g_full = np.zeros((D, n))
+    g_full[:, gids] = grad[:, gids]
+    und = sign_undetermined(g_full)
+    lr_row = np.array([lr[0]] * 3 + [lr[1]] * 3 + [lr[2]] * 4 + [lr[3]] + [lr[4]] * 3 + [lr[5]] * (D - 14))[:, None]
+    if not prec_bf16:
+        for k, s in GROUPS.items():
+            assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
+        err = np.abs(gw - W)
+        bound = 2e-3 * lr_row + 1e-6 + 4e-7 * np.abs(W) + np.where(und, 2 * lr_row, 0.0)
+        assert np.all(err <= bound), (t, np.max(err / bound), np.unravel_index(np.argmax(err / bound), err.shape))
+    else:
+        ub = 2.0 ** -7
+        for k, s in GROUPS.items():
+            sm, sv = np.abs(M[s]).max() + 1e-30, np.abs(V[s]).max() + 1e-30
+            assert np.all(np.abs(gm[s] - M[s]) <= ub * np.abs(M[s]) + 2e-4 * sm), (t, k, "m")
+            assert np.all(np.abs(gv[s] - V[s]) <= ub * np.abs(V[s]) + 4e-4 * sv), (t, k, "v")
+        err = np.abs(gw - W)
+        geo = np.arange(D)[:, None] < 11
+        bound = np.where(geo, 2e-3 * lr_row + 1e-6 + 4e-7 * np.abs(W),
+                         ub * np.abs(W) + 2 * ub * lr_row * (t + 1) + 1e-7) + np.where(und, 2 * lr_row, 0.0)
+        assert np.all(err <= bound), (t, np.max(err / bound))
+    return np.mean(np.abs(W - W0) > 0)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_restore_over_changing_views(gs, orc, bf16):
+    """Resident scene, fp32 or the bf16 form (counter bound 15)."""
+    cams = _views()
+    targets = _targets(orc, cams)
+    P = _scene(41)
+    prec = gs.GS_BF16_SH_MOM if bf16 else gs.GS_FP32
+    scene = gs.GaussianScene(P, DEG, precision=prec)
+    ctx = gs.Context(max_gaussians=N, max_visible=N, max_keys=64 * N, max_width=96, max_height=72, tile=TILE,
+                     max_sh_degree=DEG)
+    adam = gs.adam_struct(lr=LR, eps=1e-15, seed=9)
+    hp = hp32(orc, lr=LR, eps=1e-15)
+    tg = [torch.as_tensor(x, dtype=torch.float32, device="cuda") for x in targets]
+    delays = []
+    for t, k in enumerate(ORDER, start=1):
+        cam = cams[k]
+        W, M, V, Cn = _state(scene, N)
+        if bf16:
+            # the gather restores SH rows through the stored bf16 directions:
+            # the expected parameters are w - table[d] * (stored direction), so
+            # the image isolates the restore from the rounding of the directions
+            rd = torch.cat([scene.rdir_geo[:, :N], scene.rdir_sh[:, :N].float()]).cpu().numpy().astype(np.float64)
+            Wcur = W.copy()
+            for g, rows in enumerate([range(0, 3), range(3, 6), range(6, 10), range(10, 11), range(11, 14),
+                                      range(14, W.shape[0])]):
+                pl, _, _ = orc.adam_lut(t, hp.lr[g], hp)
+                for r in rows:
+                    Wcur[r] = W[r] - np.float32(pl[Cn]).astype(np.float64) * rd[r]
+        else:
+            Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)
+        rr = orc.render_loss_backward(Wcur, DEG, cam, targets[k], TILE)
+        # cull + render + backward with the restore of the coming step
+        ids, nv = ctx.cull(scene, cam, adam)
+        img = ctx.render_fwd(scene, cam, ids, nv, adam)
+        gc = ctx.render_bwd(torch.as_tensor(rr["dimage"], dtype=torch.float32, device="cuda"), scene.D)
+        full = ctx.grad_scatter(scene, ids, nv, gc)
+        ctx.sync_status()
+        gids = ids[:int(nv.item())].cpu().numpy()
+        sp = rr["splats"]
+        diff = np.setxor1d(gids, np.nonzero(sp["keep"])[0])
+        assert np.all(sp["margin"][diff] < TIE_TOL), (t, diff[sp["margin"][diff] >= TIE_TOL][:8])
+        ex = pixel_exclusions(rr, gids)
+        assert ex.mean() < 0.03
+        ok = ~ex[None].repeat(3, 0)
+        ierr = np.abs(img.cpu().numpy().astype(np.float64) - rr["image"])
+        assert ierr[ok].max() <= 1e-5, (t, ierr[ok].max())
+        g_gpu = full[:, :N].cpu().numpy().astype(np.float64)
+        errs = {g: rel_group_error(g_gpu, rr["grad"], s) for g, s in GROUPS.items()}
+        assert max(errs.values()) <= 1e-4, (t, errs)
+        d = Cn[gids]
+        delays.append(d)
+        if t > 1:
+            assert np.mean(d > 0) > 0.1, (t, np.mean(d > 0))
+        # the whole step (graph) from the same state
+        loss = ctx.step(scene, [cam], [tg[k]], adam)
+        ctx.sync_status()
+        assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
+        moved = _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids.astype(np.int32), rr["grad"], hp, LR)
+        assert moved > 0.02
+    d = np.concatenate(delays)
+    hist = np.bincount(d, minlength=16)
+    assert np.count_nonzero(hist[1:]) >= 3, hist          # several different delays were restored
+    print(f"delays of the visible Gaussians over {len(ORDER)} steps: {hist[:8].tolist()}")
+
+
+@pytest.mark.parametrize("prec_name", ["GS_FP32", "GS_BF16_SH_MOM"])
+def test_host_tier_over_changing_views(gs, orc, prec_name):
+    """Host-tier scene (SH rows streamed through a ring smaller than the
+    scene) with a counter bound of 5, so never-visible Gaussians are stepped
+    through the bound: loss and stored state after each gs_step against the
+    oracle from the same stored state."""
+    cams = _views()
+    targets = _targets(orc, cams)
+    P = _scene(41)
+    prec = getattr(gs, prec_name)
+    bf16 = prec != gs.GS_FP32
+    scene = gs.GaussianScene(P, DEG, precision=prec, tier=gs.GS_TIER_HOST_SH)
+    ctx = gs.Context(max_gaussians=N, max_visible=N, max_keys=64 * N, max_width=96, max_height=72, tile=TILE,
+                     max_sh_degree=DEG, stage_chunks=10, chunk_shift=10, stage_elem_bytes=2 if bf16 else 4)
+    adam = gs.adam_struct(lr=LR, eps=1e-15, seed=9, max_defer=5)
+    hp = hp32(orc, lr=LR, eps=1e-15, max_defer=5)
+    tg = [torch.as_tensor(x, dtype=torch.float32, device="cuda") for x in targets]
+    saw_bound = False
+    for t, k in enumerate(ORDER, start=1):
+        W, M, V, Cn = _state(scene, N)
+        Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)
+        rr = orc.render_loss_backward(Wcur, DEG, cams[k], targets[k], TILE)
+        ids, nv = ctx.cull(scene, cams[k], adam)
+        ctx.sync_status()
+        gids = ids[:int(nv.item())].cpu().numpy().astype(np.int32)
+        sp = rr["splats"]
+        diff = np.setxor1d(gids, np.nonzero(sp["keep"])[0])
+        assert np.all(sp["margin"][diff] < TIE_TOL), t
+        if t > 1:
+            assert np.mean(Cn[gids] > 0) > 0.1
+        saw_bound |= bool(np.any(Cn == 5))
+        loss = ctx.step(scene, [cams[k]], [tg[k]], adam)
+        ctx.sync_status()          # waits for the write-backs too
+        assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
+        _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids, rr["grad"], hp, LR)
+        staged, _ = ctx.host_tier_stats()
+        assert 0 < staged <= (N + 1023) // 1024
+    assert saw_bound
