@@ -149,7 +149,19 @@ typedef struct {
     void *host_rdir;       /*   unused (SH restore directions are recomputed from m, v on the device); may be NULL */
 } gs_scene;
 
-/* Adam hyper-parameters (§4.3.2).  lr per parameter group:
+/* Optimizers of the deferred update (§4.3: Adam is the method's; the paper
+ * names SGD with momentum and AdamW as optimizers the deferral carries over
+ * to).  GS_OPT_ADAM: Eq. 1.  GS_OPT_ADAMW: decoupled weight decay (each step
+ * w <- (1 - lr weight_decay) w, then the Adam step); its catch-up over d
+ * deferred steps is w <- (1 - lr weight_decay)^d w - wlut[d] m / (sqrt(v) +
+ * eps), Fig. 10's table with its i-th term weighted by (1 - lr
+ * weight_decay)^(i-1).  GS_OPT_SGDM: SGD with momentum mu = beta1 (b <- mu b
+ * + g, w <- w - lr b; no dampening; beta2 and eps unused; b lives in the m
+ * planes, v is neither read nor written); its catch-up is exact: w <- w - lr
+ * (mu + ... + mu^d) b, b <- mu^d b. */
+enum { GS_OPT_ADAM = 0, GS_OPT_ADAMW = 1, GS_OPT_SGDM = 2 };
+
+/* Optimizer hyper-parameters (§4.3.2).  lr per parameter group:
  * 0 mean, 1 log-scale, 2 quaternion, 3 opacity, 4 SH DC, 5 SH rest. */
 typedef struct {
     float lr[6];
@@ -157,6 +169,8 @@ typedef struct {
     int32_t max_defer;     /* MAX of the counter, at most 15 (4-bit counter) */
     int32_t mode;          /* GS_ADAM_DEFERRED or GS_ADAM_EAGER */
     int32_t seed;          /* stochastic-rounding seed of the BF16 form */
+    int32_t optimizer;     /* GS_OPT_ADAM (0), GS_OPT_ADAMW or GS_OPT_SGDM */
+    float weight_decay;    /* GS_OPT_ADAMW: decoupled decay lambda >= 0 with lr[g] * lambda < 1; else unused */
 } gs_adam_cfg;
 
 /* Context capacities, fixed at creation. */
@@ -266,16 +280,20 @@ GS_API gs_status gs_adam_materialize(gs_ctx *ctx, const gs_scene *scene, const g
  * scene with scene->step == step - 1 takes next) hands to the kernels, fp32,
  * computed in double from the hyper-parameters (Fig. 10, §4.3.2):
  *   param     [6][16] row-major: per parameter group g and delay d, the
- *             coefficient of the restore w -= param[g][d] m / (sqrt(v) + eps),
- *             i.e. the sum over the d skipped steps of Eq. 3's weights;
- *             0 for d = 0, d > max_defer and d >= step;
+ *             coefficient of the restore w <- decay[g][d] w - param[g][d] dir
+ *             with dir = m / (sqrt(v) + eps) (Adam, AdamW) or the momentum
+ *             buffer b (SGDM), i.e. the sum over the d skipped steps of Eq.
+ *             3's weights; 0 for d = 0, d > max_defer and d >= step;
  *   mom, var  [16]: beta1^(d+1), beta2^(d+1), the decay of m and v over the
- *             d skipped steps and the current one;
- *   step_size [6]: lr[g] / (1 - beta1^step);  bias_corr: sqrt(1 - beta2^step).
+ *             d skipped steps and the current one (SGDM: mu^(d+1), and 1);
+ *   step_size [6]: lr[g] / (1 - beta1^step) (SGDM: lr[g]);
+ *   bias_corr: sqrt(1 - beta2^step) (SGDM: 1);
+ *   decay     [6][16]: (1 - lr[g] weight_decay)^d for AdamW, else 1.
  * Host arrays owned by the caller; any may be NULL.  Touches no device.
- * GS_ERR_INVALID_ARG for a NULL adam, step < 1 or max_defer outside [1, 15]. */
+ * GS_ERR_INVALID_ARG for a NULL adam, step < 1 or hyper-parameters the
+ * optimizer cannot use (max_defer outside [1, 15], ...). */
 GS_API gs_status gs_adam_tables(const gs_adam_cfg *adam, int32_t step, float *param, float *mom, float *var,
-                                float *step_size, float *bias_corr);
+                                float *step_size, float *bias_corr, float *decay);
 
 /* Scatter compact gradients to a full [D][pitch] array (zero elsewhere). */
 GS_API gs_status gs_grad_scatter(gs_ctx *ctx, const gs_scene *scene, const int32_t *ids, const int32_t *n_vis,

@@ -6,7 +6,8 @@ include/gs_b300.h); this package only marshals arguments.  Importing it loads
 the library and fails if it has not been built.
 """
 from . import _lib
-from ._lib import GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN, GS_FP32, GS_TIER_DEVICE, GS_TIER_HOST_SH  # noqa: F401
+from ._lib import (GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN, GS_FP32, GS_OPT_ADAM, GS_OPT_ADAMW, GS_OPT_SGDM,  # noqa: F401
+                   GS_TIER_DEVICE, GS_TIER_HOST_SH)
 from .api import (Context, GaussianScene, RegionCamera, adam_struct, adam_tables, camera_struct, n_params,  # noqa: F401
                   render, split_regions)
 

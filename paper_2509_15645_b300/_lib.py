@@ -16,6 +16,7 @@ GS_FP32, GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN = 0, 1, 2
 RASTER_VARIANTS = 8
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
+GS_OPT_ADAM, GS_OPT_ADAMW, GS_OPT_SGDM = 0, 1, 2
 GS_TIER_DEVICE, GS_TIER_HOST_SH = 0, 1
 
 
@@ -33,7 +34,7 @@ class Scene(C.Structure):
 
 class AdamCfg(C.Structure):
     _fields_ = [("lr", c_f32 * 6), ("beta1", c_f32), ("beta2", c_f32), ("eps", c_f32), ("max_defer", c_i32),
-                ("mode", c_i32), ("seed", c_i32)]
+                ("mode", c_i32), ("seed", c_i32), ("optimizer", c_i32), ("weight_decay", c_f32)]
 
 
 class Config(C.Structure):
@@ -73,7 +74,7 @@ EXPORTS = {
     "gs_split_point": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32,
                                C.POINTER(c_i32), C.POINTER(c_i64), c_vp]),
     "gs_adam_tables": (c_i32, [C.POINTER(AdamCfg), c_i32, C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32),
-                               C.POINTER(c_f32), C.POINTER(c_f32)]),
+                               C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
 }

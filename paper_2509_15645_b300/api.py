@@ -82,25 +82,29 @@ def split_regions(cam, axis: int, split: int):
 
 
 def adam_struct(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, max_defer=15, mode=L.GS_ADAM_DEFERRED,
-                seed=0) -> L.AdamCfg:
+                seed=0, optimizer=L.GS_OPT_ADAM, weight_decay=0.0) -> L.AdamCfg:
+    """Optimizer hyper-parameters.  optimizer GS_OPT_ADAM, GS_OPT_ADAMW
+    (decoupled ``weight_decay``) or GS_OPT_SGDM (momentum ``beta1``)."""
     a = L.AdamCfg()
     lrs = [lr] * 6 if isinstance(lr, (int, float)) else list(lr)
     for k in range(6):
         a.lr[k] = float(lrs[k])
     a.beta1, a.beta2, a.eps, a.max_defer, a.mode, a.seed = beta1, beta2, eps, max_defer, mode, seed
+    a.optimizer, a.weight_decay = int(optimizer), float(weight_decay)
     return a
 
 
 def adam_tables(adam: L.AdamCfg, step: int) -> dict:
     """The deferred update's tables for optimizer step ``step`` as the kernels
     receive them (Fig. 10): ``param`` [6][16], ``mom`` [16], ``var`` [16],
-    ``step_size`` [6], ``bias_corr``.  Host only."""
+    ``step_size`` [6], ``bias_corr``, ``decay`` [6][16].  Host only."""
     param, mom, var, ss, bc = (C.c_float * 96)(), (C.c_float * 16)(), (C.c_float * 16)(), (C.c_float * 6)(), C.c_float()
-    st = L.load().gs_adam_tables(C.byref(adam), int(step), param, mom, var, ss, C.byref(bc))
+    dec = (C.c_float * 96)()
+    st = L.load().gs_adam_tables(C.byref(adam), int(step), param, mom, var, ss, C.byref(bc), dec)
     if st != L.GS_OK:
         raise L.GsError(st, "gs_adam_tables")
     return {"param": [list(param[g * 16:(g + 1) * 16]) for g in range(6)], "mom": list(mom), "var": list(var),
-            "step_size": list(ss), "bias_corr": bc.value}
+            "step_size": list(ss), "bias_corr": bc.value, "decay": [list(dec[g * 16:(g + 1) * 16]) for g in range(6)]}
 
 
 class GaussianScene:

@@ -45,6 +45,9 @@ struct DevLut {
     int max_defer;
     int step;                       // t
     int restore;                    // 0: render/cull without restore
+    int sgd;                        // momentum SGD: the restore direction is the buffer m itself, no v
+    float decay[N_GROUPS][LUT_N];   // AdamW: (1 - lr wd)^d of the restore; 1 otherwise
+    float wdf[N_GROUPS];            // AdamW: 1 - lr wd of the current step; 1 otherwise
 };
 
 struct DevArgs {
@@ -190,16 +193,24 @@ __device__ __forceinline__ float sqrt_fast(float x)
     return r;
 }
 
-__device__ __forceinline__ float restore_dir(float m, float v, float eps) { return __fdividef(m, sqrt_fast(v) + eps); }
-
-__device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, int d)
+// Adam and AdamW restore along m / (sqrt(v) + eps); momentum SGD along its
+// buffer b (held in the m planes), exactly.
+__device__ __forceinline__ float restore_dir(float m, float v, float eps, bool sgd = false)
 {
-    return d ? __fmaf_rn(-plut, dir, w) : w;
+    return sgd ? m : __fdividef(m, sqrt_fast(v) + eps);
 }
 
-__device__ __forceinline__ float restore_param(float w, float m, float v, float plut, int d, float eps)
+// w <- dec w - plut dir for a delay d > 0.  dec = 1 (Adam, SGD) multiplies
+// exactly, so those restores are a single FMA on w.
+__device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, float dec, int d)
 {
-    return d ? restore_with_dir(w, restore_dir(m, v, eps), plut, d) : w;
+    return d ? __fmaf_rn(-plut, dir, __fmul_rn(dec, w)) : w;
+}
+
+__device__ __forceinline__ float restore_param(float w, float m, float v, float plut, float dec, int d, float eps,
+                                               bool sgd = false)
+{
+    return d ? restore_with_dir(w, restore_dir(m, v, eps, sgd), plut, dec, d) : w;
 }
 
 // ---------------------------------------------------------------------------

@@ -284,36 +284,70 @@ DevCam gs::make_cam(const gs_camera &a, int tile_w, int tile_h)
 
 // Tables of the deferred update (Fig. 10, §4.3.2) for step t, computed in
 // double and rounded to float.  Entries with delay >= t are never used.
+// Adam: Fig. 10.  AdamW: the same recursion with its i-th term weighted by
+// rho^(i-1), rho = 1 - lr wd, and the restore's decay rho^d.  Momentum SGD
+// (mu = beta1): param[d] = lr (mu + ... + mu^d), the buffer decays by mu^(d+1)
+// and takes the gradient with weight 1; no bias correction.
 DevLut gs::make_lut(const gs_adam_cfg *a, int t, bool restore, int precision)
 {
     DevLut L{};
     L.restore = 0;
+    for (int g = 0; g < N_GROUPS; g++) {
+        L.wdf[g] = 1.f;
+        for (int i = 0; i < LUT_N; i++) L.decay[g][i] = 1.f;
+    }
     if (!a) return L;
     L.seed = (uint32_t)a->seed;
     L.stochastic = precision == GS_BF16_SH_MOM ? 1 : 0;
+    const int opt = a->optimizer;
+    L.sgd = opt == GS_OPT_SGDM;
     const double b1 = a->beta1, b2 = a->beta2;
-    const double scale = b1 / std::sqrt(b2);
-    for (int g = 0; g < N_GROUPS; g++) {
-        double prev = 0.0;
-        L.param[g][0] = 0.f;
-        for (int i = 1; i < LUT_N; i++) {
-            if (i <= a->max_defer && i <= t - 1) {
-                prev = scale * prev + (a->lr[g] * b1) / (std::sqrt(b2 / (1.0 - std::pow(b2, t - i))) * (1.0 - std::pow(b1, t - i)));
-                L.param[g][i] = (float)prev;
-            } else {
-                L.param[g][i] = 0.f;
+    if (opt == GS_OPT_SGDM) {
+        const double mu = b1;
+        for (int g = 0; g < N_GROUPS; g++) {
+            double acc = 0.0;
+            L.param[g][0] = 0.f;
+            for (int i = 1; i < LUT_N; i++) {
+                acc = mu * acc + a->lr[g] * mu;
+                L.param[g][i] = (i <= a->max_defer && i <= t - 1) ? (float)acc : 0.f;
             }
+            L.step_size[g] = a->lr[g];
         }
-        L.step_size[g] = (float)(a->lr[g] / (1.0 - std::pow(b1, t)));
+        for (int i = 0; i < LUT_N; i++) {
+            L.mom[i] = (float)std::pow(mu, i + 1);
+            L.var[i] = 1.f;
+        }
+        L.bias_corr = L.inv_bias_corr = 1.f;
+        L.omb1 = 1.f;
+        L.omb2 = 0.f;
+    } else {
+        const double scale = b1 / std::sqrt(b2);
+        for (int g = 0; g < N_GROUPS; g++) {
+            const double rho = opt == GS_OPT_ADAMW ? 1.0 - (double)a->lr[g] * a->weight_decay : 1.0;
+            double prev = 0.0;
+            L.param[g][0] = 0.f;
+            for (int i = 1; i < LUT_N; i++) {
+                if (i <= a->max_defer && i <= t - 1) {
+                    prev = scale * prev + std::pow(rho, i - 1) * (a->lr[g] * b1) /
+                                              (std::sqrt(b2 / (1.0 - std::pow(b2, t - i))) * (1.0 - std::pow(b1, t - i)));
+                    L.param[g][i] = (float)prev;
+                } else {
+                    L.param[g][i] = 0.f;
+                }
+                L.decay[g][i] = (float)std::pow(rho, i);
+            }
+            L.wdf[g] = (float)rho;
+            L.step_size[g] = (float)(a->lr[g] / (1.0 - std::pow(b1, t)));
+        }
+        for (int i = 0; i < LUT_N; i++) {
+            L.mom[i] = (float)std::pow(b1, i + 1);
+            L.var[i] = (float)std::pow(b2, i + 1);
+        }
+        L.bias_corr = (float)std::sqrt(1.0 - std::pow(b2, t));
+        L.inv_bias_corr = (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t)));
+        L.omb1 = (float)(1.0 - b1);
+        L.omb2 = (float)(1.0 - b2);
     }
-    for (int i = 0; i < LUT_N; i++) {
-        L.mom[i] = (float)std::pow(b1, i + 1);
-        L.var[i] = (float)std::pow(b2, i + 1);
-    }
-    L.bias_corr = (float)std::sqrt(1.0 - std::pow(b2, t));
-    L.inv_bias_corr = (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t)));
-    L.omb1 = (float)(1.0 - b1);
-    L.omb2 = (float)(1.0 - b2);
     L.eps = a->eps;
     L.b1 = a->beta1;
     L.b2 = a->beta2;
@@ -403,6 +437,14 @@ bool gs::valid_adam(const gs_adam_cfg *a)
     if (!a) return false;
     if (!(a->beta1 >= 0.f && a->beta1 < 1.f && a->beta2 >= 0.f && a->beta2 < 1.f && a->eps >= 0.f)) return false;
     if (a->max_defer < 1 || a->max_defer > LUT_N - 1) return false;
+    if (a->optimizer != GS_OPT_ADAM && a->optimizer != GS_OPT_ADAMW && a->optimizer != GS_OPT_SGDM) return false;
+    for (int g = 0; g < N_GROUPS; g++)
+        if (!std::isfinite(a->lr[g])) return false;
+    if (a->optimizer == GS_OPT_ADAMW) {
+        if (!(a->weight_decay >= 0.f) || !std::isfinite(a->weight_decay)) return false;
+        for (int g = 0; g < N_GROUPS; g++)
+            if (!((double)a->lr[g] * a->weight_decay < 1.0)) return false;
+    }
     return a->mode == GS_ADAM_DEFERRED || a->mode == GS_ADAM_EAGER;
 }
 
@@ -905,13 +947,15 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
 }
 
 gs_status gs_adam_tables(const gs_adam_cfg *adam, int32_t step, float *param, float *mom, float *var,
-                         float *step_size, float *bias_corr)
+                         float *step_size, float *bias_corr, float *decay)
 {
-    if (!adam || step < 1 || adam->max_defer < 1 || adam->max_defer > LUT_N - 1) return GS_ERR_INVALID_ARG;
+    if (!adam || step < 1 || !valid_adam(adam)) return GS_ERR_INVALID_ARG;
     const DevLut L = make_lut(adam, step, true);
     for (int g = 0; g < N_GROUPS; g++) {
-        for (int i = 0; i < LUT_N; i++)
+        for (int i = 0; i < LUT_N; i++) {
             if (param) param[g * LUT_N + i] = L.param[g][i];
+            if (decay) decay[g * LUT_N + i] = L.decay[g][i];
+        }
         if (step_size) step_size[g] = L.step_size[g];
     }
     for (int i = 0; i < LUT_N; i++) {

@@ -93,19 +93,26 @@ void launch_touch_chunks(const uint32_t *vmask, const uint8_t *counter, int64_t 
 // Shared copy of the step's tables.
 struct SLut {
     float param[N_GROUPS][LUT_N];
+    float decay[N_GROUPS][LUT_N];
     float mom[LUT_N], var[LUT_N];
-    float step_size[N_GROUPS];
+    float step_size[N_GROUPS], wdf[N_GROUPS];
     float bias_corr, inv_bias_corr, omb1, omb2, eps;
     uint32_t seed, step;
-    int stochastic;
+    int stochastic, sgd;
 };
 
 __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
 {
     int t = threadIdx.x;
-    if (t < N_GROUPS * LUT_N) s.param[t / LUT_N][t % LUT_N] = L.param[t / LUT_N][t % LUT_N];
+    if (t < N_GROUPS * LUT_N) {
+        s.param[t / LUT_N][t % LUT_N] = L.param[t / LUT_N][t % LUT_N];
+        s.decay[t / LUT_N][t % LUT_N] = L.decay[t / LUT_N][t % LUT_N];
+    }
     if (t < LUT_N) { s.mom[t] = L.mom[t]; s.var[t] = L.var[t]; }
-    if (t < N_GROUPS) s.step_size[t] = L.step_size[t];
+    if (t < N_GROUPS) {
+        s.step_size[t] = L.step_size[t];
+        s.wdf[t] = L.wdf[t];
+    }
     if (t == 0) {
         s.bias_corr = L.bias_corr;
         s.inv_bias_corr = L.inv_bias_corr;
@@ -115,18 +122,29 @@ __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
         s.seed = L.seed;
         s.step = (uint32_t)L.step;
         s.stochastic = L.stochastic;
+        s.sgd = L.sgd;
     }
     __syncthreads();
 }
 
-// Restore (delay d) + Eq. 1 for one value.  d = 0 is the plain Adam step.
+// Restore (delay d) + one optimizer step for one value; d = 0 is the plain
+// step.  Adam / AdamW: Eq. 1 (AdamW with the decoupled decay of the step,
+// wdf = 1 - lr wd; wdf = 1 and decay = 1 multiply exactly, so Adam's
+// arithmetic is the same as without them).  Momentum SGD: the buffer lives in
+// m (mom = mu^(d+1), omb1 = 1), v is left alone.
 __device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
 {
-    float m_new = L.mom[d] * m + L.omb1 * g;
-    float v_new = L.var[d] * v + L.omb2 * g * g;
-    float wr = restore_param(w, m, v, L.param[grp][d], d, L.eps);
-    float denom = sqrt_fast(v_new) * L.inv_bias_corr + L.eps;
-    w = wr - L.step_size[grp] * __fdividef(m_new, denom);
+    const float m_new = L.mom[d] * m + L.omb1 * g;
+    if (L.sgd) {
+        const float wr = restore_param(w, m, v, L.param[grp][d], 1.f, d, L.eps, true);
+        w = wr - L.step_size[grp] * m_new;
+        m = m_new;
+        return;
+    }
+    const float v_new = L.var[d] * v + L.omb2 * g * g;
+    const float wr = restore_param(w, m, v, L.param[grp][d], L.decay[grp][d], d, L.eps);
+    const float denom = sqrt_fast(v_new) * L.inv_bias_corr + L.eps;
+    w = __fmul_rn(L.wdf[grp], wr) - L.step_size[grp] * __fdividef(m_new, denom);
     m = m_new;
     v = v_new;
 }
@@ -171,26 +189,28 @@ template <typename T, typename IX = int64_t> struct Planes {
     {
         return ld_val(r < N_GEO ? v + go(r, i) : shv + so(r, sb));
     }
+    // v of plane r, or 0 without loading it (momentum SGD keeps no v)
+    __device__ __forceinline__ float ldv_opt(int r, IX i, IX sb, bool sgd) const { return sgd ? 0.f : ldv(r, i, sb); }
     // Store the updated w, m, v of plane r (rounded per the storage; `key` is
     // sr_plane_key of this plane and step) and the restore direction of what
     // was stored.
     __device__ __forceinline__ void store(int r, IX i, IX sb, float w, float mm, float vv, const SLut &L,
                                           uint32_t key) const
     {
-        const bool st = L.stochastic != 0;
+        const bool st = L.stochastic != 0, sgd = L.sgd != 0;
         const uint32_t bits = st ? sr_bits(key, (uint32_t)i) : 0u;
         if (r < N_GEO) {
             const IX o = go(r, i);
             const float ms = st_val(m + o, mm, st, bits);
-            const float vs = st_val(v + o, vv, st, bits >> 16);
+            const float vs = sgd ? 0.f : st_val(v + o, vv, st, bits >> 16);
             geo[o] = w;
-            if (rdir) rdir[o] = restore_dir(ms, vs, L.eps);
+            if (rdir) rdir[o] = restore_dir(ms, vs, L.eps, sgd);
         } else {
             const IX o = so(r, sb);
             const float ms = st_val(shm + o, mm, st, bits);
-            const float vs = st_val(shv + o, vv, st, bits >> 16);
+            const float vs = sgd ? 0.f : st_val(shv + o, vv, st, bits >> 16);
             st_val(shw + o, w, st, sr_w_bits(bits));
-            if (shr) st_val(shr + o, restore_dir(ms, vs, L.eps), false, 0u);
+            if (shr) st_val(shr + o, restore_dir(ms, vs, L.eps, sgd), false, 0u);
         }
     }
 };
@@ -209,7 +229,7 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
             if (r < D) {
                 w_[u] = P.ldw(r, i, sb);
                 m_[u] = P.ldm(r, i, sb);
-                v_[u] = P.ldv(r, i, sb);
+                v_[u] = P.ldv_opt(r, i, sb, L.sgd);
                 g_[u] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
             }
         }
@@ -241,7 +261,7 @@ template <typename T, typename IX>
 __device__ __forceinline__ void adam_fetch(AdamRows<IX> &a, int u, const int32_t *__restrict__ uids,
                                            const uint8_t *__restrict__ udelay, const uint32_t *__restrict__ vmask,
                                            const uint32_t *__restrict__ vprefix, const Planes<T, IX> &P,
-                                           const float *__restrict__ grad, int64_t gcap, int D, int r0)
+                                           const float *__restrict__ grad, int64_t gcap, int D, int r0, bool sgd)
 {
     a.i = (IX)uids[u];
     a.sb = P.shbase(a.i);
@@ -254,7 +274,7 @@ __device__ __forceinline__ void adam_fetch(AdamRows<IX> &a, int u, const int32_t
         if (r < D) {
             a.w[j] = P.ldw(r, a.i, a.sb);
             a.m[j] = P.ldm(r, a.i, a.sb);
-            a.v[j] = P.ldv(r, a.i, a.sb);
+            a.v[j] = P.ldv_opt(r, a.i, a.sb, sgd);
             a.g[j] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
         }
     }
@@ -281,11 +301,12 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T, IX> P, i
 #pragma unroll
     for (int j = 0; j < RG; j++) key[j] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + j)) : 0u;
     AdamRows<IX> cur, nxt;
-    adam_fetch(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
+    const bool sgd = L.sgd != 0;
+    adam_fetch(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0, sgd);
     while (true) {
         const int un = u + stride;
         const bool more = un < n_upd;
-        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
+        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0, sgd);
 #pragma unroll
         for (int j = 0; j < RG; j++) {
             const int r = r0 + j;
@@ -460,16 +481,17 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
     w.mark(TP_APPLY1, s);
 }
 
-// rdir = m / (sqrt(v) + eps) for every plane.
+// rdir = m / (sqrt(v) + eps) for every plane (momentum SGD: rdir = m).
 template <typename T>
 __global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__restrict__ args)
 {
     const float eps = args->lut.eps;
+    const bool sgd = args->lut.sgd != 0;
     const int64_t total = (int64_t)D * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
         const int64_t i = e - (int64_t)r * n, sb = P.shbase(i);
-        const float dir = restore_dir(P.ldm(r, i, sb), P.ldv(r, i, sb), eps);
+        const float dir = restore_dir(P.ldm(r, i, sb), P.ldv_opt(r, i, sb, sgd), eps, sgd);
         if (r < N_GEO) P.rdir[r * P.pitch + i] = dir;
         else st_val(P.shr + (r - N_GEO) * P.sp + sb, dir, false, 0u);
     }
@@ -485,7 +507,8 @@ void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cuda
         k_refresh_rdir<__nv_bfloat16><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, sc.n, args);
 }
 
-// Catch-up without a step: m b1^c, v b2^c, w - param_lut[c] m / (sqrt(v) + eps).
+// Catch-up without a step: m b1^c, v b2^c, decay[c] w - param_lut[c] m / (sqrt(v) + eps)
+// (momentum SGD: b mu^c, v unchanged, w - param_lut[c] b).
 template <typename T>
 __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, int64_t n, int D,
                               const DevArgs *__restrict__ args, float *w_out, float *m_out, float *v_out)
@@ -499,7 +522,8 @@ __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, 
         for (int r = 0; r < D; r++) {
             float w = P.ldw(r, i, sb);
             float mm = P.ldm(r, i, sb), vv = P.ldv(r, i, sb);
-            if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[lr_group(r)][d], d, L.eps);
+            const int g = lr_group(r);
+            if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[g][d], L.decay[g][d], d, L.eps, L.sgd);
             if (m_out) m_out[r * pitch + i] = d ? L.mom[d - 1] * mm : mm;
             if (v_out) v_out[r * pitch + i] = d ? L.var[d - 1] * vv : vv;
         }

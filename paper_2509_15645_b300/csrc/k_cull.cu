@@ -24,16 +24,20 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
 {
     __shared__ DevCam s_cam;
     __shared__ CullCam s_cc;
-    __shared__ float s_plut[3][LUT_N];
+    __shared__ float s_plut[3][LUT_N], s_dec[3][LUT_N];
     __shared__ float s_eps;
-    __shared__ int s_restore;
+    __shared__ int s_restore, s_sgd;
     __shared__ uint32_t s_cnt[CULL_BLOCK / 32];
     if (threadIdx.x < sizeof(DevCam) / 4)
         ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
     if (threadIdx.x == 0) make_cull_cam(args->cam[view], s_cc);
-    if (threadIdx.x < 3 * LUT_N) s_plut[threadIdx.x / LUT_N][threadIdx.x % LUT_N] = args->lut.param[threadIdx.x / LUT_N][threadIdx.x % LUT_N];
+    if (threadIdx.x < 3 * LUT_N) {
+        s_plut[threadIdx.x / LUT_N][threadIdx.x % LUT_N] = args->lut.param[threadIdx.x / LUT_N][threadIdx.x % LUT_N];
+        s_dec[threadIdx.x / LUT_N][threadIdx.x % LUT_N] = args->lut.decay[threadIdx.x / LUT_N][threadIdx.x % LUT_N];
+    }
     if (threadIdx.x == 0) {
         s_eps = args->lut.eps;
+        s_sgd = args->lut.sgd;
         s_restore = args->lut.restore && m != nullptr && v != nullptr && counter != nullptr;
     }
     __syncthreads();
@@ -57,7 +61,8 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                     for (int r = 0; r < 10; r++) dd[r] = __ldg(rdir + r * pitch + i);
                     const int d = counter[i];
 #pragma unroll
-                    for (int r = 0; r < 10; r++) g[r] = restore_with_dir(g[r], dd[r], s_plut[lr_group(r)][d], d);
+                    for (int r = 0; r < 10; r++)
+                        g[r] = restore_with_dir(g[r], dd[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d);
                 } else if (s_restore) {
                     // m, v loads are issued together with w, not after the counter arrives
                     float mm[10], vv[10];
@@ -68,7 +73,9 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                     }
                     const int d = counter[i];
 #pragma unroll
-                    for (int r = 0; r < 10; r++) g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], d, s_eps);
+                    for (int r = 0; r < 10; r++)
+                        g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d, s_eps,
+                                             s_sgd);
                 }
                 if (maybe_visible(g, s_cc)) {
                     Proj P;
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
     __shared__ __align__(8) uint64_t bar[CSTAGES];
     __shared__ DevCam s_cam[MAX_VIEWS];
     __shared__ CullCam s_cc[MAX_VIEWS];
-    __shared__ float s_plut[3][LUT_N];
+    __shared__ float s_plut[3][LUT_N], s_dec[3][LUT_N];
     __shared__ uint32_t s_cnt[MAX_VIEWS][CT / 32];
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -155,7 +162,10 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
     }
     if (tid < nv) make_cull_cam(args->cam[view0 + tid], s_cc[tid]);
     if (tid < MAX_VIEWS * (CT / 32)) s_cnt[tid / (CT / 32)][tid % (CT / 32)] = 0;
-    if (tid < 3 * LUT_N) s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
+    if (tid < 3 * LUT_N) {
+        s_plut[tid / LUT_N][tid % LUT_N] = args->lut.param[tid / LUT_N][tid % LUT_N];
+        s_dec[tid / LUT_N][tid % LUT_N] = args->lut.decay[tid / LUT_N][tid % LUT_N];
+    }
     const bool restore = args->lut.restore && rdir != nullptr && counter != nullptr;
     const bool select = out.umask != nullptr;
     const bool need_cnt = restore || select;
@@ -231,7 +241,9 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
                     const int k = tid + e * CT;
 #pragma unroll
                     for (int r = 0; r < CPRE; r++)
-                        if (live[e]) g[e][r] = restore_with_dir(g[e][r], st[s].dir[r][k], s_plut[lr_group(r)][d[e]], d[e]);
+                        if (live[e])
+                            g[e][r] = restore_with_dir(g[e][r], st[s].dir[r][k], s_plut[lr_group(r)][d[e]],
+                                                       s_dec[lr_group(r)][d[e]], d[e]);
                 }
             }
             for (int v = 0; v < nv; v++) {
@@ -252,7 +264,8 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
                                 for (int r = CPRE; r < CPLANES; r++) dd[r - CPRE] = __ldg(rdir + r * pitch + i);
 #pragma unroll
                                 for (int r = CPRE; r < CPLANES; r++)
-                                    g[e][r] = restore_with_dir(g[e][r], dd[r - CPRE], s_plut[lr_group(r)][d[e]], d[e]);
+                                    g[e][r] = restore_with_dir(g[e][r], dd[r - CPRE], s_plut[lr_group(r)][d[e]],
+                                                               s_dec[lr_group(r)][d[e]], d[e]);
                             }
                             full[e] = true;
                             n_full++;
@@ -303,6 +316,21 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
 #pragma unroll
         for (int o = 16; o; o >>= 1) n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
         if (lane == 0 && n_full) atomicAdd(out.n_cand, (int)n_full);
+    }
+    if (s_abort) {
+        // the block's chunks from the one it stopped in onwards: no visible
+        // Gaussian and no update-set member (mask words and counts cleared), so
+        // the compactions that follow see a consistent, smaller set
+        const int64_t nwords = (n + 31) >> 5;
+        for (int64_t c = blockIdx.x + (q_stop / PER_CHUNK) * gridDim.x; c < nchunks; c += gridDim.x) {
+            const int64_t w1 = min(nwords, (c + 1) * (int64_t)CHUNK_WORDS);
+            for (int64_t wd = c * CHUNK_WORDS + tid; wd < w1; wd += CT) {
+                for (int v = 0; v < nv; v++) out.mask[v][wd] = 0u;
+                if (select) out.umask[wd] = 0u;
+            }
+            if (tid < nv) out.chunk[tid][c] = 0u;
+            if (select && tid == 0) out.uchunk[c] = 0u;
+        }
     }
     if (s_abort && tid == 0) {
         latch(status, GS_ERR_TIMEOUT);

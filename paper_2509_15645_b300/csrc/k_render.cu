@@ -27,8 +27,9 @@ constexpr int PROJ_BLOCK = 128;
 
 struct SLutR {
     float param[N_GROUPS][LUT_N];
+    float decay[N_GROUPS][LUT_N];
     float eps;
-    int restore;
+    int restore, sgd;
 };
 
 template <int DEG, typename T>
@@ -48,10 +49,14 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
     __shared__ SLutR L;
     if (threadIdx.x < sizeof(DevCam) / 4)
         ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
-    for (int t = threadIdx.x; t < N_GROUPS * LUT_N; t += blockDim.x) L.param[t / LUT_N][t % LUT_N] = args->lut.param[t / LUT_N][t % LUT_N];
+    for (int t = threadIdx.x; t < N_GROUPS * LUT_N; t += blockDim.x) {
+        L.param[t / LUT_N][t % LUT_N] = args->lut.param[t / LUT_N][t % LUT_N];
+        L.decay[t / LUT_N][t % LUT_N] = args->lut.decay[t / LUT_N][t % LUT_N];
+    }
     if (threadIdx.x == 0) {
         L.eps = args->lut.eps;
         L.restore = args->lut.restore && sc.m && sc.v && sc.counter;
+        L.sgd = args->lut.sgd;
     }
     __syncthreads();
     const int n_vis = min(*n_vis_p, cap);
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
 #pragma unroll
                     for (int r = 0; r < D; r++) {
                         const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * sp + sb);
-                        w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], d);
+                        w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
                     }
                 } else if (sc.rdir) {
                     // host tier: geometry directions kept, SH directions recomputed from the staged m, v
@@ -92,10 +97,12 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
 #pragma unroll
                     for (int r = 0; r < D; r++) {
                         if (r < N_GEO) {
-                            w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d], d);
+                            w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d],
+                                                    L.decay[lr_group(r)][d], d);
                         } else {
                             const float mm = ld_val(msh + (r - N_GEO) * sp + sb), vv = ld_val(vsh + (r - N_GEO) * sp + sb);
-                            w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], d, L.eps);
+                            w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d,
+                                                 L.eps, L.sgd);
                         }
                     }
                 } else {
@@ -105,7 +112,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                     for (int r = 0; r < D; r++) {
                         const float mm = r < N_GEO ? ld_val(mp + r * pitch + i) : ld_val(msh + (r - N_GEO) * sp + sb);
                         const float vv = r < N_GEO ? ld_val(vp + r * pitch + i) : ld_val(vsh + (r - N_GEO) * sp + sb);
-                        w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], d, L.eps);
+                        w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d, L.eps,
+                                             L.sgd);
                     }
                 }
             }

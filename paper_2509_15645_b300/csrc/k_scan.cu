@@ -79,12 +79,14 @@ __global__ void k_scan_partials(uint32_t *partials, int g, int *total_out, int t
         ex += v[j];
     }
     if (threadIdx.x == 0 && total_out) {
-        int t = (int)tot;
-        if (total_cap > 0 && t > total_cap) {
+        // compared unsigned: a total past 2^31 (only from counts that are not
+        // a cull's) must not pass as a negative count
+        uint32_t t = tot;
+        if (total_cap > 0 && t > (uint32_t)total_cap) {
             if (status) latch(status, GS_ERR_CAPACITY);
-            t = total_cap;
+            t = (uint32_t)total_cap;
         }
-        *total_out = t;
+        *total_out = (int)min(t, 0x7fffffffu);
     }
 }
 
@@ -147,12 +149,14 @@ __global__ void __launch_bounds__(SMALL_SCAN_THREADS) k_scan_small(uint32_t *v, 
         ex += x;
     }
     if (threadIdx.x == 0 && total_out) {
-        int t = (int)tot;
-        if (total_cap > 0 && t > total_cap) {
+        // compared unsigned: a total past 2^31 (only from counts that are not
+        // a cull's) must not pass as a negative count
+        uint32_t t = tot;
+        if (total_cap > 0 && t > (uint32_t)total_cap) {
             if (status) latch(status, GS_ERR_CAPACITY);
-            t = total_cap;
+            t = (uint32_t)total_cap;
         }
-        *total_out = t;
+        *total_out = (int)min(t, 0x7fffffffu);
     }
 }
 
@@ -175,7 +179,8 @@ void scan_counts(uint32_t *v, int64_t len, int *total_out, int cap, Work &w, cud
 // reads before the first store, so a chunk costs one memory latency.
 constexpr int COMPACT_BLOCK = 256, COMPACT_WPW = CHUNK_WORDS / (COMPACT_BLOCK / 32);
 
-__global__ void __launch_bounds__(COMPACT_BLOCK) k_compact_mask(const uint32_t *__restrict__ mask, int64_t nwords,
+__global__ void __launch_bounds__(COMPACT_BLOCK) k_compact_mask(const uint32_t *__restrict__ mask, int64_t n,
+                                                                int64_t nwords,
                                                                 const uint32_t *__restrict__ chunk_ofs, int32_t *ids,
                                                                 uint32_t *word_prefix, int cap, uint8_t *counter,
                                                                 uint8_t *delay)
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(COMPACT_BLOCK) k_compact_mask(const uint32_t *
             if ((m >> lane) & 1u) {
                 const uint32_t pos = s_pref[j] + __popc(m & ((1u << lane) - 1u));
                 const int64_t id = (w0 + j) * 32 + lane;
-                if ((int)pos < cap) {
+                if (pos < (uint32_t)cap && id < n) {     // unsigned: no offset passes as negative
                     if (ids) ids[pos] = (int32_t)id;
                     if (counter) {           // optimizer update set: record the delay, clear the counter
                         delay[pos] = cv[k];
@@ -257,7 +262,7 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
         k_chunk_counts<<<w.grid(nchunks * 32, 256), 256, 0, s>>>(mask, nwords, chunk_cnt);
     scan_counts(chunk_cnt, nchunks, count_out, cap, w, s);
     k_compact_mask<<<w.grid(nchunks * COMPACT_BLOCK, COMPACT_BLOCK), COMPACT_BLOCK, 0, s>>>(
-        mask, nwords, chunk_cnt, ids, word_prefix, cap, counter, delay);
+        mask, n, nwords, chunk_cnt, ids, word_prefix, cap, counter, delay);
 }
 
 }  // namespace gs

@@ -75,3 +75,56 @@ def test_invalid_arguments(gs, step, max_defer):
     adam = gs.adam_struct(max_defer=max_defer)
     with pytest.raises(_lib.GsError):
         gs.adam_tables(adam, step)
+
+
+@pytest.mark.parametrize("wd", [0.0, 0.1, 3.0])
+@pytest.mark.parametrize("t", [1, 2, 5, 16, 17, 300])
+def test_adamw_tables_match_oracle(gs, orc, t, wd):
+    """AdamW (decoupled decay): the restore coefficient is Fig. 10's recursion
+    with its i-th term weighted by (1 - lr wd)^(i-1) and the restore's decay
+    (1 - lr wd)^d, against the oracle's tables; wd = 0 gives Adam's tables."""
+    from paper_2509_15645_b300 import _lib
+    lrs = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4]
+    adam = gs.adam_struct(lr=lrs, eps=1e-15, max_defer=15, optimizer=_lib.GS_OPT_ADAMW, weight_decay=wd)
+    T = gs.adam_tables(adam, t)
+    hp = orc.AdamHyper(lr=[_f32(x) for x in lrs], beta1=_f32(0.9), beta2=_f32(0.999), eps=1e-15, max_defer=15)
+    A = gs.adam_tables(gs.adam_struct(lr=lrs, eps=1e-15, max_defer=15), t)
+    for g in range(6):
+        wl, dec = orc.adamw_lut(t, hp.lr[g], hp, _f32(wd))
+        for d in range(1, 16):
+            assert T["decay"][g][d] == pytest.approx(dec[d], rel=F32_REL, abs=0), (g, d)
+            if d >= t:
+                assert T["param"][g][d] == 0.0
+            else:
+                assert abs(T["param"][g][d] - wl[d]) <= F32_REL * abs(wl[d]), (g, d, T["param"][g][d], wl[d])
+        if wd == 0.0:
+            assert T["param"][g] == A["param"][g] and all(x == 1.0 for x in T["decay"][g])
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.5, 0.9])
+@pytest.mark.parametrize("t", [1, 3, 40])
+def test_sgdm_tables_match_oracle(gs, orc, t, mu):
+    """Momentum SGD: restore coefficient lr (mu + ... + mu^d), buffer decay
+    mu^(d+1), the gradient taken with weight 1, no bias correction."""
+    from paper_2509_15645_b300 import _lib
+    lrs = [1e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3]
+    adam = gs.adam_struct(lr=lrs, beta1=mu, max_defer=15, optimizer=_lib.GS_OPT_SGDM)
+    T = gs.adam_tables(adam, t)
+    for g in range(6):
+        sl, mo = orc.sgdm_lut(_f32(lrs[g]), _f32(mu), 15)
+        for d in range(1, 16):
+            want = sl[d] if d < t else 0.0
+            assert abs(T["param"][g][d] - want) <= F32_REL * abs(want), (g, d)
+        assert T["step_size"][g] == _f32(lrs[g])
+    for d in range(16):
+        assert T["mom"][d] == pytest.approx(_f32(mu) ** (d + 1), rel=F32_REL, abs=1e-45)
+        assert T["var"][d] == 1.0
+    assert T["bias_corr"] == 1.0
+
+
+@pytest.mark.parametrize("bad", [dict(optimizer=3), dict(optimizer=1, weight_decay=-0.5),
+                                 dict(optimizer=1, weight_decay=float("nan")), dict(optimizer=1, weight_decay=2000.0)])
+def test_invalid_optimizer_arguments(gs, bad):
+    from paper_2509_15645_b300 import _lib
+    with pytest.raises(_lib.GsError):
+        gs.adam_tables(gs.adam_struct(lr=1e-3, **bad), 5)

@@ -367,6 +367,92 @@ def test_adam_step_parity(gs, orc, mode, n, t):
         np.testing.assert_array_equal(a[:, ~upd], b[:, ~upd])   # untouched
 
 
+@pytest.mark.parametrize("opt", ["adamw", "sgdm"])
+@pytest.mark.parametrize("mode", ["deferred", "eager"])
+@pytest.mark.parametrize("n,t", [(1000, 40), (70001, 500)])
+def test_optimizer_variant_step_parity(gs, orc, opt, mode, n, t):
+    """Deferred AdamW (decoupled decay, restore w <- decay[d] w - wlut[d] m /
+    (sqrt(v) + eps)) and deferred momentum SGD (restore w <- w - slut[d] b, b
+    <- mu^(d+1) b + g) against the oracle's steps of the same optimizer from the
+    same stored state, within FP32 rounding of each update term; counters
+    bit-exact; Gaussians outside the update set untouched."""
+    from paper_2509_15645_b300 import _lib
+    rng = np.random.default_rng(n + t + (7 if opt == "sgdm" else 0))
+    deg, D = 3, 59
+    w, m, v, cnt = _adam_state(rng, D, n, t)
+    lr = [1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4]
+    wd, mu = 0.05, 0.9
+    ids = np.sort(rng.choice(n, n // 5, replace=False)).astype(np.int32)
+    gc = (rng.normal(size=(D, ids.size)) * 1e-3).astype(np.float32)
+    scene = gs.GaussianScene(w, deg)
+    scene.m[:, :n] = torch.as_tensor(m, device="cuda")
+    scene.v[:, :n] = torch.as_tensor(v, device="cuda")
+    scene.counter[:n] = torch.as_tensor(cnt, device="cuda")
+    scene.step = t - 1
+    ctx = make_ctx(gs, n, 64, 64)
+    kind = _lib.GS_OPT_ADAMW if opt == "adamw" else _lib.GS_OPT_SGDM
+    adam = gs.adam_struct(lr=lr, eps=1e-15, beta1=mu if opt == "sgdm" else 0.9, mode=0 if mode == "deferred" else 2,
+                          optimizer=kind, weight_decay=wd)
+    ctx.refresh_rdir(scene, adam)              # m, v were set directly
+    ids_t = torch.as_tensor(ids, device="cuda")
+    nv = torch.tensor([ids.size], dtype=torch.int32, device="cuda")
+    gct = torch.zeros(D, ctx.max_visible, dtype=torch.float32, device="cuda")
+    gct[:, :ids.size] = torch.as_tensor(gc, device="cuda")
+    ctx.adam_deferred(scene, ids_t, nv, gct, adam)
+    ctx.sync_status()
+    hp = hp32(orc, lr=lr, eps=1e-15)
+    lr32 = hp.lr
+    W, M, V, Cn = f32(w), f32(m), f32(v), cnt.copy()
+    g = np.zeros((D, n))
+    g[:, ids] = f32(gc)
+    wd32, mu32 = float(np.float32(wd)), float(np.float32(mu))
+    if opt == "adamw" and mode == "deferred":
+        orc.adamw_deferred(W, M, V, Cn, ids, f32(gc), t, hp, wd32, mode=0)
+    elif opt == "adamw":
+        orc.adamw_eager(W, M, V, g, t, hp, wd32)
+    elif mode == "deferred":
+        orc.sgdm_deferred(W, M, Cn, ids, f32(gc), lr32, mu32, max_defer=15, mode=0)
+    else:
+        orc.sgdm_eager(W, M, g, lr32, mu32)
+    gw = scene.w[:, :n].cpu().numpy().astype(np.float64)
+    gm = scene.m[:, :n].cpu().numpy().astype(np.float64)
+    gv = scene.v[:, :n].cpu().numpy().astype(np.float64)
+    if mode == "deferred":
+        np.testing.assert_array_equal(scene.counter[:n].cpu().numpy(), Cn)
+    u = 2.0 ** -24
+    upd = np.zeros(n, bool)
+    upd[ids] = True
+    if mode == "deferred":
+        upd |= cnt >= 15
+        dly = np.where(upd, cnt, 0).astype(int)
+    else:
+        upd[:] = True
+        dly = np.zeros(n, int)
+    m0, v0, w0 = f32(m), f32(v), f32(w)
+    restore = np.zeros((D, n))
+    for grp, rows in enumerate([slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, D)]):
+        if opt == "adamw":
+            wl, _ = orc.adamw_lut(t, lr32[grp], hp, wd32)
+            restore[rows] = np.nan_to_num(wl)[dly] * np.abs(m0[rows]) / np.sqrt(v0[rows])
+        else:
+            sl, _ = orc.sgdm_lut(lr32[grp], mu32, 15)
+            restore[rows] = sl[dly] * np.abs(m0[rows]) + lr32[grp] * np.abs(M[rows])
+    if opt == "adamw":
+        b1p, b2p = hp.beta1 ** (dly + 1), hp.beta2 ** (dly + 1)
+        bm = 8 * u * (b1p * np.abs(m0) + (1 - hp.beta1) * np.abs(g)) + 1e-30
+        bv = 8 * u * (b2p * v0 + (1 - hp.beta2) * g * g) + 1e-38
+        checks = (("m", gm, M, bm), ("v", gv, V, bv))
+    else:
+        bm = 8 * u * (mu32 ** (dly + 1) * np.abs(m0) + np.abs(g)) + 1e-30
+        checks = (("m", gm, M, bm),)
+        np.testing.assert_array_equal(gv, v0)          # momentum SGD keeps no v: never written
+    bw = 16 * u * (np.abs(w0) + restore + np.abs(W - w0)) + 1e-30
+    for name, a, b, bound in checks + (("w", gw, W, bw),):
+        err = np.abs(a - b)
+        assert np.all(err[:, upd] <= bound[:, upd]), (name, np.max(err / bound))
+        np.testing.assert_array_equal(a[:, ~upd], b[:, ~upd])   # untouched
+
+
 def test_materialize_parity(gs, orc):
     rng = np.random.default_rng(5)
     n, D, t_done = 5000, 14, 30

@@ -58,13 +58,19 @@ def _state(scene, n):
             v.cpu().numpy().astype(np.float64), scene.counter[:n].cpu().numpy().copy())
 
 
-def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr):
+def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr, opt=None):
     """The GPU's state after step t against the oracle's deferred step from the
     stored state (W, M, V, Cn) with the GPU's visible set and the oracle's
     gradients.  fp32: FP32 rounding of each update term; bf16 stores: one bf16
-    ulp (stochastic rounding picks either neighbour) plus the step's share."""
+    ulp (stochastic rounding picks either neighbour) plus the step's share.
+    opt: None (Adam), ("adamw", weight decay) or ("sgdm", momentum)."""
     W0 = W.copy()
-    orc.adam_deferred(W, M, V, Cn, gids, grad[:, gids], t, hp)
+    if opt is None:
+        orc.adam_deferred(W, M, V, Cn, gids, grad[:, gids], t, hp)
+    elif opt[0] == "adamw":
+        orc.adamw_deferred(W, M, V, Cn, gids, grad[:, gids], t, hp, opt[1])
+    else:
+        orc.sgdm_deferred(W, M, Cn, gids, grad[:, gids], hp.lr, opt[1], max_defer=hp.max_defer)
     gw, gm, gv, gc = _state(scene, n)
     np.testing.assert_array_equal(gc, Cn)
     D = W.shape[0]
@@ -75,6 +81,8 @@ def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr):
     if not prec_bf16:
         for k, s in GROUPS.items():
             assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
+        if opt is not None and opt[0] == "sgdm":
+            np.testing.assert_array_equal(gv, V)      # momentum SGD keeps no v
         err = np.abs(gw - W)
         bound = 2e-3 * lr_row + 1e-6 + 4e-7 * np.abs(W) + np.where(und, 2 * lr_row, 0.0)
         assert np.all(err <= bound), (t, np.max(err / bound), np.unravel_index(np.argmax(err / bound), err.shape))
@@ -92,9 +100,11 @@ def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr):
     return np.mean(np.abs(W - W0) > 0)
 
 
-@pytest.mark.parametrize("bf16", [False, True])
-def test_restore_over_changing_views(gs, orc, bf16):
-    """Resident scene, fp32 or the bf16 form (counter bound 15)."""
+@pytest.mark.parametrize("bf16,opt", [(False, "adam"), (True, "adam"), (False, "adamw"), (False, "sgdm")])
+def test_restore_over_changing_views(gs, orc, bf16, opt):
+    """Resident scene, fp32 or the bf16 form (counter bound 15); Adam, and the
+    deferred AdamW and momentum SGD of §4.3 in fp32."""
+    from paper_2509_15645_b300 import _lib
     cams = _views()
     targets = _targets(orc, cams)
     P = _scene(41)
@@ -102,8 +112,11 @@ def test_restore_over_changing_views(gs, orc, bf16):
     scene = gs.GaussianScene(P, DEG, precision=prec)
     ctx = gs.Context(max_gaussians=N, max_visible=N, max_keys=64 * N, max_width=96, max_height=72, tile=TILE,
                      max_sh_degree=DEG)
-    adam = gs.adam_struct(lr=LR, eps=1e-15, seed=9)
+    wd, mu = 0.05, 0.9
+    kind = {"adam": _lib.GS_OPT_ADAM, "adamw": _lib.GS_OPT_ADAMW, "sgdm": _lib.GS_OPT_SGDM}[opt]
+    adam = gs.adam_struct(lr=LR, eps=1e-15, seed=9, optimizer=kind, weight_decay=wd, beta1=mu if opt == "sgdm" else 0.9)
     hp = hp32(orc, lr=LR, eps=1e-15)
+    ospec = None if opt == "adam" else ((opt, float(np.float32(wd))) if opt == "adamw" else (opt, float(np.float32(mu))))
     tg = [torch.as_tensor(x, dtype=torch.float32, device="cuda") for x in targets]
     delays = []
     for t, k in enumerate(ORDER, start=1):
@@ -120,6 +133,10 @@ def test_restore_over_changing_views(gs, orc, bf16):
                 pl, _, _ = orc.adam_lut(t, hp.lr[g], hp)
                 for r in rows:
                     Wcur[r] = W[r] - np.float32(pl[Cn]).astype(np.float64) * rd[r]
+        elif opt == "adamw":
+            Wcur, _, _ = orc.adamw_materialize(W, M, V, Cn, t - 1, hp, ospec[1])
+        elif opt == "sgdm":
+            Wcur, _ = orc.sgdm_materialize(W, M, Cn, hp.lr, ospec[1], max_defer=hp.max_defer)
         else:
             Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)
         rr = orc.render_loss_backward(Wcur, DEG, cam, targets[k], TILE)
@@ -149,7 +166,7 @@ def test_restore_over_changing_views(gs, orc, bf16):
         loss = ctx.step(scene, [cam], [tg[k]], adam)
         ctx.sync_status()
         assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
-        moved = _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids.astype(np.int32), rr["grad"], hp, LR)
+        moved = _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids.astype(np.int32), rr["grad"], hp, LR, ospec)
         assert moved > 0.02
     d = np.concatenate(delays)
     hist = np.bincount(d, minlength=16)
