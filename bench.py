@@ -75,6 +75,7 @@ class ClockSampler:
         self.index, self.pci = index, pci_bus_id
         self.proc = self.thread = None
         self.samples = []
+        self.nvml_error = None
 
     def _nvml_handle(self):
         import pynvml
@@ -110,8 +111,9 @@ class ClockSampler:
             self.thread = threading.Thread(target=loop, daemon=True)
             self.thread.start()
             return
-        except Exception:
+        except Exception as e:
             self.thread = None
+            self.nvml_error = repr(e)[:160]
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -149,7 +151,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 100 ms"}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 100 ms",
+                "nvml_error": self.nvml_error}
 
 
 # ---------------------------------------------------------------------------- workload

@@ -45,7 +45,6 @@ struct DevLut {
     int max_defer;
     int step;                       // t
     int restore;                    // 0: render/cull without restore
-    int sgd;                        // momentum SGD: the restore direction is the buffer m itself, no v
     float decay[N_GROUPS][LUT_N];   // AdamW: (1 - lr wd)^d of the restore; 1 otherwise
     float wdf[N_GROUPS];            // AdamW: 1 - lr wd of the current step; 1 otherwise
 };
@@ -193,24 +192,31 @@ __device__ __forceinline__ float sqrt_fast(float x)
     return r;
 }
 
+// Optimizer kinds as template arguments (GS_OPT_ADAM, GS_OPT_ADAMW,
+// GS_OPT_SGDM): each kernel that restores or steps is compiled per kind, so
+// Adam's code has no trace of the others.
 // Adam and AdamW restore along m / (sqrt(v) + eps); momentum SGD along its
 // buffer b (held in the m planes), exactly.
-__device__ __forceinline__ float restore_dir(float m, float v, float eps, bool sgd = false)
+template <int OPT = GS_OPT_ADAM>
+__device__ __forceinline__ float restore_dir(float m, float v, float eps)
 {
-    return sgd ? m : __fdividef(m, sqrt_fast(v) + eps);
+    if (OPT == GS_OPT_SGDM) return m;
+    return __fdividef(m, sqrt_fast(v) + eps);
 }
 
-// w <- dec w - plut dir for a delay d > 0.  dec = 1 (Adam, SGD) multiplies
-// exactly, so those restores are a single FMA on w.
+// w <- dec w - plut dir for a delay d > 0 (dec, the decay of the deferred
+// steps, only for AdamW).
+template <int OPT = GS_OPT_ADAM>
 __device__ __forceinline__ float restore_with_dir(float w, float dir, float plut, float dec, int d)
 {
-    return d ? __fmaf_rn(-plut, dir, __fmul_rn(dec, w)) : w;
+    if (OPT == GS_OPT_ADAMW) return d ? __fmaf_rn(-plut, dir, __fmul_rn(dec, w)) : w;
+    return d ? __fmaf_rn(-plut, dir, w) : w;
 }
 
-__device__ __forceinline__ float restore_param(float w, float m, float v, float plut, float dec, int d, float eps,
-                                               bool sgd = false)
+template <int OPT = GS_OPT_ADAM>
+__device__ __forceinline__ float restore_param(float w, float m, float v, float plut, float dec, int d, float eps)
 {
-    return d ? restore_with_dir(w, restore_dir(m, v, eps, sgd), plut, dec, d) : w;
+    return d ? restore_with_dir<OPT>(w, restore_dir<OPT>(m, v, eps), plut, dec, d) : w;
 }
 
 // ---------------------------------------------------------------------------

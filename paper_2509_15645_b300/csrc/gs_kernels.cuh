@@ -2,6 +2,8 @@
 // scratch-workspace view they share.
 #pragma once
 
+#include <type_traits>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -82,7 +84,19 @@ struct SceneView {
     int deg, D;
     int prec;             // GS_FP32, GS_BF16_SH_MOM or GS_BF16_SH_MOM_RN
     int tier;             // GS_TIER_DEVICE or GS_TIER_HOST_SH
+    int opt;              // optimizer whose state the planes hold (GS_OPT_*): picks the restoring kernels
 };
+
+// Calls f(std::integral_constant<int, GS_OPT_x>{}) for the optimizer kind
+// `opt`, so a launcher instantiates its kernel per kind.  Host only.
+template <class F> inline void with_opt(int opt, F &&f)
+{
+    switch (opt) {
+    case GS_OPT_ADAMW: f(std::integral_constant<int, GS_OPT_ADAMW>{}); break;
+    case GS_OPT_SGDM: f(std::integral_constant<int, GS_OPT_SGDM>{}); break;
+    default: f(std::integral_constant<int, GS_OPT_ADAM>{}); break;
+    }
+}
 
 // Timing points recorded inside a step (see gs_timing_enable).
 enum { TP_STEP0 = 0, TP_CULL0, TP_CULL1, TP_FWD0, TP_FWD1, TP_BWD0, TP_BWD1, TP_ADAM0, TP_APPLY0, TP_APPLY1,

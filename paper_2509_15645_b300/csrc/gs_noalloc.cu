@@ -149,6 +149,7 @@ extern "C" gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam
     sv.pitch = scene->pitch;
     sv.deg = scene->sh_degree;
     sv.D = N_GEO + 3 * (scene->sh_degree + 1) * (scene->sh_degree + 1);
+    sv.opt = adam ? adam->optimizer : GS_OPT_ADAM;
 
     const int64_t nchunks = (sv.n + CHUNK - 1) / CHUNK;
     k_noalloc_args<<<1, 128, 0, s>>>(a, args);

@@ -30,7 +30,7 @@ struct GraphCache {
     float *rdir = nullptr;
     uint8_t *counter = nullptr;
     int64_t n = 0, pitch = 0;
-    int deg = -1, n_views = 0, mode = -1, prec = -1;
+    int deg = -1, n_views = 0, mode = -1, prec = -1, opt = -1;
     int W[MAX_VIEWS] = {0}, H[MAX_VIEWS] = {0};
     float *loss = nullptr;
     bool timed = false;
@@ -300,7 +300,6 @@ DevLut gs::make_lut(const gs_adam_cfg *a, int t, bool restore, int precision)
     L.seed = (uint32_t)a->seed;
     L.stochastic = precision == GS_BF16_SH_MOM ? 1 : 0;
     const int opt = a->optimizer;
-    L.sgd = opt == GS_OPT_SGDM;
     const double b1 = a->beta1, b2 = a->beta2;
     if (opt == GS_OPT_SGDM) {
         const double mu = b1;
@@ -411,6 +410,7 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     sv.pitch = P;
     sv.deg = s->sh_degree;
     sv.D = n_params(s->sh_degree);
+    sv.opt = GS_OPT_ADAM;      // callers with optimizer hyper-parameters set their kind
     if (!host) {
         sv.sh.w = s->sh;
         sv.sh.m = s->m ? (char *)s->m + N_GEO * P * eb : nullptr;
@@ -582,6 +582,7 @@ gs_status gs_cull(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, const 
     if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
     if (!ids_out || !n_vis_out) return fail(c, GS_ERR_INVALID_ARG, "NULL output");
     if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (adam) sv.opt = adam->optimizer;
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
     a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
@@ -605,6 +606,7 @@ gs_status gs_split_point(gs_ctx *c, const gs_scene *scene, const gs_camera *cam,
     if (axis != 0 && axis != 1) return fail(c, GS_ERR_INVALID_ARG, "axis must be 0 (x) or 1 (y)");
     if (steps < 0 || steps > 32 || !split_out) return fail(c, GS_ERR_INVALID_ARG, "steps out of range or NULL output");
     if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (adam) sv.opt = adam->optimizer;
     if (c->cfg.max_views < 2) return fail(c, GS_ERR_INVALID_ARG, "splitting needs a context with max_views >= 2");
     const int T = axis == 0 ? c->cfg.tile_w : c->cfg.tile_h;
     const int tiles = ((axis == 0 ? cam->width : cam->height) + T - 1) / T;
@@ -673,6 +675,7 @@ gs_status gs_render_fwd(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, 
     if (!valid_cam(c, cam)) return fail(c, GS_ERR_INVALID_ARG, "invalid camera");
     if (!ids || !n_vis || !image_out) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
     if (adam && !valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    if (adam) sv.opt = adam->optimizer;
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
     a.cam[0] = make_cam(*cam, c->cfg.tile_w, c->cfg.tile_h);
@@ -716,6 +719,7 @@ gs_status gs_adam_deferred(gs_ctx *c, gs_scene *scene, const int32_t *ids, const
     gs_status st = scene_view(c, scene, true, sv);
     if (st) return st;
     if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    sv.opt = adam->optimizer;
     if (!ids || !n_vis || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
@@ -743,6 +747,7 @@ gs_status gs_adam_materialize(gs_ctx *c, const gs_scene *scene, const gs_adam_cf
     gs_status st = scene_view(c, scene, true, sv);
     if (st) return st;
     if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    sv.opt = adam->optimizer;
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
     a.lut = make_lut(adam, scene->step + 1, true);
@@ -758,6 +763,7 @@ gs_status gs_refresh_rdir(gs_ctx *c, const gs_scene *scene, const gs_adam_cfg *a
     gs_status st = scene_view(c, scene, true, sv);
     if (st) return st;
     if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    sv.opt = adam->optimizer;
     if (!sv.rdir) return fail(c, GS_ERR_INVALID_ARG, "scene has no rdir planes");
     cudaStream_t s = (cudaStream_t)stream;
     DevArgs a{};
@@ -1268,9 +1274,9 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
 }
 
 static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
-                          float *loss, bool timed, int variant, uint32_t first_wait)
+                          float *loss, bool timed, int variant, uint32_t first_wait, int opt)
 {
-    if (!g.exec || g.first_wait != first_wait || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
+    if (!g.exec || g.first_wait != first_wait || g.opt != opt || g.geo != sc->geo || g.sh != sc->sh || g.m != sc->m || g.v != sc->v || g.counter != sc->counter ||
         g.rdir != sc->rdir || g.n != sc->n || g.pitch != sc->pitch || g.deg != sc->sh_degree ||
         g.prec != sc->precision || g.n_views != n_views || g.mode != mode ||
         g.loss != loss || g.timed != timed || g.variant != variant)
@@ -1288,6 +1294,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
     gs_status st = scene_view(c, scene, true, sv, true);
     if (st) return st;
     if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    sv.opt = adam->optimizer;
     if (n_views < 1 || n_views > c->cfg.max_views || !views || !targets || !loss_out)
         return fail(c, GS_ERR_INVALID_ARG, "invalid views/targets/loss");
     DevArgs a{};
@@ -1308,7 +1315,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         return st;
     }
     if (!graph_matches(g, scene, views, n_views, adam->mode, loss_out, timed, c->rbs[0].variant * 16 + c->rbs[0].variant_bwd,
-                       c->w.cull_first_wait)) {
+                       c->w.cull_first_wait, adam->optimizer)) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -1382,6 +1389,7 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
         g.timed = timed;
         g.variant = c->rbs[0].variant * 16 + c->rbs[0].variant_bwd;
         g.first_wait = c->w.cull_first_wait;
+        g.opt = adam->optimizer;
         for (int v = 0; v < n_views; v++) { g.W[v] = views[v].width; g.H[v] = views[v].height; }
     }
     if (timed) {

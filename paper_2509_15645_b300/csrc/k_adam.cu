@@ -98,7 +98,7 @@ struct SLut {
     float step_size[N_GROUPS], wdf[N_GROUPS];
     float bias_corr, inv_bias_corr, omb1, omb2, eps;
     uint32_t seed, step;
-    int stochastic, sgd;
+    int stochastic;
 };
 
 __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
@@ -122,29 +122,30 @@ __device__ __forceinline__ void load_slut(SLut &s, const DevLut &L)
         s.seed = L.seed;
         s.step = (uint32_t)L.step;
         s.stochastic = L.stochastic;
-        s.sgd = L.sgd;
     }
     __syncthreads();
 }
 
 // Restore (delay d) + one optimizer step for one value; d = 0 is the plain
-// step.  Adam / AdamW: Eq. 1 (AdamW with the decoupled decay of the step,
-// wdf = 1 - lr wd; wdf = 1 and decay = 1 multiply exactly, so Adam's
-// arithmetic is the same as without them).  Momentum SGD: the buffer lives in
-// m (mom = mu^(d+1), omb1 = 1), v is left alone.
+// step.  Adam: Eq. 1.  AdamW: Eq. 1 after the decoupled decay of the step
+// (wdf = 1 - lr wd) and with the deferred steps' decay in the restore.
+// Momentum SGD: the buffer lives in m (mom = mu^(d+1), omb1 = 1), v is left
+// alone.
+template <int OPT>
 __device__ __forceinline__ void adam_value(float &w, float &m, float &v, float g, int d, int grp, const SLut &L)
 {
     const float m_new = L.mom[d] * m + L.omb1 * g;
-    if (L.sgd) {
-        const float wr = restore_param(w, m, v, L.param[grp][d], 1.f, d, L.eps, true);
+    if (OPT == GS_OPT_SGDM) {
+        const float wr = restore_param<OPT>(w, m, v, L.param[grp][d], 1.f, d, L.eps);
         w = wr - L.step_size[grp] * m_new;
         m = m_new;
         return;
     }
     const float v_new = L.var[d] * v + L.omb2 * g * g;
-    const float wr = restore_param(w, m, v, L.param[grp][d], L.decay[grp][d], d, L.eps);
+    const float wr = restore_param<OPT>(w, m, v, L.param[grp][d], L.decay[grp][d], d, L.eps);
     const float denom = sqrt_fast(v_new) * L.inv_bias_corr + L.eps;
-    w = __fmul_rn(L.wdf[grp], wr) - L.step_size[grp] * __fdividef(m_new, denom);
+    const float ws = OPT == GS_OPT_ADAMW ? __fmul_rn(L.wdf[grp], wr) : wr;
+    w = ws - L.step_size[grp] * __fdividef(m_new, denom);
     m = m_new;
     v = v_new;
 }
@@ -190,32 +191,36 @@ template <typename T, typename IX = int64_t> struct Planes {
         return ld_val(r < N_GEO ? v + go(r, i) : shv + so(r, sb));
     }
     // v of plane r, or 0 without loading it (momentum SGD keeps no v)
-    __device__ __forceinline__ float ldv_opt(int r, IX i, IX sb, bool sgd) const { return sgd ? 0.f : ldv(r, i, sb); }
+    template <int OPT> __device__ __forceinline__ float ldv_opt(int r, IX i, IX sb) const
+    {
+        return OPT == GS_OPT_SGDM ? 0.f : ldv(r, i, sb);
+    }
     // Store the updated w, m, v of plane r (rounded per the storage; `key` is
     // sr_plane_key of this plane and step) and the restore direction of what
     // was stored.
+    template <int OPT>
     __device__ __forceinline__ void store(int r, IX i, IX sb, float w, float mm, float vv, const SLut &L,
                                           uint32_t key) const
     {
-        const bool st = L.stochastic != 0, sgd = L.sgd != 0;
+        const bool st = L.stochastic != 0, sgd = OPT == GS_OPT_SGDM;
         const uint32_t bits = st ? sr_bits(key, (uint32_t)i) : 0u;
         if (r < N_GEO) {
             const IX o = go(r, i);
             const float ms = st_val(m + o, mm, st, bits);
             const float vs = sgd ? 0.f : st_val(v + o, vv, st, bits >> 16);
             geo[o] = w;
-            if (rdir) rdir[o] = restore_dir(ms, vs, L.eps, sgd);
+            if (rdir) rdir[o] = restore_dir<OPT>(ms, vs, L.eps);
         } else {
             const IX o = so(r, sb);
             const float ms = st_val(shm + o, mm, st, bits);
             const float vs = sgd ? 0.f : st_val(shv + o, vv, st, bits >> 16);
             st_val(shw + o, w, st, sr_w_bits(bits));
-            if (shr) st_val(shr + o, restore_dir(ms, vs, L.eps, sgd), false, 0u);
+            if (shr) st_val(shr + o, restore_dir<OPT>(ms, vs, L.eps), false, 0u);
         }
     }
 };
 
-template <typename T>
+template <typename T, int OPT>
 __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, int k, const float *__restrict__ grad,
                                           int64_t gcap, int d, const SLut &L)
 {
@@ -229,7 +234,7 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
             if (r < D) {
                 w_[u] = P.ldw(r, i, sb);
                 m_[u] = P.ldm(r, i, sb);
-                v_[u] = P.ldv_opt(r, i, sb, L.sgd);
+                v_[u] = P.template ldv_opt<OPT>(r, i, sb);
                 g_[u] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
             }
         }
@@ -237,8 +242,9 @@ __device__ __forceinline__ void adam_rows(const Planes<T> &P, int D, int64_t i, 
         for (int u = 0; u < UNROLL; u++) {
             int r = r0 + u;
             if (r < D) {
-                adam_value(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
-                P.store(r, i, sb, w_[u], m_[u], v_[u], L, L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)r) : 0u);
+                adam_value<OPT>(w_[u], m_[u], v_[u], g_[u], d, lr_group(r), L);
+                P.template store<OPT>(r, i, sb, w_[u], m_[u], v_[u], L,
+                                      L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)r) : 0u);
             }
         }
     }
@@ -257,11 +263,11 @@ template <typename IX> struct AdamRows {
     int d;
 };
 
-template <typename T, typename IX>
+template <int OPT, typename T, typename IX>
 __device__ __forceinline__ void adam_fetch(AdamRows<IX> &a, int u, const int32_t *__restrict__ uids,
                                            const uint8_t *__restrict__ udelay, const uint32_t *__restrict__ vmask,
                                            const uint32_t *__restrict__ vprefix, const Planes<T, IX> &P,
-                                           const float *__restrict__ grad, int64_t gcap, int D, int r0, bool sgd)
+                                           const float *__restrict__ grad, int64_t gcap, int D, int r0)
 {
     a.i = (IX)uids[u];
     a.sb = P.shbase(a.i);
@@ -274,13 +280,13 @@ __device__ __forceinline__ void adam_fetch(AdamRows<IX> &a, int u, const int32_t
         if (r < D) {
             a.w[j] = P.ldw(r, a.i, a.sb);
             a.m[j] = P.ldm(r, a.i, a.sb);
-            a.v[j] = P.ldv_opt(r, a.i, a.sb, sgd);
+            a.v[j] = P.template ldv_opt<OPT>(r, a.i, a.sb);
             a.g[j] = k >= 0 ? __ldg(grad + r * gcap + k) : 0.f;
         }
     }
 }
 
-template <typename T, typename IX>
+template <typename T, typename IX, int OPT>
 __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T, IX> P, int D, const int32_t *__restrict__ uids,
                                                            const uint8_t *__restrict__ udelay, const int *u_range,
                                                            const int *n_upd_p,
@@ -301,19 +307,18 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply(Planes<T, IX> P, i
 #pragma unroll
     for (int j = 0; j < RG; j++) key[j] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + j)) : 0u;
     AdamRows<IX> cur, nxt;
-    const bool sgd = L.sgd != 0;
-    adam_fetch(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0, sgd);
+    adam_fetch<OPT>(cur, u, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
     while (true) {
         const int un = u + stride;
         const bool more = un < n_upd;
-        if (more) adam_fetch(nxt, un, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0, sgd);
+        if (more) adam_fetch<OPT>(nxt, un, uids, udelay, vmask, vprefix, P, grad, gcap, D, r0);
 #pragma unroll
         for (int j = 0; j < RG; j++) {
             const int r = r0 + j;
             if (r < D) {
                 float w_ = cur.w[j], m_ = cur.m[j], v_ = cur.v[j];
-                adam_value(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
-                P.store(r, cur.i, cur.sb, w_, m_, v_, L, key[j]);
+                adam_value<OPT>(w_, m_, v_, cur.g[j], cur.d, lr_group(r), L);
+                P.template store<OPT>(r, cur.i, cur.sb, w_, m_, v_, L, key[j]);
             }
         }
         if (!more) break;
@@ -399,23 +404,26 @@ void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t 
     const int groups = (sc.D + RG - 1) / RG;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
     const bool u32 = offsets_fit_u32(sc);
-    if (sc.prec == GS_FP32) {
-        if (u32)
-            k_adam_apply<float, uint32_t><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float, uint32_t>(sc), sc.D, uids, udelay,
-                                                                      u_range, n_upd, vmask, vprefix, grad, gcap, args);
-        else
-            k_adam_apply<float, int64_t><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float, int64_t>(sc), sc.D, uids, udelay,
-                                                                     u_range, n_upd, vmask, vprefix, grad, gcap, args);
-    } else {
-        if (u32)
-            k_adam_apply<__nv_bfloat16, uint32_t><<<grid, ADAM_BLOCK, 0, s>>>(
-                planes_of<__nv_bfloat16, uint32_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap,
-                args);
-        else
-            k_adam_apply<__nv_bfloat16, int64_t><<<grid, ADAM_BLOCK, 0, s>>>(
-                planes_of<__nv_bfloat16, int64_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap,
-                args);
-    }
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        if (sc.prec == GS_FP32) {
+            if (u32)
+                k_adam_apply<float, uint32_t, O><<<grid, ADAM_BLOCK, 0, s>>>(
+                    planes_of<float, uint32_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap, args);
+            else
+                k_adam_apply<float, int64_t, O><<<grid, ADAM_BLOCK, 0, s>>>(
+                    planes_of<float, int64_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad, gcap, args);
+        } else {
+            if (u32)
+                k_adam_apply<__nv_bfloat16, uint32_t, O><<<grid, ADAM_BLOCK, 0, s>>>(
+                    planes_of<__nv_bfloat16, uint32_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad,
+                    gcap, args);
+            else
+                k_adam_apply<__nv_bfloat16, int64_t, O><<<grid, ADAM_BLOCK, 0, s>>>(
+                    planes_of<__nv_bfloat16, int64_t>(sc), sc.D, uids, udelay, u_range, n_upd, vmask, vprefix, grad,
+                    gcap, args);
+        }
+    });
 }
 
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
@@ -451,7 +459,7 @@ void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int6
 
 // Eager Adam (Eq. 1 for every Gaussian, every step): the baseline the
 // deferred update removes; counters are left alone.
-template <typename T>
+template <typename T, int OPT>
 __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(Planes<T> P, int64_t n, int D,
                                                            const uint32_t *__restrict__ vmask,
                                                            const uint32_t *__restrict__ vprefix,
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK) k_adam_eager(Planes<T> P, int64_t 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int k = compact_index(vmask, vprefix, i);
         if (k >= gcap) k = -1;
-        adam_rows<T>(P, D, i, k, grad, gcap, 0, L);
+        adam_rows<T, OPT>(P, D, i, k, grad, gcap, 0, L);
     }
 }
 
@@ -471,27 +479,28 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s)
 {
     w.mark(TP_APPLY0, s);
-    if (sc.prec == GS_FP32)
-        k_adam_eager<float><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.n, sc.D, vmask,
-                                                                          vprefix, grad, gcap, args);
-    else
-        k_adam_eager<__nv_bfloat16><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.n,
-                                                                                  sc.D, vmask, vprefix, grad, gcap,
-                                                                                  args);
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        if (sc.prec == GS_FP32)
+            k_adam_eager<float, O><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.n, sc.D,
+                                                                                 vmask, vprefix, grad, gcap, args);
+        else
+            k_adam_eager<__nv_bfloat16, O><<<w.grid(sc.n, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(
+                planes_of<__nv_bfloat16>(sc), sc.n, sc.D, vmask, vprefix, grad, gcap, args);
+    });
     w.mark(TP_APPLY1, s);
 }
 
 // rdir = m / (sqrt(v) + eps) for every plane (momentum SGD: rdir = m).
-template <typename T>
+template <typename T, int OPT>
 __global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__restrict__ args)
 {
     const float eps = args->lut.eps;
-    const bool sgd = args->lut.sgd != 0;
     const int64_t total = (int64_t)D * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
         const int64_t i = e - (int64_t)r * n, sb = P.shbase(i);
-        const float dir = restore_dir(P.ldm(r, i, sb), P.ldv_opt(r, i, sb, sgd), eps, sgd);
+        const float dir = restore_dir<OPT>(P.ldm(r, i, sb), P.template ldv_opt<OPT>(r, i, sb), eps);
         if (r < N_GEO) P.rdir[r * P.pitch + i] = dir;
         else st_val(P.shr + (r - N_GEO) * P.sp + sb, dir, false, 0u);
     }
@@ -501,15 +510,18 @@ void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cuda
 {
     if (!sc.rdir) return;
     const int g = w.grid((int64_t)sc.D * sc.n, 256, 4);
-    if (sc.prec == GS_FP32)
-        k_refresh_rdir<float><<<g, 256, 0, s>>>(planes_of<float>(sc), sc.D, sc.n, args);
-    else
-        k_refresh_rdir<__nv_bfloat16><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, sc.n, args);
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        if (sc.prec == GS_FP32)
+            k_refresh_rdir<float, O><<<g, 256, 0, s>>>(planes_of<float>(sc), sc.D, sc.n, args);
+        else
+            k_refresh_rdir<__nv_bfloat16, O><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, sc.n, args);
+    });
 }
 
 // Catch-up without a step: m b1^c, v b2^c, decay[c] w - param_lut[c] m / (sqrt(v) + eps)
 // (momentum SGD: b mu^c, v unchanged, w - param_lut[c] b).
-template <typename T>
+template <typename T, int OPT>
 __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, int64_t n, int D,
                               const DevArgs *__restrict__ args, float *w_out, float *m_out, float *v_out)
 {
@@ -523,7 +535,7 @@ __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, 
             float w = P.ldw(r, i, sb);
             float mm = P.ldm(r, i, sb), vv = P.ldv(r, i, sb);
             const int g = lr_group(r);
-            if (w_out) w_out[r * pitch + i] = restore_param(w, mm, vv, L.param[g][d], L.decay[g][d], d, L.eps, L.sgd);
+            if (w_out) w_out[r * pitch + i] = restore_param<OPT>(w, mm, vv, L.param[g][d], L.decay[g][d], d, L.eps);
             if (m_out) m_out[r * pitch + i] = d ? L.mom[d - 1] * mm : mm;
             if (v_out) v_out[r * pitch + i] = d ? L.var[d - 1] * vv : vv;
         }
@@ -533,12 +545,15 @@ __global__ void k_materialize(Planes<T> P, const uint8_t *__restrict__ counter, 
 void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, float *m_out, float *v_out,
                         Work &w, cudaStream_t s)
 {
-    if (sc.prec == GS_FP32)
-        k_materialize<float><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<float>(sc), sc.counter, sc.n, sc.D, args, w_out,
-                                                             m_out, v_out);
-    else
-        k_materialize<__nv_bfloat16><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.counter, sc.n,
-                                                                     sc.D, args, w_out, m_out, v_out);
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        if (sc.prec == GS_FP32)
+            k_materialize<float, O><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<float>(sc), sc.counter, sc.n, sc.D, args,
+                                                                    w_out, m_out, v_out);
+        else
+            k_materialize<__nv_bfloat16, O><<<w.grid(sc.n, 256), 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.counter,
+                                                                             sc.n, sc.D, args, w_out, m_out, v_out);
+    });
 }
 
 __global__ void k_grad_scatter(const int32_t *__restrict__ ids, const int *n_dev, int cap,

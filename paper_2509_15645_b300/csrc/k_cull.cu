@@ -14,7 +14,7 @@ namespace gs {
 
 constexpr int CULL_BLOCK = 256;
 
-template <typename MT>
+template <typename MT, int OPT>
 __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict__ geo, const MT *__restrict__ m,
                                                      const MT *__restrict__ v, const float *__restrict__ rdir,
                                                      const uint8_t *__restrict__ counter,
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
     __shared__ CullCam s_cc;
     __shared__ float s_plut[3][LUT_N], s_dec[3][LUT_N];
     __shared__ float s_eps;
-    __shared__ int s_restore, s_sgd;
+    __shared__ int s_restore;
     __shared__ uint32_t s_cnt[CULL_BLOCK / 32];
     if (threadIdx.x < sizeof(DevCam) / 4)
         ((uint32_t *)&s_cam)[threadIdx.x] = ((const uint32_t *)&args->cam[view])[threadIdx.x];
@@ -37,7 +37,6 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
     }
     if (threadIdx.x == 0) {
         s_eps = args->lut.eps;
-        s_sgd = args->lut.sgd;
         s_restore = args->lut.restore && m != nullptr && v != nullptr && counter != nullptr;
     }
     __syncthreads();
@@ -62,7 +61,7 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                     const int d = counter[i];
 #pragma unroll
                     for (int r = 0; r < 10; r++)
-                        g[r] = restore_with_dir(g[r], dd[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d);
+                        g[r] = restore_with_dir<OPT>(g[r], dd[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d);
                 } else if (s_restore) {
                     // m, v loads are issued together with w, not after the counter arrives
                     float mm[10], vv[10];
@@ -74,8 +73,8 @@ __global__ void __launch_bounds__(CULL_BLOCK, 3) k_cull(const float *__restrict_
                     const int d = counter[i];
 #pragma unroll
                     for (int r = 0; r < 10; r++)
-                        g[r] = restore_param(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d, s_eps,
-                                             s_sgd);
+                        g[r] = restore_param<OPT>(g[r], mm[r], vv[r], s_plut[lr_group(r)][d], s_dec[lr_group(r)][d], d,
+                                                  s_eps);
                 }
                 if (maybe_visible(g, s_cc)) {
                     Proj P;
@@ -142,6 +141,7 @@ struct CullOut {
     int *n_cand;          // optional: number of Gaussians whose rotation planes were read
 };
 
+template <int OPT>
 __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
                                                    const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
                                                    const DevArgs *__restrict__ args, int view0, int nv,
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
 #pragma unroll
                     for (int r = 0; r < CPRE; r++)
                         if (live[e])
-                            g[e][r] = restore_with_dir(g[e][r], st[s].dir[r][k], s_plut[lr_group(r)][d[e]],
-                                                       s_dec[lr_group(r)][d[e]], d[e]);
+                            g[e][r] = restore_with_dir<OPT>(g[e][r], st[s].dir[r][k], s_plut[lr_group(r)][d[e]],
+                                                            s_dec[lr_group(r)][d[e]], d[e]);
                 }
             }
             for (int v = 0; v < nv; v++) {
@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ ge
                                 for (int r = CPRE; r < CPLANES; r++) dd[r - CPRE] = __ldg(rdir + r * pitch + i);
 #pragma unroll
                                 for (int r = CPRE; r < CPLANES; r++)
-                                    g[e][r] = restore_with_dir(g[e][r], dd[r - CPRE], s_plut[lr_group(r)][d[e]],
-                                                               s_dec[lr_group(r)][d[e]], d[e]);
+                                    g[e][r] = restore_with_dir<OPT>(g[e][r], dd[r - CPRE], s_plut[lr_group(r)][d[e]],
+                                                                    s_dec[lr_group(r)][d[e]], d[e]);
                             }
                             full[e] = true;
                             n_full++;
@@ -349,25 +349,35 @@ static bool cull_tma_ok(const SceneView &sc)
     return restore_dir_path && aligned;
 }
 
-static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0, int nv, const CullOut &out, Work &w,
-                            cudaStream_t s)
+template <int OPT>
+static void launch_cull_tma_t(const SceneView &sc, const DevArgs *args, int view0, int nv, const CullOut &out, Work &w,
+                              cudaStream_t s)
 {
     // the stages exceed the default dynamic shared-memory limit; the raised
-    // limit is a per-device setting, recorded per device
+    // limit is a per-device setting, recorded per device (and per instance)
     static std::atomic<uint64_t> attr_devices{0};
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(attr_devices.load() & bit)) {
-        cudaFuncSetAttribute(k_cull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
+        cudaFuncSetAttribute(k_cull_tma<OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
         attr_devices.fetch_or(bit);
     }
     const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics
     if (out.n_cand) cudaMemsetAsync(out.n_cand, 0, sizeof(int), s);
     const int gt = w.grid(nchunks * CT, CT, 4);
-    k_cull_tma<<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status,
-                                         w.cull_first_wait);
+    k_cull_tma<OPT><<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out,
+                                              w.status, w.cull_first_wait);
+}
+
+// The restore through stored directions differs between optimizers only by
+// AdamW's decay: Adam and momentum SGD share one instance.
+static void launch_cull_tma(const SceneView &sc, const DevArgs *args, int view0, int nv, const CullOut &out, Work &w,
+                            cudaStream_t s)
+{
+    if (sc.opt == GS_OPT_ADAMW) launch_cull_tma_t<GS_OPT_ADAMW>(sc, args, view0, nv, out, w, s);
+    else launch_cull_tma_t<GS_OPT_ADAM>(sc, args, view0, nv, out, w, s);
 }
 
 void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *mask, uint32_t *chunk_cnt, Work &w,
@@ -382,13 +392,18 @@ void launch_cull(const SceneView &sc, const DevArgs *args, int view, uint32_t *m
         out.mask[0] = mask;
         out.chunk[0] = chunk_cnt;
         launch_cull_tma(sc, args, view, 1, out, w, s);
-    } else if (sc.prec == GS_FP32)
-        k_cull<float><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const float *)sc.m, (const float *)sc.v, sc.rdir, sc.counter,
-                                               sc.pitch, sc.n, args, view, mask, chunk_cnt);
-    else
-        k_cull<__nv_bfloat16><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const __nv_bfloat16 *)sc.m, (const __nv_bfloat16 *)sc.v,
-                                                       sc.rdir, sc.counter, sc.pitch, sc.n, args, view, mask,
-                                                       chunk_cnt);
+    } else {
+        with_opt(sc.opt, [&](auto o) {
+            constexpr int OPT = decltype(o)::value;
+            if (sc.prec == GS_FP32)
+                k_cull<float, OPT><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const float *)sc.m, (const float *)sc.v, sc.rdir,
+                                                            sc.counter, sc.pitch, sc.n, args, view, mask, chunk_cnt);
+            else
+                k_cull<__nv_bfloat16, OPT><<<g, CULL_BLOCK, 0, s>>>(sc.geo, (const __nv_bfloat16 *)sc.m,
+                                                                    (const __nv_bfloat16 *)sc.v, sc.rdir, sc.counter,
+                                                                    sc.pitch, sc.n, args, view, mask, chunk_cnt);
+        });
+    }
     if (view == 0) w.mark(TP_CULL1, s);
 }
 

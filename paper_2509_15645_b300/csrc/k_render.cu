@@ -29,10 +29,10 @@ struct SLutR {
     float param[N_GROUPS][LUT_N];
     float decay[N_GROUPS][LUT_N];
     float eps;
-    int restore, sgd;
+    int restore;
 };
 
-template <int DEG, typename T>
+template <int DEG, typename T, int OPT>
 __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, const int32_t *__restrict__ ids,
                                                                const int *n_vis_p, int cap,
                                                                const DevArgs *__restrict__ args, int view,
@@ -56,7 +56,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
     if (threadIdx.x == 0) {
         L.eps = args->lut.eps;
         L.restore = args->lut.restore && sc.m && sc.v && sc.counter;
-        L.sgd = args->lut.sgd;
     }
     __syncthreads();
     const int n_vis = min(*n_vis_p, cap);
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
 #pragma unroll
                     for (int r = 0; r < D; r++) {
                         const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * sp + sb);
-                        w[r] = restore_with_dir(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
+                        w[r] = restore_with_dir<OPT>(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
                     }
                 } else if (sc.rdir) {
                     // host tier: geometry directions kept, SH directions recomputed from the staged m, v
@@ -97,12 +96,12 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
 #pragma unroll
                     for (int r = 0; r < D; r++) {
                         if (r < N_GEO) {
-                            w[r] = restore_with_dir(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d],
-                                                    L.decay[lr_group(r)][d], d);
+                            w[r] = restore_with_dir<OPT>(w[r], __ldg(sc.rdir + r * pitch + i), L.param[lr_group(r)][d],
+                                                         L.decay[lr_group(r)][d], d);
                         } else {
                             const float mm = ld_val(msh + (r - N_GEO) * sp + sb), vv = ld_val(vsh + (r - N_GEO) * sp + sb);
-                            w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d,
-                                                 L.eps, L.sgd);
+                            w[r] = restore_param<OPT>(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d,
+                                                      L.eps);
                         }
                     }
                 } else {
@@ -112,8 +111,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                     for (int r = 0; r < D; r++) {
                         const float mm = r < N_GEO ? ld_val(mp + r * pitch + i) : ld_val(msh + (r - N_GEO) * sp + sb);
                         const float vv = r < N_GEO ? ld_val(vp + r * pitch + i) : ld_val(vsh + (r - N_GEO) * sp + sb);
-                        w[r] = restore_param(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d, L.eps,
-                                             L.sgd);
+                        w[r] = restore_param<OPT>(w[r], mm, vv, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d,
+                                                  L.eps);
                     }
                 }
             }
@@ -895,11 +894,16 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
                   RenderBufs &rb, const DevCam &cam, Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
-    auto gp = sc.prec == GS_FP32
-                  ? (sc.deg == 3 ? k_gather_project<3, float> : sc.deg == 2 ? k_gather_project<2, float>
-                     : sc.deg == 1 ? k_gather_project<1, float> : k_gather_project<0, float>)
-                  : (sc.deg == 3 ? k_gather_project<3, __nv_bfloat16> : sc.deg == 2 ? k_gather_project<2, __nv_bfloat16>
-                     : sc.deg == 1 ? k_gather_project<1, __nv_bfloat16> : k_gather_project<0, __nv_bfloat16>);
+    decltype(&k_gather_project<0, float, GS_OPT_ADAM>) gp = nullptr;
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        gp = sc.prec == GS_FP32
+                 ? (sc.deg == 3 ? k_gather_project<3, float, O> : sc.deg == 2 ? k_gather_project<2, float, O>
+                    : sc.deg == 1 ? k_gather_project<1, float, O> : k_gather_project<0, float, O>)
+                 : (sc.deg == 3 ? k_gather_project<3, __nv_bfloat16, O>
+                    : sc.deg == 2 ? k_gather_project<2, __nv_bfloat16, O>
+                    : sc.deg == 1 ? k_gather_project<1, __nv_bfloat16, O> : k_gather_project<0, __nv_bfloat16, O>);
+    });
     const int tiles = cam.tiles_x * cam.tiles_y;
     cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
     cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);

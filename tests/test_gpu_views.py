@@ -143,8 +143,6 @@ def test_restore_over_changing_views(gs, orc, bf16, opt):
         # cull + render + backward with the restore of the coming step
         ids, nv = ctx.cull(scene, cam, adam)
         img = ctx.render_fwd(scene, cam, ids, nv, adam)
-        gc = ctx.render_bwd(torch.as_tensor(rr["dimage"], dtype=torch.float32, device="cuda"), scene.D)
-        full = ctx.grad_scatter(scene, ids, nv, gc)
         ctx.sync_status()
         gids = ids[:int(nv.item())].cpu().numpy()
         sp = rr["splats"]
@@ -155,12 +153,19 @@ def test_restore_over_changing_views(gs, orc, bf16, opt):
         ok = ~ex[None].repeat(3, 0)
         ierr = np.abs(img.cpu().numpy().astype(np.float64) - rr["image"])
         assert ierr[ok].max() <= 1e-5, (t, ierr[ok].max())
+        # gradients with the tie pixels weighted 0 on both sides (a decision at
+        # FP32 resolution there may go either way and move whole gradients)
+        dimg = rr["dimage"] * ok
+        g_ref, _ = orc.backward(Wcur, DEG, rr["cam"], sp, rr["key_gid"], rr["ranges"], dimg)
+        gc = ctx.render_bwd(torch.as_tensor(dimg, dtype=torch.float32, device="cuda"), scene.D)
+        full = ctx.grad_scatter(scene, ids, nv, gc)
+        ctx.sync_status()
         g_gpu = full[:, :N].cpu().numpy().astype(np.float64)
-        errs = {g: rel_group_error(g_gpu, rr["grad"], s) for g, s in GROUPS.items()}
-        assert max(errs.values()) <= 1e-4, (t, errs)
+        errs = {g: rel_group_error(g_gpu, g_ref, s) for g, s in GROUPS.items()}
+        assert max(errs.values()) <= 1e-4, (t, errs, int(ex.sum()))
         d = Cn[gids]
         delays.append(d)
-        if t > 1:
+        if t > 1 and ORDER[t - 2] != k:
             assert np.mean(d > 0) > 0.1, (t, np.mean(d > 0))
         # the whole step (graph) from the same state
         loss = ctx.step(scene, [cam], [tg[k]], adam)
@@ -202,7 +207,7 @@ def test_host_tier_over_changing_views(gs, orc, prec_name):
         sp = rr["splats"]
         diff = np.setxor1d(gids, np.nonzero(sp["keep"])[0])
         assert np.all(sp["margin"][diff] < TIE_TOL), t
-        if t > 1:
+        if t > 1 and ORDER[t - 2] != k:
             assert np.mean(Cn[gids] > 0) > 0.1
         saw_bound |= bool(np.any(Cn == 5))
         loss = ctx.step(scene, [cams[k]], [tg[k]], adam)
