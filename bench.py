@@ -63,8 +63,8 @@ def job_rate(world, steps, ms):
 
 class ClockSampler:
     """SM clocks and throttle reasons sampled during the timed region: NVML
-    polled every ~2 ms from a thread (a timed region of a few tens of ms still
-    gets samples), else nvidia-smi every 100 ms."""
+    (libnvidia-ml through ctypes) polled every ~2 ms from a thread, so a timed
+    region of a few tens of ms still gets samples; else nvidia-smi every 100 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -77,35 +77,47 @@ class ClockSampler:
         self.samples = []
         self.nvml_error = None
 
-    def _nvml_handle(self):
-        import pynvml
-        pynvml.nvmlInit()
-        if self.pci:
-            try:
-                return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(self.pci)
-            except Exception:
-                pass
-        return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
+    # clock event reason bits of the public NVML API (nvmlClocksEventReason*)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def _nvml(self):
+        """(sm_mhz(), reasons(), max_mhz) from libnvidia-ml through ctypes."""
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = C.c_void_p()
+        if not (self.pci and lib.nvmlDeviceGetHandleByPciBusId_v2(self.pci.encode(), C.byref(h)) == 0):
+            if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        getr = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, C.c_int(1), C.byref(mx))      # 1 = NVML_CLOCK_SM
+
+        def sm_mhz():
+            v = C.c_uint(0)
+            return v.value if lib.nvmlDeviceGetClockInfo(h, C.c_int(1), C.byref(v)) == 0 else None
+
+        def reasons():
+            r = C.c_ulonglong(0)
+            if getr(h, C.byref(r)) != 0:
+                return []
+            return [k for k, b in self.REASON_BITS.items() if r.value & b]
+
+        return sm_mhz, reasons, mx.value
 
     def start(self):
         import threading
         try:
-            nv, h = self._nvml_handle()
-            bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
-                    "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
-                    "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
-                    "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
-            self.smax = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            sm_mhz, reasons, self.smax = self._nvml()
             self.stop_flag = threading.Event()
 
             def loop():
                 while not self.stop_flag.is_set():
-                    try:
-                        mhz = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                        r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                        self.samples.append((mhz, [k for k, b in bits.items() if r & b]))
-                    except Exception:
-                        pass
+                    mhz = sm_mhz()
+                    if mhz:
+                        self.samples.append((mhz, reasons()))
                     time.sleep(0.002)
 
             self.thread = threading.Thread(target=loop, daemon=True)
@@ -609,6 +621,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- image splitting (§4.4)
+
+def run_split_demo(args):
+    """Balance-aware image splitting (§4.4) on a view that crosses mem_limit:
+    1M Gaussians on the 200 x 200 m heightfield, one 1920x1080 view from 100 m
+    altitude, 80 m off-centre, looking at the origin (about 42% of the
+    Gaussians visible).  Three contexts, each sized to the counts it must hold
+    (measured first, +10%): the view whole; its two regions (gs_split_point,
+    5 rounds) rendered one after the other through one set of render buffers
+    (render_views = 1); the two regions rendered together (render_views = 2).
+    Reports each one's workspace, the peak device memory of its steps (torch's
+    allocator: scene state + workspace + targets), and its step time (CUDA
+    events over --steps steps of the same view)."""
+    import torch
+    import paper_2509_15645_b300 as gs
+    from synth import scenes
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, deg, W, H = 1_000_000, 3, 1920, 1080
+    P = scenes.heightfield_scene(n, seed=0)
+    T = scenes.heightfield_scene(n, seed=1)
+    cam = scenes.camera_lookat((80.0, 0.0, 100.0), (0.0, 0.0, 0.0), W, H, 60.0)
+    adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+    big = dict(max_gaussians=n, max_visible=n, max_keys=60_000_000, max_width=W, max_height=H, tile=(8, 4),
+               max_sh_degree=deg)
+    # target and the counts that size the contexts
+    probe = gs.Context(**big, max_views=2)
+    ts = gs.GaussianScene(T, deg, with_optimizer=False)
+    ids, nv = probe.cull(ts, cam)
+    target = probe.render_fwd(ts, cam, ids, nv).clone()
+    del ts
+    sc = gs.GaussianScene(P, deg)
+    frac = None
+    ids, nv = probe.cull(sc, cam)
+    probe.render_fwd(sc, cam, ids, nv)
+    probe.sync_status()
+    n_vis, n_keys = int(nv.item()), int(probe.counters()[1].item())
+    frac = n_vis / n
+    regions = probe.plan_split(sc, cam, adam, mem_limit=0.3)
+    assert regions is not None, "the view does not cross mem_limit"
+    reg_counts = []
+    for r in regions:
+        ids, nv = probe.cull(sc, r)
+        probe.render_fwd(sc, r, ids, nv)
+        probe.sync_status()
+        reg_counts.append((int(nv.item()), int(probe.counters()[1].item())))
+    del probe
+    torch.cuda.empty_cache()
+    res = {}
+    for name, views, rv, vis, keys in (
+            ("whole_view", 1, 0, n_vis, n_keys),
+            ("split_sequential", 2, 1, max(c[0] for c in reg_counts), max(c[1] for c in reg_counts)),
+            ("split_together", 2, 2, max(c[0] for c in reg_counts), max(c[1] for c in reg_counts))):
+        kw = dict(big, max_visible=int(vis * 1.1) + 1024, max_keys=int(keys * 1.1) + 4096)
+        ws = gs.Context.workspace_bytes(**kw, max_views=views, render_views=rv)
+        sc = gs.GaussianScene(P, deg)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        ctx = gs.Context(**kw, max_views=views, render_views=rv)
+        cams = [cam] if views == 1 else regions
+        tg = [target] if views == 1 else [r.crop(target) for r in regions]
+        loss = torch.zeros(1, device=dev)
+        for _ in range(args.warmup):
+            ctx.step(sc, cams, tg, adam, loss=loss)
+        ctx.sync_status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            ctx.step(sc, cams, tg, adam, loss=loss)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        res[name] = {"workspace_gb": round(ws / 1e9, 3), "peak_device_gb": round(torch.cuda.max_memory_allocated() / 1e9, 3),
+                     "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 4), "capacity_visible": kw["max_visible"],
+                     "capacity_keys": kw["max_keys"], "loss": round(loss.item(), 6)}
+        del ctx, sc
+        torch.cuda.empty_cache()
+    out = {"metric": "image splitting: peak device memory and step time, split vs whole view", "unit": "GB, ms",
+           "workload": "heightfield1m_1080p_sh3, view from 100 m altitude, 80 m off-centre", "gaussians": n,
+           "visible_fraction": round(frac, 4), "mem_limit": 0.3,
+           "split": {"axis": "x" if regions[0].height == H else "y",
+                     "at_px": regions[1].x0 if regions[0].height == H else regions[1].y0,
+                     "regions_visible_keys": reg_counts},
+           "results": res, "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------------------- oracle (CPU)
 
 def _oracle_step(orc, P, deg, cam, target, W_, M_, V_, C_, t, hp):
@@ -760,12 +859,16 @@ def main():
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
     ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
+    ap.add_argument("--split-demo", action="store_true",
+                    help="measure balance-aware image splitting (§4.4) on a 1M-Gaussian view that crosses mem_limit")
     ap.add_argument("--oracle-workloads", action="store_true",
                     help="with --impl reference: time the FP64 oracle on every workload, 1 thread and all cores")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference" and args.oracle_workloads:
+    if args.split_demo:
+        run_split_demo(args)
+    elif args.impl == "reference" and args.oracle_workloads:
         run_oracle_workloads(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -185,6 +185,11 @@ typedef struct {
     int64_t stage_chunks;    /* staging ring of host-tier scenes, in chunks (0: no host tier) */
     int32_t chunk_shift;     /* log2 Gaussians per chunk, 10..20 (0: 11) */
     int32_t stage_elem_bytes;/* element size of the staged SH rows: 4 (0: 4) serves every form, 2 only the bf16 forms */
+    int32_t render_views;    /* views whose render buffers (splats, tile lists, images) exist at once, 1..max_views
+                                (0: max_views).  gs_step renders its views in rounds of this many through the same
+                                buffers, gradients summed over the rounds, so the working set is bounded by one
+                                round (a view split into regions, §4.4, with render_views = 1 holds one region's
+                                buffers at a time); the cull buffers (masks, ids) are kept for max_views views */
 } gs_config;
 
 /* ------------------------------------------------------------------ context */

@@ -124,9 +124,12 @@ void launch_ids_to_mask(const int32_t *ids, const int *n_dev, int cap, uint32_t 
 void launch_mask_or(uint32_t *dst, const uint32_t *src, int64_t nwords, Work &w, cudaStream_t s);
 
 // k_adam.cu
+struct PairBufs;
+// Select, then the pair-wise apply when pb is given and the scene allows it,
+// else the member-wise compaction and apply.
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                           const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
-                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s);
+                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s, const PairBufs *pb = nullptr);
 void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, Work &w, cudaStream_t s);
 void launch_adam_select(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, uint32_t *umask,
@@ -136,6 +139,21 @@ void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t 
                        const int *u_range, const int *n_upd, Work &w, cudaStream_t s);
 void launch_adam_compact(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, int32_t *uids, uint8_t *udelay,
                          int *n_upd, Work &w, cudaStream_t s);
+// The pair-wise apply (resident scenes): update set taken as Gaussian pairs.
+struct PairBufs {
+    uint32_t *pmask;      // [n/64 + CHUNK_WORDS] pairs with a member
+    uint32_t *pchunk;     // [n/4096 + 1] per-chunk counts
+    int32_t *pids;        // [n/2 + 1] active pairs, ascending
+    uint32_t *pinfo;      // [n/2 + 1] delays and member bits of each
+    int *n_pairs;         // device count
+};
+bool adam_pairs_ok(const SceneView &sc);
+// After the select (update-set mask and per-chunk member counts): the member
+// count to n_upd, the active pairs, their delays (members' counters cleared)
+// and the apply.
+void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb,
+                       int *n_upd, Work &w, cudaStream_t s);
 void launch_touch_from_masks(const uint32_t *vmask, const uint32_t *umask, int64_t n, int shift, uint8_t *touch,
                              Work &w, cudaStream_t s);
 void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s);
@@ -203,6 +221,7 @@ struct RasterJob {
     float *dimage[MAX_VIEWS];    // forward: dL/dimage out (with targets); backward: read
     float *g9[MAX_VIEWS];        // backward: per-splat sums out
     uint32_t cap[MAX_VIEWS];     // visible capacity (list entries index records below it)
+    int cam0;                    // job view v is camera cam0 + v of the argument block
     int *work;
 };
 
@@ -224,11 +243,14 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 // backward rasterizer launch over all views; per view project_backward.
 void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
                   RenderBufs &rb, const DevCam &cam_host, Work &w, cudaStream_t s);
+// cam0: the job's views are cameras cam0.. of the argument block (a round of
+// a step's views); rbs, images, dimages and n_vis are per job view.
 void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
-                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s);
+                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s,
+                    int cam0 = 0);
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
-                     unsigned long long *stats = nullptr);
+                     unsigned long long *stats = nullptr, int cam0 = 0);
 void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                       float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
                       const int32_t *ids, bool accumulate, Work &w, cudaStream_t s);

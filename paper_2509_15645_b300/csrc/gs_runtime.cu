@@ -60,6 +60,7 @@ struct gs_ctx {
     int32_t *uids = nullptr;
     uint8_t *udelay = nullptr;
     uint32_t *amask = nullptr, *aprefix = nullptr, *achunk = nullptr;
+    PairBufs pairs{};                   // the pair-wise optimizer apply
     uint32_t *vmask[MAX_VIEWS] = {nullptr};
     uint32_t *vchunk[MAX_VIEWS] = {nullptr};
     uint32_t *vprefix[MAX_VIEWS] = {nullptr};
@@ -158,10 +159,14 @@ static bool valid_cfg(const gs_config *c)
            c->max_views >= 1 && c->max_views <= MAX_VIEWS && c->max_sh_degree >= 0 && c->max_sh_degree <= 3 &&
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h && c->stage_chunks >= 0 &&
            (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20)) &&
-           (c->stage_elem_bytes == 0 || c->stage_elem_bytes == 2 || c->stage_elem_bytes == 4);
+           (c->stage_elem_bytes == 0 || c->stage_elem_bytes == 2 || c->stage_elem_bytes == 4) &&
+           c->render_views >= 0 && c->render_views <= c->max_views;
 }
 
 static int stage_eb(const gs_config &g) { return g.stage_elem_bytes ? g.stage_elem_bytes : 4; }
+
+// Views rendered at once by gs_step (sets of render buffers).
+static int render_slots(const gs_config &g) { return g.render_views ? g.render_views : g.max_views; }
 
 static void carve(gs_ctx *c, char *base)
 {
@@ -186,6 +191,11 @@ static void carve(gs_ctx *c, char *base)
     c->uchunk = k.take<uint32_t>(NC);
     c->uids = k.take<int32_t>(N);
     c->udelay = k.take<uint8_t>(N);
+    c->pairs.pmask = k.take<uint32_t>(NW / 2 + CHUNK_WORDS);
+    c->pairs.pchunk = k.take<uint32_t>(NC / 2 + 2);
+    c->pairs.pids = k.take<int32_t>(N / 2 + 1);
+    c->pairs.pinfo = k.take<uint32_t>(N / 2 + 1);
+    c->pairs.n_pairs = k.take<int>(1);
     c->amask = k.take<uint32_t>(NW);
     c->aprefix = k.take<uint32_t>(NW);
     c->achunk = k.take<uint32_t>(NC);
@@ -200,8 +210,8 @@ static void carve(gs_ctx *c, char *base)
         c->union_prefix = k.take<uint32_t>(NW);
         c->union_chunk = k.take<uint32_t>(NC);
     }
-    // render buffers of each view a step may hold at once
-    for (int v = 0; v < g.max_views; v++) {
+    // render buffers of each view a step renders at once (a round)
+    for (int v = 0; v < render_slots(g); v++) {
         RenderBufs &rb = c->rbs[v];
         rb.cap = V;
         rb.kcap = K;
@@ -731,7 +741,7 @@ gs_status gs_adam_deferred(gs_ctx *c, gs_scene *scene, const int32_t *ids, const
     compact_mask(c->amask, sv.n, c->achunk, false, nullptr, c->aprefix, (int)sv.n, c->n_tmp, c->w, s);
     if (adam->mode == GS_ADAM_DEFERRED)
         launch_adam_deferred(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->umask, c->uchunk,
-                             c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+                             c->uids, c->udelay, &c->cnt->n_upd, c->w, s, &c->pairs);
     else
         launch_adam_eager(sv, c->args + SLOT_ADAM, c->amask, c->aprefix, grad_compact, cap, c->w, s);
     st = cuda_check(c, "gs_adam_deferred");
@@ -1056,29 +1066,40 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
 }
 
 // Render, L1 loss and backward of every view; gradients summed per Gaussian.
-// Each view's lists are prepared on its own buffers; one forward and one
-// backward rasterizer launch then cover the tiles of all views.
+// Views are rendered in rounds of render_slots: each view of a round has its
+// lists prepared on the round's buffers; one forward and one backward
+// rasterizer launch cover the tiles of the round's views; the projection
+// backward of each adds its gradients into the union layout.  The next round
+// reuses the same buffers.  (The stage timing points cover the first round.)
 static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n_views, const StepMasks &M,
                                  float *loss, cudaStream_t s)
 {
     DevArgs *args = c->args + SLOT_STEP;
-    RenderBufs *rbs[MAX_VIEWS];
-    const int *nv[MAX_VIEWS];
-    const float *dimg_c[MAX_VIEWS];
-    for (int v = 0; v < n_views; v++) {
-        rbs[v] = &c->rbs[v];
-        nv[v] = c->nvis_view + v;
-        dimg_c[v] = c->dimgs[v];
+    const int R = render_slots(c->cfg);
+    for (int v0 = 0; v0 < n_views; v0 += R) {
+        const int k = n_views - v0 < R ? n_views - v0 : R;
+        RenderBufs *rbs[MAX_VIEWS];
+        const int *nv[MAX_VIEWS];
+        const float *dimg_c[MAX_VIEWS];
+        for (int j = 0; j < k; j++) {
+            rbs[j] = &c->rbs[j];
+            nv[j] = c->nvis_view + v0 + j;
+            dimg_c[j] = c->dimgs[j];
+        }
+        if (v0 == 0) c->w.mark(TP_FWD0, s);
+        for (int j = 0; j < k; j++)
+            prepare_view(sv, args, v0 + j, c->vids[v0 + j], c->nvis_view + v0 + j, c->rbs[j], a.cam[v0 + j], c->w, s);
+        raster_forward(args, k, rbs, a.cam + v0, c->imgs, true, c->dimgs, loss, c->work, c->w, s, v0);
+        if (v0 == 0) {
+            c->w.mark(TP_FWD1, s);
+            c->w.mark(TP_BWD0, s);
+        }
+        raster_backward(args, k, rbs, a.cam + v0, dimg_c, nv, c->work + 1, c->w, s, nullptr, v0);
+        for (int j = 0; j < k; j++)
+            project_backward(sv, args, v0 + j, c->nvis_view + v0 + j, c->rbs[j], c->grad_u, M.gcap,
+                             n_views > 1 ? M.gmask : nullptr, n_views > 1 ? M.gprefix : nullptr, c->vids[v0 + j],
+                             n_views > 1, c->w, s);
     }
-    c->w.mark(TP_FWD0, s);
-    for (int v = 0; v < n_views; v++) prepare_view(sv, args, v, c->vids[v], c->nvis_view + v, c->rbs[v], a.cam[v], c->w, s);
-    raster_forward(args, n_views, rbs, a.cam, c->imgs, true, c->dimgs, loss, c->work, c->w, s);
-    c->w.mark(TP_FWD1, s);
-    c->w.mark(TP_BWD0, s);
-    raster_backward(args, n_views, rbs, a.cam, dimg_c, nv, c->work + 1, c->w, s);
-    for (int v = 0; v < n_views; v++)
-        project_backward(sv, args, v, c->nvis_view + v, c->rbs[v], c->grad_u, M.gcap, n_views > 1 ? M.gmask : nullptr,
-                         n_views > 1 ? M.gprefix : nullptr, c->vids[v], n_views > 1, c->w, s);
     c->w.mark(TP_BWD1, s);
 }
 
@@ -1086,7 +1107,10 @@ static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const S
 {
     DevArgs *args = c->args + SLOT_STEP;
     c->w.mark(TP_ADAM0, s);
-    if (mode == GS_ADAM_DEFERRED && M.selected) {
+    if (mode == GS_ADAM_DEFERRED && M.selected && adam_pairs_ok(sv)) {
+        launch_adam_pairs(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->umask, c->uchunk, c->pairs,
+                          &c->cnt->n_upd, c->w, s);
+    } else if (mode == GS_ADAM_DEFERRED && M.selected) {
         launch_adam_compact(sv, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
         c->w.mark(TP_APPLY0, s);
         launch_adam_apply(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->uids, c->udelay, nullptr,
@@ -1094,7 +1118,7 @@ static void enqueue_adam_phase(gs_ctx *c, const SceneView &sv, int mode, const S
         c->w.mark(TP_APPLY1, s);
     } else if (mode == GS_ADAM_DEFERRED)
         launch_adam_deferred(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->umask, c->uchunk, c->uids, c->udelay,
-                             &c->cnt->n_upd, c->w, s);
+                             &c->cnt->n_upd, c->w, s, &c->pairs);
     else
         launch_adam_eager(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->w, s);
     c->w.mark(TP_ADAM1, s);

@@ -428,11 +428,291 @@ void launch_adam_apply(const SceneView &sc, const DevArgs *args, const uint32_t 
 
 void launch_adam_deferred(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                           const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, int32_t *uids,
-                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s)
+                          uint8_t *udelay, int *n_upd, Work &w, cudaStream_t s, const PairBufs *pb)
 {
+    if (pb && adam_pairs_ok(sc)) {
+        int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
+        k_adam_select<<<w.grid(nchunks * ADAM_BLOCK, ADAM_BLOCK), ADAM_BLOCK, 0, s>>>(sc.counter, vmask, sc.n, args,
+                                                                                    umask, uchunk);
+        launch_adam_pairs(sc, args, vmask, vprefix, grad, gcap, umask, uchunk, *pb, n_upd, w, s);
+        return;
+    }
     launch_adam_select(sc, args, vmask, umask, uchunk, uids, udelay, n_upd, w, s);
     w.mark(TP_APPLY0, s);
     launch_adam_apply(sc, args, vmask, vprefix, grad, gcap, uids, udelay, nullptr, n_upd, w, s);
+    w.mark(TP_APPLY1, s);
+}
+
+// ---------------------------------------------------------------------------
+// The apply over Gaussian pairs (resident scenes).  The update set is taken as
+// pairs (2p, 2p + 1) with at least one member: a thread moves both Gaussians of
+// a pair with one 8-byte (fp32) or 4-byte (bf16) access per array and plane,
+// twice the bytes per instruction of the member-wise apply (Morton order keeps
+// most members in runs, so most pairs are whole).  Each block handles one
+// group of PR planes that are all geometry planes or all SH planes, so the
+// per-plane code has no branch on the plane's kind.  The arithmetic of each
+// member is the member-wise apply's, operation for operation (same results);
+// a non-member of a pair is not written.
+
+// Pair mask from the update-set mask: bit p of word w is bit 2p | bit 2p + 1.
+__device__ __forceinline__ uint32_t pair_bits16(uint32_t u)
+{
+    uint32_t x = (u | (u >> 1)) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    return (x | (x >> 8)) & 0x0000ffffu;
+}
+
+__global__ void k_pair_mask(const uint32_t *__restrict__ umask, int64_t nwords_u, uint32_t *__restrict__ pmask,
+                            int64_t nwords_p)
+{
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords_p; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u0 = 2 * w < nwords_u ? umask[2 * w] : 0u, u1 = 2 * w + 1 < nwords_u ? umask[2 * w + 1] : 0u;
+        pmask[w] = pair_bits16(u0) | (pair_bits16(u1) << 16);
+    }
+}
+
+// Per active pair: both delays and the member bits (d0 | d1 << 8 | members << 16);
+// the members' counters are cleared (the compaction's job in the member path).
+__global__ void k_pair_prep(const int32_t *__restrict__ pids, const int *n_pairs_p, const uint32_t *__restrict__ umask,
+                            uint8_t *__restrict__ counter, int64_t n, uint32_t *__restrict__ pinfo)
+{
+    const int np = *n_pairs_p;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+        const int64_t i0 = 2 * (int64_t)pids[j];
+        const bool has1 = i0 + 1 < n;
+        uint32_t bits = (umask[i0 >> 5] >> (i0 & 31)) & (has1 ? 3u : 1u);
+        const uint32_t c0 = counter[i0], c1 = has1 ? counter[i0 + 1] : 0u;
+        if (bits & 1u) counter[i0] = 0;
+        if (bits & 2u) counter[i0 + 1] = 0;
+        pinfo[j] = c0 | (c1 << 8) | (bits << 16);
+    }
+}
+
+// Two consecutive elements of a plane: loads widen to fp32, stores round per
+// the storage (stochastically with the member-wise apply's bits for bf16).
+__device__ __forceinline__ void ld2(const float *p, float &a, float &b)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld2(const __nv_bfloat16 *p, float &a, float &b)
+{
+    const uint32_t u = *reinterpret_cast<const uint32_t *>(p);
+    a = __uint_as_float(u << 16);
+    b = __uint_as_float(u & 0xffff0000u);
+}
+
+// Rounded representation of x in T: returns the bits and the value as stored.
+__device__ __forceinline__ uint32_t rnd_bits(float x, float &stored, const float *, bool, uint32_t)
+{
+    stored = x;
+    return __float_as_uint(x);
+}
+__device__ __forceinline__ uint32_t rnd_bits(float x, float &stored, const __nv_bfloat16 *, bool stochastic, uint32_t rnd)
+{
+    uint32_t u = __float_as_uint(x);
+    uint16_t b;
+    if (!stochastic || (u & 0x7f800000u) == 0x7f800000u) {
+        b = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    } else {
+        u += rnd & 0xffffu;
+        b = (uint16_t)(u >> 16);
+    }
+    stored = __uint_as_float((uint32_t)b << 16);
+    return b;
+}
+
+// Store the pair's elements whose bit is set in `sel` (bits a, b as from rnd_bits).
+__device__ __forceinline__ void st2(float *p, uint32_t a, uint32_t b, uint32_t sel)
+{
+    if (sel == 3u) *reinterpret_cast<float2 *>(p) = make_float2(__uint_as_float(a), __uint_as_float(b));
+    else if (sel == 1u) p[0] = __uint_as_float(a);
+    else if (sel == 2u) p[1] = __uint_as_float(b);
+}
+__device__ __forceinline__ void st2(__nv_bfloat16 *p, uint32_t a, uint32_t b, uint32_t sel)
+{
+    if (sel == 3u) *reinterpret_cast<uint32_t *>(p) = a | (b << 16);
+    else if (sel == 1u) p[0] = __ushort_as_bfloat16((unsigned short)a);
+    else if (sel == 2u) p[1] = __ushort_as_bfloat16((unsigned short)b);
+}
+
+constexpr int PR = 2;      // planes per thread in the pair apply
+
+struct PairRows {
+    float w[PR][2], m[PR][2], v[PR][2], g[PR][2];
+    int64_t i0;
+    uint32_t info;
+};
+
+// Planes [r0, r0 + PR) of one kind: geometry (w fp32 at geo, m, v of type T,
+// directions fp32) or SH (all of type T).
+template <typename T, bool GEO, int OPT>
+__device__ __forceinline__ void pair_fetch(PairRows &a, int j, const int32_t *__restrict__ pids,
+                                           const uint32_t *__restrict__ pinfo, const Planes<T> &P,
+                                           const uint32_t *__restrict__ vmask, const uint32_t *__restrict__ vprefix,
+                                           const float *__restrict__ grad, int64_t gcap, int r0, int rend)
+{
+    a.i0 = 2 * (int64_t)pids[j];
+    a.info = pinfo[j];
+    int k0 = (a.info & (1u << 16)) ? compact_index(vmask, vprefix, a.i0) : -1;
+    int k1 = (a.info & (2u << 16)) ? compact_index(vmask, vprefix, a.i0 + 1) : -1;
+    if (k0 >= gcap) k0 = -1;
+    if (k1 >= gcap) k1 = -1;
+#pragma unroll
+    for (int q = 0; q < PR; q++) {
+        const int r = r0 + q;
+        if (r < rend) {
+            if (GEO) {
+                ld2(P.geo + (int64_t)r * P.pitch + a.i0, a.w[q][0], a.w[q][1]);
+                ld2(P.m + (int64_t)r * P.pitch + a.i0, a.m[q][0], a.m[q][1]);
+                if (OPT != GS_OPT_SGDM) ld2(P.v + (int64_t)r * P.pitch + a.i0, a.v[q][0], a.v[q][1]);
+            } else {
+                const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
+                ld2(P.shw + o, a.w[q][0], a.w[q][1]);
+                ld2(P.shm + o, a.m[q][0], a.m[q][1]);
+                if (OPT != GS_OPT_SGDM) ld2(P.shv + o, a.v[q][0], a.v[q][1]);
+            }
+            if (OPT == GS_OPT_SGDM) a.v[q][0] = a.v[q][1] = 0.f;
+            a.g[q][0] = k0 >= 0 ? __ldg(grad + (int64_t)r * gcap + k0) : 0.f;
+            a.g[q][1] = k1 >= 0 ? __ldg(grad + (int64_t)r * gcap + k1) : 0.f;
+        }
+    }
+}
+
+template <typename T, bool GEO, int OPT>
+__device__ __forceinline__ void pair_step(const PairRows &a, const Planes<T> &P, int r0, int rend, const SLut &L,
+                                          const uint32_t *key)
+{
+    const uint32_t sel = (a.info >> 16) & 3u;
+    const int dd[2] = {(int)(a.info & 255u), (int)((a.info >> 8) & 255u)};
+    const bool st = L.stochastic != 0;
+#pragma unroll
+    for (int q = 0; q < PR; q++) {
+        const int r = r0 + q;
+        if (r >= rend) continue;
+        const int grp = lr_group(r);
+        uint32_t bw[2], bm[2], bv[2], bd[2];
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            float w = a.w[q][e], m = a.m[q][e], v = a.v[q][e];
+            bw[e] = bm[e] = bv[e] = bd[e] = 0u;
+            if (!((sel >> e) & 1u)) continue;
+            adam_value<OPT>(w, m, v, a.g[q][e], dd[e], grp, L);
+            const uint32_t bits = st ? sr_bits(key[q], (uint32_t)(a.i0 + e)) : 0u;
+            float ms, vs, ws;
+            if (GEO) {
+                bm[e] = rnd_bits(m, ms, P.m, st, bits);
+                bv[e] = OPT == GS_OPT_SGDM ? 0u : rnd_bits(v, vs, P.v, st, bits >> 16);
+                bw[e] = __float_as_uint(w);
+                bd[e] = __float_as_uint(restore_dir<OPT>(ms, OPT == GS_OPT_SGDM ? 0.f : vs, L.eps));
+            } else {
+                bm[e] = rnd_bits(m, ms, P.shm, st, bits);
+                bv[e] = OPT == GS_OPT_SGDM ? 0u : rnd_bits(v, vs, P.shv, st, bits >> 16);
+                bw[e] = rnd_bits(w, ws, P.shw, st, sr_w_bits(bits));
+                float dstored;
+                bd[e] = rnd_bits(restore_dir<OPT>(ms, OPT == GS_OPT_SGDM ? 0.f : vs, L.eps), dstored, P.shr, false, 0u);
+            }
+        }
+        if (GEO) {
+            const int64_t o = (int64_t)r * P.pitch + a.i0;
+            st2(P.geo + o, bw[0], bw[1], sel);
+            st2(P.m + o, bm[0], bm[1], sel);
+            if (OPT != GS_OPT_SGDM) st2(P.v + o, bv[0], bv[1], sel);
+            if (P.rdir) st2(P.rdir + o, bd[0], bd[1], sel);
+        } else {
+            const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
+            st2(P.shw + o, bw[0], bw[1], sel);
+            st2(P.shm + o, bm[0], bm[1], sel);
+            if (OPT != GS_OPT_SGDM) st2(P.shv + o, bv[0], bv[1], sel);
+            if (P.shr) st2(P.shr + o, bd[0], bd[1], sel);
+        }
+    }
+}
+
+// blockIdx.y: plane groups; the first n_geo_groups cover geometry planes
+// [PR y, PR y + PR) below 11, the rest SH planes 11 + PR (y - n_geo_groups) ...
+template <typename T, int OPT>
+__global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P, int D, const int32_t *__restrict__ pids,
+                                                                 const uint32_t *__restrict__ pinfo,
+                                                                 const int *n_pairs_p,
+                                                                 const uint32_t *__restrict__ vmask,
+                                                                 const uint32_t *__restrict__ vprefix,
+                                                                 const float *__restrict__ grad, int64_t gcap,
+                                                                 const DevArgs *__restrict__ args)
+{
+    __shared__ SLut L;
+    load_slut(L, args->lut);
+    const int n_pairs = *n_pairs_p;
+    constexpr int GEO_GROUPS = (N_GEO + PR - 1) / PR;
+    const bool geo = blockIdx.y < GEO_GROUPS;
+    const int r0 = geo ? (int)blockIdx.y * PR : N_GEO + ((int)blockIdx.y - GEO_GROUPS) * PR;
+    const int rend = geo ? N_GEO : D;
+    const int stride = gridDim.x * blockDim.x;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pairs) return;
+    uint32_t key[PR];
+#pragma unroll
+    for (int q = 0; q < PR; q++) key[q] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + q)) : 0u;
+    PairRows cur, nxt;
+    if (geo) {
+        pair_fetch<T, true, OPT>(cur, j, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
+        while (true) {
+            const int jn = j + stride;
+            const bool more = jn < n_pairs;
+            if (more) pair_fetch<T, true, OPT>(nxt, jn, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
+            pair_step<T, true, OPT>(cur, P, r0, rend, L, key);
+            if (!more) break;
+            cur = nxt;
+            j = jn;
+        }
+    } else {
+        pair_fetch<T, false, OPT>(cur, j, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
+        while (true) {
+            const int jn = j + stride;
+            const bool more = jn < n_pairs;
+            if (more) pair_fetch<T, false, OPT>(nxt, jn, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
+            pair_step<T, false, OPT>(cur, P, r0, rend, L, key);
+            if (!more) break;
+            cur = nxt;
+            j = jn;
+        }
+    }
+}
+
+bool adam_pairs_ok(const SceneView &sc)
+{
+    // resident planes, 8-byte aligned pair accesses (pitch is a multiple of 4)
+    auto al = [](const void *p) { return ((uintptr_t)p & 7) == 0; };
+    return !sc.sh.slot && al(sc.geo) && al(sc.m) && al(sc.v) && al(sc.sh.w) && al(sc.sh.m) && al(sc.sh.v) &&
+           (!sc.rdir || (al(sc.rdir) && al(sc.sh.rdir))) && sc.counter;
+}
+
+void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb,
+                       int *n_upd, Work &w, cudaStream_t s)
+{
+    const int64_t nw_u = (sc.n + 31) / 32, npairs = (sc.n + 1) / 2, nw_p = (npairs + 31) / 32;
+    // members of the update set (reported), from the per-chunk counts of the select
+    scan_counts(uchunk, (sc.n + CHUNK - 1) / CHUNK, n_upd, 0, w, s);
+    k_pair_mask<<<w.grid(nw_p, 256, 4), 256, 0, s>>>(umask, nw_u, pb.pmask, nw_p);
+    compact_mask(pb.pmask, npairs, pb.pchunk, false, pb.pids, nullptr, (int)npairs, pb.n_pairs, w, s);
+    k_pair_prep<<<w.grid(npairs, 256, 4), 256, 0, s>>>(pb.pids, pb.n_pairs, umask, sc.counter, sc.n, pb.pinfo);
+    constexpr int GEO_GROUPS = (N_GEO + PR - 1) / PR;
+    const int groups = GEO_GROUPS + (sc.D - N_GEO + PR - 1) / PR;
+    dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
+    w.mark(TP_APPLY0, s);
+    with_opt(sc.opt, [&](auto o) {
+        constexpr int O = decltype(o)::value;
+        if (sc.prec == GS_FP32)
+            k_adam_apply_pairs<float, O><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, pb.pids, pb.pinfo,
+                                                                    pb.n_pairs, vmask, vprefix, grad, gcap, args);
+        else
+            k_adam_apply_pairs<__nv_bfloat16, O><<<grid, ADAM_BLOCK, 0, s>>>(
+                planes_of<__nv_bfloat16>(sc), sc.D, pb.pids, pb.pinfo, pb.n_pairs, vmask, vprefix, grad, gcap, args);
+    });
     w.mark(TP_APPLY1, s);
 }
 

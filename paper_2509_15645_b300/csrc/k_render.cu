@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
     const uint32_t *__restrict__ svals = J.svals[view];
     const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
     float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
-    const DevCam &cam = args->cam[view];
-    const float *target = use_target ? args->target[view] : nullptr;
+    const DevCam &cam = args->cam[J.cam0 + view];
+    const float *target = use_target ? args->target[J.cam0 + view] : nullptr;
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
     const int x = tx0 + tl % tw;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
     const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
     const float *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
     float *__restrict__ g9 = J.g9[view];
-    const DevCam &cam = args->cam[view];
+    const DevCam &cam = args->cam[J.cam0 + view];
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
     const int x = tx0 + tl % tw;
@@ -954,9 +954,10 @@ static RasterShape raster_shape(int v, int items, int tile_w, int tile_h, const 
 }
 
 void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
-                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s)
+                    bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s, int cam0)
 {
     RasterJob J = make_job(n_views, rbs, work);
+    J.cam0 = cam0;
     for (int v = 0; v < n_views; v++) {
         J.image[v] = images[v];
         if (images[v] == rbs[v]->cfinal) J.cfinal[v] = nullptr;
@@ -996,13 +997,14 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
-                     unsigned long long *stats)
+                     unsigned long long *stats, int cam0)
 {
     for (int v = 0; v < n_views; v++) {
         const int cap = (int)rbs[v]->cap;
         launch_zero_rows(rbs[v]->g9, G9_STRIDE, cap, n_vis[v], cap, w, s, true);
     }
     RasterJob J = make_job(n_views, rbs, work);
+    J.cam0 = cam0;
     for (int v = 0; v < n_views; v++) J.dimage[v] = const_cast<float *>(dimages[v]);
     const RenderBufs &rb0 = *rbs[0];
     const RasterShape sh = raster_shape(rb0.variant_bwd, J.tile_ofs[n_views], cams[0].tile_w, cams[0].tile_h, w);

@@ -187,3 +187,22 @@ def test_noalloc_cull_rejects_before_any_launch(lib):
     for bad in (dict(beta2=1.0), dict(beta1=-0.1), dict(eps=-1.0), dict(max_defer=16), dict(max_defer=0),
                 dict(mode=7)):
         assert call(scene(), cam(), api.adam_struct(**bad)) == _lib.GS_ERR_INVALID_ARG, bad
+
+
+def test_render_rounds_bound_the_workspace(lib):
+    """gs_config.render_views: render buffers for that many views only (the
+    per-view cull buffers stay for max_views), so two regions rendered one
+    after the other need less workspace than two at once; values outside
+    0..max_views are refused."""
+    from paper_2509_15645_b300 import api
+    kw = dict(max_gaussians=1_000_000, max_visible=400_000, max_keys=8_000_000, max_width=1920, max_height=1080,
+              tile=(8, 4), max_views=2, max_sh_degree=3)
+    both = api.Context.workspace_bytes(**kw)
+    one = api.Context.workspace_bytes(**kw, render_views=1)
+    single = api.Context.workspace_bytes(**dict(kw, max_views=1))
+    assert api.Context.workspace_bytes(**kw, render_views=2) == both
+    assert one < both and both - one > 0.4 * (both - single)
+    from paper_2509_15645_b300 import _lib
+    for bad in (3, -1):
+        with pytest.raises(_lib.GsError):
+            api.Context.workspace_bytes(**kw, render_views=bad)

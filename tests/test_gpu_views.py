@@ -58,12 +58,21 @@ def _state(scene, n):
             v.cpu().numpy().astype(np.float64), scene.counter[:n].cpu().numpy().copy())
 
 
-def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr, opt=None):
+def _tie_affected(orc, Wcur, rr, ex):
+    """Gaussians whose oracle gradient changes when the tie pixels are weighted
+    0: a decision there may go the other way in FP32, so their step is not
+    determined to FP32 accuracy (excluded from the state comparison, counted)."""
+    g_m, _ = orc.backward(Wcur, DEG, rr["cam"], rr["splats"], rr["key_gid"], rr["ranges"], rr["dimage"] * ~ex[None])
+    return np.any(g_m != rr["grad"], axis=0), g_m
+
+
+def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr, opt=None, skip=None):
     """The GPU's state after step t against the oracle's deferred step from the
     stored state (W, M, V, Cn) with the GPU's visible set and the oracle's
     gradients.  fp32: FP32 rounding of each update term; bf16 stores: one bf16
     ulp (stochastic rounding picks either neighbour) plus the step's share.
-    opt: None (Adam), ("adamw", weight decay) or ("sgdm", momentum)."""
+    opt: None (Adam), ("adamw", weight decay) or ("sgdm", momentum).  skip:
+    Gaussians left out of the parameter comparison (tie-affected)."""
     W0 = W.copy()
     if opt is None:
         orc.adam_deferred(W, M, V, Cn, gids, grad[:, gids], t, hp)
@@ -73,6 +82,12 @@ def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr, op
         orc.sgdm_deferred(W, M, Cn, gids, grad[:, gids], hp.lr, opt[1], max_defer=hp.max_defer)
     gw, gm, gv, gc = _state(scene, n)
     np.testing.assert_array_equal(gc, Cn)
+    if skip is not None and skip.any():
+        keep = ~skip
+        W, M, V, W0, gw, gm, gv = (x[:, keep] for x in (W, M, V, W0, gw, gm, gv))
+        grad = grad[:, keep]
+        gids = np.nonzero(np.isin(np.nonzero(keep)[0], gids))[0]
+        n = int(keep.sum())
     D = W.shape[0]
     g_full = np.zeros((D, n))
     g_full[:, gids] = grad[:, gids]
@@ -156,7 +171,7 @@ def test_restore_over_changing_views(gs, orc, bf16, opt):
         # gradients with the tie pixels weighted 0 on both sides (a decision at
         # FP32 resolution there may go either way and move whole gradients)
         dimg = rr["dimage"] * ok
-        g_ref, _ = orc.backward(Wcur, DEG, rr["cam"], sp, rr["key_gid"], rr["ranges"], dimg)
+        affected, g_ref = _tie_affected(orc, Wcur, rr, ex)
         gc = ctx.render_bwd(torch.as_tensor(dimg, dtype=torch.float32, device="cuda"), scene.D)
         full = ctx.grad_scatter(scene, ids, nv, gc)
         ctx.sync_status()
@@ -171,7 +186,9 @@ def test_restore_over_changing_views(gs, orc, bf16, opt):
         loss = ctx.step(scene, [cam], [tg[k]], adam)
         ctx.sync_status()
         assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
-        moved = _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids.astype(np.int32), rr["grad"], hp, LR, ospec)
+        moved = _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids.astype(np.int32), rr["grad"], hp, LR, ospec,
+                            skip=affected)
+        assert affected.mean() < 0.02, (t, affected.mean())
         assert moved > 0.02
     d = np.concatenate(delays)
     hist = np.bincount(d, minlength=16)
@@ -213,7 +230,9 @@ def test_host_tier_over_changing_views(gs, orc, prec_name):
         loss = ctx.step(scene, [cams[k]], [tg[k]], adam)
         ctx.sync_status()          # waits for the write-backs too
         assert abs(loss.item() - rr["loss"]) <= 1e-5 * rr["loss"] + 1e-7, (t, loss.item(), rr["loss"])
-        _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids, rr["grad"], hp, LR)
+        affected, _ = _tie_affected(orc, Wcur, rr, pixel_exclusions(rr, gids))
+        assert affected.mean() < 0.02, (t, affected.mean())
+        _check_step(orc, scene, N, t, bf16, W, M, V, Cn, gids, rr["grad"], hp, LR, skip=affected)
         staged, _ = ctx.host_tier_stats()
         assert 0 < staged <= (N + 1023) // 1024
     assert saw_bound

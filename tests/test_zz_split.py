@@ -37,9 +37,9 @@ def _cam():
     return cam_f32(scenes.camera_lookat((0.2, -0.1, -2.0), (0.0, 0.0, 0.0), 128, 96, 60.0, up=(0, -1, 0)))
 
 
-def _ctx(gs, n, views=2):
+def _ctx(gs, n, views=2, render_views=0):
     return gs.Context(max_gaussians=n, max_visible=n, max_keys=64 * n + 4096, max_width=128, max_height=96,
-                      tile=TILE, max_views=views, max_sh_degree=DEG)
+                      tile=TILE, max_views=views, max_sh_degree=DEG, render_views=render_views)
 
 
 @pytest.mark.parametrize("axis", [0, 1])
@@ -91,17 +91,20 @@ def test_region_renders_stitch_to_the_view(gs, orc, axis, split):
     assert err[ok].max() <= 1e-5, err[ok].max()
 
 
-def test_split_step_matches_whole_view_step(gs, orc):
+@pytest.mark.parametrize("render_views", [0, 1])
+def test_split_step_matches_whole_view_step(gs, orc, render_views):
     """gs_step over a view's two regions (split where gs_split_point puts it,
     region targets cropped from the view's target) takes the whole view's
     step: loss = the view's L1 loss, one optimizer step over the union of the
-    regions' visible sets with their summed gradients."""
+    regions' visible sets with their summed gradients.  render_views = 1: the
+    regions are rendered one after the other through one set of render
+    buffers (the bounded working set of §4.4), with the same result."""
     P = _scene()
     cam, n, D = _cam(), P.shape[1], P.shape[0]
     T = f32(scenes.uniform_cube_scene(n, seed=60, sh_degree=DEG, log_scale_mean=-3.0))
     target = orc.render(T, DEG, cam, TILE)["image"]
     scene = gs.GaussianScene(P, DEG)
-    ctx = _ctx(gs, n)
+    ctx = _ctx(gs, n, render_views=render_views)
     adam = gs.adam_struct(lr=1e-3, eps=1e-15)
     hp = hp32(orc, lr=1e-3, eps=1e-15)
     regions = ctx.plan_split(scene, cam, adam, mem_limit=0.3)     # 3837 / 4000 visible: split
