@@ -114,3 +114,22 @@ def pixel_exclusions(r, gpu_ids=None):
         else:
             ex |= np.abs(dist - rr) <= 1.01
     return ex
+
+
+def cancellation_bound(sp, H, W, u=2.0 ** -24):
+    """Per-pixel bound on the FP32 compositing error that the cancellation in
+    sigma = 1/2 (A dx^2 + C dy^2) + B dx dy allows: every kept splat whose
+    3-sigma square covers the pixel adds 8 u sigma_abs, sigma_abs = (|A| +
+    2|B| + |C|) r^2 / 2 (long thin splats have large ones)."""
+    keep = np.nonzero(sp["keep"] == 1)[0]
+    con, rad = sp["conic"][keep], sp["radius"][keep]
+    sabs = 0.5 * (np.abs(con[:, 0]) + 2 * np.abs(con[:, 1]) + np.abs(con[:, 2])) * rad ** 2
+    out = np.zeros((H, W))
+    for j in np.nonzero(8 * u * sabs > 1e-7)[0]:
+        mx, my = sp["mean2d"][keep[j]]
+        r = rad[j]
+        x0, x1 = max(0, int(np.floor(mx - r - 0.5))), min(W, int(np.ceil(mx + r + 0.5)))
+        y0, y1 = max(0, int(np.floor(my - r - 0.5))), min(H, int(np.ceil(my + r + 0.5)))
+        if x0 < x1 and y0 < y1:
+            out[y0:y1, x0:x1] += 8 * u * sabs[j]
+    return out
