@@ -179,8 +179,12 @@ def build_workload(n, n_views, seed_views=2, density_of=None, width=1920, height
         clusters = max(1, round(200 * n / density_of))
     cfg = scenes.cfg_aerial(n=n, n_views=n_views, seed_views=seed_views, scale=scale, n_clusters=clusters,
                             width=width, height=height)
-    tgt_scene = scenes.heightfield_scene(n, seed=1, half_extent=cfg["half_extent"], amplitude=20.0,
-                                         wavelength=(20.0 * scale, 25.0 * scale), n_clusters=clusters)
+    # the targets are images to fit: rendered from a seed-1 scene over the same
+    # area, of at most 10M Gaussians (larger scenes would only lengthen the setup)
+    nt = min(n, 10_000_000)
+    tgt_scene = scenes.heightfield_scene(nt, seed=1, half_extent=cfg["half_extent"], amplitude=20.0,
+                                         wavelength=(20.0 * scale, 25.0 * scale),
+                                         n_clusters=max(1, round(clusters * nt / n)))
     return cfg, tgt_scene
 
 
@@ -615,10 +619,44 @@ def run_ours(args):
         out["cull_adam"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, sample_frac=0.1)
+    if rank == 0 and world == 1 and args.extra_forms and not (args.bf16_only or args.budget_gb or vps != 1 or
+                                                               args.density_of):
+        out.update(extra_forms(args))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def extra_forms(args):
+    """The batched BF16 form and the host-offload configuration, each timed by
+    this script in a subprocess of its own (same K and W) after the main line:
+    batched_bf16 = 10M resident, 4 views of 1600x1200 per step, bf16 SH and
+    moments; host_tier_40m = 40M Gaussians on the 2x2 km field (the 10M
+    field's density) with a 24 GB
+    HBM budget (SH planes and their moments in pinned host memory), 4 views of
+    1600x1200 per step, fp32 and bf16."""
+    runs = {"batched_bf16": ["--bf16-only", "--views-per-step", "4", "--image", "1600x1200"],
+            "host_tier_40m_fp32": ["--gaussians", "40000000", "--density-of", "10000000", "--budget-gb", "24",
+                                   "--views-per-step", "4", "--image", "1600x1200"],
+            "host_tier_40m_bf16": ["--gaussians", "40000000", "--density-of", "10000000", "--budget-gb", "24",
+                                   "--views-per-step", "4", "--image", "1600x1200", "--bf16-only"]}
+    out = {}
+    for name, extra in runs.items():
+        cmd = [sys.executable, os.path.abspath(__file__), "--steps", str(args.steps), "--warmup", str(args.warmup),
+               "--no-cpu-baseline", "--no-extra-forms", *extra]
+        t0 = time.time()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            line = [x for x in r.stdout.strip().splitlines() if x.startswith("{")]
+            sub = json.loads(line[-1]) if r.returncode == 0 and line else {"error": (r.stderr or r.stdout)[-400:]}
+        except Exception as e:
+            sub = {"error": repr(e)[:400]}
+        keep = ("value", "unit", "ms_per_step", "stages_ms", "cull_adam", "roofline", "clocks", "e2e", "config",
+                "host_tier", "gpu_launches", "error")
+        out[name] = {k: sub[k] for k in keep if k in sub}
+        out[name]["wall_s"] = round(time.time() - t0, 1)
+    return out
 
 
 # ---------------------------------------------------------------------------- image splitting (§4.4)
@@ -859,6 +897,8 @@ def main():
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
     ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
     ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
+    ap.add_argument("--no-extra-forms", dest="extra_forms", action="store_false",
+                    help="skip the batched-bf16 and 40M host-tier sub-records of the default line")
     ap.add_argument("--split-demo", action="store_true",
                     help="measure balance-aware image splitting (§4.4) on a 1M-Gaussian view that crosses mem_limit")
     ap.add_argument("--oracle-workloads", action="store_true",

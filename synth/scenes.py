@@ -27,6 +27,8 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, field
 
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 __all__ = [
@@ -134,27 +136,45 @@ def _random_quats(rng, n):
     return q
 
 
-def _sh_block(rng, n, sh_degree, rest_std=0.01):
-    """SH rows: DC from colours uniform in [0,1], higher coefficients N(0, rest_std^2)."""
+def _assemble(means, log_scales, quats, opac_logit, rng, n, sh_degree, morton=True, rest_std=0.01):
+    """The [D][n] float32 scene: the 11 geometry rows, then the SH rows drawn
+    from ``rng`` after everything else (DC from colours uniform in [0,1], the
+    higher coefficients N(0, rest_std^2)), in Morton order of the means.  The
+    SH rows are drawn one at a time (the same stream, in the same order, as one
+    draw of the whole block) and written straight to their place, so a large
+    scene never holds them in float64."""
     k = (sh_degree + 1) ** 2
-    sh = np.empty((k, 3, n), np.float64)
-    sh[0] = (rng.uniform(0.0, 1.0, (3, n)) - 0.5) * DC_FROM_RGB
-    if k > 1:
-        sh[1:] = rng.normal(0.0, rest_std, (k - 1, 3, n))
-    return sh.reshape(3 * k, n)
-
-
-def _assemble(means, log_scales, quats, opac_logit, sh, morton=True):
-    n = means.shape[1]
-    D = 11 + sh.shape[0]
+    D = 11 + 3 * k
+    order = morton_order(means) if morton else None
     p = np.empty((D, n), np.float32)
-    p[0:3] = means
-    p[3:6] = log_scales
-    p[6:10] = quats
-    p[10] = opac_logit
-    p[11:] = sh
-    if morton:
-        p = np.ascontiguousarray(p[:, morton_order(means)])
+    step = max(1, -(-n // 8))
+    with ThreadPoolExecutor(8) as gather_pool, ThreadPoolExecutor(1) as row_pool:
+        def put(row, values):
+            # the permutation gather in 8 slices on threads (numpy releases the GIL there)
+            if not morton:
+                p[row] = values
+                return
+            list(gather_pool.map(lambda a: p.__setitem__((row, slice(a, a + step)), values[order[a:a + step]]),
+                                 range(0, n, step)))
+
+        for r in range(3):
+            put(r, means[r])
+            put(3 + r, log_scales[r])
+        for r in range(4):
+            put(6 + r, quats[r])
+        put(10, opac_logit)
+        dc = (rng.uniform(0.0, 1.0, (3, n)) - 0.5) * DC_FROM_RGB
+        for c in range(3):
+            put(11 + c, dc[c])
+        del dc
+        pending = None
+        for r in range(3, 3 * k):
+            values = rng.normal(0.0, rest_std, n)          # the next row's draw overlaps the last row's gather
+            if pending is not None:
+                pending.result()
+            pending = row_pool.submit(put, 11 + r, values)
+        if pending is not None:
+            pending.result()
     return p
 
 
@@ -175,8 +195,7 @@ def uniform_cube_scene(n, seed, sh_degree=0, log_scale_mean=-3.0, log_scale_std=
         ls[ax, sel] = -9.0
     quats = _random_quats(rng, n)
     opac = rng.standard_normal(n)
-    sh = _sh_block(rng, n, sh_degree)
-    return _assemble(means, ls, quats, opac, sh, morton)
+    return _assemble(means, ls, quats, opac, rng, n, sh_degree, morton)
 
 
 def heightfield_scene(n, seed, half_extent=100.0, amplitude=5.0, wavelength=(20.0, 25.0),
@@ -204,8 +223,7 @@ def heightfield_scene(n, seed, half_extent=100.0, amplitude=5.0, wavelength=(20.
                          rng.normal(cluster_log_scale, 0.3, (3, n_cl))], axis=1)
     quats = _random_quats(rng, n)
     opac = rng.standard_normal(n)
-    sh = _sh_block(rng, n, sh_degree)
-    return _assemble(means, ls, quats, opac, sh, morton)
+    return _assemble(means, ls, quats, opac, rng, n, sh_degree, morton)
 
 
 def orbit_cameras(n_views, radius, altitude, width=1920, height=1080, fov_x_deg=60.0, phase=0.0):
