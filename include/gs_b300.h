@@ -333,9 +333,10 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
  * records; a tile shape allows them when tile_h is a multiple of the pixels
  * per thread and the block has 32 to 256 threads.  v = 6, 7 (32-pixel tiles
  * only): one tile per warp, 4 warps per block with batches of 64 records, or
- * 8 warps with batches of 32.  Every variant computes the same image bit for
- * bit; they differ only in speed. */
-#define GS_RASTER_VARIANTS 8
+ * 8 warps with batches of 32.  v = 8 (32-pixel tiles only): as 7, walking the
+ * list two entries at a time with paired FP32 (f32x2) arithmetic.  Every
+ * variant computes the same image bit for bit; they differ only in speed. */
+#define GS_RASTER_VARIANTS 9
 
 /* Autotuner: time every variant the context's tile shape allows on this scene
  * and view (render forward and backward separately; CUDA events, best of

@@ -663,6 +663,54 @@ __device__ __forceinline__ float splat_alpha_nb(float4 r0, float4 r1, float dx, 
 }
 
 // ---------------------------------------------------------------------------
+// Paired FP32 arithmetic (sm_100 and later: add/sub/mul/fma .rn.f32x2 on a
+// 64-bit register pair): two independent IEEE operations, each rounded as its
+// scalar form, in one instruction.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk2(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo2(f2 r)
+{
+    float a;
+    asm("{ .reg .f32 hi; mov.b64 {%0, hi}, %1; }" : "=f"(a) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float hi2(f2 r)
+{
+    float b;
+    asm("{ .reg .f32 lo; mov.b64 {lo, %0}, %1; }" : "=f"(b) : "l"(r));
+    return b;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch helpers implemented in the .cu files.
 struct Scan;   // fwd
 

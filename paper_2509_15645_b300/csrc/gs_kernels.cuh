@@ -225,7 +225,7 @@ struct RasterJob {
     int *work;
 };
 
-constexpr int N_RASTER_VARIANTS = 8;
+constexpr int N_RASTER_VARIANTS = 9;
 
 // k_lists.cu: rectangles of more tiles than this are counted and emitted by a
 // warp each (the big list the gather fills); smaller ones by a warp's lanes

@@ -325,16 +325,16 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
                 bool cl;
                 const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
                 if (a == 0.f) continue;
-                const float Tn = T[j] * (1.f - a);
+                const float Tn = __fmul_rn(T[j], __fsub_rn(1.f, a));
                 if (Tn < T_STOP) {
                     live &= ~(1u << j);
                     continue;
                 }
                 const float4 c = s2[e];
-                const float aT = a * T[j];
-                C0[j] += c.x * aT;
-                C1[j] += c.y * aT;
-                C2[j] += c.z * aT;
+                const float aT = __fmul_rn(a, T[j]);
+                C0[j] = __fmaf_rn(c.x, aT, C0[j]);
+                C1[j] = __fmaf_rn(c.y, aT, C1[j]);
+                C2[j] = __fmaf_rn(c.z, aT, C2[j]);
                 T[j] = Tn;
             }
         }
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     const float a = splat_alpha_nb(r0, r1, dx, (float)(y0 + j) + 0.5f, dy, G, cl);
                     if (STATS) n_sq += fabsf(dy) <= r0.z ? 1 : 0;
                     if (a == 0.f) continue;
-                    const float Tn = T[j] * (1.f - a);
+                    const float Tn = __fmul_rn(T[j], __fsub_rn(1.f, a));
                     if (Tn < T_STOP) {
                         live &= ~(1u << j);
                         continue;
@@ -512,23 +512,23 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     if (STATS) n_on++;
                     contrib = true;
                     const float4 c = s2[e];
-                    const float aT = a * T[j];
-                    const float gc = g0[j] * c.x + g1[j] * c.y + g2[j] * c.z;
-                    gA[j] += aT * gc;
+                    const float aT = __fmul_rn(a, T[j]);
+                    const float gc = __fmaf_rn(g2[j], c.z, __fmaf_rn(g1[j], c.y, __fmul_rn(g0[j], c.x)));
+                    gA[j] = __fmaf_rn(aT, gc, gA[j]);
                     // dL/da = g . (T c - (F - A)/(1 - a)), A through this splat
-                    const float dLda = T[j] * gc - __fdividef(gF[j] - gA[j], 1.f - a);
-                    v[6] += g0[j] * aT;
-                    v[7] += g1[j] * aT;
-                    v[8] += g2[j] * aT;
+                    const float dLda = __fmaf_rn(T[j], gc, -__fdividef(__fsub_rn(gF[j], gA[j]), __fsub_rn(1.f, a)));
+                    v[6] = __fmaf_rn(g0[j], aT, v[6]);
+                    v[7] = __fmaf_rn(g1[j], aT, v[7]);
+                    v[8] = __fmaf_rn(g2[j], aT, v[8]);
                     if (!cl) {                                   // the 0.999 clamp has no derivative
-                        const float ds = -a * dLda;
-                        v[5] += G * dLda;
-                        const float sdx = ds * dx, sdy = ds * dy;
-                        v[0] += sdx;
-                        v[1] += sdy;
-                        v[2] += sdx * dx;
-                        v[3] += sdx * dy;
-                        v[4] += sdy * dy;
+                        const float ds = __fmul_rn(-a, dLda);
+                        v[5] = __fmaf_rn(G, dLda, v[5]);
+                        const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
+                        v[0] = __fadd_rn(v[0], sdx);
+                        v[1] = __fadd_rn(v[1], sdy);
+                        v[2] = __fmaf_rn(sdx, dx, v[2]);
+                        v[3] = __fmaf_rn(sdx, dy, v[3]);
+                        v[4] = __fmaf_rn(sdy, dy, v[4]);
                     }
                     T[j] = Tn;
                 }
@@ -582,6 +582,346 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-tile rasterizers over entry pairs (variant 8): a one-warp tile (32
+// pixels, one per lane) walks its list two entries at a time.  The staging
+// writes entries 2q and 2q + 1 side by side -- five float4 per pair: (mean x,
+// mean y), (radius, opacity), (conic A, B), (conic C, blue), (red, green),
+// each as the pair's two values -- so one shared-memory load gives two
+// operands of a paired f32x2 instruction, and the per-(pixel, splat) terms of
+// both entries (alpha, and in the backward the gradient terms) take one
+// instruction each.  The transmittance runs through the two entries in order
+// with the scalar kernels' operations, so images are the same bit for bit.
+constexpr int PAIR_ROWS = 5;
+
+template <int NP, bool INDEX>
+__device__ __forceinline__ int stage_pairs(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
+                                           const float4 *__restrict__ rec1, const float4 *__restrict__ rec2,
+                                           uint32_t b, int cnt, float *q, uint32_t *s_k, uint32_t kcap_vis)
+{
+    const int lane = threadIdx.x & 31;
+    const int padded = (cnt + 1) & ~1;
+    for (int e = lane; e < padded; e += 32) {
+        float4 r0 = make_float4(0.f, 0.f, -1.f, 0.f), r1 = make_float4(0.f, 0.f, 0.f, 0.f), r2 = r1;
+        uint32_t k = 0u;
+        if (e < cnt) {
+            k = svals[b + e];
+            if (k < kcap_vis) {            // else an empty splat (never for a consistent list)
+                r0 = rec0[k];
+                r1 = rec1[k];
+                r2 = rec2[k];
+            } else {
+                k = 0u;
+            }
+        }
+        const int p = e >> 1, h = e & 1;
+        float *q0 = q + (0 * NP + p) * 4, *q1 = q + (1 * NP + p) * 4, *q2 = q + (2 * NP + p) * 4;
+        float *q3 = q + (3 * NP + p) * 4, *q4 = q + (4 * NP + p) * 4;
+        q0[h] = r0.x; q0[2 + h] = r0.y;
+        q1[h] = r0.z; q1[2 + h] = r0.w;
+        q2[h] = r1.x; q2[2 + h] = r1.y;
+        q3[h] = r1.z; q3[2 + h] = r2.z;
+        q4[h] = r2.x; q4[2 + h] = r2.y;
+        if (INDEX) s_k[e] = k;
+    }
+    __syncwarp();
+    return padded >> 1;
+}
+
+// Alphas of the pair's two entries at pixel (px, py), as splat_alpha_nb
+// computes each (same operations, paired).  in0 / in1: the entry passed the
+// warp's row test and the pixel's x test.
+struct PairAlpha {
+    f2 dx2, dy2;
+    float a0, a1, G0, G1;
+    bool cl0, cl1;
+};
+__device__ __forceinline__ PairAlpha pair_alpha(const float4 &m, const float4 &ro, const float4 &ab, const float4 &cc,
+                                                f2 px2, f2 py2, bool in0, bool in1)
+{
+    PairAlpha P;
+    P.dx2 = sub2(pk2(m.x, m.y), px2);
+    P.dy2 = sub2(pk2(m.z, m.w), py2);
+    const f2 sig2 = fma2(pk2(ab.z, ab.w), mul2(P.dx2, P.dy2),
+                         mul2(pk2(0.5f, 0.5f), fma2(pk2(ab.x, ab.y), mul2(P.dx2, P.dx2),
+                                                    mul2(pk2(cc.x, cc.y), mul2(P.dy2, P.dy2)))));
+    const float s0 = lo2(sig2), s1 = hi2(sig2);
+    P.G0 = __expf(-s0);
+    P.G1 = __expf(-s1);
+    const f2 raw2 = mul2(pk2(ro.z, ro.w), pk2(P.G0, P.G1));
+    const float raw0 = lo2(raw2), raw1 = hi2(raw2);
+    P.cl0 = raw0 > ALPHA_MAX;
+    P.cl1 = raw1 > ALPHA_MAX;
+    const float al0 = fminf(ALPHA_MAX, raw0), al1 = fminf(ALPHA_MAX, raw1);
+    const bool ok0 = in0 && fabsf(lo2(P.dy2)) <= ro.x && s0 >= 0.f && al0 >= ALPHA_MIN;
+    const bool ok1 = in1 && fabsf(hi2(P.dy2)) <= ro.y && s1 >= 0.f && al1 >= ALPHA_MIN;
+    P.a0 = ok0 ? al0 : 0.f;
+    P.a1 = ok1 ? al1 : 0.f;
+    return P;
+}
+
+template <int BATCH, int NW>
+__global__ void __launch_bounds__(32 * NW, 4) k_raster_fwd_pairs(const RasterJob J, const DevArgs *__restrict__ args,
+                                                                 int use_target, float *__restrict__ loss)
+{
+    static_assert(BATCH % 2 == 0, "entry pairs");
+    constexpr int NP = BATCH / 2;
+    __shared__ __align__(16) float q_[NW][PAIR_ROWS * NP * 4];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31;
+    float *q = q_[threadIdx.x >> 5];
+    const float4 *Q = reinterpret_cast<const float4 *>(q);
+    float loss_part = 0.f;
+    int view, tile;
+    while (next_item<true>(J, &s_item, view, tile)) {
+        const uint2 *__restrict__ ranges = J.ranges[view];
+        float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view];
+        float *__restrict__ dimage = J.dimage[view];
+        const DevCam &cam = args->cam[J.cam0 + view];
+        const float *target = use_target ? args->target[J.cam0 + view] : nullptr;
+        const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
+        const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+        const int x = tx0 + lane % tw, y = ty0 + lane / tw;
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
+        const f2 px2 = pk2(px, px), py2 = pk2(py, py);
+        const uint2 rg = ranges[tile];
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        bool live = x < W && y < H;
+        for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
+            if (!__any_sync(0xffffffffu, live)) break;
+            __syncwarp();                            // the previous batch is no longer read
+            const int np = stage_pairs<NP, false>(J.svals[view], J.rec0[view], J.rec1[view], J.rec2[view], b,
+                                                  min(BATCH, (int)(rg.y - b)), q, nullptr, J.cap[view]);
+            for (int p = 0; p < np && live; p++) {
+                const float4 m = Q[0 * NP + p], ro = Q[1 * NP + p];
+                const bool r0 = !(m.z + ro.x < wy0 - 1e-3f || m.z - ro.x > wy1 + 1e-3f);   // uniform per warp
+                const bool r1 = !(m.w + ro.y < wy0 - 1e-3f || m.w - ro.y > wy1 + 1e-3f);
+                if (!r0 && !r1) continue;
+                const float dx0 = __fsub_rn(m.x, px), dx1 = __fsub_rn(m.y, px);
+                const bool in0 = r0 && fabsf(dx0) <= ro.x, in1 = r1 && fabsf(dx1) <= ro.y;
+                if (!in0 && !in1) continue;
+                const PairAlpha A = pair_alpha(m, ro, Q[2 * NP + p], Q[3 * NP + p], px2, py2, in0, in1);
+                if (A.a0 != 0.f) {
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, A.a0));
+                    if (Tn < T_STOP) {
+                        live = false;
+                        continue;
+                    }
+                    const float4 c = Q[4 * NP + p], cz = Q[3 * NP + p];
+                    const float aT = __fmul_rn(A.a0, T);
+                    C0 = __fmaf_rn(c.x, aT, C0);
+                    C1 = __fmaf_rn(c.z, aT, C1);
+                    C2 = __fmaf_rn(cz.z, aT, C2);
+                    T = Tn;
+                }
+                if (A.a1 != 0.f) {
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, A.a1));
+                    if (Tn < T_STOP) {
+                        live = false;
+                        continue;
+                    }
+                    const float4 c = Q[4 * NP + p], cz = Q[3 * NP + p];
+                    const float aT = __fmul_rn(A.a1, T);
+                    C0 = __fmaf_rn(c.y, aT, C0);
+                    C1 = __fmaf_rn(c.w, aT, C1);
+                    C2 = __fmaf_rn(cz.w, aT, C2);
+                    T = Tn;
+                }
+            }
+        }
+        if (x < W && y < H) {
+            const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+            image[pix] = C0;
+            image[HW + pix] = C1;
+            image[2 * HW + pix] = C2;
+            if (cfinal) {
+                cfinal[pix] = C0;
+                cfinal[HW + pix] = C1;
+                cfinal[2 * HW + pix] = C2;
+            }
+            if (target) {
+                const float inv = cam.loss_inv;
+                float d0 = C0 - target[pix], d1 = C1 - target[HW + pix], d2 = C2 - target[2 * HW + pix];
+                dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
+                dimage[HW + pix] = (d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f));
+                dimage[2 * HW + pix] = (d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f));
+                loss_part += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * inv;
+            }
+        }
+    }
+    if (use_target) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
+        if (lane == 0 && loss_part != 0.f) atomicAdd(loss, loss_part);
+    }
+}
+
+// A warp's sums for one splat (v as in k_raster_bwd) into its g9 record:
+// per-lane atomics when few lanes contribute, else a warp reduction.
+__device__ __forceinline__ void emit_splat(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC, bool contrib,
+                                           float v[9], int lane)
+{
+    const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+    if (cmask == 0u) return;
+    float *row = g9 + (int64_t)k * G9_STRIDE;
+    if (__popc(cmask) <= DIRECT_LANES) {
+        if (contrib) {
+            atomicAdd(reinterpret_cast<float4 *>(row),
+                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
+            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+            if (v[8] != 0.f) atomicAdd(row + 8, v[8]);
+        }
+        return;
+    }
+    float s8 = v[8];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    const float sum = warp_transpose_sum8(v, lane);
+    const float q1 = __shfl_down_sync(0xffffffffu, sum, 4);
+    const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
+    const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
+        if (s8 != 0.f) atomicAdd(row + 8, s8);
+    } else if (lane == 16) {
+        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+    }
+}
+
+template <int BATCH, int NW, bool STATS = false>
+__global__ void __launch_bounds__(32 * NW, 4) k_raster_bwd_pairs(const RasterJob J, const DevArgs *__restrict__ args,
+                                                             unsigned long long *stats = nullptr)
+{
+    static_assert(BATCH % 2 == 0, "entry pairs");
+    constexpr int NP = BATCH / 2;
+    __shared__ __align__(16) float q_[NW][PAIR_ROWS * NP * 4];
+    __shared__ uint32_t k_[NW][BATCH];
+    __shared__ int s_item;
+    unsigned long long n_sq = 0, n_on = 0;
+    const int lane = threadIdx.x & 31;
+    float *q = q_[threadIdx.x >> 5];
+    uint32_t *s_k = k_[threadIdx.x >> 5];
+    const float4 *Q = reinterpret_cast<const float4 *>(q);
+    int view, tile;
+    while (next_item<true>(J, &s_item, view, tile)) {
+        const uint2 *__restrict__ ranges = J.ranges[view];
+        const float *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
+        float *__restrict__ g9 = J.g9[view];
+        const DevCam &cam = args->cam[J.cam0 + view];
+        const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
+        const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+        const int x = tx0 + lane % tw, y = ty0 + lane / tw;
+        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
+        const f2 px2 = pk2(px, px), py2 = pk2(py, py);
+        const uint2 rg = ranges[tile];
+        float T = 1.f, gF = 0.f, gA = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        bool live = x < W && y < H;
+        if (live) {
+            const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+            g0 = dimage[pix];
+            g1 = dimage[HW + pix];
+            g2 = dimage[2 * HW + pix];
+            gF = g0 * cfinal[pix] + g1 * cfinal[HW + pix] + g2 * cfinal[2 * HW + pix];
+        }
+        const f2 g0_2 = pk2(g0, g0), g1_2 = pk2(g1, g1), g2_2 = pk2(g2, g2);
+        for (uint32_t b = rg.x; b < rg.y; b += BATCH) {
+            if (!__any_sync(0xffffffffu, live)) break;
+            __syncwarp();
+            const int np = stage_pairs<NP, true>(J.svals[view], J.rec0[view], J.rec1[view], J.rec2[view], b,
+                                                 min(BATCH, (int)(rg.y - b)), q, s_k, J.cap[view]);
+            for (int p = 0; p < np; p++) {
+                const float4 m = Q[0 * NP + p], ro = Q[1 * NP + p];
+                const bool r0 = !(m.z + ro.x < wy0 - 1e-3f || m.z - ro.x > wy1 + 1e-3f);   // uniform per warp
+                const bool r1 = !(m.w + ro.y < wy0 - 1e-3f || m.w - ro.y > wy1 + 1e-3f);
+                if (!r0 && !r1) continue;
+                const float dx0 = __fsub_rn(m.x, px), dx1 = __fsub_rn(m.y, px);
+                const bool in0 = live && r0 && fabsf(dx0) <= ro.x;
+                bool c0 = false, c1 = false;
+                float v0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float v1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float4 ab = Q[2 * NP + p], cc = Q[3 * NP + p];
+                if (in0 || (live && r1 && fabsf(dx1) <= ro.y)) {
+                    const bool in1 = live && r1 && fabsf(dx1) <= ro.y;
+                    const PairAlpha A = pair_alpha(m, ro, ab, cc, px2, py2, in0, in1);
+                    // entry 2p then 2p + 1 through the transmittance, as the scalar kernel
+                    if (STATS) n_sq += (in0 && fabsf(lo2(A.dy2)) <= ro.x) ? 1 : 0;
+                    float a0 = A.a0, a1 = A.a1;
+                    const float T0 = T;
+                    if (a0 != 0.f) {
+                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, a0));
+                        if (Tn < T_STOP) {
+                            live = false;
+                            a0 = a1 = 0.f;
+                        } else {
+                            c0 = true;
+                            T = Tn;
+                        }
+                    }
+                    if (STATS && live) n_sq += (in1 && fabsf(hi2(A.dy2)) <= ro.y) ? 1 : 0;
+                    const float T1 = T;
+                    if (live && a1 != 0.f) {
+                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, a1));
+                        if (Tn < T_STOP) {
+                            live = false;
+                            a1 = 0.f;
+                        } else {
+                            c1 = true;
+                            T = Tn;
+                        }
+                    } else {
+                        a1 = 0.f;
+                    }
+                    if (STATS) n_on += (c0 ? 1 : 0) + (c1 ? 1 : 0);
+                    if (c0 || c1) {
+                        const float4 rg4 = Q[4 * NP + p];
+                        const f2 T2 = pk2(T0, T1), a2 = pk2(a0, a1);
+                        const f2 aT2 = mul2(a2, T2);
+                        const f2 gc2 = fma2(g2_2, pk2(cc.z, cc.w), fma2(g1_2, pk2(rg4.z, rg4.w), mul2(g0_2, pk2(rg4.x, rg4.y))));
+                        const float gA0 = __fmaf_rn(lo2(aT2), lo2(gc2), gA);
+                        const float gA1 = __fmaf_rn(hi2(aT2), hi2(gc2), gA0);
+                        gA = gA1;
+                        // dL/da = g . (T c - (F - A)/(1 - a)), A through this splat
+                        const float q0 = __fdividef(__fsub_rn(gF, gA0), __fsub_rn(1.f, a0));
+                        const float q1 = __fdividef(__fsub_rn(gF, gA1), __fsub_rn(1.f, a1));
+                        const f2 dl2 = fma2(T2, gc2, pk2(-q0, -q1));
+                        // the 0.999 clamp has no derivative; entries that do not contribute add nothing
+                        const f2 dlm2 = pk2(c0 && !A.cl0 ? lo2(dl2) : 0.f, c1 && !A.cl1 ? hi2(dl2) : 0.f);
+                        const f2 ds2 = mul2(pk2(-a0, -a1), dlm2);
+                        const f2 v5 = mul2(pk2(A.G0, A.G1), dlm2);
+                        const f2 sdx2 = mul2(ds2, A.dx2), sdy2 = mul2(ds2, A.dy2);
+                        const f2 v2 = mul2(sdx2, A.dx2), v3 = mul2(sdx2, A.dy2), v4 = mul2(sdy2, A.dy2);
+                        const f2 v6 = mul2(g0_2, aT2), v7 = mul2(g1_2, aT2), v8 = mul2(g2_2, aT2);
+                        v0[0] = lo2(sdx2); v1[0] = hi2(sdx2);
+                        v0[1] = lo2(sdy2); v1[1] = hi2(sdy2);
+                        v0[2] = lo2(v2); v1[2] = hi2(v2);
+                        v0[3] = lo2(v3); v1[3] = hi2(v3);
+                        v0[4] = lo2(v4); v1[4] = hi2(v4);
+                        v0[5] = lo2(v5); v1[5] = hi2(v5);
+                        v0[6] = lo2(v6); v1[6] = hi2(v6);
+                        v0[7] = lo2(v7); v1[7] = hi2(v7);
+                        v0[8] = lo2(v8); v1[8] = hi2(v8);
+                    }
+                }
+                emit_splat(g9, s_k[2 * p], ab.x, ab.z, cc.x, c0, v0, lane);
+                emit_splat(g9, s_k[2 * p + 1], ab.y, ab.w, cc.y, c1, v1, lane);
+            }
+        }
+    }
+    if (STATS) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            n_sq += __shfl_xor_sync(0xffffffffu, n_sq, o);
+            n_on += __shfl_xor_sync(0xffffffffu, n_on, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, n_sq);
+            atomicAdd(stats + 1, n_on);
+        }
+    }
+}
+
 typedef void (*RasterFwdFn)(const RasterJob, const DevArgs *, int, float *);
 typedef void (*RasterBwdFn)(const RasterJob, const DevArgs *, unsigned long long *);
 
@@ -598,7 +938,8 @@ static RasterFwdFn fwd_variant(int v)
     case 4: return k_raster_fwd<4, 128>;
     case 5: return k_raster_fwd<4, 256>;
     case 6: return k_raster_fwd<1, 64, 4>;
-    default: return k_raster_fwd<1, 32, 8>;
+    case 7: return k_raster_fwd<1, 32, 8>;
+    default: return k_raster_fwd_pairs<32, 8>;
     }
 }
 
@@ -620,12 +961,14 @@ static RasterBwdFn bwd_variant(int v, bool stats)
     case 12: return k_raster_bwd<1, 64, false, 4>;
     case 13: return k_raster_bwd<1, 64, true, 4>;
     case 14: return k_raster_bwd<1, 32, false, 8>;
-    default: return k_raster_bwd<1, 32, true, 8>;
+    case 15: return k_raster_bwd<1, 32, true, 8>;
+    case 16: return k_raster_bwd_pairs<32, 8, false>;
+    default: return k_raster_bwd_pairs<32, 8, true>;
     }
 }
 
 // Warps per block of a warp-tile variant, else 0.
-static int warp_tile_warps(int v) { return v == 6 ? 4 : v == 7 ? 8 : 0; }
+static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8) ? 8 : 0; }
 
 bool raster_variant_ok(int v, int tile_w, int tile_h)
 {
