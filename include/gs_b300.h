@@ -334,9 +334,12 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
  * per thread and the block has 32 to 256 threads.  v = 6, 7 (32-pixel tiles
  * only): one tile per warp, 4 warps per block with batches of 64 records, or
  * 8 warps with batches of 32.  v = 8 (32-pixel tiles only): as 7, walking the
- * list two entries at a time with paired FP32 (f32x2) arithmetic.  Every
- * variant computes the same image bit for bit; they differ only in speed. */
-#define GS_RASTER_VARIANTS 9
+ * list two entries at a time with paired FP32 (f32x2) arithmetic.  v = 9
+ * (32-pixel tiles only): as 7, each batch staged in shared memory by one TMA
+ * bulk copy of the tile's records written in list order after the sort (48
+ * bytes per key of extra traffic).  Every variant computes the same image bit
+ * for bit; they differ only in speed. */
+#define GS_RASTER_VARIANTS 10
 
 /* Autotuner: time every variant the context's tile shape allows on this scene
  * and view (render forward and backward separately; CUDA events, best of
@@ -392,14 +395,15 @@ GS_API gs_status gs_cull_noalloc(const gs_scene *scene, const gs_camera *cam, co
                                  int32_t tile_h, int32_t *ids_out, int32_t *n_vis_out, int32_t *status_out,
                                  void *stream);
 
-/* Failure-path testing (no counterpart in the paper).  Every cull block waits
- * on an mbarrier for the TMA copies it issued itself, each wait bounded; after
- * `first_wait` polls (default 2^24) of a block's first wait it gives up:
- * latches GS_ERR_TIMEOUT (gs_sync_status returns it), lets the copies it
- * issued land (waiting for them with the default bound) and returns, so the
- * context stays usable.  0 makes every block give up at once.  ctx = NULL
- * sets the limit of gs_cull_noalloc (process-wide).  Host only; gs_step
- * captures a new graph after a change. */
+/* Failure-path testing (no counterpart in the paper).  Every cull block (and
+ * every warp of the TMA-staged rasterizer, variant 9) waits on an mbarrier
+ * for the TMA copies it issued itself, each wait bounded; after `first_wait`
+ * polls (default 2^24) of its first wait it gives up: latches GS_ERR_TIMEOUT
+ * (gs_sync_status returns it), lets the copies it issued land (waiting for
+ * them with the default bound) and returns, so the context stays usable.  0
+ * makes every one give up at once.  ctx = NULL sets the limit of
+ * gs_cull_noalloc (process-wide).  Host only; gs_step captures a new graph
+ * after a change. */
 GS_API gs_status gs_set_cull_wait_limit(gs_ctx *ctx, uint32_t first_wait);
 
 /* Inspection of the last gs_render_fwd (tests, debugging).  Device pointers,

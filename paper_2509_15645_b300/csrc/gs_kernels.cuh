@@ -198,6 +198,8 @@ struct RenderBufs {
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0
     int *n_big;              // device [2]: [0] splats of the large-rectangle list, [1] long tiles
+    float4 *lrec;            // [3 kcap] splat records in list order (rec0, rec1, rec2 with rec2.w = splat index
+                             // bits), written for the TMA-staged rasterizer variant
     int32_t *big_idx;        // [cap] splats whose tiles a warp counts and emits (k_big_counts, k_big_emit)
     int variant;             // forward rasterizer variant (pixels per thread, batch), see raster_variant_ok
     int variant_bwd;         // backward rasterizer variant
@@ -221,11 +223,16 @@ struct RasterJob {
     float *dimage[MAX_VIEWS];    // forward: dL/dimage out (with targets); backward: read
     float *g9[MAX_VIEWS];        // backward: per-splat sums out
     uint32_t cap[MAX_VIEWS];     // visible capacity (list entries index records below it)
+    const float4 *lrec[MAX_VIEWS];   // records in list order (TMA-staged variant)
+    int *status;                 // device status word (a TMA wait that gave up)
+    uint32_t first_wait;         // polls of each warp's first TMA wait (CULL_WAIT_LIMIT unless a test lowers it)
     int cam0;                    // job view v is camera cam0 + v of the argument block
     int *work;
 };
 
-constexpr int N_RASTER_VARIANTS = 9;
+constexpr int N_RASTER_VARIANTS = 10;
+// The variant whose lists are staged by TMA bulk copies from records in list order.
+constexpr int RASTER_TMA_VARIANT = 9;
 
 // k_lists.cu: rectangles of more tiles than this are counted and emitted by a
 // warp each (the big list the gather fills); smaller ones by a warp's lanes

@@ -238,6 +238,7 @@ static void carve(gs_ctx *c, char *base)
         rb.fix_flag = k.take<uint8_t>(V);
         rb.n_big = k.take<int>(2);
         rb.big_idx = k.take<int32_t>(V);
+        rb.lrec = k.take<float4>(3 * (size_t)K);
         c->imgs[v] = k.take<float>(P);
         c->dimgs[v] = k.take<float>(P);
     }

@@ -922,6 +922,276 @@ __global__ void __launch_bounds__(32 * NW, 4) k_raster_bwd_pairs(const RasterJob
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged warp tiles (variant 9): the arithmetic of variant 7 (one-warp
+// tiles, PPT 1, batches of 32), with each batch of a tile's list staged in
+// shared memory by one 1-D bulk copy (cp.async.bulk) of the records in list
+// order, written after the sort by k_list_records.  Two buffers per warp: the
+// next batch lands while the current one is composited.  Every wait on a copy
+// is bounded: a warp whose copy does not arrive latches GS_ERR_TIMEOUT, lets
+// its copies in flight land and stops.
+
+__global__ void k_list_records(const uint32_t *__restrict__ svals, const int *n_keys_p, int64_t kcap,
+                               const float4 *__restrict__ rec0, const float4 *__restrict__ rec1,
+                               const float4 *__restrict__ rec2, uint32_t cap, float4 *__restrict__ lrec)
+{
+    const int64_t nk = min((int64_t)*n_keys_p, kcap);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = svals[j];
+        float4 a = make_float4(0.f, 0.f, -1.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f), c = b;
+        if (k < cap) {                      // else an empty splat (never for a consistent list)
+            a = rec0[k];
+            b = rec1[k];
+            c = rec2[k];
+            c.w = __uint_as_float(k);
+        }
+        lrec[3 * j] = a;
+        lrec[3 * j + 1] = b;
+        lrec[3 * j + 2] = c;
+    }
+}
+
+template <int BATCH> struct TmaStage {
+    float4 (*buf)[3 * BATCH];
+    uint64_t *bar;
+    uint32_t ph;            // phase parity of each buffer's barrier (bit s)
+    int lane;
+    uint32_t limit;         // polls of the next wait: the job's first-wait limit, then CULL_WAIT_LIMIT
+    __device__ __forceinline__ void issue(const float4 *lrec, uint32_t b0, int cnt, int s)
+    {
+        if (lane == 0) {
+            // generic-proxy reads of this buffer (the warp is past them) before the async-proxy write
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[s], (uint32_t)cnt * 48u);
+            bulk_g2s(buf[s], lrec + 3 * (size_t)b0, (uint32_t)cnt * 48u, &bar[s]);
+        }
+    }
+    // wait for buffer s's copy; false (for the whole warp) if a lane's wait gave up
+    __device__ __forceinline__ bool wait(int s)
+    {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], (ph >> s) & 1u, limit));
+        limit = CULL_WAIT_LIMIT;
+        ph ^= 1u << s;
+        return ok;
+    }
+};
+
+template <int BATCH, int NW>
+__global__ void __launch_bounds__(32 * NW, 5) k_raster_fwd_tma(const RasterJob J, const DevArgs *__restrict__ args,
+                                                               int use_target, float *__restrict__ loss)
+{
+    __shared__ __align__(128) float4 buf_[NW][2][3 * BATCH];
+    __shared__ __align__(8) uint64_t bar_[NW][2];
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    TmaStage<BATCH> S{buf_[wid], bar_[wid], 0u, lane, J.first_wait};
+    if (lane == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    bool dead = false;
+    float loss_part = 0.f;
+    int view, tile;
+    while (!dead && next_item<true>(J, &s_item, view, tile)) {
+        float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view];
+        float *__restrict__ dimage = J.dimage[view];
+        const DevCam &cam = args->cam[J.cam0 + view];
+        const float *target = use_target ? args->target[J.cam0 + view] : nullptr;
+        const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
+        const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+        const int x = tx0 + lane % tw, y = ty0 + lane / tw;
+        const float px = (float)x + 0.5f, pyv = (float)y + 0.5f;
+        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
+        const uint2 rg = J.ranges[view][tile];
+        const float4 *lrec = J.lrec[view];
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        bool live = x < W && y < H;
+        int s = 0;
+        if (rg.x < rg.y) S.issue(lrec, rg.x, min(BATCH, (int)(rg.y - rg.x)), 0);
+        for (uint32_t b = rg.x; b < rg.y; b += BATCH, s ^= 1) {
+            const int cnt = min(BATCH, (int)(rg.y - b));
+            if (!__any_sync(0xffffffffu, live)) {      // done early: the copy of this batch still lands
+                S.wait(s);
+                break;
+            }
+            const bool more = b + BATCH < rg.y;
+            if (more) S.issue(lrec, b + BATCH, min(BATCH, (int)(rg.y - b - BATCH)), s ^ 1);
+            if (!S.wait(s)) {
+                latch(J.status, GS_ERR_TIMEOUT);
+                if (more) mbar_wait_bounded(&S.bar[s ^ 1], (S.ph >> (s ^ 1)) & 1u, CULL_WAIT_LIMIT);
+                dead = true;
+                break;
+            }
+            const float4 *B = S.buf[s];
+            for (int e = 0; e < cnt && live; e++) {
+                const float4 r0 = B[3 * e];
+                if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+                const float dx = __fsub_rn(r0.x, px);
+                if (fabsf(dx) > r0.z) continue;
+                const float4 r1 = B[3 * e + 1];
+                float dy, G;
+                bool cl;
+                const float a = splat_alpha_nb(r0, r1, dx, pyv, dy, G, cl);
+                if (a == 0.f) continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+                if (Tn < T_STOP) {
+                    live = false;
+                    continue;
+                }
+                const float4 c = B[3 * e + 2];
+                const float aT = __fmul_rn(a, T);
+                C0 = __fmaf_rn(c.x, aT, C0);
+                C1 = __fmaf_rn(c.y, aT, C1);
+                C2 = __fmaf_rn(c.z, aT, C2);
+                T = Tn;
+            }
+            __syncwarp();                                // buffer s is read; it may be refilled
+        }
+        if (dead) break;
+        if (x < W && y < H) {
+            const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+            image[pix] = C0;
+            image[HW + pix] = C1;
+            image[2 * HW + pix] = C2;
+            if (cfinal) {
+                cfinal[pix] = C0;
+                cfinal[HW + pix] = C1;
+                cfinal[2 * HW + pix] = C2;
+            }
+            if (target) {
+                const float inv = cam.loss_inv;
+                float d0 = C0 - target[pix], d1 = C1 - target[HW + pix], d2 = C2 - target[2 * HW + pix];
+                dimage[pix] = (d0 > 0.f ? inv : (d0 < 0.f ? -inv : 0.f));
+                dimage[HW + pix] = (d1 > 0.f ? inv : (d1 < 0.f ? -inv : 0.f));
+                dimage[2 * HW + pix] = (d2 > 0.f ? inv : (d2 < 0.f ? -inv : 0.f));
+                loss_part += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * inv;
+            }
+        }
+    }
+    if (use_target) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
+        if (lane == 0 && loss_part != 0.f) atomicAdd(loss, loss_part);
+    }
+}
+
+template <int BATCH, int NW, bool STATS = false>
+__global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, const DevArgs *__restrict__ args,
+                                                           unsigned long long *stats = nullptr)
+{
+    __shared__ __align__(128) float4 buf_[NW][2][3 * BATCH];
+    __shared__ __align__(8) uint64_t bar_[NW][2];
+    __shared__ int s_item;
+    unsigned long long n_sq = 0, n_on = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    TmaStage<BATCH> S{buf_[wid], bar_[wid], 0u, lane, J.first_wait};
+    if (lane == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    bool dead = false;
+    int view, tile;
+    while (!dead && next_item<true>(J, &s_item, view, tile)) {
+        const float *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
+        float *__restrict__ g9 = J.g9[view];
+        const DevCam &cam = args->cam[J.cam0 + view];
+        const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
+        const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
+        const int x = tx0 + lane % tw, y = ty0 + lane / tw;
+        const float px = (float)x + 0.5f, pyv = (float)y + 0.5f;
+        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
+        const uint2 rg = J.ranges[view][tile];
+        const float4 *lrec = J.lrec[view];
+        float T = 1.f, gF = 0.f, gA = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        bool live = x < W && y < H;
+        if (live) {
+            const int64_t HW = (int64_t)W * H, pix = (int64_t)y * W + x;
+            g0 = dimage[pix];
+            g1 = dimage[HW + pix];
+            g2 = dimage[2 * HW + pix];
+            gF = g0 * cfinal[pix] + g1 * cfinal[HW + pix] + g2 * cfinal[2 * HW + pix];
+        }
+        int s = 0;
+        if (rg.x < rg.y) S.issue(lrec, rg.x, min(BATCH, (int)(rg.y - rg.x)), 0);
+        for (uint32_t b = rg.x; b < rg.y; b += BATCH, s ^= 1) {
+            const int cnt = min(BATCH, (int)(rg.y - b));
+            if (!__any_sync(0xffffffffu, live)) {
+                S.wait(s);
+                break;
+            }
+            const bool more = b + BATCH < rg.y;
+            if (more) S.issue(lrec, b + BATCH, min(BATCH, (int)(rg.y - b - BATCH)), s ^ 1);
+            if (!S.wait(s)) {
+                latch(J.status, GS_ERR_TIMEOUT);
+                if (more) mbar_wait_bounded(&S.bar[s ^ 1], (S.ph >> (s ^ 1)) & 1u, CULL_WAIT_LIMIT);
+                dead = true;
+                break;
+            }
+            const float4 *B = S.buf[s];
+            for (int e = 0; e < cnt; e++) {
+                const float4 r0 = B[3 * e];
+                if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+                const float dx = __fsub_rn(r0.x, px);
+                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                bool contrib = false;
+                const float4 r1 = B[3 * e + 1];
+                if (live && fabsf(dx) <= r0.z) {
+                    float dy, G;
+                    bool cl;
+                    const float a = splat_alpha_nb(r0, r1, dx, pyv, dy, G, cl);
+                    if (STATS) n_sq += fabsf(dy) <= r0.z ? 1 : 0;
+                    if (a != 0.f) {
+                        const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+                        if (Tn < T_STOP) {
+                            live = false;
+                        } else {
+                            if (STATS) n_on++;
+                            contrib = true;
+                            const float4 c = B[3 * e + 2];
+                            const float aT = __fmul_rn(a, T);
+                            const float gc = __fmaf_rn(g2, c.z, __fmaf_rn(g1, c.y, __fmul_rn(g0, c.x)));
+                            gA = __fmaf_rn(aT, gc, gA);
+                            const float dLda = __fmaf_rn(T, gc, -__fdividef(__fsub_rn(gF, gA), __fsub_rn(1.f, a)));
+                            v[6] = __fmul_rn(g0, aT);
+                            v[7] = __fmul_rn(g1, aT);
+                            v[8] = __fmul_rn(g2, aT);
+                            if (!cl) {                       // the 0.999 clamp has no derivative
+                                const float ds = __fmul_rn(-a, dLda);
+                                v[5] = __fmul_rn(G, dLda);
+                                const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
+                                v[0] = sdx;
+                                v[1] = sdy;
+                                v[2] = __fmul_rn(sdx, dx);
+                                v[3] = __fmul_rn(sdx, dy);
+                                v[4] = __fmul_rn(sdy, dy);
+                            }
+                            T = Tn;
+                        }
+                    }
+                }
+                emit_splat(g9, __float_as_uint(B[3 * e + 2].w), r1.x, r1.y, r1.z, contrib, v, lane);
+            }
+            __syncwarp();
+        }
+        if (dead) break;
+    }
+    if (STATS) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            n_sq += __shfl_xor_sync(0xffffffffu, n_sq, o);
+            n_on += __shfl_xor_sync(0xffffffffu, n_on, o);
+        }
+        if (lane == 0) {
+            atomicAdd(stats, n_sq);
+            atomicAdd(stats + 1, n_on);
+        }
+    }
+}
+
 typedef void (*RasterFwdFn)(const RasterJob, const DevArgs *, int, float *);
 typedef void (*RasterBwdFn)(const RasterJob, const DevArgs *, unsigned long long *);
 
@@ -939,7 +1209,8 @@ static RasterFwdFn fwd_variant(int v)
     case 5: return k_raster_fwd<4, 256>;
     case 6: return k_raster_fwd<1, 64, 4>;
     case 7: return k_raster_fwd<1, 32, 8>;
-    default: return k_raster_fwd_pairs<32, 8>;
+    case 8: return k_raster_fwd_pairs<32, 8>;
+    default: return k_raster_fwd_tma<32, 8>;
     }
 }
 
@@ -963,12 +1234,14 @@ static RasterBwdFn bwd_variant(int v, bool stats)
     case 14: return k_raster_bwd<1, 32, false, 8>;
     case 15: return k_raster_bwd<1, 32, true, 8>;
     case 16: return k_raster_bwd_pairs<32, 8, false>;
-    default: return k_raster_bwd_pairs<32, 8, true>;
+    case 17: return k_raster_bwd_pairs<32, 8, true>;
+    case 18: return k_raster_bwd_tma<32, 8, false>;
+    default: return k_raster_bwd_tma<32, 8, true>;
     }
 }
 
 // Warps per block of a warp-tile variant, else 0.
-static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8) ? 8 : 0; }
+static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8 || v == 9) ? 8 : 0; }
 
 bool raster_variant_ok(int v, int tile_w, int tile_h)
 {
@@ -1260,6 +1533,9 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     rb.sorted_keys = rb.tk[1];
     rb.sorted_vals = rb.tv[1];
     rb.tiles = tiles;
+    if (rb.variant == RASTER_TMA_VARIANT || rb.variant_bwd == RASTER_TMA_VARIANT)
+        k_list_records<<<w.grid(rb.kcap, 256, 8), 256, 0, s>>>(rb.sorted_vals, rb.n_keys, rb.kcap, rb.rec0, rb.rec1,
+                                                              rb.rec2, (uint32_t)rb.cap, rb.lrec);
 }
 
 static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
@@ -1278,6 +1554,7 @@ static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
         J.cfinal[v] = rb.cfinal;
         J.g9[v] = rb.g9;
         J.cap[v] = (uint32_t)rb.cap;
+        J.lrec[v] = rb.lrec;
     }
     J.work = work;
     return J;
@@ -1301,6 +1578,8 @@ void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, co
 {
     RasterJob J = make_job(n_views, rbs, work);
     J.cam0 = cam0;
+    J.status = w.status;
+    J.first_wait = w.cull_first_wait;
     for (int v = 0; v < n_views; v++) {
         J.image[v] = images[v];
         if (images[v] == rbs[v]->cfinal) J.cfinal[v] = nullptr;
@@ -1328,6 +1607,8 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 {
     prepare_view(sc, args, view, ids, n_vis, rb, cam, w, s);
     RasterJob J = single_view_job(view, rb, work);
+    J.status = w.status;
+    J.first_wait = w.cull_first_wait;
     for (int v = 0; v <= view; v++) {
         J.image[v] = image;
         J.cfinal[v] = image == rb.cfinal ? nullptr : rb.cfinal;
@@ -1348,6 +1629,8 @@ void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, c
     }
     RasterJob J = make_job(n_views, rbs, work);
     J.cam0 = cam0;
+    J.status = w.status;
+    J.first_wait = w.cull_first_wait;
     for (int v = 0; v < n_views; v++) J.dimage[v] = const_cast<float *>(dimages[v]);
     const RenderBufs &rb0 = *rbs[0];
     const RasterShape sh = raster_shape(rb0.variant_bwd, J.tile_ofs[n_views], cams[0].tile_w, cams[0].tile_h, w);
@@ -1392,6 +1675,8 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
     const int cap = (int)rb.cap;
     launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
     RasterJob J = single_view_job(view, rb, work);
+    J.status = w.status;
+    J.first_wait = w.cull_first_wait;
     for (int v = 0; v <= view; v++) J.dimage[v] = const_cast<float *>(dimage);
     const RasterShape sh = raster_shape(rb.variant_bwd, rb.tiles, cam.tile_w, cam.tile_h, w);
     cudaMemsetAsync(work, 0, sizeof(int), s);

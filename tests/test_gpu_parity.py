@@ -860,3 +860,30 @@ def test_cull_timeout_is_reported_and_the_context_recovers(gs):
     ids, nv = ctx.cull(scene, cam)
     ctx.sync_status()
     assert torch.equal(ids[:int(nv.item())], ref)
+
+
+def test_raster_tma_timeout_is_reported(gs):
+    """The TMA-staged rasterizer (variant 9) bounds its waits on its own bulk
+    copies the same way: with the first wait's limit at 0 every warp gives up,
+    lets its copies land and returns; GS_ERR_TIMEOUT is latched with no fault,
+    and with the default limit back the render equals variant 7's bit for bit."""
+    from paper_2509_15645_b300 import _lib
+    P, cam, deg, _ = _case("tile8x4_ragged")
+    camf = cam_f32(cam)
+    n = P.shape[1]
+    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=(8, 4))
+    scene = gs.GaussianScene(P, deg)
+    ids, nv = ctx.cull(scene, camf)
+    ctx.set_raster_variant(7)
+    ref = ctx.render_fwd(scene, camf, ids, nv).clone()
+    ctx.sync_status()
+    ctx.set_raster_variant(9)
+    ctx.set_cull_wait_limit(0)
+    with pytest.raises(_lib.GsError) as e:
+        ctx.render_fwd(scene, camf, ids, nv)       # the cull of the first line ran before the limit changed
+        ctx.sync_status()
+    assert e.value.status == _lib.GS_ERR_TIMEOUT
+    ctx.set_cull_wait_limit(1 << 24)
+    img = ctx.render_fwd(scene, camf, ids, nv)
+    ctx.sync_status()
+    assert torch.equal(img, ref)
