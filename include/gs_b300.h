@@ -364,6 +364,30 @@ GS_API gs_status gs_set_raster_variant(gs_ctx *ctx, int32_t variant);
 GS_API gs_status gs_raster_pair_counts(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, uint64_t *counts,
                                        void *stream);
 
+/* Densification on deferred optimizer state (§2.4 step 7 with §4.3; the
+ * paper leaves the rules to 3DGS).  For Gaussian i of `src` (resident, with
+ * optimizer state, after src->step steps): g = grad_accum[i] / denom[i] (0
+ * where denom[i] <= 0), the mean view-space gradient norm the caller
+ * accumulated; the current (caught-up) values decide: g >= grad_threshold
+ * clones it when its largest scale is at most percent_dense * extent and
+ * splits it into two children otherwise (children: scales / 1.6, means mu +
+ * R(q) (s * z_j) with z_j = normals[(j * 3 + a) * n + i], a = 0..2, j = 0, 1,
+ * standard normal values the caller draws); every Gaussian whose opacity
+ * sigmoid(logit) is below min_opacity is dropped together with its copies.
+ * A cloned row is caught up (its moments decayed over its deferred steps, its
+ * counter 0) and its clone starts with zero moments; split rows are replaced
+ * by their children (zero moments, counter 0); every other row keeps its
+ * stored values, restore directions and counter.  `dst` (device arrays of the
+ * same degree and precision, rdir present iff src has it, capacity
+ * dst->pitch) receives the survivors in their order, then the clones, then
+ * the first children, then the second children; dst->n and dst->step are set.
+ * Synchronises the stream once (to read the counts).  GS_ERR_CAPACITY, with
+ * dst->n set to the count needed and nothing written, if dst->pitch is too
+ * small.  grad_accum, denom: device fp32 [n]; normals: device fp32 [2][3][n]. */
+GS_API gs_status gs_densify(gs_ctx *ctx, const gs_scene *src, gs_scene *dst, const gs_adam_cfg *adam,
+                            const float *grad_accum, const float *denom, const float *normals, float extent,
+                            float grad_threshold, float percent_dense, float min_opacity, void *stream);
+
 /* Number of kernel launches in the captured gs_step graph (0 before the first
  * gs_step). */
 GS_API gs_status gs_step_kernel_count(const gs_ctx *ctx, int32_t *kernels);

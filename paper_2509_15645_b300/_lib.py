@@ -69,6 +69,8 @@ EXPORTS = {
     "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
                                 c_vp, c_vp]),
     "gs_set_cull_wait_limit": (c_i32, [c_vp, C.c_uint32]),
+    "gs_densify": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Scene), C.POINTER(AdamCfg), c_vp, c_vp, c_vp, c_f32, c_f32,
+                           c_f32, c_f32, c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),

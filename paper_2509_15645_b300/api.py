@@ -414,6 +414,29 @@ class Context:
         conv = [None if t < 0 else t for t in ms]
         return (chosen[0], chosen[1]), conv[:V], conv[V:]
 
+    def densify(self, scene: GaussianScene, adam, grad_accum, denom, normals, extent, grad_threshold=2e-4,
+                percent_dense=0.01, min_opacity=0.005, capacity=None, stream=None):
+        """Densification on deferred state (gs_densify): clone / split / prune
+        of ``scene`` into a new GaussianScene (returned), from the accumulated
+        view-space gradient norms ``grad_accum`` / ``denom`` (device fp32 [n])
+        and standard-normal ``normals`` (device fp32 [2][3][n]) for the
+        children of splits."""
+        cap = int(capacity or 2 * scene.n)
+        for _ in range(2):
+            dst = GaussianScene(torch.zeros(scene.D, cap), scene.sh_degree, device=self.device,
+                                with_rdir=scene.rdir_geo is not None, precision=scene.precision)
+            sc, dc = scene.struct(), dst.struct()
+            st = self.lib.gs_densify(self.h, C.byref(sc), C.byref(dc), C.byref(adam), _ptr(grad_accum.contiguous()),
+                                     _ptr(denom.contiguous()), _ptr(normals.contiguous()), float(extent),
+                                     float(grad_threshold), float(percent_dense), float(min_opacity), _stream(stream))
+            if st == L.GS_ERR_CAPACITY and dc.n > cap:
+                cap = int(dc.n)
+                continue
+            self._check(st, "gs_densify")
+            dst.n, dst.step = int(dc.n), int(dc.step)
+            return dst
+        raise L.GsError(L.GS_ERR_CAPACITY, "gs_densify")
+
     def set_cull_wait_limit(self, first_wait):
         """Polls of each cull block's first wait on its own copies before it
         gives up and latches GS_ERR_TIMEOUT (default 2^24; failure-path tests)."""

@@ -173,6 +173,15 @@ void launch_materialize(const SceneView &sc, const DevArgs *args, float *w_out, 
 void launch_grad_scatter(const int32_t *ids, const int *n_dev, int cap, const float *gc, int64_t gcap, int D,
                          float *gfull, int64_t pitch, Work &w, cudaStream_t s);
 
+// k_densify.cu: clone / split / prune on deferred state.  densify_count
+// classifies every Gaussian (masks[0..2]: survivor, clone, split; their word
+// prefixes and counts); densify_write writes the new scene's rows.
+gs_status densify_count(const SceneView &sc, const DevArgs *args, const float *accum, const float *denom,
+                        float grad_threshold, float scale_limit, float min_opacity, uint32_t *const masks[3],
+                        uint32_t *const prefixes[3], uint32_t *const chunks[3], int *counts, Work &w, cudaStream_t s);
+void densify_write(const SceneView &sc, const SceneView &dst, const DevArgs *args, const float *normals,
+                   uint32_t *const masks[3], uint32_t *const prefixes[3], const int *counts, Work &w, cudaStream_t s);
+
 // k_render.cu
 // Per-splat record of the rasterizer backward's sums: d/d(mean2d x, y), d/d(conic
 // A, B, C), d/d(opacity), d/d(rgb), padded to 12 floats so that a warp adds

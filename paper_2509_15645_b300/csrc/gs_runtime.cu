@@ -993,6 +993,66 @@ gs_status gs_set_cull_wait_limit(gs_ctx *c, uint32_t first_wait)
     return GS_OK;
 }
 
+gs_status gs_densify(gs_ctx *c, const gs_scene *src, gs_scene *dst, const gs_adam_cfg *adam, const float *grad_accum,
+                     const float *denom, const float *normals, float extent, float grad_threshold,
+                     float percent_dense, float min_opacity, void *stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    SceneView sv, dv;
+    gs_status st = scene_view(c, src, true, sv);
+    if (st) return st;
+    if (!valid_adam(adam)) return fail(c, GS_ERR_INVALID_ARG, "invalid adam config");
+    sv.opt = adam->optimizer;
+    if (src->tier != GS_TIER_DEVICE) return fail(c, GS_ERR_INVALID_ARG, "densification takes a resident scene");
+    if (!dst || !grad_accum || !denom || !normals) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    if (!(extent > 0.f) || !std::isfinite(extent) || !std::isfinite(grad_threshold) || !(percent_dense >= 0.f) ||
+        !std::isfinite(min_opacity))
+        return fail(c, GS_ERR_INVALID_ARG, "invalid densification thresholds");
+    if (dst->sh_degree != src->sh_degree || dst->precision != src->precision || dst->tier != GS_TIER_DEVICE ||
+        !dst->geo || !dst->sh || !dst->m || !dst->v || !dst->counter || (dst->pitch & 3) || dst->pitch <= 0 ||
+        ((src->rdir != nullptr) != (dst->rdir != nullptr)))
+        return fail(c, GS_ERR_INVALID_ARG, "destination scene: same degree, precision and planes, resident");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevArgs a{};
+    a.lut = make_lut(adam, src->step + 1, true);
+    set_args(c, SLOT_ADAM, a, s);
+    uint32_t *masks[3] = {c->amask, c->umask, c->mask};
+    uint32_t *prefixes[3] = {c->aprefix, c->wprefix, c->vprefix[0]};
+    uint32_t *chunks[3] = {c->achunk, c->uchunk, c->chunk};
+    densify_count(sv, c->args + SLOT_ADAM, grad_accum, denom, grad_threshold, percent_dense * extent, min_opacity,
+                  masks, prefixes, chunks, c->n_tmp, c->w, s);
+    int counts[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(counts, c->n_tmp, sizeof(counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check(c, "gs_densify counts");
+    const int64_t n_out = (int64_t)counts[0] + counts[1] + 2ll * counts[2];
+    dst->n = n_out;
+    dst->step = src->step;
+    if (n_out > dst->pitch || n_out >= (1ll << 31))
+        return fail(c, GS_ERR_CAPACITY, "densified scene has %lld Gaussians, destination pitch %lld",
+                    (long long)n_out, (long long)dst->pitch);
+    if (n_out == 0) return cuda_check(c, "gs_densify");
+    // the destination as the kernels address it (resident planes; it may hold
+    // more Gaussians than the context's capacity, which only bounds the source)
+    const int64_t eb = elem_bytes(dst->precision), P = dst->pitch;
+    dv = sv;
+    dv.geo = dst->geo;
+    dv.m = dst->m;
+    dv.v = dst->v;
+    dv.rdir = dst->rdir;
+    dv.counter = dst->counter;
+    dv.n = n_out;
+    dv.pitch = P;
+    dv.sh.w = dst->sh;
+    dv.sh.m = (char *)dst->m + N_GEO * P * eb;
+    dv.sh.v = (char *)dst->v + N_GEO * P * eb;
+    dv.sh.rdir = dst->rdir ? (char *)dst->rdir + N_GEO * P * 4 : nullptr;
+    dv.sh.ppitch = P;
+    dv.sh.slot = nullptr;
+    densify_write(sv, dv, c->args + SLOT_ADAM, normals, masks, prefixes, c->n_tmp, c->w, s);
+    return cuda_check(c, "gs_densify");
+}
+
 gs_status gs_step_kernel_count(const gs_ctx *c, int32_t *kernels)
 {
     if (!c || !kernels) return GS_ERR_INVALID_ARG;
