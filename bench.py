@@ -276,8 +276,10 @@ def run_ours(args):
     max_vis = int(min(N, max(0.6 * N if not args.density_of else 0, 3_000_000 * area * (args.density_of or N) / 10e6)))
     max_vis = int(min(N, max(max_vis, 1_000_000)))
     max_keys = int(min(160_000_000, max(16_000_000, 20 * max_vis)))
+    # list-order records (48 B per key of capacity) let the autotuner weigh the
+    # TMA-staged rasterizer variant; not under an HBM budget
     ctx_kw = dict(max_gaussians=N, max_visible=max_vis, max_keys=max_keys, max_width=W, max_height=H, tile=tile,
-                  max_views=vps, max_sh_degree=deg)
+                  max_views=vps, max_sh_degree=deg, list_records=0 if args.budget_gb else 1)
     # HBM budget: state that does not fit goes to the host tier (SH planes and
     # their optimizer state in pinned host memory, streamed by gs_step)
     tier, stage_chunks, plan, eb = gs.GS_TIER_DEVICE, 0, None, 4

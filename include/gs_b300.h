@@ -190,6 +190,9 @@ typedef struct {
                                 buffers, gradients summed over the rounds, so the working set is bounded by one
                                 round (a view split into regions, §4.4, with render_views = 1 holds one region's
                                 buffers at a time); the cull buffers (masks, ids) are kept for max_views views */
+    int32_t list_records;    /* 1: also keep each view's splat records in list order (48 bytes per key of
+                                capacity), which the TMA-staged rasterizer variant 9 needs; 0: variant 9 is not
+                                available on this context */
 } gs_config;
 
 /* ------------------------------------------------------------------ context */
@@ -335,9 +338,10 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
  * only): one tile per warp, 4 warps per block with batches of 64 records, or
  * 8 warps with batches of 32.  v = 8 (32-pixel tiles only): as 7, walking the
  * list two entries at a time with paired FP32 (f32x2) arithmetic.  v = 9
- * (32-pixel tiles only): as 7, each batch staged in shared memory by one TMA
- * bulk copy of the tile's records written in list order after the sort (48
- * bytes per key of extra traffic).  Every variant computes the same image bit
+ * (32-pixel tiles, contexts with list_records only): as 7, each batch staged
+ * in shared memory by one TMA bulk copy of the tile's records, written in
+ * list order by the first rasterizer pass that uses them (48 bytes per key
+ * of extra traffic).  Every variant computes the same image bit
  * for bit; they differ only in speed. */
 #define GS_RASTER_VARIANTS 10
 

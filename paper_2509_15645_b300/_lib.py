@@ -41,7 +41,7 @@ class Config(C.Structure):
     _fields_ = [("max_gaussians", c_i64), ("max_visible", c_i64), ("max_keys", c_i64), ("max_width", c_i32),
                 ("max_height", c_i32), ("tile_w", c_i32), ("tile_h", c_i32), ("max_views", c_i32),
                 ("max_sh_degree", c_i32), ("stage_chunks", c_i64), ("chunk_shift", c_i32), ("stage_elem_bytes", c_i32),
-                ("render_views", c_i32)]
+                ("render_views", c_i32), ("list_records", c_i32)]
 
 
 EXPORTS = {

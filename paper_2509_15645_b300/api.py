@@ -216,10 +216,11 @@ class Context:
     """One gs_ctx: scratch workspace (a torch allocation) and the hot-path calls."""
 
     def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
-                 max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0):
+                 max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0,
+                 list_records=0):
         self.lib = L.load()
         cfg = self._config(max_gaussians, max_visible, max_keys, max_width, max_height, tile, max_views,
-                           max_sh_degree, stage_chunks, chunk_shift, stage_elem_bytes, render_views)
+                           max_sh_degree, stage_chunks, chunk_shift, stage_elem_bytes, render_views, list_records)
         self.cfg = cfg
         nb = C.c_size_t(0)
         self._check(self.lib.gs_workspace_size(C.byref(cfg), C.byref(nb)), "workspace size")
@@ -232,9 +233,11 @@ class Context:
 
     @staticmethod
     def _config(max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
-                max_sh_degree=3, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0):
+                max_sh_degree=3, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0,
+                list_records=0):
         cfg = L.Config()
         cfg.render_views = int(render_views)
+        cfg.list_records = int(list_records)
         cfg.stage_chunks, cfg.chunk_shift = int(stage_chunks), int(chunk_shift)
         cfg.stage_elem_bytes = int(stage_elem_bytes)
         cfg.max_gaussians, cfg.max_visible, cfg.max_keys = int(max_gaussians), int(max_visible), int(max_keys)

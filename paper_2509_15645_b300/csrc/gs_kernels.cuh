@@ -249,7 +249,8 @@ constexpr int RASTER_TMA_VARIANT = 9;
 constexpr int BIG_RECT = 32;
 void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBufs &rb, int tiles, Work &w,
                       cudaStream_t s);
-bool raster_variant_ok(int v, int tile_w, int tile_h);
+// has_records: the context keeps list-order records (variant 9 needs them).
+bool raster_variant_ok(int v, int tile_w, int tile_h, bool has_records);
 
 void render_forward(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
                     RenderBufs &rb, const DevCam &cam_host, float *image, bool use_target, float *dimage,

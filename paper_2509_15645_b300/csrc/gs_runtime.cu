@@ -160,7 +160,7 @@ static bool valid_cfg(const gs_config *c)
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h && c->stage_chunks >= 0 &&
            (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20)) &&
            (c->stage_elem_bytes == 0 || c->stage_elem_bytes == 2 || c->stage_elem_bytes == 4) &&
-           c->render_views >= 0 && c->render_views <= c->max_views;
+           c->render_views >= 0 && c->render_views <= c->max_views && (c->list_records == 0 || c->list_records == 1);
 }
 
 static int stage_eb(const gs_config &g) { return g.stage_elem_bytes ? g.stage_elem_bytes : 4; }
@@ -238,7 +238,7 @@ static void carve(gs_ctx *c, char *base)
         rb.fix_flag = k.take<uint8_t>(V);
         rb.n_big = k.take<int>(2);
         rb.big_idx = k.take<int32_t>(V);
-        rb.lrec = k.take<float4>(3 * (size_t)K);
+        rb.lrec = g.list_records ? k.take<float4>(3 * (size_t)K) : nullptr;
         c->imgs[v] = k.take<float>(P);
         c->dimgs[v] = k.take<float>(P);
     }
@@ -504,7 +504,7 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
     c->w.status = &c->cnt->status;
     c->w.num_sms = c->num_sms;
     c->rbs[0].variant = 1;
-    if (!raster_variant_ok(c->rbs[0].variant, cfg->tile_w, cfg->tile_h)) c->rbs[0].variant = 0;
+    if (!raster_variant_ok(c->rbs[0].variant, cfg->tile_w, cfg->tile_h, cfg->list_records)) c->rbs[0].variant = 0;
     c->rbs[0].variant_bwd = c->rbs[0].variant;
     c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
     if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
@@ -848,7 +848,8 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
 
 gs_status gs_set_raster_variant(gs_ctx *c, int32_t variant)
 {
-    if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h)) return GS_ERR_INVALID_ARG;
+    if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h, c->cfg.list_records))
+        return GS_ERR_INVALID_ARG;
     c->rbs[0].variant = c->rbs[0].variant_bwd = variant;
     return GS_OK;
 }
@@ -879,7 +880,7 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
     gs_status res = GS_OK;
     for (int v = 0; v < N_RASTER_VARIANTS && res == GS_OK; v++) {
         if (ms_out) ms_out[v] = ms_out[N_RASTER_VARIANTS + v] = -1.f;
-        if (!raster_variant_ok(v, c->cfg.tile_w, c->cfg.tile_h)) continue;
+        if (!raster_variant_ok(v, c->cfg.tile_w, c->cfg.tile_h, c->cfg.list_records)) continue;
         c->rbs[0].variant = c->rbs[0].variant_bwd = v;
         float fbest = 1e30f, bbest = 1e30f;
         for (int rep = 0; rep < 4; rep++) {
@@ -887,9 +888,13 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
             render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], false, nullptr,
                            nullptr, c->w, s, c->work);
             cudaEventRecord(e1, s);
-            // the rendered image itself serves as a dense dL/dimage
+            // the rendered image itself serves as a dense dL/dimage; the TMA-staged
+            // backward is timed as after another forward variant, writing its
+            // list-order records itself
+            if (v == RASTER_TMA_VARIANT) c->rbs[0].variant = 0;
             render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u,
                             c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s, c->work);
+            c->rbs[0].variant = v;
             cudaEventRecord(e2, s);
             if (cudaEventSynchronize(e2) != cudaSuccess) {
                 res = cuda_check(c, "gs_autotune");

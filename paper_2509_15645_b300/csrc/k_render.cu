@@ -1243,9 +1243,10 @@ static RasterBwdFn bwd_variant(int v, bool stats)
 // Warps per block of a warp-tile variant, else 0.
 static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8 || v == 9) ? 8 : 0; }
 
-bool raster_variant_ok(int v, int tile_w, int tile_h)
+bool raster_variant_ok(int v, int tile_w, int tile_h, bool has_records)
 {
     if (v < 0 || v >= N_RASTER_VARIANTS) return false;
+    if (v == RASTER_TMA_VARIANT && !has_records) return false;
     if (warp_tile_warps(v)) return tile_w * tile_h == 32;
     const int ppt = 1 << (v >> 1);
     const int threads = tile_w * tile_h / ppt;
@@ -1533,9 +1534,7 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     rb.sorted_keys = rb.tk[1];
     rb.sorted_vals = rb.tv[1];
     rb.tiles = tiles;
-    if (rb.variant == RASTER_TMA_VARIANT || rb.variant_bwd == RASTER_TMA_VARIANT)
-        k_list_records<<<w.grid(rb.kcap, 256, 8), 256, 0, s>>>(rb.sorted_vals, rb.n_keys, rb.kcap, rb.rec0, rb.rec1,
-                                                              rb.rec2, (uint32_t)rb.cap, rb.lrec);
+
 }
 
 static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
@@ -1573,9 +1572,21 @@ static RasterShape raster_shape(int v, int items, int tile_w, int tile_h, const 
     return {std::max(1, std::min(items, w.num_sms * 32)), tile_w * tile_h / ppt};
 }
 
+// The list-order records of a view, written by the first rasterizer pass that
+// stages from them (the forward when it is variant 9, else the backward), so
+// their cost counts toward the variant that uses them.
+static void list_records(RenderBufs &rb, Work &w, cudaStream_t s)
+{
+    if (!rb.lrec) return;
+    k_list_records<<<w.grid(rb.kcap, 256, 8), 256, 0, s>>>(rb.sorted_vals, rb.n_keys, rb.kcap, rb.rec0, rb.rec1, rb.rec2,
+                                                          (uint32_t)rb.cap, rb.lrec);
+}
+
 void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
                     bool use_target, float *const *dimages, float *loss, int *work, Work &w, cudaStream_t s, int cam0)
 {
+    if (rbs[0]->variant == RASTER_TMA_VARIANT)
+        for (int v = 0; v < n_views; v++) list_records(*rbs[v], w, s);
     RasterJob J = make_job(n_views, rbs, work);
     J.cam0 = cam0;
     J.status = w.status;
@@ -1606,6 +1617,7 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
                     Work &w, cudaStream_t s, int *work)
 {
     prepare_view(sc, args, view, ids, n_vis, rb, cam, w, s);
+    if (rb.variant == RASTER_TMA_VARIANT) list_records(rb, w, s);
     RasterJob J = single_view_job(view, rb, work);
     J.status = w.status;
     J.first_wait = w.cull_first_wait;
@@ -1623,6 +1635,8 @@ void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, c
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
                      unsigned long long *stats, int cam0)
 {
+    if (rbs[0]->variant_bwd == RASTER_TMA_VARIANT && rbs[0]->variant != RASTER_TMA_VARIANT)
+        for (int v = 0; v < n_views; v++) list_records(*rbs[v], w, s);
     for (int v = 0; v < n_views; v++) {
         const int cap = (int)rbs[v]->cap;
         launch_zero_rows(rbs[v]->g9, G9_STRIDE, cap, n_vis[v], cap, w, s, true);
@@ -1673,6 +1687,7 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
                      int *work, unsigned long long *stats)
 {
     const int cap = (int)rb.cap;
+    if (rb.variant_bwd == RASTER_TMA_VARIANT && rb.variant != RASTER_TMA_VARIANT) list_records(rb, w, s);
     launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, s, true);
     RasterJob J = single_view_job(view, rb, work);
     J.status = w.status;

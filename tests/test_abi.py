@@ -206,3 +206,7 @@ def test_render_rounds_bound_the_workspace(lib):
     for bad in (3, -1):
         with pytest.raises(_lib.GsError):
             api.Context.workspace_bytes(**kw, render_views=bad)
+    # list-order records: 3 float4 per key of capacity and view
+    assert api.Context.workspace_bytes(**kw, list_records=1) - both >= 2 * 48 * kw["max_keys"]
+    with pytest.raises(_lib.GsError):
+        api.Context.workspace_bytes(**kw, list_records=2)

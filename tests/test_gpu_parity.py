@@ -23,9 +23,10 @@ def gs():
     return gs
 
 
-def make_ctx(gs, n, W, H, deg=3, tile=(16, 16), max_vis=None, max_keys=None, views=1):
+def make_ctx(gs, n, W, H, deg=3, tile=(16, 16), max_vis=None, max_keys=None, views=1, list_records=0):
     return gs.Context(max_gaussians=n, max_visible=max_vis or n, max_keys=max_keys or (64 * n + 4096),
-                      max_width=W, max_height=H, tile=tile, max_views=views, max_sh_degree=deg)
+                      max_width=W, max_height=H, tile=tile, max_views=views, max_sh_degree=deg,
+                      list_records=list_records)
 
 
 def _case(name):
@@ -234,7 +235,7 @@ def test_raster_variants_agree(gs, orc, name, tile):
     P, cam, deg, _ = _case(name)
     camf = cam_f32(cam)
     n, D = P.shape[1], P.shape[0]
-    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=tile)
+    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=tile, list_records=1)
     scene = gs.GaussianScene(P, deg)
     ids, nv = ctx.cull(scene, camf)
     r = orc.render(f32(P), deg, camf, tile)
@@ -258,6 +259,8 @@ def test_raster_variants_agree(gs, orc, name, tile):
         errs = {k: rel_group_error(g_gpu, g_ref, sl) for k, sl in GROUPS.items() if g_ref[sl].size}
         assert max(errs.values()) <= 1e-4, (v, errs)
     assert tried >= 2
+    if tile[0] * tile[1] == 32:
+        assert tried >= 5                    # the warp-tile variants 6-9 among them
     for im in images[1:]:
         np.testing.assert_array_equal(im, images[0])
     (vf, vb), ms_f, ms_b = ctx.autotune(scene, camf)
@@ -871,7 +874,7 @@ def test_raster_tma_timeout_is_reported(gs):
     P, cam, deg, _ = _case("tile8x4_ragged")
     camf = cam_f32(cam)
     n = P.shape[1]
-    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=(8, 4))
+    ctx = make_ctx(gs, n, camf.width, camf.height, deg=3, tile=(8, 4), list_records=1)
     scene = gs.GaussianScene(P, deg)
     ids, nv = ctx.cull(scene, camf)
     ctx.set_raster_variant(7)
