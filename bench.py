@@ -437,8 +437,9 @@ def run_ours(args):
         else:   # the autotuner renders through the resident path
             variant, variant_ms = (1, 1), {}
         if args.raster_variant is not None:
-            ctx.set_raster_variant(args.raster_variant)
-            variant = (args.raster_variant, args.raster_variant)
+            fb = [int(x) for x in str(args.raster_variant).split(",")]
+            variant = (fb[0], fb[-1])
+            ctx.set_raster_variant(variant[0], variant[1])
         ms_total, spans, clk, staged = timed_steps(sc)
         stats = []
         ctx.timing_enable(tcap)
@@ -898,7 +899,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=None,
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
     ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
-    ap.add_argument("--raster-variant", type=int, default=None, help="pin a rasterizer variant instead of the autotuned one")
+    ap.add_argument("--raster-variant", default=None,
+                    help="pin the rasterizer variant instead of the autotuned one: V, or F,B for forward and backward")
     ap.add_argument("--no-extra-forms", dest="extra_forms", action="store_false",
                     help="skip the batched-bf16 and 40M host-tier sub-records of the default line")
     ap.add_argument("--split-demo", action="store_true",

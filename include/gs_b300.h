@@ -360,6 +360,10 @@ GS_API gs_status gs_autotune(gs_ctx *ctx, const gs_scene *scene, const gs_camera
  * tile shape does not allow it. */
 GS_API gs_status gs_set_raster_variant(gs_ctx *ctx, int32_t variant);
 
+/* Select the forward and the backward rasterizer variant separately (as the
+ * autotuner does); GS_ERR_INVALID_ARG if the context does not allow either. */
+GS_API gs_status gs_set_raster_variants(gs_ctx *ctx, int32_t fwd, int32_t bwd);
+
 /* Work counts of the rasterizer backward for one view (benchmarks): renders
  * forward and backward once (the rendered image as dL/dimage) with a counting
  * instance of the backward kernel and writes counts[0] = (pixel, splat) pairs

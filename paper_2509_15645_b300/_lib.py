@@ -66,6 +66,7 @@ EXPORTS = {
     "gs_step_kernel_count": (c_i32, [c_vp, C.POINTER(c_i32)]),
     "gs_autotune": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_i32), C.POINTER(c_f32), c_vp]),
     "gs_set_raster_variant": (c_i32, [c_vp, c_i32]),
+    "gs_set_raster_variants": (c_i32, [c_vp, c_i32, c_i32]),
     "gs_cull_noalloc": (c_i32, [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32, c_vp, c_vp,
                                 c_vp, c_vp]),
     "gs_set_cull_wait_limit": (c_i32, [c_vp, C.c_uint32]),

@@ -445,8 +445,12 @@ class Context:
         gives up and latches GS_ERR_TIMEOUT (default 2^24; failure-path tests)."""
         self._check(self.lib.gs_set_cull_wait_limit(self.h, int(first_wait)), "gs_set_cull_wait_limit")
 
-    def set_raster_variant(self, v):
-        self._check(self.lib.gs_set_raster_variant(self.h, int(v)), "gs_set_raster_variant")
+    def set_raster_variant(self, v, bwd=None):
+        """Pin the rasterizer variant (forward and backward, or ``bwd`` apart)."""
+        if bwd is None:
+            self._check(self.lib.gs_set_raster_variant(self.h, int(v)), "gs_set_raster_variant")
+        else:
+            self._check(self.lib.gs_set_raster_variants(self.h, int(v), int(bwd)), "gs_set_raster_variants")
 
     def timing_enable(self, max_steps):
         self._check(self.lib.gs_timing_enable(self.h, int(max_steps)), "gs_timing_enable")

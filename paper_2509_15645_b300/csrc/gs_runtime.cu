@@ -846,6 +846,18 @@ gs_status gs_timing_read(gs_ctx *c, float *ms_out, int32_t max_steps, int32_t *s
     return GS_OK;
 }
 
+gs_status gs_set_raster_variants(gs_ctx *c, int32_t fwd, int32_t bwd)
+{
+    if (!c || !raster_variant_ok(fwd, c->cfg.tile_w, c->cfg.tile_h, c->cfg.list_records) ||
+        !raster_variant_ok(bwd, c->cfg.tile_w, c->cfg.tile_h, c->cfg.list_records))
+        return GS_ERR_INVALID_ARG;
+    for (int v = 0; v < MAX_VIEWS; v++) {
+        c->rbs[v].variant = fwd;
+        c->rbs[v].variant_bwd = bwd;
+    }
+    return GS_OK;
+}
+
 gs_status gs_set_raster_variant(gs_ctx *c, int32_t variant)
 {
     if (!c || !raster_variant_ok(variant, c->cfg.tile_w, c->cfg.tile_h, c->cfg.list_records))
