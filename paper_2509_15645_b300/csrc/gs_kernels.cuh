@@ -268,12 +268,19 @@ void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, co
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
                      unsigned long long *stats = nullptr, int cam0 = 0);
+// Visibility masks of the views rendered before this one in a step over
+// several views.  A Gaussian that none of them sees takes its gradient row by
+// plain stores (so the union layout needs no zeroing first); the others add.
+struct PrevMasks {
+    const uint32_t *m[MAX_VIEWS];
+    int n;
+};
 void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                       float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
-                      const int32_t *ids, bool accumulate, Work &w, cudaStream_t s);
+                      const int32_t *ids, const PrevMasks &prev, Work &w, cudaStream_t s);
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                      const DevCam &cam_host, const float *dimage, float *grad, int64_t gcap,
-                     const uint32_t *remap_mask, const uint32_t *remap_prefix, const int32_t *ids, bool accumulate,
+                     const uint32_t *remap_mask, const uint32_t *remap_prefix, const int32_t *ids,
                      Work &w, cudaStream_t s, int *work, unsigned long long *stats = nullptr);
 void launch_loss_l1(const float *image, const float *target, int64_t count, float *loss, float *dimage, Work &w,
                     cudaStream_t s);

@@ -709,7 +709,7 @@ gs_status gs_render_bwd(gs_ctx *c, const float *dL_dimage, float *grad_compact, 
     if (!dL_dimage || !grad_compact || cap <= 0) return fail(c, GS_ERR_INVALID_ARG, "invalid argument");
     cudaStream_t s = (cudaStream_t)stream;
     render_backward(c->fwd_sc, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], c->fwd_cam, dL_dimage, grad_compact, cap,
-                    nullptr, nullptr, nullptr, false, c->w, s, c->work);
+                    nullptr, nullptr, nullptr, c->w, s, c->work);
     return cuda_check(c, "gs_render_bwd");
 }
 
@@ -905,7 +905,7 @@ gs_status gs_autotune(gs_ctx *c, const gs_scene *scene, const gs_camera *cam, in
             // list-order records itself
             if (v == RASTER_TMA_VARIANT) c->rbs[0].variant = 0;
             render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u,
-                            c->cfg.max_visible, nullptr, nullptr, nullptr, false, c->w, s, c->work);
+                            c->cfg.max_visible, nullptr, nullptr, nullptr, c->w, s, c->work);
             c->rbs[0].variant = v;
             cudaEventRecord(e2, s);
             if (cudaEventSynchronize(e2) != cudaSuccess) {
@@ -969,7 +969,7 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
     render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], false, nullptr, nullptr,
                    c->w, s, c->work);
     render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u, c->cfg.max_visible,
-                    nullptr, nullptr, nullptr, false, c->w, s, c->work, dev);
+                    nullptr, nullptr, nullptr, c->w, s, c->work, dev);
     unsigned long long host[2] = {0, 0};
     if (cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -1137,7 +1137,6 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
         for (int v = 0; v < n_views; v++) launch_mask_or(c->union_mask, c->vmask[v], nw, c->w, s);
         compact_mask(c->union_mask, sv.n, c->union_chunk, false, nullptr, c->union_prefix, (int)c->gcap_u,
                      &c->cnt->n_union, c->w, s);
-        launch_zero_rows(c->grad_u, sv.D, c->gcap_u, &c->cnt->n_union, (int)c->gcap_u, c->w, s);
         M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u, selected};
     }
     return M;
@@ -1173,10 +1172,13 @@ static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &
             c->w.mark(TP_BWD0, s);
         }
         raster_backward(args, k, rbs, a.cam + v0, dimg_c, nv, c->work + 1, c->w, s, nullptr, v0);
-        for (int j = 0; j < k; j++)
+        for (int j = 0; j < k; j++) {
+            PrevMasks prev{};
+            for (int p = 0; p < v0 + j; p++) prev.m[prev.n++] = c->vmask[p];
             project_backward(sv, args, v0 + j, c->nvis_view + v0 + j, c->rbs[j], c->grad_u, M.gcap,
                              n_views > 1 ? M.gmask : nullptr, n_views > 1 ? M.gprefix : nullptr, c->vids[v0 + j],
-                             n_views > 1, c->w, s);
+                             prev, c->w, s);
+        }
     }
     c->w.mark(TP_BWD1, s);
 }

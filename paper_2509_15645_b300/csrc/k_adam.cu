@@ -13,6 +13,8 @@
 //                     the fp32 form, 14 B per SH parameter in the bf16 form;
 //                     coalesced because the Gaussians are stored in Morton
 //                     order and views see runs.
+#include <type_traits>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -632,6 +634,85 @@ __device__ __forceinline__ void pair_step(const PairRows &a, const Planes<T> &P,
     }
 }
 
+// bf16 form: both elements of a pair rounded by one conversion instruction
+// (cvt.rn / cvt.rs .bf16x2.f32; element 0 in the low half).  Stochastic
+// rounding (cvt.rs) takes 16 random bits per element from rbits, the low half
+// for element 0: the same bits the per-element path adds below the kept
+// mantissa (sr_bits of each element, low 16 bits for m, high 16 for v,
+// sr_w_bits for w).
+__device__ __forceinline__ uint32_t bf16x2_round(float x0, float x1, bool stochastic, uint32_t rbits)
+{
+    uint32_t d;
+    if (stochastic)
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(x1), "f"(x0), "r"(rbits));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(x1), "f"(x0));
+    return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t d) { return __uint_as_float(d << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t d) { return __uint_as_float(d & 0xffff0000u); }
+
+// Store the halves of a packed bf16 pair whose bit is set in `sel`.
+__device__ __forceinline__ void st2p(__nv_bfloat16 *p, uint32_t d, uint32_t sel)
+{
+    if (sel == 3u) *reinterpret_cast<uint32_t *>(p) = d;
+    else if (sel == 1u) reinterpret_cast<uint16_t *>(p)[0] = (uint16_t)d;
+    else if (sel == 2u) reinterpret_cast<uint16_t *>(p)[1] = (uint16_t)(d >> 16);
+}
+
+template <bool GEO, int OPT>
+__device__ __forceinline__ void pair_step_bf16(const PairRows &a, const Planes<__nv_bfloat16> &P, int r0, int rend,
+                                               const SLut &L, const uint32_t *key)
+{
+    const uint32_t sel = (a.info >> 16) & 3u;
+    const int dd[2] = {(int)(a.info & 255u), (int)((a.info >> 8) & 255u)};
+    const bool st = L.stochastic != 0;
+#pragma unroll
+    for (int q = 0; q < PR; q++) {
+        const int r = r0 + q;
+        if (r >= rend) continue;
+        const int grp = lr_group(r);
+        float w[2], m[2], v[2];
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            w[e] = a.w[q][e];
+            m[e] = a.m[q][e];
+            v[e] = a.v[q][e];
+            if ((sel >> e) & 1u) adam_value<OPT>(w[e], m[e], v[e], a.g[q][e], dd[e], grp, L);
+        }
+        const uint32_t h0 = st ? sr_bits(key[q], (uint32_t)a.i0) : 0u;
+        const uint32_t h1 = st ? sr_bits(key[q], (uint32_t)(a.i0 + 1)) : 0u;
+        const uint32_t pm = bf16x2_round(m[0], m[1], st, (h0 & 0xffffu) | (h1 << 16));
+        const uint32_t pv = OPT == GS_OPT_SGDM ? 0u : bf16x2_round(v[0], v[1], st, (h0 >> 16) | (h1 & 0xffff0000u));
+        const float d0 = restore_dir<OPT>(bf16_lo(pm), bf16_lo(pv), L.eps);
+        const float d1 = restore_dir<OPT>(bf16_hi(pm), bf16_hi(pv), L.eps);
+        if (GEO) {
+            const int64_t o = (int64_t)r * P.pitch + a.i0;
+            st2(P.geo + o, __float_as_uint(w[0]), __float_as_uint(w[1]), sel);
+            st2p(P.m + o, pm, sel);
+            if (OPT != GS_OPT_SGDM) st2p(P.v + o, pv, sel);
+            if (P.rdir) st2(P.rdir + o, __float_as_uint(d0), __float_as_uint(d1), sel);
+        } else {
+            const uint32_t pw = bf16x2_round(w[0], w[1], st, (sr_w_bits(h0) & 0xffffu) | (sr_w_bits(h1) << 16));
+            const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
+            st2p(P.shw + o, pw, sel);
+            st2p(P.shm + o, pm, sel);
+            if (OPT != GS_OPT_SGDM) st2p(P.shv + o, pv, sel);
+            if (P.shr) st2p(P.shr + o, bf16x2_round(d0, d1, false, 0u), sel);
+        }
+    }
+}
+
+template <typename T, bool GEO, int OPT>
+__device__ __forceinline__ void pair_step_any(const PairRows &a, const Planes<T> &P, int r0, int rend, const SLut &L,
+                                              const uint32_t *key)
+{
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+        pair_step_bf16<GEO, OPT>(a, P, r0, rend, L, key);
+    else
+        pair_step<T, GEO, OPT>(a, P, r0, rend, L, key);
+}
+
 // blockIdx.y: plane groups; the first n_geo_groups cover geometry planes
 // [PR y, PR y + PR) below 11, the rest SH planes 11 + PR (y - n_geo_groups) ...
 template <typename T, int OPT>
@@ -663,7 +744,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
             const int jn = j + stride;
             const bool more = jn < n_pairs;
             if (more) pair_fetch<T, true, OPT>(nxt, jn, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
-            pair_step<T, true, OPT>(cur, P, r0, rend, L, key);
+            pair_step_any<T, true, OPT>(cur, P, r0, rend, L, key);
             if (!more) break;
             cur = nxt;
             j = jn;
@@ -674,7 +755,7 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
             const int jn = j + stride;
             const bool more = jn < n_pairs;
             if (more) pair_fetch<T, false, OPT>(nxt, jn, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
-            pair_step<T, false, OPT>(cur, P, r0, rend, L, key);
+            pair_step_any<T, false, OPT>(cur, P, r0, rend, L, key);
             if (!more) break;
             cur = nxt;
             j = jn;

@@ -1264,7 +1264,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
                                                             const float *__restrict__ g9, float *__restrict__ grad,
                                                             int64_t gcap, const int32_t *__restrict__ ids,
                                                             const uint32_t *__restrict__ rmask,
-                                                            const uint32_t *__restrict__ rprefix, int accumulate,
+                                                            const uint32_t *__restrict__ rprefix, const PrevMasks prev,
                                                             int *status, const int *__restrict__ n_fix,
                                                             const int32_t *__restrict__ fix_idx,
                                                             const uint8_t *__restrict__ fix_flag)
@@ -1281,11 +1281,13 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         const int k = FIX ? fix_idx[j] : j;
         if (!FIX && fix_flag[k]) continue;
         int64_t kk = k;
+        bool accumulate = false;                   // an earlier view of the step wrote this row
         if (rmask) {
             int64_t i = ids[k];
             if (i < 0) continue;
             uint32_t word = rmask[i >> 5];
             kk = rprefix[i >> 5] + __popc(word & ((1u << (i & 31)) - 1u));
+            for (int p = 0; p < prev.n; p++) accumulate |= ((prev.m[p][i >> 5] >> (i & 31)) & 1u) != 0u;
         }
         if (kk >= gcap) {          // the caller's gradient buffer is smaller than the visible set
             latch(status, GS_ERR_CAPACITY);
@@ -1655,8 +1657,8 @@ void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, c
 }
 
 typedef void (*ProjBwdFn)(const float *, int, const int *, const DevArgs *, int, const float *, float *, int64_t,
-                          const int32_t *, const uint32_t *, const uint32_t *, int, int *, const int *, const int32_t *,
-                          const uint8_t *);
+                          const int32_t *, const uint32_t *, const uint32_t *, const PrevMasks, int *, const int *,
+                          const int32_t *, const uint8_t *);
 
 template <bool FIX> static ProjBwdFn pbwd_for(int deg)
 {
@@ -1670,20 +1672,20 @@ template <bool FIX> static ProjBwdFn pbwd_for(int deg)
 
 void project_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                       float *grad, int64_t gcap, const uint32_t *remap_mask, const uint32_t *remap_prefix,
-                      const int32_t *ids, bool accumulate, Work &w, cudaStream_t s)
+                      const int32_t *ids, const PrevMasks &prev, Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
     pbwd_for<false>(sc.deg)<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
-        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, accumulate ? 1 : 0,
+        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, prev,
         w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
     pbwd_for<true>(sc.deg)<<<w.num_sms, PROJ_BLOCK, 0, s>>>(
-        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, accumulate ? 1 : 0,
+        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, prev,
         w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
 }
 
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
                      const DevCam &cam, const float *dimage, float *grad, int64_t gcap, const uint32_t *remap_mask,
-                     const uint32_t *remap_prefix, const int32_t *ids, bool accumulate, Work &w, cudaStream_t s,
+                     const uint32_t *remap_prefix, const int32_t *ids, Work &w, cudaStream_t s,
                      int *work, unsigned long long *stats)
 {
     const int cap = (int)rb.cap;
@@ -1698,7 +1700,7 @@ void render_backward(const SceneView &sc, const DevArgs *args, int view, const i
     if (view == 0) w.mark(TP_RBWD0, s);
     bwd_variant(rb.variant_bwd, stats != nullptr)<<<sh.grid, sh.block, 0, s>>>(J, args, stats);
     if (view == 0) w.mark(TP_RBWD1, s);
-    project_backward(sc, args, view, n_vis, rb, grad, gcap, remap_mask, remap_prefix, ids, accumulate, w, s);
+    project_backward(sc, args, view, n_vis, rb, grad, gcap, remap_mask, remap_prefix, ids, PrevMasks{}, w, s);
 }
 
 }  // namespace gs

@@ -24,8 +24,10 @@ def _trained_scene(gs, orc, prec, n=20_000, deg=1, steps=5):
     """A scene after a few deferred steps over two views (delays 0..4)."""
     P = scenes.uniform_cube_scene(n, seed=90, sh_degree=deg, log_scale_mean=-3.0, log_scale_std=0.8)
     P[10] = np.random.default_rng(91).normal(-1.0, 2.5, n)          # a spread of opacities: some get pruned
-    cams = [cam_f32(scenes.camera_lookat(e, (0.0, 0.0, 0.0), 64, 48, 60.0, up=(0, -1, 0)))
-            for e in ((0.0, 0.0, -3.0), (1.6, -0.4, -2.5))]
+    # two narrow views of different parts of the cube: ~20% of the Gaussians
+    # neither sees, ~40% only one, so counters run up between the two
+    cams = [cam_f32(scenes.camera_lookat(e, la, 64, 48, 25.0, up=(0, -1, 0)))
+            for e, la in (((0.0, 0.0, -3.0), (-0.5, 0.0, 0.0)), ((1.6, -0.4, -2.5), (0.5, 0.1, 0.0)))]
     T = np.asarray(scenes.uniform_cube_scene(n, seed=92, sh_degree=deg), np.float64)
     tg = [torch.as_tensor(orc.render(T, deg, c, (16, 16))["image"], dtype=torch.float32, device="cuda") for c in cams]
     scene = gs.GaussianScene(P, deg, precision=prec)
