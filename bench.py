@@ -283,7 +283,14 @@ def run_ours(args):
     # HBM budget: state that does not fit goes to the host tier (SH planes and
     # their optimizer state in pinned host memory, streamed by gs_step)
     tier, stage_chunks, plan, eb = gs.GS_TIER_DEVICE, 0, None, 4
-    if args.budget_gb:
+    if args.cpu_optimizer:
+        # the paper's offloaded configuration: SH planes and their moments in
+        # host memory, stepped by the host cores (parameter forwarding, deferred update)
+        tier = gs.GS_TIER_HOST_CPU_OPT
+        args.no_bf16, args.bf16_only = True, False
+        plan = {"tier": "host_cpu_optimizer", "device_state_gb": round(N * (44 + 2 * 11 * 4 + 44 + 1) / 1e9, 2),
+                "host_state_gb": round(N * (D - 11) * 12 / 1e9, 2)}
+    elif args.budget_gb:
         prec0 = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
         eb = 4 if prec0 == gs.GS_FP32 else 2
         resident = N * (44 + (D - 11) * eb + 2 * D * eb + 44 + (D - 11) * eb + 1)
@@ -303,7 +310,17 @@ def run_ours(args):
                 "device_state_gb": round((geo_only if tier else resident) / 1e9, 2),
                 "stage_chunks": stage_chunks, "chunk_rows": 1 << args.chunk_shift}
     ctx = gs.Context(**ctx_kw, device=local, stage_chunks=stage_chunks, chunk_shift=args.chunk_shift,
-                     stage_elem_bytes=eb if stage_chunks else 0)
+                     stage_elem_bytes=eb if stage_chunks else 0, cpu_opt=1 if args.cpu_optimizer else 0)
+    if args.cpu_threads:
+        ctx.set_cpu_threads(args.cpu_threads)
+
+    def finish():
+        """The last step's host-side work: the host tier's write-backs, or the
+        held SH update of the host-core optimizer."""
+        if tier == gs.GS_TIER_HOST_CPU_OPT:
+            ctx.sync_status()
+        else:
+            ctx.wait_copies()
     # targets: the seed-1 scene rendered by the same library (setup, untimed)
     tscene = gs.GaussianScene(tgt_params, deg, device=dev, with_optimizer=False)
     del tgt_params
@@ -412,9 +429,11 @@ def run_ours(args):
         staged = []
         for s in range(K):
             one_step(sc, Wm + s)
-            if tier:     # host-side counters of the step just enqueued (no synchronisation)
+            if tier == gs.GS_TIER_HOST_SH:     # host-side counters of the step just enqueued (no synchronisation)
                 staged.append(ctx.host_tier_stats())
-        ctx.wait_copies()                # the last step's write-backs to host memory are timed too
+            elif tier:
+                staged.append(ctx.cpu_tier_stats())
+        finish()                         # the last step's write-backs / held update are timed too
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -431,11 +450,14 @@ def run_ours(args):
         """Autotune, time K steps of one precision form, then an untimed pass
         over the views for the counts behind the algorithmic bytes and flops."""
         sc = gs.GaussianScene(P0, deg, device=dev, precision=precision, tier=tier)
-        if tier == gs.GS_TIER_DEVICE:
+        if tier == gs.GS_TIER_DEVICE and args.raster_variant is None:
             variant, ms_f, ms_b = ctx.autotune(sc, cams[0])     # rasterizer variants for this workload (untimed)
             variant_ms = {"fwd_stage": ms_f, "bwd_stage": ms_b}
-        else:   # the autotuner renders through the resident path
-            variant, variant_ms = (1, 1), {}
+        elif tier == gs.GS_TIER_DEVICE:
+            variant, variant_ms = None, {}                       # pinned below
+        else:   # the autotuner renders through the resident path: the resident workload's choice
+            variant, variant_ms = (8, 8), {}
+            ctx.set_raster_variant(8, 8)
         if args.raster_variant is not None:
             fb = [int(x) for x in str(args.raster_variant).split(",")]
             variant = (fb[0], fb[-1])
@@ -467,8 +489,12 @@ def run_ours(args):
              "n_fp64": float(np.mean([x[4] for x in stats])), "n_cand": float(np.mean([x[5] for x in stats])),
              "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
              "kernels": kernels, "copy_trace": copy_trace,
-             "staged_chunks": float(np.mean([x[0] for x in staged])) if staged else None,
-             "staged_bytes": float(np.mean([x[1] for x in staged])) if staged else None}
+             "staged_chunks": (float(np.mean([x[0] for x in staged]))
+                               if staged and tier == gs.GS_TIER_HOST_SH else None),
+             "staged_bytes": (float(np.mean([x[1] for x in staged]))
+                              if staged and tier == gs.GS_TIER_HOST_SH else None),
+             "cpu_stats": ({k: float(np.mean([x[k] for x in staged])) for k in staged[0]}
+                           if staged and tier == gs.GS_TIER_HOST_CPU_OPT else None)}
         b_cull, b_apply, b_select = algorithmic_bytes(N, D, m["n_vis"], m["n_upd"], m["n_rest"],
                                                       bf16=precision != gs.GS_FP32, n_cand=m["n_cand"])
         m.update(b_cull=b_cull, b_apply=b_apply, b_select=b_select)
@@ -553,7 +579,7 @@ def run_ours(args):
         prefetch(0)
         for s in range(K):
             e2e_step(s, s == K - 1)
-        ctx.wait_copies()
+        finish()
         f1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
@@ -610,7 +636,19 @@ def run_ours(args):
         "gpu_launches": int(m["kernels"] * K) if m["kernels"] else None,
         "bf16_form": bf16,
     }
-    if tier:
+    if tier == gs.GS_TIER_HOST_CPU_OPT:
+        cs = m["cpu_stats"]
+        out["cpu_optimizer"] = {
+            "threads": args.cpu_threads or os.cpu_count(),
+            "forward_ms_per_step": round(cs["forward_ms"], 3), "host_update_ms_per_step": round(cs["update_ms"], 3),
+            "wait_for_update_ms_per_step": round(cs["wait_ms"], 3),
+            "h2d_bytes_per_step": round(cs["h2d_bytes"]), "d2h_bytes_per_step": round(cs["d2h_bytes"]),
+            "rows_forwarded_per_step": round(cs["rows"]), "update_set_per_step": round(cs["held_members"]),
+            "copy_trace": m["copy_trace"]}
+        out["roofline"] = {"bound": "host", "note": "host-core optimizer: the step is bound by the host's "
+                           "forwarding and deferred update; kernel rooflines are measured on the resident workloads"}
+        out["cull_adam"] = None
+    elif tier:
         out["host_tier"] = {"staged_chunks_per_step": m["staged_chunks"], "chunk_rows": 1 << args.chunk_shift,
                             "bytes_per_step": m["staged_bytes"],
                             "pcie_gbs": m["staged_bytes"] / (K_ms / K * 1e-3) / 1e9 if m["staged_bytes"] else None,
@@ -899,6 +937,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=None,
                     help="HBM budget: state that does not fit moves its SH planes to pinned host memory")
     ap.add_argument("--chunk-shift", type=int, default=11, help="log2 Gaussians per host-tier chunk")
+    ap.add_argument("--cpu-optimizer", action="store_true",
+                    help="the paper's offloaded configuration: SH planes in host memory stepped by the host cores")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="host-core optimizer threads (0: every core)")
     ap.add_argument("--raster-variant", default=None,
                     help="pin the rasterizer variant instead of the autotuned one: V, or F,B for forward and backward")
     ap.add_argument("--no-extra-forms", dest="extra_forms", action="store_false",

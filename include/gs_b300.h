@@ -10,12 +10,14 @@
  * Conventions for every call
  *  - Pointers marked "device" point to CUDA device memory on the context's
  *    device; "host" pointers to ordinary host memory.  The caller owns every
- *    buffer it passes; the context owns only its scratch workspace.
+ *    buffer it passes; the context owns only its scratch workspace and the
+ *    pinned host buffers of its host-tier steps (allocated by gs_create).
  *  - Every call is asynchronous on the given stream (a cudaStream_t passed as
  *    void*; NULL = legacy default stream) and never synchronises, except
  *    gs_sync_status, gs_create/gs_destroy, gs_timing_read, gs_autotune,
  *    gs_split_point (once per bisection round) and gs_step on a host-tier scene
- *    (which waits once for its chunk-touch map).  A context
+ *    (which waits once for its chunk-touch map, or, for GS_TIER_HOST_CPU_OPT,
+ *    for its visible set and its update-set size).  A context
  *    must be driven from one stream at a time.
  *  - Invalid arguments return GS_ERR_INVALID_ARG before anything is launched;
  *    a failed launch returns GS_ERR_CUDA.  Errors found on the device (a
@@ -89,7 +91,24 @@ enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
  * on past the end of its work on `stream` (overlapping the next step's cull);
  * gs_wait_copies makes a stream wait for them, gs_sync_status waits for them
  * on the host, and the next gs_step orders its own copies after them. */
-enum { GS_TIER_DEVICE = 0, GS_TIER_HOST_SH = 1 };
+/* GS_TIER_HOST_CPU_OPT: the paper's own offloaded configuration, with the
+ * optimizer of the SH planes on the host cores (§4.2.2 parameter forwarding,
+ * §4.3 deferred update with OpenMP), for comparison with GS_TIER_HOST_SH,
+ * whose SH rows are stepped by device kernels.  The scene is laid out as in
+ * GS_TIER_HOST_SH, fp32 only; the context needs gs_config.cpu_opt = 1.  Per
+ * gs_step: the cull (with the optimizer's select) on the device and one host
+ * synchronisation for the step's visible Gaussians (the union over its views)
+ * and their defer counters; the host forwards their SH values (the previous
+ * step's pending update applied to its members, the deferred restore of the
+ * others; nothing is written to the host planes) into a pinned block that goes
+ * to the device in pieces as they are ready; a worker thread then applies the
+ * previous step's update to the host planes while the device renders,
+ * back-propagates and steps the geometry planes; the step's SH gradients, its
+ * update set and the delays come back into host buffers and are applied by
+ * the next gs_step (or by gs_sync_status, which also waits for the worker).
+ * Read host_sh, host_m, host_v only after gs_sync_status.  The step
+ * synchronises the host twice (visible set; update-set size). */
+enum { GS_TIER_DEVICE = 0, GS_TIER_HOST_SH = 1, GS_TIER_HOST_CPU_OPT = 2 };
 
 /* Adam variants: deferred with the restore tables of Fig. 10 (the method) or
  * eager (Eq. 1 on every Gaussian each step: the baseline the paper improves). */
@@ -142,8 +161,8 @@ typedef struct {
                               the kernels recompute it from m and v */
     uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
     int32_t step;          /* optimizer steps completed; the next step is step + 1 */
-    int32_t tier;          /* GS_TIER_DEVICE or GS_TIER_HOST_SH */
-    void *host_sh;         /* GS_TIER_HOST_SH only: pinned host [D-11][pitch] SH planes, */
+    int32_t tier;          /* GS_TIER_DEVICE, GS_TIER_HOST_SH or GS_TIER_HOST_CPU_OPT */
+    void *host_sh;         /* host tiers only: host [D-11][pitch] SH planes (pinned for GS_TIER_HOST_SH), */
     void *host_m;          /*   their first moments, */
     void *host_v;          /*   and second moments (all of the SH type) */
     void *host_rdir;       /*   unused (SH restore directions are recomputed from m, v on the device); may be NULL */
@@ -193,6 +212,10 @@ typedef struct {
     int32_t list_records;    /* 1: also keep each view's splat records in list order (48 bytes per key of
                                 capacity), which the TMA-staged rasterizer variant 9 needs; 0: variant 9 is not
                                 available on this context */
+    int32_t cpu_opt;         /* 1: the context can step GS_TIER_HOST_CPU_OPT scenes (device: a [D-11][per-step
+                                visible capacity] fp32 block of forwarded SH rows and the visible ids and counters;
+                                host: pinned buffers for the same block, two steps' SH gradients and update sets
+                                of up to max_gaussians members); 0: it cannot */
 } gs_config;
 
 /* ------------------------------------------------------------------ context */
@@ -444,6 +467,50 @@ GS_API gs_status gs_set_cull_wait_limit(gs_ctx *ctx, uint32_t first_wait);
  * *n_keys the count K, *ranges[2 * tiles] the [begin, end) of each tile. */
 GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key, const uint32_t **splat_of_key,
                                  const int32_t **n_keys, const uint32_t **ranges);
+
+/* Deferred optimizer step on host arrays, on the host cores (§4.3 with
+ * OpenMP: the update GS_TIER_HOST_CPU_OPT applies to its SH planes, callable
+ * alone).  w, m, v: host [planes][pitch] fp32, the parameter rows plane0 ..
+ * plane0 + planes - 1 of the scene's parameter vector (learning-rate group of
+ * each row as in gs_step; plane0 + planes <= 59).  uids[0..n_upd): the update
+ * set, ascending Gaussian ids in [0, pitch), with udelay its delays (0..15);
+ * vids[0..n_vis): ascending ids with a gradient row, grad[r * gpitch + k] the
+ * gradient of row plane0 + r of Gaussian vids[k] (gpitch >= n_vis); members
+ * without a row step with zero gradient.  One step t = step (>= 1) with the
+ * tables of gs_adam_tables(adam, step), in FP32 (IEEE square root and
+ * division).  threads <= 0: every core.  Errors (nothing written):
+ * GS_ERR_INVALID_ARG for a null array with a non-zero count, bad sizes, ids out
+ * of order or out of range, or an invalid adam (mode must be deferred).  All
+ * memory is the caller's. */
+GS_API gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t pitch, int32_t plane0, int32_t planes,
+                                      const int32_t *uids, const uint8_t *udelay, int64_t n_upd,
+                                      const int32_t *vids, const float *grad, int64_t n_vis, int64_t gpitch,
+                                      const gs_adam_cfg *adam, int32_t step, int32_t threads);
+
+/* Parameter forwarding (§4.2.2) on host arrays: out[r * opitch + k] (host,
+ * opitch >= n) = row plane0 + r of Gaussian ids[k] as the next step, step + 1,
+ * sees it, without writing w, m, v.  counter[k]: that Gaussian's defer counter
+ * at step + 1; > 0 restores over counter[k] deferred steps (tables of step + 1),
+ * 0 applies the pending update of step `step` (uids .. gpitch as in
+ * gs_cpu_deferred_step; n_upd = 0 for none) if ids[k] is one of its members,
+ * else takes the stored value.  ids ascending.  Errors as gs_cpu_deferred_step
+ * (step >= 0 here). */
+GS_API gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0,
+                                int32_t planes, const int32_t *ids, const uint8_t *counter, int64_t n,
+                                const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
+                                const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam,
+                                int32_t step, float *out, int64_t opitch, int32_t threads);
+
+/* OpenMP threads of the host-core optimizer of GS_TIER_HOST_CPU_OPT steps
+ * (<= 0: every core; the default). */
+GS_API gs_status gs_set_cpu_threads(gs_ctx *ctx, int32_t threads);
+
+/* The last GS_TIER_HOST_CPU_OPT gs_step: stats[0] host ms forwarding the
+ * visible rows, [1] host ms of the worker's update (the previous step's),
+ * [2] host ms the step waited for that worker, [3] bytes host -> device,
+ * [4] bytes device -> host, [5] rows forwarded, [6] members in the update
+ * set the step left pending. */
+GS_API gs_status gs_cpu_tier_stats(const gs_ctx *ctx, double *stats);
 
 /* Host tier: chunks staged by the last gs_step of a GS_TIER_HOST_SH scene and
  * the bytes it moved between host and device (both directions). */

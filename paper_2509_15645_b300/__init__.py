@@ -7,8 +7,8 @@ the library and fails if it has not been built.
 """
 from . import _lib
 from ._lib import (GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN, GS_FP32, GS_OPT_ADAM, GS_OPT_ADAMW, GS_OPT_SGDM,  # noqa: F401
-                   GS_TIER_DEVICE, GS_TIER_HOST_SH)
-from .api import (Context, GaussianScene, RegionCamera, adam_struct, adam_tables, camera_struct, n_params,  # noqa: F401
-                  render, split_regions)
+                   GS_TIER_DEVICE, GS_TIER_HOST_CPU_OPT, GS_TIER_HOST_SH)
+from .api import (Context, GaussianScene, RegionCamera, adam_struct, adam_tables, camera_struct,  # noqa: F401
+                  cpu_deferred_step, cpu_forward, n_params, render, split_regions)
 
 _lib.load()

@@ -17,7 +17,7 @@ RASTER_VARIANTS = 10
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
 GS_OPT_ADAM, GS_OPT_ADAMW, GS_OPT_SGDM = 0, 1, 2
-GS_TIER_DEVICE, GS_TIER_HOST_SH = 0, 1
+GS_TIER_DEVICE, GS_TIER_HOST_SH, GS_TIER_HOST_CPU_OPT = 0, 1, 2
 
 
 class Camera(C.Structure):
@@ -41,7 +41,7 @@ class Config(C.Structure):
     _fields_ = [("max_gaussians", c_i64), ("max_visible", c_i64), ("max_keys", c_i64), ("max_width", c_i32),
                 ("max_height", c_i32), ("tile_w", c_i32), ("tile_h", c_i32), ("max_views", c_i32),
                 ("max_sh_degree", c_i32), ("stage_chunks", c_i64), ("chunk_shift", c_i32), ("stage_elem_bytes", c_i32),
-                ("render_views", c_i32), ("list_records", c_i32)]
+                ("render_views", c_i32), ("list_records", c_i32), ("cpu_opt", c_i32)]
 
 
 EXPORTS = {
@@ -81,6 +81,12 @@ EXPORTS = {
                                C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
+    "gs_cpu_deferred_step": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
+                                     c_i64, C.POINTER(AdamCfg), c_i32, c_i32]),
+    "gs_cpu_forward": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp,
+                               c_vp, c_i64, c_i64, C.POINTER(AdamCfg), c_i32, c_vp, c_i64, c_i32]),
+    "gs_set_cpu_threads": (c_i32, [c_vp, c_i32]),
+    "gs_cpu_tier_stats": (c_i32, [c_vp, C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -136,8 +136,9 @@ class GaussianScene:
         self.m = self.v = self.counter = None
         self.m_sh = self.v_sh = None
         self.rdir = self.rdir_geo = self.rdir_sh = None
-        host = tier == L.GS_TIER_HOST_SH
+        host = tier in (L.GS_TIER_HOST_SH, L.GS_TIER_HOST_CPU_OPT)
         if host:
+            assert tier == L.GS_TIER_HOST_SH or precision == L.GS_FP32, "the host-core optimizer tier is fp32"
             assert with_optimizer, "the host tier holds optimizer state"
             pin = dict(device="cpu", pin_memory=True)
             self.geo = torch.zeros(11, P, dtype=torch.float32, device=device)
@@ -191,7 +192,7 @@ class GaussianScene:
         s.v = self.v.data_ptr() if self.v is not None else None
         s.rdir = self.rdir_geo.data_ptr() if self.rdir_geo is not None else None
         s.counter = self.counter.data_ptr() if self.counter is not None else None
-        if self.tier == L.GS_TIER_HOST_SH:
+        if self.tier != L.GS_TIER_DEVICE:
             s.host_sh, s.host_m, s.host_v = self.sh.data_ptr(), self.m_sh.data_ptr(), self.v_sh.data_ptr()
             s.host_rdir = None
         s.step = self.step
@@ -205,7 +206,7 @@ class GaussianScene:
 
     def moments(self):
         """(m, v) as float32 [D][n] on the geometry's device."""
-        if self.tier == L.GS_TIER_HOST_SH:
+        if self.tier != L.GS_TIER_DEVICE:
             dev = self.geo.device
             return (torch.cat([self.m[:, :self.n].float(), self.m_sh[:, :self.n].to(dev).float()]),
                     torch.cat([self.v[:, :self.n].float(), self.v_sh[:, :self.n].to(dev).float()]))
@@ -217,10 +218,11 @@ class Context:
 
     def __init__(self, max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
                  max_sh_degree=3, device=0, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0,
-                 list_records=0):
+                 list_records=0, cpu_opt=0):
         self.lib = L.load()
         cfg = self._config(max_gaussians, max_visible, max_keys, max_width, max_height, tile, max_views,
-                           max_sh_degree, stage_chunks, chunk_shift, stage_elem_bytes, render_views, list_records)
+                           max_sh_degree, stage_chunks, chunk_shift, stage_elem_bytes, render_views, list_records,
+                           cpu_opt)
         self.cfg = cfg
         nb = C.c_size_t(0)
         self._check(self.lib.gs_workspace_size(C.byref(cfg), C.byref(nb)), "workspace size")
@@ -234,8 +236,9 @@ class Context:
     @staticmethod
     def _config(max_gaussians, max_visible, max_keys, max_width, max_height, tile=(8, 8), max_views=1,
                 max_sh_degree=3, stage_chunks=0, chunk_shift=0, stage_elem_bytes=0, render_views=0,
-                list_records=0):
+                list_records=0, cpu_opt=0):
         cfg = L.Config()
+        cfg.cpu_opt = int(cpu_opt)
         cfg.render_views = int(render_views)
         cfg.list_records = int(list_records)
         cfg.stage_chunks, cfg.chunk_shift = int(stage_chunks), int(chunk_shift)
@@ -305,6 +308,19 @@ class Context:
         ch, by = C.c_int64(0), C.c_int64(0)
         self._check(self.lib.gs_host_tier_stats(self.h, C.byref(ch), C.byref(by)), "host tier stats")
         return ch.value, by.value
+
+    def set_cpu_threads(self, threads):
+        """OpenMP threads of the host-core optimizer (GS_TIER_HOST_CPU_OPT; <= 0: every core)."""
+        self._check(self.lib.gs_set_cpu_threads(self.h, int(threads)), "gs_set_cpu_threads")
+
+    def cpu_tier_stats(self):
+        """The last GS_TIER_HOST_CPU_OPT step: host ms forwarding, host ms of the
+        worker's update, ms the step waited for the worker, bytes to / from the
+        device, rows forwarded, members held for the next step."""
+        out = (C.c_double * 7)()
+        self._check(self.lib.gs_cpu_tier_stats(self.h, out), "gs_cpu_tier_stats")
+        keys = ("forward_ms", "update_ms", "wait_ms", "h2d_bytes", "d2h_bytes", "rows", "held_members")
+        return dict(zip(keys, list(out)))
 
     def render_splats(self):
         """Projected splats of the last render, float32 [n_vis][4] each (torch
@@ -491,6 +507,47 @@ class Context:
         return loss
 
 
+def _np_ptr(a, dtype):
+    import numpy as np
+    assert isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous, "contiguous numpy array expected"
+    return a.ctypes.data
+
+
+def cpu_deferred_step(w, m, v, plane0, uids, udelay, vids, grad, adam, step, threads=0):
+    """Deferred optimizer step on host arrays (gs_cpu_deferred_step): w, m, v
+    float32 [planes][pitch] numpy arrays (updated in place), rows plane0.. of the
+    parameter vector; uids / udelay the update set; vids ascending ids with
+    gradient rows grad float32 [planes][gpitch]."""
+    import numpy as np
+    planes, pitch = w.shape
+    gp = grad.shape[1] if grad.size else max(len(vids), 1)
+    st = L.load().gs_cpu_deferred_step(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32), pitch,
+                                       int(plane0), planes, _np_ptr(uids, np.int32), _np_ptr(udelay, np.uint8),
+                                       len(uids), _np_ptr(vids, np.int32), _np_ptr(grad, np.float32), len(vids), gp,
+                                       C.byref(adam), int(step), int(threads))
+    if st != L.GS_OK:
+        raise L.GsError(st, "gs_cpu_deferred_step")
+
+
+def cpu_forward(w, m, v, plane0, ids, counter, uids, udelay, vids, grad, adam, step, threads=0):
+    """Parameter forwarding on host arrays (gs_cpu_forward): the values of
+    Gaussians ``ids`` (with defer counters ``counter`` at step + 1) as step + 1
+    sees them, float32 [planes][len(ids)]."""
+    import numpy as np
+    planes, pitch = w.shape
+    n = len(ids)
+    out = np.zeros((planes, max(n, 1)), np.float32)
+    gp = grad.shape[1] if grad.size else max(len(vids), 1)
+    st = L.load().gs_cpu_forward(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32), pitch,
+                                 int(plane0), planes, _np_ptr(ids, np.int32), _np_ptr(counter, np.uint8), n,
+                                 _np_ptr(uids, np.int32), _np_ptr(udelay, np.uint8), len(uids),
+                                 _np_ptr(vids, np.int32), _np_ptr(grad, np.float32), len(vids), gp, C.byref(adam),
+                                 int(step), _np_ptr(out, np.float32), out.shape[1], int(threads))
+    if st != L.GS_OK:
+        raise L.GsError(st, "gs_cpu_forward")
+    return out[:, :n]
+
+
 class _Render(torch.autograd.Function):
     """image = render(w) for a fixed visible set; the backward is gs_render_bwd
     followed by a scatter of the compact gradients to w's [D][pitch] layout."""
@@ -513,4 +570,5 @@ def render(gctx: Context, scene: GaussianScene, cam, ids, n_vis):
     return _Render.apply(scene.w, gctx, scene, cam, ids, n_vis)
 
 
-__all__ = ["Context", "GaussianScene", "render", "camera_struct", "adam_struct", "n_params"]
+__all__ = ["Context", "GaussianScene", "render", "camera_struct", "adam_struct", "n_params", "cpu_deferred_step",
+           "cpu_forward"]

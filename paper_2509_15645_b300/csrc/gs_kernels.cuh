@@ -49,6 +49,9 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *
 // scan_exclusive); the total goes to total_out, clamped to cap with
 // GS_ERR_CAPACITY latched above it.
 void scan_counts(uint32_t *v, int64_t len, int *total_out, int cap, Work &w, cudaStream_t s);
+// dst[k] = src[ids[k]] for k < min(*n, cap).
+void launch_gather_u8(const uint8_t *src, const int32_t *ids, const int *n, int cap, uint8_t *dst, Work &w,
+                      cudaStream_t s);
 void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool have_counts, int32_t *ids,
                   uint32_t *word_prefix, int cap, int *count_out, Work &w, cudaStream_t s, uint8_t *counter = nullptr,
                   uint8_t *delay = nullptr);
@@ -63,8 +66,15 @@ struct ShRows {
     int64_t ppitch;
     const int32_t *slot;      // host tier: chunk -> staging slot; nullptr when resident
     int shift;
+    // Forwarded rows (GS_TIER_HOST_CPU_OPT): w holds the current SH values of
+    // the step's visible Gaussians (no restore, m and v absent), Gaussian i at
+    // its rank in the visibility mask cmask (word prefix cprefix).
+    const uint32_t *cmask, *cprefix;
+    int current;
     __device__ __forceinline__ int64_t base(int64_t i) const
     {
+        if (cmask)
+            return (int64_t)__ldg(cprefix + (i >> 5)) + __popc(__ldg(cmask + (i >> 5)) & ((1u << (i & 31)) - 1u));
         if (!slot) return i;
         // a chunk the step did not stage has slot -1: never read for a staged
         // step's Gaussians; clamped so a stray index stays inside the ring

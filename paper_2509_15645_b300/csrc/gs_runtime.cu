@@ -10,6 +10,10 @@
 #include <array>
 #include <vector>
 
+#include <chrono>
+#include <thread>
+
+#include "cpu_opt.hpp"
 #include "gs_kernels.cuh"
 #include "host_plan.hpp"
 
@@ -38,6 +42,41 @@ struct GraphCache {
     uint32_t first_wait = 0;
     cudaGraphNode_t ev_node[TP_COUNT] = {nullptr};
     int kernels = 0;
+};
+
+// GS_TIER_HOST_CPU_OPT: the host side of the paper's CPU-optimizer
+// configuration.  A step's update (its members and delays, its visible ids and
+// their SH gradients) is held in the buffer set of the step's parity until the
+// next step forwards from it and a worker thread applies it.
+struct CpuUpdateBuf {
+    int32_t *uids = nullptr, *vids = nullptr;      // pinned [max_gaussians], [gcap]
+    uint8_t *udelay = nullptr;                     // pinned [max_gaussians]
+    float *grad = nullptr;                         // pinned [SH planes][gcap]
+    int64_t n_upd = 0, n_vis = 0;
+    bool have_upd = false;                         // uids / udelay copied
+    bool full = false;                             // an update not yet applied to the host planes
+    int32_t step = 0;                              // the step it belongs to
+    DevLut lut{};
+    int opt = GS_OPT_ADAM;
+    HostPlanes planes{};                           // the host planes it applies to
+};
+
+struct CpuTierState {
+    int threads = 0;                               // <= 0: every core
+    float *stage_d = nullptr;                      // device [SH planes][gcap] forwarded rows (workspace)
+    int32_t *ids_d = nullptr;                      // device [gcap] union ids of a step over several views
+    uint8_t *cnt_d = nullptr;                      // device [gcap] counters of the visible ids
+    float *stage_h = nullptr;                      // pinned [SH planes][gcap]
+    uint8_t *cnt_h = nullptr;                      // pinned [gcap]
+    int *counts_h = nullptr;                       // pinned [2]: visible count, update-set size
+    CpuUpdateBuf buf[2];
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_grad = nullptr, ev_down = nullptr;
+    bool down_pending = false;
+    std::thread worker;
+    double lazy_ms = 0.0;                          // written by the worker
+    double fwd_ms = 0.0, wait_ms = 0.0;
+    int64_t h2d = 0, d2h = 0, rows = 0, left = 0;
 };
 
 }  // namespace
@@ -100,6 +139,7 @@ struct gs_ctx {
     cudaEvent_t ev_half[2] = {nullptr, nullptr};   // write-backs of the last step that used half 0 / 1 done
     cudaEvent_t ev_sdone = nullptr;     // the previous host-tier step's work on its stream done
     int64_t last_touched = 0, last_bytes = 0;
+    CpuTierState cpu;                   // GS_TIER_HOST_CPU_OPT (cfg.cpu_opt)
     char err[512] = {0};
 };
 
@@ -160,7 +200,8 @@ static bool valid_cfg(const gs_config *c)
            c->max_width < 65536 * c->tile_w && c->max_height < 65536 * c->tile_h && c->stage_chunks >= 0 &&
            (c->chunk_shift == 0 || (c->chunk_shift >= 10 && c->chunk_shift <= 20)) &&
            (c->stage_elem_bytes == 0 || c->stage_elem_bytes == 2 || c->stage_elem_bytes == 4) &&
-           c->render_views >= 0 && c->render_views <= c->max_views && (c->list_records == 0 || c->list_records == 1);
+           c->render_views >= 0 && c->render_views <= c->max_views && (c->list_records == 0 || c->list_records == 1) &&
+           (c->cpu_opt == 0 || c->cpu_opt == 1);
 }
 
 static int stage_eb(const gs_config &g) { return g.stage_elem_bytes ? g.stage_elem_bytes : 4; }
@@ -246,6 +287,11 @@ static void carve(gs_ctx *c, char *base)
     c->w.partials = k.take<uint32_t>(1024);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
+    if (g.cpu_opt) {
+        c->cpu.stage_d = k.take<float>((size_t)(D - N_GEO) * c->gcap_u);
+        c->cpu.ids_d = k.take<int32_t>(c->gcap_u);
+        c->cpu.cnt_d = k.take<uint8_t>(c->gcap_u);
+    }
     if (g.stage_chunks > 0) {
         c->shift = g.chunk_shift ? g.chunk_shift : 11;
         c->max_chunks = (N + (1ll << c->shift) - 1) >> c->shift;
@@ -398,13 +444,18 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
     if (s->sh_degree < 0 || s->sh_degree > c->cfg.max_sh_degree) return fail(c, GS_ERR_INVALID_ARG, "sh_degree out of range");
     if (s->precision != GS_FP32 && s->precision != GS_BF16_SH_MOM && s->precision != GS_BF16_SH_MOM_RN)
         return fail(c, GS_ERR_INVALID_ARG, "unknown precision form");
-    if (s->tier != GS_TIER_DEVICE && s->tier != GS_TIER_HOST_SH) return fail(c, GS_ERR_INVALID_ARG, "unknown tier");
-    const bool host = s->tier == GS_TIER_HOST_SH;
+    if (s->tier != GS_TIER_DEVICE && s->tier != GS_TIER_HOST_SH && s->tier != GS_TIER_HOST_CPU_OPT)
+        return fail(c, GS_ERR_INVALID_ARG, "unknown tier");
+    const bool cpu = s->tier == GS_TIER_HOST_CPU_OPT;
+    const bool host = s->tier == GS_TIER_HOST_SH || cpu;
     if (host && !host_ok) return fail(c, GS_ERR_INVALID_ARG, "host-tier scenes run through gs_step (and gs_cull)");
-    if (host && (c->cfg.stage_chunks <= 0 || !s->host_sh || !s->host_m || !s->host_v || !s->m || !s->v ||
-                 !s->counter))
-        return fail(c, GS_ERR_INVALID_ARG, "host tier needs a staging ring (stage_chunks) and host_sh/m/v planes");
-    if (host && elem_bytes(s->precision) > stage_eb(c->cfg))
+    if (host && (!s->host_sh || !s->host_m || !s->host_v || !s->m || !s->v || !s->counter))
+        return fail(c, GS_ERR_INVALID_ARG, "host tiers need host_sh/m/v planes and the geometry's optimizer state");
+    if (host && !cpu && c->cfg.stage_chunks <= 0)
+        return fail(c, GS_ERR_INVALID_ARG, "host tier needs a staging ring (stage_chunks)");
+    if (cpu && (!c->cfg.cpu_opt || s->precision != GS_FP32))
+        return fail(c, GS_ERR_INVALID_ARG, "GS_TIER_HOST_CPU_OPT needs a context with cpu_opt and an fp32 scene");
+    if (host && !cpu && elem_bytes(s->precision) > stage_eb(c->cfg))
         return fail(c, GS_ERR_INVALID_ARG, "staging ring holds %d-byte rows, the scene's SH rows have %d bytes",
                     stage_eb(c->cfg), (int)elem_bytes(s->precision));
     if (!s->geo || (!host && !s->sh)) return fail(c, GS_ERR_INVALID_ARG, "geo/sh planes are NULL");
@@ -430,7 +481,17 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
         sv.sh.ppitch = P;
         sv.sh.slot = nullptr;
         sv.sh.shift = 0;
+        sv.sh.cmask = sv.sh.cprefix = nullptr;
+        sv.sh.current = 0;
+    } else if (cpu) {
+        // the step's forwarded SH rows, placed by the step (visibility mask and prefix)
+        sv.sh = ShRows{};
+        sv.sh.w = c->cpu.stage_d;
+        sv.sh.ppitch = c->gcap_u;
+        sv.sh.current = 1;
     } else {
+        sv.sh.cmask = sv.sh.cprefix = nullptr;
+        sv.sh.current = 0;
         // SH restore directions are not streamed: the kernels recompute them from the staged m, v
         sv.sh.w = c->stage[0];
         sv.sh.m = c->stage[1];
@@ -461,6 +522,8 @@ bool gs::valid_adam(const gs_adam_cfg *a)
 
 // ---------------------------------------------------------------------------
 extern "C" {
+
+static gs_status cpu_flush(gs_ctx *c);
 
 gs_status gs_workspace_size(const gs_config *cfg, size_t *bytes)
 {
@@ -530,6 +593,30 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
             return GS_ERR_CUDA;
         }
     }
+    if (cfg->cpu_opt) {
+        CpuTierState &T = c->cpu;
+        const int64_t planes = n_params(cfg->max_sh_degree) - N_GEO, G = c->gcap_u, N = cfg->max_gaussians;
+        bool ok = cudaHostAlloc((void **)&T.stage_h, planes * G * sizeof(float), cudaHostAllocDefault) == cudaSuccess &&
+                  cudaHostAlloc((void **)&T.cnt_h, G, cudaHostAllocDefault) == cudaSuccess &&
+                  cudaHostAlloc((void **)&T.counts_h, 2 * sizeof(int), cudaHostAllocDefault) == cudaSuccess;
+        for (int j = 0; j < 2 && ok; j++) {
+            CpuUpdateBuf &B = T.buf[j];
+            ok = cudaHostAlloc((void **)&B.uids, N * sizeof(int32_t), cudaHostAllocDefault) == cudaSuccess &&
+                 cudaHostAlloc((void **)&B.udelay, N, cudaHostAllocDefault) == cudaSuccess &&
+                 cudaHostAlloc((void **)&B.vids, G * sizeof(int32_t), cudaHostAllocDefault) == cudaSuccess &&
+                 cudaHostAlloc((void **)&B.grad, planes * G * sizeof(float), cudaHostAllocDefault) == cudaSuccess;
+        }
+        ok = ok && cudaStreamCreateWithFlags(&T.up, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&T.down, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.ev_up, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.ev_grad, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.ev_down, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            gs_destroy(c);
+            return GS_ERR_OOM;
+        }
+    }
     *out = c;
     return GS_OK;
 }
@@ -538,6 +625,21 @@ gs_status gs_destroy(gs_ctx *c)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
+    {
+        CpuTierState &T = c->cpu;
+        if (T.worker.joinable()) T.worker.join();
+        if (T.up) cudaStreamSynchronize(T.up);
+        if (T.down) cudaStreamSynchronize(T.down);
+        for (cudaEvent_t e : {T.ev_up, T.ev_grad, T.ev_down})
+            if (e) cudaEventDestroy(e);
+        if (T.up) cudaStreamDestroy(T.up);
+        if (T.down) cudaStreamDestroy(T.down);
+        for (void *p : {(void *)T.stage_h, (void *)T.cnt_h, (void *)T.counts_h})
+            if (p) cudaFreeHost(p);
+        for (CpuUpdateBuf &B : T.buf)
+            for (void *p : {(void *)B.uids, (void *)B.udelay, (void *)B.vids, (void *)B.grad})
+                if (p) cudaFreeHost(p);
+    }
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
     if (c->graph.graph) cudaGraphDestroy(c->graph.graph);
     timing_free(c);
@@ -572,6 +674,10 @@ gs_status gs_sync_status(gs_ctx *c, void *stream)
     if (!c) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "gs_sync_status");
+    if (c->cfg.cpu_opt) {               // host planes of GS_TIER_HOST_CPU_OPT scenes brought up to date
+        const gs_status st = cpu_flush(c);
+        if (st) return st;
+    }
     if (c->cstream && cudaStreamSynchronize(c->cstream) != cudaSuccess) return cuda_check(c, "gs_sync_status copies");
     if (c->dstream && cudaStreamSynchronize(c->dstream) != cudaSuccess) return cuda_check(c, "gs_sync_status copies");
     int st = 0;
@@ -1088,6 +1194,94 @@ gs_status gs_render_lists(const gs_ctx *c, const uint32_t **tile_of_key, const u
     return GS_OK;
 }
 
+gs_status gs_set_cpu_threads(gs_ctx *c, int32_t threads)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (c->cpu.worker.joinable()) c->cpu.worker.join();
+    c->cpu.threads = threads;
+    return GS_OK;
+}
+
+gs_status gs_cpu_tier_stats(const gs_ctx *c, double *stats)
+{
+    if (!c || !stats) return GS_ERR_INVALID_ARG;
+    const CpuTierState &T = c->cpu;
+    const double v[7] = {T.fwd_ms, T.lazy_ms, T.wait_ms, (double)T.h2d, (double)T.d2h, (double)T.rows,
+                         (double)T.left};
+    for (int i = 0; i < 7; i++) stats[i] = v[i];
+    return GS_OK;
+}
+
+// Arguments of the host-array optimizer calls (header).
+static bool cpu_args_ok(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0, int32_t planes,
+                        const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
+                        const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam, int32_t step)
+{
+    if (!w || !m || !v || pitch <= 0 || pitch >= (1ll << 31) || plane0 < 0 || planes < 1 || plane0 + planes > 59)
+        return false;
+    if (!valid_adam(adam) || adam->mode != GS_ADAM_DEFERRED || step < 0) return false;
+    if (n_upd < 0 || n_vis < 0 || (n_upd > 0 && (!uids || !udelay)) || (n_vis > 0 && (!vids || !grad)) ||
+        gpitch < n_vis)
+        return false;
+    for (int64_t u = 0; u < n_upd; u++)
+        if (uids[u] < 0 || uids[u] >= pitch || (u && uids[u] <= uids[u - 1]) || udelay[u] > adam->max_defer)
+            return false;
+    for (int64_t k = 0; k < n_vis; k++)
+        if (vids[k] < 0 || vids[k] >= pitch || (k && vids[k] <= vids[k - 1])) return false;
+    return true;
+}
+
+gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t pitch, int32_t plane0, int32_t planes,
+                               const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
+                               const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam,
+                               int32_t step, int32_t threads)
+{
+    if (step < 1 ||
+        !cpu_args_ok(w, m, v, pitch, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, gpitch, adam, step))
+        return GS_ERR_INVALID_ARG;
+    CpuUpdate U;
+    U.uids = uids;
+    U.udelay = udelay;
+    U.n_upd = n_upd;
+    U.vids = vids;
+    U.grad = grad;
+    U.n_vis = n_vis;
+    U.gpitch = gpitch;
+    U.lut = make_lut(adam, step, true, GS_FP32);
+    U.opt = adam->optimizer;
+    cpu_deferred_step(HostPlanes{w, m, v, pitch, plane0, planes}, U, threads);
+    return GS_OK;
+}
+
+gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0, int32_t planes,
+                         const int32_t *ids, const uint8_t *counter, int64_t n, const int32_t *uids,
+                         const uint8_t *udelay, int64_t n_upd, const int32_t *vids, const float *grad, int64_t n_vis,
+                         int64_t gpitch, const gs_adam_cfg *adam, int32_t step, float *out, int64_t opitch,
+                         int32_t threads)
+{
+    if (!cpu_args_ok(w, m, v, pitch, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, gpitch, adam, step) ||
+        n < 0 || (n > 0 && (!ids || !counter || !out)) || opitch < n)
+        return GS_ERR_INVALID_ARG;
+    if (n_upd > 0 && step < 1) return GS_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n; k++)
+        if (ids[k] < 0 || ids[k] >= pitch || (k && ids[k] <= ids[k - 1]) || counter[k] > adam->max_defer)
+            return GS_ERR_INVALID_ARG;
+    CpuUpdate U;
+    U.uids = uids;
+    U.udelay = udelay;
+    U.n_upd = n_upd;
+    U.vids = vids;
+    U.grad = grad;
+    U.n_vis = n_vis;
+    U.gpitch = gpitch;
+    if (n_upd > 0) U.lut = make_lut(adam, step, true, GS_FP32);
+    U.opt = adam->optimizer;
+    const DevLut Ln = make_lut(adam, step + 1, true, GS_FP32);
+    HostPlanes P{const_cast<float *>(w), const_cast<float *>(m), const_cast<float *>(v), pitch, plane0, planes};
+    cpu_forward(P, ids, counter, n, n_upd > 0 ? &U : nullptr, Ln, adam->optimizer, out, opitch, threads);
+    return GS_OK;
+}
+
 gs_status gs_host_tier_stats(const gs_ctx *c, int64_t *chunks, int64_t *bytes)
 {
     if (!c || !chunks || !bytes) return GS_ERR_INVALID_ARG;
@@ -1135,7 +1329,7 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
         const int64_t nw = (sv.n + 31) / 32;
         cudaMemsetAsync(c->union_mask, 0, nw * sizeof(uint32_t), s);
         for (int v = 0; v < n_views; v++) launch_mask_or(c->union_mask, c->vmask[v], nw, c->w, s);
-        compact_mask(c->union_mask, sv.n, c->union_chunk, false, nullptr, c->union_prefix, (int)c->gcap_u,
+        compact_mask(c->union_mask, sv.n, c->union_chunk, false, c->cpu.ids_d, c->union_prefix, (int)c->gcap_u,
                      &c->cnt->n_union, c->w, s);
         M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u, selected};
     }
@@ -1377,6 +1571,184 @@ static gs_status step_host_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv,
     return cuda_check(c, "gs_step host tier");
 }
 
+// ---------------------------------------------------------------------------
+// GS_TIER_HOST_CPU_OPT: the paper's offloaded configuration with the SH
+// optimizer on the host cores (§4.2.2 parameter forwarding, §4.3 deferred
+// update with OpenMP).
+
+static double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+static CpuUpdate cpu_update_of(const CpuUpdateBuf &B, int64_t gpitch)
+{
+    CpuUpdate U;
+    U.uids = B.uids;
+    U.udelay = B.udelay;
+    U.n_upd = B.n_upd;
+    U.vids = B.vids;
+    U.grad = B.grad;
+    U.n_vis = B.n_vis;
+    U.gpitch = gpitch;
+    U.lut = B.lut;
+    U.opt = B.opt;
+    return U;
+}
+
+// Apply every held update to its host planes, oldest first (the worker's
+// first): the host planes are then the state after the last step.
+static gs_status cpu_flush(gs_ctx *c)
+{
+    CpuTierState &T = c->cpu;
+    if (T.worker.joinable()) T.worker.join();
+    if (T.down_pending) {
+        if (cudaEventSynchronize(T.ev_down) != cudaSuccess) return cuda_check(c, "cpu tier: gradients");
+        T.down_pending = false;
+    }
+    CpuUpdateBuf *order[2] = {&T.buf[0], &T.buf[1]};
+    if (order[0]->full && order[1]->full && order[1]->step < order[0]->step) std::swap(order[0], order[1]);
+    for (CpuUpdateBuf *B : order)
+        if (B->full) {
+            cpu_deferred_step(B->planes, cpu_update_of(*B, c->gcap_u), T.threads);
+            B->full = false;
+        }
+    return GS_OK;
+}
+
+// One step.  Host: (A) the worker that applied the update of two steps back is
+// joined; (B) after the cull, the visible ids and their counters are read
+// (one synchronisation); (C) their SH rows are forwarded from the host planes
+// and the previous step's held update into a pinned block, copied to the
+// device in pieces as they are ready; (D) a worker thread applies the previous
+// step's update to the host planes.  Device (meanwhile): render with the
+// forwarded rows, backward, the select and the step of the geometry planes.
+// (E) The update-set size and members are read (second synchronisation) and
+// the SH gradients copied back on a side stream; they are held for the next
+// step.  No graph: the host takes part in every step.
+static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0, const DevArgs &a, int n_views,
+                               const gs_adam_cfg *adam, float *loss, cudaStream_t s)
+{
+    if (adam->mode != GS_ADAM_DEFERRED) return fail(c, GS_ERR_INVALID_ARG, "the host-core optimizer runs deferred");
+    CpuTierState &T = c->cpu;
+    const auto t_start = std::chrono::steady_clock::now();
+    if (T.worker.joinable()) T.worker.join();                       // (A)
+    T.wait_ms = ms_since(t_start);
+    const int planes = sv0.D - N_GEO;
+    const int64_t G = c->gcap_u;
+    const HostPlanes HP{(float *)scene->host_sh, (float *)scene->host_m, (float *)scene->host_v, scene->pitch, N_GEO,
+                        planes};
+    const int32_t t1 = scene->step + 1;
+    CpuUpdateBuf &P = T.buf[(t1 - 1) & 1], &B = T.buf[t1 & 1];
+    // held updates other than this scene's previous step are applied first
+    const bool prev_ours = P.full && P.planes.w == HP.w && P.step == t1 - 1;
+    if ((B.full || (P.full && !prev_ours))) {
+        if (prev_ours) {
+            P.full = false;                     // keep it out of the flush
+            const gs_status st = cpu_flush(c);
+            P.full = true;
+            if (st) return st;
+        } else {
+            const gs_status st = cpu_flush(c);
+            if (st) return st;
+        }
+    }
+    c->w.capturing = false;
+    c->w.tev = c->t_events ? c->t_events + (size_t)c->t_used * TP_COUNT : nullptr;
+    struct TevReset {
+        gs_ctx *c;
+        ~TevReset() { c->w.tev = nullptr; }
+    } tev_reset{c};
+    // (B)
+    const StepMasks M = enqueue_cull_phase(c, sv0, a, n_views, loss, s, adam->max_defer);
+    const int32_t *vis_d = n_views > 1 ? T.ids_d : c->vids[0];
+    const int *nvis_d = n_views > 1 ? &c->cnt->n_union : c->nvis_view;
+    launch_gather_u8(sv0.counter, vis_d, nvis_d, (int)M.gcap, T.cnt_d, c->w, s);
+    cudaMemcpyAsync(T.counts_h, nvis_d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "cpu tier: visible count");
+    const int64_t nv = std::min<int64_t>(std::max(T.counts_h[0], 0), M.gcap);
+    cudaMemcpyAsync(B.vids, vis_d, nv * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(T.cnt_h, T.cnt_d, nv, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "cpu tier: visible set");
+    if (T.down_pending) {                                            // the previous step's gradients
+        if (cudaEventSynchronize(T.ev_down) != cudaSuccess) return cuda_check(c, "cpu tier: gradients");
+        T.down_pending = false;
+    }
+    T.d2h = nv * 5 + 4;
+    // (C)
+    const CpuUpdate PU = cpu_update_of(P, G);
+    const auto t_fwd = std::chrono::steady_clock::now();
+    constexpr int64_t PIECE = 1 << 16;
+    for (int64_t k0 = 0; k0 < nv; k0 += PIECE) {
+        const int64_t k1 = std::min(nv, k0 + PIECE);
+        cpu_forward(HP, B.vids + k0, T.cnt_h + k0, k1 - k0, P.full ? &PU : nullptr, a.lut, adam->optimizer,
+                    T.stage_h + k0, G, T.threads);
+        cudaMemcpy2DAsync(T.stage_d + k0, G * sizeof(float), T.stage_h + k0, G * sizeof(float),
+                          (k1 - k0) * sizeof(float), planes, cudaMemcpyHostToDevice, T.up);
+    }
+    cudaEventRecord(T.ev_up, T.up);
+    T.fwd_ms = ms_since(t_fwd);
+    T.rows = nv;
+    T.h2d = nv * planes * (int64_t)sizeof(float);
+    // (D)
+    if (P.full) {
+        const int threads = T.threads;
+        CpuUpdateBuf *Pp = &P;
+        T.worker = std::thread([&T, Pp, G, threads] {
+            const auto t0 = std::chrono::steady_clock::now();
+            cpu_deferred_step(Pp->planes, cpu_update_of(*Pp, G), threads);
+            T.lazy_ms = ms_since(t0);
+            Pp->full = false;
+        });
+    } else {
+        T.lazy_ms = 0.0;
+    }
+    // device: render with the forwarded rows, backward, select, geometry step
+    cudaStreamWaitEvent(s, T.ev_up, 0);
+    SceneView sv = sv0;
+    sv.sh.cmask = M.gmask;
+    sv.sh.cprefix = M.gprefix;
+    enqueue_render_phase(c, sv, a, n_views, M, loss, s);
+    DevArgs *args = c->args + SLOT_STEP;
+    c->w.mark(TP_ADAM0, s);
+    if (M.selected)
+        launch_adam_compact(sv, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+    else
+        launch_adam_select(sv, args, M.gmask, c->umask, c->uchunk, c->uids, c->udelay, &c->cnt->n_upd, c->w, s);
+    SceneView gv = sv;
+    gv.D = N_GEO;                                                    // the geometry planes only
+    c->w.mark(TP_APPLY0, s);
+    launch_adam_apply(gv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->uids, c->udelay, nullptr, &c->cnt->n_upd,
+                      c->w, s);
+    c->w.mark(TP_APPLY1, s);
+    c->w.mark(TP_ADAM1, s);
+    c->w.mark(TP_STEP1, s);
+    // (E)
+    cudaMemcpyAsync(T.counts_h + 1, &c->cnt->n_upd, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(T.ev_grad, s);
+    cudaStreamWaitEvent(T.down, T.ev_grad, 0);
+    cudaMemcpy2DAsync(B.grad, G * sizeof(float), c->grad_u + (int64_t)N_GEO * M.gcap, M.gcap * sizeof(float),
+                      nv * sizeof(float), planes, cudaMemcpyDeviceToHost, T.down);
+    cudaEventRecord(T.ev_down, T.down);
+    T.down_pending = true;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "cpu tier: update size");
+    const int64_t nu = std::min<int64_t>(std::max(T.counts_h[1], 0), sv0.n);
+    cudaMemcpyAsync(B.uids, c->uids, nu * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(B.udelay, c->udelay, nu, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "cpu tier: update set");
+    B.n_upd = nu;
+    B.n_vis = nv;
+    B.step = t1;
+    B.lut = a.lut;
+    B.opt = adam->optimizer;
+    B.planes = HP;
+    B.full = true;
+    T.left = nu;
+    T.d2h += nu * 5 + nv * planes * (int64_t)sizeof(float) + 4;
+    if (c->w.tev) c->t_used++;
+    return cuda_check(c, "gs_step cpu tier");
+}
+
 static bool graph_matches(const GraphCache &g, const gs_scene *sc, const gs_camera *views, int n_views, int mode,
                           float *loss, bool timed, int variant, uint32_t first_wait, int opt)
 {
@@ -1415,6 +1787,11 @@ gs_status gs_step(gs_ctx *c, gs_scene *scene, const gs_camera *views, const floa
     if (timed && c->t_used >= c->t_max) return fail(c, GS_ERR_CAPACITY, "timing buffer full: call gs_timing_read");
     if (scene->tier == GS_TIER_HOST_SH) {
         st = step_host_tier(c, scene, sv, a, n_views, adam, loss_out, s);
+        if (!st) scene->step += 1;
+        return st;
+    }
+    if (scene->tier == GS_TIER_HOST_CPU_OPT) {
+        st = step_cpu_tier(c, scene, sv, a, n_views, adam, loss_out, s);
         if (!st) scene->step += 1;
         return st;
     }

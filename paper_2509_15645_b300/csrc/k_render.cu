@@ -83,7 +83,16 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         if (L.restore) {
             const int d = sc.counter[i];
             if (d) {
-                if (sc.rdir && sc.sh.rdir) {
+                if (sc.sh.current) {
+                    // forwarded SH rows are current: only the geometry planes are restored
+                    const T *mp = (const T *)sc.m, *vp = (const T *)sc.v;
+#pragma unroll
+                    for (int r = 0; r < N_GEO; r++) {
+                        const float dir = sc.rdir ? __ldg(sc.rdir + r * pitch + i)
+                                                  : restore_dir<OPT>(ld_val(mp + r * pitch + i), ld_val(vp + r * pitch + i), L.eps);
+                        w[r] = restore_with_dir<OPT>(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
+                    }
+                } else if (sc.rdir && sc.sh.rdir) {
                     const T *rsh = (const T *)sc.sh.rdir;
 #pragma unroll
                     for (int r = 0; r < D; r++) {

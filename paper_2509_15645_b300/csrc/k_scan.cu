@@ -265,4 +265,19 @@ void compact_mask(const uint32_t *mask, int64_t n, uint32_t *chunk_cnt, bool hav
         mask, n, nwords, chunk_cnt, ids, word_prefix, cap, counter, delay);
 }
 
+// dst[k] = src[ids[k]] for k < min(*n, cap): a byte per id (defer counters of
+// a compact id list).
+__global__ void k_gather_u8(const uint8_t *__restrict__ src, const int32_t *__restrict__ ids, const int *n_p, int cap,
+                            uint8_t *__restrict__ dst)
+{
+    const int n = min(*n_p, cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[k] = src[ids[k]];
+}
+
+void launch_gather_u8(const uint8_t *src, const int32_t *ids, const int *n, int cap, uint8_t *dst, Work &w,
+                      cudaStream_t s)
+{
+    k_gather_u8<<<w.grid(cap, 256, 4), 256, 0, s>>>(src, ids, n, cap, dst);
+}
+
 }  // namespace gs

@@ -61,7 +61,13 @@ def test_densify_matches_oracle(gs, orc, prec_name):
     g = np.where(denom > 0, accum.astype(np.float64) / np.maximum(denom, 1), 0.0)
     smax = np.exp(wc[3:6]).max(axis=0)
     thr, pd, min_op = 2e-4, 0.01, 0.005
-    extent = float(np.median(smax[g >= thr]) / pd) * 1.0001
+    # the split threshold pd * extent in the widest gap between the sorted
+    # largest scales near the median of the densified Gaussians' (no tie)
+    allv = np.sort(smax)
+    i = int(np.searchsorted(allv, np.median(smax[g >= thr])))
+    win = allv[max(i - 20, 0):i + 21]
+    j = int(np.argmax(np.diff(win)))
+    extent = float(np.sqrt(win[j] * win[j + 1]) / pd)
     opac = 1.0 / (1.0 + np.exp(-wc[10]))
     for q, lim in ((g, thr), (smax, pd * extent), (opac, min_op)):
         assert np.min(np.abs(q - lim) / lim) > 1e-5, "a decision sits on its threshold: pick other inputs"
