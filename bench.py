@@ -514,6 +514,12 @@ def run_ours(args):
                 ca[k] = round(ca[k], 4 if k.endswith("frac") else 1)
         return m
 
+    # DRAM bytes per launch of the rasterizer backward on this workload (10M,
+    # 1920x1080, one view), by variant, from one ncu capture of
+    # dram__bytes_read.sum + dram__bytes_write.sum (profiles/launches_aerial10m_1080p.md,
+    # profiles/raster_bwd_variants_aerial2m_density10m.md); other workloads: not captured
+    RASTER_BWD_TRAFFIC = {7: 125.1e6, 8: 125.1e6, 9: 219.1e6}
+
     def roofline(m):
         """Roofline entry of the kernel with the largest live event time per step."""
         st = m["st"]
@@ -529,7 +535,10 @@ def run_ours(args):
                     "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                     "peak_source": f"derived: {n_sms} SMs (device attribute) x 128 FP32 lanes x 2 flop/FMA x "
                                    f"{sm_max:g} MHz (maximum SM clock)",
-                    "algorithmic_flops_per_launch": round(flops), "traffic": None}
+                    "algorithmic_flops_per_launch": round(flops),
+                    "traffic": (RASTER_BWD_TRAFFIC.get(m["variant"][1]) if cfg_note == WORKLOAD and m["variant"]
+                                else None),
+                    "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
         b = m["b_apply"] if dom == "k_adam_apply" else m["b_cull"]
         t = st["adam_apply"] if dom == "k_adam_apply" else st["cull"]
         return {"kernel": dom, "bound": "hbm", "achieved": round(gbs(b, t), 1), "peak": peak, "unit": "GB/s",
@@ -670,18 +679,22 @@ def run_ours(args):
 
 
 def extra_forms(args):
-    """The batched BF16 form and the host-offload configuration, each timed by
-    this script in a subprocess of its own (same K and W) after the main line:
+    """The batched BF16 form, the host-offload configuration and the paper's
+    host-core optimizer configuration, each timed by this script in a
+    subprocess of its own (same K and W) after the main line:
     batched_bf16 = 10M resident, 4 views of 1600x1200 per step, bf16 SH and
     moments; host_tier_40m = 40M Gaussians on the 2x2 km field (the 10M
     field's density) with a 24 GB
     HBM budget (SH planes and their moments in pinned host memory), 4 views of
-    1600x1200 per step, fp32 and bf16."""
+    1600x1200 per step, fp32 and bf16; cpu_optimizer_10m = the 10M 1080p
+    workload with its SH planes in host memory stepped by the host cores
+    (parameter forwarding and the deferred update, §4.2.2 and §4.3)."""
     runs = {"batched_bf16": ["--bf16-only", "--views-per-step", "4", "--image", "1600x1200"],
             "host_tier_40m_fp32": ["--gaussians", "40000000", "--density-of", "10000000", "--budget-gb", "24",
                                    "--views-per-step", "4", "--image", "1600x1200"],
             "host_tier_40m_bf16": ["--gaussians", "40000000", "--density-of", "10000000", "--budget-gb", "24",
-                                   "--views-per-step", "4", "--image", "1600x1200", "--bf16-only"]}
+                                   "--views-per-step", "4", "--image", "1600x1200", "--bf16-only"],
+            "cpu_optimizer_10m": ["--cpu-optimizer"]}
     out = {}
     for name, extra in runs.items():
         cmd = [sys.executable, os.path.abspath(__file__), "--steps", str(args.steps), "--warmup", str(args.warmup),
@@ -694,7 +707,7 @@ def extra_forms(args):
         except Exception as e:
             sub = {"error": repr(e)[:400]}
         keep = ("value", "unit", "ms_per_step", "stages_ms", "cull_adam", "roofline", "clocks", "e2e", "config",
-                "host_tier", "gpu_launches", "error")
+                "host_tier", "cpu_optimizer", "gpu_launches", "error")
         out[name] = {k: sub[k] for k in keep if k in sub}
         out[name]["wall_s"] = round(time.time() - t0, 1)
     return out

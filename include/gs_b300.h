@@ -95,7 +95,9 @@ enum { GS_FP32 = 0, GS_BF16_SH_MOM = 1, GS_BF16_SH_MOM_RN = 2 };
  * optimizer of the SH planes on the host cores (§4.2.2 parameter forwarding,
  * §4.3 deferred update with OpenMP), for comparison with GS_TIER_HOST_SH,
  * whose SH rows are stepped by device kernels.  The scene is laid out as in
- * GS_TIER_HOST_SH, fp32 only; the context needs gs_config.cpu_opt = 1.  Per
+ * GS_TIER_HOST_SH except that host_sh, host_m and host_v are Gaussian-major,
+ * [pitch][D-11] (the row of Gaussian i at i * (D-11)), fp32 only; the context
+ * needs gs_config.cpu_opt = 1.  Per
  * gs_step: the cull (with the optimizer's select) on the device and one host
  * synchronisation for the step's visible Gaussians (the union over its views)
  * and their defer counters; the host forwards their SH values (the previous
@@ -470,35 +472,36 @@ GS_API gs_status gs_render_lists(const gs_ctx *ctx, const uint32_t **tile_of_key
 
 /* Deferred optimizer step on host arrays, on the host cores (§4.3 with
  * OpenMP: the update GS_TIER_HOST_CPU_OPT applies to its SH planes, callable
- * alone).  w, m, v: host [planes][pitch] fp32, the parameter rows plane0 ..
- * plane0 + planes - 1 of the scene's parameter vector (learning-rate group of
- * each row as in gs_step; plane0 + planes <= 59).  uids[0..n_upd): the update
- * set, ascending Gaussian ids in [0, pitch), with udelay its delays (0..15);
- * vids[0..n_vis): ascending ids with a gradient row, grad[r * gpitch + k] the
- * gradient of row plane0 + r of Gaussian vids[k] (gpitch >= n_vis); members
- * without a row step with zero gradient.  One step t = step (>= 1) with the
- * tables of gs_adam_tables(adam, step), in FP32 (IEEE square root and
- * division).  threads <= 0: every core.  Errors (nothing written):
- * GS_ERR_INVALID_ARG for a null array with a non-zero count, bad sizes, ids out
- * of order or out of range, or an invalid adam (mode must be deferred).  All
- * memory is the caller's. */
-GS_API gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t pitch, int32_t plane0, int32_t planes,
-                                      const int32_t *uids, const uint8_t *udelay, int64_t n_upd,
-                                      const int32_t *vids, const float *grad, int64_t n_vis, int64_t gpitch,
+ * alone).  w, m, v: host fp32, Gaussian-major: the value of parameter row
+ * plane0 + r of Gaussian i at [i * row + r] (0 <= r < planes <= row,
+ * plane0 + planes <= 59; learning-rate group of each row as in gs_step),
+ * Gaussians 0 .. n_rows - 1.  uids[0..n_upd): the update set, ascending ids
+ * below n_rows, with udelay its delays (0..max_defer); vids[0..n_vis):
+ * ascending ids with a gradient row, grad[k * grow + r] the gradient of row
+ * plane0 + r of Gaussian vids[k] (grow >= planes); members without a row step
+ * with zero gradient.  One step t = step (>= 1) with the tables of
+ * gs_adam_tables(adam, step), in FP32 (IEEE square root and division).
+ * threads <= 0: every core.  Errors (nothing written): GS_ERR_INVALID_ARG for a
+ * null array with a non-zero count, bad sizes, ids out of order or out of
+ * range, or an invalid adam (mode must be deferred).  All memory is the
+ * caller's. */
+GS_API gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t n_rows, int32_t row, int32_t plane0,
+                                      int32_t planes, const int32_t *uids, const uint8_t *udelay, int64_t n_upd,
+                                      const int32_t *vids, const float *grad, int64_t n_vis, int64_t grow,
                                       const gs_adam_cfg *adam, int32_t step, int32_t threads);
 
 /* Parameter forwarding (§4.2.2) on host arrays: out[r * opitch + k] (host,
- * opitch >= n) = row plane0 + r of Gaussian ids[k] as the next step, step + 1,
- * sees it, without writing w, m, v.  counter[k]: that Gaussian's defer counter
- * at step + 1; > 0 restores over counter[k] deferred steps (tables of step + 1),
- * 0 applies the pending update of step `step` (uids .. gpitch as in
- * gs_cpu_deferred_step; n_upd = 0 for none) if ids[k] is one of its members,
- * else takes the stored value.  ids ascending.  Errors as gs_cpu_deferred_step
- * (step >= 0 here). */
-GS_API gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0,
-                                int32_t planes, const int32_t *ids, const uint8_t *counter, int64_t n,
+ * plane-major, opitch >= n) = row plane0 + r of Gaussian ids[k] as the next
+ * step, step + 1, sees it, without writing w, m, v (laid out as in
+ * gs_cpu_deferred_step).  counter[k]: that Gaussian's defer counter at step + 1;
+ * > 0 restores over counter[k] deferred steps (tables of step + 1), 0 applies
+ * the pending update of step `step` (uids .. grow as in gs_cpu_deferred_step;
+ * n_upd = 0 for none) if ids[k] is one of its members, else takes the stored
+ * value.  ids ascending.  Errors as gs_cpu_deferred_step (step >= 0 here). */
+GS_API gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t n_rows, int32_t row,
+                                int32_t plane0, int32_t planes, const int32_t *ids, const uint8_t *counter, int64_t n,
                                 const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
-                                const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam,
+                                const float *grad, int64_t n_vis, int64_t grow, const gs_adam_cfg *adam,
                                 int32_t step, float *out, int64_t opitch, int32_t threads);
 
 /* OpenMP threads of the host-core optimizer of GS_TIER_HOST_CPU_OPT steps

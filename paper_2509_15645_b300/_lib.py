@@ -81,10 +81,10 @@ EXPORTS = {
                                C.POINTER(c_f32), C.POINTER(c_f32), C.POINTER(c_f32)]),
     "gs_step": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(c_vp), c_i32, C.POINTER(AdamCfg),
                         c_vp, c_vp]),
-    "gs_cpu_deferred_step": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
-                                     c_i64, C.POINTER(AdamCfg), c_i32, c_i32]),
-    "gs_cpu_forward": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp,
-                               c_vp, c_i64, c_i64, C.POINTER(AdamCfg), c_i32, c_vp, c_i64, c_i32]),
+    "gs_cpu_deferred_step": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp,
+                                     c_i64, c_i64, C.POINTER(AdamCfg), c_i32, c_i32]),
+    "gs_cpu_forward": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64,
+                               c_vp, c_vp, c_i64, c_i64, C.POINTER(AdamCfg), c_i32, c_vp, c_i64, c_i32]),
     "gs_set_cpu_threads": (c_i32, [c_vp, c_i32]),
     "gs_cpu_tier_stats": (c_i32, [c_vp, C.POINTER(C.c_double)]),
 }

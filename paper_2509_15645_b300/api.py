@@ -121,7 +121,10 @@ class GaussianScene:
     [11][pitch]) and ``rdir_geo`` stay on the device; the SH planes ``sh`` and
     their ``m_sh``, ``v_sh`` are pinned host tensors [D-11][pitch] that gs_step
     streams (read them after ``Context.sync_status``, or from work enqueued on a
-    stream after ``Context.wait_copies``)."""
+    stream after ``Context.wait_copies``).  tier GS_TIER_HOST_CPU_OPT (fp32):
+    the same, with ``sh``, ``m_sh``, ``v_sh`` one row per Gaussian,
+    [pitch][D-11], stepped by the host cores (read them after
+    ``Context.sync_status``)."""
 
     def __init__(self, params, sh_degree: int, device="cuda", with_optimizer=True, with_rdir=True,
                  precision=L.GS_FP32, tier=L.GS_TIER_DEVICE):
@@ -143,12 +146,18 @@ class GaussianScene:
             pin = dict(device="cpu", pin_memory=True)
             self.geo = torch.zeros(11, P, dtype=torch.float32, device=device)
             self.geo[:, :n] = src[:11].to(device)
-            self.sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
-            self.sh[:, :n] = src[11:].to(mdtype)
             self.m = torch.zeros(11, P, dtype=mdtype, device=device)
             self.v = torch.zeros(11, P, dtype=mdtype, device=device)
-            self.m_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
-            self.v_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+            if tier == L.GS_TIER_HOST_CPU_OPT:       # one row of SH values per Gaussian
+                self.sh = torch.zeros(P, D - 11, dtype=mdtype, **pin)
+                self.sh[:n] = src[11:].T.to(mdtype)
+                self.m_sh = torch.zeros(P, D - 11, dtype=mdtype, **pin)
+                self.v_sh = torch.zeros(P, D - 11, dtype=mdtype, **pin)
+            else:
+                self.sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+                self.sh[:, :n] = src[11:].to(mdtype)
+                self.m_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
+                self.v_sh = torch.zeros(D - 11, P, dtype=mdtype, **pin)
             self.counter = torch.zeros(P, dtype=torch.uint8, device=device)
             if with_rdir:     # geometry directions only: the SH ones are recomputed on the device
                 self.rdir_geo = torch.zeros(11, P, dtype=torch.float32, device=device)
@@ -198,18 +207,22 @@ class GaussianScene:
         s.step = self.step
         return s
 
+    def _sh_planes(self, t):
+        """[D-11][n] view of SH planes (host rows of the CPU-optimizer tier transposed)."""
+        return t[:self.n].T if self.tier == L.GS_TIER_HOST_CPU_OPT else t[:, :self.n]
+
     def params(self):
         """Stored parameters as float32 [D][n] on the geometry's device."""
         if self.w is not None:
             return self.w[:, :self.n]
-        return torch.cat([self.geo[:, :self.n], self.sh[:, :self.n].to(self.geo.device).float()])
+        return torch.cat([self.geo[:, :self.n], self._sh_planes(self.sh).to(self.geo.device).float()])
 
     def moments(self):
         """(m, v) as float32 [D][n] on the geometry's device."""
         if self.tier != L.GS_TIER_DEVICE:
             dev = self.geo.device
-            return (torch.cat([self.m[:, :self.n].float(), self.m_sh[:, :self.n].to(dev).float()]),
-                    torch.cat([self.v[:, :self.n].float(), self.v_sh[:, :self.n].to(dev).float()]))
+            return (torch.cat([self.m[:, :self.n].float(), self._sh_planes(self.m_sh).to(dev).float()]),
+                    torch.cat([self.v[:, :self.n].float(), self._sh_planes(self.v_sh).to(dev).float()]))
         return self.m[:, :self.n].float(), self.v[:, :self.n].float()
 
 
@@ -515,16 +528,17 @@ def _np_ptr(a, dtype):
 
 def cpu_deferred_step(w, m, v, plane0, uids, udelay, vids, grad, adam, step, threads=0):
     """Deferred optimizer step on host arrays (gs_cpu_deferred_step): w, m, v
-    float32 [planes][pitch] numpy arrays (updated in place), rows plane0.. of the
-    parameter vector; uids / udelay the update set; vids ascending ids with
-    gradient rows grad float32 [planes][gpitch]."""
+    float32 [n][planes] numpy arrays, one row per Gaussian (updated in place),
+    holding parameter rows plane0.. ; uids / udelay the update set; vids
+    ascending ids with gradient rows grad float32 [len(vids)][planes]."""
     import numpy as np
-    planes, pitch = w.shape
-    gp = grad.shape[1] if grad.size else max(len(vids), 1)
-    st = L.load().gs_cpu_deferred_step(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32), pitch,
-                                       int(plane0), planes, _np_ptr(uids, np.int32), _np_ptr(udelay, np.uint8),
-                                       len(uids), _np_ptr(vids, np.int32), _np_ptr(grad, np.float32), len(vids), gp,
-                                       C.byref(adam), int(step), int(threads))
+    n_rows, planes = w.shape
+    grow = grad.shape[1] if grad.ndim == 2 and grad.shape[1] else planes
+    st = L.load().gs_cpu_deferred_step(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32),
+                                       n_rows, planes, int(plane0), planes, _np_ptr(uids, np.int32),
+                                       _np_ptr(udelay, np.uint8), len(uids), _np_ptr(vids, np.int32),
+                                       _np_ptr(grad, np.float32), len(vids), grow, C.byref(adam), int(step),
+                                       int(threads))
     if st != L.GS_OK:
         raise L.GsError(st, "gs_cpu_deferred_step")
 
@@ -532,16 +546,17 @@ def cpu_deferred_step(w, m, v, plane0, uids, udelay, vids, grad, adam, step, thr
 def cpu_forward(w, m, v, plane0, ids, counter, uids, udelay, vids, grad, adam, step, threads=0):
     """Parameter forwarding on host arrays (gs_cpu_forward): the values of
     Gaussians ``ids`` (with defer counters ``counter`` at step + 1) as step + 1
-    sees them, float32 [planes][len(ids)]."""
+    sees them, float32 [planes][len(ids)] (w, m, v and grad as in
+    cpu_deferred_step)."""
     import numpy as np
-    planes, pitch = w.shape
+    n_rows, planes = w.shape
     n = len(ids)
     out = np.zeros((planes, max(n, 1)), np.float32)
-    gp = grad.shape[1] if grad.size else max(len(vids), 1)
-    st = L.load().gs_cpu_forward(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32), pitch,
-                                 int(plane0), planes, _np_ptr(ids, np.int32), _np_ptr(counter, np.uint8), n,
+    grow = grad.shape[1] if grad.ndim == 2 and grad.shape[1] else planes
+    st = L.load().gs_cpu_forward(_np_ptr(w, np.float32), _np_ptr(m, np.float32), _np_ptr(v, np.float32), n_rows,
+                                 planes, int(plane0), planes, _np_ptr(ids, np.int32), _np_ptr(counter, np.uint8), n,
                                  _np_ptr(uids, np.int32), _np_ptr(udelay, np.uint8), len(uids),
-                                 _np_ptr(vids, np.int32), _np_ptr(grad, np.float32), len(vids), gp, C.byref(adam),
+                                 _np_ptr(vids, np.int32), _np_ptr(grad, np.float32), len(vids), grow, C.byref(adam),
                                  int(step), _np_ptr(out, np.float32), out.shape[1], int(threads))
     if st != L.GS_OK:
         raise L.GsError(st, "gs_cpu_forward")

@@ -10,24 +10,24 @@
 
 namespace gs {
 
-// Rows [plane0, plane0 + planes) of the parameter vector, plane-major:
-// element (r, i) at r * pitch + i of each array.
+// Rows [plane0, plane0 + planes) of the parameter vector, Gaussian-major:
+// the value of row plane0 + r of Gaussian i at i * row + r of each array.
 struct HostPlanes {
     float *w, *m, *v;
-    int64_t pitch;
-    int plane0, planes;
+    int64_t row;            // floats per Gaussian, >= planes
+    int plane0, planes;     // planes <= 64
 };
 
 // One step's update, held until the host applies it: members (ascending ids)
 // with their delays, the Gaussians with a gradient row (ascending ids) and
-// those rows ([planes][gpitch], row k for vids[k]), the step's tables.
+// those rows (row k, for vids[k], at grad + k * grow), the step's tables.
 struct CpuUpdate {
     const int32_t *uids = nullptr;
     const uint8_t *udelay = nullptr;
     int64_t n_upd = 0;
     const int32_t *vids = nullptr;
     const float *grad = nullptr;
-    int64_t n_vis = 0, gpitch = 0;
+    int64_t n_vis = 0, grow = 0;
     DevLut lut{};
     int opt = GS_OPT_ADAM;
 };
@@ -37,7 +37,8 @@ struct CpuUpdate {
 void cpu_deferred_step(const HostPlanes &P, const CpuUpdate &U, int threads);
 
 // Parameter forwarding (§4.2.2 step 1): the current values of Gaussians
-// ids[0..n) for the next step, written to out[r * opitch + k], without
+// ids[0..n) (ascending) for the next step, written plane-major to
+// out[r * opitch + k] (the layout the device reads), without
 // changing the planes.  cnt[k] is Gaussian ids[k]'s defer counter at the next
 // step: > 0 restores over that many deferred steps with the next step's tables
 // `Ln`; 0 applies the member's pending update `U` (if it is in U's update set,

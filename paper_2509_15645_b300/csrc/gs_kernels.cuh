@@ -49,6 +49,9 @@ void scan_exclusive(const uint32_t *in, uint32_t *out, ScanLen L, Work &w, int *
 // scan_exclusive); the total goes to total_out, clamped to cap with
 // GS_ERR_CAPACITY latched above it.
 void scan_counts(uint32_t *v, int64_t len, int *total_out, int cap, Work &w, cudaStream_t s);
+// dst[k * planes + r] = src[r * spitch + k] for k < min(*n, cap), r < planes.
+void launch_to_rows(const float *src, int64_t spitch, int planes, const int *n, int cap, float *dst, Work &w,
+                    cudaStream_t s);
 // dst[k] = src[ids[k]] for k < min(*n, cap).
 void launch_gather_u8(const uint8_t *src, const int32_t *ids, const int *n, int cap, uint8_t *dst, Work &w,
                       cudaStream_t s);

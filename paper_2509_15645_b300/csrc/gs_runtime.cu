@@ -1213,32 +1213,29 @@ gs_status gs_cpu_tier_stats(const gs_ctx *c, double *stats)
 }
 
 // Arguments of the host-array optimizer calls (header).
-static bool cpu_args_ok(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0, int32_t planes,
-                        const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
-                        const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam, int32_t step)
+static bool cpu_args_ok(const float *w, const float *m, const float *v, int64_t n_rows, int32_t row, int32_t plane0,
+                        int32_t planes, const int32_t *uids, const uint8_t *udelay, int64_t n_upd,
+                        const int32_t *vids, const float *grad, int64_t n_vis, int64_t grow,
+                        const gs_adam_cfg *adam, int32_t step)
 {
-    if (!w || !m || !v || pitch <= 0 || pitch >= (1ll << 31) || plane0 < 0 || planes < 1 || plane0 + planes > 59)
+    if (!w || !m || !v || n_rows <= 0 || n_rows >= (1ll << 31) || plane0 < 0 || planes < 1 || planes > 64 ||
+        row < planes || plane0 + planes > 59)
         return false;
     if (!valid_adam(adam) || adam->mode != GS_ADAM_DEFERRED || step < 0) return false;
     if (n_upd < 0 || n_vis < 0 || (n_upd > 0 && (!uids || !udelay)) || (n_vis > 0 && (!vids || !grad)) ||
-        gpitch < n_vis)
+        grow < planes)
         return false;
     for (int64_t u = 0; u < n_upd; u++)
-        if (uids[u] < 0 || uids[u] >= pitch || (u && uids[u] <= uids[u - 1]) || udelay[u] > adam->max_defer)
+        if (uids[u] < 0 || uids[u] >= n_rows || (u && uids[u] <= uids[u - 1]) || udelay[u] > adam->max_defer)
             return false;
     for (int64_t k = 0; k < n_vis; k++)
-        if (vids[k] < 0 || vids[k] >= pitch || (k && vids[k] <= vids[k - 1])) return false;
+        if (vids[k] < 0 || vids[k] >= n_rows || (k && vids[k] <= vids[k - 1])) return false;
     return true;
 }
 
-gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t pitch, int32_t plane0, int32_t planes,
-                               const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
-                               const float *grad, int64_t n_vis, int64_t gpitch, const gs_adam_cfg *adam,
-                               int32_t step, int32_t threads)
+static CpuUpdate host_update(const int32_t *uids, const uint8_t *udelay, int64_t n_upd, const int32_t *vids,
+                             const float *grad, int64_t n_vis, int64_t grow, const gs_adam_cfg *adam, int32_t step)
 {
-    if (step < 1 ||
-        !cpu_args_ok(w, m, v, pitch, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, gpitch, adam, step))
-        return GS_ERR_INVALID_ARG;
     CpuUpdate U;
     U.uids = uids;
     U.udelay = udelay;
@@ -1246,38 +1243,41 @@ gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t pitch, int3
     U.vids = vids;
     U.grad = grad;
     U.n_vis = n_vis;
-    U.gpitch = gpitch;
-    U.lut = make_lut(adam, step, true, GS_FP32);
+    U.grow = grow;
+    if (step >= 1) U.lut = make_lut(adam, step, true, GS_FP32);
     U.opt = adam->optimizer;
-    cpu_deferred_step(HostPlanes{w, m, v, pitch, plane0, planes}, U, threads);
+    return U;
+}
+
+gs_status gs_cpu_deferred_step(float *w, float *m, float *v, int64_t n_rows, int32_t row, int32_t plane0,
+                               int32_t planes, const int32_t *uids, const uint8_t *udelay, int64_t n_upd,
+                               const int32_t *vids, const float *grad, int64_t n_vis, int64_t grow,
+                               const gs_adam_cfg *adam, int32_t step, int32_t threads)
+{
+    if (step < 1 || !cpu_args_ok(w, m, v, n_rows, row, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, grow,
+                                 adam, step))
+        return GS_ERR_INVALID_ARG;
+    cpu_deferred_step(HostPlanes{w, m, v, row, plane0, planes},
+                      host_update(uids, udelay, n_upd, vids, grad, n_vis, grow, adam, step), threads);
     return GS_OK;
 }
 
-gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t pitch, int32_t plane0, int32_t planes,
-                         const int32_t *ids, const uint8_t *counter, int64_t n, const int32_t *uids,
+gs_status gs_cpu_forward(const float *w, const float *m, const float *v, int64_t n_rows, int32_t row, int32_t plane0,
+                         int32_t planes, const int32_t *ids, const uint8_t *counter, int64_t n, const int32_t *uids,
                          const uint8_t *udelay, int64_t n_upd, const int32_t *vids, const float *grad, int64_t n_vis,
-                         int64_t gpitch, const gs_adam_cfg *adam, int32_t step, float *out, int64_t opitch,
+                         int64_t grow, const gs_adam_cfg *adam, int32_t step, float *out, int64_t opitch,
                          int32_t threads)
 {
-    if (!cpu_args_ok(w, m, v, pitch, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, gpitch, adam, step) ||
-        n < 0 || (n > 0 && (!ids || !counter || !out)) || opitch < n)
+    if (!cpu_args_ok(w, m, v, n_rows, row, plane0, planes, uids, udelay, n_upd, vids, grad, n_vis, grow, adam,
+                     step) ||
+        n < 0 || (n > 0 && (!ids || !counter || !out)) || opitch < n || (n_upd > 0 && step < 1))
         return GS_ERR_INVALID_ARG;
-    if (n_upd > 0 && step < 1) return GS_ERR_INVALID_ARG;
     for (int64_t k = 0; k < n; k++)
-        if (ids[k] < 0 || ids[k] >= pitch || (k && ids[k] <= ids[k - 1]) || counter[k] > adam->max_defer)
+        if (ids[k] < 0 || ids[k] >= n_rows || (k && ids[k] <= ids[k - 1]) || counter[k] > adam->max_defer)
             return GS_ERR_INVALID_ARG;
-    CpuUpdate U;
-    U.uids = uids;
-    U.udelay = udelay;
-    U.n_upd = n_upd;
-    U.vids = vids;
-    U.grad = grad;
-    U.n_vis = n_vis;
-    U.gpitch = gpitch;
-    if (n_upd > 0) U.lut = make_lut(adam, step, true, GS_FP32);
-    U.opt = adam->optimizer;
+    const CpuUpdate U = host_update(uids, udelay, n_upd, vids, grad, n_vis, grow, adam, step);
     const DevLut Ln = make_lut(adam, step + 1, true, GS_FP32);
-    HostPlanes P{const_cast<float *>(w), const_cast<float *>(m), const_cast<float *>(v), pitch, plane0, planes};
+    const HostPlanes P{const_cast<float *>(w), const_cast<float *>(m), const_cast<float *>(v), row, plane0, planes};
     cpu_forward(P, ids, counter, n, n_upd > 0 ? &U : nullptr, Ln, adam->optimizer, out, opitch, threads);
     return GS_OK;
 }
@@ -1581,7 +1581,7 @@ static double ms_since(std::chrono::steady_clock::time_point t0)
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-static CpuUpdate cpu_update_of(const CpuUpdateBuf &B, int64_t gpitch)
+static CpuUpdate cpu_update_of(const CpuUpdateBuf &B)
 {
     CpuUpdate U;
     U.uids = B.uids;
@@ -1590,7 +1590,7 @@ static CpuUpdate cpu_update_of(const CpuUpdateBuf &B, int64_t gpitch)
     U.vids = B.vids;
     U.grad = B.grad;
     U.n_vis = B.n_vis;
-    U.gpitch = gpitch;
+    U.grow = B.planes.planes;
     U.lut = B.lut;
     U.opt = B.opt;
     return U;
@@ -1610,7 +1610,7 @@ static gs_status cpu_flush(gs_ctx *c)
     if (order[0]->full && order[1]->full && order[1]->step < order[0]->step) std::swap(order[0], order[1]);
     for (CpuUpdateBuf *B : order)
         if (B->full) {
-            cpu_deferred_step(B->planes, cpu_update_of(*B, c->gcap_u), T.threads);
+            cpu_deferred_step(B->planes, cpu_update_of(*B), T.threads);
             B->full = false;
         }
     return GS_OK;
@@ -1636,7 +1636,7 @@ static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0,
     T.wait_ms = ms_since(t_start);
     const int planes = sv0.D - N_GEO;
     const int64_t G = c->gcap_u;
-    const HostPlanes HP{(float *)scene->host_sh, (float *)scene->host_m, (float *)scene->host_v, scene->pitch, N_GEO,
+    const HostPlanes HP{(float *)scene->host_sh, (float *)scene->host_m, (float *)scene->host_v, planes, N_GEO,
                         planes};
     const int32_t t1 = scene->step + 1;
     CpuUpdateBuf &P = T.buf[(t1 - 1) & 1], &B = T.buf[t1 & 1];
@@ -1676,7 +1676,7 @@ static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0,
     }
     T.d2h = nv * 5 + 4;
     // (C)
-    const CpuUpdate PU = cpu_update_of(P, G);
+    const CpuUpdate PU = cpu_update_of(P);
     const auto t_fwd = std::chrono::steady_clock::now();
     constexpr int64_t PIECE = 1 << 16;
     for (int64_t k0 = 0; k0 < nv; k0 += PIECE) {
@@ -1694,9 +1694,9 @@ static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0,
     if (P.full) {
         const int threads = T.threads;
         CpuUpdateBuf *Pp = &P;
-        T.worker = std::thread([&T, Pp, G, threads] {
+        T.worker = std::thread([&T, Pp, threads] {
             const auto t0 = std::chrono::steady_clock::now();
-            cpu_deferred_step(Pp->planes, cpu_update_of(*Pp, G), threads);
+            cpu_deferred_step(Pp->planes, cpu_update_of(*Pp), threads);
             T.lazy_ms = ms_since(t0);
             Pp->full = false;
         });
@@ -1725,10 +1725,12 @@ static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0,
     c->w.mark(TP_STEP1, s);
     // (E)
     cudaMemcpyAsync(T.counts_h + 1, &c->cnt->n_upd, sizeof(int), cudaMemcpyDeviceToHost, s);
+    // SH gradients one row per Gaussian (the host's layout), in the forwarded
+    // block (read by this step's gather, which is done)
+    launch_to_rows(c->grad_u + (int64_t)N_GEO * M.gcap, M.gcap, planes, nvis_d, (int)M.gcap, T.stage_d, c->w, s);
     cudaEventRecord(T.ev_grad, s);
     cudaStreamWaitEvent(T.down, T.ev_grad, 0);
-    cudaMemcpy2DAsync(B.grad, G * sizeof(float), c->grad_u + (int64_t)N_GEO * M.gcap, M.gcap * sizeof(float),
-                      nv * sizeof(float), planes, cudaMemcpyDeviceToHost, T.down);
+    cudaMemcpyAsync(B.grad, T.stage_d, nv * planes * sizeof(float), cudaMemcpyDeviceToHost, T.down);
     cudaEventRecord(T.ev_down, T.down);
     T.down_pending = true;
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(c, "cpu tier: update size");

@@ -1,6 +1,8 @@
 // k_scan.cu -- device-wide exclusive scan and ordered compaction of a
 // bitmask, with data-dependent lengths read from device memory so that callers
 // never synchronise (graph capture).
+#include <algorithm>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -272,6 +274,36 @@ __global__ void k_gather_u8(const uint8_t *__restrict__ src, const int32_t *__re
 {
     const int n = min(*n_p, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) dst[k] = src[ids[k]];
+}
+
+// dst[k * planes + r] = src[r * spitch + k] for k < min(*n, cap), r < planes:
+// plane-major rows to one row per element, through 32 x 32 shared tiles so
+// both sides are coalesced.
+__global__ void k_to_rows(const float *__restrict__ src, int64_t spitch, int planes, const int *n_p, int cap,
+                          float *__restrict__ dst)
+{
+    __shared__ float tile[32][33];
+    const int n = min(*n_p, cap);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    const int rt = (planes + 31) / 32;
+    for (int64_t b = blockIdx.x; b < (int64_t)rt * ((n + 31) / 32); b += gridDim.x) {
+        const int r0 = (int)(b % rt) * 32;
+        const int64_t k0 = (b / rt) * 32;
+        for (int j = ty; j < 32; j += 8)
+            if (r0 + j < planes && k0 + tx < n) tile[j][tx] = src[(int64_t)(r0 + j) * spitch + k0 + tx];
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8)
+            if (k0 + j < n && r0 + tx < planes) dst[(k0 + j) * planes + r0 + tx] = tile[tx][j];
+        __syncthreads();
+    }
+}
+
+void launch_to_rows(const float *src, int64_t spitch, int planes, const int *n, int cap, float *dst, Work &w,
+                    cudaStream_t s)
+{
+    const int64_t tiles = (int64_t)((planes + 31) / 32) * ((cap + 31) / 32);
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(tiles, 1), (int64_t)w.num_sms * 16);
+    k_to_rows<<<grid, 256, 0, s>>>(src, spitch, planes, n, cap, dst);
 }
 
 void launch_gather_u8(const uint8_t *src, const int32_t *ids, const int *n, int cap, uint8_t *dst, Work &w,

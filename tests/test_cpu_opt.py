@@ -84,8 +84,9 @@ def test_cpu_deferred_step_matches_oracle(gs, orc, kind, plane0):
     uids, udelay = _members(C, vis, max_defer)
     adam = _adam(gs, kind, max_defer, wd, mu)
     rows = slice(plane0, D)
-    w2, m2, v2, g2 = (np.array(a[rows], copy=True) for a in (w, m, v, g))
+    w2, m2, v2, g2 = (np.ascontiguousarray(a[rows].T) for a in (w, m, v, g))     # one row per Gaussian
     gs.cpu_deferred_step(w2, m2, v2, plane0, uids, udelay, vis, g2, adam, t, threads=4)
+    w2, m2, v2 = w2.T, m2.T, v2.T
     grp = np.asarray(_group_rows(D))[rows]
     lr = np.asarray(LRS)[grp]
     d = C.astype(np.float64)
@@ -121,11 +122,11 @@ def test_cpu_forward_is_the_next_steps_view(gs, orc, kind):
     uids, udelay = _members(C, vis, max_defer)
     ids = np.sort(np.random.default_rng(5).choice(n, n // 2, replace=False)).astype(np.int32)
     adam = _adam(gs, kind, max_defer, wd, mu)
-    w0, m0, v0 = w.copy(), m.copy(), v.copy()
-    out = gs.cpu_forward(w, m, v, 0, ids, C1[ids], uids, udelay, vis, g, adam, t, threads=3)
-    np.testing.assert_array_equal(w, w0)
-    np.testing.assert_array_equal(m, m0)
-    np.testing.assert_array_equal(v, v0)
+    wr, mr, vr, gr = (np.ascontiguousarray(a.T) for a in (w, m, v, g))     # one row per Gaussian
+    out = gs.cpu_forward(wr, mr, vr, 0, ids, C1[ids], uids, udelay, vis, gr, adam, t, threads=3)
+    np.testing.assert_array_equal(wr, w.T)
+    np.testing.assert_array_equal(mr, m.T)
+    np.testing.assert_array_equal(vr, v.T)
     assert (C1[ids] == 0).sum() > 100 and (C1[ids] > 0).sum() > 100
     grp = np.asarray(_group_rows(D))
     lr = np.asarray(LRS)[grp]
@@ -136,15 +137,15 @@ def test_cpu_forward_is_the_next_steps_view(gs, orc, kind):
     err = np.abs(out - want[:, ids])
     assert np.all(err <= b), float(np.max(err / b))
     # nothing pending: counter 0 takes the stored value as it is
-    out0 = gs.cpu_forward(w, m, v, 0, ids, np.zeros(len(ids), np.uint8), np.zeros(0, np.int32),
-                          np.zeros(0, np.uint8), np.zeros(0, np.int32), np.zeros((D, 0), np.float32), adam, t)
+    out0 = gs.cpu_forward(wr, mr, vr, 0, ids, np.zeros(len(ids), np.uint8), np.zeros(0, np.int32),
+                          np.zeros(0, np.uint8), np.zeros(0, np.int32), np.zeros((0, D), np.float32), adam, t)
     np.testing.assert_array_equal(out0, w[:, ids])
 
 
 def test_cpu_optimizer_rejects_bad_arguments(gs):
     from paper_2509_15645_b300 import _lib
     n, D = 100, 23
-    w, m, v, C, vis, g = _state(n, D, 3, 15)
+    w, m, v, C, vis, g = (np.ascontiguousarray(a.T) if a.ndim == 2 else a for a in _state(n, D, 3, 15))
     adam = gs.adam_struct(lr=LRS)
     uids = np.array([5, 3], np.int32)                   # not ascending
     with pytest.raises(_lib.GsError):
