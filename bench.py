@@ -597,6 +597,11 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(targets[0].numel() * 4 * vps), "d2h_bytes_per_step": 4,
                 "copies": "targets double-buffered on a copy stream (step s+1's copy overlaps step s)"}
 
+    if args.density_of or (IW, IH) != (1920, 1080) or vps != 1:
+        cfg_note = f"aerial{N / 1e6:g}m" + (f"_at_density_of_{args.density_of / 1e6:g}m" if args.density_of else "") + \
+            f"_{IW}x{IH}_sh3" + (f"_{vps}views" if vps > 1 else "")
+    else:
+        cfg_note = WORKLOAD
     main_prec = gs.GS_BF16_SH_MOM if args.bf16_only else gs.GS_FP32
     if args.budget_gb:
         args.no_bf16 = True        # the memory plan was made for one form
@@ -615,11 +620,6 @@ def run_ours(args):
                 "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in mb["st"].items()},
                 "cull_adam": mb["cull_adam"], "roofline": roofline(mb), "clocks": mb["clk"],
                 "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 * 2 + D * 2 * 2 + 1}
-    if args.density_of or (IW, IH) != (1920, 1080) or vps != 1:
-        cfg_note = f"aerial{N / 1e6:g}m" + (f"_at_density_of_{args.density_of / 1e6:g}m" if args.density_of else "") + \
-            f"_{IW}x{IH}_sh3" + (f"_{vps}views" if vps > 1 else "")
-    else:
-        cfg_note = WORKLOAD
     K_ms = m["ms"]
     out = {
         "metric": METRIC, "value": round(job_rate(world, K, K_ms), 4), "unit": UNIT, "n_gpus": world, "steps": K,

@@ -323,7 +323,9 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
                                                     s2, nullptr, J.cap[view]);
         for (int e = 0; e < nb && live; e++) {
             const float4 r0 = s0[e];
-            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // misses this warp's rows (uniform)
+            // misses this warp's rows (uniform); a warp tile is the whole tile,
+            // which every listed splat's square overlaps
+            if (!WT && (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f)) continue;
             const float dx = __fsub_rn(r0.x, px);
             if (fabsf(dx) > r0.z) continue;                          // square test on x: shared by the column
             const float4 r1 = s1[e];
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                                                    s2, s_k, J.cap[view]);
         for (int e = 0; e < nb; e++) {
             const float4 r0 = s0[e];
-            if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+            if (!WT && (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f)) continue;   // uniform per warp
             const float dx = __fsub_rn(r0.x, px);
             // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
             // G dL/da, g_r aT, g_g aT, g_b aT (ds = -a dL/da); the mean and conic
@@ -1012,7 +1014,6 @@ __global__ void __launch_bounds__(32 * NW, 5) k_raster_fwd_tma(const RasterJob J
         const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
         const int x = tx0 + lane % tw, y = ty0 + lane / tw;
         const float px = (float)x + 0.5f, pyv = (float)y + 0.5f;
-        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
         const uint2 rg = J.ranges[view][tile];
         const float4 *lrec = J.lrec[view];
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
@@ -1035,8 +1036,7 @@ __global__ void __launch_bounds__(32 * NW, 5) k_raster_fwd_tma(const RasterJob J
             }
             const float4 *B = S.buf[s];
             for (int e = 0; e < cnt && live; e++) {
-                const float4 r0 = B[3 * e];
-                if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+                const float4 r0 = B[3 * e];        // (the tile is the warp's: every listed square overlaps it)
                 const float dx = __fsub_rn(r0.x, px);
                 if (fabsf(dx) > r0.z) continue;
                 const float4 r1 = B[3 * e + 1];
@@ -1086,6 +1086,41 @@ __global__ void __launch_bounds__(32 * NW, 5) k_raster_fwd_tma(const RasterJob J
     }
 }
 
+// emit_splat for sums that are set only in contributing lanes: the other
+// lanes' values are replaced by zeros where the warp sums (no zeroing per entry).
+__device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC,
+                                               bool contrib, float v[9], int lane)
+{
+    const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+    if (cmask == 0u) return;
+    float *row = g9 + (int64_t)k * G9_STRIDE;
+    if (__popc(cmask) <= DIRECT_LANES) {
+        if (contrib) {
+            atomicAdd(reinterpret_cast<float4 *>(row),
+                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
+            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+            atomicAdd(row + 8, v[8]);
+        }
+        return;
+    }
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = contrib ? v[j] : 0.f;
+    float s8 = contrib ? v[8] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    const float sum = warp_transpose_sum8(x, lane);
+    const float q1 = __shfl_down_sync(0xffffffffu, sum, 4);
+    const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
+    const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
+        atomicAdd(row + 8, s8);
+    } else if (lane == 16) {
+        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+    }
+}
+
 template <int BATCH, int NW, bool STATS = false>
 __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, const DevArgs *__restrict__ args,
                                                            unsigned long long *stats = nullptr)
@@ -1112,7 +1147,6 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, c
         const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
         const int x = tx0 + lane % tw, y = ty0 + lane / tw;
         const float px = (float)x + 0.5f, pyv = (float)y + 0.5f;
-        const float wy0 = (float)ty0 + 0.5f, wy1 = wy0 + (float)(th - 1);
         const uint2 rg = J.ranges[view][tile];
         const float4 *lrec = J.lrec[view];
         float T = 1.f, gF = 0.f, gA = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
@@ -1142,10 +1176,9 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, c
             }
             const float4 *B = S.buf[s];
             for (int e = 0; e < cnt; e++) {
-                const float4 r0 = B[3 * e];
-                if (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f) continue;   // uniform per warp
+                const float4 r0 = B[3 * e];        // (the tile is the warp's: every listed square overlaps it)
                 const float dx = __fsub_rn(r0.x, px);
-                float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float v[9];                        // set where contrib (read only there)
                 bool contrib = false;
                 const float4 r1 = B[3 * e + 1];
                 if (live && fabsf(dx) <= r0.z) {
@@ -1168,21 +1201,20 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, c
                             v[6] = __fmul_rn(g0, aT);
                             v[7] = __fmul_rn(g1, aT);
                             v[8] = __fmul_rn(g2, aT);
-                            if (!cl) {                       // the 0.999 clamp has no derivative
-                                const float ds = __fmul_rn(-a, dLda);
-                                v[5] = __fmul_rn(G, dLda);
-                                const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
-                                v[0] = sdx;
-                                v[1] = sdy;
-                                v[2] = __fmul_rn(sdx, dx);
-                                v[3] = __fmul_rn(sdx, dy);
-                                v[4] = __fmul_rn(sdy, dy);
-                            }
+                            // the 0.999 clamp has no derivative: ds = 0 there
+                            const float ds = cl ? 0.f : __fmul_rn(-a, dLda);
+                            v[5] = cl ? 0.f : __fmul_rn(G, dLda);
+                            const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
+                            v[0] = sdx;
+                            v[1] = sdy;
+                            v[2] = __fmul_rn(sdx, dx);
+                            v[3] = __fmul_rn(sdx, dy);
+                            v[4] = __fmul_rn(sdy, dy);
                             T = Tn;
                         }
                     }
                 }
-                emit_splat(g9, __float_as_uint(B[3 * e + 2].w), r1.x, r1.y, r1.z, contrib, v, lane);
+                emit_splat_sel(g9, __float_as_uint(B[3 * e + 2].w), r1.x, r1.y, r1.z, contrib, v, lane);
             }
             __syncwarp();
         }
