@@ -220,11 +220,12 @@ def algorithmic_bytes(N, D, n_vis, n_upd, n_restore, bf16=False, n_cand=None):
     restore_frac = n_restore / max(N, 1)
     cull = (24.0 * N + 24.0 * n_restore + n_cand * (16.0 + 16.0 * restore_frac)
             + 1.0 * N + N / 8.0 + 4.0 * N / 2048.0)
-    # apply: w, m, v read + w, m, v, restore direction written per parameter of
-    # each update-set member, gradients of the visible ones, ids and delays.
-    # bf16 forms: the 11 geometry planes keep fp32 w and restore directions
-    # with bf16 m, v (20 B); SH planes hold bf16 w, m, v and direction (14 B)
-    per_member = (20.0 * 11 + 14.0 * (D - 11)) if bf16 else 28.0 * D
+    # apply: w, m, v read + w, m, v written per parameter of each update-set
+    # member, and the restore direction of each geometry plane written;
+    # gradients of the visible ones, ids and delays.  bf16 forms: the 11
+    # geometry planes keep fp32 w and direction with bf16 m, v (20 B); SH
+    # planes hold bf16 w, m, v (12 B)
+    per_member = (20.0 * 11 + 12.0 * (D - 11)) if bf16 else 28.0 * 11 + 24.0 * (D - 11)
     apply = per_member * n_upd + 4.0 * D * n_vis + 4.0 * n_upd + 1.0 * n_upd
     select = 2.0 * N + N / 4.0
     return cull, apply, select
@@ -619,7 +620,7 @@ def run_ours(args):
                 "value": round(job_rate(world, K, mb["ms"]), 4), "unit": UNIT, "ms_per_step": round(mb["ms"] / K, 4),
                 "stages_ms": {k: (round(v, 4) if v is not None else None) for k, v in mb["st"].items()},
                 "cull_adam": mb["cull_adam"], "roofline": roofline(mb), "clocks": mb["clk"],
-                "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 * 2 + D * 2 * 2 + 1}
+                "update_set": round(mb["n_upd"]), "state_bytes_per_gaussian": 11 * 4 * 2 + (D - 11) * 2 + D * 2 * 2 + 1}
     K_ms = m["ms"]
     out = {
         "metric": METRIC, "value": round(job_rate(world, K, K_ms), 4), "unit": UNIT, "n_gpus": world, "steps": K,

@@ -154,13 +154,12 @@ typedef struct {
     void *m;               /* [D][pitch] fp32 or bf16 ([11][pitch] in GS_TIER_HOST_SH), NULL = no optimizer
                               state (render only) */
     void *v;               /* like m */
-    float *rdir;           /* restore direction m / (sqrt(v) + eps) of each parameter, kept by the optimizer
-                              so a deferred restore is one multiply-add: [11][pitch] fp32 for the geometry
-                              planes followed by [D-11][pitch] of the SH storage type (so [D][pitch] fp32 in
-                              GS_FP32; 44 + 2 (D-11) bytes per pitch element in the BF16 forms).  Must equal
-                              that expression, rounded to the plane's type (all zero when m = v = 0; see
-                              gs_refresh_rdir).  GS_TIER_HOST_SH: the [11][pitch] geometry part only.  NULL:
-                              the kernels recompute it from m and v */
+    float *rdir;           /* restore direction m / (sqrt(v) + eps) of each geometry parameter, kept by the
+                              optimizer so the cull's deferred restore of every Gaussian is one multiply-add:
+                              [11][pitch] fp32 (a larger buffer is accepted; nothing past row 11 is read or
+                              written: the SH planes' directions are taken from m and v by the few restores
+                              that need them).  Must equal that expression (all zero when m = v = 0; see
+                              gs_refresh_rdir).  NULL: the kernels recompute it from m and v */
     uint8_t *counter;      /* [n] defer counters of §4.3.2 (0..max_defer) */
     int32_t step;          /* optimizer steps completed; the next step is step + 1 */
     int32_t tier;          /* GS_TIER_DEVICE, GS_TIER_HOST_SH or GS_TIER_HOST_CPU_OPT */

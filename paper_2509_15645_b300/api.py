@@ -111,11 +111,10 @@ class GaussianScene:
     """A Gaussian set with its optimizer state.
 
     precision GS_FP32: ``w`` is one [D][pitch] float32 tensor (geometry planes
-    then SH planes; ``geo`` and ``sh`` are views of it), m / v float32, and
-    ``rdir`` [D][pitch] float32 restore directions.  BF16 forms: ``geo``
-    [11][pitch] float32 (master copy), ``sh`` [D-11][pitch] bfloat16, m / v
-    bfloat16; restore directions ``rdir_geo`` [11][pitch] float32 and
-    ``rdir_sh`` [D-11][pitch] bfloat16 (one buffer, in that order).
+    then SH planes; ``geo`` and ``sh`` are views of it), m / v float32.  BF16
+    forms: ``geo`` [11][pitch] float32 (master copy), ``sh`` [D-11][pitch]
+    bfloat16, m / v bfloat16.  Both: ``rdir_geo`` [11][pitch] float32, the
+    restore directions of the geometry planes the optimizer keeps.
 
     tier GS_TIER_HOST_SH: the geometry planes with their m, v (``m``, ``v``
     [11][pitch]) and ``rdir_geo`` stay on the device; the SH planes ``sh`` and
@@ -138,7 +137,7 @@ class GaussianScene:
         self.w = None
         self.m = self.v = self.counter = None
         self.m_sh = self.v_sh = None
-        self.rdir = self.rdir_geo = self.rdir_sh = None
+        self.rdir_geo = None
         host = tier in (L.GS_TIER_HOST_SH, L.GS_TIER_HOST_CPU_OPT)
         if host:
             assert tier == L.GS_TIER_HOST_SH or precision == L.GS_FP32, "the host-core optimizer tier is fp32"
@@ -178,14 +177,8 @@ class GaussianScene:
             self.v = torch.zeros(D, P, dtype=mdtype, device=device)
             self.counter = torch.zeros(P, dtype=torch.uint8, device=device)
             if with_rdir:
-                # restore directions m / (sqrt(v) + eps), zero while m = v = 0:
-                # fp32 rows for the geometry planes, then rows of the SH type
-                gbytes = 11 * P * 4
-                buf = torch.zeros(gbytes + (D - 11) * P * mdtype.itemsize, dtype=torch.uint8, device=device)
-                self._rdir_buf = buf
-                self.rdir_geo = buf[:gbytes].view(torch.float32).view(11, P)
-                self.rdir_sh = buf[gbytes:].view(mdtype).view(D - 11, P)
-                self.rdir = buf.view(torch.float32).view(D, P) if precision == L.GS_FP32 else None
+                # restore directions m / (sqrt(v) + eps) of the geometry planes, zero while m = v = 0
+                self.rdir_geo = torch.zeros(11, P, dtype=torch.float32, device=device)
         self.step = 0
 
     def struct(self) -> L.Scene:

@@ -477,7 +477,7 @@ static gs_status scene_view(gs_ctx *c, const gs_scene *s, bool need_opt, SceneVi
         sv.sh.w = s->sh;
         sv.sh.m = s->m ? (char *)s->m + N_GEO * P * eb : nullptr;
         sv.sh.v = s->v ? (char *)s->v + N_GEO * P * eb : nullptr;
-        sv.sh.rdir = sv.rdir ? (char *)sv.rdir + N_GEO * P * 4 : nullptr;
+        sv.sh.rdir = nullptr;       // SH directions are not kept: restores take them from m, v
         sv.sh.ppitch = P;
         sv.sh.slot = nullptr;
         sv.sh.shift = 0;
@@ -1169,7 +1169,7 @@ gs_status gs_densify(gs_ctx *c, const gs_scene *src, gs_scene *dst, const gs_ada
     dv.sh.w = dst->sh;
     dv.sh.m = (char *)dst->m + N_GEO * P * eb;
     dv.sh.v = (char *)dst->v + N_GEO * P * eb;
-    dv.sh.rdir = dst->rdir ? (char *)dst->rdir + N_GEO * P * 4 : nullptr;
+    dv.sh.rdir = nullptr;
     dv.sh.ppitch = P;
     dv.sh.slot = nullptr;
     densify_write(sv, dv, c->args + SLOT_ADAM, normals, masks, prefixes, c->n_tmp, c->w, s);

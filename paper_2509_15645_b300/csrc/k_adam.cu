@@ -169,7 +169,7 @@ template <typename T, typename IX = int64_t> struct Planes {
     float *geo;
     T *m, *v;
     float *rdir;
-    T *shw, *shm, *shv, *shr;
+    T *shw, *shm, *shv;
     IX pitch, sp;
     const int32_t *slot;
     int shift;
@@ -198,8 +198,8 @@ template <typename T, typename IX = int64_t> struct Planes {
         return OPT == GS_OPT_SGDM ? 0.f : ldv(r, i, sb);
     }
     // Store the updated w, m, v of plane r (rounded per the storage; `key` is
-    // sr_plane_key of this plane and step) and the restore direction of what
-    // was stored.
+    // sr_plane_key of this plane and step) and, for a geometry plane, the
+    // restore direction of what was stored.
     template <int OPT>
     __device__ __forceinline__ void store(int r, IX i, IX sb, float w, float mm, float vv, const SLut &L,
                                           uint32_t key) const
@@ -216,8 +216,9 @@ template <typename T, typename IX = int64_t> struct Planes {
             const IX o = so(r, sb);
             const float ms = st_val(shm + o, mm, st, bits);
             const float vs = sgd ? 0.f : st_val(shv + o, vv, st, bits >> 16);
+            (void)ms;
+            (void)vs;
             st_val(shw + o, w, st, sr_w_bits(bits));
-            if (shr) st_val(shr + o, restore_dir<OPT>(ms, vs, L.eps), false, 0u);
         }
     }
 };
@@ -339,7 +340,6 @@ template <typename T, typename IX = int64_t> static Planes<T, IX> planes_of(cons
     P.shw = (T *)sc.sh.w;
     P.shm = (T *)sc.sh.m;
     P.shv = (T *)sc.sh.v;
-    P.shr = sc.rdir ? (T *)sc.sh.rdir : nullptr;
     P.pitch = (IX)sc.pitch;
     P.sp = (IX)sc.sh.ppitch;
     P.slot = sc.sh.slot;
@@ -614,8 +614,6 @@ __device__ __forceinline__ void pair_step(const PairRows &a, const Planes<T> &P,
                 bm[e] = rnd_bits(m, ms, P.shm, st, bits);
                 bv[e] = OPT == GS_OPT_SGDM ? 0u : rnd_bits(v, vs, P.shv, st, bits >> 16);
                 bw[e] = rnd_bits(w, ws, P.shw, st, sr_w_bits(bits));
-                float dstored;
-                bd[e] = rnd_bits(restore_dir<OPT>(ms, OPT == GS_OPT_SGDM ? 0.f : vs, L.eps), dstored, P.shr, false, 0u);
             }
         }
         if (GEO) {
@@ -629,7 +627,6 @@ __device__ __forceinline__ void pair_step(const PairRows &a, const Planes<T> &P,
             st2(P.shw + o, bw[0], bw[1], sel);
             st2(P.shm + o, bm[0], bm[1], sel);
             if (OPT != GS_OPT_SGDM) st2(P.shv + o, bv[0], bv[1], sel);
-            if (P.shr) st2(P.shr + o, bd[0], bd[1], sel);
         }
     }
 }
@@ -684,21 +681,22 @@ __device__ __forceinline__ void pair_step_bf16(const PairRows &a, const Planes<_
         const uint32_t h1 = st ? sr_bits(key[q], (uint32_t)(a.i0 + 1)) : 0u;
         const uint32_t pm = bf16x2_round(m[0], m[1], st, (h0 & 0xffffu) | (h1 << 16));
         const uint32_t pv = OPT == GS_OPT_SGDM ? 0u : bf16x2_round(v[0], v[1], st, (h0 >> 16) | (h1 & 0xffff0000u));
-        const float d0 = restore_dir<OPT>(bf16_lo(pm), bf16_lo(pv), L.eps);
-        const float d1 = restore_dir<OPT>(bf16_hi(pm), bf16_hi(pv), L.eps);
         if (GEO) {
             const int64_t o = (int64_t)r * P.pitch + a.i0;
             st2(P.geo + o, __float_as_uint(w[0]), __float_as_uint(w[1]), sel);
             st2p(P.m + o, pm, sel);
             if (OPT != GS_OPT_SGDM) st2p(P.v + o, pv, sel);
-            if (P.rdir) st2(P.rdir + o, __float_as_uint(d0), __float_as_uint(d1), sel);
+            if (P.rdir) {
+                const float d0 = restore_dir<OPT>(bf16_lo(pm), bf16_lo(pv), L.eps);
+                const float d1 = restore_dir<OPT>(bf16_hi(pm), bf16_hi(pv), L.eps);
+                st2(P.rdir + o, __float_as_uint(d0), __float_as_uint(d1), sel);
+            }
         } else {
             const uint32_t pw = bf16x2_round(w[0], w[1], st, (sr_w_bits(h0) & 0xffffu) | (sr_w_bits(h1) << 16));
             const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
             st2p(P.shw + o, pw, sel);
             st2p(P.shm + o, pm, sel);
             if (OPT != GS_OPT_SGDM) st2p(P.shv + o, pv, sel);
-            if (P.shr) st2p(P.shr + o, bf16x2_round(d0, d1, false, 0u), sel);
         }
     }
 }
@@ -768,7 +766,7 @@ bool adam_pairs_ok(const SceneView &sc)
     // resident planes, 8-byte aligned pair accesses (pitch is a multiple of 4)
     auto al = [](const void *p) { return ((uintptr_t)p & 7) == 0; };
     return !sc.sh.slot && al(sc.geo) && al(sc.m) && al(sc.v) && al(sc.sh.w) && al(sc.sh.m) && al(sc.sh.v) &&
-           (!sc.rdir || (al(sc.rdir) && al(sc.sh.rdir))) && sc.counter;
+           (!sc.rdir || al(sc.rdir)) && sc.counter;
 }
 
 void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
@@ -852,31 +850,29 @@ void launch_adam_eager(const SceneView &sc, const DevArgs *args, const uint32_t 
     w.mark(TP_APPLY1, s);
 }
 
-// rdir = m / (sqrt(v) + eps) for every plane (momentum SGD: rdir = m).
+// rdir = m / (sqrt(v) + eps) for every geometry plane (momentum SGD: rdir = m).
 template <typename T, int OPT>
-__global__ void k_refresh_rdir(Planes<T> P, int D, int64_t n, const DevArgs *__restrict__ args)
+__global__ void k_refresh_rdir(Planes<T> P, int64_t n, const DevArgs *__restrict__ args)
 {
     const float eps = args->lut.eps;
-    const int64_t total = (int64_t)D * n;
+    const int64_t total = (int64_t)N_GEO * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
-        const int64_t i = e - (int64_t)r * n, sb = P.shbase(i);
-        const float dir = restore_dir<OPT>(P.ldm(r, i, sb), P.template ldv_opt<OPT>(r, i, sb), eps);
-        if (r < N_GEO) P.rdir[r * P.pitch + i] = dir;
-        else st_val(P.shr + (r - N_GEO) * P.sp + sb, dir, false, 0u);
+        const int64_t i = e - (int64_t)r * n;
+        P.rdir[r * P.pitch + i] = restore_dir<OPT>(P.ldm(r, i, i), P.template ldv_opt<OPT>(r, i, i), eps);
     }
 }
 
 void launch_refresh_rdir(const SceneView &sc, const DevArgs *args, Work &w, cudaStream_t s)
 {
     if (!sc.rdir) return;
-    const int g = w.grid((int64_t)sc.D * sc.n, 256, 4);
+    const int g = w.grid((int64_t)N_GEO * sc.n, 256, 4);
     with_opt(sc.opt, [&](auto o) {
         constexpr int O = decltype(o)::value;
         if (sc.prec == GS_FP32)
-            k_refresh_rdir<float, O><<<g, 256, 0, s>>>(planes_of<float>(sc), sc.D, sc.n, args);
+            k_refresh_rdir<float, O><<<g, 256, 0, s>>>(planes_of<float>(sc), sc.n, args);
         else
-            k_refresh_rdir<__nv_bfloat16, O><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.D, sc.n, args);
+            k_refresh_rdir<__nv_bfloat16, O><<<g, 256, 0, s>>>(planes_of<__nv_bfloat16>(sc), sc.n, args);
     });
 }
 

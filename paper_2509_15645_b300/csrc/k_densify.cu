@@ -28,7 +28,7 @@ namespace {
 // (fp32 geometry, T SH) of a resident scene.
 template <typename T> struct DPlanes {
     float *geo;
-    T *m, *v, *shw, *shm, *shv, *shr;
+    T *m, *v, *shw, *shm, *shv;
     float *rdir;
     int64_t pitch;
     __device__ __forceinline__ float w(int r, int64_t i) const
@@ -43,11 +43,8 @@ template <typename T> struct DPlanes {
     {
         return ld_val(r < N_GEO ? v + r * pitch + i : shv + (r - N_GEO) * pitch + i);
     }
-    __device__ __forceinline__ float dir(int r, int64_t i) const
-    {
-        return r < N_GEO ? rdir[r * pitch + i] : ld_val(shr + (r - N_GEO) * pitch + i);
-    }
-    // stores round to nearest (densification draws no random bits)
+    // stores round to nearest (densification draws no random bits); d_ is the
+    // restore direction of a geometry plane
     __device__ __forceinline__ void put(int r, int64_t i, float w_, float m_, float v_, float d_) const
     {
         if (r < N_GEO) {
@@ -60,7 +57,6 @@ template <typename T> struct DPlanes {
             st_val(shw + o, w_, false, 0u);
             st_val(shm + o, m_, false, 0u);
             st_val(shv + o, v_, false, 0u);
-            if (shr) st_val(shr + o, d_, false, 0u);
         }
     }
 };
@@ -75,7 +71,6 @@ template <typename T> DPlanes<T> dplanes(const SceneView &sc)
     P.shm = (T *)sc.sh.m;
     P.shv = (T *)sc.sh.v;
     P.rdir = sc.rdir;
-    P.shr = sc.rdir ? (T *)sc.sh.rdir : nullptr;
     P.pitch = sc.pitch;
     return P;
 }
@@ -85,13 +80,14 @@ struct DensifyRule {
 };
 
 // Current value of plane r of Gaussian i (the catch-up of Eq. 3 with the tables
-// of the coming step), from the stored direction when the scene keeps them.
+// of the coming step): geometry planes from the stored direction when the
+// scene keeps them, SH planes from m and v.
 template <typename T, int OPT>
 __device__ __forceinline__ float current(const DPlanes<T> &P, const DevLut &L, int r, int64_t i, int d)
 {
     if (!d) return P.w(r, i);
     const int g = lr_group(r);
-    const float dir = P.rdir ? P.dir(r, i) : restore_dir<OPT>(P.mm(r, i), P.vv(r, i), L.eps);
+    const float dir = (P.rdir && r < N_GEO) ? P.rdir[r * P.pitch + i] : restore_dir<OPT>(P.mm(r, i), P.vv(r, i), L.eps);
     return restore_with_dir<OPT>(P.w(r, i), dir, L.param[g][d], L.decay[g][d], d);
 }
 
@@ -167,7 +163,6 @@ __global__ void __launch_bounds__(256) k_densify_write(DPlanes<T> P, const uint8
                     Q.shw[b] = P.shw[a];
                     Q.shm[b] = P.shm[a];
                     Q.shv[b] = P.shv[a];
-                    if (Q.shr) Q.shr[b] = P.shr ? P.shr[a] : T(0.f);
                 }
             }
             qcounter[o] = (uint8_t)d;
@@ -189,11 +184,7 @@ __global__ void __launch_bounds__(256) k_densify_write(DPlanes<T> P, const uint8
                 }
                 Q.put(r, o, w, m, v, 0.f);
                 const float mq = Q.mm(r, o), vq = Q.vv(r, o);     // the moments as stored: their direction
-                if (r < N_GEO) {
-                    if (Q.rdir) Q.rdir[r * Q.pitch + o] = restore_dir<OPT>(mq, vq, L.eps);
-                } else if (Q.shr) {
-                    st_val(Q.shr + (r - N_GEO) * Q.pitch + o, restore_dir<OPT>(mq, vq, L.eps), false, 0u);
-                }
+                if (r < N_GEO && Q.rdir) Q.rdir[r * Q.pitch + o] = restore_dir<OPT>(mq, vq, L.eps);
                 Q.put(r, o2, w, 0.f, 0.f, 0.f);
             }
             qcounter[o] = 0;

@@ -92,15 +92,8 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
                                                   : restore_dir<OPT>(ld_val(mp + r * pitch + i), ld_val(vp + r * pitch + i), L.eps);
                         w[r] = restore_with_dir<OPT>(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
                     }
-                } else if (sc.rdir && sc.sh.rdir) {
-                    const T *rsh = (const T *)sc.sh.rdir;
-#pragma unroll
-                    for (int r = 0; r < D; r++) {
-                        const float dir = r < N_GEO ? __ldg(sc.rdir + r * pitch + i) : ld_val(rsh + (r - N_GEO) * sp + sb);
-                        w[r] = restore_with_dir<OPT>(w[r], dir, L.param[lr_group(r)][d], L.decay[lr_group(r)][d], d);
-                    }
                 } else if (sc.rdir) {
-                    // host tier: geometry directions kept, SH directions recomputed from the staged m, v
+                    // geometry directions kept; SH directions from m, v (the optimizer keeps none)
                     const T *msh = (const T *)sc.sh.m, *vsh = (const T *)sc.sh.v;
 #pragma unroll
                     for (int r = 0; r < D; r++) {

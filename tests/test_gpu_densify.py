@@ -99,11 +99,10 @@ def test_densify_matches_oracle(gs, orc, prec_name):
                              bound)
         err = np.abs(a - b)
         assert np.all(err <= bound), (name, float(np.max(err / bound)), np.unravel_index(np.argmax(err / bound), err.shape))
-    # the restore directions of the new scene are those of its stored moments
-    if not bf16:
-        rd = dst.rdir[:, :dst.n].cpu().numpy().astype(np.float64)
-        want = gm / (np.sqrt(gv) + 1e-15)
-        np.testing.assert_allclose(rd, want, rtol=1e-5, atol=1e-30)
+    # the geometry restore directions of the new scene are those of its stored moments
+    rd = dst.rdir_geo[:, :dst.n].cpu().numpy().astype(np.float64)
+    want = gm[:11] / (np.sqrt(gv[:11]) + 1e-15)
+    np.testing.assert_allclose(rd, want, rtol=1e-5, atol=1e-30)
     print(f"densify ({prec_name}): {n} -> {dst.n} Gaussians, {len(split_ids)} split, "
           f"{int((big & (smax <= pd * extent)).sum())} cloned before pruning")
 

@@ -137,18 +137,7 @@ def test_restore_over_changing_views(gs, orc, bf16, opt):
     for t, k in enumerate(ORDER, start=1):
         cam = cams[k]
         W, M, V, Cn = _state(scene, N)
-        if bf16:
-            # the gather restores SH rows through the stored bf16 directions:
-            # the expected parameters are w - table[d] * (stored direction), so
-            # the image isolates the restore from the rounding of the directions
-            rd = torch.cat([scene.rdir_geo[:, :N], scene.rdir_sh[:, :N].float()]).cpu().numpy().astype(np.float64)
-            Wcur = W.copy()
-            for g, rows in enumerate([range(0, 3), range(3, 6), range(6, 10), range(10, 11), range(11, 14),
-                                      range(14, W.shape[0])]):
-                pl, _, _ = orc.adam_lut(t, hp.lr[g], hp)
-                for r in rows:
-                    Wcur[r] = W[r] - np.float32(pl[Cn]).astype(np.float64) * rd[r]
-        elif opt == "adamw":
+        if opt == "adamw":
             Wcur, _, _ = orc.adamw_materialize(W, M, V, Cn, t - 1, hp, ospec[1])
         elif opt == "sgdm":
             Wcur, _ = orc.sgdm_materialize(W, M, Cn, hp.lr, ospec[1], max_defer=hp.max_defer)
