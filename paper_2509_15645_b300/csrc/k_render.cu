@@ -417,6 +417,41 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
     return r;
 }
 
+// emit_splat for sums that are set only in contributing lanes: the other
+// lanes' values are replaced by zeros where the warp sums (no zeroing per entry).
+__device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC,
+                                               bool contrib, float v[9], int lane)
+{
+    const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
+    if (cmask == 0u) return;
+    float *row = g9 + (int64_t)k * G9_STRIDE;
+    if (__popc(cmask) <= DIRECT_LANES) {
+        if (contrib) {
+            atomicAdd(reinterpret_cast<float4 *>(row),
+                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
+            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+            atomicAdd(row + 8, v[8]);
+        }
+        return;
+    }
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = contrib ? v[j] : 0.f;
+    float s8 = contrib ? v[8] : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
+    const float sum = warp_transpose_sum8(x, lane);
+    const float q1 = __shfl_down_sync(0xffffffffu, sum, 4);
+    const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
+    const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
+        atomicAdd(row + 8, s8);
+    } else if (lane == 16) {
+        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+    }
+}
+
 // Backward of the compositing (§2.4 step 5), one front-to-back pass per tile
 // that recomputes each pixel's transmittance T_i exactly as the forward did
 // (same list, same tests, same operations) together with the colour
@@ -493,6 +528,49 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
             const float4 r0 = s0[e];
             if (!WT && (r0.y + r0.z < wy0 - 1e-3f || r0.y - r0.z > wy1 + 1e-3f)) continue;   // uniform per warp
             const float dx = __fsub_rn(r0.x, px);
+            if constexpr (PPT == 1) {
+                // one pixel per thread: the sums are set only where the pixel
+                // contributes (no zeroing per entry; emit_splat_sel masks the rest)
+                float v[9];
+                bool contrib = false;
+                if (live && fabsf(dx) <= r0.z) {
+                    const float4 r1 = s1[e];
+                    float dy, G;
+                    bool cl;
+                    const float a = splat_alpha_nb(r0, r1, dx, (float)y0 + 0.5f, dy, G, cl);
+                    if (STATS) n_sq += fabsf(dy) <= r0.z ? 1 : 0;
+                    if (a != 0.f) {
+                        const float Tn = __fmul_rn(T[0], __fsub_rn(1.f, a));
+                        if (Tn < T_STOP) {
+                            live = 0u;
+                        } else {
+                            if (STATS) n_on++;
+                            contrib = true;
+                            const float4 c = s2[e];
+                            const float aT = __fmul_rn(a, T[0]);
+                            const float gc = __fmaf_rn(g2[0], c.z, __fmaf_rn(g1[0], c.y, __fmul_rn(g0[0], c.x)));
+                            gA[0] = __fmaf_rn(aT, gc, gA[0]);
+                            const float dLda =
+                                __fmaf_rn(T[0], gc, -__fdividef(__fsub_rn(gF[0], gA[0]), __fsub_rn(1.f, a)));
+                            v[6] = __fmul_rn(g0[0], aT);
+                            v[7] = __fmul_rn(g1[0], aT);
+                            v[8] = __fmul_rn(g2[0], aT);
+                            const float ds = cl ? 0.f : __fmul_rn(-a, dLda);    // the 0.999 clamp: no derivative
+                            v[5] = cl ? 0.f : __fmul_rn(G, dLda);
+                            const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
+                            v[0] = sdx;
+                            v[1] = sdy;
+                            v[2] = __fmul_rn(sdx, dx);
+                            v[3] = __fmul_rn(sdx, dy);
+                            v[4] = __fmul_rn(sdy, dy);
+                            T[0] = Tn;
+                        }
+                    }
+                }
+                const float4 cn = s1[e];
+                emit_splat_sel(g9, s_k[e], cn.x, cn.y, cn.z, contrib, v, lane);
+                continue;
+            }
             // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
             // G dL/da, g_r aT, g_g aT, g_b aT (ds = -a dL/da); the mean and conic
             // gradients are formed from them once per (warp, splat)
@@ -1076,41 +1154,6 @@ __global__ void __launch_bounds__(32 * NW, 5) k_raster_fwd_tma(const RasterJob J
 #pragma unroll
         for (int o = 16; o; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
         if (lane == 0 && loss_part != 0.f) atomicAdd(loss, loss_part);
-    }
-}
-
-// emit_splat for sums that are set only in contributing lanes: the other
-// lanes' values are replaced by zeros where the warp sums (no zeroing per entry).
-__device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC,
-                                               bool contrib, float v[9], int lane)
-{
-    const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
-    if (cmask == 0u) return;
-    float *row = g9 + (int64_t)k * G9_STRIDE;
-    if (__popc(cmask) <= DIRECT_LANES) {
-        if (contrib) {
-            atomicAdd(reinterpret_cast<float4 *>(row),
-                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
-            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
-            atomicAdd(row + 8, v[8]);
-        }
-        return;
-    }
-    float x[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) x[j] = contrib ? v[j] : 0.f;
-    float s8 = contrib ? v[8] : 0.f;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) s8 += __shfl_xor_sync(0xffffffffu, s8, o);
-    const float sum = warp_transpose_sum8(x, lane);
-    const float q1 = __shfl_down_sync(0xffffffffu, sum, 4);
-    const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
-    const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
-    if (lane == 0) {
-        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
-        atomicAdd(row + 8, s8);
-    } else if (lane == 16) {
-        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
     }
 }
 

@@ -93,8 +93,8 @@ def test_densify_matches_oracle(gs, orc, prec_name):
         bound = rel * np.abs(b) + (2e-6 if name == "w" else 1e-12) + (2.0 ** -7 * np.abs(b) if bf16 and name != "w" else 0)
         if bf16:
             # a bf16 store is a neighbour of its FP32 value: within one ulp of the larger magnitude
-            big = np.maximum(np.abs(a), np.abs(b)) + 1e-30
-            ulp = 2.0 ** (np.floor(np.log2(big)) - 7)
+            mag = np.maximum(np.abs(a), np.abs(b)) + 1e-30
+            ulp = 2.0 ** (np.floor(np.log2(mag)) - 7)
             bound = np.where(rows_sh, np.maximum(bound, ulp + 8 * u * np.abs(b) + (2e-6 if name == "w" else 1e-12)),
                              bound)
         err = np.abs(a - b)
