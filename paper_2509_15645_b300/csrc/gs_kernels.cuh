@@ -26,6 +26,27 @@ struct Work {
     cudaEvent_t *tev;     // timing points of the current step, or nullptr
     bool capturing;       // the stream is being captured into a graph
     uint32_t cull_first_wait = CULL_WAIT_LIMIT;   // limit of each cull block's first wait (failure-path tests)
+    // A second stream for short independent kernels (the FP64 fix-ups) that
+    // run beside the main stream's work: fork() returns the stream to launch
+    // on, side_done() marks the end of that work, wait_side() makes the main
+    // stream wait for it.  Without a side stream everything stays on s.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t fork(cudaStream_t s) const
+    {
+        if (!side) return s;
+        cudaEventRecord(ev_fork, s);
+        cudaStreamWaitEvent(side, ev_fork, 0);
+        return side;
+    }
+    void side_done(cudaStream_t fs) const
+    {
+        if (side && fs == side) cudaEventRecord(ev_join, side);
+    }
+    void wait_side(cudaStream_t s) const
+    {
+        if (side) cudaStreamWaitEvent(s, ev_join, 0);
+    }
     void mark(int p, cudaStream_t s) const
     {
         if (!tev) return;

@@ -570,7 +570,11 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg, int device, void *worksp
     if (!raster_variant_ok(c->rbs[0].variant, cfg->tile_w, cfg->tile_h, cfg->list_records)) c->rbs[0].variant = 0;
     c->rbs[0].variant_bwd = c->rbs[0].variant;
     c->w.scan_grid = c->num_sms * 2 > 1024 ? 1024 : c->num_sms * 2;
-    if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    if (cudaMemset(c->cnt, 0, sizeof(Counters)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->w.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->w.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->w.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
         gs_destroy(c);
         return GS_ERR_CUDA;
     }
@@ -645,6 +649,12 @@ gs_status gs_destroy(gs_ctx *c)
     timing_free(c);
     if (c->cstream) cudaStreamSynchronize(c->cstream);
     if (c->dstream) cudaStreamSynchronize(c->dstream);
+    if (c->w.side) {
+        cudaStreamSynchronize(c->w.side);
+        cudaStreamDestroy(c->w.side);
+    }
+    for (cudaEvent_t e : {c->w.ev_fork, c->w.ev_join})
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {c->ev_vis, c->ev_upd, c->ev_done, c->ev_end, c->ev_down[0], c->ev_down[1], c->ev_half[0],
                           c->ev_half[1], c->ev_sdone})
         if (e) cudaEventDestroy(e);

@@ -429,6 +429,7 @@ void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBuf
     const int gsm = w.grid((int64_t)(cap + 31) / 32 * 32, 256);
     k_tiles_small<false><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
                                              view, rb.tile_cnt, nullptr, nullptr, nullptr, nullptr);
+    w.wait_side(s);                                       // the FP64 fix-ups (prepare_view) have landed
     k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
                                                rb.tile_cnt);
     // each tile's first key (and the key total), then the keys into their tiles' lists

@@ -1607,8 +1607,12 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
                                                           rb.rec2, rb.depth, rb.rect, rb.n_fix, rb.fix_idx,
                                                           rb.fix_flag, rb.n_big, rb.big_idx);
-    k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, s>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
-                                                    rb.rect, rb.n_big, rb.big_idx);
+    // the FP64 fix-ups beside the counting of the other splats' keys (which
+    // skips the flagged ones); the big-rectangle counts wait for them
+    const cudaStream_t fs = w.fork(s);
+    k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, fs>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
+                                                     rb.rect, rb.n_big, rb.big_idx);
+    w.side_done(fs);
     build_tile_lists(args, view, n_vis, rb, tiles, w, s);
     rb.sorted_keys = rb.tk[1];
     rb.sorted_vals = rb.tv[1];
@@ -1752,12 +1756,17 @@ void project_backward(const SceneView &sc, const DevArgs *args, int view, const 
                       const int32_t *ids, const PrevMasks &prev, Work &w, cudaStream_t s)
 {
     const int cap = (int)rb.cap;
+    // the FP64 adjoint of the flagged splats beside the FP32 one of the others
+    // (each Gaussian's rows are written by exactly one of the two)
+    const cudaStream_t fs = w.fork(s);
+    pbwd_for<true>(sc.deg)<<<w.num_sms, PROJ_BLOCK, 0, fs>>>(
+        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, prev,
+        w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
+    w.side_done(fs);
     pbwd_for<false>(sc.deg)<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(
         rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, prev,
         w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
-    pbwd_for<true>(sc.deg)<<<w.num_sms, PROJ_BLOCK, 0, s>>>(
-        rb.compact, cap, n_vis, args, view, rb.g9, grad, gcap, ids, remap_mask, remap_prefix, prev,
-        w.status, rb.n_fix, rb.fix_idx, rb.fix_flag);
+    w.wait_side(s);
 }
 
 void render_backward(const SceneView &sc, const DevArgs *args, int view, const int *n_vis, RenderBufs &rb,
