@@ -59,6 +59,19 @@ def sign_undetermined(g_full, frac=1e-4):
     return mask
 
 
+def undetermined_visible(g_full, ids, what=""):
+    """sign_undetermined restricted to the visible Gaussians ``ids`` (the others
+    step on their moments alone, which is determined), with the share of the
+    visible entries it covers printed and bounded (< 25%)."""
+    vis = np.zeros(g_full.shape[1], bool)
+    vis[ids] = True
+    und = sign_undetermined(g_full) & vis[None, :]
+    frac = float(und.sum()) / max(g_full.shape[0] * int(vis.sum()), 1)
+    print(f"{what}: {frac:.2%} of the visible Gaussians' gradient entries sign-undetermined")
+    assert frac < 0.25, (what, frac)
+    return und
+
+
 def check_lists(gpu_tiles, gpu_gids, oracle_tiles, oracle_gids, depth_bits, exclude):
     """GPU (tile, Gaussian id) sequence against the oracle's.  Keys of excluded
     Gaussians are dropped from both; within a tile, neighbours may differ in

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, sign_undetermined
+from helpers import GROUPS, TIE_TOL, cam_f32, check_lists, f32, hp32, rel_group_error, undetermined_visible
 from helpers import pixel_exclusions as _pixel_exclusions
 from synth import scenes
 
@@ -604,7 +604,7 @@ def test_bf16_form_step_parity(gs, orc):
         # stored value plus a 2^-6 relative error of the step lr * m/sqrt(v)
         g_full = np.zeros((D, n))
         g_full[:, kept] = rr["grad"][:, kept]
-        und_all = sign_undetermined(g_full)
+        und_all = undetermined_visible(g_full, kept, f"bf16 step {t}")
         und = und_all[:11]
         gerr = np.abs(gw[:11] - W[:11])
         assert np.all(gerr[~und] <= 2e-3 * lr + 1e-6), (t, np.max(gerr[~und]))
@@ -682,7 +682,7 @@ def test_step_parity(gs, orc):
                 assert rel_group_error(gm, M, s) <= 2e-4, (t, k, rel_group_error(gm, M, s))
         g_full = np.zeros((D, n))
         g_full[:, kept] = rr["grad"][:, kept]
-        und = sign_undetermined(g_full)
+        und = undetermined_visible(g_full, kept, f"step {t}")
         err = np.abs(gw - W)
         assert np.all(err[~und] <= 2e-3 * 1e-3 + 1e-6), np.max(err[~und])
         assert np.all(err[und] <= 2 * 1e-3 + 1e-6)

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import GROUPS, TIE_TOL, cam_f32, f32, hp32, pixel_exclusions, rel_group_error, sign_undetermined
+from helpers import GROUPS, TIE_TOL, cam_f32, f32, hp32, pixel_exclusions, rel_group_error, undetermined_visible
 from synth import scenes
 
 pytestmark = pytest.mark.gpu
@@ -91,7 +91,9 @@ def _check_step(orc, scene, n, t, prec_bf16, W, M, V, Cn, gids, grad, hp, lr, op
     D = W.shape[0]
     g_full = np.zeros((D, n))
     g_full[:, gids] = grad[:, gids]
-    und = sign_undetermined(g_full)
+    # entries whose FP32 gradient cannot fix the step's sign (visible Gaussians
+    # only; their share is reported and bounded)
+    und = undetermined_visible(g_full, gids, f"step {t}")
     lr_row = np.array([lr[0]] * 3 + [lr[1]] * 3 + [lr[2]] * 4 + [lr[3]] + [lr[4]] * 3 + [lr[5]] * (D - 14))[:, None]
     if not prec_bf16:
         for k, s in GROUPS.items():
