@@ -85,6 +85,59 @@ def deferred_vs_eager_on_orbit(gs, orbit_radius):
     return float(np.mean(fractions))
 
 
+def windowed_differences(orc, P, deg, r, wimg, count, seed, h=1e-4):
+    """Central differences of <wimg, image> (FP64 oracle) for `count` random
+    (parameter row, visible Gaussian) pairs.  Perturbing one Gaussian changes
+    only the pixels of its rectangle's tiles, so each side is composited on
+    those tiles alone with the lists of the unperturbed render `r`.  A pair is
+    skipped (fd None) when the perturbation changes a discrete decision: the
+    Gaussian's keep, rectangle, radius or clamps, its depth order in any of
+    its lists, or any affected pixel's contributor sequence (a kink inside
+    the difference)."""
+    oc, sp0, kg, rg = r["cam"], r["splats"], r["key_gid"], r["ranges"]
+    tx, _ = orc.tiles_of(oc)
+    tw, th = oc.tile_w, oc.tile_h
+    keys = ("keep", "rect", "radius", "rgb_clamped", "clampx", "clampy")
+    vis = np.nonzero(sp0["keep"] == 1)[0]
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        row, i = int(rng.integers(0, P.shape[0])), int(rng.choice(vis))
+        x0, x1, y0, y1 = (int(v) for v in sp0["rect"][i])
+        tiles = [b * tx + a for b in range(y0, y1) for a in range(x0, x1)]
+        sub = np.zeros_like(rg)
+        sub[tiles] = rg[tiles]
+        mask = np.zeros((oc.height, oc.width), bool)
+        mask[y0 * th:y1 * th, x0 * tw:x1 * tw] = True
+        vals, ok = [], True
+        for sg in (1.0, -1.0):
+            q = P[:, i:i + 1].copy()
+            q[row] += sg * h
+            rec = orc.project(q, deg, oc)[0]
+            ok = all(np.array_equal(rec[k], sp0[i][k]) for k in keys)
+            for t in tiles if ok else []:
+                lst = kg[rg[t, 0]:rg[t, 1]]
+                p = np.nonzero(lst == i)[0]
+                if p.size:
+                    d = rec["depth_f32"]
+                    p = int(p[0])
+                    if (p > 0 and not sp0["depth_f32"][lst[p - 1]] < d) or \
+                            (p + 1 < lst.size and not d < sp0["depth_f32"][lst[p + 1]]):
+                        ok = False
+                        break
+            if not ok:
+                break
+            sp = sp0.copy()
+            sp[i] = rec
+            img, _, _, _, hs = orc.composite(sp, oc, kg, sub)
+            if not np.array_equal(hs[mask], r["decision_hash"][mask]):
+                ok = False
+                break
+            vals.append(float(np.sum(wimg[:, mask] * img[:, mask])))
+        out.append((row, i, (vals[0] - vals[1]) / (2 * h) if ok else None))
+    return out
+
+
 def test_gradients_at_200k_against_oracle_and_differences(gs, orc):
     c = scenes.cfg_diff_check()
     P, deg, cam = f32(c["scene"]), c["sh_degree"], cam_f32(c["cams"][0])
@@ -129,3 +182,34 @@ def test_gradients_at_200k_against_oracle_and_differences(gs, orc):
             checked += 1
             assert abs(g_gpu[row, i] - fd) <= 1e-3 * abs(fd) + 1e-6 * np.abs(g_ref).max(), (row, i, g_gpu[row, i], fd)
     assert checked >= 6
+
+
+def test_gradients_at_200k_differences_on_1000_random_parameters(gs, orc):
+    """The differentiation check on 1,000 random parameters of visible
+    Gaussians (200k Gaussians, 512x512, SH degree 3, 5% near-degenerate
+    covariances): the GPU gradient through the autograd function against
+    central differences of the FP64 oracle (h = 1e-4), each evaluated on the
+    tiles its Gaussian reaches (windowed_differences); pairs with a kink inside
+    the difference are skipped and counted."""
+    c = scenes.cfg_diff_check()
+    P, deg, cam = f32(c["scene"]), c["sh_degree"], cam_f32(c["cams"][0])
+    n = P.shape[1]
+    ctx = gs.Context(max_gaussians=n, max_visible=n, max_keys=20_000_000, max_width=cam.width, max_height=cam.height,
+                     tile=(16, 16), max_sh_degree=deg)
+    scene = gs.GaussianScene(P, deg, with_optimizer=False)
+    ids, nv = ctx.cull(scene, cam)
+    w = scene.w.detach().requires_grad_(True)
+    scene.w = w
+    img = gs.render(ctx, scene, cam, ids, nv)
+    wimg = np.random.default_rng(5).normal(size=tuple(img.shape))
+    (g,) = torch.autograd.grad((img * torch.as_tensor(wimg, dtype=torch.float32, device="cuda")).sum(), w)
+    g_gpu = g[:, :n].cpu().numpy().astype(np.float64)
+    r = orc.render(P, deg, cam, (16, 16))
+    g_ref, _ = orc.backward(P, deg, r["cam"], r["splats"], r["key_gid"], r["ranges"], wimg)
+    scale = np.abs(g_ref).max()
+    res = windowed_differences(orc, P, deg, r, wimg, 1000, seed=17)
+    done = [(row, i, fd) for row, i, fd in res if fd is not None]
+    assert len(done) >= 900, (len(done), len(res))
+    ratio = max(abs(g_gpu[row, i] - fd) / (1e-3 * abs(fd) + 1e-6 * scale) for row, i, fd in done)
+    print(f"central differences: {len(done)} of {len(res)} random parameters checked, worst error / bound {ratio:.3f}")
+    assert ratio <= 1.0, ratio
