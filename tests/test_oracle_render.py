@@ -149,6 +149,31 @@ def _sphere_quadrature(nt=24, nph=48):
     return dirs, wts
 
 
+def test_sh_basis_signs_and_order_against_scipy(orc):
+    """Signs and order of the 16 basis functions: the real spherical harmonics
+    built from scipy's complex ones (Condon-Shortley phase included) as
+    sqrt(2) Im Y_l^|m| for m < 0, Y_l^0, sqrt(2) Re Y_l^m for m > 0, in the
+    order l = 0..3, m = -l..l (the convention of 3DGS colour coefficients),
+    at random directions; and each degree's truncation (deg < 3 leaves the
+    higher functions zero)."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(float(np.clip(d[2], -1.0, 1.0))), math.atan2(d[1], d[0])
+        want = []
+        for l in range(4):
+            for m in range(-l, l + 1):
+                y = complex(sph_harm_y(l, abs(m), theta, phi))
+                want.append(math.sqrt(2.0) * y.imag if m < 0 else (y.real if m == 0 else math.sqrt(2.0) * y.real))
+        for deg in range(4):
+            Y, _ = orc.sh_basis(deg, d)
+            k = (deg + 1) ** 2
+            np.testing.assert_allclose(Y[:k], want[:k], rtol=0, atol=1e-12)
+            assert np.all(Y[k:] == 0.0)
+
+
 def test_sh_basis_orthonormal_and_harmonic(orc):
     """The 16 real SH functions are orthonormal on the sphere; each Y of degree l
     extends to a harmonic homogeneous polynomial |x|^l Y(x/|x|); dY matches
