@@ -550,6 +550,15 @@ GS_API gs_status gs_split_point(gs_ctx *ctx, const gs_scene *scene, const gs_cam
  * rectangle. */
 GS_API gs_status gs_render_splats(const gs_ctx *ctx, const float **geom, const float **conic, const int32_t **n_vis);
 
+/* Inspection of the last gs_step: the gradients its optimizer used -- the
+ * loss's gradient summed over the step's views (§2.4 step 5) for every
+ * Gaussian a view saw -- as device pointers owned by the context, valid until
+ * the next call that renders or culls: (*grad)[r * (*pitch) + k] is the
+ * gradient of parameter row r of Gaussian (*ids)[k], for k below the device
+ * count **n, ids ascending.  GS_ERR_INVALID_ARG before the first gs_step. */
+GS_API gs_status gs_step_gradients(const gs_ctx *ctx, const float **grad, int64_t *pitch, const int32_t **ids,
+                                   const int32_t **n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ EXPORTS = {
                            c_f32, c_f32, c_vp]),
     "gs_render_lists": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_render_splats": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(c_vp)]),
+    "gs_step_gradients": (c_i32, [c_vp, C.POINTER(c_vp), C.POINTER(c_i64), C.POINTER(c_vp), C.POINTER(c_vp)]),
     "gs_host_tier_stats": (c_i32, [c_vp, C.POINTER(c_i64), C.POINTER(c_i64)]),
     "gs_split_point": (c_i32, [c_vp, C.POINTER(Scene), C.POINTER(Camera), C.POINTER(AdamCfg), c_i32, c_i32,
                                C.POINTER(c_i32), C.POINTER(c_i64), c_vp]),

@@ -328,6 +328,17 @@ class Context:
         keys = ("forward_ms", "update_ms", "wait_ms", "h2d_bytes", "d2h_bytes", "rows", "held_members")
         return dict(zip(keys, list(out)))
 
+    def step_gradients(self, D):
+        """(ids int32 [n], gradients float32 [D][n]) the last gs_step's optimizer
+        used (torch views of context memory, valid until the next render)."""
+        g, p, i, nv = C.c_void_p(), C.c_int64(0), C.c_void_p(), C.c_void_p()
+        self._check(self.lib.gs_step_gradients(self.h, C.byref(g), C.byref(p), C.byref(i), C.byref(nv)),
+                    "gs_step_gradients")
+        n = int(torch.as_tensor(_DeviceArray(nv.value, 1), device=self.device).item())
+        ids = torch.as_tensor(_DeviceArray(i.value, max(n, 1)), device=self.device)[:n]
+        grad = torch.as_tensor(_DeviceArray(g.value, D * p.value, "<f4"), device=self.device).view(D, p.value)[:, :n]
+        return ids, grad
+
     def render_splats(self):
         """Projected splats of the last render, float32 [n_vis][4] each (torch
         views of context memory): (mean2d x, mean2d y, radius, opacity) and

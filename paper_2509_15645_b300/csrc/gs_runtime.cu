@@ -64,7 +64,6 @@ struct CpuUpdateBuf {
 struct CpuTierState {
     int threads = 0;                               // <= 0: every core
     float *stage_d = nullptr;                      // device [SH planes][gcap] forwarded rows (workspace)
-    int32_t *ids_d = nullptr;                      // device [gcap] union ids of a step over several views
     uint8_t *cnt_d = nullptr;                      // device [gcap] counters of the visible ids
     float *stage_h = nullptr;                      // pinned [SH planes][gcap]
     uint8_t *cnt_h = nullptr;                      // pinned [gcap]
@@ -105,6 +104,9 @@ struct gs_ctx {
     uint32_t *vprefix[MAX_VIEWS] = {nullptr};
     int32_t *vids[MAX_VIEWS] = {nullptr};
     uint32_t *union_mask = nullptr, *union_prefix = nullptr, *union_chunk = nullptr;
+    int32_t *union_ids = nullptr;       // [gcap_u] ascending ids of the union of a step's views
+    int last_views = 0;                 // views of the last gs_step (0: none yet)
+    int64_t last_gpitch = 0;            // row pitch of its gradients in grad_u
     float *imgs[MAX_VIEWS] = {nullptr}, *dimgs[MAX_VIEWS] = {nullptr}, *grad_u = nullptr;
     int *work = nullptr;                // rasterizer work counters
     int64_t gcap_u = 0;
@@ -287,9 +289,9 @@ static void carve(gs_ctx *c, char *base)
     c->w.partials = k.take<uint32_t>(1024);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
+    if (g.max_views > 1) c->union_ids = k.take<int32_t>(c->gcap_u);
     if (g.cpu_opt) {
         c->cpu.stage_d = k.take<float>((size_t)(D - N_GEO) * c->gcap_u);
-        c->cpu.ids_d = k.take<int32_t>(c->gcap_u);
         c->cpu.cnt_d = k.take<uint8_t>(c->gcap_u);
     }
     if (g.stage_chunks > 0) {
@@ -1300,6 +1302,17 @@ gs_status gs_host_tier_stats(const gs_ctx *c, int64_t *chunks, int64_t *bytes)
     return GS_OK;
 }
 
+gs_status gs_step_gradients(const gs_ctx *c, const float **grad, int64_t *pitch, const int32_t **ids,
+                            const int32_t **n)
+{
+    if (!c || !c->last_views || !grad || !pitch || !ids || !n) return GS_ERR_INVALID_ARG;
+    *grad = c->grad_u;
+    *pitch = c->last_gpitch;
+    *ids = c->last_views > 1 ? c->union_ids : c->vids[0];
+    *n = c->last_views > 1 ? &c->cnt->n_union : c->nvis_view;
+    return GS_OK;
+}
+
 gs_status gs_render_splats(const gs_ctx *c, const float **geom, const float **conic, const int32_t **n_vis)
 {
     if (!c || !c->have_fwd || !geom || !conic || !n_vis) return GS_ERR_INVALID_ARG;
@@ -1339,10 +1352,12 @@ static StepMasks enqueue_cull_phase(gs_ctx *c, const SceneView &sv, const DevArg
         const int64_t nw = (sv.n + 31) / 32;
         cudaMemsetAsync(c->union_mask, 0, nw * sizeof(uint32_t), s);
         for (int v = 0; v < n_views; v++) launch_mask_or(c->union_mask, c->vmask[v], nw, c->w, s);
-        compact_mask(c->union_mask, sv.n, c->union_chunk, false, c->cpu.ids_d, c->union_prefix, (int)c->gcap_u,
+        compact_mask(c->union_mask, sv.n, c->union_chunk, false, c->union_ids, c->union_prefix, (int)c->gcap_u,
                      &c->cnt->n_union, c->w, s);
         M = StepMasks{c->union_mask, c->union_prefix, c->gcap_u, selected};
     }
+    c->last_views = n_views;
+    c->last_gpitch = M.gcap;
     return M;
 }
 
@@ -1671,7 +1686,7 @@ static gs_status step_cpu_tier(gs_ctx *c, gs_scene *scene, const SceneView &sv0,
     } tev_reset{c};
     // (B)
     const StepMasks M = enqueue_cull_phase(c, sv0, a, n_views, loss, s, adam->max_defer);
-    const int32_t *vis_d = n_views > 1 ? T.ids_d : c->vids[0];
+    const int32_t *vis_d = n_views > 1 ? c->union_ids : c->vids[0];
     const int *nvis_d = n_views > 1 ? &c->cnt->n_union : c->nvis_view;
     launch_gather_u8(sv0.counter, vis_d, nvis_d, (int)M.gcap, T.cnt_d, c->w, s);
     cudaMemcpyAsync(T.counts_h, nvis_d, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -45,33 +45,6 @@ GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "
           "sh_dc": slice(11, 14), "sh_rest": slice(14, None)}
 
 
-def sign_undetermined(g_full, frac=1e-4):
-    """Gradient entries whose FP32 value does not determine the Adam step:
-    below `frac` of their group's largest magnitude (the FP32 gradient's
-    relative error bound), its sign -- and with eps, its size relative to
-    sqrt(v) -- may differ from the FP64 value's, and an early Adam step
-    m / (sqrt(v) + eps) moves by up to +-lr either way."""
-    mask = np.zeros(g_full.shape, bool)
-    for s in GROUPS.values():
-        blk = np.abs(g_full[s])
-        if blk.size:
-            mask[s] = blk < frac * blk.max()
-    return mask
-
-
-def undetermined_visible(g_full, ids, what=""):
-    """sign_undetermined restricted to the visible Gaussians ``ids`` (the others
-    step on their moments alone, which is determined), with the share of the
-    visible entries it covers printed and bounded (< 25%)."""
-    vis = np.zeros(g_full.shape[1], bool)
-    vis[ids] = True
-    und = sign_undetermined(g_full) & vis[None, :]
-    frac = float(und.sum()) / max(g_full.shape[0] * int(vis.sum()), 1)
-    print(f"{what}: {frac:.2%} of the visible Gaussians' gradient entries sign-undetermined")
-    assert frac < 0.25, (what, frac)
-    return und
-
-
 def check_lists(gpu_tiles, gpu_gids, oracle_tiles, oracle_gids, depth_bits, exclude):
     """GPU (tile, Gaussian id) sequence against the oracle's.  Keys of excluded
     Gaussians are dropped from both; within a tile, neighbours may differ in
