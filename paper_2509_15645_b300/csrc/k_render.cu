@@ -419,41 +419,18 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
 
 // emit_splat for sums that are set only in contributing lanes: the other
 // lanes' values are replaced by zeros where the warp sums (no zeroing per entry).
-// PAIRS: a middle tier between the two -- up to PAIR_LANES contributing
-// lanes first combine with their neighbour (lane ^ 1, one shuffle per sum),
-// then the even lane of each pair with a contribution adds the pair's sums
-// (half the atomics of the direct form at a fifth of the reduction's cost).
-constexpr int PAIR_LANES = 24;
-
-template <bool PAIRS = false>
 __device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC,
                                                bool contrib, float v[9], int lane)
 {
     const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
     if (cmask == 0u) return;
     float *row = g9 + (int64_t)k * G9_STRIDE;
-    const int nc = __popc(cmask);
-    if (nc <= DIRECT_LANES) {
+    if (__popc(cmask) <= DIRECT_LANES) {
         if (contrib) {
             atomicAdd(reinterpret_cast<float4 *>(row),
                       make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
             atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
             atomicAdd(row + 8, v[8]);
-        }
-        return;
-    }
-    if (PAIRS && nc <= PAIR_LANES) {
-        float y[9];
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            y[j] = contrib ? v[j] : 0.f;
-            y[j] += __shfl_xor_sync(0xffffffffu, y[j], 1);
-        }
-        if (!(lane & 1) && ((cmask >> lane) & 3u)) {
-            atomicAdd(reinterpret_cast<float4 *>(row),
-                      make_float4(cA * y[0] + cB * y[1], cB * y[0] + cC * y[1], 0.5f * y[2], y[3]));
-            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * y[4], y[5], y[6], y[7]));
-            atomicAdd(row + 8, y[8]);
         }
         return;
     }
@@ -486,7 +463,7 @@ __device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t 
 // contributions to each splat and issues the atomic adds into g9.
 // STATS: also count the (pixel, splat) pairs that pass the square test and the
 // pairs that contribute (stats[0], stats[1]).
-template <int PPT, int BATCH, bool STATS = false, int NW = 0, bool PAIRS = false>
+template <int PPT, int BATCH, bool STATS = false, int NW = 0>
 __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const DevArgs *__restrict__ args,
                                                     unsigned long long *stats = nullptr)
 {
@@ -591,7 +568,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     }
                 }
                 const float4 cn = s1[e];
-                emit_splat_sel<PAIRS>(g9, s_k[e], cn.x, cn.y, cn.z, contrib, v, lane);
+                emit_splat_sel(g9, s_k[e], cn.x, cn.y, cn.z, contrib, v, lane);
                 continue;
             }
             // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
@@ -1310,8 +1287,7 @@ static RasterFwdFn fwd_variant(int v)
     case 6: return k_raster_fwd<1, 64, 4>;
     case 7: return k_raster_fwd<1, 32, 8>;
     case 8: return k_raster_fwd_pairs<32, 8>;
-    case 9: return k_raster_fwd_tma<32, 8>;
-    default: return k_raster_fwd<1, 32, 8>;           // 10: the forward of 7
+    default: return k_raster_fwd_tma<32, 8>;
     }
 }
 
@@ -1337,14 +1313,12 @@ static RasterBwdFn bwd_variant(int v, bool stats)
     case 16: return k_raster_bwd_pairs<32, 8, false>;
     case 17: return k_raster_bwd_pairs<32, 8, true>;
     case 18: return k_raster_bwd_tma<32, 8, false>;
-    case 19: return k_raster_bwd_tma<32, 8, true>;
-    case 20: return k_raster_bwd<1, 32, false, 8, true>;
-    default: return k_raster_bwd<1, 32, true, 8, true>;
+    default: return k_raster_bwd_tma<32, 8, true>;
     }
 }
 
 // Warps per block of a warp-tile variant, else 0.
-static int warp_tile_warps(int v) { return v == 6 ? 4 : (v >= 7 && v <= 10) ? 8 : 0; }
+static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8 || v == 9) ? 8 : 0; }
 
 bool raster_variant_ok(int v, int tile_w, int tile_h, bool has_records)
 {

@@ -260,7 +260,7 @@ def test_raster_variants_agree(gs, orc, name, tile):
         assert max(errs.values()) <= 1e-4, (v, errs)
     assert tried >= 2
     if tile[0] * tile[1] == 32:
-        assert tried >= 6                    # the warp-tile variants 6-10 among them
+        assert tried >= 5                    # the warp-tile variants 6-9 among them
     for im in images[1:]:
         np.testing.assert_array_equal(im, images[0])
     (vf, vb), ms_f, ms_b = ctx.autotune(scene, camf)
