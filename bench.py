@@ -516,10 +516,11 @@ def run_ours(args):
         return m
 
     # DRAM bytes per launch of the rasterizer backward on this workload (10M,
-    # 1920x1080, one view), by variant, from one ncu capture of
-    # dram__bytes_read.sum + dram__bytes_write.sum (profiles/launches_aerial10m_1080p.md,
-    # profiles/raster_bwd_variants_aerial2m_density10m.md); other workloads: not captured
-    RASTER_BWD_TRAFFIC = {7: 125.1e6, 8: 125.1e6, 9: 219.1e6}
+    # 1920x1080, one view), by variant, from ncu captures of
+    # dram__bytes_read.sum + dram__bytes_write.sum of the kernels as they are
+    # (profiles/launches_aerial10m_1080p.md); variant 9 changed since its capture
+    # (None); other workloads: not captured
+    RASTER_BWD_TRAFFIC = {7: 125.5e6, 8: 125.1e6, 9: None}
 
     def roofline(m):
         """Roofline entry of the kernel with the largest live event time per step."""
@@ -715,6 +716,82 @@ def extra_forms(args):
 
 
 # ---------------------------------------------------------------------------- image splitting (§4.4)
+
+def run_config_timings(args):
+    """The GPU path on the smaller workload definitions (after autotuning,
+    CUDA events over K steps after W warm-ups): the 10k-Gaussian 64x64 step
+    (gs_step, SH 0, 16x16 tiles); the 1M heightfield's 1080p orbit (gs_step over
+    the orbit's views in turn, deferred Adam, 8x4 tiles); the 200k 512x512
+    differentiation case (gs_render_fwd + gs_render_bwd through the C ABI,
+    16x16 tiles).  Inputs resident, no flush (these are small)."""
+    import torch
+    import paper_2509_15645_b300 as gs
+    from synth import scenes
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    K, Wm = args.steps, max(args.warmup, 3)
+    stream = torch.cuda.current_stream()
+    out = {"metric": "GPU ms per step on the small workload definitions", "unit": "ms", "steps": K, "warmup": Wm,
+           "results": {}}
+
+    def timed(fn):
+        for s in range(Wm):
+            fn(s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(K):
+            fn(Wm + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    def step_case(c, tile, views):
+        P, deg = c["scene"], c["sh_degree"]
+        n = P.shape[1]
+        cams = c["cams"][:views]
+        W, H = cams[0].width, cams[0].height
+        ctx = gs.Context(max_gaussians=n, max_visible=n, max_keys=min(64 * n, 80_000_000), max_width=W,
+                         max_height=H, tile=tile, max_sh_degree=deg)
+        ts = gs.GaussianScene(c["target_scene"], deg, with_optimizer=False)
+        tg = []
+        for cam in cams:
+            ids, nv = ctx.cull(ts, cam)
+            tg.append(ctx.render_fwd(ts, cam, ids, nv).clone())
+        del ts
+        sc = gs.GaussianScene(P, deg)
+        ctx.autotune(sc, cams[0])
+        adam = gs.adam_struct(lr=1e-3, eps=1e-15)
+        loss = torch.zeros(1, device=dev)
+        ms = timed(lambda s: ctx.step(sc, [cams[s % len(cams)]], [tg[s % len(cams)]], adam, loss=loss))
+        ctx.sync_status()
+        return round(ms, 4), int(ctx.counters()[0].item())
+
+    c1 = scenes.cfg_small_step()
+    ms, nv = step_case(c1, (16, 16), 1)
+    out["results"]["cube10k_64px_sh0_step"] = {"ms": ms, "steps_per_s": round(1e3 / ms, 1), "visible": nv}
+    c2 = scenes.cfg_heightfield_1m()
+    ms, nv = step_case(c2, (8, 4), 100)
+    out["results"]["heightfield1m_1080p_orbit_step"] = {"ms": ms, "steps_per_s": round(1e3 / ms, 1),
+                                                         "visible_last_view": nv}
+    c3 = scenes.cfg_diff_check()
+    P, deg, cam = c3["scene"], c3["sh_degree"], c3["cams"][0]
+    n = P.shape[1]
+    ctx = gs.Context(max_gaussians=n, max_visible=n, max_keys=20_000_000, max_width=cam.width, max_height=cam.height,
+                     tile=(16, 16), max_sh_degree=deg)
+    sc = gs.GaussianScene(P, deg, with_optimizer=False)
+    ids, nv = ctx.cull(sc, cam)
+    dimg = torch.randn(3, cam.height, cam.width, device=dev)
+
+    def fwd_bwd(s):
+        ctx.render_fwd(sc, cam, ids, nv)
+        ctx.render_bwd(dimg, sc.D)
+
+    ms = timed(fwd_bwd)
+    ctx.sync_status()
+    out["results"]["cube200k_512px_sh3_fwd_bwd"] = {"ms": round(ms, 4), "visible": int(nv.item())}
+    print(json.dumps(out), flush=True)
+
 
 def run_split_demo(args):
     """Balance-aware image splitting (§4.4) on a view that crosses mem_limit:
@@ -958,6 +1035,8 @@ def main():
                     help="pin the rasterizer variant instead of the autotuned one: V, or F,B for forward and backward")
     ap.add_argument("--no-extra-forms", dest="extra_forms", action="store_false",
                     help="skip the batched-bf16 and 40M host-tier sub-records of the default line")
+    ap.add_argument("--config-timings", action="store_true",
+                    help="time the GPU path on the smaller workload definitions (10k step, 1M orbit, 200k fwd+bwd)")
     ap.add_argument("--split-demo", action="store_true",
                     help="measure balance-aware image splitting (§4.4) on a 1M-Gaussian view that crosses mem_limit")
     ap.add_argument("--oracle-workloads", action="store_true",
@@ -967,6 +1046,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.split_demo:
         run_split_demo(args)
+    elif args.config_timings:
+        run_config_timings(args)
     elif args.impl == "reference" and args.oracle_workloads:
         run_oracle_workloads(args)
     elif args.impl == "reference":

@@ -365,10 +365,9 @@ GS_API gs_status gs_timing_read(gs_ctx *ctx, float *ms_out, int32_t max_steps, i
  * (32-pixel tiles, contexts with list_records only): as 7, each batch staged
  * in shared memory by one TMA bulk copy of the tile's records, written in
  * list order by the first rasterizer pass that uses them (48 bytes per key
- * of extra traffic).  v = 10 (64-pixel tiles only): as 7 with two vertically
- * adjacent pixels per lane.  Every variant computes the same image bit for
- * bit; they differ only in speed. */
-#define GS_RASTER_VARIANTS 11
+ * of extra traffic).  Every variant computes the same image bit
+ * for bit; they differ only in speed. */
+#define GS_RASTER_VARIANTS 10
 
 /* Autotuner: time every variant the context's tile shape allows on this scene
  * and view (render forward and backward separately; CUDA events, best of

@@ -13,7 +13,7 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_BUDGET, GS_ERR_CAPACI
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_OOM", 3: "GS_ERR_CUDA", 4: "GS_ERR_BUDGET",
                 5: "GS_ERR_CAPACITY", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_NUMERIC"}
 GS_FP32, GS_BF16_SH_MOM, GS_BF16_SH_MOM_RN = 0, 1, 2
-RASTER_VARIANTS = 11
+RASTER_VARIANTS = 10
 SPANS = ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd")
 GS_ADAM_DEFERRED, GS_ADAM_EAGER = 0, 2
 GS_OPT_ADAM, GS_OPT_ADAMW, GS_OPT_SGDM = 0, 1, 2

@@ -273,7 +273,7 @@ struct RasterJob {
     int *work;
 };
 
-constexpr int N_RASTER_VARIANTS = 11;
+constexpr int N_RASTER_VARIANTS = 10;
 // The variant whose lists are staged by TMA bulk copies from records in list order.
 constexpr int RASTER_TMA_VARIANT = 9;
 

@@ -1287,8 +1287,7 @@ static RasterFwdFn fwd_variant(int v)
     case 6: return k_raster_fwd<1, 64, 4>;
     case 7: return k_raster_fwd<1, 32, 8>;
     case 8: return k_raster_fwd_pairs<32, 8>;
-    case 9: return k_raster_fwd_tma<32, 8>;
-    default: return k_raster_fwd<2, 32, 8>;           // 10: 64-pixel warp tiles, two pixels per lane
+    default: return k_raster_fwd_tma<32, 8>;
     }
 }
 
@@ -1314,20 +1313,18 @@ static RasterBwdFn bwd_variant(int v, bool stats)
     case 16: return k_raster_bwd_pairs<32, 8, false>;
     case 17: return k_raster_bwd_pairs<32, 8, true>;
     case 18: return k_raster_bwd_tma<32, 8, false>;
-    case 19: return k_raster_bwd_tma<32, 8, true>;
-    case 20: return k_raster_bwd<2, 32, false, 8>;
-    default: return k_raster_bwd<2, 32, true, 8>;
+    default: return k_raster_bwd_tma<32, 8, true>;
     }
 }
 
 // Warps per block of a warp-tile variant, else 0.
-static int warp_tile_warps(int v) { return v == 6 ? 4 : (v >= 7 && v <= 10) ? 8 : 0; }
+static int warp_tile_warps(int v) { return v == 6 ? 4 : (v == 7 || v == 8 || v == 9) ? 8 : 0; }
 
 bool raster_variant_ok(int v, int tile_w, int tile_h, bool has_records)
 {
     if (v < 0 || v >= N_RASTER_VARIANTS) return false;
     if (v == RASTER_TMA_VARIANT && !has_records) return false;
-    if (warp_tile_warps(v)) return tile_w * tile_h == (v == 10 ? 64 : 32);
+    if (warp_tile_warps(v)) return tile_w * tile_h == 32;
     const int ppt = 1 << (v >> 1);
     const int threads = tile_w * tile_h / ppt;
     return tile_h % ppt == 0 && threads >= 32 && threads <= 256 && threads % 32 == 0;

@@ -228,8 +228,7 @@ def test_render_backward_parity(gs, orc, name):
 
 @pytest.mark.parametrize("name,tile", [("cube_offaxis_sh3", (16, 16)), ("ragged_tiles", (16, 16)),
                                        ("tile32x8", (32, 8)), ("cube10k", (8, 8)), ("cube10k", (16, 8)),
-                                       ("cube10k", (64, 4)), ("cube_offaxis_sh3", (8, 4)), ("ragged_tiles", (4, 8)),
-                                       ("ragged_tiles", (16, 4))])
+                                       ("cube10k", (64, 4)), ("cube_offaxis_sh3", (8, 4)), ("ragged_tiles", (4, 8))])
 def test_raster_variants_agree(gs, orc, name, tile):
     """Every rasterizer variant (pixels per thread, batch) the tile shape allows
     renders the same image bit for bit, and its gradients match the oracle."""
@@ -262,8 +261,6 @@ def test_raster_variants_agree(gs, orc, name, tile):
     assert tried >= 2
     if tile[0] * tile[1] == 32:
         assert tried >= 5                    # the warp-tile variants 6-9 among them
-    if tile[0] * tile[1] == 64:
-        assert tried >= 5                    # 0-3 and the two-pixel warp tiles (10)
     for im in images[1:]:
         np.testing.assert_array_equal(im, images[0])
     (vf, vb), ms_f, ms_b = ctx.autotune(scene, camf)
