@@ -479,7 +479,7 @@ def run_ours(args):
         if tier == gs.GS_TIER_DEVICE:
             pairs = np.array([ctx.raster_pair_counts(sc, cam) for cam in cams], np.float64)   # untimed
         else:
-            pairs = np.full((1, 2), np.nan)
+            pairs = np.full((1, 3), np.nan)
         st = {}
         for k in ("step", "cull", "fwd", "bwd", "adam", "adam_apply", "raster_bwd"):
             vals = [x[k] for x in spans if x[k] >= 0]
@@ -489,6 +489,7 @@ def run_ours(args):
              "n_upd": float(np.mean([x[2] for x in stats])), "n_rest": float(np.mean([x[3] for x in stats])),
              "n_fp64": float(np.mean([x[4] for x in stats])), "n_cand": float(np.mean([x[5] for x in stats])),
              "sq_pairs": float(pairs[:, 0].mean()), "on_pairs": float(pairs[:, 1].mean()),
+             "empty_keys": float(pairs[:, 2].mean()),
              "kernels": kernels, "copy_trace": copy_trace,
              "staged_chunks": (float(np.mean([x[0] for x in staged]))
                                if staged and tier == gs.GS_TIER_HOST_SH else None),
@@ -636,6 +637,7 @@ def run_ours(args):
                    "update_set": round(m["n_upd"]), "fp64_covariances_per_view": round(m["n_fp64"]),
                    "cull_pretest_survivors": round(m["n_cand"]),
                    "square_pairs_per_view": _int(m["sq_pairs"]), "contrib_pairs_per_view": _int(m["on_pairs"]),
+                   "keys_without_contributor_per_view": _int(m["empty_keys"]),
                    "raster_variant": {"fwd": m["variant"][0], "bwd": m["variant"][1]},
                    "autotune_ms": {k: [None if t is None else round(t, 4) for t in v]
                                    for k, v in m["variant_ms"].items()}},

@@ -391,8 +391,11 @@ GS_API gs_status gs_set_raster_variants(gs_ctx *ctx, int32_t fwd, int32_t bwd);
 /* Work counts of the rasterizer backward for one view (benchmarks): renders
  * forward and backward once (the rendered image as dL/dimage) with a counting
  * instance of the backward kernel and writes counts[0] = (pixel, splat) pairs
- * that pass the 3-sigma square test and counts[1] = pairs that contribute
- * (alpha >= 1/255 before the transmittance stop).  Synchronises the stream. */
+ * that pass the 3-sigma square test, counts[1] = pairs that contribute
+ * (alpha >= 1/255 before the transmittance stop) and counts[2] = (tile, splat)
+ * keys of the lists that no pixel of their tile takes as a contributor
+ * (32-pixel tiles; 0 for other tile shapes).  counts: host, 3 entries.
+ * Synchronises the stream. */
 GS_API gs_status gs_raster_pair_counts(gs_ctx *ctx, const gs_scene *scene, const gs_camera *cam, uint64_t *counts,
                                        void *stream);
 

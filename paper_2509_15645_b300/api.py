@@ -498,13 +498,14 @@ class Context:
         return [dict(zip(L.SPANS, buf[s * k:(s + 1) * k])) for s in range(n.value)]
 
     def raster_pair_counts(self, scene: GaussianScene, cam, stream=None):
-        """(square-test pairs, contributing pairs) of the backward for one view."""
-        out = (C.c_uint64 * 2)()
+        """(square-test pairs, contributing pairs, keys with no contributing pixel)
+        of the backward for one view."""
+        out = (C.c_uint64 * 3)()
         sc = scene.struct()
         cs = camera_struct(cam)
         self._check(self.lib.gs_raster_pair_counts(self.h, C.byref(sc), C.byref(cs), out, _stream(stream)),
                     "gs_raster_pair_counts")
-        return int(out[0]), int(out[1])
+        return int(out[0]), int(out[1]), int(out[2])
 
     def step_kernel_count(self):
         n = C.c_int32(0)

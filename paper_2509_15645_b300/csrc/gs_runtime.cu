@@ -92,6 +92,7 @@ struct gs_ctx {
     int *nvis_view = nullptr;    // [MAX_VIEWS] visible counts of gs_step's views
     int *n_render = nullptr;     // visible count of the last gs_render_fwd
     int *n_tmp = nullptr;
+    unsigned long long *stats = nullptr;   // counters of gs_raster_pair_counts
     int64_t nwords = 0, nchunks = 0;
     uint32_t *mask = nullptr, *wprefix = nullptr, *chunk = nullptr;
     uint32_t *umask = nullptr, *uchunk = nullptr;
@@ -227,6 +228,7 @@ static void carve(gs_ctx *c, char *base)
     c->nvis_view = k.take<int>(MAX_VIEWS);
     c->n_render = k.take<int>(1);
     c->n_tmp = k.take<int>(4);
+    c->stats = k.take<unsigned long long>(4);
     c->mask = k.take<uint32_t>(NW);
     c->wprefix = k.take<uint32_t>(NW);
     c->chunk = k.take<uint32_t>(NC);
@@ -1082,18 +1084,21 @@ gs_status gs_raster_pair_counts(gs_ctx *c, const gs_scene *scene, const gs_camer
     int32_t *ids = c->vids[0];
     launch_cull(sv, c->args + SLOT_RENDER, 0, c->mask, c->chunk, c->w, s);
     compact_mask(c->mask, sv.n, c->chunk, true, ids, c->wprefix, (int)c->cfg.max_visible, c->n_render, c->w, s);
-    unsigned long long *dev = reinterpret_cast<unsigned long long *>(c->n_tmp);   // 16 bytes of scratch
-    cudaMemsetAsync(dev, 0, 2 * sizeof(unsigned long long), s);
+    unsigned long long *dev = c->stats;
+    cudaMemsetAsync(dev, 0, 3 * sizeof(unsigned long long), s);
     render_forward(sv, c->args + SLOT_RENDER, 0, ids, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], false, nullptr, nullptr,
                    c->w, s, c->work);
+    // the empty-key count needs a warp-tile backward (one tile per warp): 7 where the tile shape allows it
+    const int vb = c->rbs[0].variant_bwd;
+    if (raster_variant_ok(7, c->cfg.tile_w, c->cfg.tile_h, false)) c->rbs[0].variant_bwd = 7;
     render_backward(sv, c->args + SLOT_RENDER, 0, c->n_render, c->rbs[0], a.cam[0], c->imgs[0], c->grad_u, c->cfg.max_visible,
                     nullptr, nullptr, nullptr, c->w, s, c->work, dev);
-    unsigned long long host[2] = {0, 0};
+    c->rbs[0].variant_bwd = vb;
+    unsigned long long host[3] = {0, 0, 0};
     if (cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return cuda_check(c, "gs_raster_pair_counts");
-    counts[0] = host[0];
-    counts[1] = host[1];
+    for (int i = 0; i < 3; i++) counts[i] = host[i];
     c->have_fwd = false;
     return GS_OK;
 }

@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
 {
     constexpr bool WT = NW > 0;
     constexpr int NS = WT ? NW : 1;
-    unsigned long long n_sq = 0, n_on = 0;
+    unsigned long long n_sq = 0, n_on = 0, n_empty = 0;
     __shared__ float4 s0_[NS][BATCH], s1_[NS][BATCH], s2_[NS][BATCH];
     __shared__ uint32_t s_k_[NS][BATCH];
     __shared__ int s_item;
@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     }
                 }
                 const float4 cn = s1[e];
+                if (STATS && WT && __ballot_sync(0xffffffffu, contrib) == 0u && lane == 0) n_empty++;
                 emit_splat_sel(g9, s_k[e], cn.x, cn.y, cn.z, contrib, v, lane);
                 continue;
             }
@@ -660,6 +661,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
         if (lane == 0) {
             atomicAdd(stats, n_sq);
             atomicAdd(stats + 1, n_on);
+            if (n_empty) atomicAdd(stats + 2, n_empty);   // held by lane 0 only
         }
     }
 }

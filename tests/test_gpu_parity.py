@@ -275,12 +275,21 @@ def test_raster_pair_counts(gs, orc):
     camf = cam_f32(cam)
     ctx = make_ctx(gs, P.shape[1], camf.width, camf.height, deg=3, tile=tile)
     scene = gs.GaussianScene(P, deg)
-    n_sq, n_on = ctx.raster_pair_counts(scene, camf)
+    n_sq, n_on, n_empty = ctx.raster_pair_counts(scene, camf)
     r = orc.render(f32(P), deg, camf, tile)
     ex = r["margin"] < TIE_TOL
     ref = int(r["n_contrib"].sum())
     assert abs(n_on - ref) <= 2 * int(ex.sum()) + 2, (n_on, ref)
     assert n_sq >= n_on > 0
+    assert n_empty == 0                        # counted on 32-pixel tiles only
+    # 8x4 tiles: keys whose tile takes the splat at no pixel, fewer than the keys
+    P2, cam2, deg2, tile2 = _case("tile8x4_ragged")
+    cam2 = cam_f32(cam2)
+    ctx2 = make_ctx(gs, P2.shape[1], cam2.width, cam2.height, deg=deg2, tile=tile2)
+    s2 = gs.GaussianScene(P2, deg2)
+    n_sq2, n_on2, n_empty2 = ctx2.raster_pair_counts(s2, cam2)
+    keys = int(orc.render(f32(P2), deg2, cam2, tile2)["key_gid"].shape[0])
+    assert 0 < n_empty2 < keys and n_on2 > 0, (n_empty2, keys)
 
 
 def test_loss_l1_kernel(gs):
