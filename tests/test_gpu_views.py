@@ -310,3 +310,43 @@ def test_cpu_optimizer_tier_pipelined_trajectory(gs, orc):
         moved = np.sqrt(np.mean((W[s] - W0[s]) ** 2))
         drift = np.sqrt(np.mean((gw[s] - W[s]) ** 2))
         assert drift <= 3e-2 * moved + 1e-9, (g, drift, moved)
+
+
+def test_cpu_optimizer_tier_two_views_per_step(gs, orc):
+    """The host-core optimizer configuration with two views per step (the
+    visible ids are the union of the views', the forwarded rows and the
+    gradients follow the union's order): the loss (sum of the views' L1
+    losses), the union's summed gradients and the stored state after each step
+    against the oracle from the same stored state (counter bound 5)."""
+    cams = _views()
+    targets = _targets(orc, cams)
+    P = _scene(41)
+    scene = gs.GaussianScene(P, DEG, tier=gs.GS_TIER_HOST_CPU_OPT)
+    ctx = gs.Context(max_gaussians=N, max_visible=N, max_keys=64 * N, max_width=96, max_height=72, tile=TILE,
+                     max_sh_degree=DEG, max_views=2, cpu_opt=1)
+    adam = gs.adam_struct(lr=LR, eps=1e-15, seed=9, max_defer=5)
+    hp = hp32(orc, lr=LR, eps=1e-15, max_defer=5)
+    tg = [torch.as_tensor(x, dtype=torch.float32, device="cuda") for x in targets]
+    for t, pair in enumerate([(0, 1), (2, 3), (1, 2), (3, 0), (0, 2), (1, 3)], start=1):
+        W, M, V, Cn = _state(scene, N)
+        Wcur, _, _ = orc.adam_materialize(W, M, V, Cn, t - 1, hp)
+        grad = np.zeros((W.shape[0], N))
+        affected = np.zeros(N, bool)
+        gids, ref_loss = [], 0.0
+        for k in pair:
+            rr = orc.render_loss_backward(Wcur, DEG, cams[k], targets[k], TILE)
+            ids, nv = ctx.cull(scene, cams[k], adam)
+            ctx.sync_status()
+            g = ids[:int(nv.item())].cpu().numpy().astype(np.int32)
+            gids.append(g)
+            grad[:, g] += rr["grad"][:, g]
+            affected |= _tie_affected(orc, Wcur, rr, pixel_exclusions(rr, g))[0]
+            ref_loss += rr["loss"]
+        union = np.union1d(gids[0], gids[1]).astype(np.int32)
+        loss = ctx.step(scene, [cams[k] for k in pair], [tg[k] for k in pair], adam)
+        ctx.sync_status()
+        assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss + 1e-7, (t, loss.item(), ref_loss)
+        assert affected.mean() < 0.04, (t, affected.mean())
+        _check_step(orc, ctx, scene, N, t, False, W, M, V, Cn, union, grad, hp, LR, skip=affected)
+        st = ctx.cpu_tier_stats()
+        assert st["rows"] == len(union)
