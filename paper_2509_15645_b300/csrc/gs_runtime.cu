@@ -1390,7 +1390,10 @@ static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &
         if (v0 == 0) c->w.mark(TP_FWD0, s);
         for (int j = 0; j < k; j++)
             prepare_view(sv, args, v0 + j, c->vids[v0 + j], c->nvis_view + v0 + j, c->rbs[j], a.cam[v0 + j], c->w, s);
-        raster_forward(args, k, rbs, a.cam + v0, c->imgs, true, c->dimgs, loss, c->work, c->w, s, v0);
+        // the step needs only the final colours the backward reads (no separate image copy)
+        float *fin[MAX_VIEWS];
+        for (int j = 0; j < k; j++) fin[j] = c->rbs[j].cfinal;
+        raster_forward(args, k, rbs, a.cam + v0, fin, true, c->dimgs, loss, c->work, c->w, s, v0);
         if (v0 == 0) {
             c->w.mark(TP_FWD1, s);
             c->w.mark(TP_BWD0, s);
