@@ -244,6 +244,8 @@ struct RenderBufs {
     float4 *lrec;            // [3 kcap] splat records in list order (rec0, rec1, rec2 with rec2.w = splat index
                              // bits), written for the TMA-staged rasterizer variant
     int32_t *big_idx;        // [cap] splats whose tiles a warp counts and emits (k_big_counts, k_big_emit)
+    uint32_t *reach;         // [cap] small-rectangle splats: bit j set when the j-th tile of the rectangle
+                             // (row-major) is reached (written by the key count, read by the emission)
     int variant;             // forward rasterizer variant (pixels per thread, batch), see raster_variant_ok
     int variant_bwd;         // backward rasterizer variant
     // filled by render_fwd

@@ -283,6 +283,7 @@ static void carve(gs_ctx *c, char *base)
         rb.fix_flag = k.take<uint8_t>(V);
         rb.n_big = k.take<int>(2);
         rb.big_idx = k.take<int32_t>(V);
+        rb.reach = k.take<uint32_t>(V);
         rb.lrec = g.list_records ? k.take<float4>(3 * (size_t)K) : nullptr;
         c->imgs[v] = k.take<float>(P);
         c->dimgs[v] = k.take<float>(P);

@@ -1,10 +1,10 @@
 // k_lists.cu -- each view's per-tile lists of the splats that can reach the
 // tile, in front-to-back order (§2.4 step 2, tile binning and sort):
 //
-//   k_tiles_small<false>, k_big_counts   the tiles each splat reaches (the
+//   k_tiles_count, k_big_counts          the tiles each splat reaches (the
 //                                        list filter): a count per tile
 //   scan_counts                          each tile's first key, the key total
-//   k_tiles_small<true>, k_big_emit      (depth, splat) keys into the tiles'
+//   k_tiles_emit, k_big_emit             (depth, splat) keys into the tiles'
 //                                        lists through per-tile cursors
 //   k_tile_sort(_long)                   each list sorted by depth (ties by
 //                                        Gaussian id) with bitonic networks
@@ -117,19 +117,122 @@ static_assert(row_by_multiply_shift_exact(BIG_RECT), "pair row index by multiply
 
 // The small rectangles' (splat, tile) pairs, load-balanced over a warp: the
 // warp takes 32 splats (kept, not FP64-flagged, at most BIG_RECT tiles: the
-// partition k_gather_project leaves to it), scans their rectangle areas, and
-// its lanes walk the concatenated pairs 32 at a time, so that the atomics of
-// different pairs are in flight together.  EMIT = false: one more key for each
-// tile reached; EMIT = true: the key (depth, k) into the tile's list at slot
-// tile_off[t] + (a cursor of t), complete but unordered until k_tile_sort.
-template <bool EMIT>
-__global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ rect, const float4 *__restrict__ rec0,
-                                                     const float4 *__restrict__ rec1,
-                                                     const uint32_t *__restrict__ depth,
-                                                     const uint8_t *__restrict__ fix_flag, const int *n_vis_p, int cap,
-                                                     int64_t kcap, const DevArgs *__restrict__ args, int view,
-                                                     uint32_t *tile_cnt, const uint32_t *__restrict__ tile_off,
-                                                     uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
+// partition k_gather_project leaves to it) and its lanes walk their
+// concatenated pairs 32 at a time, so that the atomics of different pairs are
+// in flight together.
+//   k_tiles_count: every pair of a rectangle, through the list filter; one
+//   more key for each tile reached, and each splat's reached tiles as a mask
+//   (bit j: the j-th tile of its rectangle, row-major; BIG_RECT <= 32).
+//   k_tiles_emit: only the reached pairs (the set bits of the masks), with no
+//   filter; the key (depth, k) into the tile's list at slot tile_off[t] + (a
+//   cursor of t), complete but unordered until k_tile_sort.
+constexpr int TILES_BLOCK = 256;
+static_assert(BIG_RECT <= 32, "a small rectangle's reached tiles fit one 32-bit mask");
+
+// Exclusive and total sums of `area` over the warp, and the last lane whose
+// pairs start at or before pair q of the concatenation.
+__device__ __forceinline__ int warp_excl_scan(int area, int lane, int &total)
+{
+    int incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - area;
+}
+__device__ __forceinline__ int owner_lane(int ex, int q)
+{
+    int sl = 0;
+#pragma unroll
+    for (int st = 16; st; st >>= 1) {
+        const int c = sl + st;
+        if (__shfl_sync(0xffffffffu, ex, c) <= q) sl = c;
+    }
+    return sl;
+}
+
+__global__ void __launch_bounds__(TILES_BLOCK) k_tiles_count(const uint2 *__restrict__ rect,
+                                                             const float4 *__restrict__ rec0,
+                                                             const float4 *__restrict__ rec1,
+                                                             const uint8_t *__restrict__ fix_flag, const int *n_vis_p,
+                                                             int cap, const DevArgs *__restrict__ args, int view,
+                                                             uint32_t *tile_cnt, uint32_t *__restrict__ reach)
+{
+    // the filter's results of one warp's concatenated pairs (at most 32 x 32)
+    __shared__ uint32_t s_hit[TILES_BLOCK / 32][BIG_RECT + 1];
+    const int n = min(*n_vis_p, cap);
+    const DevCam &cam = args->cam[view];
+    const int tiles_x = cam.tiles_x;
+    const int lane = threadIdx.x & 31;
+    uint32_t *hit = s_hit[threadIdx.x >> 5];
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nwarps) {
+        const int k = g * 32 + lane;
+        uint2 rc = make_uint2(0u, 0u);
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        int area = 0;
+        if (k < n && !fix_flag[k]) {
+            rc = rect[k];
+            area = (int)((rc.x >> 16) - (rc.x & 0xffff)) * (int)((rc.y >> 16) - (rc.y & 0xffff));
+            if (area > 0 && area <= BIG_RECT) {
+                r0 = rec0[k];
+                r1 = rec1[k];
+            } else {
+                area = 0;
+            }
+        }
+        int total;
+        const int ex = warp_excl_scan(area, lane, total);
+        // j / width as (j * ceil(2^16 / width)) >> 16: exact for j * width < 2^16 (here j < 32, width <= 32)
+        const int wd = area ? (int)((rc.x >> 16) - (rc.x & 0xffff)) : 1;
+        const uint32_t inv = (65536u + (uint32_t)wd - 1u) / (uint32_t)wd;
+        for (int q0 = 0; q0 < total; q0 += 32) {
+            const int q = q0 + lane;
+            const int sl = owner_lane(ex, q);
+            const uint32_t rcx = __shfl_sync(0xffffffffu, rc.x, sl), rcy = __shfl_sync(0xffffffffu, rc.y, sl);
+            const float4 a0 = make_float4(__shfl_sync(0xffffffffu, r0.x, sl), __shfl_sync(0xffffffffu, r0.y, sl),
+                                          __shfl_sync(0xffffffffu, r0.z, sl), __shfl_sync(0xffffffffu, r0.w, sl));
+            const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
+                                          __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
+            const int exs = __shfl_sync(0xffffffffu, ex, sl);
+            const uint32_t invs = __shfl_sync(0xffffffffu, inv, sl);
+            bool reached = false;
+            int t = 0;
+            if (q < total) {
+                const int x0 = (int)(rcx & 0xffff), wdt = (int)(rcx >> 16) - x0, y0 = (int)(rcy & 0xffff);
+                const int j = q - exs, row = (int)(((uint32_t)j * invs) >> 16);
+                const int tx = x0 + (j - row * wdt), ty = y0 + row;
+                float X0, X1, Y0, Y1;
+                tile_box(cam, tx, ty, X0, X1, Y0, Y1);
+                reached = splat_reaches_box(a0, a1, X0, X1, Y0, Y1);
+                t = ty * tiles_x + tx;
+            }
+            const uint32_t bits = __ballot_sync(0xffffffffu, reached);
+            if (lane == 0) hit[q0 >> 5] = bits;
+            if (reached) atomicAdd(tile_cnt + t, 1u);
+        }
+        __syncwarp();
+        // this lane's bits [ex, ex + area) of the concatenation
+        uint32_t m = 0u;
+        if (area) {
+            const int w0 = ex >> 5, b0 = ex & 31;
+            const uint32_t lo = hit[w0], hi = (b0 && w0 + 1 <= BIG_RECT) ? hit[w0 + 1] : 0u;
+            m = __funnelshift_r(lo, hi, b0);
+            if (area < 32) m &= (1u << area) - 1u;
+        }
+        if (k < n) reach[k] = m;
+        __syncwarp();                                     // hit[] is read before the next group writes it
+    }
+}
+
+__global__ void __launch_bounds__(TILES_BLOCK) k_tiles_emit(const uint2 *__restrict__ rect,
+                                                            const uint32_t *__restrict__ reach,
+                                                            const uint32_t *__restrict__ depth, const int *n_vis_p,
+                                                            int cap, int64_t kcap, const DevArgs *__restrict__ args,
+                                                            int view, const uint32_t *__restrict__ tile_off,
+                                                            uint32_t *tile_cur, uint32_t *bkey, uint32_t *bval)
 {
     const int n = min(*n_vis_p, cap);
     const DevCam &cam = args->cam[view];
@@ -139,62 +242,34 @@ __global__ void __launch_bounds__(256) k_tiles_small(const uint2 *__restrict__ r
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nwarps) {
         const int k = g * 32 + lane;
         uint2 rc = make_uint2(0u, 0u);
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        uint32_t dk = 0u;
-        int area = 0;
-        if (k < n && !fix_flag[k]) {
-            rc = rect[k];
-            area = (int)((rc.x >> 16) - (rc.x & 0xffff)) * (int)((rc.y >> 16) - (rc.y & 0xffff));
-            if (area > 0 && area <= BIG_RECT) {
-                r0 = rec0[k];
-                r1 = rec1[k];
-                if (EMIT) dk = depth[k];
-            } else {
-                area = 0;
+        uint32_t m = 0u, dk = 0u;
+        if (k < n) {
+            m = reach[k];
+            if (m) {
+                rc = rect[k];
+                dk = depth[k];
             }
         }
-        int incl = area;                                  // inclusive scan of the areas over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int ex = incl - area, total = __shfl_sync(0xffffffffu, incl, 31);
-        // j / width as (j * ceil(2^16 / width)) >> 16: exact for j * width < 2^16 (here j < 32, width <= 32)
-        const int wd = area ? (int)((rc.x >> 16) - (rc.x & 0xffff)) : 1;
+        int total;
+        const int ex = warp_excl_scan(__popc(m), lane, total);
+        const int wd = m ? (int)((rc.x >> 16) - (rc.x & 0xffff)) : 1;
         const uint32_t inv = (65536u + (uint32_t)wd - 1u) / (uint32_t)wd;
         for (int q0 = 0; q0 < total; q0 += 32) {
             const int q = q0 + lane;
-            int sl = 0;                                   // the last lane whose pairs start at or before q
-#pragma unroll
-            for (int st = 16; st; st >>= 1) {
-                const int c = sl + st;
-                if (__shfl_sync(0xffffffffu, ex, c) <= q) sl = c;
-            }
+            const int sl = owner_lane(ex, q);
             const uint32_t rcx = __shfl_sync(0xffffffffu, rc.x, sl), rcy = __shfl_sync(0xffffffffu, rc.y, sl);
-            const float4 a0 = make_float4(__shfl_sync(0xffffffffu, r0.x, sl), __shfl_sync(0xffffffffu, r0.y, sl),
-                                          __shfl_sync(0xffffffffu, r0.z, sl), __shfl_sync(0xffffffffu, r0.w, sl));
-            const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
-                                          __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
+            const uint32_t ms = __shfl_sync(0xffffffffu, m, sl), invs = __shfl_sync(0xffffffffu, inv, sl);
+            const uint32_t dks = __shfl_sync(0xffffffffu, dk, sl);
             const int exs = __shfl_sync(0xffffffffu, ex, sl);
-            const uint32_t invs = __shfl_sync(0xffffffffu, inv, sl);
-            const uint32_t dks = EMIT ? __shfl_sync(0xffffffffu, dk, sl) : 0u;
             if (q >= total) continue;
+            const int j = (int)__fns(ms, 0u, q - exs + 1);         // the (q - exs)-th set bit: a tile of the rectangle
             const int x0 = (int)(rcx & 0xffff), wdt = (int)(rcx >> 16) - x0, y0 = (int)(rcy & 0xffff);
-            const int j = q - exs, row = (int)(((uint32_t)j * invs) >> 16);
-            const int tx = x0 + (j - row * wdt), ty = y0 + row;
-            float X0, X1, Y0, Y1;
-            tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (!splat_reaches_box(a0, a1, X0, X1, Y0, Y1)) continue;
-            const int t = ty * tiles_x + tx;
-            if (!EMIT) {
-                atomicAdd(tile_cnt + t, 1u);
-            } else {
-                const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
-                if (p < kcap) {
-                    bkey[p] = dks;
-                    bval[p] = (uint32_t)(g * 32 + sl);
-                }
+            const int row = (int)(((uint32_t)j * invs) >> 16);
+            const int t = (y0 + row) * tiles_x + x0 + (j - row * wdt);
+            const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
+            if (p < kcap) {
+                bkey[p] = dks;
+                bval[p] = (uint32_t)(g * 32 + sl);
             }
         }
     }
@@ -426,16 +501,16 @@ void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBuf
     cudaMemsetAsync(rb.tile_cnt, 0, (size_t)(tiles + 1) * sizeof(uint32_t), s);
     cudaMemsetAsync(rb.tile_cur, 0, (size_t)tiles * sizeof(uint32_t), s);
     // the key count of every tile
-    const int gsm = w.grid((int64_t)(cap + 31) / 32 * 32, 256);
-    k_tiles_small<false><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
-                                             view, rb.tile_cnt, nullptr, nullptr, nullptr, nullptr);
+    const int gsm = w.grid((int64_t)(cap + 31) / 32 * 32, TILES_BLOCK);
+    k_tiles_count<<<gsm, TILES_BLOCK, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.fix_flag, n_vis, cap, args, view,
+                                              rb.tile_cnt, rb.reach);
     w.wait_side(s);                                       // the FP64 fix-ups (prepare_view) have landed
     k_big_counts<<<w.num_sms * 4, 256, 0, s>>>(rb.rec0, rb.rec1, rb.rect, rb.n_big, rb.big_idx, cap, args, view,
                                                rb.tile_cnt);
     // each tile's first key (and the key total), then the keys into their tiles' lists
     scan_counts(rb.tile_cnt, tiles + 1, rb.n_keys, (int)rb.kcap, w, s);
-    k_tiles_small<true><<<gsm, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.fix_flag, n_vis, cap, rb.kcap, args,
-                                            view, nullptr, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
+    k_tiles_emit<<<gsm, TILES_BLOCK, 0, s>>>(rb.rect, rb.reach, rb.depth, n_vis, cap, rb.kcap, args, view, rb.tile_cnt,
+                                             rb.tile_cur, rb.tk[0], rb.tv[0]);
     k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.n_big, rb.big_idx, cap, rb.kcap,
                                              args, view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
     // front-to-back order within each tile, and the tiles' ranges

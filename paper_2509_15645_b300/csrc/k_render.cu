@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
         rec2[k] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
         depth[k] = __float_as_uint(P.p[2]);
         // tiles reached: small rectangles are counted and emitted by
-        // k_tiles_small; FP64-flagged splats and large rectangles go to the big
+        // k_tiles_count / k_tiles_emit; FP64-flagged splats and large rectangles go to the big
         // list (k_big_counts, k_big_emit).  A splat that is not kept gets an
         // empty rectangle, so that every pass sees the same partition.
         if (!P.keep) P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
@@ -208,7 +208,7 @@ __device__ __forceinline__ float block_sum(float x, float *s_red)
 
 
 // Stage the tile's list entries [b, b + cnt) into shared memory (the lists
-// hold only splats that can reach the tile: k_tiles_small / k_big_emit).
+// hold only splats that can reach the tile: k_tiles_emit / k_big_emit).
 // WT: the staging belongs to one warp (warp-tile rasterizers), else to the block.
 template <bool COLOR, bool INDEX, bool WT = false>
 __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, const float4 *__restrict__ rec0,
