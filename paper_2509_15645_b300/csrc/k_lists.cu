@@ -20,8 +20,9 @@ namespace gs {
 // It only ever says "no" when no pixel can pass the per-pixel tests, so
 // dropping such splats leaves every pixel's result unchanged.
 // Every operation is an explicitly rounded intrinsic (no contraction into FMAs
-// that could differ between the kernels that inline it): the key counting and
-// the key emission, in different kernels, must take the same decisions.
+// that could differ between the kernels that inline it): the big list's key
+// counting and key emission, in different kernels, must take the same
+// decisions (the small rectangles' emission reads the count's masks).
 __device__ __forceinline__ float q_sigma(float A, float B, float C, float dx, float dy)
 {
     // 0.5 (A dx^2 + C dy^2) + B dx dy
@@ -29,7 +30,16 @@ __device__ __forceinline__ float q_sigma(float A, float B, float C, float dx, fl
     return __fadd_rn(__fmul_rn(0.5f, __fadd_rn(a, c)), __fmul_rn(__fmul_rn(B, dx), dy));
 }
 
-__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0, float X1, float Y0, float Y1)
+// The edge minimisers use the splat's ratios B / C and B / A (reach_ratios,
+// formed once per splat); a minimiser off by a rounding raises the edge's
+// minimum by a second-order amount, far inside the slack.
+__device__ __forceinline__ float2 reach_ratios(float4 r1)
+{
+    return make_float2(__fdiv_rn(r1.y, r1.z), __fdiv_rn(r1.y, r1.x));
+}
+
+__device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float2 bq, float X0, float X1, float Y0,
+                                                  float Y1)
 {
     const float margin = 1e-3f;
     const float ext = __fadd_rn(r0.z, margin);
@@ -48,14 +58,14 @@ __device__ __forceinline__ bool splat_reaches_box(float4 r0, float4 r1, float X0
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const float dx = dxs[k];
-            const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dx), C), dyl), dyh);
+            const float dy = fminf(fmaxf(-__fmul_rn(bq.x, dx), dyl), dyh);
             smin = fminf(smin, q_sigma(A, B, C, dx, dy));
         }
         const float dys[2] = {dyl, dyh};
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const float dy = dys[k];
-            const float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, dy), A), dxl), dxh);
+            const float dx = fminf(fmaxf(-__fmul_rn(bq.y, dy), dxl), dxh);
             smin = fminf(smin, q_sigma(A, B, C, dx, dy));
         }
         smin = fmaxf(smin, 0.f);
@@ -92,11 +102,12 @@ __global__ void k_big_counts(const float4 *__restrict__ rec0, const float4 *__re
         const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
         if (cnt_all <= 0) continue;
         const float4 r0 = rec0[k], r1 = rec1[k];
+        const float2 bq = reach_ratios(r1);
         for (int t = lane; t < cnt_all; t += 32) {
             const int tx = x0 + t % wdt, ty = y0 + t / wdt;
             float X0, X1, Y0, Y1;
             tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
+            if (splat_reaches_box(r0, r1, bq, X0, X1, Y0, Y1)) atomicAdd(tile_cnt + ty * cam.tiles_x + tx, 1u);
         }
     }
 }
@@ -183,6 +194,7 @@ __global__ void __launch_bounds__(TILES_BLOCK) k_tiles_count(const uint2 *__rest
                 area = 0;
             }
         }
+        const float2 bq = area ? reach_ratios(r1) : make_float2(0.f, 0.f);
         int total;
         const int ex = warp_excl_scan(area, lane, total);
         // j / width as (j * ceil(2^16 / width)) >> 16: exact for j * width < 2^16 (here j < 32, width <= 32)
@@ -196,6 +208,7 @@ __global__ void __launch_bounds__(TILES_BLOCK) k_tiles_count(const uint2 *__rest
                                           __shfl_sync(0xffffffffu, r0.z, sl), __shfl_sync(0xffffffffu, r0.w, sl));
             const float4 a1 = make_float4(__shfl_sync(0xffffffffu, r1.x, sl), __shfl_sync(0xffffffffu, r1.y, sl),
                                           __shfl_sync(0xffffffffu, r1.z, sl), 0.f);
+            const float2 bqs = make_float2(__shfl_sync(0xffffffffu, bq.x, sl), __shfl_sync(0xffffffffu, bq.y, sl));
             const int exs = __shfl_sync(0xffffffffu, ex, sl);
             const uint32_t invs = __shfl_sync(0xffffffffu, inv, sl);
             bool reached = false;
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(TILES_BLOCK) k_tiles_count(const uint2 *__rest
                 const int tx = x0 + (j - row * wdt), ty = y0 + row;
                 float X0, X1, Y0, Y1;
                 tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-                reached = splat_reaches_box(a0, a1, X0, X1, Y0, Y1);
+                reached = splat_reaches_box(a0, a1, bqs, X0, X1, Y0, Y1);
                 t = ty * tiles_x + tx;
             }
             const uint32_t bits = __ballot_sync(0xffffffffu, reached);
@@ -293,12 +306,13 @@ __global__ void k_big_emit(const uint2 *__restrict__ rect, const float4 *__restr
         const int wdt = x1 - x0, cnt_all = wdt * (y1 - y0);
         if (cnt_all <= 0) continue;
         const float4 r0 = rec0[k], r1 = rec1[k];
+        const float2 bq = reach_ratios(r1);
         const uint32_t dk = depth[k];
         for (int tt = lane; tt < cnt_all; tt += 32) {
             const int tx = x0 + tt % wdt, ty = y0 + tt / wdt;
             float X0, X1, Y0, Y1;
             tile_box(cam, tx, ty, X0, X1, Y0, Y1);
-            if (!splat_reaches_box(r0, r1, X0, X1, Y0, Y1)) continue;
+            if (!splat_reaches_box(r0, r1, bq, X0, X1, Y0, Y1)) continue;
             const int t = ty * cam.tiles_x + tx;
             const int64_t p = (int64_t)tile_off[t] + atomicAdd(tile_cur + t, 1u);
             if (p < kcap) {
