@@ -255,8 +255,10 @@ struct RenderBufs {
 };
 
 // The rasterizer's work over one or several views: (view, tile) items
-// [tile_ofs[v], tile_ofs[v + 1]) belong to view v; persistent blocks take items
-// from a work counter (zeroed before each launch) until all are done.
+// [tile_ofs[v], tile_ofs[v + 1]) are view v's tiles; persistent blocks take
+// items from a work counter (zeroed before each launch) until all are done,
+// each view's long lists first (so that none of them starts last and leaves
+// the GPU to one warp), then its other tiles in order.
 struct RasterJob {
     int n_views;
     int tile_ofs[MAX_VIEWS + 1];
@@ -269,11 +271,17 @@ struct RasterJob {
     float *g9[MAX_VIEWS];        // backward: per-splat sums out
     uint32_t cap[MAX_VIEWS];     // visible capacity (list entries index records below it)
     const float4 *lrec[MAX_VIEWS];   // records in list order (TMA-staged variant)
+    const int32_t *long_tiles[MAX_VIEWS];   // tiles whose lists exceed LONG_LIST keys (k_tile_sort)
+    const int *n_long[MAX_VIEWS];            // device: their number (null: none)
     int *status;                 // device status word (a TMA wait that gave up)
     uint32_t first_wait;         // polls of each warp's first TMA wait (CULL_WAIT_LIMIT unless a test lowers it)
     int cam0;                    // job view v is camera cam0 + v of the argument block
     int *work;
 };
+
+// Lists longer than this are sorted by a block (k_tile_sort_long) and handed
+// to the rasterizers before the others.
+constexpr int LONG_LIST = 256;
 
 constexpr int N_RASTER_VARIANTS = 10;
 // The variant whose lists are staged by TMA bulk copies from records in list order.

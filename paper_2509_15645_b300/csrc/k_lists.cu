@@ -409,7 +409,7 @@ __device__ __forceinline__ void warp_sort_list(const uint32_t *__restrict__ bkey
     }
 }
 
-constexpr int SORT_WARP_MAX = 256;       // lists up to this length: one warp, in registers
+constexpr int SORT_WARP_MAX = LONG_LIST; // lists up to this length: one warp, in registers
 constexpr int SORT_SMEM_MAX = 2048;      // longer ones up to this: one block, in shared memory (16 KB)
 
 // One warp per tile: the tile's range, and its list sorted into (tile, splat)

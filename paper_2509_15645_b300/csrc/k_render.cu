@@ -237,26 +237,45 @@ __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, c
 }
 
 // Next (view, tile) item of a persistent rasterizer block, or false when done.
-// WT: each warp takes its own items (warp-tile rasterizers).
+// WT: each warp takes its own items (warp-tile rasterizers).  View v has
+// n_long + tiles items: its long tiles (longest lists) first, then all its
+// tiles in order, where a long one is passed over (already taken).
 template <bool WT = false>
 __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &view, int &tile)
 {
-    int item;
-    if (WT) {
-        __syncwarp();                                  // the previous item's staged records are no longer read
-        if ((threadIdx.x & 31) == 0) item = atomicAdd(J.work, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-    } else {
-        __syncthreads();                               // the previous item's shared data is no longer read
-        if (threadIdx.x == 0) *s_item = atomicAdd(J.work, 1);
-        __syncthreads();
-        item = *s_item;
+    while (true) {
+        int item;
+        if (WT) {
+            __syncwarp();                              // the previous item's staged records are no longer read
+            if ((threadIdx.x & 31) == 0) item = atomicAdd(J.work, 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+        } else {
+            __syncthreads();                           // the previous item's shared data is no longer read
+            if (threadIdx.x == 0) *s_item = atomicAdd(J.work, 1);
+            __syncthreads();
+            item = *s_item;
+        }
+        int base = 0, nl = 0, idx = -1;
+        for (int v = 0; v < J.n_views; v++) {
+            const int tiles = J.tile_ofs[v + 1] - J.tile_ofs[v];
+            nl = J.n_long[v] ? min(*J.n_long[v], tiles) : 0;
+            if (item < base + nl + tiles) {
+                view = v;
+                idx = item - base;
+                break;
+            }
+            base += nl + tiles;
+        }
+        if (idx < 0) return false;
+        if (idx < nl) {
+            tile = J.long_tiles[view][idx];
+            return true;
+        }
+        tile = idx - nl;
+        if (nl == 0) return true;
+        const uint2 rg = J.ranges[view][tile];
+        if ((int)(rg.y - rg.x) <= LONG_LIST) return true;
     }
-    if (item >= J.tile_ofs[J.n_views]) return false;
-    view = 0;
-    while (item >= J.tile_ofs[view + 1]) view++;
-    tile = item - J.tile_ofs[view];
-    return true;
 }
 
 // NW > 0: warp tiles -- a tile is exactly 32 threads (tile pixels / PPT = 32)
@@ -1639,6 +1658,8 @@ static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
         J.g9[v] = rb.g9;
         J.cap[v] = (uint32_t)rb.cap;
         J.lrec[v] = rb.lrec;
+        J.long_tiles[v] = rb.long_tiles;
+        J.n_long[v] = rb.n_big + 1;
     }
     J.work = work;
     return J;
@@ -1693,7 +1714,10 @@ static RasterJob single_view_job(int view, RenderBufs &rb, int *work)
     RenderBufs *rbs[MAX_VIEWS] = {nullptr};
     for (int v = 0; v <= view; v++) rbs[v] = &rb;
     RasterJob J = make_job(view + 1, rbs, work);
-    for (int v = 0; v <= view; v++) J.tile_ofs[v + 1] = v < view ? 0 : rb.tiles;
+    for (int v = 0; v <= view; v++) {
+        J.tile_ofs[v + 1] = v < view ? 0 : rb.tiles;
+        if (v < view) J.n_long[v] = nullptr;
+    }
     return J;
 }
 
