@@ -231,6 +231,7 @@ struct RenderBufs {
     uint32_t *tile_cnt;      // [tiles + 1] keys per tile, then (scanned in place) each tile's first key
     uint32_t *tile_cur;      // [tiles] emission cursors
     int32_t *long_tiles;     // [tiles] tiles whose lists are sorted by k_tile_sort_long
+    int32_t *first_tiles;    // [tiles] tiles with more than FIRST_LIST keys (rasterized first)
     uint32_t *tk[2], *tv[2]; // keys: [0] per tile, unsorted (depth, splat); [1] sorted (tile, splat)
     int64_t kcap;            // key capacity
     uint2 *ranges;           // [tiles]
@@ -240,7 +241,7 @@ struct RenderBufs {
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes
     int32_t *fix_idx;        // [cap] their visible-set indices
     uint8_t *fix_flag;       // [cap] 1 for those, else 0
-    int *n_big;              // device [2]: [0] splats of the large-rectangle list, [1] long tiles
+    int *n_big;              // device [3]: [0] splats of the large-rectangle list, [1] long tiles, [2] first tiles
     float4 *lrec;            // [3 kcap] splat records in list order (rec0, rec1, rec2 with rec2.w = splat index
                              // bits), written for the TMA-staged rasterizer variant
     int32_t *big_idx;        // [cap] splats whose tiles a warp counts and emits (k_big_counts, k_big_emit)
@@ -257,8 +258,8 @@ struct RenderBufs {
 // The rasterizer's work over one or several views: (view, tile) items
 // [tile_ofs[v], tile_ofs[v + 1]) are view v's tiles; persistent blocks take
 // items from a work counter (zeroed before each launch) until all are done,
-// each view's long lists first (so that none of them starts last and leaves
-// the GPU to one warp), then its other tiles in order.
+// each view's long lists first (so that none of them starts late and leaves
+// the GPU to a few warps at the end), then its other tiles in order.
 struct RasterJob {
     int n_views;
     int tile_ofs[MAX_VIEWS + 1];
@@ -271,17 +272,20 @@ struct RasterJob {
     float *g9[MAX_VIEWS];        // backward: per-splat sums out
     uint32_t cap[MAX_VIEWS];     // visible capacity (list entries index records below it)
     const float4 *lrec[MAX_VIEWS];   // records in list order (TMA-staged variant)
-    const int32_t *long_tiles[MAX_VIEWS];   // tiles whose lists exceed LONG_LIST keys (k_tile_sort)
-    const int *n_long[MAX_VIEWS];            // device: their number (null: none)
+    const int32_t *first_tiles[MAX_VIEWS];  // tiles whose lists exceed FIRST_LIST keys (k_tile_sort)
+    const int *n_first[MAX_VIEWS];           // device: their number (null: none)
     int *status;                 // device status word (a TMA wait that gave up)
     uint32_t first_wait;         // polls of each warp's first TMA wait (CULL_WAIT_LIMIT unless a test lowers it)
     int cam0;                    // job view v is camera cam0 + v of the argument block
     int *work;
 };
 
-// Lists longer than this are sorted by a block (k_tile_sort_long) and handed
-// to the rasterizers before the others.
+// Lists longer than LONG_LIST are sorted by a block (k_tile_sort_long); lists
+// longer than FIRST_LIST (about three times the mean of a dense 8x4-tile
+// view; 64, 96, 160, 192 and 256 measured slower on the 10M aerial step) are
+// handed to the rasterizers before the others.
 constexpr int LONG_LIST = 256;
+constexpr int FIRST_LIST = 128;
 
 constexpr int N_RASTER_VARIANTS = 10;
 // The variant whose lists are staged by TMA bulk copies from records in list order.

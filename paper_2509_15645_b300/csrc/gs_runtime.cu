@@ -269,6 +269,7 @@ static void carve(gs_ctx *c, char *base)
         rb.tile_cnt = k.take<uint32_t>(tiles + 1);
         rb.tile_cur = k.take<uint32_t>(tiles);
         rb.long_tiles = k.take<int32_t>(tiles);
+        rb.first_tiles = k.take<int32_t>(tiles);
         for (int j = 0; j < 2; j++) {
             rb.tk[j] = k.take<uint32_t>(K);
             rb.tv[j] = k.take<uint32_t>(K);
@@ -281,7 +282,7 @@ static void carve(gs_ctx *c, char *base)
         rb.cfinal = k.take<float>(P);
         rb.fix_idx = k.take<int32_t>(V);
         rb.fix_flag = k.take<uint8_t>(V);
-        rb.n_big = k.take<int>(2);
+        rb.n_big = k.take<int>(3);
         rb.big_idx = k.take<int32_t>(V);
         rb.reach = k.take<uint32_t>(V);
         rb.lrec = g.list_records ? k.take<float4>(3 * (size_t)K) : nullptr;

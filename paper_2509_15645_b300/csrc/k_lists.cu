@@ -414,11 +414,13 @@ constexpr int SORT_SMEM_MAX = 2048;      // longer ones up to this: one block, i
 
 // One warp per tile: the tile's range, and its list sorted into (tile, splat)
 // order when it has at most SORT_WARP_MAX keys; longer lists are queued for
-// k_tile_sort_long.
+// k_tile_sort_long.  Lists of more than FIRST_LIST keys are also queued for
+// the rasterizers to take first.
 __global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ tile_off, int tiles, int64_t kcap,
                                                    const uint32_t *__restrict__ bkey,
                                                    const uint32_t *__restrict__ bval, uint32_t *skey, uint32_t *sval,
-                                                   uint2 *ranges, int *n_long, int32_t *long_tiles)
+                                                   uint2 *ranges, int *n_long, int32_t *long_tiles, int *n_first,
+                                                   int32_t *first_tiles)
 {
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -427,6 +429,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ 
         const int L = (int)(hi - lo);
         if (lane == 0) ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
         if (L <= 0) continue;
+        if (L > FIRST_LIST && lane == 0) first_tiles[atomicAdd(n_first, 1)] = t;
         if (L <= 32) warp_sort_list<32>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
         else if (L <= 64) warp_sort_list<64>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
         else if (L <= 128) warp_sort_list<128>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
@@ -530,7 +533,7 @@ void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBuf
     // front-to-back order within each tile, and the tiles' ranges
     k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
                                                                   rb.tk[1], rb.tv[1], rb.ranges, rb.n_big + 1,
-                                                                  rb.long_tiles);
+                                                                  rb.long_tiles, rb.n_big + 2, rb.first_tiles);
     static_assert(SORT_SMEM_MAX * sizeof(unsigned long long) <= 48 * 1024,
                   "the long-list buffer stays within the default dynamic shared-memory limit");
     k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(

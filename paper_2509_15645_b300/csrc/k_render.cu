@@ -238,8 +238,8 @@ __device__ __forceinline__ int stage_batch(const uint32_t *__restrict__ svals, c
 
 // Next (view, tile) item of a persistent rasterizer block, or false when done.
 // WT: each warp takes its own items (warp-tile rasterizers).  View v has
-// n_long + tiles items: its long tiles (longest lists) first, then all its
-// tiles in order, where a long one is passed over (already taken).
+// n_first + tiles items: its tiles of more than FIRST_LIST keys first, then
+// all its tiles in order, where one of those is passed over (already taken).
 template <bool WT = false>
 __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &view, int &tile)
 {
@@ -258,7 +258,7 @@ __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &
         int base = 0, nl = 0, idx = -1;
         for (int v = 0; v < J.n_views; v++) {
             const int tiles = J.tile_ofs[v + 1] - J.tile_ofs[v];
-            nl = J.n_long[v] ? min(*J.n_long[v], tiles) : 0;
+            nl = J.n_first[v] ? min(*J.n_first[v], tiles) : 0;
             if (item < base + nl + tiles) {
                 view = v;
                 idx = item - base;
@@ -268,13 +268,13 @@ __device__ __forceinline__ bool next_item(const RasterJob &J, int *s_item, int &
         }
         if (idx < 0) return false;
         if (idx < nl) {
-            tile = J.long_tiles[view][idx];
+            tile = J.first_tiles[view][idx];
             return true;
         }
         tile = idx - nl;
         if (nl == 0) return true;
         const uint2 rg = J.ranges[view][tile];
-        if ((int)(rg.y - rg.x) <= LONG_LIST) return true;
+        if ((int)(rg.y - rg.x) <= FIRST_LIST) return true;
     }
 }
 
@@ -1623,7 +1623,7 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     });
     const int tiles = cam.tiles_x * cam.tiles_y;
     cudaMemsetAsync(rb.n_fix, 0, sizeof(int), s);
-    cudaMemsetAsync(rb.n_big, 0, 2 * sizeof(int), s);
+    cudaMemsetAsync(rb.n_big, 0, 3 * sizeof(int), s);
     // gather and projection
     gp<<<w.grid(cap, PROJ_BLOCK, 12), PROJ_BLOCK, 0, s>>>(sc, ids, n_vis, cap, args, view, rb.compact, rb.rec0, rb.rec1,
                                                           rb.rec2, rb.depth, rb.rect, rb.n_fix, rb.fix_idx,
@@ -1658,8 +1658,8 @@ static RasterJob make_job(int n_views, RenderBufs *const *rbs, int *work)
         J.g9[v] = rb.g9;
         J.cap[v] = (uint32_t)rb.cap;
         J.lrec[v] = rb.lrec;
-        J.long_tiles[v] = rb.long_tiles;
-        J.n_long[v] = rb.n_big + 1;
+        J.first_tiles[v] = rb.first_tiles;
+        J.n_first[v] = rb.n_big + 2;
     }
     J.work = work;
     return J;
@@ -1716,7 +1716,7 @@ static RasterJob single_view_job(int view, RenderBufs &rb, int *work)
     RasterJob J = make_job(view + 1, rbs, work);
     for (int v = 0; v <= view; v++) {
         J.tile_ofs[v + 1] = v < view ? 0 : rb.tiles;
-        if (v < view) J.n_long[v] = nullptr;
+        if (v < view) J.n_first[v] = nullptr;
     }
     return J;
 }
