@@ -6,6 +6,8 @@
 //   scan_counts                          each tile's first key, the key total
 //   k_tiles_emit, k_big_emit             (depth, splat) keys into the tiles'
 //                                        lists through per-tile cursors
+//   k_find_long                          the long lists (and those the
+//                                        rasterizers take first)
 //   k_tile_sort(_long)                   each list sorted by depth (ties by
 //                                        Gaussian id) with bitonic networks
 #include "gs_kernels.cuh"
@@ -412,15 +414,27 @@ __device__ __forceinline__ void warp_sort_list(const uint32_t *__restrict__ bkey
 constexpr int SORT_WARP_MAX = LONG_LIST; // lists up to this length: one warp, in registers
 constexpr int SORT_SMEM_MAX = 2048;      // longer ones up to this: one block, in shared memory (16 KB)
 
+// The tiles whose lists have more than SORT_WARP_MAX keys (for
+// k_tile_sort_long) and more than FIRST_LIST keys (for the rasterizers to take
+// first), from the scanned list offsets.
+__global__ void k_find_long(const uint32_t *__restrict__ tile_off, int tiles, int64_t kcap, int *n_long,
+                            int32_t *long_tiles, int *n_first, int32_t *first_tiles)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+        const int64_t lo = min((int64_t)tile_off[t], kcap), hi = min((int64_t)tile_off[t + 1], kcap);
+        const int L = (int)(hi - lo);
+        if (L > SORT_WARP_MAX) long_tiles[atomicAdd(n_long, 1)] = t;
+        if (L > FIRST_LIST) first_tiles[atomicAdd(n_first, 1)] = t;
+    }
+}
+
 // One warp per tile: the tile's range, and its list sorted into (tile, splat)
-// order when it has at most SORT_WARP_MAX keys; longer lists are queued for
-// k_tile_sort_long.  Lists of more than FIRST_LIST keys are also queued for
-// the rasterizers to take first.
+// order when it has at most SORT_WARP_MAX keys (longer lists are
+// k_tile_sort_long's).
 __global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ tile_off, int tiles, int64_t kcap,
                                                    const uint32_t *__restrict__ bkey,
                                                    const uint32_t *__restrict__ bval, uint32_t *skey, uint32_t *sval,
-                                                   uint2 *ranges, int *n_long, int32_t *long_tiles, int *n_first,
-                                                   int32_t *first_tiles)
+                                                   uint2 *ranges)
 {
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -429,12 +443,10 @@ __global__ void __launch_bounds__(256) k_tile_sort(const uint32_t *__restrict__ 
         const int L = (int)(hi - lo);
         if (lane == 0) ranges[t] = make_uint2((uint32_t)lo, (uint32_t)hi);
         if (L <= 0) continue;
-        if (L > FIRST_LIST && lane == 0) first_tiles[atomicAdd(n_first, 1)] = t;
         if (L <= 32) warp_sort_list<32>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
         else if (L <= 64) warp_sort_list<64>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
         else if (L <= 128) warp_sort_list<128>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
         else if (L <= SORT_WARP_MAX) warp_sort_list<256>(bkey, bval, lo, L, (uint32_t)t, skey, sval, lane);
-        else if (lane == 0) long_tiles[atomicAdd(n_long, 1)] = t;
     }
 }
 
@@ -530,14 +542,19 @@ void build_tile_lists(const DevArgs *args, int view, const int *n_vis, RenderBuf
                                              rb.tile_cur, rb.tk[0], rb.tv[0]);
     k_big_emit<<<w.num_sms * 4, 256, 0, s>>>(rb.rect, rb.rec0, rb.rec1, rb.depth, rb.n_big, rb.big_idx, cap, rb.kcap,
                                              args, view, rb.tile_cnt, rb.tile_cur, rb.tk[0], rb.tv[0]);
-    // front-to-back order within each tile, and the tiles' ranges
-    k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
-                                                                  rb.tk[1], rb.tv[1], rb.ranges, rb.n_big + 1,
-                                                                  rb.long_tiles, rb.n_big + 2, rb.first_tiles);
+    // front-to-back order within each tile, and the tiles' ranges: the long
+    // lists (a block each) on the side stream beside the others (a warp each)
+    k_find_long<<<w.grid(tiles, 256, 2), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.n_big + 1, rb.long_tiles,
+                                                       rb.n_big + 2, rb.first_tiles);
     static_assert(SORT_SMEM_MAX * sizeof(unsigned long long) <= 48 * 1024,
                   "the long-list buffer stays within the default dynamic shared-memory limit");
-    k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), s>>>(
+    const cudaStream_t fs = w.fork(s);
+    k_tile_sort_long<<<w.num_sms * 6, 256, SORT_SMEM_MAX * sizeof(unsigned long long), fs>>>(
         rb.tile_cnt, rb.kcap, rb.tk[0], rb.tv[0], rb.tk[1], rb.tv[1], rb.n_big + 1, rb.long_tiles);
+    w.side_done(fs);
+    k_tile_sort<<<w.grid((int64_t)tiles * 32, 256), 256, 0, s>>>(rb.tile_cnt, tiles, rb.kcap, rb.tk[0], rb.tv[0],
+                                                                  rb.tk[1], rb.tv[1], rb.ranges);
+    w.wait_side(s);
 }
 
 }  // namespace gs
