@@ -19,7 +19,7 @@ struct ScanLen {
 constexpr uint32_t CULL_WAIT_LIMIT = 1u << 24;
 
 struct Work {
-    uint32_t *partials;   // >= 1024 scan partials
+    uint32_t *partials;   // >= 1024 scan partials (and 1024 more after them for work on the side stream)
     int *status;          // device status word
     int scan_grid;        // blocks of the scan kernels (<= 1024)
     int num_sms;
@@ -188,6 +188,14 @@ bool adam_pairs_ok(const SceneView &sc);
 void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
                        const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb,
                        int *n_upd, Work &w, cudaStream_t s);
+// The same in two parts: the pairs and their delays, which need only the
+// select (and can run beside the render), with the counters left as they are;
+// then the apply, which clears the members' counters.
+void launch_adam_pairs_prep(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb, int *n_upd,
+                            Work &w, cudaStream_t s);
+void launch_adam_pairs_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask,
+                             const uint32_t *vprefix, const float *grad, int64_t gcap, const PairBufs &pb, Work &w,
+                             cudaStream_t s);
 void launch_touch_from_masks(const uint32_t *vmask, const uint32_t *umask, int64_t n, int shift, uint8_t *touch,
                              Work &w, cudaStream_t s);
 void launch_uid_range(const int32_t *uids, const int *n_upd, int64_t id_lo, int64_t id_hi, int *range, cudaStream_t s);

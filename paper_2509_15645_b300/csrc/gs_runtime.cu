@@ -290,7 +290,7 @@ static void carve(gs_ctx *c, char *base)
         c->dimgs[v] = k.take<float>(P);
     }
     c->work = k.take<int>(4);
-    c->w.partials = k.take<uint32_t>(1024);
+    c->w.partials = k.take<uint32_t>(2048);
     c->gcap_u = g.max_views > 1 ? (N < (int64_t)g.max_views * V ? N : (int64_t)g.max_views * V) : V;
     c->grad_u = k.take<float>((size_t)D * c->gcap_u);
     if (g.max_views > 1) c->union_ids = k.take<int32_t>(c->gcap_u);
@@ -1442,6 +1442,22 @@ static void enqueue_step(gs_ctx *c, const SceneView &sv, const DevArgs &a, int n
 {
     const StepMasks M = enqueue_cull_phase(c, sv, a, n_views, loss, s,
                                            mode == GS_ADAM_DEFERRED ? a.lut.max_defer : -1);
+    if (mode == GS_ADAM_DEFERRED && M.selected && adam_pairs_ok(sv)) {
+        // the update set's pairs and delays need only the select: prepared on
+        // the side stream during the render (the gather still reads the
+        // counters; the apply clears the members')
+        const cudaStream_t fs = c->w.fork(s);
+        launch_adam_pairs_prep(sv, c->umask, c->uchunk, c->pairs, &c->cnt->n_upd, c->w, fs);
+        c->w.side_done(fs);
+        enqueue_render_phase(c, sv, a, n_views, M, loss, s);
+        DevArgs *args = c->args + SLOT_STEP;
+        c->w.mark(TP_ADAM0, s);
+        c->w.wait_side(s);
+        launch_adam_pairs_apply(sv, args, M.gmask, M.gprefix, c->grad_u, M.gcap, c->pairs, c->w, s);
+        c->w.mark(TP_ADAM1, s);
+        c->w.mark(TP_STEP1, s);
+        return;
+    }
     enqueue_render_phase(c, sv, a, n_views, M, loss, s);
     enqueue_adam_phase(c, sv, mode, M, s);
 }

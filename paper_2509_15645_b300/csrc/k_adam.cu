@@ -476,9 +476,10 @@ __global__ void k_pair_mask(const uint32_t *__restrict__ umask, int64_t nwords_u
 }
 
 // Per active pair: both delays and the member bits (d0 | d1 << 8 | members << 16);
-// the members' counters are cleared (the compaction's job in the member path).
+// with `clear`, the members' counters are cleared (the compaction's job in the
+// member path), else the apply clears them.
 __global__ void k_pair_prep(const int32_t *__restrict__ pids, const int *n_pairs_p, const uint32_t *__restrict__ umask,
-                            uint8_t *__restrict__ counter, int64_t n, uint32_t *__restrict__ pinfo)
+                            uint8_t *__restrict__ counter, int64_t n, uint32_t *__restrict__ pinfo, int clear)
 {
     const int np = *n_pairs_p;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
@@ -486,8 +487,8 @@ __global__ void k_pair_prep(const int32_t *__restrict__ pids, const int *n_pairs
         const bool has1 = i0 + 1 < n;
         uint32_t bits = (umask[i0 >> 5] >> (i0 & 31)) & (has1 ? 3u : 1u);
         const uint32_t c0 = counter[i0], c1 = has1 ? counter[i0 + 1] : 0u;
-        if (bits & 1u) counter[i0] = 0;
-        if (bits & 2u) counter[i0 + 1] = 0;
+        if (clear && (bits & 1u)) counter[i0] = 0;
+        if (clear && (bits & 2u)) counter[i0 + 1] = 0;
         pinfo[j] = c0 | (c1 << 8) | (bits << 16);
     }
 }
@@ -720,7 +721,8 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
                                                                  const uint32_t *__restrict__ vmask,
                                                                  const uint32_t *__restrict__ vprefix,
                                                                  const float *__restrict__ grad, int64_t gcap,
-                                                                 const DevArgs *__restrict__ args)
+                                                                 const DevArgs *__restrict__ args,
+                                                                 uint8_t *__restrict__ counter_clear)
 {
     __shared__ SLut L;
     load_slut(L, args->lut);
@@ -736,6 +738,9 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
 #pragma unroll
     for (int q = 0; q < PR; q++) key[q] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + q)) : 0u;
     PairRows cur, nxt;
+    // the first plane group clears the members' counters (when the pair
+    // preparation left them)
+    uint8_t *const clr = blockIdx.y == 0 ? counter_clear : nullptr;
     if (geo) {
         pair_fetch<T, true, OPT>(cur, j, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
         while (true) {
@@ -743,6 +748,10 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
             const bool more = jn < n_pairs;
             if (more) pair_fetch<T, true, OPT>(nxt, jn, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
             pair_step_any<T, true, OPT>(cur, P, r0, rend, L, key);
+            if (clr) {
+                if (cur.info & (1u << 16)) clr[cur.i0] = 0;
+                if (cur.info & (2u << 16)) clr[cur.i0 + 1] = 0;
+            }
             if (!more) break;
             cur = nxt;
             j = jn;
@@ -769,16 +778,22 @@ bool adam_pairs_ok(const SceneView &sc)
            (!sc.rdir || al(sc.rdir)) && sc.counter;
 }
 
-void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
-                       const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb,
-                       int *n_upd, Work &w, cudaStream_t s)
+static void pairs_prep(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb, int *n_upd,
+                       bool clear, Work &w, cudaStream_t s)
 {
     const int64_t nw_u = (sc.n + 31) / 32, npairs = (sc.n + 1) / 2, nw_p = (npairs + 31) / 32;
     // members of the update set (reported), from the per-chunk counts of the select
     scan_counts(uchunk, (sc.n + CHUNK - 1) / CHUNK, n_upd, 0, w, s);
     k_pair_mask<<<w.grid(nw_p, 256, 4), 256, 0, s>>>(umask, nw_u, pb.pmask, nw_p);
     compact_mask(pb.pmask, npairs, pb.pchunk, false, pb.pids, nullptr, (int)npairs, pb.n_pairs, w, s);
-    k_pair_prep<<<w.grid(npairs, 256, 4), 256, 0, s>>>(pb.pids, pb.n_pairs, umask, sc.counter, sc.n, pb.pinfo);
+    k_pair_prep<<<w.grid(npairs, 256, 4), 256, 0, s>>>(pb.pids, pb.n_pairs, umask, sc.counter, sc.n, pb.pinfo,
+                                                       clear ? 1 : 0);
+}
+
+static void pairs_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                        const float *grad, int64_t gcap, const PairBufs &pb, uint8_t *counter_clear, Work &w,
+                        cudaStream_t s)
+{
     constexpr int GEO_GROUPS = (N_GEO + PR - 1) / PR;
     const int groups = GEO_GROUPS + (sc.D - N_GEO + PR - 1) / PR;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
@@ -787,12 +802,38 @@ void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t 
         constexpr int O = decltype(o)::value;
         if (sc.prec == GS_FP32)
             k_adam_apply_pairs<float, O><<<grid, ADAM_BLOCK, 0, s>>>(planes_of<float>(sc), sc.D, pb.pids, pb.pinfo,
-                                                                    pb.n_pairs, vmask, vprefix, grad, gcap, args);
+                                                                    pb.n_pairs, vmask, vprefix, grad, gcap, args,
+                                                                    counter_clear);
         else
             k_adam_apply_pairs<__nv_bfloat16, O><<<grid, ADAM_BLOCK, 0, s>>>(
-                planes_of<__nv_bfloat16>(sc), sc.D, pb.pids, pb.pinfo, pb.n_pairs, vmask, vprefix, grad, gcap, args);
+                planes_of<__nv_bfloat16>(sc), sc.D, pb.pids, pb.pinfo, pb.n_pairs, vmask, vprefix, grad, gcap, args,
+                counter_clear);
     });
     w.mark(TP_APPLY1, s);
+}
+
+void launch_adam_pairs(const SceneView &sc, const DevArgs *args, const uint32_t *vmask, const uint32_t *vprefix,
+                       const float *grad, int64_t gcap, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb,
+                       int *n_upd, Work &w, cudaStream_t s)
+{
+    pairs_prep(sc, umask, uchunk, pb, n_upd, true, w, s);
+    pairs_apply(sc, args, vmask, vprefix, grad, gcap, pb, nullptr, w, s);
+}
+
+void launch_adam_pairs_prep(const SceneView &sc, uint32_t *umask, uint32_t *uchunk, const PairBufs &pb, int *n_upd,
+                            Work &w, cudaStream_t s)
+{
+    // scans on their own partials: this may run beside the main stream's scans
+    Work ws = w;
+    ws.partials = w.partials + 1024;
+    pairs_prep(sc, umask, uchunk, pb, n_upd, false, ws, s);
+}
+
+void launch_adam_pairs_apply(const SceneView &sc, const DevArgs *args, const uint32_t *vmask,
+                             const uint32_t *vprefix, const float *grad, int64_t gcap, const PairBufs &pb, Work &w,
+                             cudaStream_t s)
+{
+    pairs_apply(sc, args, vmask, vprefix, grad, gcap, pb, sc.counter, w, s);
 }
 
 // [first, end) of the update-set members with ids in [id_lo, id_hi): the ids
