@@ -314,8 +314,10 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 // The stages of render_forward / render_backward, for steps over several views:
 // per view prepare_view (gather, projection, keys, sorts); one forward and one
 // backward rasterizer launch over all views; per view project_backward.
+// zero_g9: also clear the view's per-splat gradient sums (on the side stream,
+// beside the list building), for a raster_backward told g9_zeroed.
 void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
-                  RenderBufs &rb, const DevCam &cam_host, Work &w, cudaStream_t s);
+                  RenderBufs &rb, const DevCam &cam_host, Work &w, cudaStream_t s, bool zero_g9 = false);
 // cam0: the job's views are cameras cam0.. of the argument block (a round of
 // a step's views); rbs, images, dimages and n_vis are per job view.
 void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams, float *const *images,
@@ -323,7 +325,7 @@ void raster_forward(const DevArgs *args, int n_views, RenderBufs *const *rbs, co
                     int cam0 = 0);
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
-                     unsigned long long *stats = nullptr, int cam0 = 0);
+                     unsigned long long *stats = nullptr, int cam0 = 0, bool g9_zeroed = false);
 // Visibility masks of the views rendered before this one in a step over
 // several views.  A Gaussian that none of them sees takes its gradient row by
 // plain stores (so the union layout needs no zeroing first); the others add.

@@ -1391,7 +1391,8 @@ static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &
         }
         if (v0 == 0) c->w.mark(TP_FWD0, s);
         for (int j = 0; j < k; j++)
-            prepare_view(sv, args, v0 + j, c->vids[v0 + j], c->nvis_view + v0 + j, c->rbs[j], a.cam[v0 + j], c->w, s);
+            prepare_view(sv, args, v0 + j, c->vids[v0 + j], c->nvis_view + v0 + j, c->rbs[j], a.cam[v0 + j], c->w, s,
+                         true);
         // the step needs only the final colours the backward reads (no separate image copy)
         float *fin[MAX_VIEWS];
         for (int j = 0; j < k; j++) fin[j] = c->rbs[j].cfinal;
@@ -1400,7 +1401,7 @@ static void enqueue_render_phase(gs_ctx *c, const SceneView &sv, const DevArgs &
             c->w.mark(TP_FWD1, s);
             c->w.mark(TP_BWD0, s);
         }
-        raster_backward(args, k, rbs, a.cam + v0, dimg_c, nv, c->work + 1, c->w, s, nullptr, v0);
+        raster_backward(args, k, rbs, a.cam + v0, dimg_c, nv, c->work + 1, c->w, s, nullptr, v0, true);
         for (int j = 0; j < k; j++) {
             PrevMasks prev{};
             for (int p = 0; p < v0 + j; p++) prev.m[prev.n++] = c->vmask[p];

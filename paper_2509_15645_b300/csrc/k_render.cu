@@ -1608,7 +1608,7 @@ void launch_loss_l1(const float *image, const float *target, int64_t count, floa
 }
 
 void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int32_t *ids, const int *n_vis,
-                  RenderBufs &rb, const DevCam &cam, Work &w, cudaStream_t s)
+                  RenderBufs &rb, const DevCam &cam, Work &w, cudaStream_t s, bool zero_g9)
 {
     const int cap = (int)rb.cap;
     decltype(&k_gather_project<0, float, GS_OPT_ADAM>) gp = nullptr;
@@ -1633,6 +1633,7 @@ void prepare_view(const SceneView &sc, const DevArgs *args, int view, const int3
     const cudaStream_t fs = w.fork(s);
     k_fix_project<<<w.num_sms, PROJ_BLOCK, 0, fs>>>(rb.compact, cap, rb.n_fix, rb.fix_idx, args, view, rb.rec0, rb.rec1,
                                                      rb.rect, rb.n_big, rb.big_idx);
+    if (zero_g9) launch_zero_rows(rb.g9, G9_STRIDE, cap, n_vis, cap, w, fs, true);
     w.side_done(fs);
     build_tile_lists(args, view, n_vis, rb, tiles, w, s);
     rb.sorted_keys = rb.tk[1];
@@ -1742,11 +1743,11 @@ void render_forward(const SceneView &sc, const DevArgs *args, int view, const in
 
 void raster_backward(const DevArgs *args, int n_views, RenderBufs *const *rbs, const DevCam *cams,
                      const float *const *dimages, const int *const *n_vis, int *work, Work &w, cudaStream_t s,
-                     unsigned long long *stats, int cam0)
+                     unsigned long long *stats, int cam0, bool g9_zeroed)
 {
     if (rbs[0]->variant_bwd == RASTER_TMA_VARIANT && rbs[0]->variant != RASTER_TMA_VARIANT)
         for (int v = 0; v < n_views; v++) list_records(*rbs[v], w, s);
-    for (int v = 0; v < n_views; v++) {
+    for (int v = 0; v < n_views && !g9_zeroed; v++) {
         const int cap = (int)rbs[v]->cap;
         launch_zero_rows(rbs[v]->g9, G9_STRIDE, cap, n_vis[v], cap, w, s, true);
     }
