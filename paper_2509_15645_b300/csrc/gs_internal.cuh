@@ -648,6 +648,8 @@ __device__ __forceinline__ float splat_alpha(float4 r0, float4 r1, float px, flo
 // The same test and alpha without branches: identical operations, so identical
 // results and decisions; the caller masks with the returned value (0 = no
 // contribution).  Used where several pixels per thread are evaluated together.
+// The caller has already taken the x half of the square test (|dx| <= r, a
+// test shared by a thread's pixel column); only the y half is taken here.
 __device__ __forceinline__ float splat_alpha_nb(float4 r0, float4 r1, float dx, float py, float &dy, float &G,
                                                bool &clamped)
 {
@@ -658,7 +660,7 @@ __device__ __forceinline__ float splat_alpha_nb(float4 r0, float4 r1, float dx, 
     float raw = __fmul_rn(r0.w, G);
     clamped = raw > ALPHA_MAX;
     float alpha = fminf(ALPHA_MAX, raw);
-    bool ok = (fabsf(dx) <= r0.z) && (fabsf(dy) <= r0.z) && (sig >= 0.f) && (alpha >= ALPHA_MIN);
+    bool ok = (fabsf(dy) <= r0.z) && (sig >= 0.f) && (alpha >= ALPHA_MIN);
     return ok ? alpha : 0.f;
 }
 

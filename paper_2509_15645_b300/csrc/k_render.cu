@@ -438,17 +438,15 @@ __device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane)
 
 // emit_splat for sums that are set only in contributing lanes: the other
 // lanes' values are replaced by zeros where the warp sums (no zeroing per entry).
-__device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC,
-                                               bool contrib, float v[9], int lane)
+__device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t k, bool contrib, float v[9], int lane)
 {
     const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
     if (cmask == 0u) return;
     float *row = g9 + (int64_t)k * G9_STRIDE;
     if (__popc(cmask) <= DIRECT_LANES) {
         if (contrib) {
-            atomicAdd(reinterpret_cast<float4 *>(row),
-                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
-            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+            atomicAdd(reinterpret_cast<float4 *>(row), make_float4(v[0], v[1], v[2], v[3]));
+            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(v[4], v[5], v[6], v[7]));
             atomicAdd(row + 8, v[8]);
         }
         return;
@@ -464,10 +462,10 @@ __device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t 
     const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
     const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
     if (lane == 0) {
-        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
+        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(sum, q1, q2, q3));
         atomicAdd(row + 8, s8);
     } else if (lane == 16) {
-        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(sum, q1, q2, q3));
     }
 }
 
@@ -479,7 +477,9 @@ __device__ __forceinline__ void emit_splat_sel(float *__restrict__ g9, uint32_t 
 // T_i R_i = (F - A_i) / (1 - a_i), so
 //   dL/da_i = g . (T_i c_i - (F - A_i) / (1 - a_i)),   dL/dc_i = g a_i T_i,
 // and nothing is replayed or divided back out of T.  A warp sums its lanes'
-// contributions to each splat and issues the atomic adds into g9.
+// contributions to each splat and issues the atomic adds into g9; the sums
+// are taken before the conic and the halves of sigma's square terms are
+// applied (once per splat, in the projection backward).
 // STATS: also count the (pixel, splat) pairs that pass the square test and the
 // pairs that contribute (stats[0], stats[1]).
 template <int PPT, int BATCH, bool STATS = false, int NW = 0>
@@ -552,8 +552,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                 // contributes (no zeroing per entry; emit_splat_sel masks the rest)
                 float v[9];
                 bool contrib = false;
+                const float4 r1 = s1[e];
                 if (live && fabsf(dx) <= r0.z) {
-                    const float4 r1 = s1[e];
                     float dy, G;
                     bool cl;
                     const float a = splat_alpha_nb(r0, r1, dx, (float)y0 + 0.5f, dy, G, cl);
@@ -586,9 +586,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                         }
                     }
                 }
-                const float4 cn = s1[e];
                 if (STATS && WT && __ballot_sync(0xffffffffu, contrib) == 0u && lane == 0) n_empty++;
-                emit_splat_sel(g9, s_k[e], cn.x, cn.y, cn.z, contrib, v, lane);
+                emit_splat_sel(g9, s_k[e], contrib, v, lane);
                 continue;
             }
             // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
@@ -640,10 +639,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                 // few contributing lanes: each adds its own sums (no warp reduction)
                 if (contrib) {
                     float *row = g9 + (int64_t)s_k[e] * G9_STRIDE;
-                    const float4 cn = s1[e];
-                    atomicAdd(reinterpret_cast<float4 *>(row),
-                              make_float4(cn.x * v[0] + cn.y * v[1], cn.y * v[0] + cn.z * v[1], 0.5f * v[2], v[3]));
-                    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+                    atomicAdd(reinterpret_cast<float4 *>(row), make_float4(v[0], v[1], v[2], v[3]));
+                    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(v[4], v[5], v[6], v[7]));
                     if (v[8] != 0.f) atomicAdd(row + 8, v[8]);
                 }
             } else if (cmask != 0u) {
@@ -658,13 +655,10 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                 const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
                 float *row = g9 + (int64_t)k * G9_STRIDE;
                 if (lane == 0) {
-                    // d/d mean = conic (sum ds d), d/d conic = (sum ds dx^2 / 2, sum ds dx dy, .)
-                    const float4 cn = s1[e];
-                    atomicAdd(reinterpret_cast<float4 *>(row),
-                              make_float4(cn.x * sum + cn.y * q1, cn.y * sum + cn.z * q1, 0.5f * q2, q3));
+                    atomicAdd(reinterpret_cast<float4 *>(row), make_float4(sum, q1, q2, q3));
                     if (s8 != 0.f) atomicAdd(row + 8, s8);
                 } else if (lane == 16) {
-                    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+                    atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(sum, q1, q2, q3));
                 }
             }
         }
@@ -862,17 +856,15 @@ __global__ void __launch_bounds__(32 * NW, 4) k_raster_fwd_pairs(const RasterJob
 
 // A warp's sums for one splat (v as in k_raster_bwd) into its g9 record:
 // per-lane atomics when few lanes contribute, else a warp reduction.
-__device__ __forceinline__ void emit_splat(float *__restrict__ g9, uint32_t k, float cA, float cB, float cC, bool contrib,
-                                           float v[9], int lane)
+__device__ __forceinline__ void emit_splat(float *__restrict__ g9, uint32_t k, bool contrib, float v[9], int lane)
 {
     const uint32_t cmask = __ballot_sync(0xffffffffu, contrib);
     if (cmask == 0u) return;
     float *row = g9 + (int64_t)k * G9_STRIDE;
     if (__popc(cmask) <= DIRECT_LANES) {
         if (contrib) {
-            atomicAdd(reinterpret_cast<float4 *>(row),
-                      make_float4(cA * v[0] + cB * v[1], cB * v[0] + cC * v[1], 0.5f * v[2], v[3]));
-            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * v[4], v[5], v[6], v[7]));
+            atomicAdd(reinterpret_cast<float4 *>(row), make_float4(v[0], v[1], v[2], v[3]));
+            atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(v[4], v[5], v[6], v[7]));
             if (v[8] != 0.f) atomicAdd(row + 8, v[8]);
         }
         return;
@@ -885,10 +877,10 @@ __device__ __forceinline__ void emit_splat(float *__restrict__ g9, uint32_t k, f
     const float q2 = __shfl_down_sync(0xffffffffu, sum, 8);
     const float q3 = __shfl_down_sync(0xffffffffu, sum, 12);
     if (lane == 0) {
-        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(cA * sum + cB * q1, cB * sum + cC * q1, 0.5f * q2, q3));
+        atomicAdd(reinterpret_cast<float4 *>(row), make_float4(sum, q1, q2, q3));
         if (s8 != 0.f) atomicAdd(row + 8, s8);
     } else if (lane == 16) {
-        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(0.5f * sum, q1, q2, q3));
+        atomicAdd(reinterpret_cast<float4 *>(row + 4), make_float4(sum, q1, q2, q3));
     }
 }
 
@@ -1007,8 +999,8 @@ __global__ void __launch_bounds__(32 * NW, 4) k_raster_bwd_pairs(const RasterJob
                         v0[8] = lo2(v8); v1[8] = hi2(v8);
                     }
                 }
-                emit_splat(g9, s_k[2 * p], ab.x, ab.z, cc.x, c0, v0, lane);
-                emit_splat(g9, s_k[2 * p + 1], ab.y, ab.w, cc.y, c1, v1, lane);
+                emit_splat(g9, s_k[2 * p], c0, v0, lane);
+                emit_splat(g9, s_k[2 * p + 1], c1, v1, lane);
             }
         }
     }
@@ -1271,7 +1263,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, c
                         }
                     }
                 }
-                emit_splat_sel(g9, __float_as_uint(B[3 * e + 2].w), r1.x, r1.y, r1.z, contrib, v, lane);
+                emit_splat_sel(g9, __float_as_uint(B[3 * e + 2].w), contrib, v, lane);
             }
             __syncwarp();
         }
@@ -1404,6 +1396,16 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         }
         Proj P;
         project_gaussian<FIX>(g, cam, P);   // as in the forward (FIX: the FP64 chain)
+        if (P.keep) {
+            // the rasterizer's sums (ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2) over the splat's pixels, with
+            // ds = -alpha dL/dalpha: the mean gradient is the conic times the first two, and sigma takes half
+            // of A dx^2 and of C dy^2
+            const float s0 = gs[0], s1 = gs[1];
+            gs[0] = P.conA * s0 + P.conB * s1;
+            gs[1] = P.conB * s0 + P.conC * s1;
+            gs[2] = 0.5f * gs[2];
+            gs[4] = 0.5f * gs[4];
+        }
         float out[N_GEO];
 #pragma unroll
         for (int r = 0; r < N_GEO; r++) out[r] = 0.f;
