@@ -244,7 +244,7 @@ struct RenderBufs {
     int64_t kcap;            // key capacity
     uint2 *ranges;           // [tiles]
     float *g9;               // [cap][G9_STRIDE] per splat, summed over its pixels (ds = -alpha dL/dalpha):
-                             // ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2, G dL/dalpha, dL/d rgb (9 used)
+                             // ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2, ds, dL/d rgb (9 used)
     int *n_keys;             // device
     float *cfinal;           // [3][H][W] final colour of the last forward render (for the backward)
     int *n_fix;              // device: Gaussians handed to the FP64 fix-up passes

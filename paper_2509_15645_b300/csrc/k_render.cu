@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                             v[7] = __fmul_rn(g1[0], aT);
                             v[8] = __fmul_rn(g2[0], aT);
                             const float ds = cl ? 0.f : __fmul_rn(-a, dLda);    // the 0.999 clamp: no derivative
-                            v[5] = cl ? 0.f : __fmul_rn(G, dLda);
+                            v[5] = ds;
                             const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
                             v[0] = sdx;
                             v[1] = sdy;
@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                 continue;
             }
             // sums over the warp's pixels: ds dx, ds dy, ds dx^2, ds dx dy, ds dy^2,
-            // G dL/da, g_r aT, g_g aT, g_b aT (ds = -a dL/da); the mean and conic
-            // gradients are formed from them once per (warp, splat)
+            // ds, g_r aT, g_g aT, g_b aT (ds = -a dL/da); the mean, conic and
+            // opacity gradients are formed from them once per splat (k_project_bwd)
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
             if (live && fabsf(dx) <= r0.z) {
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(const RasterJob J, const Dev
                     v[8] = __fmaf_rn(g2[j], aT, v[8]);
                     if (!cl) {                                   // the 0.999 clamp has no derivative
                         const float ds = __fmul_rn(-a, dLda);
-                        v[5] = __fmaf_rn(G, dLda, v[5]);
+                        v[5] = __fadd_rn(v[5], ds);
                         const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
                         v[0] = __fadd_rn(v[0], sdx);
                         v[1] = __fadd_rn(v[1], sdy);
@@ -984,7 +984,6 @@ __global__ void __launch_bounds__(32 * NW, 4) k_raster_bwd_pairs(const RasterJob
                         // the 0.999 clamp has no derivative; entries that do not contribute add nothing
                         const f2 dlm2 = pk2(c0 && !A.cl0 ? lo2(dl2) : 0.f, c1 && !A.cl1 ? hi2(dl2) : 0.f);
                         const f2 ds2 = mul2(pk2(-a0, -a1), dlm2);
-                        const f2 v5 = mul2(pk2(A.G0, A.G1), dlm2);
                         const f2 sdx2 = mul2(ds2, A.dx2), sdy2 = mul2(ds2, A.dy2);
                         const f2 v2 = mul2(sdx2, A.dx2), v3 = mul2(sdx2, A.dy2), v4 = mul2(sdy2, A.dy2);
                         const f2 v6 = mul2(g0_2, aT2), v7 = mul2(g1_2, aT2), v8 = mul2(g2_2, aT2);
@@ -993,7 +992,7 @@ __global__ void __launch_bounds__(32 * NW, 4) k_raster_bwd_pairs(const RasterJob
                         v0[2] = lo2(v2); v1[2] = hi2(v2);
                         v0[3] = lo2(v3); v1[3] = hi2(v3);
                         v0[4] = lo2(v4); v1[4] = hi2(v4);
-                        v0[5] = lo2(v5); v1[5] = hi2(v5);
+                        v0[5] = lo2(ds2); v1[5] = hi2(ds2);
                         v0[6] = lo2(v6); v1[6] = hi2(v6);
                         v0[7] = lo2(v7); v1[7] = hi2(v7);
                         v0[8] = lo2(v8); v1[8] = hi2(v8);
@@ -1252,7 +1251,7 @@ __global__ void __launch_bounds__(32 * NW) k_raster_bwd_tma(const RasterJob J, c
                             v[8] = __fmul_rn(g2, aT);
                             // the 0.999 clamp has no derivative: ds = 0 there
                             const float ds = cl ? 0.f : __fmul_rn(-a, dLda);
-                            v[5] = cl ? 0.f : __fmul_rn(G, dLda);
+                            v[5] = ds;
                             const float sdx = __fmul_rn(ds, dx), sdy = __fmul_rn(ds, dy);
                             v[0] = sdx;
                             v[1] = sdy;
@@ -1445,7 +1444,9 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         if (ok) {
             // ---- opacity logit
             float o = 1.f / (1.f + expf(-g[ROW_OPAC]));
-            out[ROW_OPAC] = gs[5] * o * (1.f - o);
+            // dL/do = sum G dL/dalpha = -(sum ds) / o (alpha = o G where it is not clamped; clamped pixels add
+            // to neither sum), times do/dlogit = o (1 - o)
+            out[ROW_OPAC] = -gs[5] * (1.f - o);
             float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
             const float *R = cam.R;
             float pxc = P.p[0], pyc = P.p[1], pz = P.p[2];
