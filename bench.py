@@ -456,9 +456,9 @@ def run_ours(args):
             variant_ms = {"fwd_stage": ms_f, "bwd_stage": ms_b}
         elif tier == gs.GS_TIER_DEVICE:
             variant, variant_ms = None, {}                       # pinned below
-        else:   # the autotuner renders through the resident path: the resident workload's choice
-            variant, variant_ms = (8, 8), {}
-            ctx.set_raster_variant(8, 8)
+        else:   # the autotuner renders through the resident path: the warp tiles it picks on the resident 10M step
+            variant, variant_ms = (7, 7), {}
+            ctx.set_raster_variant(7, 7)
         if args.raster_variant is not None:
             fb = [int(x) for x in str(args.raster_variant).split(",")]
             variant = (fb[0], fb[-1])
