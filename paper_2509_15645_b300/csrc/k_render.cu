@@ -302,9 +302,7 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
     const uint2 *__restrict__ ranges = J.ranges[view];
     const uint32_t *__restrict__ svals = J.svals[view];
     const float4 *__restrict__ rec0 = J.rec0[view], *__restrict__ rec1 = J.rec1[view], *__restrict__ rec2 = J.rec2[view];
-    float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
     const DevCam &cam = args->cam[J.cam0 + view];
-    const float *target = use_target ? args->target[J.cam0 + view] : nullptr;
     const int W = cam.width, H = cam.height, tw = cam.tile_w, th = cam.tile_h, tiles_x = cam.tiles_x;
     const int tx0 = (tile % tiles_x) * tw, ty0 = (tile / tiles_x) * th;
     const int x = tx0 + tl % tw;
@@ -364,6 +362,8 @@ __global__ void __launch_bounds__(256, NW ? 5 : 1) k_raster_fwd(const RasterJob 
     }
     const int64_t HW = (int64_t)W * H;
     const float inv = cam.loss_inv;
+    float *__restrict__ image = J.image[view], *__restrict__ cfinal = J.cfinal[view], *__restrict__ dimage = J.dimage[view];
+    const float *target = use_target ? args->target[J.cam0 + view] : nullptr;
     float part = 0.f;
 #pragma unroll
     for (int j = 0; j < PPT; j++) {
