@@ -141,12 +141,14 @@ struct CullOut {
     int *n_cand;          // optional: number of Gaussians whose rotation planes were read
 };
 
-template <int OPT>
+// ONE: a single view (nv == 1), compiled with the view loop removed.
+template <int OPT, bool ONE>
 __global__ void __launch_bounds__(CT, 4) k_cull_tma(const float *__restrict__ geo, const float *__restrict__ rdir,
                                                    const uint8_t *__restrict__ counter, int64_t pitch, int64_t n,
-                                                   const DevArgs *__restrict__ args, int view0, int nv,
+                                                   const DevArgs *__restrict__ args, int view0, int nv_arg,
                                                    const CullOut out, int *status, uint32_t first_wait)
 {
+    const int nv = ONE ? 1 : nv_arg;
     extern __shared__ __align__(128) unsigned char smem[];
     CullStage *st = reinterpret_cast<CullStage *>(smem);
     __shared__ __align__(8) uint64_t bar[CSTAGES];
@@ -360,15 +362,16 @@ static void launch_cull_tma_t(const SceneView &sc, const DevArgs *args, int view
     cudaGetDevice(&dev);
     const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(attr_devices.load() & bit)) {
-        cudaFuncSetAttribute(k_cull_tma<OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
+        cudaFuncSetAttribute(k_cull_tma<OPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
+        cudaFuncSetAttribute(k_cull_tma<OPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CULL_SMEM);
         attr_devices.fetch_or(bit);
     }
     const int64_t nchunks = (sc.n + CHUNK - 1) / CHUNK;
     if (out.umask) cudaMemsetAsync(out.uchunk, 0, (size_t)nchunks * sizeof(uint32_t), s);   // atomics
     if (out.n_cand) cudaMemsetAsync(out.n_cand, 0, sizeof(int), s);
     const int gt = w.grid(nchunks * CT, CT, 4);
-    k_cull_tma<OPT><<<gt, CT, CULL_SMEM, s>>>(sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out,
-                                              w.status, w.cull_first_wait);
+    (nv == 1 ? k_cull_tma<OPT, true> : k_cull_tma<OPT, false>)<<<gt, CT, CULL_SMEM, s>>>(
+        sc.geo, sc.rdir, sc.counter, sc.pitch, sc.n, args, view0, nv, out, w.status, w.cull_first_wait);
 }
 
 // The restore through stored directions differs between optimizers only by
