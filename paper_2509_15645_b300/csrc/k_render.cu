@@ -1376,7 +1376,9 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
             if (i < 0) continue;
             uint32_t word = rmask[i >> 5];
             kk = rprefix[i >> 5] + __popc(word & ((1u << (i & 31)) - 1u));
-            for (int p = 0; p < prev.n; p++) accumulate |= ((prev.m[p][i >> 5] >> (i & 31)) & 1u) != 0u;
+#pragma unroll
+            for (int p = 0; p < MAX_VIEWS; p++)        // constant indices: the masks stay kernel parameters
+                if (p < prev.n) accumulate |= ((prev.m[p][i >> 5] >> (i & 31)) & 1u) != 0u;
         }
         if (kk >= gcap) {          // the caller's gradient buffer is smaller than the visible set
             latch(status, GS_ERR_CAPACITY);
