@@ -521,7 +521,7 @@ def run_ours(args):
     # dram__bytes_read.sum + dram__bytes_write.sum of the kernels as they are
     # (profiles/launches_aerial10m_1080p.md); variants 8 and 9 changed since
     # their captures (None); other workloads: not captured
-    RASTER_BWD_TRAFFIC = {7: 127.8e6, 8: None, 9: None}
+    RASTER_BWD_TRAFFIC = {7: 127.9e6, 8: None, 9: None}
 
     def roofline(m):
         """Roofline entry of the kernel with the largest live event time per step."""
