@@ -60,8 +60,13 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_gather_project(SceneView sc, con
     __syncthreads();
     const int n_vis = min(*n_vis_p, cap);
     const int64_t pitch = sc.pitch;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_vis; k += gridDim.x * blockDim.x) {
-        const int64_t i = ids[k];
+    const int stride = gridDim.x * blockDim.x;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i_next = k < n_vis ? ids[k] : 0;
+    for (; k < n_vis; k += stride) {
+        // this thread's next id loaded one item ahead (its planes' loads wait on it)
+        const int64_t i = i_next;
+        if (k + stride < n_vis) i_next = ids[k + stride];
         if (i < 0 || i >= sc.n) {           // caller-supplied id out of range: an empty splat
             rec0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             rec1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
