@@ -1373,6 +1373,18 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
     const int n_items = FIX ? min(*n_fix, n_vis) : n_vis;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_items; j += gridDim.x * blockDim.x) {
         const int k = FIX ? fix_idx[j] : j;
+        // the splat's loads are issued before the flag that may skip it arrives
+        float g[N_GEO];
+#pragma unroll
+        for (int r = 0; r < N_GEO; r++) g[r] = compact[r * (int64_t)cap + k];
+        float gs[9];
+        {
+            const float4 *row = reinterpret_cast<const float4 *>(g9 + (int64_t)k * G9_STRIDE);
+            const float4 a = row[0], b = row[1];
+            gs[0] = a.x; gs[1] = a.y; gs[2] = a.z; gs[3] = a.w;
+            gs[4] = b.x; gs[5] = b.y; gs[6] = b.z; gs[7] = b.w;
+            gs[8] = g9[(int64_t)k * G9_STRIDE + 8];
+        }
         if (!FIX && fix_flag[k]) continue;
         int64_t kk = k;
         bool accumulate = false;                   // an earlier view of the step wrote this row
@@ -1388,17 +1400,6 @@ __global__ void __launch_bounds__(PROJ_BLOCK) k_project_bwd(const float *__restr
         if (kk >= gcap) {          // the caller's gradient buffer is smaller than the visible set
             latch(status, GS_ERR_CAPACITY);
             continue;
-        }
-        float g[N_GEO];
-#pragma unroll
-        for (int r = 0; r < N_GEO; r++) g[r] = compact[r * (int64_t)cap + k];
-        float gs[9];
-        {
-            const float4 *row = reinterpret_cast<const float4 *>(g9 + (int64_t)k * G9_STRIDE);
-            const float4 a = row[0], b = row[1];
-            gs[0] = a.x; gs[1] = a.y; gs[2] = a.z; gs[3] = a.w;
-            gs[4] = b.x; gs[5] = b.y; gs[6] = b.z; gs[7] = b.w;
-            gs[8] = g9[(int64_t)k * G9_STRIDE + 8];
         }
         Proj P;
         project_gaussian<FIX>(g, cam, P);   // as in the forward (FIX: the FP64 chain)
