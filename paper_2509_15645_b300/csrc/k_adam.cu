@@ -702,6 +702,73 @@ __device__ __forceinline__ void pair_step_bf16(const PairRows &a, const Planes<_
     }
 }
 
+// bf16 SH planes: four planes per thread, each array's pair of values kept
+// packed (one bf16x2 register) until it is stepped.  The arithmetic of each
+// plane is pair_step_bf16's.
+constexpr int PR_SH16 = 4;
+struct PairRowsSH16 {
+    uint32_t w[PR_SH16], m[PR_SH16], v[PR_SH16];
+    float g[PR_SH16][2];
+    int64_t i0;
+    uint32_t info;
+};
+
+template <int OPT>
+__device__ __forceinline__ void pair_fetch_sh16(PairRowsSH16 &a, int j, const int32_t *__restrict__ pids,
+                                                const uint32_t *__restrict__ pinfo,
+                                                const Planes<__nv_bfloat16> &P, const uint32_t *__restrict__ vmask,
+                                                const uint32_t *__restrict__ vprefix, const float *__restrict__ grad,
+                                                int64_t gcap, int r0, int rend)
+{
+    a.i0 = 2 * (int64_t)pids[j];
+    a.info = pinfo[j];
+    int k0 = (a.info & (1u << 16)) ? compact_index(vmask, vprefix, a.i0) : -1;
+    int k1 = (a.info & (2u << 16)) ? compact_index(vmask, vprefix, a.i0 + 1) : -1;
+    if (k0 >= gcap) k0 = -1;
+    if (k1 >= gcap) k1 = -1;
+#pragma unroll
+    for (int q = 0; q < PR_SH16; q++) {
+        const int r = r0 + q;
+        if (r < rend) {
+            const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
+            a.w[q] = *reinterpret_cast<const uint32_t *>(P.shw + o);
+            a.m[q] = *reinterpret_cast<const uint32_t *>(P.shm + o);
+            a.v[q] = OPT == GS_OPT_SGDM ? 0u : *reinterpret_cast<const uint32_t *>(P.shv + o);
+            a.g[q][0] = k0 >= 0 ? __ldg(grad + (int64_t)r * gcap + k0) : 0.f;
+            a.g[q][1] = k1 >= 0 ? __ldg(grad + (int64_t)r * gcap + k1) : 0.f;
+        }
+    }
+}
+
+template <int OPT>
+__device__ __forceinline__ void pair_step_sh16(const PairRowsSH16 &a, const Planes<__nv_bfloat16> &P, int r0, int rend,
+                                               const SLut &L, const uint32_t *key)
+{
+    const uint32_t sel = (a.info >> 16) & 3u;
+    const int dd[2] = {(int)(a.info & 255u), (int)((a.info >> 8) & 255u)};
+    const bool st = L.stochastic != 0;
+#pragma unroll
+    for (int q = 0; q < PR_SH16; q++) {
+        const int r = r0 + q;
+        if (r >= rend) continue;
+        const int grp = lr_group(r);
+        float w[2] = {bf16_lo(a.w[q]), bf16_hi(a.w[q])}, m[2] = {bf16_lo(a.m[q]), bf16_hi(a.m[q])};
+        float v[2] = {bf16_lo(a.v[q]), bf16_hi(a.v[q])};
+#pragma unroll
+        for (int e = 0; e < 2; e++)
+            if ((sel >> e) & 1u) adam_value<OPT>(w[e], m[e], v[e], a.g[q][e], dd[e], grp, L);
+        const uint32_t h0 = st ? sr_bits(key[q], (uint32_t)a.i0) : 0u;
+        const uint32_t h1 = st ? sr_bits(key[q], (uint32_t)(a.i0 + 1)) : 0u;
+        const uint32_t pm = bf16x2_round(m[0], m[1], st, (h0 & 0xffffu) | (h1 << 16));
+        const uint32_t pv = OPT == GS_OPT_SGDM ? 0u : bf16x2_round(v[0], v[1], st, (h0 >> 16) | (h1 & 0xffff0000u));
+        const uint32_t pw = bf16x2_round(w[0], w[1], st, (sr_w_bits(h0) & 0xffffu) | (sr_w_bits(h1) << 16));
+        const int64_t o = (int64_t)(r - N_GEO) * P.sp + a.i0;
+        st2p(P.shw + o, pw, sel);
+        st2p(P.shm + o, pm, sel);
+        if (OPT != GS_OPT_SGDM) st2p(P.shv + o, pv, sel);
+    }
+}
+
 template <typename T, bool GEO, int OPT>
 __device__ __forceinline__ void pair_step_any(const PairRows &a, const Planes<T> &P, int r0, int rend, const SLut &L,
                                               const uint32_t *key)
@@ -713,7 +780,10 @@ __device__ __forceinline__ void pair_step_any(const PairRows &a, const Planes<T>
 }
 
 // blockIdx.y: plane groups; the first n_geo_groups cover geometry planes
-// [PR y, PR y + PR) below 11, the rest SH planes 11 + PR (y - n_geo_groups) ...
+// [PR y, PR y + PR) below 11, the rest SH planes 11 + PS (y - n_geo_groups) ...
+// with PS = PR (fp32) or PR_SH16 (bf16).
+template <typename T> __host__ __device__ constexpr int sh_planes_per_thread() { return std::is_same<T, __nv_bfloat16>::value ? PR_SH16 : PR; }
+
 template <typename T, int OPT>
 __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P, int D, const int32_t *__restrict__ pids,
                                                                  const uint32_t *__restrict__ pinfo,
@@ -728,15 +798,28 @@ __global__ void __launch_bounds__(ADAM_BLOCK, 4) k_adam_apply_pairs(Planes<T> P,
     load_slut(L, args->lut);
     const int n_pairs = *n_pairs_p;
     constexpr int GEO_GROUPS = (N_GEO + PR - 1) / PR;
+    constexpr int PS = sh_planes_per_thread<T>();
     const bool geo = blockIdx.y < GEO_GROUPS;
-    const int r0 = geo ? (int)blockIdx.y * PR : N_GEO + ((int)blockIdx.y - GEO_GROUPS) * PR;
+    const int r0 = geo ? (int)blockIdx.y * PR : N_GEO + ((int)blockIdx.y - GEO_GROUPS) * PS;
     const int rend = geo ? N_GEO : D;
     const int stride = gridDim.x * blockDim.x;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_pairs) return;
-    uint32_t key[PR];
+    uint32_t key[PS];
 #pragma unroll
-    for (int q = 0; q < PR; q++) key[q] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + q)) : 0u;
+    for (int q = 0; q < PS; q++) key[q] = L.stochastic ? sr_plane_key(L.seed, L.step, (uint32_t)(r0 + q)) : 0u;
+    if constexpr (PS == PR_SH16) {
+        if (!geo) {
+            // four planes' loads in flight per pair (as many as the fp32 form's two planes of this pair
+            // and the next): no prefetch of the next pair
+            for (; j < n_pairs; j += stride) {
+                PairRowsSH16 c16;
+                pair_fetch_sh16<OPT>(c16, j, pids, pinfo, P, vmask, vprefix, grad, gcap, r0, rend);
+                pair_step_sh16<OPT>(c16, P, r0, rend, L, key);
+            }
+            return;
+        }
+    }
     PairRows cur, nxt;
     // the first plane group clears the members' counters (when the pair
     // preparation left them)
@@ -795,7 +878,8 @@ static void pairs_apply(const SceneView &sc, const DevArgs *args, const uint32_t
                         cudaStream_t s)
 {
     constexpr int GEO_GROUPS = (N_GEO + PR - 1) / PR;
-    const int groups = GEO_GROUPS + (sc.D - N_GEO + PR - 1) / PR;
+    const int ps = sc.prec == GS_FP32 ? sh_planes_per_thread<float>() : sh_planes_per_thread<__nv_bfloat16>();
+    const int groups = GEO_GROUPS + (sc.D - N_GEO + ps - 1) / ps;
     dim3 grid(w.grid(sc.n, ADAM_BLOCK, 32) / groups + 1, groups);
     w.mark(TP_APPLY0, s);
     with_opt(sc.opt, [&](auto o) {
